@@ -1,0 +1,181 @@
+"""FP64 CPU oracle for the vector reserve recurrence (Tucker & Bull, arXiv 1401.1757).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import this package.  The CUDA library and its
+Python binding never import it, and it imports nothing from them.
+
+The arithmetic lives in ``rsv_oracle.c`` (plain C99, FP64, no fused
+multiply-add); this module compiles it with gcc on first use and marshals NumPy
+arrays through ctypes.  See the C file for what each function computes and
+which passage of the paper it follows.  Every function is pinned by the CPU
+tests in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = [os.path.join(_HERE, "rsv_oracle.c"), os.path.join(_HERE, "rsv_nested_oracle.c")]
+_LIB_PATH = os.path.join(_HERE, "_build", "librsv_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SL_ANNUITY, JL_REVERSIONARY, TERM_ASSURANCE, ENDOWMENT = 0, 1, 2, 3
+
+CFLAGS = ["-std=gnu99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle library with gcc (idempotent).  Returns its path."""
+    srcs = [s for s in _SRC if os.path.exists(s)]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, *srcs, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def use_library(path=None):
+    """Load the oracle from ``path`` instead of the default build (None: back to the
+    default).  Used by the mutation tests, which compile deliberately broken copies
+    of the oracle source to show that the pins catch them."""
+    global _lib
+    with _lock:
+        _lib = None
+    if path is not None:
+        _load(path)
+
+
+def _load(path=None):
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(path or build())
+            i32, i64, dp, ip = C.c_int32, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int32)
+            lib.orc_n_states.argtypes = [C.c_int]
+            lib.orc_transition.argtypes = [C.c_int, C.c_double, C.c_double, dp]
+            lib.orc_cashflow.argtypes = [C.c_int, C.c_double, C.c_double, dp]
+            lib.orc_steps.argtypes = [C.c_int] * 6 + [C.c_double, dp]
+            lib.orc_chain.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                      C.c_int, dp, dp, dp, dp, C.c_int, dp, dp, C.c_int, C.c_int, dp]
+            lib.orc_reserves_batch.argtypes = [i64, ip, ip, ip, ip, ip, ip, ip, dp, dp,
+                                               i32, i32, dp, i32, i32, dp, i32, i32, dp, dp]
+            lib.orc_max_threads.restype = C.c_int
+            if hasattr(lib, "orc_nested_node"):
+                _bind_nested(lib)
+            _lib = lib
+    return _lib
+
+
+def _bind_nested(lib):
+    dp, ip, u64 = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_uint64
+    lib.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+    lib.orc_gauss_pair.argtypes = [u64, C.c_uint32, C.c_uint32, C.c_uint32, dp]
+    lib.orc_vasicek_path.argtypes = [u64, C.c_uint32, C.c_uint32, C.c_double, C.c_double, C.c_double,
+                                     C.c_double, C.c_double, C.c_int, dp, dp]
+    lib.orc_nested_node.argtypes = [C.c_int64, ip, ip, C.POINTER(C.c_double), C.c_int32, C.c_int32, dp,
+                                    u64, C.c_uint32, C.c_int32, C.c_int32, C.c_double, C.c_double,
+                                    C.c_double, C.c_double, C.c_int32, C.c_int32, C.POINTER(C.c_int32),
+                                    C.c_int32, C.c_int32, dp]
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _p(a, t=C.c_double):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def n_states(product: int) -> int:
+    return _load().orc_n_states(product)
+
+
+def transition(product: int, px: float, py: float = 0.0) -> np.ndarray:
+    """Full-state W (row = state at the start, column = state at the end)."""
+    n = n_states(product)
+    W = np.zeros(n * n)
+    _load().orc_transition(product, px, py, _p(W))
+    return W.reshape(n, n)
+
+
+def cashflow(product: int, amount: float, rho: float = 0.0) -> np.ndarray:
+    n = n_states(product)
+    c = np.zeros(n)
+    _load().orc_cashflow(product, amount, rho, _p(c))
+    return c
+
+
+def steps(product: int, age1: int, age2: int, term: int, n_ages: int, horizon: int = 0,
+          amount: float = 1.0):
+    """(S, boundary vector r_S) of a policy."""
+    rS = np.zeros(4)
+    S = _load().orc_steps(product, age1, age2, term, n_ages, horizon, amount, _p(rS))
+    return S, rS[: n_states(product)].copy()
+
+
+def chain(product: int, age1: int, amount: float, table_x, v, *, age2: int = 0, term: int = 0,
+          rho: float = 0.0, table_y=None, table_fx=None, table_fy=None, vf=None, horizon: int = 0,
+          method: str = "recurrence") -> np.ndarray:
+    """Reserve vectors r_t, t = 0..S, of one policy under one discount sequence.
+
+    Returns an array [S+1, n] (full state space).  ``table_fx``/``table_fy`` and
+    ``vf`` give survival and discounting over the fraction f of a step; they
+    default to the one-step ones (f = 1).
+    """
+    lib = _load()
+    tx = _d(table_x)
+    ty = _d(table_y) if table_y is not None else tx
+    tfx = _d(table_fx) if table_fx is not None else tx
+    tfy = _d(table_fy) if table_fy is not None else (ty if table_fx is None else tfx)
+    v = _d(v)
+    vf = _d(vf) if vf is not None else v
+    n = n_states(product)
+    out = np.zeros((len(v) + 1) * n)
+    m = {"recurrence": 0, "summation": 1}[method]
+    S = lib.orc_chain(product, age1, age2, term, amount, rho, len(tx), _p(tx), _p(ty), _p(tfx),
+                      _p(tfy), len(v), _p(v), _p(vf), horizon, m, _p(out))
+    if S < 0:
+        raise ValueError(f"orc_chain failed with code {S}")
+    return out[: (S + 1) * n].reshape(S + 1, n)
+
+
+def reserves_batch(pol: dict, tables, v, horizon: int = 0, nthreads: int = 0, totals: bool = True):
+    """V0[p, s] (FP64) of every policy in every scenario, f = 1, by the recurrence.
+
+    ``pol`` is a dict of arrays as made by ``synth``; ``tables`` is [n_tables,
+    n_ages] or [n_ages]; ``v`` is [n_scen, n_steps].  Returns (V0, scen_total).
+    """
+    lib = _load()
+    tables = np.atleast_2d(_d(tables))
+    v = np.atleast_2d(_d(v))
+    n = len(pol["product"])
+    V0 = np.zeros((n, v.shape[0]))
+    tot = np.zeros(v.shape[0]) if totals else None
+    a = {k: _i(pol[k]) for k in ("product", "age1_m", "age2_m", "term_m", "state0", "table1", "table2")}
+    amount, rho = _d(pol["amount"]), _d(pol["reversion"])
+    st = lib.orc_reserves_batch(n, _p(a["product"], C.c_int32), _p(a["age1_m"], C.c_int32),
+                                _p(a["age2_m"], C.c_int32), _p(a["term_m"], C.c_int32),
+                                _p(a["state0"], C.c_int32), _p(a["table1"], C.c_int32),
+                                _p(a["table2"], C.c_int32), _p(amount), _p(rho),
+                                tables.shape[0], tables.shape[1], _p(tables), v.shape[0], v.shape[1],
+                                _p(v), horizon, nthreads, _p(V0), _p(tot) if totals else None)
+    if st != 0:
+        raise ValueError(f"orc_reserves_batch failed with code {st}")
+    return V0, tot
+
+
+def max_threads() -> int:
+    return _load().orc_max_threads()

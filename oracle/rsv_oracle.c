@@ -1,0 +1,295 @@
+/*
+ * rsv_oracle.c -- plain FP64 CPU oracle for the vector reserve recurrence of
+ * M. Tucker and J. M. Bull, "An efficient algorithm for the calculation of
+ * reserves for non-unit linked life policies" (arXiv 1401.1757).
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this library.  The CUDA library never
+ * calls it and the two share no code, headers or tables.
+ *
+ * What it computes, in the paper's notation (Section 3):
+ *   - full-state Markov transition matrices W_{x,t,g} of the use cases in
+ *     Section 4 (row j = state at the start of the step, column i = state at
+ *     t+g; rows sum to one; "0 = alive" labelling makes them upper triangular);
+ *   - the cash-flow vectors c_{x,t} of the four products;
+ *   - the reserve vector r_{x,t} for every t, two independent ways:
+ *       (a) backward substitution of Eq. (generalForm),
+ *             r_t = v_t^f W_{t,f} c_t + v_t W_{t,1} r_{t+1},
+ *           from the boundary vector r_S (Section 3.8.2);
+ *       (b) the prospective-reserve definition, Eq. (basicReserveSummation),
+ *             r_{t,j} = sum_{s>=t} d(t, s+f) sum_i w(t, s+f)_{j,i} c_{s,i},
+ *           with multi-step discount factors and transition probabilities
+ *           built from one-step ones by Eqs. (recRel_Discounts) and
+ *           (recRel_Probabilities) (Section 3.6.1).  O(S^2).
+ * No state is removed (no zero-reserve-state reduction, Section 3.6.4): the
+ * full vector is returned, and zero-reserve states come out as zeros.
+ *
+ * Every function is pinned by the CPU tests (closed forms under a flat rate
+ * and constant force, brute-force enumeration over death times on tiny
+ * inputs, recurrence == summation, the paper's printed scalar recurrences,
+ * and the structural invariants of W and r).
+ *
+ * Build: plain C99, -O2 -ffp-contract=off (no fused multiply-add, so the
+ * same IEEE double operations run on x86-64 and AArch64), OpenMP optional.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_MAXN 4
+
+enum { ORC_SL_ANNUITY = 0, ORC_JL_REVERSIONARY = 1, ORC_TERM_ASSURANCE = 2, ORC_ENDOWMENT = 3 };
+
+/* Number of survival states of the product's full model (Section 4):
+ * single life alive/dead (4.1), single life alive/died-in-step/dead for
+ * assurances (4.1.3), two lives 00/01/10/11 (4.2). */
+int orc_n_states(int product)
+{
+    switch (product) {
+    case ORC_SL_ANNUITY: return 2;
+    case ORC_JL_REVERSIONARY: return 4;
+    case ORC_TERM_ASSURANCE:
+    case ORC_ENDOWMENT: return 3;
+    default: return -1;
+    }
+}
+
+/* W_{x,t,g} for survival probabilities px = gp_x (and py = gp_y for two
+ * lives) over the interval of length g.  Row-major n x n, W[j*n + i] =
+ * w_{j,i} = Pr[state i at t+g | state j at t]. */
+int orc_transition(int product, double px, double py, double *W)
+{
+    int n = orc_n_states(product);
+    if (n < 0) return -1;
+    double qx = 1.0 - px, qy = 1.0 - py;
+    for (int k = 0; k < n * n; ++k) W[k] = 0.0;
+    if (product == ORC_SL_ANNUITY) {            /* Eq. (two state, single life) */
+        W[0 * 2 + 0] = px; W[0 * 2 + 1] = qx;
+        W[1 * 2 + 1] = 1.0;
+    } else if (product == ORC_JL_REVERSIONARY) {  /* Section 4.2, binary labels */
+        W[0 * 4 + 0] = px * py; W[0 * 4 + 1] = px * qy; W[0 * 4 + 2] = qx * py; W[0 * 4 + 3] = qx * qy;
+        W[1 * 4 + 1] = px; W[1 * 4 + 3] = qx;
+        W[2 * 4 + 2] = py; W[2 * 4 + 3] = qy;
+        W[3 * 4 + 3] = 1.0;
+    } else {                                     /* Eq. (three state, single life) */
+        W[0 * 3 + 0] = px; W[0 * 3 + 1] = qx;
+        W[1 * 3 + 2] = 1.0;
+        W[2 * 3 + 2] = 1.0;
+    }
+    return n;
+}
+
+/* Nominal cash-flow vector c_{x,t} (paid at t+f according to the state then).
+ *   SL annuity (4.1.1):        (A, 0)
+ *   JL reversionary (4.2.1):   (A, A, rho*A, 0): A while (x) lives, rho*A to (y) after (x) dies
+ *   term / endowment (4.1.3):  (0, A, 0): benefit in the "died in step" state */
+int orc_cashflow(int product, double amount, double rho, double *c)
+{
+    int n = orc_n_states(product);
+    if (n < 0) return -1;
+    for (int k = 0; k < n; ++k) c[k] = 0.0;
+    if (product == ORC_SL_ANNUITY) c[0] = amount;
+    else if (product == ORC_JL_REVERSIONARY) { c[0] = amount; c[1] = amount; c[2] = rho * amount; }
+    else c[1] = amount;
+    return n;
+}
+
+/* Number of projection steps S of a policy and its boundary vector r_S.
+ * Whole-life annuities run to the limiting age: a table of n_ages entries
+ * means p_k = 0 for k >= n_ages, so S = n_ages - (youngest age) (Sections
+ * 4.1.1, 4.2.1: sp_120 = 0).  term_m > 0 limits the term.  Assurances run for
+ * their term.  An endowment pays its sum at maturity if alive: boundary
+ * r_S = (A, 0, 0) (Section 4.1.2, A_{x+n:0} = 1).  A horizon > 0 truncates
+ * the projection with r_horizon = 0, dropping later cash flows. */
+int orc_steps(int product, int age1, int age2, int term, int n_ages, int horizon,
+              double amount, double *rS)
+{
+    int n = orc_n_states(product), S;
+    if (n < 0) return -1;
+    if (product == ORC_SL_ANNUITY || product == ORC_JL_REVERSIONARY) {
+        int young = (product == ORC_JL_REVERSIONARY && age2 < age1) ? age2 : age1;
+        S = n_ages - young;
+        if (S < 0) S = 0;
+        if (term > 0 && term < S) S = term;
+    } else {
+        S = term;
+    }
+    for (int k = 0; k < n; ++k) rS[k] = 0.0;
+    if (horizon > 0 && horizon < S) {
+        S = horizon;                          /* truncated: r_S = 0 */
+    } else if (product == ORC_ENDOWMENT) {
+        rS[0] = amount;
+    }
+    return S;
+}
+
+static double table_at(const double *tab, int n_ages, int k)
+{
+    return (k >= 0 && k < n_ages) ? tab[k] : 0.0;
+}
+
+/* y = W x  (n x n times n) */
+static void matvec(int n, const double *W, const double *x, double *y)
+{
+    for (int j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += W[j * n + i] * x[i];
+        y[j] = s;
+    }
+}
+
+/* C = A B  (n x n) */
+static void matmul(int n, const double *A, const double *B, double *C)
+{
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) s += A[j * n + k] * B[k * n + i];
+            C[j * n + i] = s;
+        }
+}
+
+/* One chain (one policy under one discount sequence), every t.
+ *
+ * p1x/p1y: one-step survival tables of the two lives (p1y unused for one
+ * life), indexed by age in months; pfx/pfy: survival over the fraction f of
+ * the step (equal to p1x/p1y when f = 1).  v[t]: discount factor over step t;
+ * vf[t]: discount from t to t+f (v^f; equal to v when f = 1).
+ * method 0: backward recurrence, Eq. (generalForm); method 1: summation,
+ * Eq. (basicReserveSummation).
+ * r_out[(S+1) * n] receives r_t for t = 0..S (r_S is the boundary).
+ * Returns S, or a negative code: -1 bad product, -2 scenario too short. */
+int orc_chain(int product, int age1, int age2, int term, double amount, double rho,
+              int n_ages, const double *p1x, const double *p1y,
+              const double *pfx, const double *pfy,
+              int n_steps, const double *v, const double *vf,
+              int horizon, int method, double *r_out)
+{
+    double rS[ORC_MAXN], c[ORC_MAXN];
+    int n = orc_n_states(product);
+    if (n < 0) return -1;
+    int S = orc_steps(product, age1, age2, term, n_ages, horizon, amount, rS);
+    if (S > n_steps) return -2;
+    orc_cashflow(product, amount, rho, c);
+    for (int j = 0; j < n; ++j) r_out[S * n + j] = rS[j];
+
+    if (method == 0) {
+        double W1[ORC_MAXN * ORC_MAXN], Wf[ORC_MAXN * ORC_MAXN], a[ORC_MAXN], b[ORC_MAXN];
+        for (int t = S - 1; t >= 0; --t) {
+            orc_transition(product, table_at(p1x, n_ages, age1 + t),
+                           p1y ? table_at(p1y, n_ages, age2 + t) : 0.0, W1);
+            orc_transition(product, table_at(pfx, n_ages, age1 + t),
+                           pfy ? table_at(pfy, n_ages, age2 + t) : 0.0, Wf);
+            matvec(n, Wf, c, a);                          /* W_{t,f} c_t     */
+            matvec(n, W1, &r_out[(t + 1) * n], b);        /* W_{t,1} r_{t+1} */
+            for (int j = 0; j < n; ++j) r_out[t * n + j] = vf[t] * a[j] + v[t] * b[j];
+        }
+        return S;
+    }
+
+    /* Summation: for each t, walk s = t..S-1 keeping the running products
+     * prod_{u=t}^{s-1} v_u and prod_{u=t}^{s-1} W_{u,1}. */
+    double M[ORC_MAXN * ORC_MAXN], M2[ORC_MAXN * ORC_MAXN], W1[ORC_MAXN * ORC_MAXN],
+           Wf[ORC_MAXN * ORC_MAXN], P[ORC_MAXN * ORC_MAXN], a[ORC_MAXN];
+    for (int t = 0; t < S; ++t) {
+        double acc[ORC_MAXN] = {0};
+        double d = 1.0;                                   /* d(t, s) */
+        for (int k = 0; k < n * n; ++k) M[k] = (k / n == k % n) ? 1.0 : 0.0;
+        for (int s = t; s < S; ++s) {
+            orc_transition(product, table_at(p1x, n_ages, age1 + s),
+                           p1y ? table_at(p1y, n_ages, age2 + s) : 0.0, W1);
+            orc_transition(product, table_at(pfx, n_ages, age1 + s),
+                           pfy ? table_at(pfy, n_ages, age2 + s) : 0.0, Wf);
+            matmul(n, M, Wf, P);                          /* w(t, s+f) */
+            matvec(n, P, c, a);
+            for (int j = 0; j < n; ++j) acc[j] += d * vf[s] * a[j];
+            matmul(n, M, W1, M2);                         /* w(t, s+1) */
+            memcpy(M, M2, sizeof(double) * n * n);
+            d *= v[s];                                    /* d(t, s+1) */
+        }
+        /* the boundary vector r_S acts as a cash flow at time S */
+        matvec(n, M, rS, a);
+        for (int j = 0; j < n; ++j) r_out[t * n + j] = acc[j] + d * a[j];
+    }
+    return S;
+}
+
+/* Reserves at valuation for a whole portfolio under n_scen scenarios, f = 1,
+ * by the backward recurrence (method 0 of orc_chain).
+ *
+ * Policies are given as arrays (structure of arrays).  tables[n_tables *
+ * n_ages] holds one-step survival p_k per table.  v[n_scen * n_steps] holds
+ * the per-step discount factors of each scenario.  V0[p * n_scen + s]
+ * receives the reserve of policy p in its valuation state state0[p];
+ * scen_total[s] (optional) the sum of V0 over policies, summed in policy
+ * order.  nthreads <= 0 uses the OpenMP default; policies are shared among
+ * threads with a dynamic schedule.  Returns 0, or -1 bad record, -2 a
+ * scenario shorter than a policy's projection. */
+int orc_reserves_batch(int64_t n_pol, const int32_t *product, const int32_t *age1,
+                       const int32_t *age2, const int32_t *term, const int32_t *state0,
+                       const int32_t *tab1, const int32_t *tab2,
+                       const double *amount, const double *rho,
+                       int32_t n_tables, int32_t n_ages, const double *tables,
+                       int32_t n_scen, int32_t n_steps, const double *v,
+                       int32_t horizon, int32_t nthreads,
+                       double *V0, double *scen_total)
+{
+    int status = 0;
+    (void)nthreads;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        double *r = (double *)malloc(sizeof(double) * ORC_MAXN * ((size_t)n_steps + 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (int64_t p = 0; p < n_pol; ++p) {
+            int n = orc_n_states(product[p]);
+            if (!r || n < 0 || tab1[p] < 0 || tab1[p] >= n_tables || tab2[p] < 0 ||
+                tab2[p] >= n_tables || state0[p] < 0 || state0[p] >= n) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+                status = -1;
+                continue;
+            }
+            const double *tx = tables + (size_t)tab1[p] * n_ages;
+            const double *ty = tables + (size_t)tab2[p] * n_ages;
+            for (int32_t s = 0; s < n_scen; ++s) {
+                const double *vs = v + (size_t)s * n_steps;
+                int S = orc_chain(product[p], age1[p], age2[p], term[p], amount[p], rho[p],
+                                  n_ages, tx, ty, tx, ty, n_steps, vs, vs, horizon, 0, r);
+                if (S < 0) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+                    status = S;
+                    V0[p * n_scen + s] = 0.0;
+                    continue;
+                }
+                V0[p * n_scen + s] = r[state0[p]];
+            }
+        }
+        free(r);
+    }
+    if (status == 0 && scen_total) {
+        for (int32_t s = 0; s < n_scen; ++s) scen_total[s] = 0.0;
+        for (int64_t p = 0; p < n_pol; ++p)
+            for (int32_t s = 0; s < n_scen; ++s) scen_total[s] += V0[p * n_scen + s];
+    }
+    return status;
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,68 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case copies ``oracle/rsv_oracle.c``, plants one mistake (a transposed
+matrix entry, an age or step index off by one, a dropped term, a wrong sign, a
+wrong boundary or cash flow), compiles the copy on the CPU and runs the pin
+checks of ``test_oracle_pins`` against it.  At least one pin has to fail for
+every mutant.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import tests.test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "rsv_oracle.c")
+
+MUTANTS = {
+    "transposed_two_life_entries": ("W[0 * 4 + 1] = px * qy; W[0 * 4 + 2] = qx * py;",
+                                    "W[0 * 4 + 1] = qx * py; W[0 * 4 + 2] = px * qy;"),
+    "age_index_off_by_one": ("orc_transition(product, table_at(p1x, n_ages, age1 + t),",
+                             "orc_transition(product, table_at(p1x, n_ages, age1 + t + 1),"),
+    "dropped_continuation": ("r_out[t * n + j] = vf[t] * a[j] + v[t] * b[j];",
+                             "r_out[t * n + j] = vf[t] * a[j] + b[j];"),
+    "wrong_sign_q": ("double qx = 1.0 - px, qy = 1.0 - py;", "double qx = px - 1.0, qy = 1.0 - py;"),
+    "endowment_boundary": ("rS[0] = amount;", "rS[0] = 0.0;"),
+    "steps_off_by_one": ("S = n_ages - young;", "S = n_ages - young - 1;"),
+    "discount_index": ("r_out[t * n + j] = vf[t] * a[j] + v[t] * b[j];",
+                       "r_out[t * n + j] = vf[t] * a[j] + v[t + 1] * b[j];"),
+    "reversion_cash_flow": ("c[2] = rho * amount;", "c[2] = amount;"),
+    "summation_discount_order": ("acc[j] += d * vf[s] * a[j];", "acc[j] += d * a[j];"),
+    "summation_matrix_order": ("matmul(n, M, Wf, P);", "matmul(n, Wf, M, P);"),
+}
+
+PIN_CHECKS = [
+    lambda: pins.test_closed_forms_single_life(0.05, 240),
+    lambda: pins.test_closed_forms_two_life(0.5),
+    lambda: pins.test_closed_form_whole_life_to_limiting_age(),
+    lambda: pins.test_brute_force_single_life(0),
+    lambda: pins.test_brute_force_two_life(0),
+    lambda: pins.test_printed_reversionary_recurrence(),
+    lambda: pins.test_printed_assurance_and_endowment_recurrences(),
+    lambda: pins.test_transition_rows_sum_to_one_and_upper_triangular(1),
+    lambda: pins.test_two_life_matrix_entries(),
+]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    mutated = tmp_path / "mut.c"
+    mutated.write_text(src.replace(old, new, 1))
+    lib = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", *oracle.CFLAGS, "-o", str(lib), str(mutated), "-lm"])
+    oracle.use_library(str(lib))
+    caught = []
+    try:
+        for i, check in enumerate(PIN_CHECKS):
+            try:
+                check()
+            except (AssertionError, ValueError):
+                caught.append(i)
+    finally:
+        oracle.use_library(None)
+    assert caught, f"no pin caught mutant {name}"
