@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark: policy-scenario reserve valuations per second on one GB300 (or N).
+
+Workload (one "step"): the 100,000-policy four-product mix (40% single-life
+annuities, 20% joint-life reversionary annuities with 3 states and reversion
+50-100%, 20% term assurances 5-40 y, 20% endowments 10-30 y; ages 20-85) under
+1,000 exact-step Vasicek scenarios (a=0.1, b=0.04, sigma=0.01, r0=0.03) of
+1,200 monthly discount factors: 1e8 policy-scenario chains, the backward
+vector reserve recurrence of every chain to t = 0, the reserves written out
+and the per-scenario portfolio totals summed in FP64.
+
+Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
+launching stream, with a 256 MiB write between steps to flush L2 (the inputs
+are L2-sized).  ``value`` = chains of all ranks / (sum of step times, max over
+ranks).  ``e2e`` times the same step through the C ABI with host buffers: the
+scenario, portfolio and table uploads and the device-to-host copy of every
+reserve are inside the timed region.
+
+``--impl reference`` times the FP64 CPU oracle instead (rank 0, host cores,
+a bounded sample of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "policy-scenario reserve valuations/s (plain vs surrogate) at stated error"
+N_POL, N_SCEN, N_STEPS = 100_000, 1000, 1200
+WORKLOAD = ("100,000-policy mix (40% SL annuities, 20% JL reversionary 3-state, 20% term 5-40y, "
+            "20% endowments 10-30y, ages 20-85) x 1,000 Vasicek scenarios x 1,200 monthly steps")
+
+# FP32 operations per chain-step of each form (add/sub/mul/min/max = 1, FMA = 2),
+# counted from the formulas the kernels evaluate.
+FLOPS = {"f32": {0: 3, 1: 13, 2: 3, 3: 3},
+         "f32comp": {0: 20, 1: 89, 2: 21, 3: 21},
+         "f64": {0: 3, 1: 13, 2: 3, 3: 3}}
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = 2 * FP32_LANES * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 at 2070 MHz
+
+FORMS = {"f64": 0, "f32": 1, "f32comp": 2}
+
+
+def policy_steps(pol, n_ages=1440, horizon=0):
+    """Projection length of each policy (the same rules as the library applies)."""
+    prod, a1, a2, term = pol["product"], pol["age1_m"], pol["age2_m"], pol["term_m"]
+    S = np.where(prod == 0, np.maximum(0, n_ages - a1),
+                 np.where(prod == 1, np.maximum(0, n_ages - np.minimum(a1, a2)), term))
+    S = np.where((prod <= 1) & (term > 0), np.minimum(S, term), S)
+    if horizon > 0:
+        S = np.minimum(S, horizon)
+    return S.astype(np.int64)
+
+
+def algorithmic_flops(pol, form, n_scen):
+    S = policy_steps(pol)
+    return float(sum(FLOPS[form][p] * S[pol["product"] == p].sum() for p in range(4)) * n_scen)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1401_1757_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(form):
+    """DRAM bytes per launch of the recurrence kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "recur_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    e = d.get(form)
+    if not e or e.get("kernel_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.lines, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def reference_arm(args, rank):
+    """The FP64 CPU oracle on the host cores, a bounded sample of the workload per step."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    pol = synth.portfolio_mix(N_POL, seed=0)
+    tab = synth.gm_monthly_survival()
+    v = synth.vasicek_paths(N_SCEN, N_STEPS, seed=0)
+    n_sample = args.ref_policies
+    sub = synth.take(pol, slice(0, n_sample))
+    threads = os.cpu_count() or 1
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.reserves_batch(sub, tab, v, nthreads=threads)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    per = sum(times) / len(times)
+    value = n_sample * N_SCEN / per
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "valuations/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"first {n_sample} policies x {N_SCEN} scenarios per step"},
+            "cpu_baseline": {"value": value, "unit": "valuations/s", "cores": threads, "kind": "oracle",
+                             "sample": f"first {n_sample} of {N_POL} policies x all {N_SCEN} scenarios"},
+            "e2e": {"value": value, "unit": "valuations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(pol, tab, v, n_sample, gpu_rows):
+    """Oracle timed on the host cores on the first n_sample policies x all
+    scenarios; also the max relative error of each GPU form on that sample."""
+    import oracle
+    oracle.build()
+    sub = synth.take(pol, slice(0, n_sample))
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ref, _ = oracle.reserves_batch(sub, tab, v, nthreads=threads)
+    dt = time.perf_counter() - t0
+    errs = {}
+    scale = np.maximum(np.abs(ref), 1e-9 * np.abs(sub["amount"])[:, None])
+    for form, rows in gpu_rows.items():
+        e = np.abs(rows.astype(np.float64) - ref) / scale
+        errs[form] = {"max_rel_err": float(e.max()), "p99_rel_err": float(np.quantile(e, 0.99)),
+                      "median_rel_err": float(np.median(e))}
+    return {"value": n_sample * v.shape[0] / dt, "unit": "valuations/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {n_sample} of {len(pol['product'])} policies x all {v.shape[0]} scenarios "
+                      f"({dt:.1f} s wall)"}, errs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--forms", default="f32comp,f32,f64")
+    ap.add_argument("--cpu-sample", type=int, default=2000, help="policies in the CPU oracle sample")
+    ap.add_argument("--ref-policies", type=int, default=1000, help="policies per reference-arm step")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1401_1757_gb300 import rsv
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    # weak scaling: every rank values the full portfolio under its own scenario set
+    pol = synth.portfolio_mix(N_POL, seed=0)
+    tab = synth.gm_monthly_survival()
+    v = synth.vasicek_paths(N_SCEN, N_STEPS, seed=rank)
+    stream = torch.cuda.current_stream()
+    ctx = rsv.rsv_create(local, stream)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+
+    V0 = torch.empty((N_POL, N_SCEN), dtype=torch.float32, device="cuda")
+    tot = torch.empty(N_SCEN, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    outs = rsv.RSV_OUT_V0 | rsv.RSV_OUT_SCEN_TOTAL
+    forms = [f for f in args.forms.split(",") if f]
+    head = forms[0]
+    results, sample_rows = {}, {}
+    clocks = None
+    for form in forms:
+        fid = FORMS[form]
+        best, tune_ms = rsv.rsv_tune(ctx, fid, reps=1)
+        K = args.steps if form != "f64" else min(args.steps, 3)
+        for _ in range(args.warmup):
+            rsv.rsv_compute_reserves(ctx, fid, outs, on_device=True, V0=V0, scen_total=tot)
+        torch.cuda.synchronize()
+        sampler = None
+        if form == head:
+            sampler = ClockSampler(local)
+            sampler.start()
+            time.sleep(0.5)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = []
+        kern_ms = []
+        t_wall = time.perf_counter()
+        for _ in range(K):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rsv.rsv_compute_reserves(ctx, fid, outs, on_device=True, V0=V0, scen_total=tot)
+            e1.record(stream)
+            evs.append((e0, e1))
+            kern_ms.append(rsv.rsv_last_kernel_ms(ctx))   # waits for this step's kernel
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall
+        if world > 1:
+            dist.barrier()
+        if sampler:
+            clocks = sampler.stop()
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        total_ms = sum(step_ms)
+        if world > 1:
+            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        per_ms = total_ms / K
+        chains = N_POL * N_SCEN
+        results[form] = {
+            "valuations_s": world * chains / (per_ms / 1e3),
+            "ms_per_step": per_ms, "kernel_ms": statistics.mean(kern_ms), "steps": K,
+            "variant": rsv.rsv_variant_name(fid, best),
+            "tune_ms": {rsv.rsv_variant_name(fid, i): round(m, 3) for i, m in enumerate(tune_ms)},
+            "wall_s_incl_flush": wall,
+        }
+        sample_rows[form] = V0[: args.cpu_sample].cpu().numpy()
+
+    # end to end through the C ABI with host buffers (head form)
+    e2e = None
+    if not args.no_e2e:
+        fid = FORMS[head]
+        v_host = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+        recs = rsv.policy_records(pol)
+        V0_host = torch.empty((N_POL, N_SCEN), dtype=torch.float32).pin_memory()
+        tot_host = torch.empty(N_SCEN, dtype=torch.float64).pin_memory()
+        V0n, totn = V0_host.numpy(), tot_host.numpy()
+
+        def e2e_step():
+            rsv.rsv_load_decrements(ctx, 0, tab)
+            rsv.rsv_load_scenarios(ctx, v_host)
+            rsv.rsv_load_portfolio(ctx, recs)
+            rsv.rsv_compute_reserves(ctx, fid, outs, on_device=False, V0=V0n, scen_total=totn)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        if world > 1:
+            dist.barrier()
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            e2e_step()
+            times.append(time.perf_counter() - t0)
+        tot_s = sum(times)
+        if world > 1:
+            t = torch.tensor([tot_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot_s = float(t.item())
+        e2e = {"value": world * N_POL * N_SCEN * args.steps / tot_s, "unit": "valuations/s",
+               "h2d_bytes_per_step": int(v.nbytes + recs.nbytes + tab.nbytes),
+               "d2h_bytes_per_step": int(V0_host.numel() * 4 + tot_host.numel() * 8),
+               "ms_per_step": 1e3 * tot_s / args.steps}
+
+    rsv.rsv_destroy(ctx)
+    if rank != 0:
+        return
+
+    cpu, errs = (None, {})
+    if not args.no_cpu:
+        cpu, errs = cpu_baseline(pol, tab, v, args.cpu_sample, sample_rows)
+    for f in results:
+        results[f].update(errs.get(f, {}))
+
+    h = results[head]
+    flops = algorithmic_flops(pol, head, N_SCEN)
+    achieved = flops / (h["kernel_ms"] / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": measured_traffic(head),
+            "kernel": f"recur_kernel ({h['variant']})",
+            "peak_note": "FP32 FMA pipe, 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal units x max clock)",
+            "flops_per_launch": flops}
+    line = {
+        "metric": METRIC, "value": h["valuations_s"], "unit": "valuations/s", "n_gpus": world,
+        "steps": h["steps"], "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-compensated" if head == "f32comp" else head,
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "policies": N_POL, "scenarios": N_SCEN, "steps": N_STEPS,
+                   "form": head, "variant": h["variant"], "l2": "flushed between timed steps (256 MiB write)",
+                   "scenario_seed": "rank"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 3 * h["steps"],
+        "clocks": clocks,
+        "forms": results,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * rsv.h -- C ABI of the GB300 reserve library.
+ *
+ * The library evaluates the vector reserve recurrence of Tucker & Bull,
+ * "An efficient algorithm for the calculation of reserves for non-unit
+ * linked life policies" (arXiv 1401.1757), Eq. (generalForm):
+ *
+ *     r_{x,t} = v_t^f W_{x,t,f} c_{x,t} + v_t W_{x,t,1} r_{x+1,t},
+ *
+ * by backward substitution from a boundary vector (Section 3.8.2), for every
+ * policy x scenario of a portfolio, with f = 1 (cash flows at the end of each
+ * monthly step), after the zero-reserve states of each product are removed
+ * (Section 3.6.4).  Products (Section 4):
+ *
+ *   RSV_SL_ANNUITY       level single-life annuity, 1 reduced state
+ *                        (Section 4.1.1: r = v p (A + r')).
+ *   RSV_JL_REVERSIONARY  joint-life annuity paying A while the first life
+ *                        lives and rho*A to the second life after the first
+ *                        dies; two-life binary-labelled model of Section 4.2
+ *                        with state 11 removed: 3 reduced states 00, 01, 10.
+ *   RSV_TERM_ASSURANCE   level term assurance, benefit at the end of the month
+ *                        of death; three-state model of Section 4.1.3 reduced
+ *                        to 1 state: r = v (q S + p r').
+ *   RSV_ENDOWMENT        endowment assurance: the term assurance plus the sum
+ *                        at maturity if alive (Section 4.1.2 boundary
+ *                        A_{x+n:0} = 1).
+ *
+ * Conventions shared by every entry point:
+ *  - Status codes only; no C++ exception crosses the ABI.  On failure the
+ *    context keeps a message, read with rsv_last_error().
+ *  - Every rsv_load_* copies its input: the caller may free it on return.
+ *  - Output buffers are owned and sized by the caller.
+ *  - A context is used by one host thread at a time.
+ *  - Ages are whole months; one projection step is one month; table entry k
+ *    is the probability of surviving one month from age k months.  Ages at or
+ *    beyond a table's length have survival probability 0 (the limiting age,
+ *    Sections 4.1.1 and 4.2.1).
+ *  - The paper's assumptions (Section 3.7) are checked and reported as
+ *    RSV_E_ASSUMPTION: survival probabilities in [0, 1], discount factors
+ *    finite and > 0, reversion in [0, 1], scenarios at least as long as every
+ *    projection, finite amounts.
+ */
+#ifndef RSV_H
+#define RSV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsv_ctx rsv_ctx;
+
+typedef enum {
+    RSV_OK = 0,
+    RSV_E_ARG = -1,        /* bad argument, size or pointer                          */
+    RSV_E_NOMEM = -2,      /* device or host allocation failed                       */
+    RSV_E_CUDA = -3,       /* a CUDA call failed (message in rsv_last_error)         */
+    RSV_E_STATE = -4,      /* call order: e.g. compute before the data is loaded     */
+    RSV_E_TIMEOUT = -5,    /* a bounded device-side wait ran out                      */
+    RSV_E_ASSUMPTION = -6  /* input breaks an assumption of Section 3.7              */
+} rsv_status;
+
+enum { RSV_SL_ANNUITY = 0, RSV_JL_REVERSIONARY = 1, RSV_TERM_ASSURANCE = 2, RSV_ENDOWMENT = 3 };
+
+/* Arithmetic of the recurrence. */
+enum {
+    RSV_FORM_F64 = 0,      /* plain FP64 on the GPU                                  */
+    RSV_FORM_F32 = 1,      /* plain FP32                                              */
+    RSV_FORM_F32_COMP = 2  /* FP32 with compensated (double-float) accumulation and
+                              hi/lo-split inputs                                      */
+};
+
+/* rsv_opts.outputs bits */
+enum {
+    RSV_OUT_V0 = 1,         /* reserve at valuation of every policy x scenario        */
+    RSV_OUT_SCEN_TOTAL = 2, /* per-scenario portfolio total, FP64, fixed summation order */
+    RSV_OUT_PT_MEAN = 4,    /* per-(policy, step) mean over scenarios, FP64            */
+    RSV_OUT_TRAJ = 8        /* full trajectory r_t of every chain (small runs only)    */
+};
+
+/* One policy record (48 bytes). */
+typedef struct {
+    int32_t product;   /* RSV_SL_ANNUITY .. RSV_ENDOWMENT                              */
+    int32_t age1_m;    /* age of the (first) life at valuation, whole months >= 0      */
+    int32_t age2_m;    /* age of the second life; RSV_JL_REVERSIONARY only             */
+    int32_t term_m;    /* term in months; 0 = whole life (annuities only); assurances
+                          and endowments need term_m >= 0                              */
+    int32_t state0;    /* reduced state at valuation: 0 for every product; the JL
+                          product also accepts 1 (only the first life alive) and 2
+                          (only the second life alive)                                 */
+    int32_t table1;    /* decrement table of the first life                            */
+    int32_t table2;    /* decrement table of the second life (JL only)                 */
+    int32_t reserved;  /* must be 0                                                    */
+    double amount;     /* annuity amount per monthly step, or sum assured              */
+    double reversion;  /* rho in [0, 1]; RSV_JL_REVERSIONARY only                      */
+} rsv_policy;
+
+typedef struct {
+    int32_t form;      /* RSV_FORM_*                                                   */
+    int32_t outputs;   /* RSV_OUT_* bits                                               */
+    int32_t horizon;   /* > 0: truncate every projection at this many steps with
+                          r_horizon = 0 (later cash flows dropped); 0 = none           */
+    int32_t on_device; /* 1: output pointers are device pointers and the call is
+                          asynchronous on the context stream; 0: host pointers, the
+                          call blocks until the results are in host memory            */
+    int32_t variant;   /* kernel variant index, -1 = the tuned/default one (see
+                          rsv_variant_count / rsv_tune)                                */
+    int32_t reserved[3];
+} rsv_opts;
+
+/* Outputs of rsv_compute_reserves.  Any pointer may be NULL when its bit is
+ * clear.  Layouts (n = portfolio size, S = n_scen, T = n_steps):
+ *   V0 / V0d     [n][S]        float / double; the reserve in the policy's
+ *                              valuation state; either or both may be given
+ *   scen_total   [S]           double; sum of V0 over the portfolio
+ *   pt_mean      [n][T + 1]    double; mean over scenarios of r_t in state0,
+ *                              t = 0..T (entries past a policy's term are its
+ *                              boundary value or 0)
+ *   traj         [n][T + 1][S] double; r_t in state0 of every chain
+ */
+typedef struct {
+    float *V0;
+    double *V0d;
+    double *scen_total;
+    double *pt_mean;
+    double *traj;
+} rsv_out;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  The stream is not owned.
+ * Errors: RSV_E_ARG (out NULL), RSV_E_CUDA (device unusable). */
+rsv_status rsv_create(rsv_ctx **out, int device, void *cuda_stream);
+
+/* Release every device buffer of the context and the context itself.
+ * Synchronizes the context stream first.  NULL is accepted. */
+rsv_status rsv_destroy(rsv_ctx *ctx);
+
+/* Change the stream later calls are issued on (not owned). */
+rsv_status rsv_set_stream(rsv_ctx *ctx, void *cuda_stream);
+
+/* Load decrement table `table_id` (0 <= id < 8): p_monthly[k] = probability
+ * of surviving one month from age k months, k = 0..n_ages_m-1 (host FP64,
+ * copied).  Survival is 0 from age n_ages_m on.  These are the one-step
+ * survival probabilities that populate W_{x,t,1} (Sections 3.5, 4).
+ * Errors: RSV_E_ARG (bad id, NULL, n_ages_m < 1 or > 4096),
+ * RSV_E_ASSUMPTION (an entry outside [0, 1] or not finite, Section 3.7.3). */
+rsv_status rsv_load_decrements(rsv_ctx *ctx, int32_t table_id, const double *p_monthly,
+                               int32_t n_ages_m);
+
+/* Load the portfolio: n records (host, copied).  Validation of the records
+ * against the tables happens at compute time.
+ * Errors: RSV_E_ARG (NULL with n > 0, n < 0, n > 2^31 - 1). */
+rsv_status rsv_load_portfolio(rsv_ctx *ctx, const rsv_policy *pols, int64_t n);
+
+/* Load a scenario set: v = per-step discount factors (host FP64, copied),
+ * v_{s,t} = exp(-integral of the force of interest over step t) in scenario s
+ * (Section 3.4).  layout 0: v[s * n_steps + t]; layout 1: v[t * n_scen + s].
+ * The same sequence discounts every policy valued under scenario s.
+ * Errors: RSV_E_ARG (NULL, n_scen < 1, n_steps < 1, bad layout),
+ * RSV_E_ASSUMPTION (a factor not finite or <= 0, Section 3.7.2). */
+rsv_status rsv_load_scenarios(rsv_ctx *ctx, const double *v, int32_t n_scen, int32_t n_steps,
+                              int32_t layout);
+
+/* Reserves of every policy x scenario by backward substitution of Eq.
+ * (generalForm), f = 1, from r_S = 0 (annuities, term assurances) or
+ * r_S = (amount) (endowments at maturity), where S is the policy's number of
+ * steps: to the limiting age for whole-life annuities (to the younger life's
+ * for the JL product), the term otherwise, capped by opts->horizon.
+ * Errors: RSV_E_STATE (tables, portfolio or scenarios missing), RSV_E_ARG
+ * (bad opts, a NULL output whose bit is set, a trajectory request above 1 GiB,
+ * a record with a bad product, table id or state, or whose ages plus steps
+ * exceed 4096), RSV_E_ASSUMPTION (reversion outside [0, 1], amount not
+ * finite, a projection longer than n_steps), RSV_E_CUDA, RSV_E_NOMEM. */
+rsv_status rsv_compute_reserves(rsv_ctx *ctx, const rsv_opts *opts, rsv_out *out);
+
+/* Kernel variants of a form (policies x scenarios per thread, CTA size):
+ * how many there are, and a printable description of one. */
+int32_t rsv_variant_count(int32_t form);
+const char *rsv_variant_name(int32_t form, int32_t variant);
+
+/* Autotuner: time every variant of `form` on the loaded data (the same
+ * outputs as `opts`), keep the fastest as the context's default for that
+ * form and return its index in *best (may be NULL).  reps >= 1 timed runs
+ * per variant after one warm-up run; best of reps is compared.
+ * ms_out (optional) receives rsv_variant_count(form) times in ms.
+ * Errors: as rsv_compute_reserves. */
+rsv_status rsv_tune(rsv_ctx *ctx, const rsv_opts *opts, int32_t reps, int32_t *best,
+                    float *ms_out);
+
+/* Wait for all work issued on the context stream; returns RSV_E_CUDA or
+ * RSV_E_TIMEOUT if a kernel reported one. */
+rsv_status rsv_synchronize(rsv_ctx *ctx);
+
+/* Message of the last failed call on ctx (owned by ctx, valid until the next
+ * call).  Never NULL. */
+const char *rsv_last_error(const rsv_ctx *ctx);
+
+/* Device time in ms of the last recurrence kernel issued by
+ * rsv_compute_reserves on ctx (CUDA events on the context stream; valid after
+ * the call has completed).  Returns -1 if unknown. */
+float rsv_last_kernel_ms(rsv_ctx *ctx);
+
+/* Number of streaming multiprocessors of the context's device. */
+int32_t rsv_device_sm_count(const rsv_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSV_H */

@@ -1,0 +1,354 @@
+// recur_kernel.cuh -- the backward vector reserve recurrence on sm_103a.
+//
+// Eq. (generalForm) of Tucker & Bull with f = 1 and zero-reserve states
+// removed (Section 3.6.4) becomes, per policy and scenario, per unit amount:
+//   K_ANN  r_t = v_t p_t (1 + r_{t+1})                          (Section 4.1.1)
+//   K_ASS  r_t = v_t (q_t + p_t r_{t+1})                        (Section 4.1.3)
+//   K_JL   three states of the two-life model (Section 4.2), c = (1, 1, rho):
+//            r01 = v px (1 + r01')          r10 = v py (rho + r10')
+//            r00 = v [px py (1 + r00') + px qy (1 + r01') + qx py (rho + r10')]
+//                = v px py (1 + r00') + qy r01 + qx r10   (r01, r10 of this step)
+// run backward from the boundary r_S (Section 3.8.2).
+//
+// Mapping.  A work item is one tile of P policies (same kind, similar S) times
+// one chunk of 32*M scenarios, owned by one warp: lane l holds scenarios
+// s0 .. s0+M-1 of all P policies (P*M chains in registers).  Per step a lane
+// makes one vector load of its M discount factors (coalesced across the
+// warp, step-major plane) and, per policy, one shared-memory broadcast of the
+// decrement-table entry.  The table is staged once per CTA by TMA.  Warps
+// claim items from an atomic queue in decreasing-cost order (persistent grid,
+// no inter-warp synchronisation after staging).
+#pragma once
+
+#include "rsv_device.cuh"
+
+namespace rsv {
+
+// ---------------------------------------------------------------- traits ----
+template <int FORM>
+struct Tr;
+
+template <>
+struct Tr<F_F64> {
+    using Val = double;
+    using TabE = double2;  // (p, q)
+    using VE = double;
+    __device__ static Val p(const TabE& e) { return e.x; }
+    __device__ static Val q(const TabE& e) { return e.y; }
+    __device__ static Val v(const VE& e) { return e; }
+    __device__ static Val pair(float h, float l) { return (double)h + (double)l; }
+    __device__ static Val cst(float x) { return (double)x; }
+    __device__ static double dbl(Val x) { return x; }
+};
+
+template <>
+struct Tr<F_F32> {
+    using Val = float;
+    using TabE = float2;   // (p, q)
+    using VE = float;
+    __device__ static Val p(const TabE& e) { return e.x; }
+    __device__ static Val q(const TabE& e) { return e.y; }
+    __device__ static Val v(const VE& e) { return e; }
+    __device__ static Val pair(float h, float) { return h; }
+    __device__ static Val cst(float x) { return x; }
+    __device__ static double dbl(Val x) { return (double)x; }
+};
+
+template <>
+struct Tr<F_COMP> {
+    using Val = df;
+    using TabE = float4;   // (p_hi, p_lo, q_hi, q_lo)
+    using VE = float2;     // (v_hi, v_lo)
+    __device__ static Val p(const TabE& e) { return df{e.x, e.y}; }
+    __device__ static Val q(const TabE& e) { return df{e.z, e.w}; }
+    __device__ static Val v(const VE& e) { return df{e.x, e.y}; }
+    __device__ static Val pair(float h, float l) { return df{h, l}; }
+    __device__ static Val cst(float x) { return df{x, 0.0f}; }
+    __device__ static double dbl(Val x) { return df_to_double(x); }
+};
+
+// ------------------------------------------------------- step arithmetic ----
+// Plain forms (double or float): explicit roundings and fused multiply-adds.
+__device__ __forceinline__ float p_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double p_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float p_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double p_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float p_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double p_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <class R>
+__device__ __forceinline__ R step_ann(R v, R p, R V) {       // v p (1 + V)
+    R g = p_mul(v, p);
+    return p_fma(g, V, g);
+}
+template <class R>
+__device__ __forceinline__ R step_ass(R v, R p, R q, R V) {  // v (q + p V)
+    return p_mul(v, p_fma(p, V, q));
+}
+template <class R>
+__device__ __forceinline__ void step_jl(R v, R px, R qx, R py, R qy, R rho, R& V00, R& V01, R& V10) {
+    R gx = p_mul(v, px), gy = p_mul(v, py);
+    R n01 = p_fma(gx, V01, gx);                 // v px (1 + r01')
+    R n10 = p_mul(gy, p_add(rho, V10));         // v py (rho + r10')
+    R gxy = p_mul(gx, py);
+    R t = p_fma(gxy, V00, gxy);                 // v px py (1 + r00')
+    t = p_fma(qy, n01, t);                      //   + qy r01
+    V00 = p_fma(qx, n10, t);                    //   + qx r10
+    V01 = n01;
+    V10 = n10;
+}
+
+// Compensated form: every quantity is a double-float; inputs arrive as
+// hi/lo pairs of their FP64 values.
+__device__ __forceinline__ df step_ann(df v, df p, df V) {
+    return df_mul(df_mul(v, p), df_add_one(V));
+}
+__device__ __forceinline__ df step_ass(df v, df p, df q, df V) {
+    return df_mul(v, df_add_pos(q, df_mul(p, V)));
+}
+__device__ __forceinline__ void step_jl(df v, df px, df qx, df py, df qy, df rho, df& V00, df& V01,
+                                        df& V10) {
+    df gx = df_mul(v, px), gy = df_mul(v, py);
+    df n01 = df_mul(gx, df_add_one(V01));
+    df n10 = df_mul(gy, df_add_pos(rho, V10));
+    df t0 = df_mul(df_mul(gx, py), df_add_one(V00));
+    df t1 = df_mul(qy, n01);
+    df t2 = df_mul(qx, n10);
+    V00 = df_add_pos(df_add_pos(t0, t1), t2);
+    V01 = n01;
+    V10 = n10;
+}
+
+// M consecutive scenario-plane elements of one lane, one vector load.
+template <class E, int M>
+struct alignas(sizeof(E) * M) Pack {
+    E e[M];
+};
+
+// ------------------------------------------------------------- one item ----
+template <int FORM, int P, int M, int KIND, bool EXTRA>
+struct Tile {
+    using T = Tr<FORM>;
+    using Val = typename T::Val;
+    using TabE = typename T::TabE;
+    using VE = typename T::VE;
+    using VP = Pack<VE, M>;
+    static constexpr int NS = (KIND == K_JL) ? 3 : 1;
+
+    const RecurArgs& a;
+    const TabE* __restrict__ tab;
+    const VE* __restrict__ vplane;
+    int s0;
+    int idx1[P], idx2[P], Sp[P], st0[P], pol[P];
+    Val rho[P];
+    double amt[P];
+    Val V[NS][P][M];
+
+    __device__ __forceinline__ Tile(const RecurArgs& args, const TabE* t, int tile, int chunk, int lane)
+        : a(args), tab(t), vplane(static_cast<const VE*>(args.v)) {
+        s0 = (chunk * 32 + lane) * M;
+        const SlotRec* rec = a.slots + (size_t)tile * P;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const SlotRec r = rec[i];
+            idx1[i] = r.idx1;
+            idx2[i] = r.idx2;
+            Sp[i] = r.S;
+            st0[i] = r.state0;
+            pol[i] = r.pol;
+            rho[i] = T::pair(r.rho_h, r.rho_l);
+            amt[i] = (EXTRA && r.pol >= 0) ? a.amount[r.pol] : 0.0;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                V[0][i][m] = T::cst(r.bnd);
+#pragma unroll
+                for (int k = 1; k < NS; ++k) V[k][i][m] = T::cst(0.0f);
+            }
+        }
+    }
+
+    __device__ __forceinline__ VP load(int t) const {
+        return *reinterpret_cast<const VP*>(vplane + (size_t)t * a.s_pad + s0);
+    }
+
+    __device__ __forceinline__ Val out_state(int i, int m) const {
+        if constexpr (NS == 1) return V[0][i][m];
+        else return st0[i] == 0 ? V[0][i][m] : (st0[i] == 1 ? V[1][i][m] : V[2][i][m]);
+    }
+
+    // traj / pt_mean side outputs of r_t for policy i (diagnostic runs only)
+    __device__ __forceinline__ void record(int t, int i) {
+        if (pol[i] < 0) return;
+        double sum = 0.0;
+        const size_t row = (size_t)pol[i] * (a.n_steps + 1) + t;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int s = s0 + m;
+            if (s < a.n_scen) {
+                const double x = amt[i] * T::dbl(out_state(i, m));
+                if (a.traj) a.traj[row * a.n_scen + s] = x;
+                sum += x;
+            }
+        }
+        if (a.pt_sum) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if ((threadIdx.x & 31) == 0) atomicAdd(&a.pt_sum[row], sum);
+        }
+    }
+
+    template <bool CHECK>
+    __device__ __forceinline__ void step(int t, const VP& vv) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            if (CHECK && t >= Sp[i]) continue;
+            const TabE e1 = tab[idx1[i] + t];
+            const Val px = T::p(e1), qx = T::q(e1);
+            if constexpr (KIND == K_JL) {
+                const TabE e2 = tab[idx2[i] + t];
+                const Val py = T::p(e2), qy = T::q(e2);
+#pragma unroll
+                for (int m = 0; m < M; ++m)
+                    step_jl(T::v(vv.e[m]), px, qx, py, qy, rho[i], V[0][i][m], V[1][i][m], V[2][i][m]);
+            } else if constexpr (KIND == K_ANN) {
+#pragma unroll
+                for (int m = 0; m < M; ++m) V[0][i][m] = step_ann(T::v(vv.e[m]), px, V[0][i][m]);
+            } else {
+#pragma unroll
+                for (int m = 0; m < M; ++m) V[0][i][m] = step_ass(T::v(vv.e[m]), px, qx, V[0][i][m]);
+            }
+            if constexpr (EXTRA) record(t, i);
+        }
+    }
+
+    static constexpr int U = 4;   // steps per prefetch group
+
+    __device__ __forceinline__ void load_group(VP (&g)[U], int t) const {
+#pragma unroll
+        for (int u = 0; u < U; ++u) g[u] = load(t - u);
+    }
+    __device__ __forceinline__ void run_group(const VP (&g)[U], int t) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) step<false>(t - u, g[u]);
+    }
+
+    __device__ __forceinline__ void run(int tile) {
+        const int Smax = Sp[0], Smin = Sp[P - 1];
+        if constexpr (EXTRA) {
+            // r at t = S_i (the boundary) for the side outputs
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                if (Sp[i] <= a.n_steps) record(Sp[i], i);
+        }
+        int t = Smax - 1;
+        for (; t >= Smin; --t) step<true>(t, load(t));      // ragged head: some policies idle
+        if (t + 1 >= 2 * U) {                                 // bulk: double-buffered groups
+            VP A[U], B[U];
+            load_group(A, t);
+            for (;;) {
+                bool more = (t - U + 1) >= U;
+                if (more) load_group(B, t - U);
+                run_group(A, t);
+                t -= U;
+                if (!more) break;
+                more = (t - U + 1) >= U;
+                if (more) load_group(A, t - U);
+                run_group(B, t);
+                t -= U;
+                if (!more) break;
+            }
+        }
+        for (; t >= 0; --t) step<false>(t, load(t));
+
+        // epilogue: scale by the amount, write V0, per-tile scenario sums
+        double part[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) part[m] = 0.0;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            if (pol[i] < 0) continue;
+            const double A = a.amount[pol[i]];
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const int s = s0 + m;
+                if (s < a.n_scen) {
+                    const double x = A * T::dbl(out_state(i, m));
+                    const size_t o = (size_t)pol[i] * a.n_scen + s;
+                    if (a.V0f) a.V0f[o] = (float)x;
+                    if (a.V0d) a.V0d[o] = x;
+                    part[m] += x;
+                }
+            }
+        }
+        if (a.partial) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) a.partial[(size_t)tile * a.s_pad + s0 + m] = part[m];
+        }
+    }
+};
+
+template <int FORM, int P, int M, int NT, bool EXTRA>
+__global__ void __launch_bounds__(NT) recur_kernel(const RecurArgs a) {
+    using TabE = typename Tr<FORM>::TabE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint64_t bar;
+    TabE* tab = reinterpret_cast<TabE*>(smem_raw);
+    if (!stage_to_smem(tab, a.tab, (uint32_t)a.tab_bytes, &bar, a.status)) return;
+
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(a.counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= a.n_items) break;
+        const int tile = item / a.n_chunks;
+        const int chunk = item - tile * a.n_chunks;
+        const int kind = a.tile_kind[tile];
+        if (kind == K_JL) {
+            Tile<FORM, P, M, K_JL, EXTRA> w(a, tab, tile, chunk, lane);
+            w.run(tile);
+        } else if (kind == K_ANN) {
+            Tile<FORM, P, M, K_ANN, EXTRA> w(a, tab, tile, chunk, lane);
+            w.run(tile);
+        } else {
+            Tile<FORM, P, M, K_ASS, EXTRA> w(a, tab, tile, chunk, lane);
+            w.run(tile);
+        }
+    }
+}
+
+// ------------------------------------------------------ variant registry ----
+struct Variant {
+    int form, P, M, NT;
+    bool extra;
+    const char* name;
+    cudaError_t (*launch)(const RecurArgs&, int grid, size_t smem, cudaStream_t st);
+    cudaError_t (*occupancy)(int* blocks_per_sm, size_t smem);
+};
+
+template <int FORM, int P, int M, int NT, bool EXTRA>
+cudaError_t launch_recur(const RecurArgs& a, int grid, size_t smem, cudaStream_t st) {
+    auto k = recur_kernel<FORM, P, M, NT, EXTRA>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int FORM, int P, int M, int NT, bool EXTRA>
+cudaError_t occupancy_recur(int* blocks, size_t smem) {
+    auto k = recur_kernel<FORM, P, M, NT, EXTRA>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, NT, smem);
+}
+
+#define RSV_VARIANT(FORM, P, M, NT, EXTRA, NAME) \
+    Variant { FORM, P, M, NT, EXTRA, NAME, &launch_recur<FORM, P, M, NT, EXTRA>, &occupancy_recur<FORM, P, M, NT, EXTRA> }
+
+// Each form's translation unit defines these.
+const Variant* variants_f64(int* n);
+const Variant* variants_f32(int* n);
+const Variant* variants_comp(int* n);
+
+}  // namespace rsv

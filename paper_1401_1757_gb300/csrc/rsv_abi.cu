@@ -1,0 +1,666 @@
+// rsv_abi.cu -- host side of the C ABI declared in include/rsv.h.
+//
+// Loads copy the caller's host data; compute builds (and caches) the device
+// work layout: the decrement tables in the form's entry format, the policy
+// tiles grouped by reduced model and sorted by decreasing projection length
+// (so the persistent kernel's queue hands out the longest work first, as the
+// paper's dynamic OpenMP schedule did, Section 5.1.1), and the scratch of the
+// per-scenario totals.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rsv.h"
+#include "recur_kernel.cuh"
+
+using namespace rsv;
+
+namespace {
+
+constexpr int kMaxTables = 8;
+constexpr int kMaxAgeSteps = 4096;       // age + steps bound of the staged tables
+constexpr size_t kMaxSmem = 200 * 1024;  // staged tables per CTA
+constexpr size_t kMaxTraj = size_t(1) << 30;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= n && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+        if (e == cudaSuccess) n = bytes;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+// One policy after validation: reduced model, steps, boundary.
+struct PolPrep {
+    int kind, S, idx_age1, idx_age2, table1, table2, state0, pol;
+    float bnd;
+    double rho;
+};
+
+struct Layout {            // cached tiling for one (P, horizon, data generation)
+    int P = -1, horizon = -1;
+    unsigned long long gen = ~0ull;
+    int n_tiles = 0, tab_pad = 0, n_tab = 0;
+    double chain_steps = 0;  // sum over policies of S (per scenario)
+    DevBuf slots, kinds;
+};
+
+const Variant* variant_list(int form, int* n) {
+    switch (form) {
+    case F_F64: return variants_f64(n);
+    case F_F32: return variants_f32(n);
+    case F_COMP: return variants_comp(n);
+    default: *n = 0; return nullptr;
+    }
+}
+
+__global__ void split_planes_kernel(const double* __restrict__ v, int layout, int n_scen, int n_steps,
+                                    int s_pad, double* __restrict__ p64, float* __restrict__ p32,
+                                    float2* __restrict__ p2) {
+    const size_t total = (size_t)n_steps * s_pad;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int t = (int)(i / s_pad), s = (int)(i % s_pad);
+        double x = 1.0;   // padding scenarios: any finite factor, never written out
+        if (s < n_scen) x = layout == 0 ? v[(size_t)s * n_steps + t] : v[(size_t)t * n_scen + s];
+        const float h = __double2float_rn(x);
+        p64[i] = x;
+        p32[i] = h;
+        p2[i] = make_float2(h, __double2float_rn(x - (double)h));
+    }
+}
+
+// Fixed-order two-level sum of the per-tile scenario sums (deterministic).
+__global__ void reduce_tiles_kernel(const double* __restrict__ partial, int n_tiles, int s_pad, int G,
+                                    double* __restrict__ part2) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= s_pad) return;
+    const int t0 = blockIdx.y * G, t1 = min(n_tiles, t0 + G);
+    double acc = 0.0;
+    for (int t = t0; t < t1; ++t) acc += partial[(size_t)t * s_pad + s];
+    part2[(size_t)blockIdx.y * s_pad + s] = acc;
+}
+
+__global__ void reduce_groups_kernel(const double* __restrict__ part2, int n_groups, int s_pad, int n_scen,
+                                     double* __restrict__ total) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_scen) return;
+    double acc = 0.0;
+    for (int g = 0; g < n_groups; ++g) acc += part2[(size_t)g * s_pad + s];
+    total[s] = acc;
+}
+
+__global__ void scale_kernel(double* __restrict__ x, size_t n, double f) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        x[i] *= f;
+}
+
+}  // namespace
+
+struct rsv_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err = "no error";
+
+    std::vector<double> tab[kMaxTables];
+    unsigned long long tab_gen = 1;
+
+    std::vector<rsv_policy> pols;
+    unsigned long long pol_gen = 1;
+    DevBuf d_amount;
+    bool amount_dirty = true;
+
+    int n_scen = 0, n_steps = 0, s_pad = 0;
+    DevBuf d_vstage, d_v64, d_v32, d_v2;
+
+    DevBuf d_tab[3];
+    int tab_pad_of[3] = {-1, -1, -1};
+    int n_tab_of[3] = {-1, -1, -1};
+    unsigned long long tab_gen_of[3] = {0, 0, 0};
+
+    Layout lay;
+    DevBuf d_ctl;       // [0] queue head, [1] status
+    DevBuf d_partial, d_part2;
+    DevBuf d_o_v0f, d_o_v0d, d_o_tot, d_o_pt, d_o_traj;   // staging for host outputs
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool ev_recorded = false;
+    int tuned[3] = {-1, -1, -1};
+};
+
+namespace {
+
+rsv_status fail(rsv_ctx* c, rsv_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return st;
+}
+
+#define CU(call)                                                                                \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? RSV_E_NOMEM : RSV_E_CUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                         \
+    } while (0)
+
+int table_len(const rsv_ctx* c, int id) { return (int)c->tab[id].size(); }
+
+// Validate every record against the tables and the scenario length and
+// derive its reduced model (Section 3.6.4), steps and boundary.
+rsv_status prep_policies(rsv_ctx* c, int horizon, std::vector<PolPrep>& out, int& tab_pad, int& n_tab,
+                         double& chain_steps) {
+    const int64_t n = (int64_t)c->pols.size();
+    out.resize(n);
+    int need = 1;
+    n_tab = 1;
+    chain_steps = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const rsv_policy& r = c->pols[i];
+        PolPrep& q = out[i];
+        if (r.product < RSV_SL_ANNUITY || r.product > RSV_ENDOWMENT || r.reserved != 0)
+            return fail(c, RSV_E_ARG, "policy %lld: bad product %d", (long long)i, r.product);
+        const bool jl = r.product == RSV_JL_REVERSIONARY;
+        if (r.table1 < 0 || r.table1 >= kMaxTables || c->tab[r.table1].empty() ||
+            (jl && (r.table2 < 0 || r.table2 >= kMaxTables || c->tab[r.table2].empty())))
+            return fail(c, RSV_E_ARG, "policy %lld: decrement table not loaded", (long long)i);
+        if (r.age1_m < 0 || (jl && r.age2_m < 0) || r.term_m < 0)
+            return fail(c, RSV_E_ARG, "policy %lld: negative age or term", (long long)i);
+        if (r.state0 < 0 || r.state0 > (jl ? 2 : 0))
+            return fail(c, RSV_E_ARG, "policy %lld: bad state0 %d", (long long)i, r.state0);
+        if (!std::isfinite(r.amount))
+            return fail(c, RSV_E_ASSUMPTION, "policy %lld: amount not finite", (long long)i);
+        if (jl && !(r.reversion >= 0.0 && r.reversion <= 1.0))
+            return fail(c, RSV_E_ASSUMPTION, "policy %lld: reversion outside [0,1]", (long long)i);
+        int S;
+        if (r.product == RSV_SL_ANNUITY) {
+            S = std::max(0, table_len(c, r.table1) - r.age1_m);
+            if (r.term_m > 0) S = std::min(S, r.term_m);
+        } else if (jl) {   // payable while either life can be alive
+            S = std::max(0, std::max(table_len(c, r.table1) - r.age1_m, table_len(c, r.table2) - r.age2_m));
+            if (r.term_m > 0) S = std::min(S, r.term_m);
+        } else {
+            S = r.term_m;
+        }
+        float bnd = r.product == RSV_ENDOWMENT ? 1.0f : 0.0f;
+        if (horizon > 0 && horizon < S) {
+            S = horizon;
+            bnd = 0.0f;   // truncated projection: r_horizon = 0
+        }
+        if (S > c->n_steps)
+            return fail(c, RSV_E_ASSUMPTION, "policy %lld: %d steps but scenarios have %d", (long long)i, S,
+                        c->n_steps);
+        const int top = std::max(r.age1_m + S, jl ? r.age2_m + S : 0);
+        if (top > kMaxAgeSteps)
+            return fail(c, RSV_E_ARG, "policy %lld: age + steps %d exceeds %d", (long long)i, top, kMaxAgeSteps);
+        need = std::max(need, top);
+        n_tab = std::max(n_tab, std::max(r.table1, jl ? r.table2 : 0) + 1);
+        q.kind = jl ? K_JL : (r.product == RSV_SL_ANNUITY ? K_ANN : K_ASS);
+        q.S = S;
+        q.idx_age1 = r.age1_m;
+        q.idx_age2 = jl ? r.age2_m : 0;
+        q.table1 = r.table1;
+        q.table2 = jl ? r.table2 : 0;
+        q.state0 = r.state0;
+        q.pol = (int)i;
+        q.bnd = bnd;
+        q.rho = jl ? r.reversion : 0.0;
+        chain_steps += S;
+    }
+    for (int t = 0; t < n_tab; ++t) need = std::max(need, table_len(c, t));
+    tab_pad = (need + 31) / 32 * 32;
+    return RSV_OK;
+}
+
+rsv_status build_layout(rsv_ctx* c, int P, int horizon) {
+    Layout& L = c->lay;
+    const unsigned long long gen = c->pol_gen * 1000003ull + c->tab_gen * 7919ull + (unsigned)c->n_steps;
+    if (L.P == P && L.horizon == horizon && L.gen == gen) return RSV_OK;
+    std::vector<PolPrep> pp;
+    int tab_pad, n_tab;
+    double cs;
+    rsv_status st = prep_policies(c, horizon, pp, tab_pad, n_tab, cs);
+    if (st != RSV_OK) return st;
+
+    // group by reduced model, longest projection first
+    static const int kind_rank[3] = {1, 2, 0};   // JL tiles, then annuities, then assurances
+    std::vector<int> order(pp.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (pp[x].kind != pp[y].kind) return kind_rank[pp[x].kind] < kind_rank[pp[y].kind];
+        return pp[x].S > pp[y].S;
+    });
+    std::vector<SlotRec> slots;
+    std::vector<int> kinds;
+    std::vector<double> cost;
+    size_t i = 0;
+    while (i < order.size()) {
+        const int kind = pp[order[i]].kind;
+        SlotRec last{};
+        for (int k = 0; k < P; ++k) {
+            SlotRec s;
+            if (i < order.size() && pp[order[i]].kind == kind) {
+                const PolPrep& q = pp[order[i]];
+                s.idx1 = q.table1 * tab_pad + q.idx_age1;
+                s.idx2 = q.table2 * tab_pad + q.idx_age2;
+                s.S = q.S;
+                s.pol = q.pol;
+                s.rho_h = (float)q.rho;
+                s.rho_l = (float)(q.rho - (double)s.rho_h);
+                s.state0 = q.state0;
+                s.bnd = q.bnd;
+                ++i;
+            } else {
+                s = last;       // padding: same shape, never written out
+                s.pol = -1;
+            }
+            last = s;
+            slots.push_back(s);
+        }
+        kinds.push_back(kind);
+        const double w = kind == K_JL ? 4.5 : 1.0;
+        cost.push_back(w * slots[slots.size() - P].S);
+    }
+    // tiles in decreasing cost order (longest-processing-time first)
+    const int n_tiles = (int)kinds.size();
+    std::vector<int> to(n_tiles);
+    for (int t = 0; t < n_tiles; ++t) to[t] = t;
+    std::stable_sort(to.begin(), to.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<SlotRec> s2((size_t)n_tiles * P);
+    std::vector<int> k2(n_tiles);
+    for (int t = 0; t < n_tiles; ++t) {
+        k2[t] = kinds[to[t]];
+        std::copy(slots.begin() + (size_t)to[t] * P, slots.begin() + (size_t)(to[t] + 1) * P,
+                  s2.begin() + (size_t)t * P);
+    }
+    CU(L.slots.ensure(std::max<size_t>(1, s2.size()) * sizeof(SlotRec)));
+    CU(L.kinds.ensure(std::max<size_t>(1, k2.size()) * sizeof(int)));
+    if (n_tiles) {
+        CU(cudaMemcpyAsync(L.slots.p, s2.data(), s2.size() * sizeof(SlotRec), cudaMemcpyHostToDevice, c->stream));
+        CU(cudaMemcpyAsync(L.kinds.p, k2.data(), k2.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    L.P = P;
+    L.horizon = horizon;
+    L.gen = gen;
+    L.n_tiles = n_tiles;
+    L.tab_pad = tab_pad;
+    L.n_tab = n_tab;
+    L.chain_steps = cs;
+    return RSV_OK;
+}
+
+// Decrement tables in the entry format of `form`, zero survival past each
+// table's end, staged per CTA.
+rsv_status build_tables(rsv_ctx* c, int form, size_t& smem) {
+    const int pad = c->lay.tab_pad, n_tab = c->lay.n_tab;
+    const size_t esz = form == F_F32 ? sizeof(float2) : 16;
+    smem = (size_t)n_tab * pad * esz;
+    if (smem > kMaxSmem)
+        return fail(c, RSV_E_ARG, "decrement tables need %zu bytes of shared memory (max %zu)", smem, kMaxSmem);
+    if (c->tab_pad_of[form] == pad && c->n_tab_of[form] == n_tab && c->tab_gen_of[form] == c->tab_gen)
+        return RSV_OK;
+    std::vector<unsigned char> h(smem);
+    for (int t = 0; t < n_tab; ++t) {
+        for (int k = 0; k < pad; ++k) {
+            const double p = k < table_len(c, t) ? c->tab[t][k] : 0.0;
+            const double q = 1.0 - p;
+            const size_t i = (size_t)t * pad + k;
+            if (form == F_F64) {
+                reinterpret_cast<double2*>(h.data())[i] = make_double2(p, q);
+            } else if (form == F_F32) {
+                reinterpret_cast<float2*>(h.data())[i] = make_float2((float)p, (float)q);
+            } else {
+                const float ph = (float)p, qh = (float)q;
+                reinterpret_cast<float4*>(h.data())[i] =
+                    make_float4(ph, (float)(p - (double)ph), qh, (float)(q - (double)qh));
+            }
+        }
+    }
+    CU(c->d_tab[form].ensure(smem));
+    CU(cudaMemcpyAsync(c->d_tab[form].p, h.data(), smem, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->tab_pad_of[form] = pad;
+    c->n_tab_of[form] = n_tab;
+    c->tab_gen_of[form] = c->tab_gen;
+    return RSV_OK;
+}
+
+rsv_status upload_amounts(rsv_ctx* c) {
+    if (!c->amount_dirty) return RSV_OK;
+    std::vector<double> a(c->pols.size());
+    for (size_t i = 0; i < a.size(); ++i) a[i] = c->pols[i].amount;
+    CU(c->d_amount.ensure(std::max<size_t>(1, a.size()) * sizeof(double)));
+    if (!a.empty()) {
+        CU(cudaMemcpyAsync(c->d_amount.p, a.data(), a.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    c->amount_dirty = false;
+    return RSV_OK;
+}
+
+rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
+    if (!c) return RSV_E_ARG;
+    if (!o || !out) return fail(c, RSV_E_ARG, "opts and out must not be NULL");
+    if (o->form < F_F64 || o->form > F_COMP) return fail(c, RSV_E_ARG, "bad form %d", o->form);
+    if (o->horizon < 0 || (o->on_device != 0 && o->on_device != 1))
+        return fail(c, RSV_E_ARG, "bad horizon or on_device");
+    if (c->pols.empty() && c->n_scen == 0) return fail(c, RSV_E_STATE, "no portfolio and no scenarios loaded");
+    if (c->n_scen == 0) return fail(c, RSV_E_STATE, "no scenarios loaded");
+    bool any_tab = false;
+    for (auto& t : c->tab) any_tab |= !t.empty();
+    if (!any_tab) return fail(c, RSV_E_STATE, "no decrement table loaded");
+    const int outs = o->outputs;
+    if (outs & ~15) return fail(c, RSV_E_ARG, "bad outputs bits 0x%x", outs);
+    if ((outs & RSV_OUT_V0) && !out->V0 && !out->V0d) return fail(c, RSV_E_ARG, "V0 requested but NULL");
+    if ((outs & RSV_OUT_SCEN_TOTAL) && !out->scen_total) return fail(c, RSV_E_ARG, "scen_total NULL");
+    if ((outs & RSV_OUT_PT_MEAN) && !out->pt_mean) return fail(c, RSV_E_ARG, "pt_mean NULL");
+    if ((outs & RSV_OUT_TRAJ) && !out->traj) return fail(c, RSV_E_ARG, "traj NULL");
+
+    const int64_t n_pol = (int64_t)c->pols.size();
+    const int T = c->n_steps, NSc = c->n_scen;
+    const size_t n_v0 = (size_t)n_pol * NSc;
+    const size_t n_pt = (size_t)n_pol * (T + 1);
+    const size_t n_traj = n_pt * NSc;
+    if ((outs & RSV_OUT_TRAJ) && n_traj * sizeof(double) > kMaxTraj)
+        return fail(c, RSV_E_ARG, "trajectory output of %zu bytes exceeds 1 GiB", n_traj * sizeof(double));
+
+    int nv = 0;
+    const Variant* vl = variant_list(o->form, &nv);
+    const bool extra = (outs & (RSV_OUT_PT_MEAN | RSV_OUT_TRAJ)) != 0;
+    int vi;
+    if (extra) {
+        vi = nv - 1;
+    } else if (o->variant >= 0) {
+        if (o->variant >= nv - 1) return fail(c, RSV_E_ARG, "variant %d out of range", o->variant);
+        vi = o->variant;
+    } else {
+        vi = c->tuned[o->form] >= 0 ? c->tuned[o->form] : 0;
+    }
+    const Variant& V = vl[vi];
+
+    rsv_status st = build_layout(c, V.P, o->horizon);
+    if (st != RSV_OK) return st;
+    size_t smem = 0;
+    if ((st = build_tables(c, o->form, smem)) != RSV_OK) return st;
+    if ((st = upload_amounts(c)) != RSV_OK) return st;
+
+    const Layout& L = c->lay;
+    float* V0f = (outs & RSV_OUT_V0) ? out->V0 : nullptr;
+    double* V0d = (outs & RSV_OUT_V0) ? out->V0d : nullptr;
+    double* tot = (outs & RSV_OUT_SCEN_TOTAL) ? out->scen_total : nullptr;
+    double* pt = (outs & RSV_OUT_PT_MEAN) ? out->pt_mean : nullptr;
+    double* traj = (outs & RSV_OUT_TRAJ) ? out->traj : nullptr;
+    float* hV0f = V0f;
+    double *hV0d = V0d, *htot = tot, *hpt = pt, *htraj = traj;
+    if (!o->on_device) {   // device staging of host outputs
+        if (V0f) { CU(c->d_o_v0f.ensure(n_v0 * sizeof(float))); V0f = c->d_o_v0f.as<float>(); }
+        if (V0d) { CU(c->d_o_v0d.ensure(n_v0 * sizeof(double))); V0d = c->d_o_v0d.as<double>(); }
+        if (tot) { CU(c->d_o_tot.ensure(NSc * sizeof(double))); tot = c->d_o_tot.as<double>(); }
+        if (pt) { CU(c->d_o_pt.ensure(n_pt * sizeof(double))); pt = c->d_o_pt.as<double>(); }
+        if (traj) { CU(c->d_o_traj.ensure(n_traj * sizeof(double))); traj = c->d_o_traj.as<double>(); }
+    }
+    CU(c->d_ctl.ensure(2 * sizeof(int32_t)));
+    CU(cudaMemsetAsync(c->d_ctl.p, 0, 2 * sizeof(int32_t), c->stream));
+    if (pt) CU(cudaMemsetAsync(pt, 0, n_pt * sizeof(double), c->stream));
+    if (traj) CU(cudaMemsetAsync(traj, 0, n_traj * sizeof(double), c->stream));
+    if (tot) CU(c->d_partial.ensure((size_t)std::max(1, L.n_tiles) * c->s_pad * sizeof(double)));
+    if (tot && L.n_tiles == 0) CU(cudaMemsetAsync(tot, 0, NSc * sizeof(double), c->stream));
+
+    RecurArgs a{};
+    a.tab = c->d_tab[o->form].p;
+    a.tab_bytes = (int32_t)smem;
+    a.v = o->form == F_F64 ? c->d_v64.p : (o->form == F_F32 ? c->d_v32.p : c->d_v2.p);
+    a.s_pad = c->s_pad;
+    a.n_scen = NSc;
+    a.n_steps = T;
+    a.slots = L.slots.as<SlotRec>();
+    a.tile_kind = L.kinds.as<int32_t>();
+    a.amount = c->d_amount.as<double>();
+    a.n_tiles = L.n_tiles;
+    a.n_chunks = (NSc + 32 * V.M - 1) / (32 * V.M);
+    const long long items = (long long)L.n_tiles * a.n_chunks;
+    if (items > 0x7fffffffLL) return fail(c, RSV_E_ARG, "too many work items (%lld)", items);
+    a.n_items = (int32_t)items;
+    a.counter = c->d_ctl.as<int32_t>();
+    a.status = c->d_ctl.as<int32_t>() + 1;
+    a.V0f = V0f;
+    a.V0d = V0d;
+    a.partial = tot ? c->d_partial.as<double>() : nullptr;
+    a.pt_sum = pt;
+    a.traj = traj;
+
+    if (L.n_tiles > 0) {
+        int bps = 0;
+        CU(V.occupancy(&bps, smem));
+        if (bps < 1) return fail(c, RSV_E_CUDA, "variant %s cannot be resident with %zu B smem", V.name, smem);
+        const long long warps_needed = items;
+        long long grid = (long long)c->sm_count * bps;
+        grid = std::max(1LL, std::min(grid, (warps_needed * 32 + V.NT - 1) / V.NT));
+        CU(cudaEventRecord(c->ev0, c->stream));
+        CU(V.launch(a, (int)grid, smem, c->stream));
+        CU(cudaEventRecord(c->ev1, c->stream));
+        c->ev_recorded = true;
+        if (tot) {
+            const int G = 256, groups = (L.n_tiles + G - 1) / G;
+            CU(c->d_part2.ensure((size_t)groups * c->s_pad * sizeof(double)));
+            dim3 g1((c->s_pad + 127) / 128, groups);
+            reduce_tiles_kernel<<<g1, 128, 0, c->stream>>>(a.partial, L.n_tiles, c->s_pad, G, c->d_part2.as<double>());
+            CU(cudaGetLastError());
+            reduce_groups_kernel<<<(NSc + 127) / 128, 128, 0, c->stream>>>(c->d_part2.as<double>(), groups, c->s_pad,
+                                                                          NSc, tot);
+            CU(cudaGetLastError());
+        }
+        if (pt) {
+            scale_kernel<<<c->sm_count * 4, 256, 0, c->stream>>>(pt, n_pt, 1.0 / NSc);
+            CU(cudaGetLastError());
+        }
+    }
+    if (!o->on_device) {
+        if (hV0f) CU(cudaMemcpyAsync(hV0f, V0f, n_v0 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        if (hV0d) CU(cudaMemcpyAsync(hV0d, V0d, n_v0 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (htot) CU(cudaMemcpyAsync(htot, tot, NSc * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (hpt) CU(cudaMemcpyAsync(hpt, pt, n_pt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (htraj) CU(cudaMemcpyAsync(htraj, traj, n_traj * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        return rsv_synchronize(c);
+    }
+    return RSV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rsv_status rsv_create(rsv_ctx** out, int device, void* cuda_stream) {
+    if (!out) return RSV_E_ARG;
+    *out = nullptr;
+    rsv_ctx* c = new (std::nothrow) rsv_ctx();
+    if (!c) return RSV_E_NOMEM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e != cudaSuccess) {
+        delete c;
+        return RSV_E_CUDA;
+    }
+    *out = c;
+    return RSV_OK;
+}
+
+rsv_status rsv_destroy(rsv_ctx* c) {
+    if (!c) return RSV_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (DevBuf* b : {&c->d_amount, &c->d_vstage, &c->d_v64, &c->d_v32, &c->d_v2, &c->d_tab[0], &c->d_tab[1],
+                      &c->d_tab[2], &c->lay.slots, &c->lay.kinds, &c->d_ctl, &c->d_partial, &c->d_part2,
+                      &c->d_o_v0f, &c->d_o_v0d, &c->d_o_tot, &c->d_o_pt, &c->d_o_traj})
+        b->release();
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+    return RSV_OK;
+}
+
+rsv_status rsv_set_stream(rsv_ctx* c, void* cuda_stream) {
+    if (!c) return RSV_E_ARG;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    return RSV_OK;
+}
+
+rsv_status rsv_load_decrements(rsv_ctx* c, int32_t table_id, const double* p, int32_t n) {
+    if (!c) return RSV_E_ARG;
+    if (table_id < 0 || table_id >= kMaxTables) return fail(c, RSV_E_ARG, "table id %d outside [0,8)", table_id);
+    if (!p || n < 1 || n > kMaxAgeSteps) return fail(c, RSV_E_ARG, "bad table pointer or length %d", n);
+    for (int k = 0; k < n; ++k)
+        if (!(p[k] >= 0.0 && p[k] <= 1.0))
+            return fail(c, RSV_E_ASSUMPTION, "table %d entry %d = %g is not a probability", table_id, k, p[k]);
+    c->tab[table_id].assign(p, p + n);
+    ++c->tab_gen;
+    return RSV_OK;
+}
+
+rsv_status rsv_load_portfolio(rsv_ctx* c, const rsv_policy* pols, int64_t n) {
+    if (!c) return RSV_E_ARG;
+    if (n < 0 || n > 0x7fffffffLL || (n > 0 && !pols)) return fail(c, RSV_E_ARG, "bad portfolio size %lld", (long long)n);
+    c->pols.assign(pols, pols + n);
+    ++c->pol_gen;
+    c->amount_dirty = true;
+    return RSV_OK;
+}
+
+rsv_status rsv_load_scenarios(rsv_ctx* c, const double* v, int32_t n_scen, int32_t n_steps, int32_t layout) {
+    if (!c) return RSV_E_ARG;
+    if (!v || n_scen < 1 || n_steps < 1 || (layout != 0 && layout != 1))
+        return fail(c, RSV_E_ARG, "bad scenario arguments");
+    const size_t n = (size_t)n_scen * n_steps;
+    for (size_t i = 0; i < n; ++i)
+        if (!(std::isfinite(v[i]) && v[i] > 0.0))
+            return fail(c, RSV_E_ASSUMPTION, "discount factor %zu = %g is not finite and positive", i, v[i]);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    const int s_pad = (n_scen + 127) / 128 * 128;
+    const size_t np = (size_t)n_steps * s_pad;
+    CU(c->d_vstage.ensure(n * sizeof(double)));
+    CU(c->d_v64.ensure(np * sizeof(double)));
+    CU(c->d_v32.ensure(np * sizeof(float)));
+    CU(c->d_v2.ensure(np * sizeof(float2)));
+    CU(cudaMemcpyAsync(c->d_vstage.p, v, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    split_planes_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(c->d_vstage.as<double>(), layout, n_scen, n_steps,
+                                                                s_pad, c->d_v64.as<double>(), c->d_v32.as<float>(),
+                                                                c->d_v2.as<float2>());
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(c->stream));
+    c->n_scen = n_scen;
+    c->n_steps = n_steps;
+    c->s_pad = s_pad;
+    c->lay.gen = ~0ull;   // scenario length changes validation
+    return RSV_OK;
+}
+
+rsv_status rsv_compute_reserves(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
+    if (!c) return RSV_E_ARG;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return compute(c, o, out);
+}
+
+int32_t rsv_variant_count(int32_t form) {
+    int n = 0;
+    variant_list(form, &n);
+    return n > 0 ? n - 1 : 0;
+}
+
+const char* rsv_variant_name(int32_t form, int32_t variant) {
+    int n = 0;
+    const Variant* v = variant_list(form, &n);
+    if (!v || variant < 0 || variant >= n) return "";
+    return v[variant].name;
+}
+
+rsv_status rsv_tune(rsv_ctx* c, const rsv_opts* opts, int32_t reps, int32_t* best, float* ms_out) {
+    if (!c) return RSV_E_ARG;
+    if (!opts || reps < 1) return fail(c, RSV_E_ARG, "bad tune arguments");
+    const int nv = rsv_variant_count(opts->form);
+    if (nv < 1) return fail(c, RSV_E_ARG, "bad form %d", opts->form);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    const size_t n_v0 = c->pols.size() * (size_t)c->n_scen;
+    CU(c->d_o_v0f.ensure(std::max<size_t>(1, n_v0) * sizeof(float)));
+    CU(c->d_o_tot.ensure(std::max(1, c->n_scen) * sizeof(double)));
+    rsv_opts o = *opts;
+    o.outputs = RSV_OUT_V0 | RSV_OUT_SCEN_TOTAL;
+    o.on_device = 1;
+    rsv_out out{};
+    out.V0 = c->d_o_v0f.as<float>();
+    out.scen_total = c->d_o_tot.as<double>();
+    int arg = -1;
+    float best_ms = 0.0f;
+    for (int v = 0; v < nv; ++v) {
+        o.variant = v;
+        float vbest = -1.0f;
+        for (int r = 0; r <= reps; ++r) {
+            rsv_status st = compute(c, &o, &out);
+            if (st != RSV_OK) return st;
+            if ((st = rsv_synchronize(c)) != RSV_OK) return st;
+            const float ms = rsv_last_kernel_ms(c);
+            if (r > 0 && (vbest < 0 || ms < vbest)) vbest = ms;
+        }
+        if (ms_out) ms_out[v] = vbest;
+        if (arg < 0 || vbest < best_ms) {
+            arg = v;
+            best_ms = vbest;
+        }
+    }
+    c->tuned[opts->form] = arg;
+    if (best) *best = arg;
+    return RSV_OK;
+}
+
+rsv_status rsv_synchronize(rsv_ctx* c) {
+    if (!c) return RSV_E_ARG;
+    CU(cudaStreamSynchronize(c->stream));
+    if (c->d_ctl.p) {
+        int32_t ctl[2] = {0, 0};
+        CU(cudaMemcpy(ctl, c->d_ctl.p, sizeof ctl, cudaMemcpyDeviceToHost));
+        if (ctl[1] == DEV_TIMEOUT) return fail(c, RSV_E_TIMEOUT, "a bounded device wait ran out (table staging)");
+    }
+    return RSV_OK;
+}
+
+const char* rsv_last_error(const rsv_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+float rsv_last_kernel_ms(rsv_ctx* c) {
+    if (!c || !c->ev_recorded) return -1.0f;
+    if (cudaEventSynchronize(c->ev1) != cudaSuccess) return -1.0f;
+    float ms = -1.0f;
+    if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) != cudaSuccess) return -1.0f;
+    return ms;
+}
+
+int32_t rsv_device_sm_count(const rsv_ctx* c) { return c ? c->sm_count : 0; }
+
+}  // extern "C"

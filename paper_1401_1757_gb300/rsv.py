@@ -1,0 +1,214 @@
+"""ctypes binding of the C ABI in include/rsv.h (argument marshalling only).
+
+Every function keeps its C name.  Arrays go in as NumPy arrays (host) or torch
+tensors (device or pinned host); nothing here computes a reserve.  Loading
+fails loudly when the CUDA library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "librsv.so")
+
+RSV_OK, RSV_E_ARG, RSV_E_NOMEM, RSV_E_CUDA, RSV_E_STATE, RSV_E_TIMEOUT, RSV_E_ASSUMPTION = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "RSV_OK", -1: "RSV_E_ARG", -2: "RSV_E_NOMEM", -3: "RSV_E_CUDA", -4: "RSV_E_STATE",
+                -5: "RSV_E_TIMEOUT", -6: "RSV_E_ASSUMPTION"}
+RSV_SL_ANNUITY, RSV_JL_REVERSIONARY, RSV_TERM_ASSURANCE, RSV_ENDOWMENT = 0, 1, 2, 3
+RSV_FORM_F64, RSV_FORM_F32, RSV_FORM_F32_COMP = 0, 1, 2
+FORM_NAMES = {0: "f64", 1: "f32", 2: "f32comp"}
+RSV_OUT_V0, RSV_OUT_SCEN_TOTAL, RSV_OUT_PT_MEAN, RSV_OUT_TRAJ = 1, 2, 4, 8
+
+
+class rsv_policy(C.Structure):
+    _fields_ = [("product", C.c_int32), ("age1_m", C.c_int32), ("age2_m", C.c_int32),
+                ("term_m", C.c_int32), ("state0", C.c_int32), ("table1", C.c_int32),
+                ("table2", C.c_int32), ("reserved", C.c_int32), ("amount", C.c_double),
+                ("reversion", C.c_double)]
+
+
+POLICY_DTYPE = np.dtype([("product", "<i4"), ("age1_m", "<i4"), ("age2_m", "<i4"), ("term_m", "<i4"),
+                         ("state0", "<i4"), ("table1", "<i4"), ("table2", "<i4"), ("reserved", "<i4"),
+                         ("amount", "<f8"), ("reversion", "<f8")])
+assert POLICY_DTYPE.itemsize == C.sizeof(rsv_policy) == 48
+
+
+class rsv_opts(C.Structure):
+    _fields_ = [("form", C.c_int32), ("outputs", C.c_int32), ("horizon", C.c_int32),
+                ("on_device", C.c_int32), ("variant", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
+class rsv_out(C.Structure):
+    _fields_ = [("V0", C.c_void_p), ("V0d", C.c_void_p), ("scen_total", C.c_void_p),
+                ("pt_mean", C.c_void_p), ("traj", C.c_void_p)]
+
+
+class RsvError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+# Exported symbols of librsv.so that include/rsv.h declares.
+EXPORTS = ["rsv_create", "rsv_destroy", "rsv_set_stream", "rsv_load_decrements", "rsv_load_portfolio",
+           "rsv_load_scenarios", "rsv_compute_reserves", "rsv_variant_count", "rsv_variant_name",
+           "rsv_tune", "rsv_synchronize", "rsv_last_error", "rsv_last_kernel_ms", "rsv_device_sm_count"]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load librsv.so (raises if it is missing: the product has no CPU path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library {path} is not built; run __graft_entry__.build() "
+                          "(there is no CPU fallback)")
+    try:  # share the CUDA runtime that torch already loaded, if any
+        import torch  # noqa: F401
+    except Exception:
+        pass
+    lib = C.CDLL(path)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    sig = {
+        "rsv_create": ([C.POINTER(vp), C.c_int, vp], i32),
+        "rsv_destroy": ([vp], i32),
+        "rsv_set_stream": ([vp, vp], i32),
+        "rsv_load_decrements": ([vp, i32, vp, i32], i32),
+        "rsv_load_portfolio": ([vp, vp, i64], i32),
+        "rsv_load_scenarios": ([vp, vp, i32, i32, i32], i32),
+        "rsv_compute_reserves": ([vp, C.POINTER(rsv_opts), C.POINTER(rsv_out)], i32),
+        "rsv_variant_count": ([i32], i32),
+        "rsv_variant_name": ([i32, i32], C.c_char_p),
+        "rsv_tune": ([vp, C.POINTER(rsv_opts), i32, C.POINTER(i32), C.POINTER(C.c_float)], i32),
+        "rsv_synchronize": ([vp], i32),
+        "rsv_last_error": ([vp], C.c_char_p),
+        "rsv_last_kernel_ms": ([vp], C.c_float),
+        "rsv_device_sm_count": ([vp], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes, f.restype = args, res
+    _lib = lib
+    return lib
+
+
+def _check(ctx, st):
+    if st != RSV_OK:
+        msg = _lib.rsv_last_error(ctx).decode() if ctx else ""
+        raise RsvError(st, msg)
+
+
+def _ptr(x):
+    """Address of a NumPy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def rsv_create(device: int = 0, stream=None):
+    """Returns an opaque context handle.  ``stream``: a torch.cuda.Stream, a raw
+    cudaStream_t integer, or None (legacy default stream)."""
+    lib = load_library()
+    h = C.c_void_p()
+    s = getattr(stream, "cuda_stream", stream)
+    _check(None, lib.rsv_create(C.byref(h), device, s))
+    return h
+
+
+def rsv_destroy(ctx):
+    _check(ctx, load_library().rsv_destroy(ctx))
+
+
+def rsv_set_stream(ctx, stream):
+    _check(ctx, _lib.rsv_set_stream(ctx, getattr(stream, "cuda_stream", stream)))
+
+
+def rsv_load_decrements(ctx, table_id: int, p_monthly):
+    p = np.ascontiguousarray(p_monthly, dtype=np.float64)
+    _check(ctx, _lib.rsv_load_decrements(ctx, table_id, p.ctypes.data, len(p)))
+
+
+def policy_records(pol) -> np.ndarray:
+    """Policy records in the ABI layout from a dict of arrays (as made by ``synth``)
+    or an existing record array."""
+    if isinstance(pol, np.ndarray) and pol.dtype == POLICY_DTYPE:
+        return np.ascontiguousarray(pol)
+    n = len(pol["product"])
+    rec = np.zeros(n, POLICY_DTYPE)
+    for k in ("product", "age1_m", "age2_m", "term_m", "state0", "table1", "table2", "amount", "reversion"):
+        rec[k] = pol[k]
+    return rec
+
+
+def rsv_load_portfolio(ctx, pol):
+    rec = policy_records(pol)
+    _check(ctx, _lib.rsv_load_portfolio(ctx, rec.ctypes.data if len(rec) else None, len(rec)))
+
+
+def rsv_load_scenarios(ctx, v, layout: int = 0):
+    """v: host FP64 [n_scen, n_steps] (layout 0) or [n_steps, n_scen] (layout 1);
+    a NumPy array or a (pinned) CPU torch tensor."""
+    if isinstance(v, np.ndarray):
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        ptr, shape = v.ctypes.data, v.shape
+    else:
+        assert v.dtype.__str__() == "torch.float64" and v.device.type == "cpu" and v.is_contiguous()
+        ptr, shape = v.data_ptr(), tuple(v.shape)
+    n_scen, n_steps = (shape[0], shape[1]) if layout == 0 else (shape[1], shape[0])
+    _check(ctx, _lib.rsv_load_scenarios(ctx, ptr, n_scen, n_steps, layout))
+
+
+def rsv_compute_reserves(ctx, form: int = RSV_FORM_F32_COMP, outputs: int = RSV_OUT_V0, horizon: int = 0,
+                         on_device: bool = False, variant: int = -1, V0=None, V0d=None, scen_total=None,
+                         pt_mean=None, traj=None):
+    """Runs the recurrence.  Output buffers (NumPy for on_device=False, CUDA
+    torch tensors for on_device=True) are caller-sized; see include/rsv.h."""
+    o = rsv_opts(form, outputs, horizon, 1 if on_device else 0, variant)
+    out = rsv_out(_ptr(V0), _ptr(V0d), _ptr(scen_total), _ptr(pt_mean), _ptr(traj))
+    _check(ctx, _lib.rsv_compute_reserves(ctx, C.byref(o), C.byref(out)))
+
+
+def rsv_variant_count(form: int) -> int:
+    return load_library().rsv_variant_count(form)
+
+
+def rsv_variant_name(form: int, variant: int) -> str:
+    return load_library().rsv_variant_name(form, variant).decode()
+
+
+def rsv_tune(ctx, form: int, horizon: int = 0, reps: int = 3):
+    """Times every kernel variant of ``form`` on the loaded data; keeps the fastest
+    as the context default.  Returns (best index, [ms per variant])."""
+    n = rsv_variant_count(form)
+    ms = (C.c_float * n)()
+    best = C.c_int32(-1)
+    o = rsv_opts(form, RSV_OUT_V0 | RSV_OUT_SCEN_TOTAL, horizon, 1, -1)
+    _check(ctx, _lib.rsv_tune(ctx, C.byref(o), reps, C.byref(best), ms))
+    return best.value, list(ms)
+
+
+def rsv_synchronize(ctx):
+    _check(ctx, _lib.rsv_synchronize(ctx))
+
+
+def rsv_last_error(ctx) -> str:
+    return _lib.rsv_last_error(ctx).decode()
+
+
+def rsv_last_kernel_ms(ctx) -> float:
+    return float(_lib.rsv_last_kernel_ms(ctx))
+
+
+def rsv_device_sm_count(ctx) -> int:
+    return int(_lib.rsv_device_sm_count(ctx))

@@ -1,0 +1,241 @@
+"""GPU parity: the CUDA recurrence (through the C ABI) against the FP64 oracle.
+
+Error metric: rel = |V_gpu - V_ref| / max(|V_ref|, 1e-9 * amount).  Bounds:
+  * FP64 form: 1e-12 (same arithmetic, different operation order over <= 1440
+    steps: a few hundred roundings of 2^-53).
+  * compensated FP32 form: 1e-6, the target relative accuracy; the
+    double-float state carries about 44 bits, so it lands far inside.
+  * plain FP32 form: 2e-4.  Rounding v to FP32 alone is a relative error of up
+    to 2^-24 per step, systematic under a flat rate, so ~t * 6e-8 (4e-5 at 720
+    steps); the 3-state product doubles it.  This form is measured, not
+    expected to meet 1e-6.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_1401_1757_gb300 import rsv
+
+pytestmark = pytest.mark.gpu
+
+TOL = {rsv.RSV_FORM_F64: 1e-12, rsv.RSV_FORM_F32_COMP: 1e-6, rsv.RSV_FORM_F32: 2e-4}
+FORMS = [rsv.RSV_FORM_F64, rsv.RSV_FORM_F32_COMP, rsv.RSV_FORM_F32]
+V0T = rsv.RSV_OUT_V0 | rsv.RSV_OUT_SCEN_TOTAL
+
+
+def rel_err(got, ref, amount):
+    scale = np.maximum(np.abs(ref), 1e-9 * np.abs(np.asarray(amount))[:, None])
+    return np.abs(got - ref) / scale
+
+
+@pytest.fixture
+def ctx():
+    assert torch.cuda.is_available()
+    h = rsv.rsv_create(0, torch.cuda.current_stream())
+    yield h
+    rsv.rsv_destroy(h)
+
+
+def run(ctx, pol, tab, v, form, horizon=0, variant=-1, tables=None):
+    if tables is None:
+        rsv.rsv_load_decrements(ctx, 0, tab)
+    else:
+        for i, t in enumerate(tables):
+            rsv.rsv_load_decrements(ctx, i, t)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    n, S = len(pol["product"]), v.shape[0]
+    V0 = np.zeros((n, S))
+    tot = np.zeros(S)
+    rsv.rsv_compute_reserves(ctx, form, V0T, horizon=horizon, variant=variant, V0d=V0, scen_total=tot)
+    return V0, tot
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_config1_full(ctx, form):
+    """1,000 single-life level annuities, ages 60-90, GM mortality, flat 4%."""
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_single_life(1000, seed=0)
+    v = synth.flat_scenarios(n_steps=720)
+    V0, tot = run(ctx, pol, tab, v, form)
+    ref, ref_tot = oracle.reserves_batch(pol, tab, v)
+    err = rel_err(V0, ref, pol["amount"])
+    print(f"config-1 form {rsv.FORM_NAMES[form]}: max rel err {err.max():.3e}, median {np.median(err):.3e}")
+    assert err.max() <= TOL[form]
+    assert abs(tot[0] - ref_tot[0]) <= TOL[form] * ref_tot[0]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_mix_vasicek_ragged(ctx, form):
+    """Four-product mix, 300 policies x 157 Vasicek scenarios (ragged against
+    every chunk width), 1200 steps."""
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_mix(300, seed=21)
+    v = synth.vasicek_paths(157, 1200, seed=21)
+    V0, tot = run(ctx, pol, tab, v, form)
+    ref, ref_tot = oracle.reserves_batch(pol, tab, v)
+    err = rel_err(V0, ref, pol["amount"])
+    for p in range(4):
+        m = pol["product"] == p
+        print(f"mix form {rsv.FORM_NAMES[form]} product {p}: max rel err {err[m].max():.3e}")
+    assert err.max() <= TOL[form]
+    assert np.max(np.abs(tot - ref_tot) / ref_tot) <= TOL[form]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_every_variant_agrees(ctx, form):
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_mix(130, seed=5)
+    v = synth.vasicek_paths(70, 1200, seed=5)
+    ref, _ = oracle.reserves_batch(pol, tab, v)
+    for var in range(rsv.rsv_variant_count(form)):
+        V0, _ = run(ctx, pol, tab, v, form, variant=var)
+        err = rel_err(V0, ref, pol["amount"]).max()
+        assert err <= TOL[form], (rsv.rsv_variant_name(form, var), err)
+
+
+@pytest.mark.parametrize("form", [rsv.RSV_FORM_F64, rsv.RSV_FORM_F32_COMP])
+def test_trajectory_every_step_every_state(ctx, form):
+    """r_t at every t, in every reduced state (JL states 00, 01, 10 via state0),
+    against the oracle's full-state vectors."""
+    tab = synth.gm_monthly_survival()
+    base = synth.portfolio_mix(24, seed=8)
+    jl = np.where(base["product"] == 1)[0]
+    extra = synth.take(base, np.concatenate([jl, jl]))
+    extra["state0"][: len(jl)] = 1
+    extra["state0"][len(jl):] = 2
+    pol = {k: np.concatenate([base[k], extra[k]]) for k in base}
+    n = len(pol["product"])
+    v = synth.vasicek_paths(37, 1200, seed=8)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    T = v.shape[1]
+    traj = np.zeros((n, T + 1, 37))
+    pt = np.zeros((n, T + 1))
+    rsv.rsv_compute_reserves(ctx, form, rsv.RSV_OUT_TRAJ | rsv.RSV_OUT_PT_MEAN, traj=traj, pt_mean=pt)
+    worst = 0.0
+    for p in range(n):
+        ref_s = []
+        for s in range(37):
+            r = oracle.chain(int(pol["product"][p]), int(pol["age1_m"][p]), float(pol["amount"][p]), tab, v[s],
+                             age2=int(pol["age2_m"][p]), term=int(pol["term_m"][p]), rho=float(pol["reversion"][p]))
+            ref = r[:, int(pol["state0"][p])]
+            S = len(ref) - 1
+            got = traj[p, : S + 1, s]
+            scale = np.maximum(np.abs(ref), 1e-9 * pol["amount"][p])
+            worst = max(worst, float(np.max(np.abs(got - ref) / scale)))
+            assert np.all(traj[p, S + 1:, s] == 0.0)
+            ref_s.append(np.concatenate([ref, np.zeros(T - S)]))
+        ref_mean = np.mean(ref_s, axis=0)
+        scale = np.maximum(np.abs(ref_mean), 1e-9 * pol["amount"][p])
+        worst = max(worst, float(np.max(np.abs(pt[p] - ref_mean) / scale)))
+    print(f"trajectory form {rsv.FORM_NAMES[form]}: max rel err {worst:.3e}")
+    assert worst <= TOL[form]
+
+
+def test_edge_cases(ctx):
+    """Empty portfolio; policies with nothing left to pay (age at the limiting
+    age); an endowment at maturity (term 0: reserve = sum assured); one
+    scenario; horizon truncation; two decrement tables."""
+    tab = synth.gm_monthly_survival()
+    tab2 = synth.gm_monthly_survival(A=0.0003, B=0.00002)
+    v = synth.vasicek_paths(1, 1500, seed=3)
+    pol = synth.portfolio_mix(8, seed=3)
+    pol["age1_m"][:3] = [1440, 1439, 0]
+    pol["product"][:3] = [0, 0, 0]
+    pol["term_m"][:3] = 0
+    pol["product"][3], pol["term_m"][3] = 3, 0
+    pol["product"][4], pol["age2_m"][4], pol["reversion"][4] = 1, 400, 0.75
+    pol["table2"][4], pol["term_m"][4] = 1, 0
+    for form in FORMS:
+        V0, tot = run(ctx, pol, tab, v, form, tables=[tab, tab2])
+        ref, _ = oracle.reserves_batch(pol, np.stack([tab, tab2]), v)
+        assert V0[0, 0] == 0.0
+        assert V0[3, 0] == pol["amount"][3]
+        assert rel_err(V0, ref, pol["amount"]).max() <= TOL[form]
+        Vh, _ = run(ctx, pol, tab, v, form, horizon=100, tables=[tab, tab2])
+        refh, _ = oracle.reserves_batch(pol, np.stack([tab, tab2]), v, horizon=100)
+        assert rel_err(Vh, refh, pol["amount"]).max() <= TOL[form]
+    empty = synth.take(pol, slice(0, 0))
+    rsv.rsv_load_portfolio(ctx, empty)
+    tot = np.ones(1)
+    rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F32_COMP, rsv.RSV_OUT_SCEN_TOTAL, scen_total=tot)
+    assert tot[0] == 0.0
+
+
+def test_assumption_and_state_errors(ctx):
+    tab = synth.gm_monthly_survival()
+    with pytest.raises(rsv.RsvError) as e:
+        rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F32, rsv.RSV_OUT_SCEN_TOTAL, scen_total=np.zeros(1))
+    assert e.value.status == rsv.RSV_E_STATE
+    bad = tab.copy()
+    bad[5] = 1.5
+    with pytest.raises(rsv.RsvError) as e:
+        rsv.rsv_load_decrements(ctx, 0, bad)
+    assert e.value.status == rsv.RSV_E_ASSUMPTION
+    v = synth.flat_scenarios(n_steps=100)
+    v[0, 7] = -0.1
+    with pytest.raises(rsv.RsvError) as e:
+        rsv.rsv_load_scenarios(ctx, v)
+    assert e.value.status == rsv.RSV_E_ASSUMPTION
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_scenarios(ctx, synth.flat_scenarios(n_steps=100))
+    pol = synth.portfolio_single_life(4)
+    rsv.rsv_load_portfolio(ctx, pol)     # whole-life annuities need > 100 steps
+    with pytest.raises(rsv.RsvError) as e:
+        rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F32, rsv.RSV_OUT_SCEN_TOTAL, scen_total=np.zeros(1))
+    assert e.value.status == rsv.RSV_E_ASSUMPTION
+    pol = synth.portfolio_mix(10, seed=1)
+    pol["reversion"][pol["product"] == 1] = 1.2
+    rsv.rsv_load_scenarios(ctx, synth.flat_scenarios(n_steps=1200))
+    rsv.rsv_load_portfolio(ctx, pol)
+    with pytest.raises(rsv.RsvError) as e:
+        rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F32, rsv.RSV_OUT_SCEN_TOTAL, scen_total=np.zeros(1))
+    assert e.value.status == rsv.RSV_E_ASSUMPTION
+    pol["reversion"][:] = 0.5
+    pol["product"][0] = 9
+    rsv.rsv_load_portfolio(ctx, pol)
+    with pytest.raises(rsv.RsvError) as e:
+        rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F32, rsv.RSV_OUT_SCEN_TOTAL, scen_total=np.zeros(1))
+    assert e.value.status == rsv.RSV_E_ARG
+
+
+def test_deterministic_reruns(ctx):
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_mix(500, seed=2)
+    v = synth.vasicek_paths(64, 1200, seed=2)
+    a = run(ctx, pol, tab, v, rsv.RSV_FORM_F32_COMP)
+    b = run(ctx, pol, tab, v, rsv.RSV_FORM_F32_COMP)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_config2_full_size_sampled(ctx):
+    """100,000-policy mix x 1,000 Vasicek scenarios x 1,200 steps, the benchmark's
+    launch configuration (tuned variant, device outputs): sampled policies
+    against the oracle, and the FP64 totals against the FP64 sum of V0."""
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_mix(100_000, seed=0)
+    v = synth.vasicek_paths(1000, 1200, seed=0)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    form = rsv.RSV_FORM_F32_COMP
+    rsv.rsv_tune(ctx, form, reps=1)
+    V0 = torch.empty((100_000, 1000), dtype=torch.float32, device="cuda")
+    tot = torch.empty(1000, dtype=torch.float64, device="cuda")
+    rsv.rsv_compute_reserves(ctx, form, V0T, on_device=True, V0=V0, scen_total=tot)
+    rsv.rsv_synchronize(ctx)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(100_000, 300, replace=False))
+    sub = synth.take(pol, idx)
+    ref, _ = oracle.reserves_batch(sub, tab, v)
+    got = V0[torch.as_tensor(idx, device="cuda")].double().cpu().numpy()
+    # V0 is stored as FP32: its rounding (2^-24 relative) adds to the recurrence error
+    err = rel_err(got, ref, sub["amount"])
+    print(f"config-2 sampled: max rel err {err.max():.3e}")
+    assert err.max() <= 1e-6
+    host_sum = V0.double().sum(dim=0).cpu().numpy()
+    assert np.max(np.abs(tot.cpu().numpy() - host_sum) / host_sum) <= 1e-9
