@@ -195,17 +195,23 @@ def cpu_baseline(pol, tab, v, n_sample, gpu_rows):
 
 
 def main():
+    global N_POL, N_SCEN, WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", default="f32comp,f32,f64")
-    ap.add_argument("--cpu-sample", type=int, default=2000, help="policies in the CPU oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=500, help="policies in the CPU oracle sample")
+    ap.add_argument("--policies", type=int, default=100_000, help="smaller portfolios for profiling runs")
+    ap.add_argument("--scenarios", type=int, default=1000, help="smaller scenario sets for profiling runs")
     ap.add_argument("--ref-policies", type=int, default=1000, help="policies per reference-arm step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
+    if (args.policies, args.scenarios) != (N_POL, N_SCEN):
+        N_POL, N_SCEN = args.policies, args.scenarios
+        WORKLOAD = f"profiling case: {N_POL}-policy mix x {N_SCEN} Vasicek scenarios x {N_STEPS} monthly steps"
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -325,6 +331,8 @@ def main():
 
     rsv.rsv_destroy(ctx)
     if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
         return
 
     cpu, errs = (None, {})

@@ -2,13 +2,16 @@
 #include "recur_kernel.cuh"
 
 namespace rsv {
+// (form, policies per thread P, scenarios per thread M, threads per CTA, minimum
+// resident CTAs per SM (caps registers), side outputs)
 static const Variant kComp[] = {
-    RSV_VARIANT(F_COMP, 2, 1, 256, false, "comp P2xM1 nt256"),
-    RSV_VARIANT(F_COMP, 4, 1, 256, false, "comp P4xM1 nt256"),
-    RSV_VARIANT(F_COMP, 2, 2, 256, false, "comp P2xM2 nt256"),
-    RSV_VARIANT(F_COMP, 4, 2, 128, false, "comp P4xM2 nt128"),
-    RSV_VARIANT(F_COMP, 1, 2, 256, false, "comp P1xM2 nt256"),
-    RSV_VARIANT(F_COMP, 2, 1, 256, true, "comp P2xM1 nt256 side-outputs"),
+    RSV_VARIANT(F_COMP, 2, 2, 256, 1, false, "comp P2xM2 nt256"),
+    RSV_VARIANT(F_COMP, 2, 2, 256, 3, false, "comp P2xM2 nt256 min3"),
+    RSV_VARIANT(F_COMP, 2, 1, 256, 3, false, "comp P2xM1 nt256 min3"),
+    RSV_VARIANT(F_COMP, 4, 1, 256, 2, false, "comp P4xM1 nt256 min2"),
+    RSV_VARIANT(F_COMP, 1, 2, 256, 3, false, "comp P1xM2 nt256 min3"),
+    RSV_VARIANT(F_COMP, 2, 1, 128, 6, false, "comp P2xM1 nt128 min6"),
+    RSV_VARIANT(F_COMP, 2, 1, 256, 1, true, "comp P2xM1 nt256 side-outputs"),
 };
 const Variant* variants_comp(int* n) {
     *n = (int)(sizeof(kComp) / sizeof(kComp[0]));

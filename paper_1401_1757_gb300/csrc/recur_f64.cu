@@ -5,10 +5,10 @@ namespace rsv {
 // The last entry of each list is the variant with trajectory / per-step-mean
 // outputs; the others are the tunable fast variants.
 static const Variant kF64[] = {
-    RSV_VARIANT(F_F64, 2, 1, 128, false, "f64 P2xM1 nt128"),
-    RSV_VARIANT(F_F64, 4, 1, 128, false, "f64 P4xM1 nt128"),
-    RSV_VARIANT(F_F64, 2, 2, 128, false, "f64 P2xM2 nt128"),
-    RSV_VARIANT(F_F64, 2, 1, 128, true, "f64 P2xM1 nt128 side-outputs"),
+    RSV_VARIANT(F_F64, 2, 2, 128, 1, false, "f64 P2xM2 nt128"),
+    RSV_VARIANT(F_F64, 4, 1, 128, 1, false, "f64 P4xM1 nt128"),
+    RSV_VARIANT(F_F64, 2, 1, 128, 1, false, "f64 P2xM1 nt128"),
+    RSV_VARIANT(F_F64, 2, 1, 128, 1, true, "f64 P2xM1 nt128 side-outputs"),
 };
 const Variant* variants_f64(int* n) {
     *n = (int)(sizeof(kF64) / sizeof(kF64[0]));

@@ -98,23 +98,28 @@ __device__ __forceinline__ void step_jl(R v, R px, R qx, R py, R qy, R rho, R& V
     V10 = n10;
 }
 
-// Compensated form: every quantity is a double-float; inputs arrive as
-// hi/lo pairs of their FP64 values.
+// Compensated form.  Quantities that multiply along the chain (the discount
+// x survival factors and the running reserve) are double-floats built from
+// hi/lo inputs, so their per-step error stays near 2^-44 and cannot compound.
+// Terms injected additively at one step (the assurance's death probability
+// q, the reversion rho, and the JL one-step death transitions qy r01 + qx r10)
+// enter the reserve once, weighted by their own share of it, so their FP32
+// rounding bounds the relative error of every r_t by a few 2^-24 (~2e-7)
+// however long the projection.
 __device__ __forceinline__ df step_ann(df v, df p, df V) {
     return df_mul(df_mul(v, p), df_add_one(V));
 }
 __device__ __forceinline__ df step_ass(df v, df p, df q, df V) {
-    return df_mul(v, df_add_pos(q, df_mul(p, V)));
+    return df_mul(v, df_add_float_pos(df_mul(p, V), q.h));
 }
 __device__ __forceinline__ void step_jl(df v, df px, df qx, df py, df qy, df rho, df& V00, df& V01,
                                         df& V10) {
     df gx = df_mul(v, px), gy = df_mul(v, py);
     df n01 = df_mul(gx, df_add_one(V01));
-    df n10 = df_mul(gy, df_add_pos(rho, V10));
+    df n10 = df_mul(gy, df_add_float_pos(V10, rho.h));
     df t0 = df_mul(df_mul(gx, py), df_add_one(V00));
-    df t1 = df_mul(qy, n01);
-    df t2 = df_mul(qx, n10);
-    V00 = df_add_pos(df_add_pos(t0, t1), t2);
+    const float t12 = __fmaf_rn(qx.h, n10.h, __fmul_rn(qy.h, n01.h));
+    V00 = df_add_float_pos(t0, t12);
     V01 = n01;
     V10 = n10;
 }
@@ -287,8 +292,8 @@ struct Tile {
     }
 };
 
-template <int FORM, int P, int M, int NT, bool EXTRA>
-__global__ void __launch_bounds__(NT) recur_kernel(const RecurArgs a) {
+template <int FORM, int P, int M, int NT, int MINB, bool EXTRA>
+__global__ void __launch_bounds__(NT, MINB) recur_kernel(const RecurArgs a) {
     using TabE = typename Tr<FORM>::TabE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint64_t bar;
@@ -326,25 +331,28 @@ struct Variant {
     cudaError_t (*occupancy)(int* blocks_per_sm, size_t smem);
 };
 
-template <int FORM, int P, int M, int NT, bool EXTRA>
+template <int FORM, int P, int M, int NT, int MINB, bool EXTRA>
 cudaError_t launch_recur(const RecurArgs& a, int grid, size_t smem, cudaStream_t st) {
-    auto k = recur_kernel<FORM, P, M, NT, EXTRA>;
+    auto k = recur_kernel<FORM, P, M, NT, MINB, EXTRA>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NT, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int FORM, int P, int M, int NT, bool EXTRA>
+template <int FORM, int P, int M, int NT, int MINB, bool EXTRA>
 cudaError_t occupancy_recur(int* blocks, size_t smem) {
-    auto k = recur_kernel<FORM, P, M, NT, EXTRA>;
+    auto k = recur_kernel<FORM, P, M, NT, MINB, EXTRA>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, NT, smem);
 }
 
-#define RSV_VARIANT(FORM, P, M, NT, EXTRA, NAME) \
-    Variant { FORM, P, M, NT, EXTRA, NAME, &launch_recur<FORM, P, M, NT, EXTRA>, &occupancy_recur<FORM, P, M, NT, EXTRA> }
+#define RSV_VARIANT(FORM, P, M, NT, MINB, EXTRA, NAME)                          \
+    Variant {                                                                    \
+        FORM, P, M, NT, EXTRA, NAME, &launch_recur<FORM, P, M, NT, MINB, EXTRA>, \
+            &occupancy_recur<FORM, P, M, NT, MINB, EXTRA>                        \
+    }
 
 // Each form's translation unit defines these.
 const Variant* variants_f64(int* n);

@@ -97,6 +97,15 @@ __device__ __forceinline__ df df_add_one(df a) {
     return df{s, e};
 }
 
+// a + b for df a >= 0 and float b >= 0 (b carries no tail).
+__device__ __forceinline__ df df_add_float_pos(df a, float b) {
+    float hi = fmaxf(a.h, b), lo = fminf(a.h, b);
+    float s = __fadd_rn(hi, lo);
+    float e = __fsub_rn(lo, __fsub_rn(s, hi));
+    e = __fadd_rn(e, a.l);
+    return df{s, e};
+}
+
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.h + (double)a.l; }
 
 // ------------------------------------------------------------------------
