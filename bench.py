@@ -46,7 +46,7 @@ WORKLOAD = ("100,000-policy mix (40% SL annuities, 20% JL reversionary 3-state, 
 # FP32 operations per chain-step of each form (add/sub/mul/min/max = 1, FMA = 2),
 # counted from the formulas the kernels evaluate.
 FLOPS = {"f32": {0: 3, 1: 13, 2: 3, 3: 3},
-         "f32comp": {0: 20, 1: 89, 2: 21, 3: 21},
+         "f32comp": {0: 20, 1: 71, 2: 20, 3: 20},
          "f64": {0: 3, 1: 13, 2: 3, 3: 3}}
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = 2 * FP32_LANES * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 at 2070 MHz
@@ -71,11 +71,11 @@ def algorithmic_flops(pol, form, n_scen):
 
 
 def kernel_source_hash():
+    """Hash of the sources the valuation recurrence kernel is built from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1401_1757_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in ("rsv_device.cuh", "recur_kernel.cuh", "recur_comp.cu", "recur_f32.cu", "recur_f64.cu"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -173,6 +173,53 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
+NESTED = dict(n_pol=2000, n_outer=100, n_nodes=40, node_step=12, n_inner=1000)
+NESTED_WORKLOAD = ("nested brute force: 2,000 single-life annuities (ages 60-90) x 100 outer Vasicek paths x "
+                   "40 annual nodes x 1,000 inner paths, compensated FP32")
+
+
+def bench_nested(rsv, torch, tab, steps, warmup):
+    """The nested valuation: live (policy, outer path, node, inner path) valuations per
+    second, device time of the whole pipeline (outer paths, inner-path generation,
+    recurrence, node statistics), plus the closed-form inner expectation."""
+    cfg = NESTED
+    pol = synth.portfolio_single_life(cfg["n_pol"], seed=0)
+    S = policy_steps(pol)
+    live = chain_steps = 0
+    for n in range(cfg["n_nodes"]):
+        rem = S - n * cfg["node_step"]
+        live += int((rem > 0).sum())
+        chain_steps += int(rem[rem > 0].sum())
+    scale = cfg["n_outer"] * cfg["n_inner"]
+    ctx = rsv.rsv_create(torch.cuda.current_device(), torch.cuda.current_stream())
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    NO, NN, NI = cfg["n_outer"], cfg["n_nodes"], cfg["n_inner"]
+    mean = torch.empty((NO, NN), dtype=torch.float64, device="cuda")
+    q = torch.empty((NO, NN), dtype=torch.float64, device="cuda")
+    spec = dict(n_outer=NO, n_nodes=NN, node_step_m=cfg["node_step"], seed=0, on_device=True, L_mean=mean, L_q995=q)
+    res = {}
+    for mode, name, ni in [(rsv.RSV_NESTED_MC, "brute_force", NI), (rsv.RSV_NESTED_CURVE, "curve", 1)]:
+        for _ in range(warmup):
+            rsv.rsv_compute_nested(ctx, rsv.RSV_FORM_F32_COMP, n_inner=NI, mode=mode, **spec)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            rsv.rsv_compute_nested(ctx, rsv.RSV_FORM_F32_COMP, n_inner=NI, mode=mode, **spec)
+            ms.append(rsv.rsv_last_kernel_ms(ctx))
+        t = statistics.mean(ms) / 1e3
+        vals = live * (cfg["n_outer"] * ni)
+        res[name] = {"valuations_s": vals / t, "ms": t * 1e3, "valuations": vals,
+                     "chain_steps_s": chain_steps * cfg["n_outer"] * ni / t}
+    rsv.rsv_destroy(ctx)
+    res["workload"] = NESTED_WORKLOAD
+    res["live_valuations"] = live * scale
+    res["chain_steps"] = chain_steps * scale
+    res["paper_brute_force_estimate"] = ("the paper's cost model (Section 5.3.2) for its 500k portfolio is "
+                                         "~550 h on a 2-core laptop")
+    return res
+
+
 def cpu_baseline(pol, tab, v, n_sample, gpu_rows):
     """Oracle timed on the host cores on the first n_sample policies x all
     scenarios; also the max relative error of each GPU form on that sample."""
@@ -202,12 +249,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", default="f32comp,f32,f64")
-    ap.add_argument("--cpu-sample", type=int, default=500, help="policies in the CPU oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=1500, help="policies in the CPU oracle sample")
     ap.add_argument("--policies", type=int, default=100_000, help="smaller portfolios for profiling runs")
     ap.add_argument("--scenarios", type=int, default=1000, help="smaller scenario sets for profiling runs")
     ap.add_argument("--ref-policies", type=int, default=1000, help="policies per reference-arm step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-nested", action="store_true")
     args = ap.parse_args()
     if (args.policies, args.scenarios) != (N_POL, N_SCEN):
         N_POL, N_SCEN = args.policies, args.scenarios
@@ -292,7 +340,12 @@ def main():
             "tune_ms": {rsv.rsv_variant_name(fid, i): round(m, 3) for i, m in enumerate(tune_ms)},
             "wall_s_incl_flush": wall,
         }
-        sample_rows[form] = V0[: args.cpu_sample].cpu().numpy()
+        # accuracy sample: the same launch writing FP64 reserves for the first policies
+        V0d = torch.empty((N_POL, N_SCEN), dtype=torch.float64, device="cuda")
+        rsv.rsv_compute_reserves(ctx, fid, rsv.RSV_OUT_V0, on_device=True, V0d=V0d)
+        torch.cuda.synchronize()
+        sample_rows[form] = V0d[: args.cpu_sample].cpu().numpy()
+        del V0d
 
     # end to end through the C ABI with host buffers (head form)
     e2e = None
@@ -330,6 +383,9 @@ def main():
                "ms_per_step": 1e3 * tot_s / args.steps}
 
     rsv.rsv_destroy(ctx)
+    nested = None
+    if not args.no_nested and rank == 0:
+        nested = bench_nested(rsv, torch, tab, steps=2, warmup=1)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -363,6 +419,7 @@ def main():
         "gpu_launches": 3 * h["steps"],
         "clocks": clocks,
         "forms": results,
+        "nested": nested,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -174,6 +174,61 @@ rsv_status rsv_load_scenarios(rsv_ctx *ctx, const double *v, int32_t n_scen, int
  * finite, a projection longer than n_steps), RSV_E_CUDA, RSV_E_NOMEM. */
 rsv_status rsv_compute_reserves(rsv_ctx *ctx, const rsv_opts *opts, rsv_out *out);
 
+/* ---- Nested ("brute force") valuation -------------------------------------
+ * Section 2 of the paper: at each future valuation node every policy is
+ * valued under 1000 Monte Carlo scenarios, and the 99.5% liability is the
+ * 5th largest of the 1000.  Outer Vasicek paths o start at r0; node n is at
+ * month n * node_step_m of the outer path; inner paths (o, n, i) start from
+ * the outer path's short rate at the node.  The liability of inner path i is
+ *   L_{o,n,i} = sum_p amount_p sum_j pi_{p,n,j} r_{p,j}(node),
+ * pi = probability of reduced state j at the node from the valuation state
+ * (deterministic mortality), r = reserve at the node by the recurrence of
+ * rsv_compute_reserves on the inner path's monthly discount factors.
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed, counter
+ * (k, o, 0, 2 << 24) for outer path o and (k, i, n, (3 << 24) | o) for inner
+ * path i of node n, words 0,1 -> step 2k and 2,3 -> step 2k+1 as uniforms
+ * (w + 1/2) 2^-32, Box-Muller; exact monthly Vasicek steps of (r, integral
+ * of r), v = exp(-integral of r), all in FP64. */
+enum {
+    RSV_NESTED_MC = 0,     /* inner Monte Carlo ("brute force")                       */
+    RSV_NESTED_CURVE = 2   /* inner expectation in closed form: the recurrence on the
+                              Vasicek forward curve P(t+1|r)/P(t|r) (one chain each)   */
+};
+
+typedef struct {
+    int32_t n_outer;      /* outer paths, >= 1                                         */
+    int32_t n_nodes;      /* valuation nodes (months 0, node_step_m, ...), >= 1        */
+    int32_t node_step_m;  /* months between nodes, >= 1                                */
+    int32_t n_inner;      /* inner paths per (outer path, node), 1 .. 1048576           */
+    uint64_t seed;        /* Philox key                                                */
+    double a, b, sigma;   /* Vasicek dr = a (b - r) dt + sigma dW; a > 0, sigma >= 0    */
+    double r0;            /* short rate at month 0                                     */
+    int32_t mode;         /* RSV_NESTED_MC or RSV_NESTED_CURVE                         */
+    int32_t batch_outer;  /* outer paths per inner-path batch; 0 = fit 4 GiB           */
+} rsv_nested_spec;
+
+/* Outputs (caller-sized; host or device pointers per rsv_opts.on_device):
+ *   L_mean [n_outer][n_nodes]  mean over inner paths of L_{o,n,i}
+ *   L_q995 [n_outer][n_nodes]  k-th largest of the n_inner values, k =
+ *                              ceil(0.005 n_inner) (5th of 1000); with
+ *                              RSV_NESTED_CURVE both equal the curve value
+ *   r_node [n_outer][n_nodes]  outer short rate at the node (optional)
+ *   D0     [n_outer][n_nodes]  outer discount product month 0 -> node (optional)
+ *   L_all  [n_outer][n_nodes][n_inner] every L_{o,n,i} (optional; n_inner = 1
+ *                              with RSV_NESTED_CURVE)
+ * Values are at the node (not discounted to 0). */
+typedef struct {
+    double *L_mean, *L_q995, *r_node, *D0, *L_all;
+} rsv_nested_out;
+
+/* Nested valuation of the loaded portfolio (tables and portfolio needed, no
+ * scenario set).  opts->form selects the arithmetic, opts->outputs and
+ * opts->horizon must be 0.  Blocking unless opts->on_device.
+ * Errors: RSV_E_STATE, RSV_E_ARG (bad spec, NULL L_mean/L_q995, a record as
+ * in rsv_compute_reserves), RSV_E_ASSUMPTION, RSV_E_CUDA, RSV_E_NOMEM. */
+rsv_status rsv_compute_nested(rsv_ctx *ctx, const rsv_opts *opts, const rsv_nested_spec *spec,
+                              rsv_nested_out *out);
+
 /* Kernel variants of a form (policies x scenarios per thread, CTA size):
  * how many there are, and a printable description of one. */
 int32_t rsv_variant_count(int32_t form);

@@ -76,15 +76,14 @@ def _load(path=None):
 
 
 def _bind_nested(lib):
-    dp, ip, u64 = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_uint64
+    dp, ip, u32 = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_uint32
     lib.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
-    lib.orc_gauss_pair.argtypes = [u64, C.c_uint32, C.c_uint32, C.c_uint32, dp]
-    lib.orc_vasicek_path.argtypes = [u64, C.c_uint32, C.c_uint32, C.c_double, C.c_double, C.c_double,
-                                     C.c_double, C.c_double, C.c_int, dp, dp]
-    lib.orc_nested_node.argtypes = [C.c_int64, ip, ip, C.POINTER(C.c_double), C.c_int32, C.c_int32, dp,
-                                    u64, C.c_uint32, C.c_int32, C.c_int32, C.c_double, C.c_double,
-                                    C.c_double, C.c_double, C.c_int32, C.c_int32, C.POINTER(C.c_int32),
-                                    C.c_int32, C.c_int32, dp]
+    lib.orc_gauss_pair.argtypes = [C.c_uint64, u32, u32, u32, u32, dp]
+    lib.orc_vasicek_path.argtypes = [C.c_uint64, u32, u32, u32, C.c_double, C.c_double, C.c_double,
+                                     C.c_double, C.c_int, dp, dp]
+    lib.orc_nested_node.argtypes = [C.c_int64, ip, ip, dp, C.c_int32, C.c_int32, dp, C.c_uint64,
+                                    C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                    C.c_int32, C.c_int32, ip, dp, dp, dp]
 
 
 def _d(a):
@@ -179,3 +178,58 @@ def reserves_batch(pol: dict, tables, v, horizon: int = 0, nthreads: int = 0, to
 
 def max_threads() -> int:
     return _load().orc_max_threads()
+
+
+# ------------------------------------------------------------------ nested ----
+STREAM_OUTER, STREAM_INNER = 2, 3
+
+
+def philox4x32_10(ctr, key):
+    c = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (C.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    out = (C.c_uint32 * 4)()
+    _load().orc_philox4x32_10(c, k, out)
+    return [int(x) for x in out]
+
+
+def gauss_pairs(seed, k, c1, c2, c3):
+    z = np.zeros(4)
+    _load().orc_gauss_pair(seed, k, c1, c2, c3, _p(z))
+    return z
+
+
+def vasicek_path(seed, c1, c2, c3, n_steps, r_start, a=0.1, b=0.04, sigma=0.01):
+    """(v[0..n_steps), r after n_steps) of one counter-based Vasicek path."""
+    v = np.zeros(max(1, n_steps))
+    r = C.c_double()
+    _load().orc_vasicek_path(seed, c1, c2, c3, a, b, sigma, r_start, n_steps, _p(v), C.byref(r))
+    return v[:n_steps], r.value
+
+
+def outer_path(seed, o, n_steps, r0=0.03, a=0.1, b=0.04, sigma=0.01):
+    return vasicek_path(seed, o, 0, STREAM_OUTER << 24, n_steps, r0, a, b, sigma)
+
+
+def inner_path(seed, o, n, i, n_steps, r_start, a=0.1, b=0.04, sigma=0.01):
+    return vasicek_path(seed, i, n, (STREAM_INNER << 24) | o, n_steps, r_start, a, b, sigma)
+
+
+def nested_node(pol, tables, seed, o, n, idx, node_step=12, a=0.1, b=0.04, sigma=0.01, r0=0.03):
+    """Liabilities L_{o,n,i} (FP64) for the inner paths ``idx`` of node n of outer
+    path o, and (rate at the node, discount product 0 -> node)."""
+    lib = _load()
+    tables = np.atleast_2d(_d(tables))
+    nn = len(pol["product"])
+    ipol = np.ascontiguousarray(np.stack([pol["age1_m"], pol["age2_m"], pol["term_m"], pol["state0"],
+                                          pol["table1"], pol["table2"]], axis=1).astype(np.int32))
+    dpol = np.ascontiguousarray(np.stack([pol["amount"], pol["reversion"]], axis=1).astype(np.float64))
+    prod = _i(pol["product"])
+    idx = _i(np.atleast_1d(idx))
+    L = np.zeros(len(idx))
+    rn, d0 = C.c_double(), C.c_double()
+    st = lib.orc_nested_node(nn, _p(prod, C.c_int32), _p(ipol, C.c_int32), _p(dpol), tables.shape[0],
+                             tables.shape[1], _p(tables), seed, a, b, sigma, r0, node_step, o, n, len(idx),
+                             _p(idx, C.c_int32), _p(L), C.byref(rn), C.byref(d0))
+    if st != 0:
+        raise ValueError(f"orc_nested_node failed with code {st}")
+    return L, rn.value, d0.value

@@ -1,0 +1,365 @@
+// nested.cu -- the nested ("brute force") Solvency II valuation on sm_103a.
+//
+// Tucker & Bull (Section 2) value every policy under 1000 Monte Carlo
+// scenarios at each future valuation node and take the 5th largest of the
+// 1000 liabilities as the 99.5% value.  Here, for outer Vasicek paths o,
+// nodes n at months m_n = n * node_step and inner paths i started from the
+// outer path's short rate at the node:
+//
+//   L_{o,n,i} = sum_p amount_p sum_j pi_{p,n,j} r_{p,j}(node; inner path i)
+//
+// where pi_{p,n,j} is the probability that policy p is in reduced state j at
+// the node (deterministic mortality, FP64 on the host) and r_{p,j} is the
+// reserve at the node by the backward recurrence (Eq. generalForm) on the
+// inner path's discount factors -- the same tile kernels as the valuation
+// run, started t_off = m_n steps later.
+//
+// Random numbers: Philox4x32-10 (Salmon et al., SC'11), counter (k, c1, c2,
+// c3), key (seed lo, seed hi); step 2k takes words 0,1 and step 2k+1 words
+// 2,3 as uniforms (w + 1/2) 2^-32, Box-Muller in FP64.  Outer path o:
+// (k, o, 0, 2 << 24); inner path (o, n, i): (k, i, n, (3 << 24) | o).
+// Vasicek exact monthly step of (r, integral of r) (Glasserman 2004 3.3.1);
+// v = exp(-integral), FP64, stored in the form's plane format.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "nested.cuh"
+
+namespace rsv {
+
+// ------------------------------------------------------------ generator ----
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                              uint32_t k1, uint32_t (&out)[4]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+VasStep vasicek_step_constants(double a, double b, double sigma, double dt) {
+    VasStep s;
+    const double one_m_e = -std::expm1(-a * dt), one_m_e2 = -std::expm1(-2.0 * a * dt);
+    const double var_r = sigma * sigma * one_m_e2 / (2.0 * a);
+    const double var_i = sigma * sigma / (a * a) * (dt - 2.0 * one_m_e / a + one_m_e2 / (2.0 * a));
+    const double cov = sigma * sigma / (2.0 * a * a) * one_m_e * one_m_e;
+    s.e = std::exp(-a * dt);
+    s.k1 = one_m_e / a;
+    s.l11 = std::sqrt(var_r);
+    s.l21 = s.l11 > 0 ? cov / s.l11 : 0.0;
+    s.l22 = std::sqrt(std::max(var_i - s.l21 * s.l21, 0.0));
+    s.b = b;
+    s.dt = dt;
+    return s;
+}
+
+// One path: n_steps monthly steps from rate r; calls `emit(t, v_t)`.
+template <class Emit>
+__device__ __forceinline__ double vasicek_path(const VasStep& s, uint64_t seed, uint32_t c1, uint32_t c2,
+                                               uint32_t c3, double r, int n_steps, Emit emit) {
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const double inv32 = 2.3283064365386963e-10;   // 2^-32
+    for (int t = 0; t < n_steps; t += 2) {
+        uint32_t w[4];
+        philox4x32_10((uint32_t)(t >> 1), c1, c2, c3, k0, k1, w);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (t + h >= n_steps) break;
+            const double u1 = ((double)w[2 * h] + 0.5) * inv32;
+            const double u2 = ((double)w[2 * h + 1] + 0.5) * inv32;
+            const double R = sqrt(-2.0 * log(u1));
+            double sn, cs;
+            sincospi(2.0 * u2, &sn, &cs);
+            const double z1 = R * cs, z2 = R * sn;
+            const double I = s.b * s.dt + (r - s.b) * s.k1 + s.l21 * z1 + s.l22 * z2;
+            r = s.b + (r - s.b) * s.e + s.l11 * z1;
+            emit(t + h, exp(-I), r);
+        }
+    }
+    return r;
+}
+
+__global__ void outer_paths_kernel(VasStep s, uint64_t seed, int n_outer, int n_nodes, int node_step, double r0,
+                                   double* __restrict__ r_node, double* __restrict__ d0) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n_outer) return;
+    r_node[(size_t)o * n_nodes] = r0;
+    d0[(size_t)o * n_nodes] = 1.0;
+    int next = 1;
+    double D = 1.0;
+    vasicek_path(s, seed, (uint32_t)o, 0u, 2u << 24, r0, (n_nodes - 1) * node_step,
+                 [&](int t, double v, double r_after) {
+                     D *= v;
+                     if (t + 1 == next * node_step) {
+                         r_node[(size_t)o * n_nodes + next] = r_after;
+                         d0[(size_t)o * n_nodes + next] = D;
+                         ++next;
+                     }
+                 });
+}
+
+template <class VE>
+__device__ __forceinline__ VE to_plane(double x);
+template <>
+__device__ __forceinline__ double to_plane<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_plane<float>(double x) { return __double2float_rn(x); }
+template <>
+__device__ __forceinline__ float2 to_plane<float2>(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+// Inner paths of outer paths [o0, o0 + B), every node: one thread per path.
+// Plane layout [B][n_nodes][Lmax][i_pad]; node n fills rows 0 .. Ln[n]-1.
+template <class VE>
+__global__ void inner_paths_kernel(VasStep s, uint64_t seed, int o0, int B, int n_nodes, int n_inner, int i_pad,
+                                   int Lmax, const int* __restrict__ Ln, const double* __restrict__ r_node,
+                                   VE* __restrict__ plane) {
+    const size_t total = (size_t)B * n_nodes * i_pad;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % i_pad);
+        const int n = (int)((idx / i_pad) % n_nodes);
+        const int ol = (int)(idx / ((size_t)i_pad * n_nodes));
+        const int o = o0 + ol;
+        VE* base = plane + ((size_t)ol * n_nodes + n) * Lmax * i_pad + i;
+        const int L = Ln[n];
+        if (i >= n_inner) {   // padding lanes read finite factors
+            for (int t = 0; t < L; ++t) base[(size_t)t * i_pad] = to_plane<VE>(1.0);
+            continue;
+        }
+        vasicek_path(s, seed, (uint32_t)i, (uint32_t)n, (3u << 24) | (uint32_t)o, r_node[(size_t)o * n_nodes + n],
+                     L, [&](int t, double v, double) { base[(size_t)t * i_pad] = to_plane<VE>(v); });
+    }
+}
+
+// Conditional forward discount curve of the Vasicek model at each node (the
+// expectation of the inner loop): vbar_tau = P((tau+1) dt | r) / P(tau dt | r)
+// with the zero-coupon price P(T | r) = A(T) exp(-B(T) r) (Vasicek 1977).
+__device__ __forceinline__ double vasicek_lnP(double T, double r, double a, double b, double sigma) {
+    const double B = -expm1(-a * T) / a;
+    return (B - T) * (a * a * b - 0.5 * sigma * sigma) / (a * a) - sigma * sigma * B * B / (4.0 * a) - B * r;
+}
+
+template <class VE>
+__global__ void curve_planes_kernel(double a, double b, double sigma, double dt, int o0, int B, int n_nodes,
+                                    int i_pad, int Lmax, const int* __restrict__ Ln,
+                                    const double* __restrict__ r_node, VE* __restrict__ plane) {
+    const size_t total = (size_t)B * n_nodes * Lmax;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int t = (int)(idx % Lmax);
+        const int n = (int)((idx / Lmax) % n_nodes);
+        const int ol = (int)(idx / ((size_t)Lmax * n_nodes));
+        if (t >= Ln[n]) continue;
+        const double r = r_node[(size_t)(o0 + ol) * n_nodes + n];
+        const double v = exp(vasicek_lnP((t + 1) * dt, r, a, b, sigma) - vasicek_lnP(t * dt, r, a, b, sigma));
+        VE* row = plane + (((size_t)ol * n_nodes + n) * Lmax + t) * i_pad;
+        row[0] = to_plane<VE>(v);
+        for (int i = 1; i < 32; ++i) row[i] = to_plane<VE>(1.0);
+    }
+}
+
+// ------------------------------------------------------- nested recurrence ----
+// One CTA per item (o, n, chunk of 32 inner paths); its warps share the
+// policy tiles, each lane accumulates the pi-weighted reserves of its path,
+// and the CTA adds the warps' sums in a fixed order (deterministic).
+template <int FORM, int P, int NT>
+__global__ void __launch_bounds__(NT) nested_kernel(const NestedArgs a) {
+    using TabE = typename Tr<FORM>::TabE;
+    using VE = typename Tr<FORM>::VE;
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint64_t bar;
+    __shared__ int s_item;
+    __shared__ double red[NW][32];
+    TabE* tab = reinterpret_cast<TabE*>(smem_raw);
+    if (!stage_to_smem(tab, a.tab, (uint32_t)a.tab_bytes, &bar, a.status)) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= a.n_items) break;
+        // items run node-major: early nodes (longest projections) first
+        const int chunk = item % a.n_chunks;
+        const int ol = (item / a.n_chunks) % a.B;
+        const int n = item / (a.n_chunks * a.B);
+        const int m = n * a.node_step;
+        const VE* plane = static_cast<const VE*>(a.v) + ((size_t)ol * a.n_nodes + n) * a.Lmax * a.i_pad;
+        const TileEnv env{a.slots, plane, a.i_pad, a.n_inner, 0, nullptr, nullptr, nullptr};
+        const double* wts = a.wts + (size_t)n * 3;
+        const size_t wstride = (size_t)a.n_nodes * 3;
+        double acc[1] = {0.0};
+        for (int tile = warp; tile < a.n_tiles; tile += NW) {
+            if (a.slots[(size_t)tile * P].S < m) continue;   // whole tile ended before the node
+            const int kind = a.tile_kind[tile];
+            if (kind == K_JL) {
+                Tile<FORM, P, 1, K_JL, false> w(env, tab, tile, chunk, lane, m);
+                w.run_steps();
+                w.epilogue_weighted(acc, wts, wstride);
+            } else if (kind == K_ANN) {
+                Tile<FORM, P, 1, K_ANN, false> w(env, tab, tile, chunk, lane, m);
+                w.run_steps();
+                w.epilogue_weighted(acc, wts, wstride);
+            } else {
+                Tile<FORM, P, 1, K_ASS, false> w(env, tab, tile, chunk, lane, m);
+                w.run_steps();
+                w.epilogue_weighted(acc, wts, wstride);
+            }
+        }
+        red[warp][lane] = acc[0];
+        __syncthreads();
+        if (warp == 0) {
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) sum += red[w][lane];
+            const int i = chunk * 32 + lane;
+            if (i < a.n_inner)
+                a.L_all[((size_t)(a.o0 + ol) * a.n_nodes + n) * a.n_inner + i] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// Mean and k-th largest over the inner paths of each (o, n), one CTA each.
+// The k-th largest is found by descending thresholds: the largest value
+// below the current threshold and its multiplicity, until k values are
+// covered, so ties need no special care.
+__global__ void node_stats_kernel(const double* __restrict__ L_all, int n_inner, int k, double* __restrict__ mean,
+                                  double* __restrict__ kth) {
+    __shared__ double sd[256];
+    __shared__ int si[256];
+    const size_t on = blockIdx.x;
+    const double* x = L_all + on * n_inner;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n_inner; i += blockDim.x) s += x[i];
+    sd[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sd[threadIdx.x] += sd[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mean[on] = sd[0] / n_inner;
+    __syncthreads();
+    double thr = INFINITY;
+    int left = k;
+    for (int round = 0; round < k; ++round) {
+        double mx = -INFINITY;
+        for (int i = threadIdx.x; i < n_inner; i += blockDim.x)
+            if (x[i] < thr) mx = fmax(mx, x[i]);
+        sd[threadIdx.x] = mx;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + w]);
+            __syncthreads();
+        }
+        const double m = sd[0];
+        __syncthreads();
+        int c = 0;
+        for (int i = threadIdx.x; i < n_inner; i += blockDim.x) c += (x[i] == m);
+        si[threadIdx.x] = c;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) si[threadIdx.x] += si[threadIdx.x + w];
+            __syncthreads();
+        }
+        const int cnt = si[0];
+        __syncthreads();
+        if (cnt >= left || m == -INFINITY) {
+            if (threadIdx.x == 0) kth[on] = m;
+            break;
+        }
+        left -= cnt;
+        thr = m;
+    }
+}
+
+// ------------------------------------------------------------- launchers ----
+template <int FORM, int P, int NT>
+cudaError_t launch_nested_t(const NestedArgs& a, int sm_count, size_t smem, cudaStream_t st) {
+    auto k = nested_kernel<FORM, P, NT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, NT, smem);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) return cudaErrorInvalidConfiguration;
+    const long long grid = std::min<long long>((long long)sm_count * bps, std::max(1, a.n_items));
+    k<<<(int)grid, NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+int nested_tile_width(int form) { return form == F_F32 ? 4 : 2; }
+
+cudaError_t launch_nested(int form, const NestedArgs& a, int sm_count, size_t smem, cudaStream_t st) {
+    switch (form) {
+    case F_F64: return launch_nested_t<F_F64, 2, 256>(a, sm_count, smem, st);
+    case F_F32: return launch_nested_t<F_F32, 4, 256>(a, sm_count, smem, st);
+    default: return launch_nested_t<F_COMP, 2, 256>(a, sm_count, smem, st);
+    }
+}
+
+cudaError_t launch_outer_paths(const VasStep& s, uint64_t seed, int n_outer, int n_nodes, int node_step, double r0,
+                               double* r_node, double* d0, cudaStream_t st) {
+    outer_paths_kernel<<<(n_outer + 63) / 64, 64, 0, st>>>(s, seed, n_outer, n_nodes, node_step, r0, r_node, d0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inner_paths(int form, const VasStep& s, uint64_t seed, int o0, int B, int n_nodes, int n_inner,
+                               int i_pad, int Lmax, const int* Ln, const double* r_node, void* plane, int sm_count,
+                               cudaStream_t st) {
+    const int grid = sm_count * 8;
+    if (form == F_F64)
+        inner_paths_kernel<double><<<grid, 128, 0, st>>>(s, seed, o0, B, n_nodes, n_inner, i_pad, Lmax, Ln, r_node,
+                                                          static_cast<double*>(plane));
+    else if (form == F_F32)
+        inner_paths_kernel<float><<<grid, 128, 0, st>>>(s, seed, o0, B, n_nodes, n_inner, i_pad, Lmax, Ln, r_node,
+                                                         static_cast<float*>(plane));
+    else
+        inner_paths_kernel<float2><<<grid, 128, 0, st>>>(s, seed, o0, B, n_nodes, n_inner, i_pad, Lmax, Ln, r_node,
+                                                          static_cast<float2*>(plane));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_curve_planes(int form, double a, double b, double sigma, int o0, int B, int n_nodes, int i_pad,
+                                int Lmax, const int* Ln, const double* r_node, void* plane, int sm_count,
+                                cudaStream_t st) {
+    const int grid = sm_count * 8;
+    const double dt = 1.0 / 12.0;
+    if (form == F_F64)
+        curve_planes_kernel<double><<<grid, 128, 0, st>>>(a, b, sigma, dt, o0, B, n_nodes, i_pad, Lmax, Ln, r_node,
+                                                           static_cast<double*>(plane));
+    else if (form == F_F32)
+        curve_planes_kernel<float><<<grid, 128, 0, st>>>(a, b, sigma, dt, o0, B, n_nodes, i_pad, Lmax, Ln, r_node,
+                                                          static_cast<float*>(plane));
+    else
+        curve_planes_kernel<float2><<<grid, 128, 0, st>>>(a, b, sigma, dt, o0, B, n_nodes, i_pad, Lmax, Ln, r_node,
+                                                           static_cast<float2*>(plane));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_node_stats(const double* L_all, int n_on, int n_inner, int k, double* mean, double* kth,
+                              cudaStream_t st) {
+    if (n_on <= 0) return cudaSuccess;
+    node_stats_kernel<<<n_on, 256, 0, st>>>(L_all, n_inner, k, mean, kth);
+    return cudaGetLastError();
+}
+
+}  // namespace rsv

@@ -1,0 +1,42 @@
+// nested.cuh -- arguments and launchers of the nested valuation kernels.
+#pragma once
+
+#include "recur_kernel.cuh"
+
+namespace rsv {
+
+struct NestedArgs {
+    const void* tab;          // staged decrement tables (form's entry format)
+    int32_t tab_bytes;
+    const void* v;            // inner-path planes of this batch [B][n_nodes][Lmax][i_pad]
+    int32_t i_pad, n_inner, Lmax, n_nodes, node_step, B, o0;
+    const SlotRec* slots;     // policy tiles (valuation-time ages and steps)
+    const int32_t* tile_kind;
+    int32_t n_tiles;
+    const double* wts;        // [n_pol][n_nodes][3] amount x in-force probability per reduced state
+    int32_t n_chunks, n_items;
+    int32_t* counter;
+    int32_t* status;
+    double* L_all;            // [n_outer][n_nodes][n_inner]
+};
+
+// Constants of one exact monthly Vasicek step of (r, integral of r):
+// I = b dt + (r - b) k1 + l21 z1 + l22 z2, r' = b + (r - b) e + l11 z1.
+struct VasStep {
+    double e, k1, l11, l21, l22, b, dt;
+};
+VasStep vasicek_step_constants(double a, double b, double sigma, double dt);
+int nested_tile_width(int form);
+cudaError_t launch_nested(int form, const NestedArgs& a, int sm_count, size_t smem, cudaStream_t st);
+cudaError_t launch_outer_paths(const VasStep& s, uint64_t seed, int n_outer, int n_nodes, int node_step, double r0,
+                               double* r_node, double* d0, cudaStream_t st);
+cudaError_t launch_inner_paths(int form, const VasStep& s, uint64_t seed, int o0, int B, int n_nodes, int n_inner,
+                               int i_pad, int Lmax, const int* Ln, const double* r_node, void* plane, int sm_count,
+                               cudaStream_t st);
+cudaError_t launch_curve_planes(int form, double a, double b, double sigma, int o0, int B, int n_nodes, int i_pad,
+                                int Lmax, const int* Ln, const double* r_node, void* plane, int sm_count,
+                                cudaStream_t st);
+cudaError_t launch_node_stats(const double* L_all, int n_on, int n_inner, int k, double* mean, double* kth,
+                              cudaStream_t st);
+
+}  // namespace rsv

@@ -105,7 +105,10 @@ __device__ __forceinline__ void step_jl(R v, R px, R qx, R py, R qy, R rho, R& V
 // q, the reversion rho, and the JL one-step death transitions qy r01 + qx r10)
 // enter the reserve once, weighted by their own share of it, so their FP32
 // rounding bounds the relative error of every r_t by a few 2^-24 (~2e-7)
-// however long the projection.
+// however long the projection.  The double-floats are never renormalised:
+// their tails carry the accumulated compensation and grow to ~1e-5 of the
+// head over a thousand steps, so a computed value enters an FP32 term as
+// head + tail, not as its head alone.
 __device__ __forceinline__ df step_ann(df v, df p, df V) {
     return df_mul(df_mul(v, p), df_add_one(V));
 }
@@ -118,7 +121,7 @@ __device__ __forceinline__ void step_jl(df v, df px, df qx, df py, df qy, df rho
     df n01 = df_mul(gx, df_add_one(V01));
     df n10 = df_mul(gy, df_add_float_pos(V10, rho.h));
     df t0 = df_mul(df_mul(gx, py), df_add_one(V00));
-    const float t12 = __fmaf_rn(qx.h, n10.h, __fmul_rn(qy.h, n01.h));
+    const float t12 = __fmaf_rn(qx.h, __fadd_rn(n10.h, n10.l), __fmul_rn(qy.h, __fadd_rn(n01.h, n01.l)));
     V00 = df_add_float_pos(t0, t12);
     V01 = n01;
     V10 = n10;
@@ -131,6 +134,18 @@ struct alignas(sizeof(E) * M) Pack {
 };
 
 // ------------------------------------------------------------- one item ----
+// Where a tile reads its discount factors and writes its side outputs.
+struct TileEnv {
+    const SlotRec* slots;
+    const void* v;       // scenario plane, rows = steps from the valuation point, [rows][s_pad]
+    int s_pad;
+    int n_valid;         // valid scenario columns
+    int n_steps;         // side-output row length - 1
+    const double* amount;
+    double* traj;
+    double* pt_sum;
+};
+
 template <int FORM, int P, int M, int KIND, bool EXTRA>
 struct Tile {
     using T = Tr<FORM>;
@@ -140,7 +155,7 @@ struct Tile {
     using VP = Pack<VE, M>;
     static constexpr int NS = (KIND == K_JL) ? 3 : 1;
 
-    const RecurArgs& a;
+    const TileEnv& e;
     const TabE* __restrict__ tab;
     const VE* __restrict__ vplane;
     int s0;
@@ -149,20 +164,25 @@ struct Tile {
     double amt[P];
     Val V[NS][P][M];
 
-    __device__ __forceinline__ Tile(const RecurArgs& args, const TabE* t, int tile, int chunk, int lane)
-        : a(args), tab(t), vplane(static_cast<const VE*>(args.v)) {
+    // t_off > 0 starts every policy of the tile t_off steps after valuation (a
+    // valuation node of the nested run): ages advance by t_off, the remaining
+    // projection is S - t_off, and row 0 of the plane is the node's first step.
+    // Policies already past their end (S < t_off) become padding.
+    __device__ __forceinline__ Tile(const TileEnv& env, const TabE* t, int tile, int chunk, int lane,
+                                    int t_off = 0)
+        : e(env), tab(t), vplane(static_cast<const VE*>(env.v)) {
         s0 = (chunk * 32 + lane) * M;
-        const SlotRec* rec = a.slots + (size_t)tile * P;
+        const SlotRec* rec = e.slots + (size_t)tile * P;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             const SlotRec r = rec[i];
-            idx1[i] = r.idx1;
-            idx2[i] = r.idx2;
-            Sp[i] = r.S;
+            idx1[i] = r.idx1 + t_off;
+            idx2[i] = r.idx2 + t_off;
+            Sp[i] = r.S - t_off;
             st0[i] = r.state0;
-            pol[i] = r.pol;
+            pol[i] = Sp[i] < 0 ? -1 : r.pol;
             rho[i] = T::pair(r.rho_h, r.rho_l);
-            amt[i] = (EXTRA && r.pol >= 0) ? a.amount[r.pol] : 0.0;
+            amt[i] = (EXTRA && pol[i] >= 0) ? e.amount[pol[i]] : 0.0;
 #pragma unroll
             for (int m = 0; m < M; ++m) {
                 V[0][i][m] = T::cst(r.bnd);
@@ -173,7 +193,7 @@ struct Tile {
     }
 
     __device__ __forceinline__ VP load(int t) const {
-        return *reinterpret_cast<const VP*>(vplane + (size_t)t * a.s_pad + s0);
+        return *reinterpret_cast<const VP*>(vplane + (size_t)t * e.s_pad + s0);
     }
 
     __device__ __forceinline__ Val out_state(int i, int m) const {
@@ -185,20 +205,20 @@ struct Tile {
     __device__ __forceinline__ void record(int t, int i) {
         if (pol[i] < 0) return;
         double sum = 0.0;
-        const size_t row = (size_t)pol[i] * (a.n_steps + 1) + t;
+        const size_t row = (size_t)pol[i] * (e.n_steps + 1) + t;
 #pragma unroll
         for (int m = 0; m < M; ++m) {
             const int s = s0 + m;
-            if (s < a.n_scen) {
+            if (s < e.n_valid) {
                 const double x = amt[i] * T::dbl(out_state(i, m));
-                if (a.traj) a.traj[row * a.n_scen + s] = x;
+                if (e.traj) e.traj[row * e.n_valid + s] = x;
                 sum += x;
             }
         }
-        if (a.pt_sum) {
+        if (e.pt_sum) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            if ((threadIdx.x & 31) == 0) atomicAdd(&a.pt_sum[row], sum);
+            if ((threadIdx.x & 31) == 0) atomicAdd(&e.pt_sum[row], sum);
         }
     }
 
@@ -237,13 +257,15 @@ struct Tile {
         for (int u = 0; u < U; ++u) step<false>(t - u, g[u]);
     }
 
-    __device__ __forceinline__ void run(int tile) {
-        const int Smax = Sp[0], Smin = Sp[P - 1];
+    // Backward substitution from each policy's boundary down to t = 0.
+    __device__ __forceinline__ void run_steps() {
+        const int Smax = Sp[0];
+        const int Smin = Sp[P - 1] > 0 ? Sp[P - 1] : 0;
         if constexpr (EXTRA) {
             // r at t = S_i (the boundary) for the side outputs
 #pragma unroll
             for (int i = 0; i < P; ++i)
-                if (Sp[i] <= a.n_steps) record(Sp[i], i);
+                if (Sp[i] >= 0 && Sp[i] <= e.n_steps) record(Sp[i], i);
         }
         int t = Smax - 1;
         for (; t >= Smin; --t) step<true>(t, load(t));      // ragged head: some policies idle
@@ -264,30 +286,57 @@ struct Tile {
             }
         }
         for (; t >= 0; --t) step<false>(t, load(t));
+    }
 
-        // epilogue: scale by the amount, write V0, per-tile scenario sums
+    // Epilogue of a valuation run: scale by the amount, write V0, per-tile
+    // scenario sums.
+    __device__ __forceinline__ void epilogue_v0(int tile, float* V0f, double* V0d, double* partial) {
         double part[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) part[m] = 0.0;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             if (pol[i] < 0) continue;
-            const double A = a.amount[pol[i]];
+            const double A = e.amount[pol[i]];
 #pragma unroll
             for (int m = 0; m < M; ++m) {
                 const int s = s0 + m;
-                if (s < a.n_scen) {
+                if (s < e.n_valid) {
                     const double x = A * T::dbl(out_state(i, m));
-                    const size_t o = (size_t)pol[i] * a.n_scen + s;
-                    if (a.V0f) a.V0f[o] = (float)x;
-                    if (a.V0d) a.V0d[o] = x;
+                    const size_t o = (size_t)pol[i] * e.n_valid + s;
+                    if (V0f) V0f[o] = (float)x;
+                    if (V0d) V0d[o] = x;
                     part[m] += x;
                 }
             }
         }
-        if (a.partial) {
+        if (partial) {
 #pragma unroll
-            for (int m = 0; m < M; ++m) a.partial[(size_t)tile * a.s_pad + s0 + m] = part[m];
+            for (int m = 0; m < M; ++m) partial[(size_t)tile * e.s_pad + s0 + m] = part[m];
+        }
+    }
+
+    // Epilogue of a nested valuation: add sum_j w_j r_j of every policy to acc,
+    // with w = amount x in-force probability of each reduced state at the node
+    // (wts[pol * stride + j]).
+    __device__ __forceinline__ void epilogue_weighted(double (&acc)[M], const double* __restrict__ wts,
+                                                      size_t stride) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            if (pol[i] < 0) continue;
+            const double* w = wts + (size_t)pol[i] * stride;
+            const double w0 = w[0];
+            double w1 = 0.0, w2 = 0.0;
+            if constexpr (NS == 3) {
+                w1 = w[1];
+                w2 = w[2];
+            }
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                double x = w0 * T::dbl(V[0][i][m]);
+                if constexpr (NS == 3) x += w1 * T::dbl(V[1][i][m]) + w2 * T::dbl(V[2][i][m]);
+                acc[m] += x;
+            }
         }
     }
 };
@@ -300,6 +349,7 @@ __global__ void __launch_bounds__(NT, MINB) recur_kernel(const RecurArgs a) {
     TabE* tab = reinterpret_cast<TabE*>(smem_raw);
     if (!stage_to_smem(tab, a.tab, (uint32_t)a.tab_bytes, &bar, a.status)) return;
 
+    const TileEnv env{a.slots, a.v, a.s_pad, a.n_scen, a.n_steps, a.amount, a.traj, a.pt_sum};
     const int lane = threadIdx.x & 31;
     for (;;) {
         int item = 0;
@@ -310,14 +360,17 @@ __global__ void __launch_bounds__(NT, MINB) recur_kernel(const RecurArgs a) {
         const int chunk = item - tile * a.n_chunks;
         const int kind = a.tile_kind[tile];
         if (kind == K_JL) {
-            Tile<FORM, P, M, K_JL, EXTRA> w(a, tab, tile, chunk, lane);
-            w.run(tile);
+            Tile<FORM, P, M, K_JL, EXTRA> w(env, tab, tile, chunk, lane);
+            w.run_steps();
+            w.epilogue_v0(tile, a.V0f, a.V0d, a.partial);
         } else if (kind == K_ANN) {
-            Tile<FORM, P, M, K_ANN, EXTRA> w(a, tab, tile, chunk, lane);
-            w.run(tile);
+            Tile<FORM, P, M, K_ANN, EXTRA> w(env, tab, tile, chunk, lane);
+            w.run_steps();
+            w.epilogue_v0(tile, a.V0f, a.V0d, a.partial);
         } else {
-            Tile<FORM, P, M, K_ASS, EXTRA> w(a, tab, tile, chunk, lane);
-            w.run(tile);
+            Tile<FORM, P, M, K_ASS, EXTRA> w(env, tab, tile, chunk, lane);
+            w.run_steps();
+            w.epilogue_v0(tile, a.V0f, a.V0d, a.partial);
         }
     }
 }

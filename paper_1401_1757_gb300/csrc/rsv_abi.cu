@@ -15,7 +15,7 @@
 #include <vector>
 
 #include "rsv.h"
-#include "recur_kernel.cuh"
+#include "nested.cuh"
 
 using namespace rsv;
 
@@ -140,6 +140,7 @@ struct rsv_ctx {
     DevBuf d_ctl;       // [0] queue head, [1] status
     DevBuf d_partial, d_part2;
     DevBuf d_o_v0f, d_o_v0d, d_o_tot, d_o_pt, d_o_traj;   // staging for host outputs
+    DevBuf d_nest_w, d_nest_ln, d_nest_rn, d_nest_d0, d_nest_plane, d_nest_mean, d_nest_kth, d_nest_all;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool ev_recorded = false;
     int tuned[3] = {-1, -1, -1};
@@ -169,8 +170,8 @@ int table_len(const rsv_ctx* c, int id) { return (int)c->tab[id].size(); }
 
 // Validate every record against the tables and the scenario length and
 // derive its reduced model (Section 3.6.4), steps and boundary.
-rsv_status prep_policies(rsv_ctx* c, int horizon, std::vector<PolPrep>& out, int& tab_pad, int& n_tab,
-                         double& chain_steps) {
+rsv_status prep_policies(rsv_ctx* c, int horizon, int max_steps, std::vector<PolPrep>& out, int& tab_pad,
+                         int& n_tab, double& chain_steps) {
     const int64_t n = (int64_t)c->pols.size();
     out.resize(n);
     int need = 1;
@@ -208,9 +209,9 @@ rsv_status prep_policies(rsv_ctx* c, int horizon, std::vector<PolPrep>& out, int
             S = horizon;
             bnd = 0.0f;   // truncated projection: r_horizon = 0
         }
-        if (S > c->n_steps)
+        if (S > max_steps)
             return fail(c, RSV_E_ASSUMPTION, "policy %lld: %d steps but scenarios have %d", (long long)i, S,
-                        c->n_steps);
+                        max_steps);
         const int top = std::max(r.age1_m + S, jl ? r.age2_m + S : 0);
         if (top > kMaxAgeSteps)
             return fail(c, RSV_E_ARG, "policy %lld: age + steps %d exceeds %d", (long long)i, top, kMaxAgeSteps);
@@ -233,14 +234,14 @@ rsv_status prep_policies(rsv_ctx* c, int horizon, std::vector<PolPrep>& out, int
     return RSV_OK;
 }
 
-rsv_status build_layout(rsv_ctx* c, int P, int horizon) {
+rsv_status build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
     Layout& L = c->lay;
-    const unsigned long long gen = c->pol_gen * 1000003ull + c->tab_gen * 7919ull + (unsigned)c->n_steps;
+    const unsigned long long gen = c->pol_gen * 1000003ull + c->tab_gen * 7919ull + (unsigned)max_steps;
     if (L.P == P && L.horizon == horizon && L.gen == gen) return RSV_OK;
     std::vector<PolPrep> pp;
     int tab_pad, n_tab;
     double cs;
-    rsv_status st = prep_policies(c, horizon, pp, tab_pad, n_tab, cs);
+    rsv_status st = prep_policies(c, horizon, max_steps, pp, tab_pad, n_tab, cs);
     if (st != RSV_OK) return st;
 
     // group by reduced model, longest projection first
@@ -400,7 +401,7 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     }
     const Variant& V = vl[vi];
 
-    rsv_status st = build_layout(c, V.P, o->horizon);
+    rsv_status st = build_layout(c, V.P, o->horizon, c->n_steps);
     if (st != RSV_OK) return st;
     size_t smem = 0;
     if ((st = build_tables(c, o->form, smem)) != RSV_OK) return st;
@@ -488,6 +489,162 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     return RSV_OK;
 }
 
+// In-force weights amount x Pr[reduced state j at node n] (FP64), the
+// remaining projection length per node, and the nested launch sequence.
+rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* sp, rsv_nested_out* out) {
+    if (!o || !sp || !out) return fail(c, RSV_E_ARG, "opts, spec and out must not be NULL");
+    if (o->form < F_F64 || o->form > F_COMP) return fail(c, RSV_E_ARG, "bad form %d", o->form);
+    if (o->outputs != 0 || o->horizon != 0 || (o->on_device != 0 && o->on_device != 1))
+        return fail(c, RSV_E_ARG, "nested runs take outputs = 0, horizon = 0, on_device 0/1");
+    if (sp->n_outer < 1 || sp->n_nodes < 1 || sp->node_step_m < 1 || sp->n_inner < 1 || sp->n_inner > (1 << 20))
+        return fail(c, RSV_E_ARG, "bad nested sizes");
+    if ((long long)(sp->n_nodes - 1) * sp->node_step_m > kMaxAgeSteps)
+        return fail(c, RSV_E_ARG, "last node beyond %d months", kMaxAgeSteps);
+    if (sp->mode != RSV_NESTED_MC && sp->mode != RSV_NESTED_CURVE) return fail(c, RSV_E_ARG, "bad mode %d", sp->mode);
+    if (!(sp->a > 0.0) || !(sp->sigma >= 0.0) || !std::isfinite(sp->a) || !std::isfinite(sp->b) ||
+        !std::isfinite(sp->sigma) || !std::isfinite(sp->r0) || sp->batch_outer < 0)
+        return fail(c, RSV_E_ARG, "bad Vasicek parameters");
+    if (!out->L_mean || !out->L_q995) return fail(c, RSV_E_ARG, "L_mean and L_q995 are required");
+    bool any_tab = false;
+    for (auto& t : c->tab) any_tab |= !t.empty();
+    if (!any_tab) return fail(c, RSV_E_STATE, "no decrement table loaded");
+
+    const int form = o->form, P = nested_tile_width(form);
+    rsv_status st = build_layout(c, P, 0, kMaxAgeSteps);
+    if (st != RSV_OK) return st;
+    size_t smem = 0;
+    if ((st = build_tables(c, form, smem)) != RSV_OK) return st;
+    const Layout& L = c->lay;
+    const int n_pol = (int)c->pols.size(), NN = sp->n_nodes, NO = sp->n_outer, step = sp->node_step_m;
+    const bool mc = sp->mode == RSV_NESTED_MC;
+    const int n_inner = mc ? sp->n_inner : 1;
+    const int i_pad = (n_inner + 31) / 32 * 32;
+
+    // weights and remaining lengths
+    std::vector<double> w((size_t)std::max(1, n_pol) * NN * 3, 0.0);
+    std::vector<int> Ln(NN, 0);
+    for (int p = 0; p < n_pol; ++p) {
+        const rsv_policy& r = c->pols[p];
+        const bool jl = r.product == RSV_JL_REVERSIONARY, ann = r.product <= RSV_JL_REVERSIONARY;
+        int S;
+        if (r.product == RSV_SL_ANNUITY) {
+            S = std::max(0, table_len(c, r.table1) - r.age1_m);
+            if (r.term_m > 0) S = std::min(S, r.term_m);
+        } else if (jl) {
+            S = std::max(0, std::max(table_len(c, r.table1) - r.age1_m, table_len(c, r.table2) - r.age2_m));
+            if (r.term_m > 0) S = std::min(S, r.term_m);
+        } else {
+            S = r.term_m;
+        }
+        const std::vector<double>& tx = c->tab[r.table1];
+        const std::vector<double>& ty = c->tab[jl ? r.table2 : r.table1];
+        double Px = 1.0, Py = 1.0;
+        int u = 0;
+        for (int n = 0; n < NN; ++n) {
+            const int m = n * step;
+            for (; u < m; ++u) {
+                Px *= (r.age1_m + u < (int)tx.size()) ? tx[r.age1_m + u] : 0.0;
+                if (jl) Py *= (r.age2_m + u < (int)ty.size()) ? ty[r.age2_m + u] : 0.0;
+            }
+            if (S < m || (ann && r.term_m > 0 && r.term_m <= m)) continue;   // ended before the node
+            Ln[n] = std::max(Ln[n], S - m);
+            double* wp = &w[((size_t)p * NN + n) * 3];
+            if (!jl) {
+                wp[0] = r.amount * Px;
+            } else if (r.state0 == 0) {
+                wp[0] = r.amount * Px * Py;
+                wp[1] = r.amount * Px * (1.0 - Py);
+                wp[2] = r.amount * (1.0 - Px) * Py;
+            } else if (r.state0 == 1) {
+                wp[1] = r.amount * Px;
+            } else {
+                wp[2] = r.amount * Py;
+            }
+        }
+    }
+    const int Lmax = std::max(1, *std::max_element(Ln.begin(), Ln.end()));
+    const size_t esz = form == F_F32 ? sizeof(float) : 8;
+    const size_t per_outer = (size_t)NN * Lmax * i_pad * esz;
+    int B = sp->batch_outer > 0 ? sp->batch_outer : (int)std::max<size_t>(1, (size_t(4) << 30) / per_outer);
+    B = std::min(B, NO);
+
+    CU(c->d_nest_w.ensure(w.size() * sizeof(double)));
+    CU(c->d_nest_ln.ensure(NN * sizeof(int)));
+    CU(c->d_nest_rn.ensure((size_t)NO * NN * sizeof(double)));
+    CU(c->d_nest_d0.ensure((size_t)NO * NN * sizeof(double)));
+    CU(c->d_nest_plane.ensure((size_t)B * per_outer));
+    CU(c->d_nest_mean.ensure((size_t)NO * NN * sizeof(double)));
+    CU(c->d_nest_kth.ensure((size_t)NO * NN * sizeof(double)));
+    double* Lall = (o->on_device && out->L_all) ? out->L_all : nullptr;
+    if (!Lall) {
+        CU(c->d_nest_all.ensure((size_t)NO * NN * n_inner * sizeof(double)));
+        Lall = c->d_nest_all.as<double>();
+    }
+    CU(c->d_ctl.ensure(2 * sizeof(int32_t)));
+    CU(cudaMemcpyAsync(c->d_nest_w.p, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_nest_ln.p, Ln.data(), NN * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemsetAsync(c->d_ctl.p, 0, 2 * sizeof(int32_t), c->stream));
+
+    const VasStep vs = vasicek_step_constants(sp->a, sp->b, sp->sigma, 1.0 / 12.0);
+    CU(cudaEventRecord(c->ev0, c->stream));
+    CU(launch_outer_paths(vs, sp->seed, NO, NN, step, sp->r0, c->d_nest_rn.as<double>(), c->d_nest_d0.as<double>(),
+                          c->stream));
+    NestedArgs a{};
+    a.tab = c->d_tab[form].p;
+    a.tab_bytes = (int32_t)smem;
+    a.v = c->d_nest_plane.p;
+    a.i_pad = i_pad;
+    a.n_inner = n_inner;
+    a.Lmax = Lmax;
+    a.n_nodes = NN;
+    a.node_step = step;
+    a.slots = L.slots.as<SlotRec>();
+    a.tile_kind = L.kinds.as<int32_t>();
+    a.n_tiles = L.n_tiles;
+    a.wts = c->d_nest_w.as<double>();
+    a.n_chunks = i_pad / 32;
+    a.counter = c->d_ctl.as<int32_t>();
+    a.status = c->d_ctl.as<int32_t>() + 1;
+    a.L_all = Lall;
+    for (int o0 = 0; o0 < NO; o0 += B) {
+        const int Bc = std::min(B, NO - o0);
+        if (mc)
+            CU(launch_inner_paths(form, vs, sp->seed, o0, Bc, NN, n_inner, i_pad, Lmax, c->d_nest_ln.as<int>(),
+                                  c->d_nest_rn.as<double>(), c->d_nest_plane.p, c->sm_count, c->stream));
+        else
+            CU(launch_curve_planes(form, sp->a, sp->b, sp->sigma, o0, Bc, NN, i_pad, Lmax, c->d_nest_ln.as<int>(),
+                                   c->d_nest_rn.as<double>(), c->d_nest_plane.p, c->sm_count, c->stream));
+        const long long items = (long long)NN * Bc * a.n_chunks;
+        if (items > 0x7fffffffLL) return fail(c, RSV_E_ARG, "too many nested work items");
+        a.B = Bc;
+        a.o0 = o0;
+        a.n_items = (int32_t)items;
+        CU(cudaMemsetAsync(c->d_ctl.p, 0, sizeof(int32_t), c->stream));
+        if (L.n_tiles > 0) {
+            CU(launch_nested(form, a, c->sm_count, smem, c->stream));
+        } else {
+            CU(cudaMemsetAsync(Lall + (size_t)o0 * NN * n_inner, 0, (size_t)Bc * NN * n_inner * sizeof(double),
+                               c->stream));
+        }
+    }
+    const int k = mc ? std::max(1, (int)std::ceil(0.005 * n_inner - 1e-9)) : 1;
+    CU(launch_node_stats(Lall, NO * NN, n_inner, k, c->d_nest_mean.as<double>(), c->d_nest_kth.as<double>(),
+                         c->stream));
+    CU(cudaEventRecord(c->ev1, c->stream));
+    c->ev_recorded = true;
+
+    const size_t on = (size_t)NO * NN;
+    const cudaMemcpyKind kind = o->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CU(cudaMemcpyAsync(out->L_mean, c->d_nest_mean.p, on * sizeof(double), kind, c->stream));
+    CU(cudaMemcpyAsync(out->L_q995, c->d_nest_kth.p, on * sizeof(double), kind, c->stream));
+    if (out->r_node) CU(cudaMemcpyAsync(out->r_node, c->d_nest_rn.p, on * sizeof(double), kind, c->stream));
+    if (out->D0) CU(cudaMemcpyAsync(out->D0, c->d_nest_d0.p, on * sizeof(double), kind, c->stream));
+    if (out->L_all && Lall != out->L_all)
+        CU(cudaMemcpyAsync(out->L_all, Lall, on * n_inner * sizeof(double), kind, c->stream));
+    if (!o->on_device) return rsv_synchronize(c);
+    return RSV_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -517,7 +674,9 @@ rsv_status rsv_destroy(rsv_ctx* c) {
     cudaStreamSynchronize(c->stream);
     for (DevBuf* b : {&c->d_amount, &c->d_vstage, &c->d_v64, &c->d_v32, &c->d_v2, &c->d_tab[0], &c->d_tab[1],
                       &c->d_tab[2], &c->lay.slots, &c->lay.kinds, &c->d_ctl, &c->d_partial, &c->d_part2,
-                      &c->d_o_v0f, &c->d_o_v0d, &c->d_o_tot, &c->d_o_pt, &c->d_o_traj})
+                      &c->d_o_v0f, &c->d_o_v0d, &c->d_o_tot, &c->d_o_pt, &c->d_o_traj, &c->d_nest_w,
+                      &c->d_nest_ln, &c->d_nest_rn, &c->d_nest_d0, &c->d_nest_plane, &c->d_nest_mean,
+                      &c->d_nest_kth, &c->d_nest_all})
         b->release();
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -586,6 +745,13 @@ rsv_status rsv_compute_reserves(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
     return compute(c, o, out);
+}
+
+rsv_status rsv_compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* sp, rsv_nested_out* out) {
+    if (!c) return RSV_E_ARG;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return compute_nested(c, o, sp, out);
 }
 
 int32_t rsv_variant_count(int32_t form) {

@@ -46,6 +46,20 @@ class rsv_out(C.Structure):
                 ("pt_mean", C.c_void_p), ("traj", C.c_void_p)]
 
 
+RSV_NESTED_MC, RSV_NESTED_CURVE = 0, 2
+
+
+class rsv_nested_spec(C.Structure):
+    _fields_ = [("n_outer", C.c_int32), ("n_nodes", C.c_int32), ("node_step_m", C.c_int32),
+                ("n_inner", C.c_int32), ("seed", C.c_uint64), ("a", C.c_double), ("b", C.c_double),
+                ("sigma", C.c_double), ("r0", C.c_double), ("mode", C.c_int32), ("batch_outer", C.c_int32)]
+
+
+class rsv_nested_out(C.Structure):
+    _fields_ = [("L_mean", C.c_void_p), ("L_q995", C.c_void_p), ("r_node", C.c_void_p), ("D0", C.c_void_p),
+                ("L_all", C.c_void_p)]
+
+
 class RsvError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -56,7 +70,7 @@ _lib = None
 
 # Exported symbols of librsv.so that include/rsv.h declares.
 EXPORTS = ["rsv_create", "rsv_destroy", "rsv_set_stream", "rsv_load_decrements", "rsv_load_portfolio",
-           "rsv_load_scenarios", "rsv_compute_reserves", "rsv_variant_count", "rsv_variant_name",
+           "rsv_load_scenarios", "rsv_compute_reserves", "rsv_compute_nested", "rsv_variant_count", "rsv_variant_name",
            "rsv_tune", "rsv_synchronize", "rsv_last_error", "rsv_last_kernel_ms", "rsv_device_sm_count"]
 
 
@@ -82,6 +96,8 @@ def load_library(path: str = LIB_PATH):
         "rsv_load_portfolio": ([vp, vp, i64], i32),
         "rsv_load_scenarios": ([vp, vp, i32, i32, i32], i32),
         "rsv_compute_reserves": ([vp, C.POINTER(rsv_opts), C.POINTER(rsv_out)], i32),
+        "rsv_compute_nested": ([vp, C.POINTER(rsv_opts), C.POINTER(rsv_nested_spec), C.POINTER(rsv_nested_out)],
+                               i32),
         "rsv_variant_count": ([i32], i32),
         "rsv_variant_name": ([i32, i32], C.c_char_p),
         "rsv_tune": ([vp, C.POINTER(rsv_opts), i32, C.POINTER(i32), C.POINTER(C.c_float)], i32),
@@ -177,6 +193,18 @@ def rsv_compute_reserves(ctx, form: int = RSV_FORM_F32_COMP, outputs: int = RSV_
     o = rsv_opts(form, outputs, horizon, 1 if on_device else 0, variant)
     out = rsv_out(_ptr(V0), _ptr(V0d), _ptr(scen_total), _ptr(pt_mean), _ptr(traj))
     _check(ctx, _lib.rsv_compute_reserves(ctx, C.byref(o), C.byref(out)))
+
+
+def rsv_compute_nested(ctx, form: int = RSV_FORM_F32_COMP, *, n_outer: int, n_nodes: int, node_step_m: int = 12,
+                       n_inner: int = 1000, seed: int = 0, a: float = 0.1, b: float = 0.04, sigma: float = 0.01,
+                       r0: float = 0.03, mode: int = RSV_NESTED_MC, batch_outer: int = 0, on_device: bool = False,
+                       L_mean=None, L_q995=None, r_node=None, D0=None, L_all=None):
+    """Nested valuation (see include/rsv.h).  Output buffers are caller-sized
+    ([n_outer, n_nodes] and [n_outer, n_nodes, n_inner])."""
+    o = rsv_opts(form, 0, 0, 1 if on_device else 0, -1)
+    sp = rsv_nested_spec(n_outer, n_nodes, node_step_m, n_inner, seed, a, b, sigma, r0, mode, batch_outer)
+    out = rsv_nested_out(_ptr(L_mean), _ptr(L_q995), _ptr(r_node), _ptr(D0), _ptr(L_all))
+    _check(ctx, _lib.rsv_compute_nested(ctx, C.byref(o), C.byref(sp), C.byref(out)))
 
 
 def rsv_variant_count(form: int) -> int:
