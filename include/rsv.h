@@ -58,7 +58,8 @@ typedef enum {
     RSV_E_CUDA = -3,       /* a CUDA call failed (message in rsv_last_error)         */
     RSV_E_STATE = -4,      /* call order: e.g. compute before the data is loaded     */
     RSV_E_TIMEOUT = -5,    /* a bounded device-side wait ran out                      */
-    RSV_E_ASSUMPTION = -6  /* input breaks an assumption of Section 3.7              */
+    RSV_E_ASSUMPTION = -6, /* input breaks an assumption of Section 3.7              */
+    RSV_E_LIMIT = -7       /* sizes beyond the fixed scratch of rsv_reserves_noalloc  */
 } rsv_status;
 
 enum { RSV_SL_ANNUITY = 0, RSV_JL_REVERSIONARY = 1, RSV_TERM_ASSURANCE = 2, RSV_ENDOWMENT = 3 };
@@ -228,6 +229,46 @@ typedef struct {
  * in rsv_compute_reserves), RSV_E_ASSUMPTION, RSV_E_CUDA, RSV_E_NOMEM. */
 rsv_status rsv_compute_nested(rsv_ctx *ctx, const rsv_opts *opts, const rsv_nested_spec *spec,
                               rsv_nested_out *out);
+
+/* ---- Valuation without allocation ------------------------------------------
+ * (The paper has no counterpart: this serves a kind of caller, not a step of
+ * the method.)
+ *
+ * For callers that cannot allocate device memory: a serving process whose
+ * device memory belongs to another allocator (a fixed arena or pool that must
+ * remain its only owner), or latency-bound code that cannot take the
+ * device-wide synchronisation a cudaMalloc may imply.  Every input and output
+ * is the caller's device memory; the call allocates nothing (no cudaMalloc,
+ * no cudaFree, no allocating library routine) and uses no context.
+ *
+ * Computes what rsv_compute_reserves computes with RSV_FORM_F32_COMP,
+ * outputs V0d and scen_total, one decrement table: the reserve at valuation of
+ * every policy under every scenario, V0[p * n_scen + s] (FP64), and the
+ * per-scenario totals over the portfolio (FP64, fixed summation order).
+ *   pols       [n_pol] records (device), table1 (and table2) must be 0
+ *   p_monthly  [n_ages] one-month survival by age in months (device), 1..4096
+ *   v          [n_steps][n_scen] discount factors, step-major (device)
+ *   V0         [n_pol][n_scen] output (device); scen_total [n_scen] (device,
+ *              optional, NULL to skip)
+ * Working memory is one static 32 MiB device array in the library, held by
+ * every GPU that loads it until the process exits.  A call needs
+ * 256 B + 64 KiB + n_steps x s_pad x 8 + n_pol x 44 + ceil(n_pol / 256) x
+ * n_scen x 8 bytes of it (s_pad = n_scen rounded up to 128, each term rounded
+ * up to 256 B); larger calls return RSV_E_LIMIT before any GPU work (100,000
+ * policies x 1,000 scenarios x 1,200 steps needs 17.4 MB).
+ * The first call on a device looks up the array's device address (with that
+ * device current) and keeps it; make that first call before any stream
+ * capture.  Every call shares the array and leaves its contents behind; each
+ * call re-initialises what it reads, but calls whose GPU work overlaps (other
+ * streams or host threads) race on it: serialise them.  The call is issued on
+ * `cuda_stream` (NULL = legacy default) and blocks until it has finished.
+ * Errors: RSV_E_ARG (NULL pointer, bad size, a record the main entry point
+ * would reject), RSV_E_LIMIT, RSV_E_ASSUMPTION (a table entry outside [0, 1], a
+ * discount factor not finite and positive), RSV_E_CUDA, RSV_E_TIMEOUT; on an
+ * error the outputs are unspecified. */
+rsv_status rsv_reserves_noalloc(int device, void *cuda_stream, const rsv_policy *pols, int32_t n_pol,
+                                const double *p_monthly, int32_t n_ages, const double *v, int32_t n_scen,
+                                int32_t n_steps, double *V0, double *scen_total);
 
 /* Kernel variants of a form (policies x scenarios per thread, CTA size):
  * how many there are, and a printable description of one. */

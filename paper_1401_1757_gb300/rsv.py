@@ -15,8 +15,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "librsv.so")
 
 RSV_OK, RSV_E_ARG, RSV_E_NOMEM, RSV_E_CUDA, RSV_E_STATE, RSV_E_TIMEOUT, RSV_E_ASSUMPTION = 0, -1, -2, -3, -4, -5, -6
+RSV_E_LIMIT = -7
 STATUS_NAMES = {0: "RSV_OK", -1: "RSV_E_ARG", -2: "RSV_E_NOMEM", -3: "RSV_E_CUDA", -4: "RSV_E_STATE",
-                -5: "RSV_E_TIMEOUT", -6: "RSV_E_ASSUMPTION"}
+                -5: "RSV_E_TIMEOUT", -6: "RSV_E_ASSUMPTION", -7: "RSV_E_LIMIT"}
 RSV_SL_ANNUITY, RSV_JL_REVERSIONARY, RSV_TERM_ASSURANCE, RSV_ENDOWMENT = 0, 1, 2, 3
 RSV_FORM_F64, RSV_FORM_F32, RSV_FORM_F32_COMP = 0, 1, 2
 FORM_NAMES = {0: "f64", 1: "f32", 2: "f32comp"}
@@ -71,7 +72,8 @@ _lib = None
 # Exported symbols of librsv.so that include/rsv.h declares.
 EXPORTS = ["rsv_create", "rsv_destroy", "rsv_set_stream", "rsv_load_decrements", "rsv_load_portfolio",
            "rsv_load_scenarios", "rsv_compute_reserves", "rsv_compute_nested", "rsv_variant_count", "rsv_variant_name",
-           "rsv_tune", "rsv_synchronize", "rsv_last_error", "rsv_last_kernel_ms", "rsv_device_sm_count"]
+           "rsv_tune", "rsv_synchronize", "rsv_last_error", "rsv_last_kernel_ms", "rsv_device_sm_count",
+           "rsv_reserves_noalloc"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -105,6 +107,7 @@ def load_library(path: str = LIB_PATH):
         "rsv_last_error": ([vp], C.c_char_p),
         "rsv_last_kernel_ms": ([vp], C.c_float),
         "rsv_device_sm_count": ([vp], i32),
+        "rsv_reserves_noalloc": ([C.c_int, vp, vp, i32, vp, i32, vp, i32, i32, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -240,3 +243,19 @@ def rsv_last_kernel_ms(ctx) -> float:
 
 def rsv_device_sm_count(ctx) -> int:
     return int(_lib.rsv_device_sm_count(ctx))
+
+
+def rsv_reserves_noalloc(device: int, stream, pols, p_monthly, v, V0, scen_total=None):
+    """The valuation without allocation (see include/rsv.h): every argument is a
+    CUDA torch tensor the caller owns -- ``pols`` the 48-byte records as uint8
+    [n_pol * 48], ``p_monthly`` float64 [n_ages], ``v`` float64 step-major
+    [n_steps, n_scen], ``V0`` float64 [n_pol, n_scen], ``scen_total`` float64
+    [n_scen] or None."""
+    lib = load_library()
+    n_pol = pols.numel() // 48
+    n_steps, n_scen = int(v.shape[0]), int(v.shape[1])
+    st = lib.rsv_reserves_noalloc(device, getattr(stream, "cuda_stream", stream), _ptr(pols), n_pol,
+                                  _ptr(p_monthly), int(p_monthly.numel()), _ptr(v), n_scen, n_steps, _ptr(V0),
+                                  _ptr(scen_total))
+    if st != RSV_OK:
+        raise RsvError(st, "rsv_reserves_noalloc")
