@@ -270,6 +270,96 @@ rsv_status rsv_reserves_noalloc(int device, void *cuda_stream, const rsv_policy 
                                 const double *p_monthly, int32_t n_ages, const double *v, int32_t n_scen,
                                 int32_t n_steps, double *V0, double *scen_total);
 
+/* ---- Surrogate network ------------------------------------------------------
+ * The inner loop of the nested valuation (Section 2) estimates the expected
+ * reserve of a policy in a reduced state at a node given the short rate there.
+ * Under the Vasicek model with deterministic mortality that expectation is
+ * exactly the recurrence (Eq. generalForm) on the forward curve
+ * P(t+1|r)/P(t|r), because the reserve is linear in the discount products
+ * (Eq. basicReserveSummation).  The surrogate is a perceptron
+ * 32 -> 256 -> 256 -> 256 -> 256 -> 1 with exact-erf GELU, BF16 weights and
+ * activations and FP32 accumulation on the tensor cores, FP32 master weights
+ * and Adam; it predicts ln(reserve per unit amount) from 16 features (product
+ * and state one-hot, ages, reversion, remaining term, rate, ln amount and
+ * three products of them; zero-padded to 32).  The parameters are one flat
+ * FP32 vector: W1 [32][256], b1 [256], W2 [256][256], b2, W3, b3, W4, b4
+ * (each W row-major [in][out]), w5 [256], b5 [1]. */
+int64_t rsv_mlp_param_count(void);
+
+/* He-normal initialisation (seeded), or set / read all parameters (host
+ * FP32, rsv_mlp_param_count() values).  Setting resets the Adam state. */
+rsv_status rsv_mlp_init(rsv_ctx *ctx, uint64_t seed);
+rsv_status rsv_mlp_set_params(rsv_ctx *ctx, const float *params, int64_t n);
+rsv_status rsv_mlp_get_params(rsv_ctx *ctx, float *params, int64_t n);
+
+/* Network output for n rows of 32 host FP32 features (rounded to BF16 on the
+ * way in), 1 <= n <= 2^20; y (host) receives n outputs. */
+rsv_status rsv_mlp_forward(rsv_ctx *ctx, const float *X, int64_t n, float *y);
+
+/* Gradient of the mean squared error (1/n) sum (y - target)^2 over n rows
+ * (n a multiple of 64, <= 2^20), in the flat parameter layout (host); loss
+ * receives the mean squared error.  Uses the network's current parameters. */
+rsv_status rsv_mlp_gradient(rsv_ctx *ctx, const float *X, const float *target, int64_t n, float *grads,
+                            float *loss);
+
+typedef struct {
+    int64_t n_train;     /* labelled training queries (>= 1024)                       */
+    int64_t n_val;       /* held-out queries scored against the recurrence (>= 1024)  */
+    int32_t epochs;      /* passes of n_train / batch random batches                  */
+    int32_t batch;       /* multiple of 64, <= 65536                                  */
+    double lr;           /* Adam peak learning rate (cosine decay to 2%)              */
+    uint64_t seed;       /* query sampling (Philox streams 6, 7), batches, init       */
+    double a, b, sigma, r0;  /* Vasicek model of the node rates and of the labels     */
+    int32_t max_node_m;  /* nodes sampled at months 0, 12, ... up to this              */
+    double widen;        /* node rates drawn from the model's distribution, sd x widen */
+    double tol;          /* relative error above which a bucket falls back          */
+} rsv_surrogate_cfg;
+
+typedef struct {
+    double train_loss;                  /* last batch mean squared error (normalised) */
+    double val_max_rel, val_p99_rel, val_median_rel, val_rms_rel;  /* held out     */
+    double frac_fallback;               /* held-out share valued by the recurrence  */
+    double combined_max_rel;            /* max error of what the network serves     */
+    double label_ms, train_ms, infer_ms;/* device times: labels, training, scoring  */
+    int64_t n_label, n_infer, n_buckets, n_flagged;
+    double y_mean, y_std;               /* target normalisation                     */
+} rsv_surrogate_report;
+
+/* Train the surrogate on the loaded portfolio (decrement tables and policies
+ * needed): sample n_train + n_val queries (a policy, an annual node before its
+ * end, a reduced state its lives can be in, a rate from the model at that
+ * month), label them with the FP64 recurrence on the forward curve, train,
+ * and score the held-out queries.  Buckets (product and state x age x
+ * remaining term x rate) whose error on the first half of the held-out
+ * queries exceeds tol, or that hold fewer than 16 of them, are flagged; the
+ * second half measures the error of what the network then serves.  The
+ * network is (re)used as initialised if rsv_mlp_init / set_params was called.
+ * Errors: RSV_E_ARG, RSV_E_STATE, RSV_E_CUDA, RSV_E_NOMEM. */
+rsv_status rsv_surrogate_train(rsv_ctx *ctx, const rsv_surrogate_cfg *cfg, rsv_surrogate_report *report);
+
+/* A valuation query: policy index (into the loaded portfolio), node month m
+ * (0 <= m < the policy's steps), reduced state (0; JL also 1, 2) and the
+ * short rate at the node. */
+typedef struct {
+    int32_t pol, m, state, reserved;
+    double r;
+} rsv_query;
+
+enum {
+    RSV_QUERY_NETWORK = 0,     /* the trained network alone                              */
+    RSV_QUERY_RECURRENCE = 1,  /* the FP64 recurrence on the forward curve (the label)    */
+    RSV_QUERY_FALLBACK = 2     /* the network, with flagged buckets by the recurrence     */
+};
+
+/* Expected reserve (amount x per-unit value) of n host queries into reserve
+ * (host FP64, n values).  RSV_QUERY_RECURRENCE needs no trained network; the
+ * Vasicek parameters are those of the last rsv_surrogate_train (defaults
+ * a = 0.1, b = 0.04, sigma = 0.01 before any).  The device time of the
+ * evaluation is available from rsv_last_kernel_ms.
+ * Errors: RSV_E_ARG (a bad query), RSV_E_STATE (no portfolio; no trained
+ * network for the network modes), RSV_E_CUDA, RSV_E_NOMEM. */
+rsv_status rsv_surrogate_query(rsv_ctx *ctx, const rsv_query *queries, int64_t n, int32_t how, double *reserve);
+
 /* Kernel variants of a form (policies x scenarios per thread, CTA size):
  * how many there are, and a printable description of one. */
 int32_t rsv_variant_count(int32_t form);

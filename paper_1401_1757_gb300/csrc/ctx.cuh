@@ -1,0 +1,140 @@
+// ctx.cuh -- the library context shared by the translation units of the C ABI.
+#pragma once
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "rsv.h"
+#include "mlp.cuh"
+#include "recur_kernel.cuh"
+#include "surrogate.cuh"
+
+namespace rsv {
+
+constexpr int kMaxTables = 8;
+constexpr int kMaxAgeSteps = 4096;       // age + steps bound of the staged tables
+constexpr size_t kMaxSmem = 200 * 1024;  // staged tables per CTA
+constexpr size_t kMaxTraj = size_t(1) << 30;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= n && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+        if (e == cudaSuccess) n = bytes;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+// One policy after validation: reduced model, steps, boundary.
+struct PolPrep {
+    int kind, S, idx_age1, idx_age2, table1, table2, state0, pol;
+    float bnd;
+    double rho;
+};
+
+struct Layout {            // cached tiling for one (P, horizon, data generation)
+    int P = -1, horizon = -1;
+    unsigned long long gen = ~0ull;
+    int n_tiles = 0, tab_pad = 0, n_tab = 0;
+    double chain_steps = 0;  // sum over policies of S (per scenario)
+    DevBuf slots, kinds;
+};
+
+// The trained surrogate: target normalisation, the per-bucket fallback map
+// and its work buffers.
+constexpr int SUR_NB_PS = 6, SUR_NB_AGE = 10, SUR_NB_TERM = 8, SUR_NB_R = 8;
+constexpr int SUR_NBUCKETS = SUR_NB_PS * SUR_NB_AGE * SUR_NB_TERM * SUR_NB_R;
+
+struct SurrogateState {
+    bool trained = false;
+    double y_mean = 0.0, y_std = 1.0;   // normalisation of ln(reserve per unit amount)
+    double tol = 1e-3;                  // fallback threshold (relative)
+    double a = 0.1, b = 0.04, sigma = 0.01, r0 = 0.03;   // Vasicek model of the labels
+    std::vector<unsigned char> flag;    // per bucket: 1 = value by the recurrence
+    DevBuf d_flag, d_q, d_lab, d_y, d_X, d_pred, d_err, d_aux;
+};
+
+}  // namespace rsv
+
+using rsv::DevBuf;
+
+struct rsv_ctx {
+    using Layout = rsv::Layout;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err = "no error";
+
+    std::vector<double> tab[rsv::kMaxTables];
+    unsigned long long tab_gen = 1;
+
+    std::vector<rsv_policy> pols;
+    unsigned long long pol_gen = 1;
+    DevBuf d_amount;
+    bool amount_dirty = true;
+
+    int n_scen = 0, n_steps = 0, s_pad = 0;
+    DevBuf d_vstage, d_v64, d_v32, d_v2;
+
+    DevBuf d_tab[3];
+    int tab_pad_of[3] = {-1, -1, -1};
+    int n_tab_of[3] = {-1, -1, -1};
+    unsigned long long tab_gen_of[3] = {0, 0, 0};
+
+    Layout lay;
+    DevBuf d_ctl;       // [0] queue head, [1] status
+    DevBuf d_partial, d_part2;
+    DevBuf d_o_v0f, d_o_v0d, d_o_tot, d_o_pt, d_o_traj;   // staging for host outputs
+    DevBuf d_nest_w, d_nest_ln, d_nest_rn, d_nest_d0, d_nest_plane, d_nest_mean, d_nest_kth, d_nest_all;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool ev_recorded = false;
+    int tuned[3] = {-1, -1, -1};
+    // surrogate network and its data
+    rsv::Mlp mlp;
+    bool mlp_ready = false;
+    DevBuf d_pols;                  // policy records on the device (surrogate queries)
+    unsigned long long pols_dev_gen = 0;
+    rsv::SurrogateState sur;
+};
+
+
+namespace rsv {
+
+inline rsv_status fail(rsv_ctx* c, rsv_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return st;
+}
+
+// Cached device work layout (policy tiles) and decrement tables in a form's
+// entry format (rsv_abi.cu).
+rsv_status build_layout(rsv_ctx* c, int P, int horizon, int max_steps);
+rsv_status build_tables(rsv_ctx* c, int form, size_t& smem);
+
+#define CU(call)                                                                                \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return rsv::fail(c, e_ == cudaErrorMemoryAllocation ? RSV_E_NOMEM : RSV_E_CUDA, "%s: %s", \
+                             #call, cudaGetErrorString(e_));                                    \
+    } while (0)
+
+}  // namespace rsv

@@ -15,52 +15,12 @@
 #include <vector>
 
 #include "rsv.h"
+#include "ctx.cuh"
 #include "nested.cuh"
 
 using namespace rsv;
 
 namespace {
-
-constexpr int kMaxTables = 8;
-constexpr int kMaxAgeSteps = 4096;       // age + steps bound of the staged tables
-constexpr size_t kMaxSmem = 200 * 1024;  // staged tables per CTA
-constexpr size_t kMaxTraj = size_t(1) << 30;
-
-struct DevBuf {
-    void* p = nullptr;
-    size_t n = 0;
-    cudaError_t ensure(size_t bytes) {
-        if (bytes <= n && p) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        n = 0;
-        cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
-        if (e == cudaSuccess) n = bytes;
-        return e;
-    }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        n = 0;
-    }
-    template <class T>
-    T* as() const { return static_cast<T*>(p); }
-};
-
-// One policy after validation: reduced model, steps, boundary.
-struct PolPrep {
-    int kind, S, idx_age1, idx_age2, table1, table2, state0, pol;
-    float bnd;
-    double rho;
-};
-
-struct Layout {            // cached tiling for one (P, horizon, data generation)
-    int P = -1, horizon = -1;
-    unsigned long long gen = ~0ull;
-    int n_tiles = 0, tab_pad = 0, n_tab = 0;
-    double chain_steps = 0;  // sum over policies of S (per scenario)
-    DevBuf slots, kinds;
-};
 
 const Variant* variant_list(int form, int* n) {
     switch (form) {
@@ -114,57 +74,7 @@ __global__ void scale_kernel(double* __restrict__ x, size_t n, double f) {
 
 }  // namespace
 
-struct rsv_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int sm_count = 0;
-    std::string err = "no error";
-
-    std::vector<double> tab[kMaxTables];
-    unsigned long long tab_gen = 1;
-
-    std::vector<rsv_policy> pols;
-    unsigned long long pol_gen = 1;
-    DevBuf d_amount;
-    bool amount_dirty = true;
-
-    int n_scen = 0, n_steps = 0, s_pad = 0;
-    DevBuf d_vstage, d_v64, d_v32, d_v2;
-
-    DevBuf d_tab[3];
-    int tab_pad_of[3] = {-1, -1, -1};
-    int n_tab_of[3] = {-1, -1, -1};
-    unsigned long long tab_gen_of[3] = {0, 0, 0};
-
-    Layout lay;
-    DevBuf d_ctl;       // [0] queue head, [1] status
-    DevBuf d_partial, d_part2;
-    DevBuf d_o_v0f, d_o_v0d, d_o_tot, d_o_pt, d_o_traj;   // staging for host outputs
-    DevBuf d_nest_w, d_nest_ln, d_nest_rn, d_nest_d0, d_nest_plane, d_nest_mean, d_nest_kth, d_nest_all;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    bool ev_recorded = false;
-    int tuned[3] = {-1, -1, -1};
-};
-
 namespace {
-
-rsv_status fail(rsv_ctx* c, rsv_status st, const char* fmt, ...) {
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    if (c) c->err = buf;
-    return st;
-}
-
-#define CU(call)                                                                                \
-    do {                                                                                        \
-        cudaError_t e_ = (call);                                                                \
-        if (e_ != cudaSuccess)                                                                  \
-            return fail(c, e_ == cudaErrorMemoryAllocation ? RSV_E_NOMEM : RSV_E_CUDA, "%s: %s", \
-                        #call, cudaGetErrorString(e_));                                         \
-    } while (0)
 
 int table_len(const rsv_ctx* c, int id) { return (int)c->tab[id].size(); }
 
@@ -234,7 +144,9 @@ rsv_status prep_policies(rsv_ctx* c, int horizon, int max_steps, std::vector<Pol
     return RSV_OK;
 }
 
-rsv_status build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
+}  // namespace
+
+rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
     Layout& L = c->lay;
     const unsigned long long gen = c->pol_gen * 1000003ull + c->tab_gen * 7919ull + (unsigned)max_steps;
     if (L.P == P && L.horizon == horizon && L.gen == gen) return RSV_OK;
@@ -314,7 +226,7 @@ rsv_status build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
 
 // Decrement tables in the entry format of `form`, zero survival past each
 // table's end, staged per CTA.
-rsv_status build_tables(rsv_ctx* c, int form, size_t& smem) {
+rsv_status rsv::build_tables(rsv_ctx* c, int form, size_t& smem) {
     const int pad = c->lay.tab_pad, n_tab = c->lay.n_tab;
     const size_t esz = form == F_F32 ? sizeof(float2) : 16;
     smem = (size_t)n_tab * pad * esz;
@@ -347,6 +259,8 @@ rsv_status build_tables(rsv_ctx* c, int form, size_t& smem) {
     c->tab_gen_of[form] = c->tab_gen;
     return RSV_OK;
 }
+
+namespace {
 
 rsv_status upload_amounts(rsv_ctx* c) {
     if (!c->amount_dirty) return RSV_OK;

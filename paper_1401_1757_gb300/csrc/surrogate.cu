@@ -1,0 +1,651 @@
+// surrogate.cu -- the reserve surrogate of the nested valuation's inner loop.
+//
+// The inner Monte Carlo loop of the nested valuation estimates, for a policy
+// in reduced state j at a node with short rate r, E[r_j | r].  Under the
+// Vasicek model with deterministic mortality that expectation is exactly the
+// recurrence (Eq. generalForm) run on the forward curve P(t+1|r)/P(t|r) (the
+// recurrence is linear in the discount products, Eq. basicReserveSummation).
+// Labels are that recurrence, in FP64, for sampled (policy, node, state,
+// rate) queries of the loaded portfolio; the network learns
+// ln(reserve per unit amount) from 16 features.  Held-out queries are scored
+// against the same recurrence; buckets (product and state x age x remaining
+// term x rate) whose error exceeds the tolerance fall back to the recurrence.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "ctx.cuh"
+#include "philox.cuh"
+#include "surrogate.cuh"
+
+namespace rsv {
+
+__device__ __forceinline__ int sur_bucket(const PolSur& P, int m, int state, double r) {
+    const int ps = P.product == RSV_SL_ANNUITY ? 0
+                   : P.product == RSV_JL_REVERSIONARY ? 1 + state
+                   : P.product == RSV_TERM_ASSURANCE ? 4 : 5;
+    const int ab = min(SUR_NB_AGE - 1, max(0, (int)(((P.age1 + m) / 12.0 - 20.0) / 10.0)));
+    const int tb = min(SUR_NB_TERM - 1, max(0, (int)((P.S - m) / 120.0)));
+    const int rb = min(SUR_NB_R - 1, max(0, (int)floor((r + 0.02) / 0.02)));
+    return ((ps * SUR_NB_AGE + ab) * SUR_NB_TERM + tb) * SUR_NB_R + rb;
+}
+
+namespace {
+
+// Queries: policy uniform, an annual node before the policy's end (at most
+// max_node_m), a reduced state its lives can be in, and a short rate from the
+// model's distribution at that month widened by `widen` standard deviations.
+__global__ void sample_queries_kernel(const PolSur* __restrict__ pols, int n_pol, uint64_t seed, uint32_t stream,
+                                      long long n, double a, double b, double sigma, double r0, double widen,
+                                      int max_node_m, SurQuery* __restrict__ out) {
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const double inv32 = 2.3283064365386963e-10;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        uint32_t w[4], g[4];
+        philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), 0u, stream << 24, k0, k1, w);
+        philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), 1u, stream << 24, k0, k1, g);
+        SurQuery Q;
+        Q.pol = (int)(w[0] % (uint32_t)n_pol);
+        const PolSur P = pols[Q.pol];
+        if (P.S < 1) {
+            Q.m = 0;
+            Q.state = -1;
+            Q.r = r0;
+            Q.bucket = 0;
+            out[q] = Q;
+            continue;
+        }
+        const int maxk = min((P.S - 1) / 12, max_node_m / 12);
+        Q.m = 12 * (int)(w[1] % (uint32_t)(maxk + 1));
+        Q.state = 0;
+        if (P.product == RSV_JL_REVERSIONARY) {
+            const bool x = P.age1 + Q.m < P.lim1, y = P.age2 + Q.m < P.lim2;
+            int cand[3], nc = 0;
+            if (x && y) cand[nc++] = 0;
+            if (x) cand[nc++] = 1;
+            if (y) cand[nc++] = 2;
+            Q.state = nc ? cand[w[2] % (uint32_t)nc] : -1;
+        }
+        const double t = Q.m / 12.0;
+        const double mean = b + (r0 - b) * exp(-a * t);
+        const double sd = sigma * sqrt(-expm1(-2.0 * a * t) / (2.0 * a));
+        const double u1 = ((double)g[0] + 0.5) * inv32, u2 = ((double)g[1] + 0.5) * inv32;
+        const double z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+        Q.r = mean + widen * sd * z;
+        Q.bucket = sur_bucket(P, Q.m, Q.state, Q.r);
+        out[q] = Q;
+    }
+}
+
+}  // namespace
+
+// Reserve per unit amount in the query's state: the FP64 recurrence on the
+// Vasicek forward curve from the policy's end back to the node.  With `flag`,
+// only queries whose bucket is flagged are valued (the fallback).
+__global__ void sur_label_kernel(const PolSur* __restrict__ pols, const double2* __restrict__ tab, int tab_pad,
+                                 const SurQuery* __restrict__ qs, long long n, double a, double b, double sigma,
+                                 const unsigned char* __restrict__ flag, double* __restrict__ V) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const SurQuery Q = qs[i];
+        if (flag && (Q.state < 0 || !flag[Q.bucket])) continue;
+        if (Q.state < 0) {
+            V[i] = 0.0;
+            continue;
+        }
+        const PolSur P = pols[Q.pol];
+        const int Sn = P.S - Q.m;
+        const int i1 = P.tab1 * tab_pad + P.age1 + Q.m, i2 = P.tab2 * tab_pad + P.age2 + Q.m;
+        double V00 = P.product == RSV_ENDOWMENT ? 1.0 : 0.0, V01 = 0.0, V10 = 0.0;
+        double lnP_next = vasicek_lnP(Sn / 12.0, Q.r, a, b, sigma);
+        for (int t = Sn - 1; t >= 0; --t) {
+            const double lnP = vasicek_lnP(t / 12.0, Q.r, a, b, sigma);
+            const double v = exp(lnP_next - lnP);
+            lnP_next = lnP;
+            const double2 ex = tab[i1 + t];
+            if (P.product == RSV_SL_ANNUITY) {
+                V00 = v * ex.x * (1.0 + V00);
+            } else if (P.product == RSV_JL_REVERSIONARY) {
+                const double2 ey = tab[i2 + t];
+                const double n01 = v * ex.x * (1.0 + V01);
+                const double n10 = v * ey.x * (P.rho + V10);
+                V00 = v * ex.x * ey.x * (1.0 + V00) + ey.y * n01 + ex.y * n10;
+                V01 = n01;
+                V10 = n10;
+            } else {
+                V00 = v * (ex.y + ex.x * V00);
+            }
+        }
+        V[i] = Q.state == 0 ? V00 : (Q.state == 1 ? V01 : V10);
+    }
+}
+
+// Features of a query (zero-padded to MLP_IN, BF16).
+__global__ void sur_features_kernel(const PolSur* __restrict__ pols, const SurQuery* __restrict__ qs, long long n,
+                                    __nv_bfloat16* __restrict__ X) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const SurQuery Q = qs[i];
+        const PolSur P = pols[Q.pol];
+        float f[MLP_IN];
+#pragma unroll
+        for (int k = 0; k < MLP_IN; ++k) f[k] = 0.0f;
+        f[P.product] = 1.0f;
+        f[4 + max(0, Q.state)] = 1.0f;
+        const bool jl = P.product == RSV_JL_REVERSIONARY;
+        const float age1 = ((P.age1 + Q.m) / 12.0f - 60.0f) / 25.0f;
+        const float rem = (P.S - Q.m) / 12.0f / 40.0f;
+        const float rr = (float)((Q.r - 0.04) / 0.02);
+        f[7] = age1;
+        f[8] = jl ? ((P.age2 + Q.m) / 12.0f - 60.0f) / 25.0f : 0.0f;
+        f[9] = jl ? (float)P.rho : 0.0f;
+        f[10] = rem;
+        f[11] = rr;
+        f[12] = (float)((log(fmax(P.amount, 1e-30)) - 9.0) / 2.0);
+        f[13] = age1 * age1;
+        f[14] = rem * rem;
+        f[15] = rr * rem;
+        __nv_bfloat16* row = X + i * MLP_IN;
+#pragma unroll
+        for (int k = 0; k < MLP_IN; k += 2)
+            *reinterpret_cast<__nv_bfloat162*>(row + k) = __floats2bfloat162_rn(f[k], f[k + 1]);
+    }
+}
+
+__global__ void sur_to_reserve_kernel(const float* __restrict__ yhat, long long n, double mu, double sd,
+                                      double* __restrict__ V) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        V[i] = exp((double)yhat[i] * sd + mu);
+}
+
+namespace {
+
+__global__ void targets_kernel(const double* __restrict__ V, long long n, double mu, double sd, float* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (float)((log(V[i]) - mu) / sd);
+}
+
+__global__ void gather_kernel(const __nv_bfloat16* __restrict__ X, const float* __restrict__ y, long long n,
+                              uint64_t seed, uint32_t step, int B, __nv_bfloat16* __restrict__ Xb,
+                              float* __restrict__ yb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B) return;
+    uint32_t w[4];
+    philox4x32_10((uint32_t)i, step, 0u, 5u << 24, (uint32_t)seed, (uint32_t)(seed >> 32), w);
+    const long long j = (long long)((((uint64_t)w[0] << 32) | w[1]) % (uint64_t)n);
+    const uint4* src = reinterpret_cast<const uint4*>(X + j * MLP_IN);
+    uint4* dst = reinterpret_cast<uint4*>(Xb + (size_t)i * MLP_IN);
+#pragma unroll
+    for (int k = 0; k < MLP_IN * 2 / 16; ++k) dst[k] = src[k];
+    yb[i] = y[j];
+}
+
+// relative error of the surrogate's reserve against the label
+__global__ void rel_err_kernel(const double* __restrict__ pred, const double* __restrict__ V, long long n,
+                               double* __restrict__ err) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        err[i] = V[i] > 0.0 ? pred[i] / V[i] - 1.0 : 0.0;
+}
+
+// ln-moments of the labels (FP64, fixed order per block, then on the host)
+__global__ void log_moments_kernel(const double* __restrict__ V, long long n, double* __restrict__ part) {
+    __shared__ double s1[256], s2[256];
+    double a = 0.0, b2 = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double l = log(V[i]);
+        a += l;
+        b2 += l * l;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b2;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+            s2[threadIdx.x] += s2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s1[0];
+        part[2 * blockIdx.x + 1] = s2[0];
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host ----
+rsv_status sur_upload_policies(rsv_ctx* c, std::vector<PolSur>& host) {
+    host.resize(c->pols.size());
+    for (size_t i = 0; i < host.size(); ++i) {
+        const rsv_policy& r = c->pols[i];
+        PolSur& p = host[i];
+        const bool jl = r.product == RSV_JL_REVERSIONARY;
+        p.product = r.product;
+        p.age1 = r.age1_m;
+        p.age2 = jl ? r.age2_m : 0;
+        p.tab1 = r.table1;
+        p.tab2 = jl ? r.table2 : r.table1;
+        p.lim1 = (int)c->tab[r.table1].size();
+        p.lim2 = (int)c->tab[p.tab2].size();
+        int S;
+        if (r.product == RSV_SL_ANNUITY) {
+            S = std::max(0, p.lim1 - r.age1_m);
+            if (r.term_m > 0) S = std::min(S, r.term_m);
+        } else if (jl) {
+            S = std::max(0, std::max(p.lim1 - r.age1_m, p.lim2 - r.age2_m));
+            if (r.term_m > 0) S = std::min(S, r.term_m);
+        } else {
+            S = r.term_m;
+        }
+        p.S = S;
+        p.amount = r.amount;
+        p.rho = jl ? r.reversion : 0.0;
+    }
+    CU(c->d_pols.ensure(std::max<size_t>(1, host.size()) * sizeof(PolSur)));
+    CU(cudaMemcpyAsync(c->d_pols.p, host.data(), host.size() * sizeof(PolSur), cudaMemcpyHostToDevice, c->stream));
+    c->pols_dev_gen = c->pol_gen;
+    return RSV_OK;
+}
+
+// Reserves per unit amount of n queries (device) by the network; with
+// `fallback`, queries in flagged buckets are then valued by the recurrence.
+rsv_status sur_predict(rsv_ctx* c, const SurQuery* q, long long n, double* V, bool fallback, int batch) {
+    SurrogateState& s = c->sur;
+    CU(c->mlp.ensure(batch));
+    for (long long o = 0; o < n; o += batch) {
+        const int nb = (int)std::min<long long>(batch, n - o);
+        const int nb_pad = (nb + 63) / 64 * 64;
+        if (nb_pad != nb) CU(cudaMemsetAsync(c->mlp.X, 0, (size_t)nb_pad * MLP_IN * 2, c->stream));
+        sur_features_kernel<<<c->sm_count * 4, 256, 0, c->stream>>>(c->d_pols.as<PolSur>(), q + o, nb, c->mlp.X);
+        CU(cudaGetLastError());
+        CU(c->mlp.forward(c->mlp.X, nb_pad, c->mlp.y, nullptr, c->stream));
+        sur_to_reserve_kernel<<<c->sm_count * 4, 256, 0, c->stream>>>(c->mlp.y, nb, s.y_mean, s.y_std, V + o);
+        CU(cudaGetLastError());
+    }
+    if (fallback) {
+        size_t smem;
+        rsv_status st = build_tables(c, F_F64, smem);
+        if (st != RSV_OK) return st;
+        sur_label_kernel<<<c->sm_count * 8, 128, 0, c->stream>>>(
+            c->d_pols.as<PolSur>(), c->d_tab[F_F64].as<double2>(), c->tab_pad_of[F_F64], q, n, s.a, s.b, s.sigma,
+            s.d_flag.as<unsigned char>(), V);
+        CU(cudaGetLastError());
+    }
+    return RSV_OK;
+}
+
+}  // namespace rsv
+
+// ------------------------------------------------------------------ ABI ----
+namespace rsv {
+namespace {
+
+// He-normal weights, zero biases, a small head (SplitMix64 + Box-Muller).
+void he_init(std::vector<float>& p, uint64_t seed) {
+    uint64_t st = seed * 0x9E3779B97F4A7C15ull + 1;
+    auto next = [&]() {
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto gauss = [&]() {
+        const double u1 = ((next() >> 11) + 0.5) * 0x1.0p-53, u2 = ((next() >> 11) + 0.5) * 0x1.0p-53;
+        return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+    };
+    p.assign(mlp_n_params(), 0.0f);
+    for (int l = 1; l <= 4; ++l) {
+        const double sd = std::sqrt(2.0 / mlp_in_dim(l));
+        for (size_t i = 0; i < (size_t)mlp_in_dim(l) * MLP_H; ++i) p[mlp_w_off(l) + i] = (float)(sd * gauss());
+    }
+    for (int k = 0; k < MLP_H; ++k) p[mlp_w5_off() + k] = (float)(gauss() / std::sqrt((double)MLP_H));
+}
+
+rsv_status mlp_upload(rsv_ctx* c, const float* host) {
+    CU(c->mlp.ensure(64));
+    CU(cudaMemcpyAsync(c->mlp.params, host, mlp_n_params() * 4, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemsetAsync(c->mlp.adam_m, 0, mlp_n_params() * 4, c->stream));
+    CU(cudaMemsetAsync(c->mlp.adam_v, 0, mlp_n_params() * 4, c->stream));
+    c->mlp.step = 0;
+    CU(c->mlp.refresh_bf16(c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->mlp_ready = true;
+    return RSV_OK;
+}
+
+__global__ void f32_to_bf16_rows(const float* __restrict__ x, long long n, __nv_bfloat16* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
+rsv_status mlp_stage_inputs(rsv_ctx* c, const float* X, long long n, long long n_pad) {
+    CU(c->mlp.ensure((int)n_pad));
+    CU(c->sur.d_aux.ensure((size_t)n_pad * MLP_IN * 4));
+    CU(cudaMemsetAsync(c->sur.d_aux.p, 0, (size_t)n_pad * MLP_IN * 4, c->stream));
+    CU(cudaMemcpyAsync(c->sur.d_aux.p, X, (size_t)n * MLP_IN * 4, cudaMemcpyHostToDevice, c->stream));
+    f32_to_bf16_rows<<<c->sm_count * 4, 256, 0, c->stream>>>(c->sur.d_aux.as<float>(), n_pad * MLP_IN, c->mlp.X);
+    CU(cudaGetLastError());
+    return RSV_OK;
+}
+
+__global__ void query_prep_kernel(const PolSur* __restrict__ pols, int n_pol, const rsv_query* __restrict__ in,
+                                  long long n, SurQuery* __restrict__ out, int* __restrict__ bad) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const rsv_query r = in[i];
+        SurQuery Q;
+        Q.pol = r.pol;
+        Q.m = r.m;
+        Q.state = r.state;
+        Q.r = r.r;
+        Q.bucket = 0;
+        const bool ok = r.pol >= 0 && r.pol < n_pol && r.m >= 0 && isfinite(r.r) && r.state >= 0 &&
+                        r.state <= (pols[r.pol >= 0 && r.pol < n_pol ? r.pol : 0].product == RSV_JL_REVERSIONARY ? 2 : 0) &&
+                        r.m < pols[r.pol >= 0 && r.pol < n_pol ? r.pol : 0].S;
+        if (!ok) {
+            atomicAdd(bad, 1);
+            Q.pol = 0;
+            Q.state = -1;
+        } else {
+            Q.bucket = sur_bucket(pols[r.pol], r.m, r.state, r.r);
+        }
+        out[i] = Q;
+    }
+}
+
+__global__ void scale_by_amount_kernel(const PolSur* __restrict__ pols, const SurQuery* __restrict__ q, long long n,
+                                       double* __restrict__ V) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        V[i] = q[i].state < 0 ? 0.0 : V[i] * pols[q[i].pol].amount;
+}
+
+}  // namespace
+}  // namespace rsv
+
+using namespace rsv;
+
+extern "C" {
+
+rsv_status rsv_surrogate_query(rsv_ctx* c, const rsv_query* queries, int64_t n, int32_t how, double* reserve) {
+    if (!c) return RSV_E_ARG;
+    if (!queries || !reserve || n < 1 || n > (int64_t(1) << 31) || how < RSV_QUERY_NETWORK || how > RSV_QUERY_FALLBACK)
+        return fail(c, RSV_E_ARG, "bad query arguments");
+    if (c->pols.empty()) return fail(c, RSV_E_STATE, "no portfolio loaded");
+    if (how != RSV_QUERY_RECURRENCE && !c->sur.trained) return fail(c, RSV_E_STATE, "surrogate not trained");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice failed");
+    rsv_status st = build_layout(c, 2, 0, kMaxAgeSteps);
+    if (st != RSV_OK) return st;
+    size_t smem;
+    if ((st = build_tables(c, F_F64, smem)) != RSV_OK) return st;
+    if (c->pols_dev_gen != c->pol_gen) {
+        std::vector<PolSur> hp;
+        if ((st = sur_upload_policies(c, hp)) != RSV_OK) return st;
+    }
+    SurrogateState& s = c->sur;
+    CU(s.d_aux.ensure((size_t)n * sizeof(rsv_query) + 16));
+    CU(s.d_q.ensure((size_t)n * sizeof(SurQuery)));
+    CU(s.d_pred.ensure((size_t)n * 8));
+    CU(s.d_err.ensure(16));
+    CU(cudaMemsetAsync(s.d_err.p, 0, 16, c->stream));
+    CU(cudaMemcpyAsync(s.d_aux.p, queries, (size_t)n * sizeof(rsv_query), cudaMemcpyHostToDevice, c->stream));
+    SurQuery* q = s.d_q.as<SurQuery>();
+    const int grid = c->sm_count * 8;
+    query_prep_kernel<<<grid, 256, 0, c->stream>>>(c->d_pols.as<PolSur>(), (int)c->pols.size(),
+                                                   s.d_aux.as<rsv_query>(), n, q, s.d_err.as<int>());
+    CU(cudaGetLastError());
+    double* V = s.d_pred.as<double>();
+    CU(cudaEventRecord(c->ev0, c->stream));
+    if (how == RSV_QUERY_RECURRENCE) {
+        sur_label_kernel<<<grid, 128, 0, c->stream>>>(c->d_pols.as<PolSur>(), c->d_tab[F_F64].as<double2>(),
+                                                      c->tab_pad_of[F_F64], q, n, s.a, s.b, s.sigma, nullptr, V);
+        CU(cudaGetLastError());
+    } else if ((st = sur_predict(c, q, n, V, how == RSV_QUERY_FALLBACK, 65536)) != RSV_OK) {
+        return st;
+    }
+    CU(cudaEventRecord(c->ev1, c->stream));
+    c->ev_recorded = true;
+    scale_by_amount_kernel<<<grid, 256, 0, c->stream>>>(c->d_pols.as<PolSur>(), q, n, V);
+    CU(cudaGetLastError());
+    int bad = 0;
+    CU(cudaMemcpyAsync(&bad, s.d_err.p, 4, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(reserve, V, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (bad) return fail(c, RSV_E_ARG, "%d queries name a bad policy, state or month", bad);
+    return RSV_OK;
+}
+
+int64_t rsv_mlp_param_count(void) { return (int64_t)mlp_n_params(); }
+
+rsv_status rsv_mlp_init(rsv_ctx* c, uint64_t seed) {
+    if (!c) return RSV_E_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice failed");
+    std::vector<float> p;
+    he_init(p, seed);
+    c->sur.trained = false;
+    return mlp_upload(c, p.data());
+}
+
+rsv_status rsv_mlp_set_params(rsv_ctx* c, const float* params, int64_t n) {
+    if (!c) return RSV_E_ARG;
+    if (!params || n != (int64_t)mlp_n_params()) return fail(c, RSV_E_ARG, "expected %zu parameters", mlp_n_params());
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice failed");
+    c->sur.trained = false;
+    return mlp_upload(c, params);
+}
+
+rsv_status rsv_mlp_get_params(rsv_ctx* c, float* params, int64_t n) {
+    if (!c) return RSV_E_ARG;
+    if (!params || n != (int64_t)mlp_n_params()) return fail(c, RSV_E_ARG, "expected %zu parameters", mlp_n_params());
+    if (!c->mlp_ready) return fail(c, RSV_E_STATE, "network not initialised");
+    CU(cudaMemcpyAsync(params, c->mlp.params, mlp_n_params() * 4, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return RSV_OK;
+}
+
+rsv_status rsv_mlp_forward(rsv_ctx* c, const float* X, int64_t n, float* y) {
+    if (!c) return RSV_E_ARG;
+    if (!X || !y || n < 1 || n > (1 << 20)) return fail(c, RSV_E_ARG, "bad forward arguments");
+    if (!c->mlp_ready) return fail(c, RSV_E_STATE, "network not initialised");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice failed");
+    const long long n_pad = (n + 63) / 64 * 64;
+    rsv_status st = mlp_stage_inputs(c, X, n, n_pad);
+    if (st != RSV_OK) return st;
+    CU(c->mlp.forward(c->mlp.X, (int)n_pad, c->mlp.y, nullptr, c->stream));
+    CU(cudaMemcpyAsync(y, c->mlp.y, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return RSV_OK;
+}
+
+rsv_status rsv_mlp_gradient(rsv_ctx* c, const float* X, const float* target, int64_t n, float* grads, float* loss) {
+    if (!c) return RSV_E_ARG;
+    if (!X || !target || !grads || n < 64 || n % 64 || n > (1 << 20))
+        return fail(c, RSV_E_ARG, "bad gradient arguments (n a multiple of 64)");
+    if (!c->mlp_ready) return fail(c, RSV_E_STATE, "network not initialised");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice failed");
+    rsv_status st = mlp_stage_inputs(c, X, n, n);
+    if (st != RSV_OK) return st;
+    CU(cudaMemcpyAsync(c->mlp.t, target, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
+    CU(c->mlp.forward(c->mlp.X, (int)n, c->mlp.y, c->mlp.t, c->stream));
+    CU(c->mlp.backward(c->mlp.X, (int)n, c->stream));
+    CU(cudaMemcpyAsync(grads, c->mlp.grads, mlp_n_params() * 4, cudaMemcpyDeviceToHost, c->stream));
+    float l = 0.0f;
+    CU(cudaMemcpyAsync(&l, c->mlp.loss, 4, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (loss) *loss = l / (float)n;
+    return RSV_OK;
+}
+
+rsv_status rsv_surrogate_train(rsv_ctx* c, const rsv_surrogate_cfg* cfg, rsv_surrogate_report* rep) {
+    if (!c) return RSV_E_ARG;
+    if (!cfg || !rep) return fail(c, RSV_E_ARG, "cfg and report must not be NULL");
+    if (cfg->n_train < 1024 || cfg->n_val < 1024 || cfg->epochs < 0 || cfg->batch < 64 || cfg->batch % 64 ||
+        cfg->batch > 65536 || !(cfg->lr > 0) || !(cfg->a > 0) || !(cfg->sigma >= 0) || !(cfg->tol > 0) ||
+        cfg->max_node_m < 0 || !(cfg->widen >= 0))
+        return fail(c, RSV_E_ARG, "bad surrogate configuration");
+    if (c->pols.empty()) return fail(c, RSV_E_STATE, "no portfolio loaded");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice failed");
+    rsv_status st = build_layout(c, 2, 0, kMaxAgeSteps);   // validates the records
+    if (st != RSV_OK) return st;
+    size_t smem;
+    if ((st = build_tables(c, F_F64, smem)) != RSV_OK) return st;
+    std::vector<PolSur> hp;
+    if ((st = sur_upload_policies(c, hp)) != RSV_OK) return st;
+    SurrogateState& s = c->sur;
+    s.a = cfg->a;
+    s.b = cfg->b;
+    s.sigma = cfg->sigma;
+    s.r0 = cfg->r0;
+    s.tol = cfg->tol;
+    const long long nt = cfg->n_train, nv = cfg->n_val, n = nt + nv;
+    CU(s.d_q.ensure((size_t)n * sizeof(SurQuery)));
+    CU(s.d_lab.ensure((size_t)n * 8));
+    CU(s.d_y.ensure((size_t)n * 4));
+    CU(s.d_X.ensure((size_t)n * MLP_IN * 2));
+    CU(s.d_err.ensure((size_t)nv * 8));
+    SurQuery* q = s.d_q.as<SurQuery>();
+    cudaEvent_t e0, e1, e2, e3;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&e2);
+    cudaEventCreate(&e3);
+
+    // queries (train: stream 6, held out: stream 7) and their labels
+    const int grid = c->sm_count * 8;
+    sample_queries_kernel<<<grid, 128, 0, c->stream>>>(c->d_pols.as<PolSur>(), (int)hp.size(), cfg->seed, 6u, nt,
+                                                       cfg->a, cfg->b, cfg->sigma, cfg->r0, cfg->widen,
+                                                       cfg->max_node_m, q);
+    sample_queries_kernel<<<grid, 128, 0, c->stream>>>(c->d_pols.as<PolSur>(), (int)hp.size(), cfg->seed, 7u, nv,
+                                                       cfg->a, cfg->b, cfg->sigma, cfg->r0, cfg->widen,
+                                                       cfg->max_node_m, q + nt);
+    CU(cudaGetLastError());
+    CU(cudaEventRecord(e0, c->stream));
+    sur_label_kernel<<<grid, 128, 0, c->stream>>>(c->d_pols.as<PolSur>(), c->d_tab[F_F64].as<double2>(),
+                                                  c->tab_pad_of[F_F64], q, n, cfg->a, cfg->b, cfg->sigma, nullptr,
+                                                  s.d_lab.as<double>());
+    CU(cudaGetLastError());
+    CU(cudaEventRecord(e1, c->stream));
+    // target normalisation from the training labels
+    const int mb = 256;
+    DevBuf part;
+    CU(part.ensure(mb * 2 * 8));
+    log_moments_kernel<<<mb, 256, 0, c->stream>>>(s.d_lab.as<double>(), nt, part.as<double>());
+    std::vector<double> hpart(mb * 2);
+    CU(cudaMemcpyAsync(hpart.data(), part.p, mb * 2 * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    part.release();
+    double s1 = 0, s2 = 0;
+    for (int i = 0; i < mb; ++i) {
+        s1 += hpart[2 * i];
+        s2 += hpart[2 * i + 1];
+    }
+    s.y_mean = s1 / nt;
+    s.y_std = std::sqrt(std::max(s2 / nt - s.y_mean * s.y_mean, 1e-12));
+    if (!std::isfinite(s.y_mean)) return fail(c, RSV_E_ASSUMPTION, "a training label is not positive");
+    targets_kernel<<<grid, 256, 0, c->stream>>>(s.d_lab.as<double>(), n, s.y_mean, s.y_std, s.d_y.as<float>());
+    sur_features_kernel<<<grid, 256, 0, c->stream>>>(c->d_pols.as<PolSur>(), q, n, s.d_X.as<__nv_bfloat16>());
+    CU(cudaGetLastError());
+
+    // training: Adam on random batches, cosine learning rate
+    if (!c->mlp_ready) {
+        std::vector<float> p;
+        he_init(p, cfg->seed);
+        if ((st = mlp_upload(c, p.data())) != RSV_OK) return st;
+    }
+    const int B = cfg->batch;
+    CU(c->mlp.ensure(std::max(B, 65536)));
+    const long long steps = (long long)cfg->epochs * (nt / B);
+    CU(cudaEventRecord(e2, c->stream));
+    for (long long k = 0; k < steps; ++k) {
+        const float lr = (float)(cfg->lr * (0.02 + 0.98 * 0.5 * (1.0 + std::cos(3.141592653589793 * k / steps))));
+        gather_kernel<<<(B + 255) / 256, 256, 0, c->stream>>>(s.d_X.as<__nv_bfloat16>(), s.d_y.as<float>(), nt,
+                                                              cfg->seed, (uint32_t)k, B, c->mlp.X, c->mlp.t);
+        CU(cudaGetLastError());
+        CU(c->mlp.forward(c->mlp.X, B, nullptr, c->mlp.t, c->stream));
+        CU(c->mlp.backward(c->mlp.X, B, c->stream));
+        CU(c->mlp.adam_step(lr, c->stream));
+    }
+    CU(cudaEventRecord(e3, c->stream));
+    float last = 0.0f;
+    if (steps > 0) CU(cudaMemcpyAsync(&last, c->mlp.loss, 4, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    float label_ms = 0, train_ms = 0;
+    cudaEventElapsedTime(&label_ms, e0, e1);
+    cudaEventElapsedTime(&train_ms, e2, e3);
+
+    // held-out scoring against the recurrence
+    CU(s.d_pred.ensure((size_t)nv * 8));
+    CU(cudaEventRecord(e0, c->stream));
+    if ((st = sur_predict(c, q + nt, nv, s.d_pred.as<double>(), false, 65536)) != RSV_OK) return st;
+    CU(cudaEventRecord(e1, c->stream));
+    rel_err_kernel<<<grid, 256, 0, c->stream>>>(s.d_pred.as<double>(), s.d_lab.as<double>() + nt, nv,
+                                                s.d_err.as<double>());
+    CU(cudaGetLastError());
+    std::vector<double> err(nv);
+    std::vector<SurQuery> hq(nv);
+    CU(cudaMemcpyAsync(err.data(), s.d_err.p, (size_t)nv * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(hq.data(), q + nt, (size_t)nv * sizeof(SurQuery), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    float infer_ms = 0;
+    cudaEventElapsedTime(&infer_ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    cudaEventDestroy(e3);
+
+    // statistics; fallback map calibrated on the first half, judged on the second
+    std::vector<double> ae;
+    ae.reserve(nv);
+    for (long long i = 0; i < nv; ++i)
+        if (hq[i].state >= 0) ae.push_back(std::fabs(err[i]));
+    std::vector<double> srt = ae;
+    std::sort(srt.begin(), srt.end());
+    auto quant = [&](const std::vector<double>& v, double f) { return v.empty() ? 0.0 : v[(size_t)(f * (v.size() - 1))]; };
+    double rms = 0;
+    for (double x : ae) rms += x * x;
+    rms = ae.empty() ? 0 : std::sqrt(rms / ae.size());
+    std::vector<double> bmax(SUR_NBUCKETS, 0.0);
+    std::vector<long long> bcnt(SUR_NBUCKETS, 0);
+    const long long half = nv / 2;
+    for (long long i = 0; i < half; ++i) {
+        if (hq[i].state < 0) continue;
+        bmax[hq[i].bucket] = std::max(bmax[hq[i].bucket], std::fabs(err[i]));
+        ++bcnt[hq[i].bucket];
+    }
+    s.flag.assign(SUR_NBUCKETS, 0);
+    long long n_flag = 0;
+    for (int k = 0; k < SUR_NBUCKETS; ++k) {
+        s.flag[k] = (bcnt[k] < 16 || bmax[k] > cfg->tol) ? 1 : 0;   // unseen or inaccurate: recurrence
+        n_flag += s.flag[k];
+    }
+    CU(s.d_flag.ensure(SUR_NBUCKETS));
+    CU(cudaMemcpyAsync(s.d_flag.p, s.flag.data(), SUR_NBUCKETS, cudaMemcpyHostToDevice, c->stream));
+    double comb = 0;
+    long long fb = 0, m2 = 0;
+    for (long long i = half; i < nv; ++i) {
+        if (hq[i].state < 0) continue;
+        ++m2;
+        if (s.flag[hq[i].bucket]) ++fb;
+        else comb = std::max(comb, std::fabs(err[i]));
+    }
+    CU(cudaStreamSynchronize(c->stream));
+    s.trained = true;
+    rep->train_loss = last / B;
+    rep->val_max_rel = srt.empty() ? 0 : srt.back();
+    rep->val_p99_rel = quant(srt, 0.99);
+    rep->val_median_rel = quant(srt, 0.5);
+    rep->val_rms_rel = rms;
+    rep->frac_fallback = m2 ? (double)fb / m2 : 0.0;
+    rep->combined_max_rel = comb;
+    rep->label_ms = label_ms;
+    rep->train_ms = train_ms;
+    rep->infer_ms = infer_ms;
+    rep->n_label = n;
+    rep->n_infer = nv;
+    rep->n_buckets = SUR_NBUCKETS;
+    rep->n_flagged = n_flag;
+    rep->y_mean = s.y_mean;
+    rep->y_std = s.y_std;
+    return RSV_OK;
+}
+
+}  // extern "C"

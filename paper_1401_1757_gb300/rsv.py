@@ -61,6 +61,25 @@ class rsv_nested_out(C.Structure):
                 ("L_all", C.c_void_p)]
 
 
+class rsv_surrogate_cfg(C.Structure):
+    _fields_ = [("n_train", C.c_int64), ("n_val", C.c_int64), ("epochs", C.c_int32), ("batch", C.c_int32),
+                ("lr", C.c_double), ("seed", C.c_uint64), ("a", C.c_double), ("b", C.c_double),
+                ("sigma", C.c_double), ("r0", C.c_double), ("max_node_m", C.c_int32), ("widen", C.c_double),
+                ("tol", C.c_double)]
+
+
+class rsv_surrogate_report(C.Structure):
+    _fields_ = [("train_loss", C.c_double), ("val_max_rel", C.c_double), ("val_p99_rel", C.c_double),
+                ("val_median_rel", C.c_double), ("val_rms_rel", C.c_double), ("frac_fallback", C.c_double),
+                ("combined_max_rel", C.c_double), ("label_ms", C.c_double), ("train_ms", C.c_double),
+                ("infer_ms", C.c_double), ("n_label", C.c_int64), ("n_infer", C.c_int64),
+                ("n_buckets", C.c_int64), ("n_flagged", C.c_int64), ("y_mean", C.c_double), ("y_std", C.c_double)]
+
+
+QUERY_DTYPE = np.dtype([("pol", "<i4"), ("m", "<i4"), ("state", "<i4"), ("reserved", "<i4"), ("r", "<f8")])
+RSV_QUERY_NETWORK, RSV_QUERY_RECURRENCE, RSV_QUERY_FALLBACK = 0, 1, 2
+
+
 class RsvError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -73,7 +92,8 @@ _lib = None
 EXPORTS = ["rsv_create", "rsv_destroy", "rsv_set_stream", "rsv_load_decrements", "rsv_load_portfolio",
            "rsv_load_scenarios", "rsv_compute_reserves", "rsv_compute_nested", "rsv_variant_count", "rsv_variant_name",
            "rsv_tune", "rsv_synchronize", "rsv_last_error", "rsv_last_kernel_ms", "rsv_device_sm_count",
-           "rsv_reserves_noalloc"]
+           "rsv_reserves_noalloc", "rsv_mlp_param_count", "rsv_mlp_init", "rsv_mlp_set_params",
+           "rsv_mlp_get_params", "rsv_mlp_forward", "rsv_mlp_gradient", "rsv_surrogate_train", "rsv_surrogate_query"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -108,6 +128,14 @@ def load_library(path: str = LIB_PATH):
         "rsv_last_kernel_ms": ([vp], C.c_float),
         "rsv_device_sm_count": ([vp], i32),
         "rsv_reserves_noalloc": ([C.c_int, vp, vp, i32, vp, i32, vp, i32, i32, vp, vp], i32),
+        "rsv_mlp_param_count": ([], i64),
+        "rsv_mlp_init": ([vp, C.c_uint64], i32),
+        "rsv_mlp_set_params": ([vp, vp, i64], i32),
+        "rsv_mlp_get_params": ([vp, vp, i64], i32),
+        "rsv_mlp_forward": ([vp, vp, i64, vp], i32),
+        "rsv_mlp_gradient": ([vp, vp, vp, i64, vp, vp], i32),
+        "rsv_surrogate_train": ([vp, C.POINTER(rsv_surrogate_cfg), C.POINTER(rsv_surrogate_report)], i32),
+        "rsv_surrogate_query": ([vp, vp, i64, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -259,3 +287,55 @@ def rsv_reserves_noalloc(device: int, stream, pols, p_monthly, v, V0, scen_total
                                   _ptr(scen_total))
     if st != RSV_OK:
         raise RsvError(st, "rsv_reserves_noalloc")
+
+
+def rsv_mlp_param_count() -> int:
+    return int(load_library().rsv_mlp_param_count())
+
+
+def rsv_mlp_init(ctx, seed: int = 0):
+    _check(ctx, _lib.rsv_mlp_init(ctx, seed))
+
+
+def rsv_mlp_set_params(ctx, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(ctx, _lib.rsv_mlp_set_params(ctx, p.ctypes.data, p.size))
+
+
+def rsv_mlp_get_params(ctx):
+    p = np.zeros(rsv_mlp_param_count(), np.float32)
+    _check(ctx, _lib.rsv_mlp_get_params(ctx, p.ctypes.data, p.size))
+    return p
+
+
+def rsv_mlp_forward(ctx, X):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.zeros(X.shape[0], np.float32)
+    _check(ctx, _lib.rsv_mlp_forward(ctx, X.ctypes.data, X.shape[0], y.ctypes.data))
+    return y
+
+
+def rsv_mlp_gradient(ctx, X, target):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    t = np.ascontiguousarray(target, dtype=np.float32)
+    g = np.zeros(rsv_mlp_param_count(), np.float32)
+    loss = C.c_float()
+    _check(ctx, _lib.rsv_mlp_gradient(ctx, X.ctypes.data, t.ctypes.data, X.shape[0], g.ctypes.data,
+                                      C.byref(loss)))
+    return g, loss.value
+
+
+def rsv_surrogate_train(ctx, n_train=10_000_000, n_val=1_000_000, epochs=20, batch=8192, lr=2e-3, seed=0,
+                        a=0.1, b=0.04, sigma=0.01, r0=0.03, max_node_m=600, widen=1.5, tol=1e-3) -> dict:
+    cfg = rsv_surrogate_cfg(n_train, n_val, epochs, batch, lr, seed, a, b, sigma, r0, max_node_m, widen, tol)
+    rep = rsv_surrogate_report()
+    _check(ctx, _lib.rsv_surrogate_train(ctx, C.byref(cfg), C.byref(rep)))
+    return {k: getattr(rep, k) for k, _ in rsv_surrogate_report._fields_}
+
+
+def rsv_surrogate_query(ctx, queries, how=RSV_QUERY_FALLBACK):
+    """queries: a QUERY_DTYPE record array (pol, m, state, r); returns FP64 reserves."""
+    q = np.ascontiguousarray(queries, dtype=QUERY_DTYPE)
+    out = np.zeros(len(q))
+    _check(ctx, _lib.rsv_surrogate_query(ctx, q.ctypes.data, len(q), how, out.ctypes.data))
+    return out

@@ -1,0 +1,148 @@
+"""GPU tests of the surrogate network (BF16 tensor-core kernels, FP32
+accumulation) and of its recurrence labels, against the FP64 references.
+
+Bounds.  With the reference evaluated with BF16 storage at the same points
+as the GPU, the two differ by FP32 accumulation order (~1e-6 relative),
+erff/expf against FP64 erf/exp, and the occasional BF16 rounding flip of an
+activation whose FP32 and FP64 pre-activations straddle a rounding boundary
+(one flip moves an output by ~2^-8 of one of 256 terms): forward outputs
+within 2e-3 of the output scale, gradients within 2e-2 in norm per parameter
+block.  Against the reference without BF16 storage the BF16 rounding itself
+(2^-9 relative per value, 4 layers) bounds the forward difference by ~3e-2.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import mlp as ref
+from paper_1401_1757_gb300 import rsv
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def ctx():
+    h = rsv.rsv_create(0, torch.cuda.current_stream())
+    yield h
+    rsv.rsv_destroy(h)
+
+
+def random_params(seed):
+    rng = np.random.default_rng(seed)
+    p = np.zeros(ref.n_params())
+    o = 0
+    for i, j in ref.dims():
+        p[o:o + i * j] = rng.normal(0, math.sqrt(2.0 / i), i * j)
+        o += i * j
+        p[o:o + j] = rng.normal(0, 0.05, j)
+        o += j
+    p[o:o + 256] = rng.normal(0, 1 / 16, 256)
+    p[o + 256] = 0.1
+    return p.astype(np.float32).astype(np.float64)
+
+
+def test_mlp_forward_matches_reference(ctx):
+    p = random_params(1)
+    rng = np.random.default_rng(2)
+    X = rng.normal(0, 1, (300, 32)).astype(np.float32)     # not a multiple of 64: padded rows
+    rsv.rsv_mlp_set_params(ctx, p)
+    assert np.array_equal(rsv.rsv_mlp_get_params(ctx), p.astype(np.float32))
+    y = rsv.rsv_mlp_forward(ctx, X).astype(np.float64)
+    y_bf, _, _ = ref.forward(p, X.astype(np.float64), bf16_storage=True)
+    y_64, _, _ = ref.forward(p, X.astype(np.float64), bf16_storage=False)
+    scale = np.max(np.abs(y_bf))
+    print("forward: vs bf16-storage reference", np.max(np.abs(y - y_bf)) / scale,
+          "vs FP64 reference", np.linalg.norm(y - y_64) / np.linalg.norm(y_64))
+    assert np.max(np.abs(y - y_bf)) <= 2e-3 * scale
+    assert np.linalg.norm(y - y_64) <= 3e-2 * np.linalg.norm(y_64)
+
+
+def test_mlp_gradient_matches_reference(ctx):
+    p = random_params(3)
+    rng = np.random.default_rng(4)
+    X = rng.normal(0, 1, (256, 32)).astype(np.float32)
+    t = rng.normal(0, 1, 256).astype(np.float32)
+    rsv.rsv_mlp_set_params(ctx, p)
+    g, loss = rsv.rsv_mlp_gradient(ctx, X, t)
+    loss_ref, g_ref = ref.loss_and_grad(p, X.astype(np.float64), t.astype(np.float64), bf16_storage=True)
+    assert abs(loss - loss_ref) <= 2e-3 * loss_ref
+    o = 0
+    blocks = []
+    for i, j in ref.dims():
+        blocks += [(o, o + i * j), (o + i * j, o + i * j + j)]
+        o += i * j + j
+    blocks += [(o, o + 256), (o + 256, o + 257)]
+    worst = 0.0
+    for a, b in blocks:
+        d = np.linalg.norm(g[a:b] - g_ref[a:b]) / max(np.linalg.norm(g_ref[a:b]), 1e-30)
+        worst = max(worst, d)
+    print("gradient: worst block relative difference", worst)
+    assert worst <= 2e-2
+
+
+def test_recurrence_labels_match_oracle(ctx):
+    """RSV_QUERY_RECURRENCE (the surrogate's label and fallback) is the
+    recurrence on the Vasicek forward curve: against the oracle's full-state
+    recurrence on the zero-coupon curve, every product and JL state."""
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_mix(40, seed=6)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rng = np.random.default_rng(7)
+    qs = []
+    for p in range(40):
+        S = oracle.steps(int(pol["product"][p]), int(pol["age1_m"][p]), int(pol["age2_m"][p]),
+                         int(pol["term_m"][p]), 1440)[0]
+        m = int(rng.integers(0, S))
+        states = [0, 1, 2] if pol["product"][p] == 1 else [0]
+        for st in states:
+            qs.append((p, m, st, float(rng.uniform(-0.01, 0.09))))
+    q = np.zeros(len(qs), rsv.QUERY_DTYPE)
+    for k, (p, m, st, r) in enumerate(qs):
+        q[k] = (p, m, st, 0, r)
+    got = rsv.rsv_surrogate_query(ctx, q, how=rsv.RSV_QUERY_RECURRENCE)
+    worst = 0.0
+    for k, (p, m, st, r) in enumerate(qs):
+        prod = int(pol["product"][p])
+        term = int(pol["term_m"][p])
+        S = oracle.steps(prod, int(pol["age1_m"][p]), int(pol["age2_m"][p]), term, 1440)[0]
+        curve = np.array([synth.vasicek_zcb((t + 1) / 12, r) / synth.vasicek_zcb(t / 12, r) for t in range(S - m)])
+        rr = oracle.chain(prod, int(pol["age1_m"][p]) + m, float(pol["amount"][p]), tab, curve,
+                          age2=int(pol["age2_m"][p]) + m, term=max(0, term - m) if term else 0,
+                          rho=float(pol["reversion"][p]))
+        want = rr[0, st]
+        if want == 0.0:
+            assert got[k] == 0.0
+            continue
+        worst = max(worst, abs(got[k] - want) / abs(want))
+    print("labels: max rel err", worst)
+    assert worst <= 1e-12
+
+
+def test_surrogate_learns_and_falls_back(ctx):
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_mix(5000, seed=8)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_mlp_init(ctx, 5)
+    rep = rsv.rsv_surrogate_train(ctx, n_train=400_000, n_val=40_000, epochs=3, batch=4096, lr=2e-3, seed=5)
+    print("short training:", {k: round(v, 6) if isinstance(v, float) else v for k, v in rep.items()})
+    assert rep["val_median_rel"] < 0.05
+    assert rep["combined_max_rel"] <= 1e-3 or rep["frac_fallback"] == 1.0
+    # fallback queries are the recurrence exactly; network queries are finite and positive
+    rng = np.random.default_rng(9)
+    q = np.zeros(200, rsv.QUERY_DTYPE)
+    S = [oracle.steps(int(pol["product"][p]), int(pol["age1_m"][p]), int(pol["age2_m"][p]),
+                      int(pol["term_m"][p]), 1440)[0] for p in range(200)]
+    for k in range(200):
+        q[k] = (k, int(rng.integers(0, S[k]) // 12 * 12), 0, 0, 0.03)
+    net = rsv.rsv_surrogate_query(ctx, q, how=rsv.RSV_QUERY_NETWORK)
+    rec = rsv.rsv_surrogate_query(ctx, q, how=rsv.RSV_QUERY_RECURRENCE)
+    fb = rsv.rsv_surrogate_query(ctx, q, how=rsv.RSV_QUERY_FALLBACK)
+    assert np.all(np.isfinite(net)) and np.all(net > 0)
+    same = (fb == rec) | (fb == net)
+    assert np.all(same)
