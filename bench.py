@@ -40,6 +40,7 @@ import synth  # noqa: E402
 
 METRIC = "policy-scenario reserve valuations/s (plain vs surrogate) at stated error"
 N_POL, N_SCEN, N_STEPS = 100_000, 1000, 1200
+N_POL_MIX = 100_000
 WORKLOAD = ("100,000-policy mix (40% SL annuities, 20% JL reversionary 3-state, 20% term 5-40y, "
             "20% endowments 10-30y, ages 20-85) x 1,000 Vasicek scenarios x 1,200 monthly steps")
 
@@ -220,6 +221,36 @@ def bench_nested(rsv, torch, tab, steps, warmup):
     return res
 
 
+SURROGATE_WORKLOAD = ("MLP surrogate of the inner-loop expectation: 32->4x256->1 GELU, BF16 weights and activations, "
+                      "FP32 accumulation, trained on 10M recurrence labels of the 100,000-policy mix, scored on 1M "
+                      "held-out queries")
+
+
+def bench_surrogate(rsv, torch, tab, epochs, lr=2e-3, n_train=10_000_000, n_val=1_000_000):
+    """Train the surrogate on recurrence labels of the four-product portfolio and
+    score it; throughput of the network against the recurrence it replaces."""
+    pol = synth.portfolio_mix(N_POL_MIX, seed=0)
+    ctx = rsv.rsv_create(torch.cuda.current_device(), torch.cuda.current_stream())
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_mlp_init(ctx, 0)
+    rep = rsv.rsv_surrogate_train(ctx, n_train=n_train, n_val=n_val, epochs=epochs, batch=8192, lr=lr, seed=0)
+    rsv.rsv_destroy(ctx)
+    flops_q = 2 * (32 * 256 + 3 * 256 * 256 + 256)
+    return {
+        "workload": SURROGATE_WORKLOAD, "epochs": epochs, "lr": lr,
+        "held_out": {k: rep[k] for k in ("val_max_rel", "val_p99_rel", "val_median_rel", "val_rms_rel")},
+        "tol": 1e-3, "frac_fallback": rep["frac_fallback"], "combined_max_rel": rep["combined_max_rel"],
+        "buckets_flagged": f"{rep['n_flagged']} of {rep['n_buckets']}",
+        "residual_target_sd": rep["y_std"],
+        "network_queries_s": rep["n_infer"] / (rep["infer_ms"] / 1e3),
+        "network_tflops": rep["n_infer"] * flops_q / (rep["infer_ms"] / 1e3) / 1e12,
+        "recurrence_fp64_queries_s": rep["n_label"] / (rep["label_ms"] / 1e3),
+        "train_s": rep["train_ms"] / 1e3,
+        "train_samples_s": epochs * (n_train // 8192) * 8192 / max(rep["train_ms"] / 1e3, 1e-9),
+    }
+
+
 def cpu_baseline(pol, tab, v, n_sample, gpu_rows):
     """Oracle timed on the host cores on the first n_sample policies x all
     scenarios; also the max relative error of each GPU form on that sample."""
@@ -256,6 +287,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-nested", action="store_true")
+    ap.add_argument("--surrogate-epochs", type=int, default=0, help="train and score the surrogate (0: skip)")
+    ap.add_argument("--surrogate-lr", type=float, default=2e-3)
     args = ap.parse_args()
     if (args.policies, args.scenarios) != (N_POL, N_SCEN):
         N_POL, N_SCEN = args.policies, args.scenarios
@@ -386,6 +419,9 @@ def main():
     nested = None
     if not args.no_nested and rank == 0:
         nested = bench_nested(rsv, torch, tab, steps=2, warmup=1)
+    surrogate = None
+    if args.surrogate_epochs > 0 and rank == 0:
+        surrogate = bench_surrogate(rsv, torch, tab, args.surrogate_epochs, lr=args.surrogate_lr)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -420,6 +456,7 @@ def main():
         "clocks": clocks,
         "forms": results,
         "nested": nested,
+        "surrogate": surrogate,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

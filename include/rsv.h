@@ -191,9 +191,12 @@ rsv_status rsv_compute_reserves(rsv_ctx *ctx, const rsv_opts *opts, rsv_out *out
  * (w + 1/2) 2^-32, Box-Muller; exact monthly Vasicek steps of (r, integral
  * of r), v = exp(-integral of r), all in FP64. */
 enum {
-    RSV_NESTED_MC = 0,     /* inner Monte Carlo ("brute force")                       */
-    RSV_NESTED_CURVE = 2   /* inner expectation in closed form: the recurrence on the
-                              Vasicek forward curve P(t+1|r)/P(t|r) (one chain each)   */
+    RSV_NESTED_MC = 0,        /* inner Monte Carlo ("brute force")                       */
+    RSV_NESTED_SURROGATE = 1, /* inner expectation by the trained surrogate network, with
+                                 the recurrence on the forward curve for flagged buckets
+                                 (needs rsv_surrogate_train with the same a, b, sigma)  */
+    RSV_NESTED_CURVE = 2      /* inner expectation in closed form: the recurrence on the
+                                 Vasicek forward curve P(t+1|r)/P(t|r) (one chain each)   */
 };
 
 typedef struct {
@@ -216,10 +219,12 @@ typedef struct {
  *   r_node [n_outer][n_nodes]  outer short rate at the node (optional)
  *   D0     [n_outer][n_nodes]  outer discount product month 0 -> node (optional)
  *   L_all  [n_outer][n_nodes][n_inner] every L_{o,n,i} (optional; n_inner = 1
- *                              with RSV_NESTED_CURVE)
+ *                              with RSV_NESTED_CURVE and RSV_NESTED_SURROGATE)
  * Values are at the node (not discounted to 0). */
 typedef struct {
     double *L_mean, *L_q995, *r_node, *D0, *L_all;
+    int64_t *n_fallback;  /* optional, host: queries the surrogate mode valued by the
+                             recurrence (its network valued the rest)                  */
 } rsv_nested_out;
 
 /* Nested valuation of the loaded portfolio (tables and portfolio needed, no
@@ -291,6 +296,15 @@ int64_t rsv_mlp_param_count(void);
 rsv_status rsv_mlp_init(rsv_ctx *ctx, uint64_t seed);
 rsv_status rsv_mlp_set_params(rsv_ctx *ctx, const float *params, int64_t n);
 rsv_status rsv_mlp_get_params(rsv_ctx *ctx, float *params, int64_t n);
+
+/* Kernels that evaluate the network for inference (rsv_mlp_forward,
+ * rsv_surrogate_query, the nested surrogate mode): RSV_MLP_TCGEN05 (default)
+ * runs all layers and the head in one kernel on the tcgen05 tensor cores with
+ * TMEM accumulators; RSV_MLP_MMA_SYNC runs the per-layer mma.sync kernels the
+ * training uses.  Both compute the same network in BF16 with FP32
+ * accumulation. */
+enum { RSV_MLP_MMA_SYNC = 0, RSV_MLP_TCGEN05 = 1 };
+rsv_status rsv_mlp_set_backend(rsv_ctx *ctx, int32_t backend);
 
 /* Network output for n rows of 32 host FP32 features (rounded to BF16 on the
  * way in), 1 <= n <= 2^20; y (host) receives n outputs. */

@@ -6,9 +6,11 @@ with exact-erf GELU, flat parameters W1 [32][256], b1, W2, b2, W3, b3, W4, b4
 Backward pass written out by the chain rule.
 
 ``bf16=True`` evaluates the same definition with BF16 storage where the GPU
-stores BF16 -- the inputs, the four weight matrices, the activations and the
-back-propagated pre-activation gradients that feed the matrix products --
-and FP64 everywhere else, so the two differ only by FP32 accumulation order
+stores BF16 -- the inputs (each feature as an exact hi + lo pair of BF16
+values, which the first layer reads against the same weights), the four
+weight matrices, the activations the matrix products read (the head reads
+the last hidden layer unrounded) and the back-propagated pre-activation
+gradients that feed the matrix products -- and FP64 everywhere else, so the two differ only by FP32 accumulation order
 and rare BF16 rounding flips.  Pinned against central finite differences.
 """
 from __future__ import annotations
@@ -63,11 +65,12 @@ def gelu_grad(z):
 def forward(p, X, bf16_storage=False):
     layers, w5, b5 = unpack(p)
     r = bf16 if bf16_storage else (lambda x: np.asarray(x, dtype=np.float64))
-    A = r(X)
+    X = np.asarray(X, dtype=np.float64)
+    A = bf16(X) + bf16(X - bf16(X)) if bf16_storage else X
     Zs, As = [], [A]
-    for W, b in layers:
+    for li, (W, b) in enumerate(layers):
         Z = A @ r(W) + b
-        A = r(gelu(Z))
+        A = gelu(Z) if li == len(layers) - 1 else r(gelu(Z))
         Zs.append(Z)
         As.append(A)
     y = A @ w5 + b5

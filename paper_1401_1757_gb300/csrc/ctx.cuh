@@ -66,6 +66,10 @@ struct SurrogateState {
     double a = 0.1, b = 0.04, sigma = 0.01, r0 = 0.03;   // Vasicek model of the labels
     std::vector<unsigned char> flag;    // per bucket: 1 = value by the recurrence
     DevBuf d_flag, d_q, d_lab, d_y, d_X, d_pred, d_err, d_aux;
+    DevBuf d_curve, d_comm, d_lnb;      // forward-curve increments, commutation columns, ln base values
+    double curve_key[3] = {0.0, 0.0, -1.0};
+    int comm_pad = -1, comm_ntab = -1;
+    unsigned long long comm_gen = 0;
 };
 
 }  // namespace rsv

@@ -4,6 +4,9 @@
 //
 // Forward per layer l = 1..4:  Z_l = A_{l-1} W_l + b_l,  A_l = gelu(Z_l)
 // (A_0 = features), head y = A_4 w5 + b5.  Loss: mean squared error.
+// The activations the tensor cores read are BF16; the head reads the last
+// hidden layer in FP32, since BF16 rounding of its 256 inputs alone would put
+// ~1e-3 of noise on the output, the size of the surrogate's error target.
 // Backward: dZ_4 = (dy w5^T) * gelu'(Z_4); for l = 4..1: dW_l = A_{l-1}^T dZ_l,
 // db_l = column sums of dZ_l, dZ_{l-1} = (dZ_l W_l^T) * gelu'(Z_{l-1}).
 // Every product runs on the tensor cores (mlp_gemm.cuh); sums over the batch
@@ -37,7 +40,7 @@ cudaError_t gemm(const GemmArgs& g, cudaStream_t st) {
 
 // y[r] = A4[r] . w5 + b5; with a target: dy[r] = 2 (y - t) / B and the
 // per-block sums of squared errors (fixed order).
-__global__ void head_fwd_kernel(const __nv_bfloat16* __restrict__ A4, const float* __restrict__ w5,
+__global__ void head_fwd_kernel(const float* __restrict__ A4, const float* __restrict__ w5,
                                 const float* __restrict__ b5, int B, float* __restrict__ y,
                                 const float* __restrict__ target, float* __restrict__ dy,
                                 float* __restrict__ sq_part) {
@@ -47,7 +50,7 @@ __global__ void head_fwd_kernel(const __nv_bfloat16* __restrict__ A4, const floa
     float se = 0.0f;
     if (r < B) {
         float s = 0.0f;
-        for (int k = lane; k < MLP_H; k += 32) s += __bfloat162float(A4[(size_t)r * MLP_H + k]) * w5[k];
+        for (int k = lane; k < MLP_H; k += 32) s += A4[(size_t)r * MLP_H + k] * w5[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         s += b5[0];
@@ -121,6 +124,21 @@ __global__ void to_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __res
         y[i] = __float2bfloat16_rn(x[i]);
 }
 
+// [W1; W1] in BF16 from the FP32 W1 [MLP_IN][MLP_H]
+__global__ void tied_w1_kernel(const float* __restrict__ w1, __nv_bfloat16* __restrict__ y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MLP_IN * MLP_H; i += gridDim.x * blockDim.x) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(w1[i]);
+        y[i] = b;
+        y[MLP_IN * MLP_H + i] = b;
+    }
+}
+
+// dW1 = dW1' (hi rows) + dW1' (lo rows): the gradient of tied weights
+__global__ void fold_dw1_kernel(const float* __restrict__ dw, float* __restrict__ g) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MLP_IN * MLP_H; i += gridDim.x * blockDim.x)
+        g[i] = dw[i] + dw[MLP_IN * MLP_H + i];
+}
+
 }  // namespace
 
 cudaError_t Mlp::ensure(int batch) {
@@ -139,17 +157,19 @@ cudaError_t Mlp::ensure(int batch) {
         ALLOC(grads, P * 4);
         ALLOC(adam_m, P * 4);
         ALLOC(adam_v, P * 4);
-        ALLOC(wbf, (size_t)MLP_IN * MLP_H * 2 + 3 * (size_t)MLP_H * MLP_H * 2);
+        ALLOC(wbf, (size_t)MLP_XW * MLP_H * 2 + 3 * (size_t)MLP_H * MLP_H * 2);
+        ALLOC(dW1, (size_t)MLP_XW * MLP_H * 4);
         cudaMemset(adam_m, 0, P * 4);
         cudaMemset(adam_v, 0, P * 4);
     }
-    ALLOC(X, B * MLP_IN * 2);
+    ALLOC(X, B * MLP_XW * 2);
     for (int l = 0; l < 4; ++l) {
         ALLOC(Z[l], B * MLP_H * 4);
         ALLOC(A[l], B * MLP_H * 2);
         ALLOC(dZf[l], B * MLP_H * 4);
         ALLOC(dZb[l], B * MLP_H * 2);
     }
+    ALLOC(A4f, B * MLP_H * 4);
     ALLOC(y, B * 4);
     ALLOC(t, B * 4);
     ALLOC(dy, B * 4);
@@ -161,7 +181,7 @@ cudaError_t Mlp::ensure(int batch) {
 }
 
 void Mlp::release() {
-    void* ps[] = {params, grads, adam_m, adam_v, wbf, X, y, t, dy, sq, loss};
+    void* ps[] = {params, grads, adam_m, adam_v, wbf, dW1, A4f, X, y, t, dy, sq, loss, wt};
     for (void* p : ps)
         if (p) cudaFree(p);
     for (int l = 0; l < 4; ++l) {
@@ -173,15 +193,16 @@ void Mlp::release() {
     *this = Mlp();
 }
 
-__nv_bfloat16* Mlp::wb(int l) const {   // BF16 copy of W_l, [in][H]
+__nv_bfloat16* Mlp::wb(int l) const {   // BF16 copy of W_l as the GEMM reads it, [k][H]
     size_t o = 0;
-    for (int i = 1; i < l; ++i) o += (size_t)mlp_in_dim(i) * MLP_H;
+    for (int i = 1; i < l; ++i) o += (size_t)mlp_k_dim(i) * MLP_H;
     return wbf + o;
 }
 
 cudaError_t Mlp::refresh_bf16(cudaStream_t st) {
-    for (int l = 1; l <= 4; ++l) {
-        const size_t n = (size_t)mlp_in_dim(l) * MLP_H;
+    tied_w1_kernel<<<32, 256, 0, st>>>(params + mlp_w_off(1), wb(1));
+    for (int l = 2; l <= 4; ++l) {
+        const size_t n = (size_t)MLP_H * MLP_H;
         to_bf16_kernel<<<64, 256, 0, st>>>(params + mlp_w_off(l), wb(l), n);
     }
     return cudaGetLastError();
@@ -198,16 +219,17 @@ cudaError_t Mlp::forward(const __nv_bfloat16* Xin, int B, float* yout, const flo
         g.B = wb(l);
         g.M = B;
         g.N = MLP_H;
-        g.K = mlp_in_dim(l);
+        g.K = mlp_k_dim(l);
         g.lda = g.K;
         g.ldb = MLP_H;
         g.Cf = Z[l - 1];
         g.Cb = A[l - 1];
         g.bias = params + mlp_b_off(l);
+        g.Af = l == 4 ? A4f : nullptr;
         if ((e = gemm<true, false, EPI_BIAS_GELU>(g, st)) != cudaSuccess) return e;
         in = A[l - 1];
     }
-    head_fwd_kernel<<<(B + 7) / 8, 256, 0, st>>>(A[3], params + mlp_w5_off(), params + mlp_w5_off() + MLP_H, B,
+    head_fwd_kernel<<<(B + 7) / 8, 256, 0, st>>>(A4f, params + mlp_w5_off(), params + mlp_w5_off() + MLP_H, B,
                                                   yout, target, dy, target ? sq : nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (target) {
@@ -221,13 +243,13 @@ cudaError_t Mlp::forward(const __nv_bfloat16* Xin, int B, float* yout, const flo
 cudaError_t Mlp::backward(const __nv_bfloat16* Xin, int B, cudaStream_t st) {
     cudaError_t e;
     const size_t w5 = mlp_w5_off();
-    colsum_kernel<<<(MLP_H + 127) / 128, 128, 0, st>>>(nullptr, A[3], dy, B, MLP_H, grads + w5);
+    colsum_kernel<<<(MLP_H + 127) / 128, 128, 0, st>>>(A4f, nullptr, dy, B, MLP_H, grads + w5);
     colsum_kernel<<<1, 32, 0, st>>>(dy, nullptr, nullptr, B, 1, grads + w5 + MLP_H);
     head_bwd_kernel<<<(unsigned)(((size_t)B * MLP_H + 255) / 256), 256, 0, st>>>(dy, params + w5, Z[3], B, dZf[3],
                                                                                  dZb[3]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     for (int l = 4; l >= 1; --l) {
-        const int K = mlp_in_dim(l);
+        const int K = mlp_k_dim(l);
         // dW_l = A_{l-1}^T dZ_l : A operand stored [B][K] = [k][m]; B operand dZ_l stored [B][H] = [k][n]
         GemmArgs g{};
         g.A = l > 1 ? A[l - 2] : Xin;
@@ -237,8 +259,12 @@ cudaError_t Mlp::backward(const __nv_bfloat16* Xin, int B, cudaStream_t st) {
         g.K = B;
         g.lda = K;
         g.ldb = MLP_H;
-        g.Cf = grads + mlp_w_off(l);
+        g.Cf = l > 1 ? grads + mlp_w_off(l) : dW1;
         if ((e = gemm<false, false, EPI_F32>(g, st)) != cudaSuccess) return e;
+        if (l == 1) {
+            fold_dw1_kernel<<<32, 256, 0, st>>>(dW1, grads + mlp_w_off(1));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         colsum_kernel<<<(MLP_H + 127) / 128, 128, 0, st>>>(dZf[l - 1], nullptr, nullptr, B, MLP_H,
                                                           grads + mlp_b_off(l));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -30,6 +30,7 @@ struct GemmArgs {
     float* Cf;               // FP32 output [M][N] (EPI_F32, EPI_BIAS_GELU: Z, EPI_GELU_BWD: G)
     __nv_bfloat16* Cb;       // BF16 output [M][N] (activations or gradients)
     const float* bias;       // [N] (EPI_BIAS_GELU)
+    float* Af;               // FP32 activations [M][N] (EPI_BIAS_GELU, optional)
     const float* Zin;        // [M][N] pre-activations (EPI_GELU_BWD)
 };
 
@@ -188,7 +189,9 @@ __global__ void __launch_bounds__(GTHREADS) gemm_bf16_kernel(const GemmArgs g) {
                     v0 += g.bias[col];
                     v1 += g.bias[col + 1];
                     if (g.Cf) *reinterpret_cast<float2*>(g.Cf + o) = make_float2(v0, v1);
-                    *reinterpret_cast<__nv_bfloat162*>(g.Cb + o) = __floats2bfloat162_rn(gelu_f(v0), gelu_f(v1));
+                    const float a0 = gelu_f(v0), a1 = gelu_f(v1);
+                    *reinterpret_cast<__nv_bfloat162*>(g.Cb + o) = __floats2bfloat162_rn(a0, a1);
+                    if (g.Af) *reinterpret_cast<float2*>(g.Af + o) = make_float2(a0, a1);
                 } else {
                     const float2 z = *reinterpret_cast<const float2*>(g.Zin + o);
                     v0 *= gelu_grad_f(z.x);

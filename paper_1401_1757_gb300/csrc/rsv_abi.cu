@@ -67,6 +67,24 @@ __global__ void reduce_groups_kernel(const double* __restrict__ part2, int n_gro
     total[s] = acc;
 }
 
+// L[k] = base[k] + sum over q in [seg[k], seg[k+1]) of w[q] V[q], one block per
+// (outer path, node), fixed order.
+__global__ void segment_wsum_kernel(const long long* __restrict__ seg, const double* __restrict__ w,
+                                    const double* __restrict__ V, const double* __restrict__ base,
+                                    double* __restrict__ L) {
+    __shared__ double sd[256];
+    const long long a = seg[blockIdx.x], b = seg[blockIdx.x + 1];
+    double s = 0.0;
+    for (long long q = a + threadIdx.x; q < b; q += blockDim.x) s += w[q] * V[q];
+    sd[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) sd[threadIdx.x] += sd[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) L[blockIdx.x] = base[blockIdx.x] + sd[0];
+}
+
 __global__ void scale_kernel(double* __restrict__ x, size_t n, double f) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         x[i] *= f;
@@ -414,7 +432,13 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
         return fail(c, RSV_E_ARG, "bad nested sizes");
     if ((long long)(sp->n_nodes - 1) * sp->node_step_m > kMaxAgeSteps)
         return fail(c, RSV_E_ARG, "last node beyond %d months", kMaxAgeSteps);
-    if (sp->mode != RSV_NESTED_MC && sp->mode != RSV_NESTED_CURVE) return fail(c, RSV_E_ARG, "bad mode %d", sp->mode);
+    if (sp->mode != RSV_NESTED_MC && sp->mode != RSV_NESTED_CURVE && sp->mode != RSV_NESTED_SURROGATE)
+        return fail(c, RSV_E_ARG, "bad mode %d", sp->mode);
+    if (sp->mode == RSV_NESTED_SURROGATE) {
+        if (!c->sur.trained) return fail(c, RSV_E_STATE, "surrogate not trained");
+        if (c->sur.a != sp->a || c->sur.b != sp->b || c->sur.sigma != sp->sigma)
+            return fail(c, RSV_E_ARG, "the surrogate was trained for other Vasicek parameters");
+    }
     if (!(sp->a > 0.0) || !(sp->sigma >= 0.0) || !std::isfinite(sp->a) || !std::isfinite(sp->b) ||
         !std::isfinite(sp->sigma) || !std::isfinite(sp->r0) || sp->batch_outer < 0)
         return fail(c, RSV_E_ARG, "bad Vasicek parameters");
@@ -431,12 +455,13 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
     const Layout& L = c->lay;
     const int n_pol = (int)c->pols.size(), NN = sp->n_nodes, NO = sp->n_outer, step = sp->node_step_m;
     const bool mc = sp->mode == RSV_NESTED_MC;
+    const bool sur = sp->mode == RSV_NESTED_SURROGATE;
     const int n_inner = mc ? sp->n_inner : 1;
     const int i_pad = (n_inner + 31) / 32 * 32;
 
     // weights and remaining lengths
     std::vector<double> w((size_t)std::max(1, n_pol) * NN * 3, 0.0);
-    std::vector<int> Ln(NN, 0);
+    std::vector<int> Ln(NN, 0), Sp(std::max(1, n_pol), 0);
     for (int p = 0; p < n_pol; ++p) {
         const rsv_policy& r = c->pols[p];
         const bool jl = r.product == RSV_JL_REVERSIONARY, ann = r.product <= RSV_JL_REVERSIONARY;
@@ -450,6 +475,7 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
         } else {
             S = r.term_m;
         }
+        Sp[p] = S;
         const std::vector<double>& tx = c->tab[r.table1];
         const std::vector<double>& ty = c->tab[jl ? r.table2 : r.table1];
         double Px = 1.0, Py = 1.0;
@@ -520,7 +546,53 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
     a.counter = c->d_ctl.as<int32_t>();
     a.status = c->d_ctl.as<int32_t>() + 1;
     a.L_all = Lall;
-    for (int o0 = 0; o0 < NO; o0 += B) {
+    if (sur) {
+        // one query per in-force (policy, state) and (outer path, node), at the node's rate
+        const size_t on_n = (size_t)NO * NN;
+        std::vector<double> rn(on_n), base(on_n, 0.0);
+        CU(cudaMemcpyAsync(rn.data(), c->d_nest_rn.p, on_n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        std::vector<rsv_query> hq;
+        std::vector<double> hw;
+        std::vector<long long> seg(on_n + 1, 0);
+        for (int o = 0; o < NO; ++o)
+            for (int n = 0; n < NN; ++n) {
+                const size_t k = (size_t)o * NN + n;
+                seg[k] = (long long)hq.size();
+                const int m = n * step;
+                for (int p = 0; p < n_pol; ++p)
+                    for (int j = 0; j < 3; ++j) {
+                        const double wj = w[((size_t)p * NN + n) * 3 + j];
+                        if (wj == 0.0) continue;
+                        if (Sp[p] == m) {   // matures at the node: its boundary value, no projection
+                            base[k] += c->pols[p].product == RSV_ENDOWMENT ? wj : 0.0;
+                            continue;
+                        }
+                        rsv_query q{p, m, j, 0, rn[k]};
+                        hq.push_back(q);
+                        hw.push_back(wj);
+                    }
+            }
+        seg[on_n] = (long long)hq.size();
+        const long long nq = (long long)hq.size();
+        CU(c->d_nest_plane.ensure(std::max<size_t>(1, (size_t)nq) * 16 + (on_n + 1) * 8 + on_n * 8));
+        double* dV = c->d_nest_plane.as<double>();
+        double* dw = dV + std::max<long long>(1, nq);
+        long long* dseg = reinterpret_cast<long long*>(dw + std::max<long long>(1, nq));
+        double* dbase = reinterpret_cast<double*>(dseg + on_n + 1);
+        long long nfb = 0;
+        if (nq > 0) {
+            st = sur_value_queries(c, hq.data(), nq, dV, &nfb);
+            if (st != RSV_OK) return st;
+            CU(cudaMemcpyAsync(dw, hw.data(), nq * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        }
+        CU(cudaMemcpyAsync(dseg, seg.data(), (on_n + 1) * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+        CU(cudaMemcpyAsync(dbase, base.data(), on_n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        segment_wsum_kernel<<<(unsigned)on_n, 256, 0, c->stream>>>(dseg, dw, dV, dbase, Lall);
+        CU(cudaGetLastError());
+        if (out->n_fallback) *out->n_fallback = nfb;
+    }
+    for (int o0 = 0; o0 < NO && !sur; o0 += B) {
         const int Bc = std::min(B, NO - o0);
         if (mc)
             CU(launch_inner_paths(form, vs, sp->seed, o0, Bc, NN, n_inner, i_pad, Lmax, c->d_nest_ln.as<int>(),
@@ -590,8 +662,11 @@ rsv_status rsv_destroy(rsv_ctx* c) {
                       &c->d_tab[2], &c->lay.slots, &c->lay.kinds, &c->d_ctl, &c->d_partial, &c->d_part2,
                       &c->d_o_v0f, &c->d_o_v0d, &c->d_o_tot, &c->d_o_pt, &c->d_o_traj, &c->d_nest_w,
                       &c->d_nest_ln, &c->d_nest_rn, &c->d_nest_d0, &c->d_nest_plane, &c->d_nest_mean,
-                      &c->d_nest_kth, &c->d_nest_all})
+                      &c->d_nest_kth, &c->d_nest_all, &c->d_pols, &c->sur.d_flag, &c->sur.d_q, &c->sur.d_lab,
+                      &c->sur.d_y, &c->sur.d_X, &c->sur.d_pred, &c->sur.d_err, &c->sur.d_aux, &c->sur.d_curve,
+                      &c->sur.d_comm, &c->sur.d_lnb})
         b->release();
+    c->mlp.release();
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;

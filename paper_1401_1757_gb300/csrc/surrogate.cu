@@ -81,12 +81,58 @@ __global__ void sample_queries_kernel(const PolSur* __restrict__ pols, int n_pol
 
 }  // namespace
 
+// Forward-curve increments of the Vasicek zero-coupon price at monthly points:
+// ln P(T_{t+1} | r) - ln P(T_t | r) = dA_t - dB_t r with T_t = t/12 and
+// B(T) = (1 - e^{-aT})/a, ln P = (B - T)(a^2 b - sigma^2/2)/a^2 - sigma^2 B^2/(4a) - B r
+// (Vasicek 1977).  dB is formed without cancellation.
+__global__ void sur_curve_kernel(double a, double b, double sigma, int n, double2* __restrict__ curve) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double T0 = t / 12.0, T1 = (t + 1) / 12.0;
+    const double B0 = -expm1(-a * T0) / a, B1 = -expm1(-a * T1) / a;
+    const double dB = exp(-a * T0) * (-expm1(-a / 12.0)) / a;
+    const double K1 = (a * a * b - 0.5 * sigma * sigma) / (a * a), K2 = sigma * sigma / (4.0 * a);
+    curve[t] = make_double2((dB - 1.0 / 12.0) * K1 - K2 * dB * (B0 + B1), dB);
+}
+
+// Commutation columns of each decrement table at each flat reference rate
+// delta (one thread per (table, rate)): l_k = prod_{j<k} p_j from month 0,
+// D_k = v^k l_k, N_k = sum_{j>=k} D_j, C_k = v^{k+1} l_k q_k, M_k = sum_{j>=k} C_j,
+// v = exp(-delta/12); survival is zero past the table's end.
+__global__ void sur_comm_kernel(const double2* __restrict__ tab, int tab_pad, int n_tab, double* __restrict__ comm) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n_tab * SUR_COMM_N) return;
+    const int t = id / SUR_COMM_N, g = id % SUR_COMM_N;
+    const int CL = sur_comm_len(tab_pad);
+    double* D = comm + (size_t)id * 3 * CL;
+    double* N = D + CL;
+    double* M = N + CL;
+    const double v = exp(-(SUR_COMM_LO + g * SUR_COMM_STEP) / 12.0);
+    double l = 1.0, vk = 1.0;
+    for (int k = 0; k <= tab_pad; ++k) {
+        const double p = k < tab_pad ? tab[(size_t)t * tab_pad + k].x : 0.0;
+        D[k] = vk * l;
+        M[k] = vk * v * l * (1.0 - p);   // C_k, summed below
+        l *= p;
+        vk *= v;
+    }
+    D[tab_pad + 1] = 0.0;
+    double sn = 0.0, sm = 0.0;
+    N[tab_pad + 1] = 0.0;
+    M[tab_pad + 1] = 0.0;
+    for (int k = tab_pad; k >= 0; --k) {
+        sn += D[k];
+        sm += M[k];
+        N[k] = sn;
+        M[k] = sm;
+    }
+}
+
 // Reserve per unit amount in the query's state: the FP64 recurrence on the
 // Vasicek forward curve from the policy's end back to the node.  With `flag`,
 // only queries whose bucket is flagged are valued (the fallback).
-__global__ void sur_label_kernel(const PolSur* __restrict__ pols, const double2* __restrict__ tab, int tab_pad,
-                                 const SurQuery* __restrict__ qs, long long n, double a, double b, double sigma,
-                                 const unsigned char* __restrict__ flag, double* __restrict__ V) {
+__global__ void sur_label_kernel(const PolSur* __restrict__ pols, const SurTables T, const SurQuery* __restrict__ qs,
+                                 long long n, const unsigned char* __restrict__ flag, double* __restrict__ V) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const SurQuery Q = qs[i];
         if (flag && (Q.state < 0 || !flag[Q.bucket])) continue;
@@ -96,18 +142,17 @@ __global__ void sur_label_kernel(const PolSur* __restrict__ pols, const double2*
         }
         const PolSur P = pols[Q.pol];
         const int Sn = P.S - Q.m;
-        const int i1 = P.tab1 * tab_pad + P.age1 + Q.m, i2 = P.tab2 * tab_pad + P.age2 + Q.m;
+        const double2* tx = T.tab + (size_t)P.tab1 * T.tab_pad + P.age1 + Q.m;
+        const double2* ty = T.tab + (size_t)P.tab2 * T.tab_pad + P.age2 + Q.m;
         double V00 = P.product == RSV_ENDOWMENT ? 1.0 : 0.0, V01 = 0.0, V10 = 0.0;
-        double lnP_next = vasicek_lnP(Sn / 12.0, Q.r, a, b, sigma);
         for (int t = Sn - 1; t >= 0; --t) {
-            const double lnP = vasicek_lnP(t / 12.0, Q.r, a, b, sigma);
-            const double v = exp(lnP_next - lnP);
-            lnP_next = lnP;
-            const double2 ex = tab[i1 + t];
+            const double2 dc = T.curve[t];   // month t after the node
+            const double v = exp(dc.x - dc.y * Q.r);
+            const double2 ex = tx[t];
             if (P.product == RSV_SL_ANNUITY) {
                 V00 = v * ex.x * (1.0 + V00);
             } else if (P.product == RSV_JL_REVERSIONARY) {
-                const double2 ey = tab[i2 + t];
+                const double2 ey = ty[t];
                 const double n01 = v * ex.x * (1.0 + V01);
                 const double n10 = v * ey.x * (P.rho + V10);
                 V00 = v * ex.x * ey.x * (1.0 + V00) + ey.y * n01 + ex.y * n10;
@@ -120,16 +165,74 @@ __global__ void sur_label_kernel(const PolSur* __restrict__ pols, const double2*
         V[i] = Q.state == 0 ? V00 : (Q.state == 1 ? V01 : V10);
     }
 }
+// Base value per unit amount from the commutation columns at flat rate
+// grid point g: the classical actuarial values (annuity (N_{x+1} - N_{x+n+1})/D_x,
+// term assurance (M_x - M_{x+n})/D_x, pure endowment D_{x+n}/D_x) for n
+// months from attained month x.  The joint-life state 00 takes a_x + rho a_y
+// (the joint-life annuity it omits is left to the network).
+__device__ double sur_base_value(const PolSur& P, const SurTables& T, int g, int m, int state) {
+    const int CL = sur_comm_len(T.tab_pad), n = P.S - m;
+    auto col = [&](int tab) { return T.comm + ((size_t)tab * SUR_COMM_N + g) * 3 * CL; };
+    auto ann = [&](int tab, int x) {
+        const double* D = col(tab);
+        const int e = min(x + n, T.tab_pad);
+        return D[x] > 0.0 ? (D[CL + x + 1] - D[CL + e + 1]) / D[x] : 0.0;
+    };
+    const int x = P.age1 + m;
+    if (P.product == RSV_SL_ANNUITY) return ann(P.tab1, x);
+    if (P.product == RSV_JL_REVERSIONARY) {
+        const int y = P.age2 + m;
+        if (state == 1) return ann(P.tab1, x);
+        if (state == 2) return P.rho * ann(P.tab2, y);
+        return ann(P.tab1, x) + P.rho * ann(P.tab2, y);
+    }
+    const double* D = col(P.tab1);
+    if (!(D[x] > 0.0)) return 1.0;   // past the table: death in the first month
+    const int e = min(x + n, T.tab_pad + 1);
+    const double A1 = (D[2 * CL + x] - D[2 * CL + e]) / D[x];
+    return P.product == RSV_TERM_ASSURANCE ? A1 : A1 + D[e] / D[x];
+}
 
-// Features of a query (zero-padded to MLP_IN, BF16).
-__global__ void sur_features_kernel(const PolSur* __restrict__ pols, const SurQuery* __restrict__ qs, long long n,
-                                    __nv_bfloat16* __restrict__ X) {
+// ln of the base value at the query's own flat rate: the Vasicek yield to
+// half the remaining term (between one month and 15 years), interpolated
+// linearly in ln between the two neighbouring grid rates.  Returns the yield
+// through *delta.  0 where the base value is not positive.
+__device__ double sur_ln_base(const PolSur& P, const SurTables& T, const SurQuery& Q, double* delta) {
+    const int n = P.S - Q.m;
+    const double h = min(max(n / 2, 1), 180) / 12.0;
+    const double d = -vasicek_lnP(h, Q.r, T.a, T.b, T.sigma) / h;
+    *delta = d;
+    const double u = fmin(fmax((d - SUR_COMM_LO) / SUR_COMM_STEP, 0.0), (double)(SUR_COMM_N - 1));
+    const int g0 = min((int)u, SUR_COMM_N - 2);
+    const double f = u - g0;
+    const double b0 = sur_base_value(P, T, g0, Q.m, Q.state), b1 = sur_base_value(P, T, g0 + 1, Q.m, Q.state);
+    if (!(b0 > 0.0) || !(b1 > 0.0)) return 0.0;
+    return (1.0 - f) * log(b0) + f * log(b1);
+}
+
+// A feature row as exact hi + lo BF16 halves (the first layer's weights are
+// tied across the halves, so it sees each feature to ~16 bits).
+__device__ __forceinline__ void sur_store_features(const float (&f)[MLP_IN], __nv_bfloat16* row) {
+#pragma unroll
+    for (int k = 0; k < MLP_IN; ++k) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(f[k]);
+        row[k] = h;
+        row[MLP_IN + k] = __float2bfloat16_rn(f[k] - __bfloat162float(h));
+    }
+}
+
+// Features of a query (zero-padded to MLP_IN, hi + lo BF16) and the ln base
+// value the network's output is added to.
+__global__ void sur_features_kernel(const PolSur* __restrict__ pols, const SurTables T, const SurQuery* __restrict__ qs,
+                                    long long n, __nv_bfloat16* __restrict__ X, double* __restrict__ lnb) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const SurQuery Q = qs[i];
         const PolSur P = pols[Q.pol];
         float f[MLP_IN];
 #pragma unroll
         for (int k = 0; k < MLP_IN; ++k) f[k] = 0.0f;
+        double base = 0.0, delta = 0.0;
+        if (Q.state >= 0) base = sur_ln_base(P, T, Q, &delta);
         f[P.product] = 1.0f;
         f[4 + max(0, Q.state)] = 1.0f;
         const bool jl = P.product == RSV_JL_REVERSIONARY;
@@ -145,24 +248,27 @@ __global__ void sur_features_kernel(const PolSur* __restrict__ pols, const SurQu
         f[13] = age1 * age1;
         f[14] = rem * rem;
         f[15] = rr * rem;
-        __nv_bfloat16* row = X + i * MLP_IN;
-#pragma unroll
-        for (int k = 0; k < MLP_IN; k += 2)
-            *reinterpret_cast<__nv_bfloat162*>(row + k) = __floats2bfloat162_rn(f[k], f[k + 1]);
+        f[16] = (float)(log1p((double)(P.S - Q.m)) / 7.0);
+        f[17] = (float)(base / 4.0);
+        f[18] = (float)((delta - 0.04) / 0.02);
+        sur_store_features(f, X + i * MLP_XW);
+        lnb[i] = base;
     }
 }
 
-__global__ void sur_to_reserve_kernel(const float* __restrict__ yhat, long long n, double mu, double sd,
-                                      double* __restrict__ V) {
+// reserve per unit = exp(network output, denormalised, + ln base value)
+__global__ void sur_to_reserve_kernel(const float* __restrict__ yhat, const double* __restrict__ lnb, long long n,
+                                      double mu, double sd, double* __restrict__ V) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        V[i] = exp((double)yhat[i] * sd + mu);
+        V[i] = exp((double)yhat[i] * sd + mu + lnb[i]);
 }
 
 namespace {
 
-__global__ void targets_kernel(const double* __restrict__ V, long long n, double mu, double sd, float* __restrict__ y) {
+__global__ void targets_kernel(const double* __restrict__ V, const double* __restrict__ lnb, long long n, double mu,
+                               double sd, float* __restrict__ y) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        y[i] = (float)((log(V[i]) - mu) / sd);
+        y[i] = (float)((log(V[i]) - lnb[i] - mu) / sd);
 }
 
 __global__ void gather_kernel(const __nv_bfloat16* __restrict__ X, const float* __restrict__ y, long long n,
@@ -173,10 +279,10 @@ __global__ void gather_kernel(const __nv_bfloat16* __restrict__ X, const float* 
     uint32_t w[4];
     philox4x32_10((uint32_t)i, step, 0u, 5u << 24, (uint32_t)seed, (uint32_t)(seed >> 32), w);
     const long long j = (long long)((((uint64_t)w[0] << 32) | w[1]) % (uint64_t)n);
-    const uint4* src = reinterpret_cast<const uint4*>(X + j * MLP_IN);
-    uint4* dst = reinterpret_cast<uint4*>(Xb + (size_t)i * MLP_IN);
+    const uint4* src = reinterpret_cast<const uint4*>(X + j * MLP_XW);
+    uint4* dst = reinterpret_cast<uint4*>(Xb + (size_t)i * MLP_XW);
 #pragma unroll
-    for (int k = 0; k < MLP_IN * 2 / 16; ++k) dst[k] = src[k];
+    for (int k = 0; k < MLP_XW * 2 / 16; ++k) dst[k] = src[k];
     yb[i] = y[j];
 }
 
@@ -187,12 +293,13 @@ __global__ void rel_err_kernel(const double* __restrict__ pred, const double* __
         err[i] = V[i] > 0.0 ? pred[i] / V[i] - 1.0 : 0.0;
 }
 
-// ln-moments of the labels (FP64, fixed order per block, then on the host)
-__global__ void log_moments_kernel(const double* __restrict__ V, long long n, double* __restrict__ part) {
+// moments of ln(label / base value) (FP64, fixed order per block, then on the host)
+__global__ void log_moments_kernel(const double* __restrict__ V, const double* __restrict__ lnb, long long n,
+                                   double* __restrict__ part) {
     __shared__ double s1[256], s2[256];
     double a = 0.0, b2 = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double l = log(V[i]);
+        const double l = log(V[i]) - lnb[i];
         a += l;
         b2 += l * l;
     }
@@ -215,6 +322,43 @@ __global__ void log_moments_kernel(const double* __restrict__ V, long long n, do
 }  // namespace
 
 // ------------------------------------------------------------------ host ----
+// The F64 decrement table, the forward-curve increments of the surrogate's
+// Vasicek model and the commutation columns, rebuilt when their inputs change.
+rsv_status sur_tables(rsv_ctx* c, SurTables& T) {
+    SurrogateState& s = c->sur;
+    size_t smem;
+    rsv_status st = build_tables(c, F_F64, smem);
+    if (st != RSV_OK) return st;
+    const int pad = c->tab_pad_of[F_F64], n_tab = c->n_tab_of[F_F64];
+    if (s.curve_key[0] != s.a || s.curve_key[1] != s.b || s.curve_key[2] != s.sigma) {
+        CU(s.d_curve.ensure((size_t)(kMaxAgeSteps + 1) * sizeof(double2)));
+        sur_curve_kernel<<<(kMaxAgeSteps + 1 + 127) / 128, 128, 0, c->stream>>>(s.a, s.b, s.sigma, kMaxAgeSteps + 1,
+                                                                               s.d_curve.as<double2>());
+        CU(cudaGetLastError());
+        s.curve_key[0] = s.a;
+        s.curve_key[1] = s.b;
+        s.curve_key[2] = s.sigma;
+    }
+    if (s.comm_pad != pad || s.comm_ntab != n_tab || s.comm_gen != c->tab_gen) {
+        const int jobs = n_tab * SUR_COMM_N;
+        CU(s.d_comm.ensure((size_t)jobs * 3 * sur_comm_len(pad) * sizeof(double)));
+        sur_comm_kernel<<<(jobs + 63) / 64, 64, 0, c->stream>>>(c->d_tab[F_F64].as<double2>(), pad, n_tab,
+                                                               s.d_comm.as<double>());
+        CU(cudaGetLastError());
+        s.comm_pad = pad;
+        s.comm_ntab = n_tab;
+        s.comm_gen = c->tab_gen;
+    }
+    T.tab = c->d_tab[F_F64].as<double2>();
+    T.tab_pad = pad;
+    T.curve = s.d_curve.as<double2>();
+    T.comm = s.d_comm.as<double>();
+    T.a = s.a;
+    T.b = s.b;
+    T.sigma = s.sigma;
+    return RSV_OK;
+}
+
 rsv_status sur_upload_policies(rsv_ctx* c, std::vector<PolSur>& host) {
     host.resize(c->pols.size());
     for (size_t i = 0; i < host.size(); ++i) {
@@ -252,24 +396,32 @@ rsv_status sur_upload_policies(rsv_ctx* c, std::vector<PolSur>& host) {
 // `fallback`, queries in flagged buckets are then valued by the recurrence.
 rsv_status sur_predict(rsv_ctx* c, const SurQuery* q, long long n, double* V, bool fallback, int batch) {
     SurrogateState& s = c->sur;
+    SurTables T;
+    rsv_status st = sur_tables(c, T);
+    if (st != RSV_OK) return st;
     CU(c->mlp.ensure(batch));
+    batch = batch / 128 * 128;
+    CU(s.d_lnb.ensure((size_t)batch * sizeof(double)));
     for (long long o = 0; o < n; o += batch) {
         const int nb = (int)std::min<long long>(batch, n - o);
-        const int nb_pad = (nb + 63) / 64 * 64;
-        if (nb_pad != nb) CU(cudaMemsetAsync(c->mlp.X, 0, (size_t)nb_pad * MLP_IN * 2, c->stream));
-        sur_features_kernel<<<c->sm_count * 4, 256, 0, c->stream>>>(c->d_pols.as<PolSur>(), q + o, nb, c->mlp.X);
+        const int nb_pad = (nb + 127) / 128 * 128;
+        if (nb_pad != nb) CU(cudaMemsetAsync(c->mlp.X, 0, (size_t)nb_pad * MLP_XW * 2, c->stream));
+        sur_features_kernel<<<c->sm_count * 4, 256, 0, c->stream>>>(c->d_pols.as<PolSur>(), T, q + o, nb, c->mlp.X,
+                                                                    s.d_lnb.as<double>());
         CU(cudaGetLastError());
-        CU(c->mlp.forward(c->mlp.X, nb_pad, c->mlp.y, nullptr, c->stream));
-        sur_to_reserve_kernel<<<c->sm_count * 4, 256, 0, c->stream>>>(c->mlp.y, nb, s.y_mean, s.y_std, V + o);
+        if (c->mlp.use_tc) {
+            CU(c->d_ctl.ensure(2 * sizeof(int32_t)));
+            CU(c->mlp.forward_tc(c->mlp.X, nb_pad, c->mlp.y, c->sm_count, c->d_ctl.as<int32_t>() + 1, c->stream));
+        } else {
+            CU(c->mlp.forward(c->mlp.X, nb_pad, c->mlp.y, nullptr, c->stream));
+        }
+        sur_to_reserve_kernel<<<c->sm_count * 4, 256, 0, c->stream>>>(c->mlp.y, s.d_lnb.as<double>(), nb, s.y_mean,
+                                                                      s.y_std, V + o);
         CU(cudaGetLastError());
     }
     if (fallback) {
-        size_t smem;
-        rsv_status st = build_tables(c, F_F64, smem);
-        if (st != RSV_OK) return st;
-        sur_label_kernel<<<c->sm_count * 8, 128, 0, c->stream>>>(
-            c->d_pols.as<PolSur>(), c->d_tab[F_F64].as<double2>(), c->tab_pad_of[F_F64], q, n, s.a, s.b, s.sigma,
-            s.d_flag.as<unsigned char>(), V);
+        sur_label_kernel<<<c->sm_count * 8, 128, 0, c->stream>>>(c->d_pols.as<PolSur>(), T, q, n,
+                                                                 s.d_flag.as<unsigned char>(), V);
         CU(cudaGetLastError());
     }
     return RSV_OK;
@@ -314,9 +466,14 @@ rsv_status mlp_upload(rsv_ctx* c, const float* host) {
     return RSV_OK;
 }
 
-__global__ void f32_to_bf16_rows(const float* __restrict__ x, long long n, __nv_bfloat16* __restrict__ y) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        y[i] = __float2bfloat16_rn(x[i]);
+// FP32 feature rows [n][MLP_IN] -> hi + lo BF16 rows [n][MLP_XW]
+__global__ void f32_to_bf16_rows(const float* __restrict__ x, long long rows, __nv_bfloat16* __restrict__ y) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
+        float f[MLP_IN];
+#pragma unroll
+        for (int k = 0; k < MLP_IN; ++k) f[k] = x[r * MLP_IN + k];
+        sur_store_features(f, y + r * MLP_XW);
+    }
 }
 
 rsv_status mlp_stage_inputs(rsv_ctx* c, const float* X, long long n, long long n_pad) {
@@ -324,13 +481,14 @@ rsv_status mlp_stage_inputs(rsv_ctx* c, const float* X, long long n, long long n
     CU(c->sur.d_aux.ensure((size_t)n_pad * MLP_IN * 4));
     CU(cudaMemsetAsync(c->sur.d_aux.p, 0, (size_t)n_pad * MLP_IN * 4, c->stream));
     CU(cudaMemcpyAsync(c->sur.d_aux.p, X, (size_t)n * MLP_IN * 4, cudaMemcpyHostToDevice, c->stream));
-    f32_to_bf16_rows<<<c->sm_count * 4, 256, 0, c->stream>>>(c->sur.d_aux.as<float>(), n_pad * MLP_IN, c->mlp.X);
+    f32_to_bf16_rows<<<c->sm_count * 4, 256, 0, c->stream>>>(c->sur.d_aux.as<float>(), n_pad, c->mlp.X);
     CU(cudaGetLastError());
     return RSV_OK;
 }
 
 __global__ void query_prep_kernel(const PolSur* __restrict__ pols, int n_pol, const rsv_query* __restrict__ in,
-                                  long long n, SurQuery* __restrict__ out, int* __restrict__ bad) {
+                                  long long n, SurQuery* __restrict__ out, int* __restrict__ bad,
+                                  const unsigned char* __restrict__ flag, unsigned long long* __restrict__ n_flag) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const rsv_query r = in[i];
         SurQuery Q;
@@ -348,6 +506,7 @@ __global__ void query_prep_kernel(const PolSur* __restrict__ pols, int n_pol, co
             Q.state = -1;
         } else {
             Q.bucket = sur_bucket(pols[r.pol], r.m, r.state, r.r);
+            if (flag && flag[Q.bucket]) atomicAdd(n_flag, 1ull);
         }
         out[i] = Q;
     }
@@ -360,6 +519,37 @@ __global__ void scale_by_amount_kernel(const PolSur* __restrict__ pols, const Su
 }
 
 }  // namespace
+
+// Per-unit expected reserves (device, n values) of host-built queries by the
+// network with fallback; *n_fallback receives the number valued by the
+// recurrence.  Used by the nested valuation's surrogate mode.
+rsv_status sur_value_queries(rsv_ctx* c, const rsv_query* hq, long long n, double* V, long long* n_fallback) {
+    SurrogateState& s = c->sur;
+    if (c->pols_dev_gen != c->pol_gen) {
+        std::vector<PolSur> hp;
+        rsv_status st = sur_upload_policies(c, hp);
+        if (st != RSV_OK) return st;
+    }
+    CU(s.d_aux.ensure((size_t)n * sizeof(rsv_query) + 16));
+    CU(s.d_q.ensure((size_t)n * sizeof(SurQuery)));
+    CU(s.d_err.ensure(16));
+    CU(cudaMemsetAsync(s.d_err.p, 0, 16, c->stream));
+    CU(cudaMemcpyAsync(s.d_aux.p, hq, (size_t)n * sizeof(rsv_query), cudaMemcpyHostToDevice, c->stream));
+    SurQuery* q = s.d_q.as<SurQuery>();
+    query_prep_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(
+        c->d_pols.as<PolSur>(), (int)c->pols.size(), s.d_aux.as<rsv_query>(), n, q, s.d_err.as<int>(),
+        s.d_flag.as<unsigned char>(), reinterpret_cast<unsigned long long*>(s.d_err.as<char>() + 8));
+    CU(cudaGetLastError());
+    rsv_status st = sur_predict(c, q, n, V, true, 65536);
+    if (st != RSV_OK) return st;
+    long long cnt[2] = {0, 0};
+    CU(cudaMemcpyAsync(cnt, s.d_err.p, 16, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if ((int)cnt[0]) return fail(c, RSV_E_ARG, "a nested surrogate query is invalid");
+    if (n_fallback) *n_fallback = cnt[1];
+    return RSV_OK;
+}
+
 }  // namespace rsv
 
 using namespace rsv;
@@ -391,13 +581,15 @@ rsv_status rsv_surrogate_query(rsv_ctx* c, const rsv_query* queries, int64_t n, 
     SurQuery* q = s.d_q.as<SurQuery>();
     const int grid = c->sm_count * 8;
     query_prep_kernel<<<grid, 256, 0, c->stream>>>(c->d_pols.as<PolSur>(), (int)c->pols.size(),
-                                                   s.d_aux.as<rsv_query>(), n, q, s.d_err.as<int>());
+                                                   s.d_aux.as<rsv_query>(), n, q, s.d_err.as<int>(), nullptr,
+                                                   nullptr);
     CU(cudaGetLastError());
     double* V = s.d_pred.as<double>();
     CU(cudaEventRecord(c->ev0, c->stream));
     if (how == RSV_QUERY_RECURRENCE) {
-        sur_label_kernel<<<grid, 128, 0, c->stream>>>(c->d_pols.as<PolSur>(), c->d_tab[F_F64].as<double2>(),
-                                                      c->tab_pad_of[F_F64], q, n, s.a, s.b, s.sigma, nullptr, V);
+        SurTables T;
+        if ((st = sur_tables(c, T)) != RSV_OK) return st;
+        sur_label_kernel<<<grid, 128, 0, c->stream>>>(c->d_pols.as<PolSur>(), T, q, n, nullptr, V);
         CU(cudaGetLastError());
     } else if ((st = sur_predict(c, q, n, V, how == RSV_QUERY_FALLBACK, 65536)) != RSV_OK) {
         return st;
@@ -442,15 +634,28 @@ rsv_status rsv_mlp_get_params(rsv_ctx* c, float* params, int64_t n) {
     return RSV_OK;
 }
 
+rsv_status rsv_mlp_set_backend(rsv_ctx* c, int32_t backend) {
+    if (!c) return RSV_E_ARG;
+    if (backend != RSV_MLP_MMA_SYNC && backend != RSV_MLP_TCGEN05) return fail(c, RSV_E_ARG, "bad backend");
+    c->mlp.use_tc = backend == RSV_MLP_TCGEN05;
+    return RSV_OK;
+}
+
 rsv_status rsv_mlp_forward(rsv_ctx* c, const float* X, int64_t n, float* y) {
     if (!c) return RSV_E_ARG;
     if (!X || !y || n < 1 || n > (1 << 20)) return fail(c, RSV_E_ARG, "bad forward arguments");
     if (!c->mlp_ready) return fail(c, RSV_E_STATE, "network not initialised");
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice failed");
-    const long long n_pad = (n + 63) / 64 * 64;
+    const long long n_pad = (n + 127) / 128 * 128;
     rsv_status st = mlp_stage_inputs(c, X, n, n_pad);
     if (st != RSV_OK) return st;
-    CU(c->mlp.forward(c->mlp.X, (int)n_pad, c->mlp.y, nullptr, c->stream));
+    if (c->mlp.use_tc) {
+        CU(c->d_ctl.ensure(2 * sizeof(int32_t)));
+        CU(cudaMemsetAsync(c->d_ctl.p, 0, 2 * sizeof(int32_t), c->stream));
+        CU(c->mlp.forward_tc(c->mlp.X, (int)n_pad, c->mlp.y, c->sm_count, c->d_ctl.as<int32_t>() + 1, c->stream));
+    } else {
+        CU(c->mlp.forward(c->mlp.X, (int)n_pad, c->mlp.y, nullptr, c->stream));
+    }
     CU(cudaMemcpyAsync(y, c->mlp.y, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     return RSV_OK;
@@ -500,7 +705,7 @@ rsv_status rsv_surrogate_train(rsv_ctx* c, const rsv_surrogate_cfg* cfg, rsv_sur
     CU(s.d_q.ensure((size_t)n * sizeof(SurQuery)));
     CU(s.d_lab.ensure((size_t)n * 8));
     CU(s.d_y.ensure((size_t)n * 4));
-    CU(s.d_X.ensure((size_t)n * MLP_IN * 2));
+    CU(s.d_X.ensure((size_t)n * MLP_XW * 2));
     CU(s.d_err.ensure((size_t)nv * 8));
     SurQuery* q = s.d_q.as<SurQuery>();
     cudaEvent_t e0, e1, e2, e3;
@@ -518,17 +723,21 @@ rsv_status rsv_surrogate_train(rsv_ctx* c, const rsv_surrogate_cfg* cfg, rsv_sur
                                                        cfg->a, cfg->b, cfg->sigma, cfg->r0, cfg->widen,
                                                        cfg->max_node_m, q + nt);
     CU(cudaGetLastError());
+    SurTables T;
+    if ((st = sur_tables(c, T)) != RSV_OK) return st;
+    CU(s.d_lnb.ensure((size_t)n * sizeof(double)));
     CU(cudaEventRecord(e0, c->stream));
-    sur_label_kernel<<<grid, 128, 0, c->stream>>>(c->d_pols.as<PolSur>(), c->d_tab[F_F64].as<double2>(),
-                                                  c->tab_pad_of[F_F64], q, n, cfg->a, cfg->b, cfg->sigma, nullptr,
-                                                  s.d_lab.as<double>());
+    sur_label_kernel<<<grid, 128, 0, c->stream>>>(c->d_pols.as<PolSur>(), T, q, n, nullptr, s.d_lab.as<double>());
     CU(cudaGetLastError());
     CU(cudaEventRecord(e1, c->stream));
+    sur_features_kernel<<<grid, 256, 0, c->stream>>>(c->d_pols.as<PolSur>(), T, q, n, s.d_X.as<__nv_bfloat16>(),
+                                                     s.d_lnb.as<double>());
+    CU(cudaGetLastError());
     // target normalisation from the training labels
     const int mb = 256;
     DevBuf part;
     CU(part.ensure(mb * 2 * 8));
-    log_moments_kernel<<<mb, 256, 0, c->stream>>>(s.d_lab.as<double>(), nt, part.as<double>());
+    log_moments_kernel<<<mb, 256, 0, c->stream>>>(s.d_lab.as<double>(), s.d_lnb.as<double>(), nt, part.as<double>());
     std::vector<double> hpart(mb * 2);
     CU(cudaMemcpyAsync(hpart.data(), part.p, mb * 2 * 8, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
@@ -541,8 +750,8 @@ rsv_status rsv_surrogate_train(rsv_ctx* c, const rsv_surrogate_cfg* cfg, rsv_sur
     s.y_mean = s1 / nt;
     s.y_std = std::sqrt(std::max(s2 / nt - s.y_mean * s.y_mean, 1e-12));
     if (!std::isfinite(s.y_mean)) return fail(c, RSV_E_ASSUMPTION, "a training label is not positive");
-    targets_kernel<<<grid, 256, 0, c->stream>>>(s.d_lab.as<double>(), n, s.y_mean, s.y_std, s.d_y.as<float>());
-    sur_features_kernel<<<grid, 256, 0, c->stream>>>(c->d_pols.as<PolSur>(), q, n, s.d_X.as<__nv_bfloat16>());
+    targets_kernel<<<grid, 256, 0, c->stream>>>(s.d_lab.as<double>(), s.d_lnb.as<double>(), n, s.y_mean, s.y_std,
+                                                s.d_y.as<float>());
     CU(cudaGetLastError());
 
     // training: Adam on random batches, cosine learning rate

@@ -19,11 +19,23 @@ struct SurQuery {  // a policy in a reduced state at a node month with a short r
     double r;
 };
 
-__global__ void sur_label_kernel(const PolSur* pols, const double2* tab, int tab_pad, const SurQuery* qs, long long n,
-                                 double a, double b, double sigma, const unsigned char* flag, double* V);
-__global__ void sur_features_kernel(const PolSur* pols, const SurQuery* qs, long long n, __nv_bfloat16* X);
+// Tables the surrogate's kernels share (device pointers).
+struct SurTables {
+    const double2* tab;    // F64 decrement table entries (p, q), tab_pad per table
+    int tab_pad;
+    const double2* curve;  // per month t: (dA_t, dB_t), ln P((t+1)/12 | r) - ln P(t/12 | r) = dA_t - dB_t r
+    const double* comm;    // commutation columns D, N, M per (table, grid rate), sur_comm_len(tab_pad) entries each
+    double a, b, sigma;    // the Vasicek model
+};
 
-__global__ void sur_to_reserve_kernel(const float* __restrict__ yhat, long long n, double mu, double sd,
-                                      double* __restrict__ V);
+// Flat reference rates of the commutation columns (continuous, per year).
+constexpr double SUR_COMM_LO = -0.10, SUR_COMM_STEP = 0.0025;
+constexpr int SUR_COMM_N = 141;
+__host__ __device__ constexpr int sur_comm_len(int tab_pad) { return tab_pad + 2; }
 
+}  // namespace rsv
+
+#include "rsv.h"
+namespace rsv {
+rsv_status sur_value_queries(rsv_ctx* c, const rsv_query* hq, long long n, double* V, long long* n_fallback);
 }  // namespace rsv

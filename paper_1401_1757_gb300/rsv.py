@@ -47,7 +47,7 @@ class rsv_out(C.Structure):
                 ("pt_mean", C.c_void_p), ("traj", C.c_void_p)]
 
 
-RSV_NESTED_MC, RSV_NESTED_CURVE = 0, 2
+RSV_NESTED_MC, RSV_NESTED_SURROGATE, RSV_NESTED_CURVE = 0, 1, 2
 
 
 class rsv_nested_spec(C.Structure):
@@ -58,7 +58,7 @@ class rsv_nested_spec(C.Structure):
 
 class rsv_nested_out(C.Structure):
     _fields_ = [("L_mean", C.c_void_p), ("L_q995", C.c_void_p), ("r_node", C.c_void_p), ("D0", C.c_void_p),
-                ("L_all", C.c_void_p)]
+                ("L_all", C.c_void_p), ("n_fallback", C.c_void_p)]
 
 
 class rsv_surrogate_cfg(C.Structure):
@@ -93,7 +93,7 @@ EXPORTS = ["rsv_create", "rsv_destroy", "rsv_set_stream", "rsv_load_decrements",
            "rsv_load_scenarios", "rsv_compute_reserves", "rsv_compute_nested", "rsv_variant_count", "rsv_variant_name",
            "rsv_tune", "rsv_synchronize", "rsv_last_error", "rsv_last_kernel_ms", "rsv_device_sm_count",
            "rsv_reserves_noalloc", "rsv_mlp_param_count", "rsv_mlp_init", "rsv_mlp_set_params",
-           "rsv_mlp_get_params", "rsv_mlp_forward", "rsv_mlp_gradient", "rsv_surrogate_train", "rsv_surrogate_query"]
+           "rsv_mlp_get_params", "rsv_mlp_set_backend", "rsv_mlp_forward", "rsv_mlp_gradient", "rsv_surrogate_train", "rsv_surrogate_query"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -133,6 +133,7 @@ def load_library(path: str = LIB_PATH):
         "rsv_mlp_set_params": ([vp, vp, i64], i32),
         "rsv_mlp_get_params": ([vp, vp, i64], i32),
         "rsv_mlp_forward": ([vp, vp, i64, vp], i32),
+        "rsv_mlp_set_backend": ([vp, i32], i32),
         "rsv_mlp_gradient": ([vp, vp, vp, i64, vp, vp], i32),
         "rsv_surrogate_train": ([vp, C.POINTER(rsv_surrogate_cfg), C.POINTER(rsv_surrogate_report)], i32),
         "rsv_surrogate_query": ([vp, vp, i64, i32, vp], i32),
@@ -229,12 +230,12 @@ def rsv_compute_reserves(ctx, form: int = RSV_FORM_F32_COMP, outputs: int = RSV_
 def rsv_compute_nested(ctx, form: int = RSV_FORM_F32_COMP, *, n_outer: int, n_nodes: int, node_step_m: int = 12,
                        n_inner: int = 1000, seed: int = 0, a: float = 0.1, b: float = 0.04, sigma: float = 0.01,
                        r0: float = 0.03, mode: int = RSV_NESTED_MC, batch_outer: int = 0, on_device: bool = False,
-                       L_mean=None, L_q995=None, r_node=None, D0=None, L_all=None):
+                       L_mean=None, L_q995=None, r_node=None, D0=None, L_all=None, n_fallback=None):
     """Nested valuation (see include/rsv.h).  Output buffers are caller-sized
     ([n_outer, n_nodes] and [n_outer, n_nodes, n_inner])."""
     o = rsv_opts(form, 0, 0, 1 if on_device else 0, -1)
     sp = rsv_nested_spec(n_outer, n_nodes, node_step_m, n_inner, seed, a, b, sigma, r0, mode, batch_outer)
-    out = rsv_nested_out(_ptr(L_mean), _ptr(L_q995), _ptr(r_node), _ptr(D0), _ptr(L_all))
+    out = rsv_nested_out(_ptr(L_mean), _ptr(L_q995), _ptr(r_node), _ptr(D0), _ptr(L_all), _ptr(n_fallback))
     _check(ctx, _lib.rsv_compute_nested(ctx, C.byref(o), C.byref(sp), C.byref(out)))
 
 
@@ -306,6 +307,13 @@ def rsv_mlp_get_params(ctx):
     p = np.zeros(rsv_mlp_param_count(), np.float32)
     _check(ctx, _lib.rsv_mlp_get_params(ctx, p.ctypes.data, p.size))
     return p
+
+
+RSV_MLP_MMA_SYNC, RSV_MLP_TCGEN05 = 0, 1
+
+
+def rsv_mlp_set_backend(ctx, backend: int):
+    _check(ctx, _lib.rsv_mlp_set_backend(ctx, backend))
 
 
 def rsv_mlp_forward(ctx, X):

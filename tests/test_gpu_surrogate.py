@@ -61,6 +61,26 @@ def test_mlp_forward_matches_reference(ctx):
     assert np.linalg.norm(y - y_64) <= 3e-2 * np.linalg.norm(y_64)
 
 
+def test_tcgen05_inference_matches_mma_sync_and_reference(ctx):
+    """The fused tcgen05 inference kernel (TMEM accumulators, TMA-staged
+    swizzled operands) computes the same network as the per-layer mma.sync
+    kernels: same BF16 operands, FP32 accumulation in another order."""
+    p = random_params(11)
+    rng = np.random.default_rng(12)
+    X = rng.normal(0, 1, (1000, 32)).astype(np.float32)     # 8 tiles of 128, the last one ragged
+    rsv.rsv_mlp_set_params(ctx, p)
+    rsv.rsv_mlp_set_backend(ctx, rsv.RSV_MLP_MMA_SYNC)
+    y_mma = rsv.rsv_mlp_forward(ctx, X).astype(np.float64)
+    rsv.rsv_mlp_set_backend(ctx, rsv.RSV_MLP_TCGEN05)
+    y_tc = rsv.rsv_mlp_forward(ctx, X).astype(np.float64)
+    y_bf, _, _ = ref.forward(p, X.astype(np.float64), bf16_storage=True)
+    scale = np.max(np.abs(y_bf))
+    print("tcgen05 vs mma.sync", np.max(np.abs(y_tc - y_mma)) / scale, "vs reference",
+          np.max(np.abs(y_tc - y_bf)) / scale)
+    assert np.max(np.abs(y_tc - y_bf)) <= 2e-3 * scale
+    assert np.max(np.abs(y_tc - y_mma)) <= 2e-3 * scale
+
+
 def test_mlp_gradient_matches_reference(ctx):
     p = random_params(3)
     rng = np.random.default_rng(4)
