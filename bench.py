@@ -44,10 +44,15 @@ N_POL_MIX = 100_000
 WORKLOAD = ("100,000-policy mix (40% SL annuities, 20% JL reversionary 3-state, 20% term 5-40y, "
             "20% endowments 10-30y, ages 20-85) x 1,000 Vasicek scenarios x 1,200 monthly steps")
 
-# FP32 operations per chain-step of each form (add/sub/mul/min/max = 1, FMA = 2),
-# counted from the formulas the kernels evaluate.
+# FP32 (FP64 for f64) operations per chain-step of each form and product
+# (add/sub/mul/min/max = 1, FMA = 2), counted from the formulas the kernels
+# evaluate: plain annuity v*p then an FMA; compensated annuity a double-float
+# product (7) and the shifted update 1 + g R (9); compensated assurance two
+# double-float products and an ordered sum (20); compensated JL three
+# products, two shifted updates, 1 + r00, the FP32 death terms and an ordered
+# sum (66).
 FLOPS = {"f32": {0: 3, 1: 13, 2: 3, 3: 3},
-         "f32comp": {0: 20, 1: 71, 2: 20, 3: 20},
+         "f32comp": {0: 16, 1: 66, 2: 20, 3: 20},
          "f64": {0: 3, 1: 13, 2: 3, 3: 3}}
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = 2 * FP32_LANES * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 at 2070 MHz
@@ -179,11 +184,13 @@ NESTED_WORKLOAD = ("nested brute force: 2,000 single-life annuities (ages 60-90)
                    "40 annual nodes x 1,000 inner paths, compensated FP32")
 
 
-def bench_nested(rsv, torch, tab, steps, warmup):
+def bench_nested(rsv, torch, tab, steps, warmup, n_outer=None, sur_epochs=10, sur_train=3_000_000):
     """The nested valuation: live (policy, outer path, node, inner path) valuations per
     second, device time of the whole pipeline (outer paths, inner-path generation,
     recurrence, node statistics), plus the closed-form inner expectation."""
-    cfg = NESTED
+    cfg = dict(NESTED)
+    if n_outer:
+        cfg["n_outer"] = n_outer
     pol = synth.portfolio_single_life(cfg["n_pol"], seed=0)
     S = policy_steps(pol)
     live = chain_steps = 0
@@ -200,20 +207,49 @@ def bench_nested(rsv, torch, tab, steps, warmup):
     q = torch.empty((NO, NN), dtype=torch.float64, device="cuda")
     spec = dict(n_outer=NO, n_nodes=NN, node_step_m=cfg["node_step"], seed=0, on_device=True, L_mean=mean, L_q995=q)
     res = {}
-    for mode, name, ni in [(rsv.RSV_NESTED_MC, "brute_force", NI), (rsv.RSV_NESTED_CURVE, "curve", 1)]:
+    modes = [(rsv.RSV_NESTED_MC, "brute_force", NI), (rsv.RSV_NESTED_CURVE, "curve", 1)]
+    if sur_epochs > 0:
+        # the surrogate, trained on this portfolio's own recurrence labels up to the last node
+        t0 = time.perf_counter()
+        rsv.rsv_mlp_init(ctx, 0)
+        rep = rsv.rsv_surrogate_train(ctx, n_train=sur_train, n_val=max(200_000, sur_train // 10), epochs=sur_epochs,
+                                      batch=8192, lr=2e-3, seed=0, max_node_m=(NN - 1) * cfg["node_step"])
+        res["surrogate_training"] = {"labels": sur_train, "epochs": sur_epochs, "wall_s": time.perf_counter() - t0,
+                                     "held_out_median_rel": rep["val_median_rel"],
+                                     "served_max_rel": rep["combined_max_rel"],
+                                     "fallback_share": rep["frac_fallback"]}
+        modes.append((rsv.RSV_NESTED_SURROGATE, "surrogate", 1))
+    means = {}
+    for mode, name, ni in modes:
+        nfb = np.zeros(1, np.int64)
         for _ in range(warmup):
-            rsv.rsv_compute_nested(ctx, rsv.RSV_FORM_F32_COMP, n_inner=NI, mode=mode, **spec)
+            rsv.rsv_compute_nested(ctx, rsv.RSV_FORM_F32_COMP, n_inner=NI, mode=mode, n_fallback=nfb, **spec)
         torch.cuda.synchronize()
-        ms = []
+        ms, walls = [], []
         for _ in range(steps):
-            rsv.rsv_compute_nested(ctx, rsv.RSV_FORM_F32_COMP, n_inner=NI, mode=mode, **spec)
+            w0 = time.perf_counter()
+            rsv.rsv_compute_nested(ctx, rsv.RSV_FORM_F32_COMP, n_inner=NI, mode=mode, n_fallback=nfb, **spec)
             ms.append(rsv.rsv_last_kernel_ms(ctx))
+            torch.cuda.synchronize()
+            walls.append(time.perf_counter() - w0)
         t = statistics.mean(ms) / 1e3
         vals = live * (cfg["n_outer"] * ni)
-        res[name] = {"valuations_s": vals / t, "ms": t * 1e3, "valuations": vals,
-                     "chain_steps_s": chain_steps * cfg["n_outer"] * ni / t}
+        res[name] = {"valuations_s": vals / t, "ms": t * 1e3, "wall_ms": statistics.mean(walls) * 1e3,
+                     "valuations": vals, "chain_steps_s": chain_steps * cfg["n_outer"] * ni / t}
+        if mode == rsv.RSV_NESTED_SURROGATE:
+            res[name]["fallback_queries"] = int(nfb[0])
+            res[name]["note"] = ("valuations = (policy, outer path, node) expectations, each replacing n_inner "
+                                 "inner-path valuations; ms is the device time of the whole call")
+        means[name] = mean.cpu().numpy().copy()
+    if "surrogate" in means:
+        exact = means["curve"]
+        live_m = exact > 0
+        res["node_liability_max_rel_vs_exact"] = {
+            k: float(np.max(np.abs(means[k] - exact)[live_m] / exact[live_m])) for k in ("brute_force", "surrogate")}
+        res["surrogate_speedup_vs_brute_force"] = res["brute_force"]["ms"] / res["surrogate"]["ms"]
     rsv.rsv_destroy(ctx)
-    res["workload"] = NESTED_WORKLOAD
+    res["workload"] = NESTED_WORKLOAD if cfg["n_outer"] == NESTED["n_outer"] else \
+        f"profiling case: {NESTED_WORKLOAD.replace('100 outer', str(cfg['n_outer']) + ' outer')}"
     res["live_valuations"] = live * scale
     res["chain_steps"] = chain_steps * scale
     res["paper_brute_force_estimate"] = ("the paper's cost model (Section 5.3.2) for its 500k portfolio is "
@@ -238,9 +274,10 @@ def bench_surrogate(rsv, torch, tab, epochs, lr=2e-3, n_train=10_000_000, n_val=
     rsv.rsv_destroy(ctx)
     flops_q = 2 * (32 * 256 + 3 * 256 * 256 + 256)
     return {
-        "workload": SURROGATE_WORKLOAD, "epochs": epochs, "lr": lr,
+        "workload": SURROGATE_WORKLOAD if (n_train, n_val) == (10_000_000, 1_000_000) else
+        f"profiling case: {n_train} labels, {n_val} held-out queries", "epochs": epochs, "lr": lr,
         "held_out": {k: rep[k] for k in ("val_max_rel", "val_p99_rel", "val_median_rel", "val_rms_rel")},
-        "tol": 1e-3, "frac_fallback": rep["frac_fallback"], "combined_max_rel": rep["combined_max_rel"],
+        "tol": 1e-3, "margin": 0.3, "frac_fallback": rep["frac_fallback"], "combined_max_rel": rep["combined_max_rel"],
         "buckets_flagged": f"{rep['n_flagged']} of {rep['n_buckets']}",
         "residual_target_sd": rep["y_std"],
         "network_queries_s": rep["n_infer"] / (rep["infer_ms"] / 1e3),
@@ -289,6 +326,9 @@ def main():
     ap.add_argument("--no-nested", action="store_true")
     ap.add_argument("--surrogate-epochs", type=int, default=0, help="train and score the surrogate (0: skip)")
     ap.add_argument("--surrogate-lr", type=float, default=2e-3)
+    ap.add_argument("--surrogate-train", type=int, default=10_000_000, help="training labels (profiling runs: fewer)")
+    ap.add_argument("--surrogate-val", type=int, default=1_000_000, help="held-out queries")
+    ap.add_argument("--nested-outer", type=int, default=NESTED["n_outer"], help="outer paths (profiling runs: fewer)")
     args = ap.parse_args()
     if (args.policies, args.scenarios) != (N_POL, N_SCEN):
         N_POL, N_SCEN = args.policies, args.scenarios
@@ -418,10 +458,11 @@ def main():
     rsv.rsv_destroy(ctx)
     nested = None
     if not args.no_nested and rank == 0:
-        nested = bench_nested(rsv, torch, tab, steps=2, warmup=1)
+        nested = bench_nested(rsv, torch, tab, steps=2, warmup=1, n_outer=args.nested_outer)
     surrogate = None
     if args.surrogate_epochs > 0 and rank == 0:
-        surrogate = bench_surrogate(rsv, torch, tab, args.surrogate_epochs, lr=args.surrogate_lr)
+        surrogate = bench_surrogate(rsv, torch, tab, args.surrogate_epochs, lr=args.surrogate_lr,
+                                    n_train=args.surrogate_train, n_val=args.surrogate_val)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()

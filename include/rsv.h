@@ -326,7 +326,9 @@ typedef struct {
     double a, b, sigma, r0;  /* Vasicek model of the node rates and of the labels     */
     int32_t max_node_m;  /* nodes sampled at months 0, 12, ... up to this              */
     double widen;        /* node rates drawn from the model's distribution, sd x widen */
-    double tol;          /* relative error above which a bucket falls back          */
+    double tol;          /* relative error the network may serve                    */
+    double margin;       /* (0, 1]: a bucket is served only if its calibration
+                            maximum error is below margin x tol                    */
 } rsv_surrogate_cfg;
 
 typedef struct {
@@ -344,9 +346,11 @@ typedef struct {
  * end, a reduced state its lives can be in, a rate from the model at that
  * month), label them with the FP64 recurrence on the forward curve, train,
  * and score the held-out queries.  Buckets (product and state x age x
- * remaining term x rate) whose error on the first half of the held-out
- * queries exceeds tol, or that hold fewer than 16 of them, are flagged; the
- * second half measures the error of what the network then serves.  The
+ * remaining term x the node rate's z-score under the model) whose error on
+ * the first half of the held-out queries exceeds margin x tol, or that hold
+ * fewer than 32 of them, are flagged, as are rates beyond 4 standard
+ * deviations; the second half measures the error of what the network then
+ * serves.  The
  * network is (re)used as initialised if rsv_mlp_init / set_params was called.
  * Errors: RSV_E_ARG, RSV_E_STATE, RSV_E_CUDA, RSV_E_NOMEM. */
 rsv_status rsv_surrogate_train(rsv_ctx *ctx, const rsv_surrogate_cfg *cfg, rsv_surrogate_report *report);

@@ -56,7 +56,11 @@ struct Layout {            // cached tiling for one (P, horizon, data generation
 
 // The trained surrogate: target normalisation, the per-bucket fallback map
 // and its work buffers.
-constexpr int SUR_NB_PS = 6, SUR_NB_AGE = 10, SUR_NB_TERM = 8, SUR_NB_R = 8;
+// Fallback buckets: product and state x age of the life the state depends on
+// (10-year bins from 20) x remaining term (10-year bins) x the node rate's
+// z-score under the model at that month (half-sd bins on [-4, 4), then one
+// bin beyond 4 sd that is always valued by the recurrence).
+constexpr int SUR_NB_PS = 6, SUR_NB_AGE = 10, SUR_NB_TERM = 8, SUR_NB_R = 17;
 constexpr int SUR_NBUCKETS = SUR_NB_PS * SUR_NB_AGE * SUR_NB_TERM * SUR_NB_R;
 
 struct SurrogateState {

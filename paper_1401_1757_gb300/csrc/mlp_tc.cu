@@ -1,16 +1,18 @@
 // mlp_tc.cu -- surrogate inference on the 5th-generation tensor cores
 // (tcgen05.mma, accumulators in TMEM, operands staged by TMA).
 //
-// One CTA (4 warps) runs the whole network on 128-row tiles of queries:
+// One CTA (16 warps) runs the whole network on 128-row tiles of queries:
 //   for l = 1..4:  D = A_{l-1} . W_l  (tcgen05.mma m128 n256 k16, FP32 in TMEM)
 //                  A_l = gelu(D + b_l) (BF16, written back into shared memory as
 //                  the next layer's A operand)
 //   y = gelu(D_4 + b_4) . w5 + b5     (FP32 head from the TMEM accumulator)
 // A and W^T are K-major BF16 tiles in shared memory with the 128-byte swizzle
-// (TMA writes them; the epilogue writes A_l with the same pattern).  Warp w
-// owns TMEM lanes 32w..32w+31, i.e. rows 32w.. of the tile; thread 0 issues
-// the TMA copies and the MMAs.  Every mbarrier wait is bounded; on a timeout
-// the kernel records it in the status word, frees its TMEM and returns.
+// (TMA writes them; the epilogue writes A_l with the same pattern).  A warp
+// may only read its own quarter of the TMEM lanes, so warp w reads lanes
+// 32 (w % 4) .. +31 (rows of the tile) and columns 64 (w / 4) .. +63: four
+// warps per lane quarter share the epilogue.  Thread 0 issues the TMA copies
+// and the MMAs.  Every mbarrier wait is bounded; on a timeout the kernel
+// records it in the status word, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -32,6 +34,8 @@ constexpr int W_SLAB = TN * 128;                // 32 KiB
 constexpr int A_BYTES = 4 * A_SLAB;             // 64 KiB (K = 256)
 constexpr int W_BYTES = 4 * W_SLAB;             // 128 KiB
 constexpr uint32_t kPoll = 1u << 24;
+constexpr int kThreads = 512;                   // 16 warps: 4 lane quarters x 4 column groups
+constexpr int kColsPerWarp = TN / 4;            // 64
 
 struct TcArgs {
     const float* bias[4];
@@ -113,7 +117,7 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int k, int rows) {
 }
 
 // ---- the kernel -------------------------------------------------------------
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     mlp_fwd_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapW1,
                       const __grid_constant__ CUtensorMap mapW2, const __grid_constant__ CUtensorMap mapW3,
                       const __grid_constant__ CUtensorMap mapW4, const TcArgs a) {
@@ -124,6 +128,7 @@ __global__ void __launch_bounds__(128, 1)
     unsigned char* Wbuf = base + A_BYTES;
     __shared__ uint64_t bar_x, bar_w, bar_mma;
     __shared__ uint32_t tmem_slot;
+    __shared__ float head_part[4][TM];   // partial head sums per column group
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -178,13 +183,14 @@ __global__ void __launch_bounds__(128, 1)
                 mbar_arrive_expect_tx(&bar_w, 4 * W_SLAB);
                 for (int s = 0; s < 4; ++s) tma_load_2d(Wbuf + s * W_SLAB, maps[l + 1], s * SLAB_K, 0, &bar_w);
             }
-            // epilogue: row = 32 warp + lane, 256 accumulator columns in chunks of 32
-            const int row = warp * 32 + lane;
+            // epilogue: row = 32 (warp % 4) + lane, columns 64 (warp / 4) .. +63 in chunks of 32
+            const int quarter = warp & 3, cgrp = warp >> 2;
+            const int row = quarter * 32 + lane;
             const float* bias = a.bias[l];
             float ysum = 0.0f;
-            for (int c0 = 0; c0 < TN; c0 += 32) {
+            for (int c0 = cgrp * kColsPerWarp; c0 < (cgrp + 1) * kColsPerWarp; c0 += 32) {
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + c0, v);
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = gelu_f(v[i] + bias[c0 + i]);
                 if (l < 3) {
@@ -199,9 +205,12 @@ __global__ void __launch_bounds__(128, 1)
                     for (int i = 0; i < 32; ++i) ysum += v[i] * a.w5[c0 + i];
                 }
             }
-            if (l == 3) {
-                const int r = tile * TM + row;
-                a.y[r] = ysum + a.w5[TN];
+            if (l == 3) {   // uniform across the block
+                head_part[cgrp][row] = ysum;
+                __syncthreads();
+                if (cgrp == 0)
+                    a.y[tile * TM + row] =
+                        ((head_part[0][row] + head_part[1][row]) + (head_part[2][row] + head_part[3][row])) + a.w5[TN];
             }
             fence_before();
             fence_async_smem();   // A_l written by the generic proxy, read next by the tensor cores
@@ -299,7 +308,7 @@ cudaError_t Mlp::forward_tc(const __nv_bfloat16* Xin, int n, float* yout, int sm
         cudaSuccess)
         return e;
     const int grid = std::min(a.n_tiles, sm_count);
-    mlp_fwd_tc_kernel<<<grid, 128, smem, st>>>(mx, mw[0], mw[1], mw[2], mw[3], a);
+    mlp_fwd_tc_kernel<<<grid, kThreads, smem, st>>>(mx, mw[0], mw[1], mw[2], mw[3], a);
     return cudaGetLastError();
 }
 

@@ -109,22 +109,31 @@ __device__ __forceinline__ void step_jl(R v, R px, R qx, R py, R qy, R rho, R& V
 // their tails carry the accumulated compensation and grow to ~1e-5 of the
 // head over a thousand steps, so a computed value enters an FP32 term as
 // head + tail, not as its head alone.
-__device__ __forceinline__ df step_ann(df v, df p, df V) {
-    return df_mul(df_mul(v, p), df_add_one(V));
+//
+// Annuity-type states are carried shifted, R = 1 + r (boundary R_S = 1):
+// r_t = g_t (1 + r_{t+1}) becomes R_t = 1 + g_t R_{t+1}, one df_one_plus_mul.
+// The JL state 10 is carried as A = 1 + r10 / rho, which obeys the same
+// update with g = v py.
+__device__ __forceinline__ df step_ann(df v, df p, df R) {
+    return df_one_plus_mul(df_mul(v, p), R);
 }
 __device__ __forceinline__ df step_ass(df v, df p, df q, df V) {
     return df_mul(v, df_add_float_pos(df_mul(p, V), q.h));
 }
+// V00 = r00; V01 = R01 = 1 + r01; V10 = A10 = 1 + r10 / rho.
 __device__ __forceinline__ void step_jl(df v, df px, df qx, df py, df qy, df rho, df& V00, df& V01,
                                         df& V10) {
     df gx = df_mul(v, px), gy = df_mul(v, py);
-    df n01 = df_mul(gx, df_add_one(V01));
-    df n10 = df_mul(gy, df_add_float_pos(V10, rho.h));
+    const df R01 = df_one_plus_mul(gx, V01);
+    const df A10 = df_one_plus_mul(gy, V10);
     df t0 = df_mul(df_mul(gx, py), df_add_one(V00));
-    const float t12 = __fmaf_rn(qx.h, __fadd_rn(n10.h, n10.l), __fmul_rn(qy.h, __fadd_rn(n01.h, n01.l)));
+    // qy r01 + qx rho (r10 / rho) of this step; R - 1 is exact for 1 <= R.h < 2^24
+    const float r01 = __fadd_rn(__fsub_rn(R01.h, 1.0f), R01.l);
+    const float a10 = __fadd_rn(__fsub_rn(A10.h, 1.0f), A10.l);
+    const float t12 = __fmaf_rn(__fmul_rn(qx.h, rho.h), a10, __fmul_rn(qy.h, r01));
     V00 = df_add_float_pos(t0, t12);
-    V01 = n01;
-    V10 = n10;
+    V01 = R01;
+    V10 = A10;
 }
 
 // M consecutive scenario-plane elements of one lane, one vector load.
@@ -185,9 +194,9 @@ struct Tile {
             amt[i] = (EXTRA && pol[i] >= 0) ? e.amount[pol[i]] : 0.0;
 #pragma unroll
             for (int m = 0; m < M; ++m) {
-                V[0][i][m] = T::cst(r.bnd);
+                V[0][i][m] = T::cst((SHIFTED && KIND == K_ANN) ? 1.0f + r.bnd : r.bnd);
 #pragma unroll
-                for (int k = 1; k < NS; ++k) V[k][i][m] = T::cst(0.0f);
+                for (int k = 1; k < NS; ++k) V[k][i][m] = T::cst(SHIFTED ? 1.0f : 0.0f);
             }
         }
     }
@@ -196,9 +205,23 @@ struct Tile {
         return *reinterpret_cast<const VP*>(vplane + (size_t)t * e.s_pad + s0);
     }
 
-    __device__ __forceinline__ Val out_state(int i, int m) const {
-        if constexpr (NS == 1) return V[0][i][m];
-        else return st0[i] == 0 ? V[0][i][m] : (st0[i] == 1 ? V[1][i][m] : V[2][i][m]);
+    // The compensated form carries annuity-type states shifted (see step_ann):
+    // the ANN state and JL state 01 as 1 + r, JL state 10 as 1 + r / rho.
+    static constexpr bool SHIFTED = FORM == F_COMP && KIND != K_ASS;
+
+    // r of state k of policy i, scenario m, in FP64
+    __device__ __forceinline__ double dval(int k, int i, int m) const {
+        const double x = T::dbl(V[k][i][m]);
+        if constexpr (SHIFTED) {
+            if (KIND == K_ANN || k == 1) return x - 1.0;
+            if (k == 2) return T::dbl(rho[i]) * (x - 1.0);
+        }
+        return x;
+    }
+
+    __device__ __forceinline__ double out_state(int i, int m) const {
+        if constexpr (NS == 1) return dval(0, i, m);
+        else return dval(st0[i] == 0 ? 0 : (st0[i] == 1 ? 1 : 2), i, m);
     }
 
     // traj / pt_mean side outputs of r_t for policy i (diagnostic runs only)
@@ -210,7 +233,7 @@ struct Tile {
         for (int m = 0; m < M; ++m) {
             const int s = s0 + m;
             if (s < e.n_valid) {
-                const double x = amt[i] * T::dbl(out_state(i, m));
+                const double x = amt[i] * out_state(i, m);
                 if (e.traj) e.traj[row * e.n_valid + s] = x;
                 sum += x;
             }
@@ -302,7 +325,7 @@ struct Tile {
             for (int m = 0; m < M; ++m) {
                 const int s = s0 + m;
                 if (s < e.n_valid) {
-                    const double x = A * T::dbl(out_state(i, m));
+                    const double x = A * out_state(i, m);
                     const size_t o = (size_t)pol[i] * e.n_valid + s;
                     if (V0f) V0f[o] = (float)x;
                     if (V0d) V0d[o] = x;
@@ -333,8 +356,8 @@ struct Tile {
             }
 #pragma unroll
             for (int m = 0; m < M; ++m) {
-                double x = w0 * T::dbl(V[0][i][m]);
-                if constexpr (NS == 3) x += w1 * T::dbl(V[1][i][m]) + w2 * T::dbl(V[2][i][m]);
+                double x = w0 * dval(0, i, m);
+                if constexpr (NS == 3) x += w1 * dval(1, i, m) + w2 * dval(2, i, m);
                 acc[m] += x;
             }
         }

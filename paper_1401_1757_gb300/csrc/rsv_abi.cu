@@ -85,6 +85,34 @@ __global__ void segment_wsum_kernel(const long long* __restrict__ seg, const dou
     if (threadIdx.x == 0) L[blockIdx.x] = base[blockIdx.x] + sd[0];
 }
 
+// The surrogate mode's queries: node n's list of in-force (policy, state)
+// queries (offsets noff[n], weights nw) repeated for every outer path o, at
+// that path's node rate.  Segment k = o NN + n spans
+// [o Qn + noff[n], o Qn + noff[n+1]) and starts from base[n].
+__global__ void expand_node_queries_kernel(const rsv_query* __restrict__ nq, const double* __restrict__ nw,
+                                           long long Qn, int NO, int NN, int step, const double* __restrict__ rn,
+                                           rsv_query* __restrict__ q, double* __restrict__ w) {
+    const long long n_all = Qn * NO;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_all; i += (long long)gridDim.x * blockDim.x) {
+        const long long o = i / Qn, j = i - o * Qn;
+        rsv_query x = nq[j];
+        x.r = rn[o * NN + x.m / step];
+        q[i] = x;
+        w[i] = nw[j];
+    }
+}
+
+__global__ void node_segments_kernel(const long long* __restrict__ noff, const double* __restrict__ nbase,
+                                     long long Qn, int NO, int NN, long long* __restrict__ seg,
+                                     double* __restrict__ base) {
+    const long long on_n = (long long)NO * NN;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k <= on_n; k += (long long)gridDim.x * blockDim.x) {
+        const long long o = k / NN, n = k - o * NN;
+        seg[k] = k == on_n ? Qn * NO : o * Qn + noff[n];
+        if (k < on_n) base[k] = nbase[n];
+    }
+}
+
 __global__ void scale_kernel(double* __restrict__ x, size_t n, double f) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         x[i] *= f;
@@ -512,7 +540,7 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
     CU(c->d_nest_ln.ensure(NN * sizeof(int)));
     CU(c->d_nest_rn.ensure((size_t)NO * NN * sizeof(double)));
     CU(c->d_nest_d0.ensure((size_t)NO * NN * sizeof(double)));
-    CU(c->d_nest_plane.ensure((size_t)B * per_outer));
+    if (!sur) CU(c->d_nest_plane.ensure((size_t)B * per_outer));
     CU(c->d_nest_mean.ensure((size_t)NO * NN * sizeof(double)));
     CU(c->d_nest_kth.ensure((size_t)NO * NN * sizeof(double)));
     double* Lall = (o->on_device && out->L_all) ? out->L_all : nullptr;
@@ -547,47 +575,63 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
     a.status = c->d_ctl.as<int32_t>() + 1;
     a.L_all = Lall;
     if (sur) {
-        // one query per in-force (policy, state) and (outer path, node), at the node's rate
+        // one query per in-force (policy, state) and (outer path, node), at the
+        // node's rate; the lists depend on the node only and are expanded over
+        // the outer paths on the device
         const size_t on_n = (size_t)NO * NN;
-        std::vector<double> rn(on_n), base(on_n, 0.0);
-        CU(cudaMemcpyAsync(rn.data(), c->d_nest_rn.p, on_n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaStreamSynchronize(c->stream));
-        std::vector<rsv_query> hq;
-        std::vector<double> hw;
-        std::vector<long long> seg(on_n + 1, 0);
-        for (int o = 0; o < NO; ++o)
-            for (int n = 0; n < NN; ++n) {
-                const size_t k = (size_t)o * NN + n;
-                seg[k] = (long long)hq.size();
-                const int m = n * step;
-                for (int p = 0; p < n_pol; ++p)
-                    for (int j = 0; j < 3; ++j) {
-                        const double wj = w[((size_t)p * NN + n) * 3 + j];
-                        if (wj == 0.0) continue;
-                        if (Sp[p] == m) {   // matures at the node: its boundary value, no projection
-                            base[k] += c->pols[p].product == RSV_ENDOWMENT ? wj : 0.0;
-                            continue;
-                        }
-                        rsv_query q{p, m, j, 0, rn[k]};
-                        hq.push_back(q);
-                        hw.push_back(wj);
+        std::vector<rsv_query> nq;
+        std::vector<double> nw, nbase(NN, 0.0);
+        std::vector<long long> noff(NN + 1, 0);
+        for (int n = 0; n < NN; ++n) {
+            noff[n] = (long long)nq.size();
+            const int m = n * step;
+            for (int p = 0; p < n_pol; ++p)
+                for (int j = 0; j < 3; ++j) {
+                    const double wj = w[((size_t)p * NN + n) * 3 + j];
+                    if (wj == 0.0) continue;
+                    if (Sp[p] == m) {   // matures at the node: its boundary value, no projection
+                        nbase[n] += c->pols[p].product == RSV_ENDOWMENT ? wj : 0.0;
+                        continue;
                     }
-            }
-        seg[on_n] = (long long)hq.size();
-        const long long nq = (long long)hq.size();
-        CU(c->d_nest_plane.ensure(std::max<size_t>(1, (size_t)nq) * 16 + (on_n + 1) * 8 + on_n * 8));
-        double* dV = c->d_nest_plane.as<double>();
-        double* dw = dV + std::max<long long>(1, nq);
-        long long* dseg = reinterpret_cast<long long*>(dw + std::max<long long>(1, nq));
-        double* dbase = reinterpret_cast<double*>(dseg + on_n + 1);
-        long long nfb = 0;
-        if (nq > 0) {
-            st = sur_value_queries(c, hq.data(), nq, dV, &nfb);
-            if (st != RSV_OK) return st;
-            CU(cudaMemcpyAsync(dw, hw.data(), nq * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+                    nq.push_back(rsv_query{p, m, j, 0, 0.0});
+                    nw.push_back(wj);
+                }
         }
-        CU(cudaMemcpyAsync(dseg, seg.data(), (on_n + 1) * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
-        CU(cudaMemcpyAsync(dbase, base.data(), on_n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        noff[NN] = (long long)nq.size();
+        const long long Qn = (long long)nq.size(), nq_all = Qn * NO;
+        // device: [V | w | queries | node lists | seg | base]
+        const size_t bytes = (size_t)std::max<long long>(1, nq_all) * (16 + sizeof(rsv_query)) +
+                             (size_t)std::max<long long>(1, Qn) * (sizeof(rsv_query) + 8) + (NN + 1) * 8 + NN * 8 +
+                             (on_n + 1) * 8 + on_n * 8 + 64;
+        CU(c->d_nest_plane.ensure(bytes));
+        char* cur = static_cast<char*>(c->d_nest_plane.p);
+        auto take = [&](size_t n) { char* r = cur; cur += (n + 7) / 8 * 8; return r; };
+        double* dV = reinterpret_cast<double*>(take(std::max<long long>(1, nq_all) * 8));
+        double* dw = reinterpret_cast<double*>(take(std::max<long long>(1, nq_all) * 8));
+        rsv_query* dq = reinterpret_cast<rsv_query*>(take(std::max<long long>(1, nq_all) * sizeof(rsv_query)));
+        rsv_query* dnq = reinterpret_cast<rsv_query*>(take(std::max<long long>(1, Qn) * sizeof(rsv_query)));
+        double* dnw = reinterpret_cast<double*>(take(std::max<long long>(1, Qn) * 8));
+        long long* dnoff = reinterpret_cast<long long*>(take((NN + 1) * 8));
+        double* dnbase = reinterpret_cast<double*>(take(NN * 8));
+        long long* dseg = reinterpret_cast<long long*>(take((on_n + 1) * 8));
+        double* dbase = reinterpret_cast<double*>(take(on_n * 8));
+        if (Qn > 0) {
+            CU(cudaMemcpyAsync(dnq, nq.data(), Qn * sizeof(rsv_query), cudaMemcpyHostToDevice, c->stream));
+            CU(cudaMemcpyAsync(dnw, nw.data(), Qn * 8, cudaMemcpyHostToDevice, c->stream));
+        }
+        CU(cudaMemcpyAsync(dnoff, noff.data(), (NN + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+        CU(cudaMemcpyAsync(dnbase, nbase.data(), NN * 8, cudaMemcpyHostToDevice, c->stream));
+        node_segments_kernel<<<(unsigned)((on_n + 256) / 256), 256, 0, c->stream>>>(dnoff, dnbase, Qn, NO, NN, dseg,
+                                                                                  dbase);
+        CU(cudaGetLastError());
+        long long nfb = 0;
+        if (nq_all > 0) {
+            expand_node_queries_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(dnq, dnw, Qn, NO, NN, step,
+                                                                               c->d_nest_rn.as<double>(), dq, dw);
+            CU(cudaGetLastError());
+            st = sur_value_queries(c, dq, nq_all, dseg, (int)on_n, Lmax, dV, &nfb);
+            if (st != RSV_OK) return st;
+        }
         segment_wsum_kernel<<<(unsigned)on_n, 256, 0, c->stream>>>(dseg, dw, dV, dbase, Lall);
         CU(cudaGetLastError());
         if (out->n_fallback) *out->n_fallback = nfb;

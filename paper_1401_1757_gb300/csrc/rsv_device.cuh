@@ -106,6 +106,19 @@ __device__ __forceinline__ df df_add_float_pos(df a, float b) {
     return df{s, e};
 }
 
+// 1 + g R for df g >= 0 and R >= 1 (a shifted reserve R = 1 + r).  The head
+// h = fl(1 + g.h R.h) is one FMA; h - 1 is exact for 1 <= h < 2^24, so a
+// second FMA recovers the rounding error of h to within 2^-24 of itself, and
+// the cross terms add the tails.  Five operations, no ordering needed.
+__device__ __forceinline__ df df_one_plus_mul(df g, df R) {
+    const float h = __fmaf_rn(g.h, R.h, 1.0f);
+    const float d = __fsub_rn(h, 1.0f);
+    float e = __fmaf_rn(g.h, R.h, -d);
+    e = __fmaf_rn(g.h, R.l, e);
+    e = __fmaf_rn(g.l, R.h, e);
+    return df{h, e};
+}
+
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.h + (double)a.l; }
 
 // ------------------------------------------------------------------------

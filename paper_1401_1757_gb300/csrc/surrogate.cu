@@ -22,13 +22,27 @@
 
 namespace rsv {
 
-__device__ __forceinline__ int sur_bucket(const PolSur& P, int m, int state, double r) {
+// z-score of a node rate under the Vasicek model at month m from r0 (the
+// rate at month 0 is r0 itself: anything else is out of the model's range).
+__device__ __forceinline__ double sur_rate_z(int m, double r, double a, double b, double sigma, double r0) {
+    const double t = m / 12.0;
+    const double mean = b + (r0 - b) * exp(-a * t);
+    const double sd = sigma * sqrt(-expm1(-2.0 * a * t) / (2.0 * a));
+    if (sd > 0.0) return (r - mean) / sd;
+    return r == mean ? 0.0 : 1e30;
+}
+
+__device__ __forceinline__ int sur_bucket(const PolSur& P, int m, int state, double r, double a, double b,
+                                          double sigma, double r0) {
     const int ps = P.product == RSV_SL_ANNUITY ? 0
                    : P.product == RSV_JL_REVERSIONARY ? 1 + state
                    : P.product == RSV_TERM_ASSURANCE ? 4 : 5;
-    const int ab = min(SUR_NB_AGE - 1, max(0, (int)(((P.age1 + m) / 12.0 - 20.0) / 10.0)));
+    int age = P.age1;   // the life (or for state 00 the older life) the value depends on
+    if (P.product == RSV_JL_REVERSIONARY) age = state == 2 ? P.age2 : (state == 1 ? P.age1 : max(P.age1, P.age2));
+    const int ab = min(SUR_NB_AGE - 1, max(0, (int)(((age + m) / 12.0 - 20.0) / 10.0)));
     const int tb = min(SUR_NB_TERM - 1, max(0, (int)((P.S - m) / 120.0)));
-    const int rb = min(SUR_NB_R - 1, max(0, (int)floor((r + 0.02) / 0.02)));
+    const double z = sur_rate_z(m, r, a, b, sigma, r0);
+    const int rb = fabs(z) < 4.0 ? min(SUR_NB_R - 2, max(0, (int)floor(2.0 * z + 8.0))) : SUR_NB_R - 1;
     return ((ps * SUR_NB_AGE + ab) * SUR_NB_TERM + tb) * SUR_NB_R + rb;
 }
 
@@ -74,7 +88,7 @@ __global__ void sample_queries_kernel(const PolSur* __restrict__ pols, int n_pol
         const double u1 = ((double)g[0] + 0.5) * inv32, u2 = ((double)g[1] + 0.5) * inv32;
         const double z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
         Q.r = mean + widen * sd * z;
-        Q.bucket = sur_bucket(P, Q.m, Q.state, Q.r);
+        Q.bucket = sur_bucket(P, Q.m, Q.state, Q.r, a, b, sigma, r0);
         out[q] = Q;
     }
 }
@@ -129,7 +143,34 @@ __global__ void sur_comm_kernel(const double2* __restrict__ tab, int tab_pad, in
 }
 
 // Reserve per unit amount in the query's state: the FP64 recurrence on the
-// Vasicek forward curve from the policy's end back to the node.  With `flag`,
+// Vasicek forward curve from the policy's end back to the node; vt(t) is the
+// one-month discount factor t months after the node.
+template <class VT>
+__device__ __forceinline__ double sur_recurrence(const PolSur& P, const SurTables& T, const SurQuery& Q, VT vt) {
+    const int Sn = P.S - Q.m;
+    const double2* tx = T.tab + (size_t)P.tab1 * T.tab_pad + P.age1 + Q.m;
+    const double2* ty = T.tab + (size_t)P.tab2 * T.tab_pad + P.age2 + Q.m;
+    double V00 = P.product == RSV_ENDOWMENT ? 1.0 : 0.0, V01 = 0.0, V10 = 0.0;
+    for (int t = Sn - 1; t >= 0; --t) {
+        const double v = vt(t);
+        const double2 ex = tx[t];
+        if (P.product == RSV_SL_ANNUITY) {
+            V00 = v * ex.x * (1.0 + V00);
+        } else if (P.product == RSV_JL_REVERSIONARY) {
+            const double2 ey = ty[t];
+            const double n01 = v * ex.x * (1.0 + V01);
+            const double n10 = v * ey.x * (P.rho + V10);
+            V00 = v * ex.x * ey.x * (1.0 + V00) + ey.y * n01 + ex.y * n10;
+            V01 = n01;
+            V10 = n10;
+        } else {
+            V00 = v * (ex.y + ex.x * V00);
+        }
+    }
+    return Q.state == 0 ? V00 : (Q.state == 1 ? V01 : V10);
+}
+
+// The recurrence for n independent queries (one thread each).  With `flag`,
 // only queries whose bucket is flagged are valued (the fallback).
 __global__ void sur_label_kernel(const PolSur* __restrict__ pols, const SurTables T, const SurQuery* __restrict__ qs,
                                  long long n, const unsigned char* __restrict__ flag, double* __restrict__ V) {
@@ -140,36 +181,44 @@ __global__ void sur_label_kernel(const PolSur* __restrict__ pols, const SurTable
             V[i] = 0.0;
             continue;
         }
-        const PolSur P = pols[Q.pol];
-        const int Sn = P.S - Q.m;
-        const double2* tx = T.tab + (size_t)P.tab1 * T.tab_pad + P.age1 + Q.m;
-        const double2* ty = T.tab + (size_t)P.tab2 * T.tab_pad + P.age2 + Q.m;
-        double V00 = P.product == RSV_ENDOWMENT ? 1.0 : 0.0, V01 = 0.0, V10 = 0.0;
-        for (int t = Sn - 1; t >= 0; --t) {
+        const double r = Q.r;
+        V[i] = sur_recurrence(pols[Q.pol], T, Q, [&](int t) {
             const double2 dc = T.curve[t];   // month t after the node
-            const double v = exp(dc.x - dc.y * Q.r);
-            const double2 ex = tx[t];
-            if (P.product == RSV_SL_ANNUITY) {
-                V00 = v * ex.x * (1.0 + V00);
-            } else if (P.product == RSV_JL_REVERSIONARY) {
-                const double2 ey = ty[t];
-                const double n01 = v * ex.x * (1.0 + V01);
-                const double n10 = v * ey.x * (P.rho + V10);
-                V00 = v * ex.x * ey.x * (1.0 + V00) + ey.y * n01 + ex.y * n10;
-                V01 = n01;
-                V10 = n10;
-            } else {
-                V00 = v * (ex.y + ex.x * V00);
-            }
-        }
-        V[i] = Q.state == 0 ? V00 : (Q.state == 1 ? V01 : V10);
+            return exp(dc.x - dc.y * r);
+        });
     }
 }
+
+// The fallback of the nested valuation: the queries of one (outer path, node)
+// share its short rate, so each block builds that curve once in shared memory
+// (Lmax months) and values the segment's flagged queries from it.
+__global__ void sur_fallback_nodes_kernel(const PolSur* __restrict__ pols, const SurTables T,
+                                          const SurQuery* __restrict__ qs, const long long* __restrict__ seg, int Lmax,
+                                          const unsigned char* __restrict__ flag, double* __restrict__ V) {
+    extern __shared__ double vcur[];
+    const long long b = seg[blockIdx.x], e = seg[blockIdx.x + 1];
+    if (b == e) return;
+    const double r = qs[b].r;
+    for (int t = threadIdx.x; t < Lmax; t += blockDim.x) {
+        const double2 dc = T.curve[t];
+        vcur[t] = exp(dc.x - dc.y * r);
+    }
+    __syncthreads();
+    for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
+        const SurQuery Q = qs[i];
+        if (Q.state < 0 || !flag[Q.bucket]) continue;
+        V[i] = sur_recurrence(pols[Q.pol], T, Q, [&](int t) { return vcur[t]; });
+    }
+}
+
 // Base value per unit amount from the commutation columns at flat rate
 // grid point g: the classical actuarial values (annuity (N_{x+1} - N_{x+n+1})/D_x,
 // term assurance (M_x - M_{x+n})/D_x, pure endowment D_{x+n}/D_x) for n
-// months from attained month x.  The joint-life state 00 takes a_x + rho a_y
-// (the joint-life annuity it omits is left to the network).
+// months from attained month x.  The joint-life state 00 is the reversionary
+// a_x + rho (a_y - a_xy), with the joint-life annuity a_xy estimated from the
+// two single-life values: for constant monthly forces a monthly annuity in
+// arrears satisfies ln(1 + 1/a) = (delta + mu)/12, and the joint life's force
+// is the sum of the two, so ln(1 + 1/a_xy) = ln(1 + 1/a_x) + ln(1 + 1/a_y) - delta/12.
 __device__ double sur_base_value(const PolSur& P, const SurTables& T, int g, int m, int state) {
     const int CL = sur_comm_len(T.tab_pad), n = P.S - m;
     auto col = [&](int tab) { return T.comm + ((size_t)tab * SUR_COMM_N + g) * 3 * CL; };
@@ -184,7 +233,11 @@ __device__ double sur_base_value(const PolSur& P, const SurTables& T, int g, int
         const int y = P.age2 + m;
         if (state == 1) return ann(P.tab1, x);
         if (state == 2) return P.rho * ann(P.tab2, y);
-        return ann(P.tab1, x) + P.rho * ann(P.tab2, y);
+        const double ax = ann(P.tab1, x), ay = ann(P.tab2, y);
+        if (!(ax > 0.0) || !(ay > 0.0)) return ax + P.rho * ay;
+        const double e = log1p(1.0 / ax) + log1p(1.0 / ay) - (SUR_COMM_LO + g * SUR_COMM_STEP) / 12.0;
+        const double axy = e > 0.0 ? fmin(1.0 / expm1(e), fmin(ax, ay)) : fmin(ax, ay);
+        return ax + P.rho * (ay - axy);
     }
     const double* D = col(P.tab1);
     if (!(D[x] > 0.0)) return 1.0;   // past the table: death in the first month
@@ -487,7 +540,8 @@ rsv_status mlp_stage_inputs(rsv_ctx* c, const float* X, long long n, long long n
 }
 
 __global__ void query_prep_kernel(const PolSur* __restrict__ pols, int n_pol, const rsv_query* __restrict__ in,
-                                  long long n, SurQuery* __restrict__ out, int* __restrict__ bad,
+                                  long long n, double a, double b, double sigma, double r0,
+                                  SurQuery* __restrict__ out, int* __restrict__ bad,
                                   const unsigned char* __restrict__ flag, unsigned long long* __restrict__ n_flag) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const rsv_query r = in[i];
@@ -505,7 +559,7 @@ __global__ void query_prep_kernel(const PolSur* __restrict__ pols, int n_pol, co
             Q.pol = 0;
             Q.state = -1;
         } else {
-            Q.bucket = sur_bucket(pols[r.pol], r.m, r.state, r.r);
+            Q.bucket = sur_bucket(pols[r.pol], r.m, r.state, r.r, a, b, sigma, r0);
             if (flag && flag[Q.bucket]) atomicAdd(n_flag, 1ull);
         }
         out[i] = Q;
@@ -520,28 +574,32 @@ __global__ void scale_by_amount_kernel(const PolSur* __restrict__ pols, const Su
 
 }  // namespace
 
-// Per-unit expected reserves (device, n values) of host-built queries by the
+// Per-unit expected reserves (device, n values) of device queries by the
 // network with fallback; *n_fallback receives the number valued by the
 // recurrence.  Used by the nested valuation's surrogate mode.
-rsv_status sur_value_queries(rsv_ctx* c, const rsv_query* hq, long long n, double* V, long long* n_fallback) {
+rsv_status sur_value_queries(rsv_ctx* c, const rsv_query* dq, long long n, const long long* seg, int n_seg, int Lmax,
+                             double* V, long long* n_fallback) {
     SurrogateState& s = c->sur;
     if (c->pols_dev_gen != c->pol_gen) {
         std::vector<PolSur> hp;
         rsv_status st = sur_upload_policies(c, hp);
         if (st != RSV_OK) return st;
     }
-    CU(s.d_aux.ensure((size_t)n * sizeof(rsv_query) + 16));
     CU(s.d_q.ensure((size_t)n * sizeof(SurQuery)));
     CU(s.d_err.ensure(16));
     CU(cudaMemsetAsync(s.d_err.p, 0, 16, c->stream));
-    CU(cudaMemcpyAsync(s.d_aux.p, hq, (size_t)n * sizeof(rsv_query), cudaMemcpyHostToDevice, c->stream));
     SurQuery* q = s.d_q.as<SurQuery>();
     query_prep_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(
-        c->d_pols.as<PolSur>(), (int)c->pols.size(), s.d_aux.as<rsv_query>(), n, q, s.d_err.as<int>(),
-        s.d_flag.as<unsigned char>(), reinterpret_cast<unsigned long long*>(s.d_err.as<char>() + 8));
+        c->d_pols.as<PolSur>(), (int)c->pols.size(), dq, n, s.a, s.b, s.sigma, s.r0, q,
+        s.d_err.as<int>(), s.d_flag.as<unsigned char>(), reinterpret_cast<unsigned long long*>(s.d_err.as<char>() + 8));
     CU(cudaGetLastError());
-    rsv_status st = sur_predict(c, q, n, V, true, 65536);
+    rsv_status st = sur_predict(c, q, n, V, false, 65536);
     if (st != RSV_OK) return st;
+    SurTables T;
+    if ((st = sur_tables(c, T)) != RSV_OK) return st;
+    sur_fallback_nodes_kernel<<<n_seg, 256, (size_t)Lmax * sizeof(double), c->stream>>>(
+        c->d_pols.as<PolSur>(), T, q, seg, Lmax, s.d_flag.as<unsigned char>(), V);
+    CU(cudaGetLastError());
     long long cnt[2] = {0, 0};
     CU(cudaMemcpyAsync(cnt, s.d_err.p, 16, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
@@ -581,8 +639,8 @@ rsv_status rsv_surrogate_query(rsv_ctx* c, const rsv_query* queries, int64_t n, 
     SurQuery* q = s.d_q.as<SurQuery>();
     const int grid = c->sm_count * 8;
     query_prep_kernel<<<grid, 256, 0, c->stream>>>(c->d_pols.as<PolSur>(), (int)c->pols.size(),
-                                                   s.d_aux.as<rsv_query>(), n, q, s.d_err.as<int>(), nullptr,
-                                                   nullptr);
+                                                   s.d_aux.as<rsv_query>(), n, s.a, s.b, s.sigma, s.r0, q,
+                                                   s.d_err.as<int>(), nullptr, nullptr);
     CU(cudaGetLastError());
     double* V = s.d_pred.as<double>();
     CU(cudaEventRecord(c->ev0, c->stream));
@@ -685,7 +743,7 @@ rsv_status rsv_surrogate_train(rsv_ctx* c, const rsv_surrogate_cfg* cfg, rsv_sur
     if (!cfg || !rep) return fail(c, RSV_E_ARG, "cfg and report must not be NULL");
     if (cfg->n_train < 1024 || cfg->n_val < 1024 || cfg->epochs < 0 || cfg->batch < 64 || cfg->batch % 64 ||
         cfg->batch > 65536 || !(cfg->lr > 0) || !(cfg->a > 0) || !(cfg->sigma >= 0) || !(cfg->tol > 0) ||
-        cfg->max_node_m < 0 || !(cfg->widen >= 0))
+        cfg->max_node_m < 0 || !(cfg->widen >= 0) || !(cfg->margin > 0) || !(cfg->margin <= 1))
         return fail(c, RSV_E_ARG, "bad surrogate configuration");
     if (c->pols.empty()) return fail(c, RSV_E_STATE, "no portfolio loaded");
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice failed");
@@ -823,7 +881,9 @@ rsv_status rsv_surrogate_train(rsv_ctx* c, const rsv_surrogate_cfg* cfg, rsv_sur
     s.flag.assign(SUR_NBUCKETS, 0);
     long long n_flag = 0;
     for (int k = 0; k < SUR_NBUCKETS; ++k) {
-        s.flag[k] = (bcnt[k] < 16 || bmax[k] > cfg->tol) ? 1 : 0;   // unseen or inaccurate: recurrence
+        // unseen, thinly seen, not clearly inside the tolerance, or a rate
+        // beyond 4 sd of the model: recurrence
+        s.flag[k] = (bcnt[k] < 32 || bmax[k] > cfg->margin * cfg->tol || k % SUR_NB_R == SUR_NB_R - 1) ? 1 : 0;
         n_flag += s.flag[k];
     }
     CU(s.d_flag.ensure(SUR_NBUCKETS));

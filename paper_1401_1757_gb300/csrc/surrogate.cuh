@@ -37,5 +37,10 @@ __host__ __device__ constexpr int sur_comm_len(int tab_pad) { return tab_pad + 2
 
 #include "rsv.h"
 namespace rsv {
-rsv_status sur_value_queries(rsv_ctx* c, const rsv_query* hq, long long n, double* V, long long* n_fallback);
+// Per-unit expected reserves (device, n values) of n device queries grouped
+// in n_seg segments of one short rate each (device offsets seg[n_seg + 1]),
+// each at most Lmax months long: the network, then flagged buckets by the
+// recurrence.  *n_fallback receives the number valued by the recurrence.
+rsv_status sur_value_queries(rsv_ctx* c, const rsv_query* dq, long long n, const long long* seg, int n_seg, int Lmax,
+                             double* V, long long* n_fallback);
 }  // namespace rsv

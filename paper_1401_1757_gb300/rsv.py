@@ -65,7 +65,7 @@ class rsv_surrogate_cfg(C.Structure):
     _fields_ = [("n_train", C.c_int64), ("n_val", C.c_int64), ("epochs", C.c_int32), ("batch", C.c_int32),
                 ("lr", C.c_double), ("seed", C.c_uint64), ("a", C.c_double), ("b", C.c_double),
                 ("sigma", C.c_double), ("r0", C.c_double), ("max_node_m", C.c_int32), ("widen", C.c_double),
-                ("tol", C.c_double)]
+                ("tol", C.c_double), ("margin", C.c_double)]
 
 
 class rsv_surrogate_report(C.Structure):
@@ -334,8 +334,8 @@ def rsv_mlp_gradient(ctx, X, target):
 
 
 def rsv_surrogate_train(ctx, n_train=10_000_000, n_val=1_000_000, epochs=20, batch=8192, lr=2e-3, seed=0,
-                        a=0.1, b=0.04, sigma=0.01, r0=0.03, max_node_m=600, widen=1.5, tol=1e-3) -> dict:
-    cfg = rsv_surrogate_cfg(n_train, n_val, epochs, batch, lr, seed, a, b, sigma, r0, max_node_m, widen, tol)
+                        a=0.1, b=0.04, sigma=0.01, r0=0.03, max_node_m=600, widen=1.5, tol=1e-3, margin=0.3) -> dict:
+    cfg = rsv_surrogate_cfg(n_train, n_val, epochs, batch, lr, seed, a, b, sigma, r0, max_node_m, widen, tol, margin)
     rep = rsv_surrogate_report()
     _check(ctx, _lib.rsv_surrogate_train(ctx, C.byref(cfg), C.byref(rep)))
     return {k: getattr(rep, k) for k, _ in rsv_surrogate_report._fields_}

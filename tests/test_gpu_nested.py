@@ -154,7 +154,7 @@ def test_surrogate_mode_gain_over_brute_force(ctx):
     rsv.rsv_load_decrements(ctx, 0, tab)
     rsv.rsv_load_portfolio(ctx, pol)
     rsv.rsv_mlp_init(ctx, 1)
-    rep = rsv.rsv_surrogate_train(ctx, n_train=2_000_000, n_val=200_000, epochs=8, batch=8192, lr=2e-3, seed=1,
+    rep = rsv.rsv_surrogate_train(ctx, n_train=3_000_000, n_val=400_000, epochs=10, batch=8192, lr=2e-3, seed=1,
                                   max_node_m=480)
     NO, NN = 8, 40
     spec = dict(n_outer=NO, n_nodes=NN, node_step_m=12, seed=4, n_inner=1000)
