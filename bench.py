@@ -49,10 +49,10 @@ WORKLOAD = ("100,000-policy mix (40% SL annuities, 20% JL reversionary 3-state, 
 # evaluate: plain annuity v*p then an FMA; compensated annuity a double-float
 # product (7) and the shifted update 1 + g R (9); compensated assurance two
 # double-float products and an ordered sum (20); compensated JL three
-# products, two shifted updates, 1 + r00, the FP32 death terms and an ordered
-# sum (66).
+# double-float products (21), two shifted updates (18), the FP32 death terms
+# (9) and the shifted state-00 update c + g R with an ordered sum (13): 61.
 FLOPS = {"f32": {0: 3, 1: 13, 2: 3, 3: 3},
-         "f32comp": {0: 16, 1: 66, 2: 20, 3: 20},
+         "f32comp": {0: 16, 1: 61, 2: 20, 3: 20},
          "f64": {0: 3, 1: 13, 2: 3, 3: 3}}
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = 2 * FP32_LANES * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 at 2070 MHz
@@ -257,6 +257,30 @@ def bench_nested(rsv, torch, tab, steps, warmup, n_outer=None, sur_epochs=10, su
     return res
 
 
+def bench_config1(rsv, torch, tab, reps=20):
+    """Config 1 (1,000 annuities, one flat 4% rate, FP64): a latency-bound run with
+    one scenario.  Kernel time of the scenario-parallel FP64 kernel against the
+    parallel-in-time scan (one warp per chain, lanes over blocks of steps)."""
+    pol = synth.portfolio_single_life(1000, seed=0)
+    v = synth.flat_scenarios(n_steps=720)
+    ctx = rsv.rsv_create(torch.cuda.current_device(), torch.cuda.current_stream())
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    V0 = torch.empty((1000, 1), dtype=torch.float64, device="cuda")
+    res = {"workload": "1,000 single-life annuities (ages 60-90) x 1 flat 4% scenario x up to 720 steps, FP64"}
+    for name, var in (("scenario_parallel", -1), ("time_scan", rsv.RSV_VARIANT_TIME_SCAN)):
+        ms = []
+        for i in range(reps + 3):
+            rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_V0, on_device=True, variant=var, V0d=V0)
+            if i >= 3:
+                ms.append(rsv.rsv_last_kernel_ms(ctx))
+        t = statistics.median(ms)
+        res[name] = {"kernel_ms": t, "valuations_s": 1000 / (t / 1e3)}
+    rsv.rsv_destroy(ctx)
+    return res
+
+
 SURROGATE_WORKLOAD = ("MLP surrogate of the inner-loop expectation: 32->4x256->1 GELU, BF16 weights and activations, "
                       "FP32 accumulation, trained on 10M recurrence labels of the 100,000-policy mix, scored on 1M "
                       "held-out queries")
@@ -329,6 +353,8 @@ def main():
     ap.add_argument("--surrogate-train", type=int, default=10_000_000, help="training labels (profiling runs: fewer)")
     ap.add_argument("--surrogate-val", type=int, default=1_000_000, help="held-out queries")
     ap.add_argument("--nested-outer", type=int, default=NESTED["n_outer"], help="outer paths (profiling runs: fewer)")
+    ap.add_argument("--nested-surrogate-epochs", type=int, default=10,
+                    help="train the surrogate on the nested portfolio and time its mode (0: skip)")
     args = ap.parse_args()
     if (args.policies, args.scenarios) != (N_POL, N_SCEN):
         N_POL, N_SCEN = args.policies, args.scenarios
@@ -456,9 +482,11 @@ def main():
                "ms_per_step": 1e3 * tot_s / args.steps}
 
     rsv.rsv_destroy(ctx)
-    nested = None
+    nested = config1 = None
     if not args.no_nested and rank == 0:
-        nested = bench_nested(rsv, torch, tab, steps=2, warmup=1, n_outer=args.nested_outer)
+        config1 = bench_config1(rsv, torch, tab)
+        nested = bench_nested(rsv, torch, tab, steps=2, warmup=1, n_outer=args.nested_outer,
+                              sur_epochs=args.nested_surrogate_epochs)
     surrogate = None
     if args.surrogate_epochs > 0 and rank == 0:
         surrogate = bench_surrogate(rsv, torch, tab, args.surrogate_epochs, lr=args.surrogate_lr,
@@ -496,6 +524,7 @@ def main():
         "gpu_launches": 3 * h["steps"],
         "clocks": clocks,
         "forms": results,
+        "config1_latency": config1,
         "nested": nested,
         "surrogate": surrogate,
     }

@@ -97,6 +97,15 @@ typedef struct {
     double reversion;  /* rho in [0, 1]; RSV_JL_REVERSIONARY only                      */
 } rsv_policy;
 
+/* rsv_opts.variant: the backward recurrence as a parallel-in-time scan.  Each
+ * step of Eq. generalForm is an affine map of the next step's reserve vector;
+ * one warp takes one chain (policy x scenario), its lanes compose the maps of
+ * 32 blocks of steps, and a warp suffix scan composes the blocks.  For few
+ * scenarios (a flat rate) or very long projections, where the scenario-
+ * parallel kernels leave lanes idle.  FP64 form only; outputs V0, the
+ * per-scenario totals and the trajectory (not per-step means). */
+#define RSV_VARIANT_TIME_SCAN (-2)
+
 typedef struct {
     int32_t form;      /* RSV_FORM_*                                                   */
     int32_t outputs;   /* RSV_OUT_* bits                                               */
@@ -106,7 +115,7 @@ typedef struct {
                           asynchronous on the context stream; 0: host pointers, the
                           call blocks until the results are in host memory            */
     int32_t variant;   /* kernel variant index, -1 = the tuned/default one (see
-                          rsv_variant_count / rsv_tune)                                */
+                          rsv_variant_count / rsv_tune), or RSV_VARIANT_TIME_SCAN     */
     int32_t reserved[3];
 } rsv_opts;
 

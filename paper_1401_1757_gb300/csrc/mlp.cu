@@ -84,17 +84,37 @@ __global__ void head_bwd_kernel(const float* __restrict__ dy, const float* __res
     dZb[i] = __float2bfloat16_rn(g);
 }
 
-// out[c] = sum_r X[r][c] * (wr ? wr[r] : 1), rows in order: one thread per column.
-__global__ void colsum_kernel(const float* __restrict__ X, const __nv_bfloat16* __restrict__ Xb,
-                              const float* __restrict__ wr, int R, int C, float* __restrict__ out) {
+// out[c] = sum_r X[r][c] * (wr ? wr[r] : 1) in two fixed-order passes: sums
+// over chunks of kColsumRows rows (one thread per column and chunk), then
+// over the chunks.
+constexpr int kColsumRows = 128;
+
+__global__ void colsum_partial_kernel(const float* __restrict__ X, const float* __restrict__ wr, int R, int C,
+                                      float* __restrict__ part) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, ch = blockIdx.y;
+    if (c >= C) return;
+    const int r1 = min(R, (ch + 1) * kColsumRows);
+    float s = 0.0f;
+    for (int r = ch * kColsumRows; r < r1; ++r) {
+        const float x = X[(size_t)r * C + c];
+        s += wr ? x * wr[r] : x;
+    }
+    part[(size_t)ch * C + c] = s;
+}
+
+__global__ void colsum_final_kernel(const float* __restrict__ part, int n_chunks, int C, float* __restrict__ out) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
     float s = 0.0f;
-    for (int r = 0; r < R; ++r) {
-        const float x = X ? X[(size_t)r * C + c] : __bfloat162float(Xb[(size_t)r * C + c]);
-        s += wr ? x * wr[r] : x;
-    }
+    for (int ch = 0; ch < n_chunks; ++ch) s += part[(size_t)ch * C + c];
     out[c] = s;
+}
+
+cudaError_t colsum(const float* X, const float* wr, int R, int C, float* part, float* out, cudaStream_t st) {
+    const int n_chunks = (R + kColsumRows - 1) / kColsumRows;
+    colsum_partial_kernel<<<dim3((C + 127) / 128, n_chunks), 128, 0, st>>>(X, wr, R, C, part);
+    colsum_final_kernel<<<(C + 127) / 128, 128, 0, st>>>(part, n_chunks, C, out);
+    return cudaGetLastError();
 }
 
 __global__ void sum_kernel(const float* __restrict__ x, int n, float* __restrict__ out) {
@@ -174,6 +194,7 @@ cudaError_t Mlp::ensure(int batch) {
     ALLOC(t, B * 4);
     ALLOC(dy, B * 4);
     ALLOC(sq, (B / 8 + 1) * 4);
+    ALLOC(part, (B / 128 + 1) * MLP_H * 4);
     ALLOC(loss, 4);
 #undef ALLOC
     cap = batch;
@@ -181,7 +202,7 @@ cudaError_t Mlp::ensure(int batch) {
 }
 
 void Mlp::release() {
-    void* ps[] = {params, grads, adam_m, adam_v, wbf, dW1, A4f, X, y, t, dy, sq, loss, wt};
+    void* ps[] = {params, grads, adam_m, adam_v, wbf, dW1, A4f, X, y, t, dy, sq, loss, wt, part};
     for (void* p : ps)
         if (p) cudaFree(p);
     for (int l = 0; l < 4; ++l) {
@@ -243,8 +264,8 @@ cudaError_t Mlp::forward(const __nv_bfloat16* Xin, int B, float* yout, const flo
 cudaError_t Mlp::backward(const __nv_bfloat16* Xin, int B, cudaStream_t st) {
     cudaError_t e;
     const size_t w5 = mlp_w5_off();
-    colsum_kernel<<<(MLP_H + 127) / 128, 128, 0, st>>>(A4f, nullptr, dy, B, MLP_H, grads + w5);
-    colsum_kernel<<<1, 32, 0, st>>>(dy, nullptr, nullptr, B, 1, grads + w5 + MLP_H);
+    if ((e = colsum(A4f, dy, B, MLP_H, part, grads + w5, st)) != cudaSuccess) return e;
+    if ((e = colsum(dy, nullptr, B, 1, part, grads + w5 + MLP_H, st)) != cudaSuccess) return e;
     head_bwd_kernel<<<(unsigned)(((size_t)B * MLP_H + 255) / 256), 256, 0, st>>>(dy, params + w5, Z[3], B, dZf[3],
                                                                                  dZb[3]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -265,9 +286,7 @@ cudaError_t Mlp::backward(const __nv_bfloat16* Xin, int B, cudaStream_t st) {
             fold_dw1_kernel<<<32, 256, 0, st>>>(dW1, grads + mlp_w_off(1));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        colsum_kernel<<<(MLP_H + 127) / 128, 128, 0, st>>>(dZf[l - 1], nullptr, nullptr, B, MLP_H,
-                                                          grads + mlp_b_off(l));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = colsum(dZf[l - 1], nullptr, B, MLP_H, part, grads + mlp_b_off(l), st)) != cudaSuccess) return e;
         if (l > 1) {
             // dZ_{l-1} = (dZ_l W_l^T) * gelu'(Z_{l-1}) : B operand W_l stored [K][H] = [n][k]
             GemmArgs h{};

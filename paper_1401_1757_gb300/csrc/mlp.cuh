@@ -37,6 +37,7 @@ struct Mlp {
     float* dZf[4] = {};
     __nv_bfloat16* dZb[4] = {};
     float *y = nullptr, *t = nullptr, *dy = nullptr, *sq = nullptr, *loss = nullptr;
+    float* part = nullptr;          // column-sum partials [cap / 128 + 1][MLP_H]
     __nv_bfloat16* wt = nullptr;    // W_l^T (K-major) BF16 copies for the tcgen05 inference kernel
     bool use_tc = true;             // inference on tcgen05 (else the mma.sync kernels)
 

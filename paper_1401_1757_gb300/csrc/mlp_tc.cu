@@ -129,8 +129,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ uint64_t bar_x, bar_w, bar_mma;
     __shared__ uint32_t tmem_slot;
     __shared__ float head_part[4][TM];   // partial head sums per column group
+    __shared__ float bias_s[4][TN];      // b_1..b_4
+    __shared__ float w5_s[TN + 1];       // head weights and bias
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < 4 * TN; i += kThreads) bias_s[i / TN][i % TN] = a.bias[i / TN][i % TN];
+    for (int i = tid; i <= TN; i += kThreads) w5_s[i] = a.w5[i];
     if (tid == 0) {
         mbar_init(&bar_x, 1);
         mbar_init(&bar_w, 1);
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // epilogue: row = 32 (warp % 4) + lane, columns 64 (warp / 4) .. +63 in chunks of 32
             const int quarter = warp & 3, cgrp = warp >> 2;
             const int row = quarter * 32 + lane;
-            const float* bias = a.bias[l];
+            const float* bias = bias_s[l];
             float ysum = 0.0f;
             for (int c0 = cgrp * kColsPerWarp; c0 < (cgrp + 1) * kColsPerWarp; c0 += 32) {
                 float v[32];
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) ysum += v[i] * a.w5[c0 + i];
+                    for (int i = 0; i < 32; ++i) ysum += v[i] * w5_s[c0 + i];
                 }
             }
             if (l == 3) {   // uniform across the block
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 __syncthreads();
                 if (cgrp == 0)
                     a.y[tile * TM + row] =
-                        ((head_part[0][row] + head_part[1][row]) + (head_part[2][row] + head_part[3][row])) + a.w5[TN];
+                        ((head_part[0][row] + head_part[1][row]) + (head_part[2][row] + head_part[3][row])) + w5_s[TN];
             }
             fence_before();
             fence_async_smem();   // A_l written by the generic proxy, read next by the tensor cores

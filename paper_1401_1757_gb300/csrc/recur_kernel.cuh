@@ -113,25 +113,25 @@ __device__ __forceinline__ void step_jl(R v, R px, R qx, R py, R qy, R rho, R& V
 // Annuity-type states are carried shifted, R = 1 + r (boundary R_S = 1):
 // r_t = g_t (1 + r_{t+1}) becomes R_t = 1 + g_t R_{t+1}, one df_one_plus_mul.
 // The JL state 10 is carried as A = 1 + r10 / rho, which obeys the same
-// update with g = v py.
+// update with g = v py, and the JL state 00 as R00 = 1 + r00:
+// R00_t = (1 + qy r01 + qx r10) + v px py R00_{t+1}.
 __device__ __forceinline__ df step_ann(df v, df p, df R) {
     return df_one_plus_mul(df_mul(v, p), R);
 }
 __device__ __forceinline__ df step_ass(df v, df p, df q, df V) {
     return df_mul(v, df_add_float_pos(df_mul(p, V), q.h));
 }
-// V00 = r00; V01 = R01 = 1 + r01; V10 = A10 = 1 + r10 / rho.
+// V00 = R00 = 1 + r00; V01 = R01 = 1 + r01; V10 = A10 = 1 + r10 / rho.
 __device__ __forceinline__ void step_jl(df v, df px, df qx, df py, df qy, df rho, df& V00, df& V01,
                                         df& V10) {
     df gx = df_mul(v, px), gy = df_mul(v, py);
     const df R01 = df_one_plus_mul(gx, V01);
     const df A10 = df_one_plus_mul(gy, V10);
-    df t0 = df_mul(df_mul(gx, py), df_add_one(V00));
     // qy r01 + qx rho (r10 / rho) of this step; R - 1 is exact for 1 <= R.h < 2^24
     const float r01 = __fadd_rn(__fsub_rn(R01.h, 1.0f), R01.l);
     const float a10 = __fadd_rn(__fsub_rn(A10.h, 1.0f), A10.l);
     const float t12 = __fmaf_rn(__fmul_rn(qx.h, rho.h), a10, __fmul_rn(qy.h, r01));
-    V00 = df_add_float_pos(t0, t12);
+    V00 = df_float_plus_mul(__fadd_rn(1.0f, t12), df_mul(gx, py), V00);
     V01 = R01;
     V10 = A10;
 }
@@ -194,7 +194,7 @@ struct Tile {
             amt[i] = (EXTRA && pol[i] >= 0) ? e.amount[pol[i]] : 0.0;
 #pragma unroll
             for (int m = 0; m < M; ++m) {
-                V[0][i][m] = T::cst((SHIFTED && KIND == K_ANN) ? 1.0f + r.bnd : r.bnd);
+                V[0][i][m] = T::cst(SHIFTED ? 1.0f + r.bnd : r.bnd);
 #pragma unroll
                 for (int k = 1; k < NS; ++k) V[k][i][m] = T::cst(SHIFTED ? 1.0f : 0.0f);
             }
@@ -206,22 +206,25 @@ struct Tile {
     }
 
     // The compensated form carries annuity-type states shifted (see step_ann):
-    // the ANN state and JL state 01 as 1 + r, JL state 10 as 1 + r / rho.
+    // the ANN state and JL states 00 and 01 as 1 + r, JL state 10 as 1 + r / rho.
     static constexpr bool SHIFTED = FORM == F_COMP && KIND != K_ASS;
 
     // r of state k of policy i, scenario m, in FP64
     __device__ __forceinline__ double dval(int k, int i, int m) const {
         const double x = T::dbl(V[k][i][m]);
-        if constexpr (SHIFTED) {
-            if (KIND == K_ANN || k == 1) return x - 1.0;
-            if (k == 2) return T::dbl(rho[i]) * (x - 1.0);
-        }
+        if constexpr (SHIFTED) return k == 2 ? T::dbl(rho[i]) * (x - 1.0) : x - 1.0;
         return x;
     }
 
+    // (the state is selected among compile-time indices: a runtime index into
+    // V would move the whole register array to local memory)
     __device__ __forceinline__ double out_state(int i, int m) const {
-        if constexpr (NS == 1) return dval(0, i, m);
-        else return dval(st0[i] == 0 ? 0 : (st0[i] == 1 ? 1 : 2), i, m);
+        if constexpr (NS == 1) {
+            return dval(0, i, m);
+        } else {
+            const double x0 = dval(0, i, m), x1 = dval(1, i, m), x2 = dval(2, i, m);
+            return st0[i] == 0 ? x0 : (st0[i] == 1 ? x1 : x2);
+        }
     }
 
     // traj / pt_mean side outputs of r_t for policy i (diagnostic runs only)

@@ -17,6 +17,7 @@
 #include "rsv.h"
 #include "ctx.cuh"
 #include "nested.cuh"
+#include "scan.cuh"
 
 using namespace rsv;
 
@@ -350,18 +351,23 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     int nv = 0;
     const Variant* vl = variant_list(o->form, &nv);
     const bool extra = (outs & (RSV_OUT_PT_MEAN | RSV_OUT_TRAJ)) != 0;
+    const bool scan = o->variant == RSV_VARIANT_TIME_SCAN;
+    if (scan && o->form != F_F64) return fail(c, RSV_E_ARG, "the time-scan variant runs the FP64 form");
+    if (scan && (outs & RSV_OUT_PT_MEAN)) return fail(c, RSV_E_ARG, "the time-scan variant has no per-step means");
     int vi;
-    if (extra) {
+    if (extra || scan) {
         vi = nv - 1;
     } else if (o->variant >= 0) {
         if (o->variant >= nv - 1) return fail(c, RSV_E_ARG, "variant %d out of range", o->variant);
         vi = o->variant;
-    } else {
+    } else if (o->variant == -1) {
         vi = c->tuned[o->form] >= 0 ? c->tuned[o->form] : 0;
+    } else {
+        return fail(c, RSV_E_ARG, "variant %d out of range", o->variant);
     }
     const Variant& V = vl[vi];
 
-    rsv_status st = build_layout(c, V.P, o->horizon, c->n_steps);
+    rsv_status st = build_layout(c, scan ? 1 : V.P, o->horizon, c->n_steps);
     if (st != RSV_OK) return st;
     size_t smem = 0;
     if ((st = build_tables(c, o->form, smem)) != RSV_OK) return st;
@@ -400,7 +406,7 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     a.tile_kind = L.kinds.as<int32_t>();
     a.amount = c->d_amount.as<double>();
     a.n_tiles = L.n_tiles;
-    a.n_chunks = (NSc + 32 * V.M - 1) / (32 * V.M);
+    a.n_chunks = scan ? NSc : (NSc + 32 * V.M - 1) / (32 * V.M);   // the scan: one chain per item
     const long long items = (long long)L.n_tiles * a.n_chunks;
     if (items > 0x7fffffffLL) return fail(c, RSV_E_ARG, "too many work items (%lld)", items);
     a.n_items = (int32_t)items;
@@ -413,15 +419,21 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     a.traj = traj;
 
     if (L.n_tiles > 0) {
-        int bps = 0;
-        CU(V.occupancy(&bps, smem));
-        if (bps < 1) return fail(c, RSV_E_CUDA, "variant %s cannot be resident with %zu B smem", V.name, smem);
-        const long long warps_needed = items;
-        long long grid = (long long)c->sm_count * bps;
-        grid = std::max(1LL, std::min(grid, (warps_needed * 32 + V.NT - 1) / V.NT));
-        CU(cudaEventRecord(c->ev0, c->stream));
-        CU(V.launch(a, (int)grid, smem, c->stream));
-        CU(cudaEventRecord(c->ev1, c->stream));
+        if (scan) {
+            CU(cudaEventRecord(c->ev0, c->stream));
+            CU(launch_scan(a, c->sm_count, smem, c->stream));
+            CU(cudaEventRecord(c->ev1, c->stream));
+        } else {
+            int bps = 0;
+            CU(V.occupancy(&bps, smem));
+            if (bps < 1) return fail(c, RSV_E_CUDA, "variant %s cannot be resident with %zu B smem", V.name, smem);
+            const long long warps_needed = items;
+            long long grid = (long long)c->sm_count * bps;
+            grid = std::max(1LL, std::min(grid, (warps_needed * 32 + V.NT - 1) / V.NT));
+            CU(cudaEventRecord(c->ev0, c->stream));
+            CU(V.launch(a, (int)grid, smem, c->stream));
+            CU(cudaEventRecord(c->ev1, c->stream));
+        }
         c->ev_recorded = true;
         if (tot) {
             const int G = 256, groups = (L.n_tiles + G - 1) / G;

@@ -119,6 +119,19 @@ __device__ __forceinline__ df df_one_plus_mul(df g, df R) {
     return df{h, e};
 }
 
+// c + g R for float c >= 1 and df g, R >= 0: the product as in df_mul, then
+// the head sum ordered by magnitude (Fast2Sum) and the tails added.
+__device__ __forceinline__ df df_float_plus_mul(float c, df g, df R) {
+    const float p = __fmul_rn(g.h, R.h);
+    float e = __fmaf_rn(g.h, R.h, -p);
+    e = __fmaf_rn(g.h, R.l, e);
+    e = __fmaf_rn(g.l, R.h, e);
+    const float hi = fmaxf(p, c), lo = fminf(p, c);
+    const float s = __fadd_rn(hi, lo);
+    const float err = __fsub_rn(lo, __fsub_rn(s, hi));
+    return df{s, __fadd_rn(err, e)};
+}
+
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.h + (double)a.l; }
 
 // ------------------------------------------------------------------------

@@ -235,8 +235,10 @@ __device__ double sur_base_value(const PolSur& P, const SurTables& T, int g, int
         if (state == 2) return P.rho * ann(P.tab2, y);
         const double ax = ann(P.tab1, x), ay = ann(P.tab2, y);
         if (!(ax > 0.0) || !(ay > 0.0)) return ax + P.rho * ay;
-        const double e = log1p(1.0 / ax) + log1p(1.0 / ay) - (SUR_COMM_LO + g * SUR_COMM_STEP) / 12.0;
-        const double axy = e > 0.0 ? fmin(1.0 / expm1(e), fmin(ax, ay)) : fmin(ax, ay);
+        // an estimate: FP32 is ample (train and inference use the same function)
+        const float e = log1pf((float)(1.0 / ax)) + log1pf((float)(1.0 / ay)) -
+                        (float)((SUR_COMM_LO + g * SUR_COMM_STEP) / 12.0);
+        const double axy = e > 0.0f ? fmin((double)(1.0f / expm1f(e)), fmin(ax, ay)) : fmin(ax, ay);
         return ax + P.rho * (ay - axy);
     }
     const double* D = col(P.tab1);
@@ -249,18 +251,24 @@ __device__ double sur_base_value(const PolSur& P, const SurTables& T, int g, int
 // ln of the base value at the query's own flat rate: the Vasicek yield to
 // half the remaining term (between one month and 15 years), interpolated
 // linearly in ln between the two neighbouring grid rates.  Returns the yield
-// through *delta.  0 where the base value is not positive.
+// through *delta.  0 where the base value is not positive.  The yield and the
+// logarithms are FP32 (the same deterministic function at training and at
+// inference; its rounding, ~1e-7, is far below the network's error); the
+// commutation ratios stay FP64.
 __device__ double sur_ln_base(const PolSur& P, const SurTables& T, const SurQuery& Q, double* delta) {
     const int n = P.S - Q.m;
-    const double h = min(max(n / 2, 1), 180) / 12.0;
-    const double d = -vasicek_lnP(h, Q.r, T.a, T.b, T.sigma) / h;
+    const float h = min(max(n / 2, 1), 180) / 12.0f;
+    const float a = (float)T.a, B = -expm1f(-a * h) / a;
+    const float lnP = (B - h) * (float)((T.a * T.a * T.b - 0.5 * T.sigma * T.sigma) / (T.a * T.a)) -
+                      (float)(T.sigma * T.sigma / (4.0 * T.a)) * B * B - B * (float)Q.r;
+    const double d = (double)(-lnP / h);
     *delta = d;
     const double u = fmin(fmax((d - SUR_COMM_LO) / SUR_COMM_STEP, 0.0), (double)(SUR_COMM_N - 1));
     const int g0 = min((int)u, SUR_COMM_N - 2);
     const double f = u - g0;
     const double b0 = sur_base_value(P, T, g0, Q.m, Q.state), b1 = sur_base_value(P, T, g0 + 1, Q.m, Q.state);
     if (!(b0 > 0.0) || !(b1 > 0.0)) return 0.0;
-    return (1.0 - f) * log(b0) + f * log(b1);
+    return (1.0 - f) * (double)logf((float)b0) + f * (double)logf((float)b1);
 }
 
 // A feature row as exact hi + lo BF16 halves (the first layer's weights are
@@ -297,11 +305,11 @@ __global__ void sur_features_kernel(const PolSur* __restrict__ pols, const SurTa
         f[9] = jl ? (float)P.rho : 0.0f;
         f[10] = rem;
         f[11] = rr;
-        f[12] = (float)((log(fmax(P.amount, 1e-30)) - 9.0) / 2.0);
+        f[12] = (logf((float)fmax(P.amount, 1e-30)) - 9.0f) / 2.0f;
         f[13] = age1 * age1;
         f[14] = rem * rem;
         f[15] = rr * rem;
-        f[16] = (float)(log1p((double)(P.S - Q.m)) / 7.0);
+        f[16] = log1pf((float)(P.S - Q.m)) / 7.0f;
         f[17] = (float)(base / 4.0);
         f[18] = (float)((delta - 0.04) / 0.02);
         sur_store_features(f, X + i * MLP_XW);

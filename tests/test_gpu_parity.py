@@ -239,3 +239,92 @@ def test_config2_full_size_sampled(ctx):
     assert err.max() <= 1e-6
     host_sum = V0.double().sum(dim=0).cpu().numpy()
     assert np.max(np.abs(tot.cpu().numpy() - host_sum) / host_sum) <= 1e-9
+
+
+@pytest.mark.parametrize("form", [rsv.RSV_FORM_F32, rsv.RSV_FORM_F32_COMP])
+def test_config5_full_size_sampled(ctx, form):
+    """1,000,000 single-life annuities (ages 60-90) x 1,000 Vasicek scenarios x
+    600 monthly steps (50 years: the projection is truncated there with
+    r_600 = 0), plain batched FP32 and compensated FP32, device outputs: 4 GB
+    of V0.  Sampled policies against the oracle with the same horizon; the
+    FP64 totals against the FP64 sum of V0."""
+    tab = synth.gm_monthly_survival()
+    n = 1_000_000
+    pol = synth.portfolio_single_life(n, seed=5)
+    v = synth.vasicek_paths(1000, 600, seed=5)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    V0 = torch.empty((n, 1000), dtype=torch.float32, device="cuda")
+    tot = torch.empty(1000, dtype=torch.float64, device="cuda")
+    rsv.rsv_compute_reserves(ctx, form, V0T, horizon=600, on_device=True, V0=V0, scen_total=tot)
+    rsv.rsv_synchronize(ctx)
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(n, 200, replace=False))
+    sub = synth.take(pol, idx)
+    ref, _ = oracle.reserves_batch(sub, tab, v, horizon=600)
+    got = V0[torch.as_tensor(idx, device="cuda")].double().cpu().numpy()
+    err = rel_err(got, ref, sub["amount"])
+    print(f"config-5 sampled, form {rsv.FORM_NAMES[form]}: max rel err {err.max():.3e}")
+    assert err.max() <= (1e-6 if form == rsv.RSV_FORM_F32_COMP else TOL[form])
+    host_sum = V0.double().sum(dim=0).cpu().numpy()
+    assert np.max(np.abs(tot.cpu().numpy() - host_sum) / host_sum) <= 1e-9
+    del V0
+
+
+def test_time_scan_config1(ctx):
+    """The parallel-in-time scan (one warp per chain, lanes over blocks of
+    steps) on config 1: 1,000 annuities under one flat rate, FP64."""
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_single_life(1000, seed=0)
+    v = synth.flat_scenarios(n_steps=720)
+    V0, tot = run(ctx, pol, tab, v, rsv.RSV_FORM_F64, variant=rsv.RSV_VARIANT_TIME_SCAN)
+    ref, ref_tot = oracle.reserves_batch(pol, tab, v)
+    err = rel_err(V0, ref, pol["amount"])
+    print(f"time scan config 1: max rel err {err.max():.3e}")
+    assert err.max() <= 1e-12
+    assert abs(tot[0] - ref_tot[0]) <= 1e-12 * ref_tot[0]
+
+
+def test_time_scan_mix_trajectory_and_horizon(ctx):
+    """The scan on every product and JL state (state0 0, 1, 2), 5 Vasicek
+    scenarios: r_t at every t against the oracle's full-state recurrence, and a
+    truncated horizon against the oracle's."""
+    tab = synth.gm_monthly_survival()
+    base = synth.portfolio_mix(24, seed=9)
+    jl = np.where(base["product"] == 1)[0]
+    extra = synth.take(base, np.concatenate([jl, jl]))
+    extra["state0"][: len(jl)] = 1
+    extra["state0"][len(jl):] = 2
+    pol = {k: np.concatenate([base[k], extra[k]]) for k in base}
+    n = len(pol["product"])
+    v = synth.vasicek_paths(5, 1200, seed=9)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    T = v.shape[1]
+    traj = np.zeros((n, T + 1, 5))
+    rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_TRAJ, variant=rsv.RSV_VARIANT_TIME_SCAN, traj=traj)
+    worst = 0.0
+    for p in range(n):
+        for s in range(5):
+            r = oracle.chain(int(pol["product"][p]), int(pol["age1_m"][p]), float(pol["amount"][p]), tab, v[s],
+                             age2=int(pol["age2_m"][p]), term=int(pol["term_m"][p]), rho=float(pol["reversion"][p]))
+            ref = r[:, int(pol["state0"][p])]
+            S = len(ref) - 1
+            scale = np.maximum(np.abs(ref), 1e-9 * pol["amount"][p])
+            worst = max(worst, float(np.max(np.abs(traj[p, : S + 1, s] - ref) / scale)))
+            assert np.all(traj[p, S + 1:, s] == 0.0)
+    print(f"time scan trajectory: max rel err {worst:.3e}")
+    assert worst <= 1e-12
+    V0, _ = run(ctx, pol, tab, v, rsv.RSV_FORM_F64, horizon=240, variant=rsv.RSV_VARIANT_TIME_SCAN)
+    ref, _ = oracle.reserves_batch(pol, tab, v, horizon=240)
+    assert rel_err(V0, ref, pol["amount"]).max() <= 1e-12
+    for form in (rsv.RSV_FORM_F32, rsv.RSV_FORM_F32_COMP):
+        with pytest.raises(rsv.RsvError) as e:
+            run(ctx, pol, tab, v, form, variant=rsv.RSV_VARIANT_TIME_SCAN)
+        assert e.value.status == rsv.RSV_E_ARG
+    with pytest.raises(rsv.RsvError) as e:
+        rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_PT_MEAN, variant=rsv.RSV_VARIANT_TIME_SCAN,
+                                 pt_mean=np.zeros((n, T + 1)))
+    assert e.value.status == rsv.RSV_E_ARG
