@@ -281,6 +281,59 @@ def bench_config1(rsv, torch, tab, reps=20):
     return res
 
 
+FIG1_STEPS = (60, 120, 240, 360, 480, 600, 720)
+FIG1_WORKLOAD = ("the paper's algorithm comparison (Section 5.2): single-life annuities from age 60 with a term of "
+                 "S months, one flat 4% scenario, FP64, the reserve at every step; time per policy")
+
+
+def bench_figure1(rsv, torch, tab, n_pol=60_000, reps=3):
+    """Summation (O(S^2)) against recurrence (O(S)) as the projection length S
+    grows, on the GPU: the summation-definition kernel, the time scan and the
+    scenario-parallel recurrence kernel, each writing the whole trajectory."""
+    v = synth.flat_scenarios(n_steps=max(FIG1_STEPS))
+    ctx = rsv.rsv_create(torch.cuda.current_device(), torch.cuda.current_stream())
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_scenarios(ctx, v)
+    traj = torch.empty((n_pol, v.shape[1] + 1, 1), dtype=torch.float64, device="cuda")
+    res = {"workload": FIG1_WORKLOAD + f" ({n_pol} policies)", "S": list(FIG1_STEPS),
+           "gpu_summation_us": [], "gpu_time_scan_us": [], "gpu_recurrence_us": []}
+    for S in FIG1_STEPS:
+        pol = synth.portfolio_single_life(n_pol, seed=0, age_lo_y=60, age_hi_y=60)
+        pol["term_m"][:] = S
+        rsv.rsv_load_portfolio(ctx, pol)
+        for key, var in (("gpu_summation_us", rsv.RSV_VARIANT_SUMMATION), ("gpu_time_scan_us", rsv.RSV_VARIANT_TIME_SCAN),
+                         ("gpu_recurrence_us", -1)):
+            ms = []
+            for i in range(reps + 1):
+                rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_TRAJ, on_device=True, variant=var,
+                                         traj=traj)
+                if i > 0:
+                    ms.append(rsv.rsv_last_kernel_ms(ctx))
+            res[key].append(statistics.median(ms) * 1e3 / n_pol)
+    rsv.rsv_destroy(ctx)
+    del traj
+    return res
+
+
+def cpu_figure1(tab, n_pol=2000):
+    """The same comparison for the FP64 CPU oracle (its summation and its
+    recurrence, every step, all host cores): time per policy."""
+    import oracle
+    oracle.build()
+    v = synth.flat_scenarios(n_steps=max(FIG1_STEPS))
+    threads = os.cpu_count() or 1
+    res = {"workload": FIG1_WORKLOAD + f" ({n_pol} policies)", "cores": threads, "S": list(FIG1_STEPS),
+           "cpu_summation_us": [], "cpu_recurrence_us": []}
+    for S in FIG1_STEPS:
+        pol = synth.portfolio_single_life(n_pol, seed=0, age_lo_y=60, age_hi_y=60)
+        pol["term_m"][:] = S
+        for key, method in (("cpu_summation_us", "summation"), ("cpu_recurrence_us", "recurrence")):
+            t0 = time.perf_counter()
+            oracle.reserves_batch(pol, tab, v, nthreads=threads, method=method, totals=False)
+            res[key].append((time.perf_counter() - t0) * 1e6 / n_pol)
+    return res
+
+
 SURROGATE_WORKLOAD = ("MLP surrogate of the inner-loop expectation: 32->4x256->1 GELU, BF16 weights and activations, "
                       "FP32 accumulation, trained on 10M recurrence labels of the 100,000-policy mix, scored on 1M "
                       "held-out queries")
@@ -482,9 +535,10 @@ def main():
                "ms_per_step": 1e3 * tot_s / args.steps}
 
     rsv.rsv_destroy(ctx)
-    nested = config1 = None
+    nested = config1 = figure1 = None
     if not args.no_nested and rank == 0:
         config1 = bench_config1(rsv, torch, tab)
+        figure1 = bench_figure1(rsv, torch, tab)
         nested = bench_nested(rsv, torch, tab, steps=2, warmup=1, n_outer=args.nested_outer,
                               sur_epochs=args.nested_surrogate_epochs)
     surrogate = None
@@ -499,6 +553,8 @@ def main():
     cpu, errs = (None, {})
     if not args.no_cpu:
         cpu, errs = cpu_baseline(pol, tab, v, args.cpu_sample, sample_rows)
+        if figure1 is not None:
+            figure1["cpu_oracle"] = cpu_figure1(tab)
     for f in results:
         results[f].update(errs.get(f, {}))
 
@@ -525,6 +581,7 @@ def main():
         "clocks": clocks,
         "forms": results,
         "config1_latency": config1,
+        "summation_vs_recurrence": figure1,
         "nested": nested,
         "surrogate": surrogate,
     }

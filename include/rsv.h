@@ -106,6 +106,14 @@ typedef struct {
  * per-scenario totals and the trajectory (not per-step means). */
 #define RSV_VARIANT_TIME_SCAN (-2)
 
+/* rsv_opts.variant: the reserves by their summation definition
+ * (Eq. basicReserveSummation, Section 3.8.1), O(S^2) per chain: one thread per
+ * step t sums the discounted, matrix-weighted cash flows of steps t .. S-1.
+ * For measuring the summation against the recurrence; its results equal the
+ * recurrence's to rounding.  FP64 form only; outputs V0, the per-scenario
+ * totals and the trajectory (not per-step means). */
+#define RSV_VARIANT_SUMMATION (-3)
+
 typedef struct {
     int32_t form;      /* RSV_FORM_*                                                   */
     int32_t outputs;   /* RSV_OUT_* bits                                               */
@@ -115,7 +123,8 @@ typedef struct {
                           asynchronous on the context stream; 0: host pointers, the
                           call blocks until the results are in host memory            */
     int32_t variant;   /* kernel variant index, -1 = the tuned/default one (see
-                          rsv_variant_count / rsv_tune), or RSV_VARIANT_TIME_SCAN     */
+                          rsv_variant_count / rsv_tune), RSV_VARIANT_TIME_SCAN or
+                          RSV_VARIANT_SUMMATION                                        */
     int32_t reserved[3];
 } rsv_opts;
 

@@ -68,6 +68,8 @@ def _load(path=None):
                                       C.c_int, dp, dp, dp, dp, C.c_int, dp, dp, C.c_int, C.c_int, dp]
             lib.orc_reserves_batch.argtypes = [i64, ip, ip, ip, ip, ip, ip, ip, dp, dp,
                                                i32, i32, dp, i32, i32, dp, i32, i32, dp, dp]
+            lib.orc_reserves_batch_method.argtypes = [i64, ip, ip, ip, ip, ip, ip, ip, dp, dp,
+                                                      i32, i32, dp, i32, i32, dp, i32, i32, i32, dp, dp]
             lib.orc_max_threads.restype = C.c_int
             if hasattr(lib, "orc_nested_node"):
                 _bind_nested(lib)
@@ -151,8 +153,10 @@ def chain(product: int, age1: int, amount: float, table_x, v, *, age2: int = 0, 
     return out[: (S + 1) * n].reshape(S + 1, n)
 
 
-def reserves_batch(pol: dict, tables, v, horizon: int = 0, nthreads: int = 0, totals: bool = True):
-    """V0[p, s] (FP64) of every policy in every scenario, f = 1, by the recurrence.
+def reserves_batch(pol: dict, tables, v, horizon: int = 0, nthreads: int = 0, totals: bool = True,
+                   method: str = "recurrence"):
+    """V0[p, s] (FP64) of every policy in every scenario, f = 1, by the recurrence
+    (or, with ``method="summation"``, by the summation definition at every step).
 
     ``pol`` is a dict of arrays as made by ``synth``; ``tables`` is [n_tables,
     n_ages] or [n_ages]; ``v`` is [n_scen, n_steps].  Returns (V0, scen_total).
@@ -165,12 +169,13 @@ def reserves_batch(pol: dict, tables, v, horizon: int = 0, nthreads: int = 0, to
     tot = np.zeros(v.shape[0]) if totals else None
     a = {k: _i(pol[k]) for k in ("product", "age1_m", "age2_m", "term_m", "state0", "table1", "table2")}
     amount, rho = _d(pol["amount"]), _d(pol["reversion"])
-    st = lib.orc_reserves_batch(n, _p(a["product"], C.c_int32), _p(a["age1_m"], C.c_int32),
-                                _p(a["age2_m"], C.c_int32), _p(a["term_m"], C.c_int32),
-                                _p(a["state0"], C.c_int32), _p(a["table1"], C.c_int32),
-                                _p(a["table2"], C.c_int32), _p(amount), _p(rho),
-                                tables.shape[0], tables.shape[1], _p(tables), v.shape[0], v.shape[1],
-                                _p(v), horizon, nthreads, _p(V0), _p(tot) if totals else None)
+    m = {"recurrence": 0, "summation": 1}[method]
+    st = lib.orc_reserves_batch_method(n, _p(a["product"], C.c_int32), _p(a["age1_m"], C.c_int32),
+                                       _p(a["age2_m"], C.c_int32), _p(a["term_m"], C.c_int32),
+                                       _p(a["state0"], C.c_int32), _p(a["table1"], C.c_int32),
+                                       _p(a["table2"], C.c_int32), _p(amount), _p(rho),
+                                       tables.shape[0], tables.shape[1], _p(tables), v.shape[0], v.shape[1],
+                                       _p(v), horizon, nthreads, m, _p(V0), _p(tot) if totals else None)
     if st != 0:
         raise ValueError(f"orc_reserves_batch failed with code {st}")
     return V0, tot

@@ -218,7 +218,9 @@ int orc_chain(int product, int age1, int age2, int term, double amount, double r
 }
 
 /* Reserves at valuation for a whole portfolio under n_scen scenarios, f = 1,
- * by the backward recurrence (method 0 of orc_chain).
+ * by the backward recurrence (method 0 of orc_chain) or, in
+ * orc_reserves_batch_method with method 1, by the summation definition
+ * evaluated at every step (the O(S^2) method the recurrence replaces).
  *
  * Policies are given as arrays (structure of arrays).  tables[n_tables *
  * n_ages] holds one-step survival p_k per table.  v[n_scen * n_steps] holds
@@ -228,14 +230,14 @@ int orc_chain(int product, int age1, int age2, int term, double amount, double r
  * order.  nthreads <= 0 uses the OpenMP default; policies are shared among
  * threads with a dynamic schedule.  Returns 0, or -1 bad record, -2 a
  * scenario shorter than a policy's projection. */
-int orc_reserves_batch(int64_t n_pol, const int32_t *product, const int32_t *age1,
-                       const int32_t *age2, const int32_t *term, const int32_t *state0,
-                       const int32_t *tab1, const int32_t *tab2,
-                       const double *amount, const double *rho,
-                       int32_t n_tables, int32_t n_ages, const double *tables,
-                       int32_t n_scen, int32_t n_steps, const double *v,
-                       int32_t horizon, int32_t nthreads,
-                       double *V0, double *scen_total)
+int orc_reserves_batch_method(int64_t n_pol, const int32_t *product, const int32_t *age1,
+                              const int32_t *age2, const int32_t *term, const int32_t *state0,
+                              const int32_t *tab1, const int32_t *tab2,
+                              const double *amount, const double *rho,
+                              int32_t n_tables, int32_t n_ages, const double *tables,
+                              int32_t n_scen, int32_t n_steps, const double *v,
+                              int32_t horizon, int32_t nthreads, int32_t method,
+                              double *V0, double *scen_total)
 {
     int status = 0;
     (void)nthreads;
@@ -263,7 +265,7 @@ int orc_reserves_batch(int64_t n_pol, const int32_t *product, const int32_t *age
             for (int32_t s = 0; s < n_scen; ++s) {
                 const double *vs = v + (size_t)s * n_steps;
                 int S = orc_chain(product[p], age1[p], age2[p], term[p], amount[p], rho[p],
-                                  n_ages, tx, ty, tx, ty, n_steps, vs, vs, horizon, 0, r);
+                                  n_ages, tx, ty, tx, ty, n_steps, vs, vs, horizon, method, r);
                 if (S < 0) {
 #ifdef _OPENMP
 #pragma omp critical
@@ -283,6 +285,20 @@ int orc_reserves_batch(int64_t n_pol, const int32_t *product, const int32_t *age
             for (int32_t s = 0; s < n_scen; ++s) scen_total[s] += V0[p * n_scen + s];
     }
     return status;
+}
+
+int orc_reserves_batch(int64_t n_pol, const int32_t *product, const int32_t *age1,
+                       const int32_t *age2, const int32_t *term, const int32_t *state0,
+                       const int32_t *tab1, const int32_t *tab2,
+                       const double *amount, const double *rho,
+                       int32_t n_tables, int32_t n_ages, const double *tables,
+                       int32_t n_scen, int32_t n_steps, const double *v,
+                       int32_t horizon, int32_t nthreads,
+                       double *V0, double *scen_total)
+{
+    return orc_reserves_batch_method(n_pol, product, age1, age2, term, state0, tab1, tab2, amount, rho,
+                                     n_tables, n_ages, tables, n_scen, n_steps, v, horizon, nthreads, 0,
+                                     V0, scen_total);
 }
 
 int orc_max_threads(void)

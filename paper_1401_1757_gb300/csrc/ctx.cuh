@@ -51,6 +51,7 @@ struct Layout {            // cached tiling for one (P, horizon, data generation
     unsigned long long gen = ~0ull;
     int n_tiles = 0, tab_pad = 0, n_tab = 0;
     double chain_steps = 0;  // sum over policies of S (per scenario)
+    int max_S = 0;           // longest projection
     DevBuf slots, kinds;
 };
 

@@ -18,6 +18,7 @@
 #include "ctx.cuh"
 #include "nested.cuh"
 #include "scan.cuh"
+#include "summation.cuh"
 
 using namespace rsv;
 
@@ -268,6 +269,8 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
     L.tab_pad = tab_pad;
     L.n_tab = n_tab;
     L.chain_steps = cs;
+    L.max_S = 0;
+    for (const PolPrep& q : pp) L.max_S = std::max(L.max_S, q.S);
     return RSV_OK;
 }
 
@@ -351,11 +354,13 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     int nv = 0;
     const Variant* vl = variant_list(o->form, &nv);
     const bool extra = (outs & (RSV_OUT_PT_MEAN | RSV_OUT_TRAJ)) != 0;
-    const bool scan = o->variant == RSV_VARIANT_TIME_SCAN;
-    if (scan && o->form != F_F64) return fail(c, RSV_E_ARG, "the time-scan variant runs the FP64 form");
-    if (scan && (outs & RSV_OUT_PT_MEAN)) return fail(c, RSV_E_ARG, "the time-scan variant has no per-step means");
+    const bool scan = o->variant == RSV_VARIANT_TIME_SCAN, summ = o->variant == RSV_VARIANT_SUMMATION;
+    if ((scan || summ) && o->form != F_F64) return fail(c, RSV_E_ARG, "the %s variant runs the FP64 form",
+                                                        scan ? "time-scan" : "summation");
+    if ((scan || summ) && (outs & RSV_OUT_PT_MEAN))
+        return fail(c, RSV_E_ARG, "the %s variant has no per-step means", scan ? "time-scan" : "summation");
     int vi;
-    if (extra || scan) {
+    if (extra || scan || summ) {
         vi = nv - 1;
     } else if (o->variant >= 0) {
         if (o->variant >= nv - 1) return fail(c, RSV_E_ARG, "variant %d out of range", o->variant);
@@ -367,7 +372,7 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     }
     const Variant& V = vl[vi];
 
-    rsv_status st = build_layout(c, scan ? 1 : V.P, o->horizon, c->n_steps);
+    rsv_status st = build_layout(c, (scan || summ) ? 1 : V.P, o->horizon, c->n_steps);
     if (st != RSV_OK) return st;
     size_t smem = 0;
     if ((st = build_tables(c, o->form, smem)) != RSV_OK) return st;
@@ -406,8 +411,10 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     a.tile_kind = L.kinds.as<int32_t>();
     a.amount = c->d_amount.as<double>();
     a.n_tiles = L.n_tiles;
-    a.n_chunks = scan ? NSc : (NSc + 32 * V.M - 1) / (32 * V.M);   // the scan: one chain per item
-    const long long items = (long long)L.n_tiles * a.n_chunks;
+    // the scan: one chain per item; the summation: one block of 32 steps of a chain per item
+    const int wpc = summ ? ((outs & RSV_OUT_TRAJ) ? (L.max_S + 1 + 31) / 32 : 1) : 1;
+    a.n_chunks = (scan || summ) ? NSc : (NSc + 32 * V.M - 1) / (32 * V.M);
+    const long long items = (long long)L.n_tiles * a.n_chunks * wpc;
     if (items > 0x7fffffffLL) return fail(c, RSV_E_ARG, "too many work items (%lld)", items);
     a.n_items = (int32_t)items;
     a.counter = c->d_ctl.as<int32_t>();
@@ -419,9 +426,10 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     a.traj = traj;
 
     if (L.n_tiles > 0) {
-        if (scan) {
+        if (scan || summ) {
             CU(cudaEventRecord(c->ev0, c->stream));
-            CU(launch_scan(a, c->sm_count, smem, c->stream));
+            if (scan) CU(launch_scan(a, c->sm_count, smem, c->stream));
+            else CU(launch_summation(a, wpc, c->sm_count, smem, c->stream));
             CU(cudaEventRecord(c->ev1, c->stream));
         } else {
             int bps = 0;

@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "RSV_OK", -1: "RSV_E_ARG", -2: "RSV_E_NOMEM", -3: "RSV_E_CUDA
 RSV_SL_ANNUITY, RSV_JL_REVERSIONARY, RSV_TERM_ASSURANCE, RSV_ENDOWMENT = 0, 1, 2, 3
 RSV_FORM_F64, RSV_FORM_F32, RSV_FORM_F32_COMP = 0, 1, 2
 RSV_VARIANT_TIME_SCAN = -2   # the FP64 parallel-in-time scan (see include/rsv.h)
+RSV_VARIANT_SUMMATION = -3   # the FP64 O(S^2) summation definition
 FORM_NAMES = {0: "f64", 1: "f32", 2: "f32comp"}
 RSV_OUT_V0, RSV_OUT_SCEN_TOTAL, RSV_OUT_PT_MEAN, RSV_OUT_TRAJ = 1, 2, 4, 8
 

@@ -328,3 +328,48 @@ def test_time_scan_mix_trajectory_and_horizon(ctx):
         rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_PT_MEAN, variant=rsv.RSV_VARIANT_TIME_SCAN,
                                  pt_mean=np.zeros((n, T + 1)))
     assert e.value.status == rsv.RSV_E_ARG
+
+
+def test_summation_variant_matches_oracle(ctx):
+    """The O(S^2) summation-definition kernel: r_t at every t of every product
+    and JL state against the oracle's summation, V0 of config 1, and errors."""
+    tab = synth.gm_monthly_survival()
+    base = synth.portfolio_mix(20, seed=10)
+    jl = np.where(base["product"] == 1)[0]
+    extra = synth.take(base, np.concatenate([jl, jl]))
+    extra["state0"][: len(jl)] = 1
+    extra["state0"][len(jl):] = 2
+    pol = {k: np.concatenate([base[k], extra[k]]) for k in base}
+    n = len(pol["product"])
+    v = synth.vasicek_paths(3, 1200, seed=10)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    T = v.shape[1]
+    traj = np.zeros((n, T + 1, 3))
+    V0 = np.zeros((n, 3))
+    rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_TRAJ | rsv.RSV_OUT_V0,
+                             variant=rsv.RSV_VARIANT_SUMMATION, traj=traj, V0d=V0)
+    worst = 0.0
+    for p in range(n):
+        for s in range(3):
+            r = oracle.chain(int(pol["product"][p]), int(pol["age1_m"][p]), float(pol["amount"][p]), tab, v[s],
+                             age2=int(pol["age2_m"][p]), term=int(pol["term_m"][p]), rho=float(pol["reversion"][p]),
+                             method="summation")
+            ref = r[:, int(pol["state0"][p])]
+            S = len(ref) - 1
+            scale = np.maximum(np.abs(ref), 1e-9 * pol["amount"][p])
+            worst = max(worst, float(np.max(np.abs(traj[p, : S + 1, s] - ref) / scale)))
+            assert np.all(traj[p, S + 1:, s] == 0.0)
+            assert V0[p, s] == traj[p, 0, s]
+    print(f"summation kernel trajectory: max rel err {worst:.3e}")
+    assert worst <= 1e-12
+    cpol = synth.portfolio_single_life(1000, seed=0)
+    cv = synth.flat_scenarios(n_steps=720)
+    got, tot = run(ctx, cpol, tab, cv, rsv.RSV_FORM_F64, variant=rsv.RSV_VARIANT_SUMMATION)
+    ref, ref_tot = oracle.reserves_batch(cpol, tab, cv, method="summation")
+    assert rel_err(got, ref, cpol["amount"]).max() <= 1e-12
+    assert abs(tot[0] - ref_tot[0]) <= 1e-12 * ref_tot[0]
+    with pytest.raises(rsv.RsvError) as e:
+        run(ctx, cpol, tab, cv, rsv.RSV_FORM_F32_COMP, variant=rsv.RSV_VARIANT_SUMMATION)
+    assert e.value.status == rsv.RSV_E_ARG
