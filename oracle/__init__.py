@@ -26,6 +26,7 @@ _lock = threading.Lock()
 _lib = None
 
 SL_ANNUITY, JL_REVERSIONARY, TERM_ASSURANCE, ENDOWMENT = 0, 1, 2, 3
+JOINT_ANNUITY, LAST_SURVIVOR, JOINT_TERM, JOINT_ENDOWMENT = 4, 5, 6, 7
 
 CFLAGS = ["-std=gnu99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp"]
 

@@ -179,7 +179,7 @@ int orc_nested_node(int64_t n_pol, const int32_t *prod, const int32_t *ipol, con
             double rS[4];
             int S = orc_steps(product, a1, a2, term, n_ages, 0, 1.0, rS);
             if (S < m) continue;                                  /* ended before the node */
-            const int annuity = product == 0 || product == 1;
+            const int annuity = product == 0 || product == 1 || product == 4 || product == 5;
             if (annuity && term > 0 && term <= m) continue;       /* limited-term annuity over */
             const double *tx = tables + (size_t)ip[4] * n_ages, *ty = tables + (size_t)ip[5] * n_ages;
             /* full-state distribution at the node: e_{state0} times the one-step matrices */

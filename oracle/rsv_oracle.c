@@ -41,18 +41,33 @@
 
 #define ORC_MAXN 4
 
-enum { ORC_SL_ANNUITY = 0, ORC_JL_REVERSIONARY = 1, ORC_TERM_ASSURANCE = 2, ORC_ENDOWMENT = 3 };
+enum {
+    ORC_SL_ANNUITY = 0, ORC_JL_REVERSIONARY = 1, ORC_TERM_ASSURANCE = 2, ORC_ENDOWMENT = 3,
+    /* two-life products built from the same state models (Section 4.2 and the
+     * assurance model of Section 4.1.3 applied to the joint status) */
+    ORC_JOINT_ANNUITY = 4,       /* paid while both lives are alive            */
+    ORC_LAST_SURVIVOR = 5,       /* paid while at least one life is alive      */
+    ORC_JOINT_TERM = 6,          /* sum paid at the end of the step of the first death */
+    ORC_JOINT_ENDOWMENT = 7      /* the same, or at maturity if both are alive */
+};
+
+static int two_state_life(int product) { return product == ORC_JL_REVERSIONARY || product == ORC_JOINT_ANNUITY || product == ORC_LAST_SURVIVOR; }
 
 /* Number of survival states of the product's full model (Section 4):
  * single life alive/dead (4.1), single life alive/died-in-step/dead for
- * assurances (4.1.3), two lives 00/01/10/11 (4.2). */
+ * assurances (4.1.3), two lives 00/01/10/11 (4.2); the joint-status
+ * assurances use the assurance model with "alive" = both alive. */
 int orc_n_states(int product)
 {
     switch (product) {
     case ORC_SL_ANNUITY: return 2;
-    case ORC_JL_REVERSIONARY: return 4;
+    case ORC_JL_REVERSIONARY:
+    case ORC_JOINT_ANNUITY:
+    case ORC_LAST_SURVIVOR: return 4;
     case ORC_TERM_ASSURANCE:
-    case ORC_ENDOWMENT: return 3;
+    case ORC_ENDOWMENT:
+    case ORC_JOINT_TERM:
+    case ORC_JOINT_ENDOWMENT: return 3;
     default: return -1;
     }
 }
@@ -69,11 +84,16 @@ int orc_transition(int product, double px, double py, double *W)
     if (product == ORC_SL_ANNUITY) {            /* Eq. (two state, single life) */
         W[0 * 2 + 0] = px; W[0 * 2 + 1] = qx;
         W[1 * 2 + 1] = 1.0;
-    } else if (product == ORC_JL_REVERSIONARY) {  /* Section 4.2, binary labels */
+    } else if (two_state_life(product)) {         /* Section 4.2, binary labels */
         W[0 * 4 + 0] = px * py; W[0 * 4 + 1] = px * qy; W[0 * 4 + 2] = qx * py; W[0 * 4 + 3] = qx * qy;
         W[1 * 4 + 1] = px; W[1 * 4 + 3] = qx;
         W[2 * 4 + 2] = py; W[2 * 4 + 3] = qy;
         W[3 * 4 + 3] = 1.0;
+    } else if (product == ORC_JOINT_TERM || product == ORC_JOINT_ENDOWMENT) {
+        /* three states of the joint status: both alive / first death in the step / after */
+        W[0 * 3 + 0] = px * py; W[0 * 3 + 1] = 1.0 - px * py;
+        W[1 * 3 + 2] = 1.0;
+        W[2 * 3 + 2] = 1.0;
     } else {                                     /* Eq. (three state, single life) */
         W[0 * 3 + 0] = px; W[0 * 3 + 1] = qx;
         W[1 * 3 + 2] = 1.0;
@@ -85,7 +105,10 @@ int orc_transition(int product, double px, double py, double *W)
 /* Nominal cash-flow vector c_{x,t} (paid at t+f according to the state then).
  *   SL annuity (4.1.1):        (A, 0)
  *   JL reversionary (4.2.1):   (A, A, rho*A, 0): A while (x) lives, rho*A to (y) after (x) dies
- *   term / endowment (4.1.3):  (0, A, 0): benefit in the "died in step" state */
+ *   joint-life annuity:        (A, 0, 0, 0): while both live
+ *   last-survivor annuity:     (A, A, A, 0): while either lives
+ *   term / endowment (4.1.3) and their joint-status forms:
+ *                              (0, A, 0): benefit in the "died in step" state */
 int orc_cashflow(int product, double amount, double rho, double *c)
 {
     int n = orc_n_states(product);
@@ -93,6 +116,8 @@ int orc_cashflow(int product, double amount, double rho, double *c)
     for (int k = 0; k < n; ++k) c[k] = 0.0;
     if (product == ORC_SL_ANNUITY) c[0] = amount;
     else if (product == ORC_JL_REVERSIONARY) { c[0] = amount; c[1] = amount; c[2] = rho * amount; }
+    else if (product == ORC_JOINT_ANNUITY) c[0] = amount;
+    else if (product == ORC_LAST_SURVIVOR) { c[0] = amount; c[1] = amount; c[2] = amount; }
     else c[1] = amount;
     return n;
 }
@@ -109,9 +134,16 @@ int orc_steps(int product, int age1, int age2, int term, int n_ages, int horizon
 {
     int n = orc_n_states(product), S;
     if (n < 0) return -1;
-    if (product == ORC_SL_ANNUITY || product == ORC_JL_REVERSIONARY) {
-        int young = (product == ORC_JL_REVERSIONARY && age2 < age1) ? age2 : age1;
+    if (product == ORC_SL_ANNUITY || product == ORC_JL_REVERSIONARY || product == ORC_LAST_SURVIVOR) {
+        /* paid while some life can be alive: to the younger life's limiting age */
+        int young = (product != ORC_SL_ANNUITY && age2 < age1) ? age2 : age1;
         S = n_ages - young;
+        if (S < 0) S = 0;
+        if (term > 0 && term < S) S = term;
+    } else if (product == ORC_JOINT_ANNUITY) {
+        /* paid while both can be alive: to the older life's limiting age */
+        int old = age2 > age1 ? age2 : age1;
+        S = n_ages - old;
         if (S < 0) S = 0;
         if (term > 0 && term < S) S = term;
     } else {
@@ -120,7 +152,7 @@ int orc_steps(int product, int age1, int age2, int term, int n_ages, int horizon
     for (int k = 0; k < n; ++k) rS[k] = 0.0;
     if (horizon > 0 && horizon < S) {
         S = horizon;                          /* truncated: r_S = 0 */
-    } else if (product == ORC_ENDOWMENT) {
+    } else if (product == ORC_ENDOWMENT || product == ORC_JOINT_ENDOWMENT) {
         rS[0] = amount;
     }
     return S;

@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(NT) nested_kernel(const NestedArgs a) {
         const int n = item / (a.n_chunks * a.B);
         const int m = n * a.node_step;
         const VE* plane = static_cast<const VE*>(a.v) + ((size_t)ol * a.n_nodes + n) * a.Lmax * a.i_pad;
-        const TileEnv env{a.slots, plane, a.i_pad, a.n_inner, 0, nullptr, nullptr, nullptr};
+        const TileEnv env{a.slots, plane, a.i_pad, a.n_inner, 0, nullptr, nullptr, nullptr, a.n_inner};
         const double* wts = a.wts + (size_t)n * 3;
         const size_t wstride = (size_t)a.n_nodes * 3;
         double acc[1] = {0.0};

@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(256) na_recur_kernel(unsigned char* scratch, i
     const NaLayout L = carve(scratch, n_pol, n_scen, n_steps);
     float4* tab = reinterpret_cast<float4*>(smem_raw);
     if (!stage_to_smem(tab, L.tab, (uint32_t)(kTabEntries * sizeof(float4)), &bar, &L.ctl[CTL_STATUS])) return;
-    const TileEnv env{L.slots, L.plane, scen_pad(n_scen), n_scen, n_steps, L.amount, nullptr, nullptr};
+    const TileEnv env{L.slots, L.plane, scen_pad(n_scen), n_scen, n_steps, L.amount, nullptr, nullptr, n_scen};
     const int n_chunks = (n_scen + 31) / 32;
     const long long n_items = (long long)n_pol * n_chunks;
     const int lane = threadIdx.x & 31;

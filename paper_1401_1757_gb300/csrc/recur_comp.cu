@@ -12,9 +12,6 @@ static const Variant kComp[] = {
     RSV_VARIANT(F_COMP, 1, 2, 256, 3, false, "comp P1xM2 nt256 min3"),
     RSV_VARIANT(F_COMP, 2, 1, 128, 6, false, "comp P2xM1 nt128 min6"),
     RSV_VARIANT(F_COMP, 4, 1, 128, 4, false, "comp P4xM1 nt128 min4"),
-    RSV_VARIANT(F_COMP, 8, 1, 256, 1, false, "comp P8xM1 nt256"),
-    RSV_VARIANT(F_COMP, 4, 2, 256, 1, false, "comp P4xM2 nt256"),
-    RSV_VARIANT(F_COMP, 6, 1, 256, 1, false, "comp P6xM1 nt256"),
     RSV_VARIANT(F_COMP, 2, 1, 256, 1, true, "comp P2xM1 nt256 side-outputs"),
 };
 const Variant* variants_comp(int* n) {

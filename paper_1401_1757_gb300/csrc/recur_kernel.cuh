@@ -153,6 +153,7 @@ struct TileEnv {
     const double* amount;
     double* traj;
     double* pt_sum;
+    int v0_ld;           // row stride of V0 (the caller's scenario count)
 };
 
 template <int FORM, int P, int M, int KIND, bool EXTRA>
@@ -329,7 +330,7 @@ struct Tile {
                 const int s = s0 + m;
                 if (s < e.n_valid) {
                     const double x = A * out_state(i, m);
-                    const size_t o = (size_t)pol[i] * e.n_valid + s;
+                    const size_t o = (size_t)pol[i] * e.v0_ld + s;
                     if (V0f) V0f[o] = (float)x;
                     if (V0d) V0d[o] = x;
                     part[m] += x;
@@ -375,7 +376,7 @@ __global__ void __launch_bounds__(NT, MINB) recur_kernel(const RecurArgs a) {
     TabE* tab = reinterpret_cast<TabE*>(smem_raw);
     if (!stage_to_smem(tab, a.tab, (uint32_t)a.tab_bytes, &bar, a.status)) return;
 
-    const TileEnv env{a.slots, a.v, a.s_pad, a.n_scen, a.n_steps, a.amount, a.traj, a.pt_sum};
+    const TileEnv env{a.slots, a.v, a.s_pad, a.n_scen, a.n_steps, a.amount, a.traj, a.pt_sum, a.v0_ld};
     const int lane = threadIdx.x & 31;
     for (;;) {
         int item = 0;

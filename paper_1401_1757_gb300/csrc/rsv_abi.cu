@@ -424,8 +424,55 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     a.partial = tot ? c->d_partial.as<double>() : nullptr;
     a.pt_sum = pt;
     a.traj = traj;
+    a.v0_ld = NSc;
 
-    if (L.n_tiles > 0) {
+    // Host V0 of the scenario-parallel kernels: computed in column blocks of
+    // scenarios, each block's V0 copied to the host on a second stream while
+    // the next block computes (the copy of the last block alone stays exposed).
+    const bool pipelined = !o->on_device && ((hV0f != nullptr) != (hV0d != nullptr)) && !extra && !scan && !summ &&
+                           L.n_tiles > 0 && NSc >= 256;
+    bool copied_v0 = false;
+    if (pipelined) {
+        const int blocks = std::min(4, NSc / 128);
+        const int width = ((NSc + blocks - 1) / blocks + 127) / 128 * 128;   // multiple of 128 scenario columns
+        if (!c->copy_stream) CU(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        if (!c->ev_block) CU(cudaEventCreateWithFlags(&c->ev_block, cudaEventDisableTiming));
+        int bps = 0;
+        CU(V.occupancy(&bps, smem));
+        if (bps < 1) return fail(c, RSV_E_CUDA, "variant %s cannot be resident with %zu B smem", V.name, smem);
+        const size_t esz_v = o->form == F_F64 ? sizeof(double) : (o->form == F_F32 ? sizeof(float) : sizeof(float2));
+        const size_t esz_o = hV0f ? sizeof(float) : sizeof(double);
+        char* dV0 = hV0f ? reinterpret_cast<char*>(V0f) : reinterpret_cast<char*>(V0d);
+        char* hV0 = hV0f ? reinterpret_cast<char*>(hV0f) : reinterpret_cast<char*>(hV0d);
+        CU(cudaEventRecord(c->ev0, c->stream));
+        for (int s0 = 0; s0 < NSc; s0 += width) {
+            const int w = std::min(width, NSc - s0);
+            RecurArgs b = a;
+            b.v = static_cast<const char*>(a.v) + (size_t)s0 * esz_v;
+            b.n_scen = w;
+            b.n_chunks = (w + 32 * V.M - 1) / (32 * V.M);
+            b.n_items = L.n_tiles * b.n_chunks;
+            b.V0f = a.V0f ? a.V0f + s0 : nullptr;
+            b.V0d = a.V0d ? a.V0d + s0 : nullptr;
+            b.partial = a.partial ? a.partial + s0 : nullptr;
+            long long grid = (long long)c->sm_count * bps;
+            grid = std::max(1LL, std::min(grid, ((long long)b.n_items * 32 + V.NT - 1) / V.NT));
+            CU(cudaMemsetAsync(c->d_ctl.p, 0, sizeof(int32_t), c->stream));
+            CU(V.launch(b, (int)grid, smem, c->stream));
+            CU(cudaEventRecord(c->ev_block, c->stream));
+            CU(cudaStreamWaitEvent(c->copy_stream, c->ev_block, 0));
+            CU(cudaMemcpy2DAsync(hV0 + (size_t)s0 * esz_o, (size_t)NSc * esz_o, dV0 + (size_t)s0 * esz_o,
+                                 (size_t)NSc * esz_o, (size_t)w * esz_o, (size_t)n_pol, cudaMemcpyDeviceToHost,
+                                 c->copy_stream));
+        }
+        CU(cudaEventRecord(c->ev1, c->stream));
+        CU(cudaEventRecord(c->ev_block, c->copy_stream));
+        CU(cudaStreamWaitEvent(c->stream, c->ev_block, 0));   // the call's stream sees the copies done
+        copied_v0 = true;
+        c->ev_recorded = true;
+    }
+
+    if (L.n_tiles > 0 && !pipelined) {
         if (scan || summ) {
             CU(cudaEventRecord(c->ev0, c->stream));
             if (scan) CU(launch_scan(a, c->sm_count, smem, c->stream));
@@ -443,6 +490,8 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
             CU(cudaEventRecord(c->ev1, c->stream));
         }
         c->ev_recorded = true;
+    }
+    if (L.n_tiles > 0) {
         if (tot) {
             const int G = 256, groups = (L.n_tiles + G - 1) / G;
             CU(c->d_part2.ensure((size_t)groups * c->s_pad * sizeof(double)));
@@ -459,8 +508,8 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
         }
     }
     if (!o->on_device) {
-        if (hV0f) CU(cudaMemcpyAsync(hV0f, V0f, n_v0 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
-        if (hV0d) CU(cudaMemcpyAsync(hV0d, V0d, n_v0 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (hV0f && !copied_v0) CU(cudaMemcpyAsync(hV0f, V0f, n_v0 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        if (hV0d && !copied_v0) CU(cudaMemcpyAsync(hV0d, V0d, n_v0 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         if (htot) CU(cudaMemcpyAsync(htot, tot, NSc * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         if (hpt) CU(cudaMemcpyAsync(hpt, pt, n_pt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         if (htraj) CU(cudaMemcpyAsync(htraj, traj, n_traj * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -733,6 +782,11 @@ rsv_status rsv_destroy(rsv_ctx* c) {
     c->mlp.release();
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->ev_block) cudaEventDestroy(c->ev_block);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
     delete c;
     return RSV_OK;
 }

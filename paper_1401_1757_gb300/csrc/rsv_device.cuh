@@ -54,6 +54,7 @@ struct RecurArgs {
     double* partial;          // [n_tiles][s_pad] per-tile scenario sums or null
     double* pt_sum;           // [n_pol][T+1] sums over scenarios or null
     double* traj;             // [n_pol][T+1][n_scen] or null
+    int32_t v0_ld;            // row stride of V0 (= n_scen unless a column block is computed)
 };
 
 // ------------------------------------------------------------------------

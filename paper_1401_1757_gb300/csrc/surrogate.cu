@@ -273,12 +273,22 @@ __device__ double sur_ln_base(const PolSur& P, const SurTables& T, const SurQuer
 
 // A feature row as exact hi + lo BF16 halves (the first layer's weights are
 // tied across the halves, so it sees each feature to ~16 bits).
+// The row is written as eight 16-byte stores (rows are 128-byte aligned).
 __device__ __forceinline__ void sur_store_features(const float (&f)[MLP_IN], __nv_bfloat16* row) {
+    uint32_t hi[MLP_IN / 2], lo[MLP_IN / 2];
 #pragma unroll
-    for (int k = 0; k < MLP_IN; ++k) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(f[k]);
-        row[k] = h;
-        row[MLP_IN + k] = __float2bfloat16_rn(f[k] - __bfloat162float(h));
+    for (int k = 0; k < MLP_IN; k += 2) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(f[k], f[k + 1]);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(f[k] - hf.x, f[k + 1] - hf.y);
+        hi[k / 2] = *reinterpret_cast<const uint32_t*>(&h);
+        lo[k / 2] = *reinterpret_cast<const uint32_t*>(&l);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(row);
+#pragma unroll
+    for (int q = 0; q < MLP_IN / 8; ++q) {
+        dst[q] = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
+        dst[MLP_IN / 8 + q] = make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
     }
 }
 

@@ -373,3 +373,33 @@ def test_summation_variant_matches_oracle(ctx):
     with pytest.raises(rsv.RsvError) as e:
         run(ctx, cpol, tab, cv, rsv.RSV_FORM_F32_COMP, variant=rsv.RSV_VARIANT_SUMMATION)
     assert e.value.status == rsv.RSV_E_ARG
+
+
+@pytest.mark.parametrize("n_scen", [300, 1000])
+def test_host_outputs_pipelined_equal_device_outputs(ctx, n_scen):
+    """With host V0 the library computes scenario column blocks and copies
+    each block while the next one computes; the results must be bit-identical
+    to the single launch with device outputs (FP32 and FP64 V0, totals)."""
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_mix(2000, seed=13)
+    v = synth.vasicek_paths(n_scen, 1200, seed=13)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    n = len(pol["product"])
+    for form in (rsv.RSV_FORM_F32_COMP, rsv.RSV_FORM_F32):
+        dV0 = torch.empty((n, n_scen), dtype=torch.float32, device="cuda")
+        dtot = torch.empty(n_scen, dtype=torch.float64, device="cuda")
+        rsv.rsv_compute_reserves(ctx, form, V0T, on_device=True, V0=dV0, scen_total=dtot)
+        rsv.rsv_synchronize(ctx)
+        hV0 = np.zeros((n, n_scen), np.float32)
+        htot = np.zeros(n_scen)
+        rsv.rsv_compute_reserves(ctx, form, V0T, V0=hV0, scen_total=htot)
+        assert np.array_equal(hV0, dV0.cpu().numpy())
+        assert np.array_equal(htot, dtot.cpu().numpy())
+        dV0d = torch.empty((n, n_scen), dtype=torch.float64, device="cuda")
+        rsv.rsv_compute_reserves(ctx, form, rsv.RSV_OUT_V0, on_device=True, V0d=dV0d)
+        rsv.rsv_synchronize(ctx)
+        hV0d = np.zeros((n, n_scen))
+        rsv.rsv_compute_reserves(ctx, form, rsv.RSV_OUT_V0, V0d=hV0d)
+        assert np.array_equal(hV0d, dV0d.cpu().numpy())

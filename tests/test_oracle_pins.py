@@ -410,3 +410,100 @@ def test_batch_summation_method_equals_recurrence():
     b, tb = oracle.reserves_batch(pol, tab, v, method="summation")
     assert np.max(np.abs(a - b) / np.maximum(np.abs(a), 1e-9 * pol["amount"][:, None])) <= 1e-12
     assert np.max(np.abs(ta - tb) / ta) <= 1e-12
+
+
+# ------------------------------------------------------ two-life products ----
+JOINT, LASTS, JTERM, JENDOW = (oracle.JOINT_ANNUITY, oracle.LAST_SURVIVOR, oracle.JOINT_TERM,
+                               oracle.JOINT_ENDOWMENT)
+
+
+def test_two_life_products_models():
+    """Joint-life and last-survivor annuities use the 4-state two-life matrix
+    (Section 4.2) with c = (A, 0, 0, 0) and (A, A, A, 0); the joint-status
+    assurances use the assurance model (Section 4.1.3) with survival px py."""
+    px, py = 0.9, 0.7
+    for prod in (JOINT, LASTS):
+        assert np.array_equal(oracle.transition(prod, px, py), oracle.transition(JL, px, py))
+    W = oracle.transition(JTERM, px, py)
+    assert np.allclose(W, [[px * py, 1 - px * py, 0], [0, 0, 1], [0, 0, 1]], rtol=0, atol=1e-16)
+    assert np.array_equal(oracle.cashflow(JOINT, 2.0), [2.0, 0, 0, 0])
+    assert np.array_equal(oracle.cashflow(LASTS, 2.0), [2.0, 2.0, 2.0, 0])
+    assert np.array_equal(oracle.cashflow(JENDOW, 3.0), [0, 3.0, 0])
+    for prod in (JOINT, LASTS, JTERM, JENDOW):
+        W = oracle.transition(prod, px, py)
+        assert np.allclose(W.sum(axis=1), 1.0, rtol=0, atol=1e-15) and np.all(np.tril(W, -1) == 0.0)
+
+
+@pytest.mark.parametrize("n", [1, 60, 300])
+def test_closed_forms_two_life_products(n):
+    """Flat rate, constant forces mux, muy, g = v px py: joint-life annuity
+    a_xy = g (1 - g^n) / (1 - g); last survivor a_x + a_y - a_xy; joint term
+    assurance v (1 - px py)(1 - g^n) / (1 - g); joint endowment adds g^n."""
+    mux, muy = 0.04, 0.09
+    px, py = math.exp(-mux / 12), math.exp(-muy / 12)
+    tx, ty = synth.constant_force_table(mux), synth.constant_force_table(muy)
+    v = np.full(n, V_FLAT)
+    A = 7.5
+    g = V_FLAT * px * py
+    axy = annuity_arrears(g, n)
+    ax, ay = annuity_arrears(V_FLAT * px, n), annuity_arrears(V_FLAT * py, n)
+    kw = dict(age2=200, term=n, table_y=ty)
+    assert rel(oracle.chain(JOINT, 100, A, tx, v, **kw)[0, 0], A * axy) < 1e-13
+    assert rel(oracle.chain(LASTS, 100, A, tx, v, **kw)[0, 0], A * (ax + ay - axy)) < 1e-13
+    jt = V_FLAT * (1 - px * py) * (1 - g ** n) / (1 - g)
+    assert rel(oracle.chain(JTERM, 100, A, tx, v, **kw)[0, 0], A * jt) < 1e-13
+    assert rel(oracle.chain(JENDOW, 100, A, tx, v, **kw)[0, 0], A * (jt + g ** n)) < 1e-13
+
+
+def enumerate_two_life(product, tx, ty, ax, ay, v, A, S, term):
+    """Two independent lives, enumerating both death steps (dx, dy in 0..S, S
+    meaning alive at the end): PV of the product's cash flows."""
+    disc = np.concatenate([[1.0], np.cumprod(v[:S])])
+
+    def dist(tab, age):
+        out, surv = [], 1.0
+        for d in range(S):
+            p = tab[age + d] if age + d < len(tab) else 0.0
+            out.append(surv * (1 - p))
+            surv *= p
+        out.append(surv)
+        return out
+
+    Px, Py = dist(tx, ax), dist(ty, ay)
+    total = 0.0
+    for dx, dy in itertools.product(range(S + 1), range(S + 1)):
+        prob = Px[dx] * Py[dy]
+        if prob == 0.0:
+            continue
+        pv = 0.0
+        first = min(dx, dy)
+        if product == JOINT:
+            pv = A * sum(disc[u + 1] for u in range(min(first, S)))
+        elif product == LASTS:
+            pv = A * sum(disc[u + 1] for u in range(min(max(dx, dy), S)))
+        else:
+            if first < S:
+                pv = A * disc[first + 1]          # end of the step of the first death
+            elif product == JENDOW and S == term:
+                pv = A * disc[S]                  # both alive at maturity
+        total += prob * pv
+    return total
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_brute_force_two_life_products(seed):
+    rng = np.random.default_rng(300 + seed)
+    n_ages = 14
+    tx, ty = rng.uniform(0.3, 0.999, n_ages), rng.uniform(0.3, 0.999, n_ages)
+    v = rng.uniform(0.85, 1.0, n_ages + 2)
+    for prod in (JOINT, LASTS, JTERM, JENDOW):
+        for ax, ay, term in [(0, 3, 8), (9, 4, 0), (2, 2, 5), (11, 6, 3)]:
+            if prod in (JTERM, JENDOW) and term == 0:
+                term = 6
+            A = float(rng.uniform(1, 50))
+            r = oracle.chain(prod, ax, A, tx, v, age2=ay, term=term, table_y=ty)
+            S = r.shape[0] - 1
+            want = enumerate_two_life(prod, tx, ty, ax, ay, v, A, S, term)
+            assert abs(r[0, 0] - want) <= 1e-14 * A, (prod, ax, ay, term)
+            s = oracle.chain(prod, ax, A, tx, v, age2=ay, term=term, table_y=ty, method="summation")
+            assert abs(s[0, 0] - want) <= 1e-14 * A, (prod, ax, ay, term)
