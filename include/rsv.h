@@ -24,6 +24,15 @@
  *   RSV_ENDOWMENT        endowment assurance: the term assurance plus the sum
  *                        at maturity if alive (Section 4.1.2 boundary
  *                        A_{x+n:0} = 1).
+ *   Two-life products on the same models (Section 4.2; the assurances use
+ *   the model of Section 4.1.3 on the joint status "both alive"):
+ *   RSV_JOINT_ANNUITY    A while both lives are alive: 1 reduced state,
+ *                        r = v px py (A + r'), to the older life's limiting age.
+ *   RSV_LAST_SURVIVOR    A while at least one life is alive: the RSV_JL_REVERSIONARY
+ *                        model with rho = 1 (the reversion field is ignored).
+ *   RSV_JOINT_TERM       the sum at the end of the month of the first death
+ *                        within the term: r = v ((1 - px py) S + px py r').
+ *   RSV_JOINT_ENDOWMENT  RSV_JOINT_TERM plus the sum at maturity if both are alive.
  *
  * Conventions shared by every entry point:
  *  - Status codes only; no C++ exception crosses the ABI.  On failure the
@@ -62,7 +71,10 @@ typedef enum {
     RSV_E_LIMIT = -7       /* sizes beyond the fixed scratch of rsv_reserves_noalloc  */
 } rsv_status;
 
-enum { RSV_SL_ANNUITY = 0, RSV_JL_REVERSIONARY = 1, RSV_TERM_ASSURANCE = 2, RSV_ENDOWMENT = 3 };
+enum {
+    RSV_SL_ANNUITY = 0, RSV_JL_REVERSIONARY = 1, RSV_TERM_ASSURANCE = 2, RSV_ENDOWMENT = 3,
+    RSV_JOINT_ANNUITY = 4, RSV_LAST_SURVIVOR = 5, RSV_JOINT_TERM = 6, RSV_JOINT_ENDOWMENT = 7
+};
 
 /* Arithmetic of the recurrence. */
 enum {
@@ -82,16 +94,16 @@ enum {
 
 /* One policy record (48 bytes). */
 typedef struct {
-    int32_t product;   /* RSV_SL_ANNUITY .. RSV_ENDOWMENT                              */
+    int32_t product;   /* RSV_SL_ANNUITY .. RSV_JOINT_ENDOWMENT                        */
     int32_t age1_m;    /* age of the (first) life at valuation, whole months >= 0      */
-    int32_t age2_m;    /* age of the second life; RSV_JL_REVERSIONARY only             */
+    int32_t age2_m;    /* age of the second life; two-life products only               */
     int32_t term_m;    /* term in months; 0 = whole life (annuities only); assurances
                           and endowments need term_m >= 0                              */
     int32_t state0;    /* reduced state at valuation: 0 for every product; the JL
-                          product also accepts 1 (only the first life alive) and 2
-                          (only the second life alive)                                 */
+                          and last-survivor products also accept 1 (only the first
+                          life alive) and 2 (only the second life alive)               */
     int32_t table1;    /* decrement table of the first life                            */
-    int32_t table2;    /* decrement table of the second life (JL only)                 */
+    int32_t table2;    /* decrement table of the second life (two-life products)       */
     int32_t reserved;  /* must be 0                                                    */
     double amount;     /* annuity amount per monthly step, or sum assured              */
     double reversion;  /* rho in [0, 1]; RSV_JL_REVERSIONARY only                      */
@@ -285,8 +297,9 @@ rsv_status rsv_compute_nested(rsv_ctx *ctx, const rsv_opts *opts, const rsv_nest
  * call re-initialises what it reads, but calls whose GPU work overlaps (other
  * streams or host threads) race on it: serialise them.  The call is issued on
  * `cuda_stream` (NULL = legacy default) and blocks until it has finished.
+ * It takes the single-table products RSV_SL_ANNUITY .. RSV_ENDOWMENT.
  * Errors: RSV_E_ARG (NULL pointer, bad size, a record the main entry point
- * would reject), RSV_E_LIMIT, RSV_E_ASSUMPTION (a table entry outside [0, 1], a
+ * would reject, a two-life product other than RSV_JL_REVERSIONARY), RSV_E_LIMIT, RSV_E_ASSUMPTION (a table entry outside [0, 1], a
  * discount factor not finite and positive), RSV_E_CUDA, RSV_E_TIMEOUT; on an
  * error the outputs are unspecified. */
 rsv_status rsv_reserves_noalloc(int device, void *cuda_stream, const rsv_policy *pols, int32_t n_pol,

@@ -1,6 +1,7 @@
 // ctx.cuh -- the library context shared by the translation units of the C ABI.
 #pragma once
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
@@ -39,6 +40,47 @@ struct DevBuf {
     T* as() const { return static_cast<T*>(p); }
 };
 
+// How a product maps onto the reduced models (Section 3.6.4): its kernel
+// kind, whether it reads a second life, and its number of projection steps
+// from the tables' lengths (the limiting ages) and the term.
+struct ProductModel {
+    int kind;          // K_ANN, K_ASS, K_JL, K_ANN2, K_ASS2
+    bool two_life;     // reads the second life's age and table
+    bool multi_state;  // the 3-state JL model (state0 may be 1 or 2)
+    bool annuity;      // paid while (some) life is alive; term_m 0 = to the limiting age
+    float bnd;         // boundary r_S per unit amount at maturity (endowments: 1)
+};
+
+inline bool product_model(int product, ProductModel& m) {
+    switch (product) {
+    case RSV_SL_ANNUITY: m = {K_ANN, false, false, true, 0.0f}; return true;
+    case RSV_JL_REVERSIONARY: m = {K_JL, true, true, true, 0.0f}; return true;
+    case RSV_TERM_ASSURANCE: m = {K_ASS, false, false, false, 0.0f}; return true;
+    case RSV_ENDOWMENT: m = {K_ASS, false, false, false, 1.0f}; return true;
+    case RSV_JOINT_ANNUITY: m = {K_ANN2, true, false, true, 0.0f}; return true;
+    case RSV_LAST_SURVIVOR: m = {K_JL, true, true, true, 0.0f}; return true;
+    case RSV_JOINT_TERM: m = {K_ASS2, true, false, false, 0.0f}; return true;
+    case RSV_JOINT_ENDOWMENT: m = {K_ASS2, true, false, false, 1.0f}; return true;
+    default: return false;
+    }
+}
+
+// Steps of a policy (len1, len2: its tables' lengths).  Reversionary and
+// last-survivor annuities run while either life can be alive, the joint-life
+// annuity while both can; term_m > 0 limits an annuity; assurances run for
+// their term.
+inline int product_steps(const rsv_policy& r, int len1, int len2) {
+    int S;
+    switch (r.product) {
+    case RSV_SL_ANNUITY: S = std::max(0, len1 - r.age1_m); break;
+    case RSV_JL_REVERSIONARY:
+    case RSV_LAST_SURVIVOR: S = std::max(0, std::max(len1 - r.age1_m, len2 - r.age2_m)); break;
+    case RSV_JOINT_ANNUITY: S = std::max(0, std::min(len1 - r.age1_m, len2 - r.age2_m)); break;
+    default: return r.term_m;
+    }
+    return r.term_m > 0 ? std::min(S, r.term_m) : S;
+}
+
 // One policy after validation: reduced model, steps, boundary.
 struct PolPrep {
     int kind, S, idx_age1, idx_age2, table1, table2, state0, pol;
@@ -52,6 +94,7 @@ struct Layout {            // cached tiling for one (P, horizon, data generation
     int n_tiles = 0, tab_pad = 0, n_tab = 0;
     double chain_steps = 0;  // sum over policies of S (per scenario)
     int max_S = 0;           // longest projection
+    bool has_two = false;    // two-life single-state tiles present
     DevBuf slots, kinds;
 };
 

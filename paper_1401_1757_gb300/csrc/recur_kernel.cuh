@@ -85,6 +85,13 @@ template <class R>
 __device__ __forceinline__ R step_ass(R v, R p, R q, R V) {  // v (q + p V)
     return p_mul(v, p_fma(p, V, q));
 }
+// Joint status "both alive" of two independent lives: p = px py and
+// q = 1 - px py = qx + px qy (the latter without cancellation).
+template <class R>
+__device__ __forceinline__ void joint_pq(R px, R qx, R py, R qy, R& p, R& q) {
+    p = p_mul(px, py);
+    q = p_fma(px, qy, qx);
+}
 template <class R>
 __device__ __forceinline__ void step_jl(R v, R px, R qx, R py, R qy, R rho, R& V00, R& V01, R& V10) {
     R gx = p_mul(v, px), gy = p_mul(v, py);
@@ -120,6 +127,11 @@ __device__ __forceinline__ df step_ann(df v, df p, df R) {
 }
 __device__ __forceinline__ df step_ass(df v, df p, df q, df V) {
     return df_mul(v, df_add_float_pos(df_mul(p, V), q.h));
+}
+// the joint survival as a double-float product; q enters one step additively (FP32 head)
+__device__ __forceinline__ void joint_pq(df px, df qx, df py, df qy, df& p, df& q) {
+    p = df_mul(px, py);
+    q = df{__fmaf_rn(px.h, qy.h, qx.h), 0.0f};
 }
 // V00 = R00 = 1 + r00; V01 = R01 = 1 + r01; V10 = A10 = 1 + r10 / rho.
 __device__ __forceinline__ void step_jl(df v, df px, df qx, df py, df qy, df rho, df& V00, df& V01,
@@ -208,7 +220,7 @@ struct Tile {
 
     // The compensated form carries annuity-type states shifted (see step_ann):
     // the ANN state and JL states 00 and 01 as 1 + r, JL state 10 as 1 + r / rho.
-    static constexpr bool SHIFTED = FORM == F_COMP && KIND != K_ASS;
+    static constexpr bool SHIFTED = FORM == F_COMP && (KIND == K_ANN || KIND == K_ANN2 || KIND == K_JL);
 
     // r of state k of policy i, scenario m, in FP64
     __device__ __forceinline__ double dval(int k, int i, int m) const {
@@ -262,6 +274,14 @@ struct Tile {
 #pragma unroll
                 for (int m = 0; m < M; ++m)
                     step_jl(T::v(vv.e[m]), px, qx, py, qy, rho[i], V[0][i][m], V[1][i][m], V[2][i][m]);
+            } else if constexpr (KIND == K_ANN2 || KIND == K_ASS2) {
+                const TabE e2 = tab[idx2[i] + t];
+                Val p, q;
+                joint_pq(px, qx, T::p(e2), T::q(e2), p, q);
+#pragma unroll
+                for (int m = 0; m < M; ++m)
+                    V[0][i][m] = KIND == K_ANN2 ? step_ann(T::v(vv.e[m]), p, V[0][i][m])
+                                                : step_ass(T::v(vv.e[m]), p, q, V[0][i][m]);
             } else if constexpr (KIND == K_ANN) {
 #pragma unroll
                 for (int m = 0; m < M; ++m) V[0][i][m] = step_ann(T::v(vv.e[m]), px, V[0][i][m]);
@@ -368,7 +388,19 @@ struct Tile {
     }
 };
 
-template <int FORM, int P, int M, int NT, int MINB, bool EXTRA>
+// One work item of one reduced model.
+template <int FORM, int P, int M, int KIND, bool EXTRA, class TabE>
+__device__ __forceinline__ void run_item(const TileEnv& env, const TabE* tab, int tile, int chunk, int lane,
+                                         const RecurArgs& a) {
+    Tile<FORM, P, M, KIND, EXTRA> w(env, tab, tile, chunk, lane);
+    w.run_steps();
+    w.epilogue_v0(tile, a.V0f, a.V0d, a.partial);
+}
+
+// TWO: the portfolio has two-life single-state tiles (K_ANN2, K_ASS2).  The
+// kernel is compiled with and without them: the three hot models alone keep
+// their register allocation free of spills.
+template <int FORM, int P, int M, int NT, int MINB, bool EXTRA, bool TWO>
 __global__ void __launch_bounds__(NT, MINB) recur_kernel(const RecurArgs a) {
     using TabE = typename Tr<FORM>::TabE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -386,18 +418,12 @@ __global__ void __launch_bounds__(NT, MINB) recur_kernel(const RecurArgs a) {
         const int tile = item / a.n_chunks;
         const int chunk = item - tile * a.n_chunks;
         const int kind = a.tile_kind[tile];
-        if (kind == K_JL) {
-            Tile<FORM, P, M, K_JL, EXTRA> w(env, tab, tile, chunk, lane);
-            w.run_steps();
-            w.epilogue_v0(tile, a.V0f, a.V0d, a.partial);
-        } else if (kind == K_ANN) {
-            Tile<FORM, P, M, K_ANN, EXTRA> w(env, tab, tile, chunk, lane);
-            w.run_steps();
-            w.epilogue_v0(tile, a.V0f, a.V0d, a.partial);
-        } else {
-            Tile<FORM, P, M, K_ASS, EXTRA> w(env, tab, tile, chunk, lane);
-            w.run_steps();
-            w.epilogue_v0(tile, a.V0f, a.V0d, a.partial);
+        if (kind == K_JL) run_item<FORM, P, M, K_JL, EXTRA>(env, tab, tile, chunk, lane, a);
+        else if (kind == K_ANN) run_item<FORM, P, M, K_ANN, EXTRA>(env, tab, tile, chunk, lane, a);
+        else if (!TWO || kind == K_ASS) run_item<FORM, P, M, K_ASS, EXTRA>(env, tab, tile, chunk, lane, a);
+        else if constexpr (TWO) {
+            if (kind == K_ANN2) run_item<FORM, P, M, K_ANN2, EXTRA>(env, tab, tile, chunk, lane, a);
+            else run_item<FORM, P, M, K_ASS2, EXTRA>(env, tab, tile, chunk, lane, a);
         }
     }
 }
@@ -407,31 +433,35 @@ struct Variant {
     int form, P, M, NT;
     bool extra;
     const char* name;
-    cudaError_t (*launch)(const RecurArgs&, int grid, size_t smem, cudaStream_t st);
-    cudaError_t (*occupancy)(int* blocks_per_sm, size_t smem);
+    // [0]: the three single-table/JL models; [1]: also the two-life single-state ones
+    cudaError_t (*launch[2])(const RecurArgs&, int grid, size_t smem, cudaStream_t st);
+    cudaError_t (*occupancy[2])(int* blocks_per_sm, size_t smem);
 };
 
-template <int FORM, int P, int M, int NT, int MINB, bool EXTRA>
+template <int FORM, int P, int M, int NT, int MINB, bool EXTRA, bool TWO>
 cudaError_t launch_recur(const RecurArgs& a, int grid, size_t smem, cudaStream_t st) {
-    auto k = recur_kernel<FORM, P, M, NT, MINB, EXTRA>;
+    auto k = recur_kernel<FORM, P, M, NT, MINB, EXTRA, TWO>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NT, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int FORM, int P, int M, int NT, int MINB, bool EXTRA>
+template <int FORM, int P, int M, int NT, int MINB, bool EXTRA, bool TWO>
 cudaError_t occupancy_recur(int* blocks, size_t smem) {
-    auto k = recur_kernel<FORM, P, M, NT, MINB, EXTRA>;
+    auto k = recur_kernel<FORM, P, M, NT, MINB, EXTRA, TWO>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, NT, smem);
 }
 
-#define RSV_VARIANT(FORM, P, M, NT, MINB, EXTRA, NAME)                          \
-    Variant {                                                                    \
-        FORM, P, M, NT, EXTRA, NAME, &launch_recur<FORM, P, M, NT, MINB, EXTRA>, \
-            &occupancy_recur<FORM, P, M, NT, MINB, EXTRA>                        \
+#define RSV_VARIANT(FORM, P, M, NT, MINB, EXTRA, NAME)                                              \
+    Variant {                                                                                        \
+        FORM, P, M, NT, EXTRA, NAME,                                                                 \
+            {&launch_recur<FORM, P, M, NT, MINB, EXTRA, false>, &launch_recur<FORM, P, M, NT, MINB, EXTRA, true>}, \
+        {                                                                                            \
+            &occupancy_recur<FORM, P, M, NT, MINB, EXTRA, false>, &occupancy_recur<FORM, P, M, NT, MINB, EXTRA, true> \
+        }                                                                                            \
     }
 
 // Each form's translation unit defines these.

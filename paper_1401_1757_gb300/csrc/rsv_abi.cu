@@ -138,31 +138,23 @@ rsv_status prep_policies(rsv_ctx* c, int horizon, int max_steps, std::vector<Pol
     for (int64_t i = 0; i < n; ++i) {
         const rsv_policy& r = c->pols[i];
         PolPrep& q = out[i];
-        if (r.product < RSV_SL_ANNUITY || r.product > RSV_ENDOWMENT || r.reserved != 0)
+        ProductModel pm;
+        if (!product_model(r.product, pm) || r.reserved != 0)
             return fail(c, RSV_E_ARG, "policy %lld: bad product %d", (long long)i, r.product);
-        const bool jl = r.product == RSV_JL_REVERSIONARY;
+        const bool two = pm.two_life;
         if (r.table1 < 0 || r.table1 >= kMaxTables || c->tab[r.table1].empty() ||
-            (jl && (r.table2 < 0 || r.table2 >= kMaxTables || c->tab[r.table2].empty())))
+            (two && (r.table2 < 0 || r.table2 >= kMaxTables || c->tab[r.table2].empty())))
             return fail(c, RSV_E_ARG, "policy %lld: decrement table not loaded", (long long)i);
-        if (r.age1_m < 0 || (jl && r.age2_m < 0) || r.term_m < 0)
+        if (r.age1_m < 0 || (two && r.age2_m < 0) || r.term_m < 0)
             return fail(c, RSV_E_ARG, "policy %lld: negative age or term", (long long)i);
-        if (r.state0 < 0 || r.state0 > (jl ? 2 : 0))
+        if (r.state0 < 0 || r.state0 > (pm.multi_state ? 2 : 0))
             return fail(c, RSV_E_ARG, "policy %lld: bad state0 %d", (long long)i, r.state0);
         if (!std::isfinite(r.amount))
             return fail(c, RSV_E_ASSUMPTION, "policy %lld: amount not finite", (long long)i);
-        if (jl && !(r.reversion >= 0.0 && r.reversion <= 1.0))
+        if (r.product == RSV_JL_REVERSIONARY && !(r.reversion >= 0.0 && r.reversion <= 1.0))
             return fail(c, RSV_E_ASSUMPTION, "policy %lld: reversion outside [0,1]", (long long)i);
-        int S;
-        if (r.product == RSV_SL_ANNUITY) {
-            S = std::max(0, table_len(c, r.table1) - r.age1_m);
-            if (r.term_m > 0) S = std::min(S, r.term_m);
-        } else if (jl) {   // payable while either life can be alive
-            S = std::max(0, std::max(table_len(c, r.table1) - r.age1_m, table_len(c, r.table2) - r.age2_m));
-            if (r.term_m > 0) S = std::min(S, r.term_m);
-        } else {
-            S = r.term_m;
-        }
-        float bnd = r.product == RSV_ENDOWMENT ? 1.0f : 0.0f;
+        int S = product_steps(r, table_len(c, r.table1), two ? table_len(c, r.table2) : 0);
+        float bnd = pm.bnd;
         if (horizon > 0 && horizon < S) {
             S = horizon;
             bnd = 0.0f;   // truncated projection: r_horizon = 0
@@ -170,21 +162,21 @@ rsv_status prep_policies(rsv_ctx* c, int horizon, int max_steps, std::vector<Pol
         if (S > max_steps)
             return fail(c, RSV_E_ASSUMPTION, "policy %lld: %d steps but scenarios have %d", (long long)i, S,
                         max_steps);
-        const int top = std::max(r.age1_m + S, jl ? r.age2_m + S : 0);
+        const int top = std::max(r.age1_m + S, two ? r.age2_m + S : 0);
         if (top > kMaxAgeSteps)
             return fail(c, RSV_E_ARG, "policy %lld: age + steps %d exceeds %d", (long long)i, top, kMaxAgeSteps);
         need = std::max(need, top);
-        n_tab = std::max(n_tab, std::max(r.table1, jl ? r.table2 : 0) + 1);
-        q.kind = jl ? K_JL : (r.product == RSV_SL_ANNUITY ? K_ANN : K_ASS);
+        n_tab = std::max(n_tab, std::max(r.table1, two ? r.table2 : 0) + 1);
+        q.kind = pm.kind;
         q.S = S;
         q.idx_age1 = r.age1_m;
-        q.idx_age2 = jl ? r.age2_m : 0;
+        q.idx_age2 = two ? r.age2_m : 0;
         q.table1 = r.table1;
-        q.table2 = jl ? r.table2 : 0;
+        q.table2 = two ? r.table2 : 0;
         q.state0 = r.state0;
         q.pol = (int)i;
         q.bnd = bnd;
-        q.rho = jl ? r.reversion : 0.0;
+        q.rho = r.product == RSV_JL_REVERSIONARY ? r.reversion : (r.product == RSV_LAST_SURVIVOR ? 1.0 : 0.0);
         chain_steps += S;
     }
     for (int t = 0; t < n_tab; ++t) need = std::max(need, table_len(c, t));
@@ -205,13 +197,15 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
     if (st != RSV_OK) return st;
 
     // group by reduced model, longest projection first
-    static const int kind_rank[3] = {1, 2, 0};   // JL tiles, then annuities, then assurances
-    std::vector<int> order(pp.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        if (pp[x].kind != pp[y].kind) return kind_rank[pp[x].kind] < kind_rank[pp[y].kind];
-        return pp[x].S > pp[y].S;
-    });
+    // JL tiles, then joint and single-life annuities, then assurances
+    static const int kind_rank[5] = {2, 4, 0, 1, 3};
+    // stable counting sort on (kind rank, S descending): S <= kMaxAgeSteps
+    const int nb = 5 * (kMaxAgeSteps + 1);
+    std::vector<int> bucket_start(nb + 1, 0), order(pp.size());
+    auto key = [&](const PolPrep& q) { return kind_rank[q.kind] * (kMaxAgeSteps + 1) + (kMaxAgeSteps - q.S); };
+    for (const PolPrep& q : pp) ++bucket_start[key(q) + 1];
+    for (int b = 0; b < nb; ++b) bucket_start[b + 1] += bucket_start[b];
+    for (size_t i = 0; i < pp.size(); ++i) order[bucket_start[key(pp[i])]++] = (int)i;
     std::vector<SlotRec> slots;
     std::vector<int> kinds;
     std::vector<double> cost;
@@ -240,14 +234,29 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
             slots.push_back(s);
         }
         kinds.push_back(kind);
-        const double w = kind == K_JL ? 4.5 : 1.0;
+        const double w = kind == K_JL ? 4.5 : (kind == K_ANN2 || kind == K_ASS2 ? 1.4 : 1.0);
         cost.push_back(w * slots[slots.size() - P].S);
     }
-    // tiles in decreasing cost order (longest-processing-time first)
+    // tiles in decreasing cost order (longest-processing-time first): the
+    // tiles of each kind are already in decreasing cost, so merge the runs
+    // (ties keep creation order)
     const int n_tiles = (int)kinds.size();
     std::vector<int> to(n_tiles);
-    for (int t = 0; t < n_tiles; ++t) to[t] = t;
-    std::stable_sort(to.begin(), to.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    {
+        std::vector<int> head, end;
+        for (int t = 0; t < n_tiles; ++t)
+            if (t == 0 || kinds[t] != kinds[t - 1]) {
+                if (t) end.push_back(t);
+                head.push_back(t);
+            }
+        if (n_tiles) end.push_back(n_tiles);
+        for (int out = 0; out < n_tiles; ++out) {
+            int best = -1;
+            for (size_t r = 0; r < head.size(); ++r)
+                if (head[r] < end[r] && (best < 0 || cost[head[r]] > cost[head[best]])) best = (int)r;
+            to[out] = head[best]++;
+        }
+    }
     std::vector<SlotRec> s2((size_t)n_tiles * P);
     std::vector<int> k2(n_tiles);
     for (int t = 0; t < n_tiles; ++t) {
@@ -259,8 +268,9 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
     CU(L.kinds.ensure(std::max<size_t>(1, k2.size()) * sizeof(int)));
     if (n_tiles) {
         CU(cudaMemcpyAsync(L.slots.p, s2.data(), s2.size() * sizeof(SlotRec), cudaMemcpyHostToDevice, c->stream));
+        // pageable sources: each copy is staged before the call returns, so the
+        // vectors may go out of scope without a stream synchronisation
         CU(cudaMemcpyAsync(L.kinds.p, k2.data(), k2.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-        CU(cudaStreamSynchronize(c->stream));
     }
     L.P = P;
     L.horizon = horizon;
@@ -270,7 +280,11 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
     L.n_tab = n_tab;
     L.chain_steps = cs;
     L.max_S = 0;
-    for (const PolPrep& q : pp) L.max_S = std::max(L.max_S, q.S);
+    L.has_two = false;
+    for (const PolPrep& q : pp) {
+        L.max_S = std::max(L.max_S, q.S);
+        L.has_two |= q.kind == K_ANN2 || q.kind == K_ASS2;
+    }
     return RSV_OK;
 }
 
@@ -302,8 +316,7 @@ rsv_status rsv::build_tables(rsv_ctx* c, int form, size_t& smem) {
         }
     }
     CU(c->d_tab[form].ensure(smem));
-    CU(cudaMemcpyAsync(c->d_tab[form].p, h.data(), smem, cudaMemcpyHostToDevice, c->stream));
-    CU(cudaStreamSynchronize(c->stream));
+    CU(cudaMemcpyAsync(c->d_tab[form].p, h.data(), smem, cudaMemcpyHostToDevice, c->stream));   // staged
     c->tab_pad_of[form] = pad;
     c->n_tab_of[form] = n_tab;
     c->tab_gen_of[form] = c->tab_gen;
@@ -319,7 +332,6 @@ rsv_status upload_amounts(rsv_ctx* c) {
     CU(c->d_amount.ensure(std::max<size_t>(1, a.size()) * sizeof(double)));
     if (!a.empty()) {
         CU(cudaMemcpyAsync(c->d_amount.p, a.data(), a.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        CU(cudaStreamSynchronize(c->stream));
     }
     c->amount_dirty = false;
     return RSV_OK;
@@ -425,6 +437,7 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     a.pt_sum = pt;
     a.traj = traj;
     a.v0_ld = NSc;
+    const int two = L.has_two ? 1 : 0;   // kernels compiled with the two-life single-state models
 
     // Host V0 of the scenario-parallel kernels: computed in column blocks of
     // scenarios, each block's V0 copied to the host on a second stream while
@@ -438,7 +451,7 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
         if (!c->copy_stream) CU(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
         if (!c->ev_block) CU(cudaEventCreateWithFlags(&c->ev_block, cudaEventDisableTiming));
         int bps = 0;
-        CU(V.occupancy(&bps, smem));
+        CU(V.occupancy[two](&bps, smem));
         if (bps < 1) return fail(c, RSV_E_CUDA, "variant %s cannot be resident with %zu B smem", V.name, smem);
         const size_t esz_v = o->form == F_F64 ? sizeof(double) : (o->form == F_F32 ? sizeof(float) : sizeof(float2));
         const size_t esz_o = hV0f ? sizeof(float) : sizeof(double);
@@ -458,7 +471,7 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
             long long grid = (long long)c->sm_count * bps;
             grid = std::max(1LL, std::min(grid, ((long long)b.n_items * 32 + V.NT - 1) / V.NT));
             CU(cudaMemsetAsync(c->d_ctl.p, 0, sizeof(int32_t), c->stream));
-            CU(V.launch(b, (int)grid, smem, c->stream));
+            CU(V.launch[two](b, (int)grid, smem, c->stream));
             CU(cudaEventRecord(c->ev_block, c->stream));
             CU(cudaStreamWaitEvent(c->copy_stream, c->ev_block, 0));
             CU(cudaMemcpy2DAsync(hV0 + (size_t)s0 * esz_o, (size_t)NSc * esz_o, dV0 + (size_t)s0 * esz_o,
@@ -480,13 +493,13 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
             CU(cudaEventRecord(c->ev1, c->stream));
         } else {
             int bps = 0;
-            CU(V.occupancy(&bps, smem));
+            CU(V.occupancy[two](&bps, smem));
             if (bps < 1) return fail(c, RSV_E_CUDA, "variant %s cannot be resident with %zu B smem", V.name, smem);
             const long long warps_needed = items;
             long long grid = (long long)c->sm_count * bps;
             grid = std::max(1LL, std::min(grid, (warps_needed * 32 + V.NT - 1) / V.NT));
             CU(cudaEventRecord(c->ev0, c->stream));
-            CU(V.launch(a, (int)grid, smem, c->stream));
+            CU(V.launch[two](a, (int)grid, smem, c->stream));
             CU(cudaEventRecord(c->ev1, c->stream));
         }
         c->ev_recorded = true;
@@ -561,33 +574,26 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
     std::vector<int> Ln(NN, 0), Sp(std::max(1, n_pol), 0);
     for (int p = 0; p < n_pol; ++p) {
         const rsv_policy& r = c->pols[p];
-        const bool jl = r.product == RSV_JL_REVERSIONARY, ann = r.product <= RSV_JL_REVERSIONARY;
-        int S;
-        if (r.product == RSV_SL_ANNUITY) {
-            S = std::max(0, table_len(c, r.table1) - r.age1_m);
-            if (r.term_m > 0) S = std::min(S, r.term_m);
-        } else if (jl) {
-            S = std::max(0, std::max(table_len(c, r.table1) - r.age1_m, table_len(c, r.table2) - r.age2_m));
-            if (r.term_m > 0) S = std::min(S, r.term_m);
-        } else {
-            S = r.term_m;
-        }
+        ProductModel pm;
+        product_model(r.product, pm);   // validated by build_layout
+        const bool jl = pm.multi_state, two = pm.two_life, ann = pm.annuity;
+        const int S = product_steps(r, table_len(c, r.table1), two ? table_len(c, r.table2) : 0);
         Sp[p] = S;
         const std::vector<double>& tx = c->tab[r.table1];
-        const std::vector<double>& ty = c->tab[jl ? r.table2 : r.table1];
+        const std::vector<double>& ty = c->tab[two ? r.table2 : r.table1];
         double Px = 1.0, Py = 1.0;
         int u = 0;
         for (int n = 0; n < NN; ++n) {
             const int m = n * step;
             for (; u < m; ++u) {
                 Px *= (r.age1_m + u < (int)tx.size()) ? tx[r.age1_m + u] : 0.0;
-                if (jl) Py *= (r.age2_m + u < (int)ty.size()) ? ty[r.age2_m + u] : 0.0;
+                if (two) Py *= (r.age2_m + u < (int)ty.size()) ? ty[r.age2_m + u] : 0.0;
             }
             if (S < m || (ann && r.term_m > 0 && r.term_m <= m)) continue;   // ended before the node
             Ln[n] = std::max(Ln[n], S - m);
             double* wp = &w[((size_t)p * NN + n) * 3];
             if (!jl) {
-                wp[0] = r.amount * Px;
+                wp[0] = two ? r.amount * Px * Py : r.amount * Px;   // joint products: both alive
             } else if (r.state0 == 0) {
                 wp[0] = r.amount * Px * Py;
                 wp[1] = r.amount * Px * (1.0 - Py);
@@ -659,7 +665,9 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
                     const double wj = w[((size_t)p * NN + n) * 3 + j];
                     if (wj == 0.0) continue;
                     if (Sp[p] == m) {   // matures at the node: its boundary value, no projection
-                        nbase[n] += c->pols[p].product == RSV_ENDOWMENT ? wj : 0.0;
+                        ProductModel pm;
+                        product_model(c->pols[p].product, pm);
+                        nbase[n] += pm.bnd * wj;
                         continue;
                     }
                     nq.push_back(rsv_query{p, m, j, 0, 0.0});

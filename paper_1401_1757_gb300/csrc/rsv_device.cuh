@@ -12,7 +12,9 @@ namespace rsv {
 enum Kind : int32_t {
     K_ANN = 0,  // 1 state, r = v p (c + r')            (Section 4.1.1)
     K_ASS = 1,  // 1 state, r = v (q c + p r')          (Section 4.1.3, reduced)
-    K_JL = 2    // 3 states 00, 01, 10 of the two-life model (Section 4.2)
+    K_JL = 2,   // 3 states 00, 01, 10 of the two-life model (Section 4.2)
+    K_ANN2 = 3, // 1 state, r = v px py (c + r')       (joint-life annuity)
+    K_ASS2 = 4  // 1 state, r = v ((1 - px py) c + px py r')  (joint-status assurance)
 };
 
 enum Form : int32_t { F_F64 = 0, F_F32 = 1, F_COMP = 2 };

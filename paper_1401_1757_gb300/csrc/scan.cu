@@ -74,12 +74,17 @@ struct StepMaps {
 
     __device__ __forceinline__ void at(int t, Aff1& m, int kind) const {
         const double vt = v[(size_t)t * s_pad];
-        const double2 e = tab[idx1 + t];
-        if (kind == K_ANN) {   // r = v p (1 + r')
-            const double g = vt * e.x;
+        double p = tab[idx1 + t].x, q = tab[idx1 + t].y;
+        if (kind == K_ANN2 || kind == K_ASS2) {   // joint status: p = px py, q = qx + px qy
+            const double2 ey = tab[idx2 + t];
+            q = q + p * ey.y;
+            p = p * ey.x;
+        }
+        if (kind == K_ANN || kind == K_ANN2) {   // r = v p (1 + r')
+            const double g = vt * p;
             m = Aff1{g, g};
-        } else {               // r = v (q + p r')
-            m = Aff1{vt * e.y, vt * e.x};
+        } else {                                 // r = v (q + p r')
+            m = Aff1{vt * q, vt * p};
         }
     }
     __device__ __forceinline__ void at(int t, Aff3& m, int) const {

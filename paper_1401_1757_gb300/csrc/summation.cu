@@ -23,12 +23,18 @@ __device__ double sum_reserve(const double2* tab, const double* v, int s_pad, co
     const int S = rec.S;
     const double rho = (double)rec.rho_h + (double)rec.rho_l;
     if (kind != K_JL) {
+        const bool joint = kind == K_ANN2 || kind == K_ASS2, ann = kind == K_ANN || kind == K_ANN2;
         double D = 1.0, r = 0.0;   // D = prod_{u=t}^{s-1} v_u p_u
         for (int s = t; s < S; ++s) {
             const double vs = v[(size_t)s * s_pad];
-            const double2 e = tab[rec.idx1 + s];
-            r += kind == K_ANN ? D * vs * e.x : D * vs * e.y;   // annuity: paid if alive at s+1; assurance: death in s
-            D *= vs * e.x;
+            double p = tab[rec.idx1 + s].x, q = tab[rec.idx1 + s].y;
+            if (joint) {   // joint status: p = px py, q = qx + px qy
+                const double2 ey = tab[rec.idx2 + s];
+                q = q + p * ey.y;
+                p = p * ey.x;
+            }
+            r += ann ? D * vs * p : D * vs * q;   // annuity: paid if alive at s+1; assurance: death in s
+            D *= vs * p;
         }
         return r + D * rec.bnd;
     }

@@ -431,6 +431,9 @@ rsv_status sur_tables(rsv_ctx* c, SurTables& T) {
 }
 
 rsv_status sur_upload_policies(rsv_ctx* c, std::vector<PolSur>& host) {
+    for (size_t i = 0; i < c->pols.size(); ++i)
+        if (c->pols[i].product > RSV_ENDOWMENT)
+            return fail(c, RSV_E_ARG, "policy %zu: the surrogate covers products 0-3 (SL, JL, term, endowment)", i);
     host.resize(c->pols.size());
     for (size_t i = 0; i < host.size(); ++i) {
         const rsv_policy& r = c->pols[i];

@@ -19,6 +19,7 @@ RSV_E_LIMIT = -7
 STATUS_NAMES = {0: "RSV_OK", -1: "RSV_E_ARG", -2: "RSV_E_NOMEM", -3: "RSV_E_CUDA", -4: "RSV_E_STATE",
                 -5: "RSV_E_TIMEOUT", -6: "RSV_E_ASSUMPTION", -7: "RSV_E_LIMIT"}
 RSV_SL_ANNUITY, RSV_JL_REVERSIONARY, RSV_TERM_ASSURANCE, RSV_ENDOWMENT = 0, 1, 2, 3
+RSV_JOINT_ANNUITY, RSV_LAST_SURVIVOR, RSV_JOINT_TERM, RSV_JOINT_ENDOWMENT = 4, 5, 6, 7
 RSV_FORM_F64, RSV_FORM_F32, RSV_FORM_F32_COMP = 0, 1, 2
 RSV_VARIANT_TIME_SCAN = -2   # the FP64 parallel-in-time scan (see include/rsv.h)
 RSV_VARIANT_SUMMATION = -3   # the FP64 O(S^2) summation definition

@@ -28,6 +28,10 @@ SL_ANNUITY = 0          # single-life level annuity, monthly in arrears (Section
 JL_REVERSIONARY = 1     # joint-life annuity with reversion rho to the second life (Section 4.2.1)
 TERM_ASSURANCE = 2      # level term assurance, benefit at end of month of death (Section 4.1.3)
 ENDOWMENT = 3           # endowment assurance: term assurance + maturity payment (Sections 4.1.2-4.1.3)
+JOINT_ANNUITY = 4       # paid while both lives are alive
+LAST_SURVIVOR = 5       # paid while at least one life is alive
+JOINT_TERM = 6          # sum at the end of the month of the first death within the term
+JOINT_ENDOWMENT = 7     # joint term assurance + maturity payment if both are alive
 
 PRODUCT_NAMES = {SL_ANNUITY: "sl_annuity", JL_REVERSIONARY: "jl_reversionary",
                  TERM_ASSURANCE: "term_assurance", ENDOWMENT: "endowment"}
@@ -116,6 +120,27 @@ def portfolio_mix(n: int = 100_000, seed: int = 0, age_lo_y: int = 20, age_hi_y:
     pol["amount"][:] = np.where(annuity, ann, sums)
     pol["reversion"][:] = np.where(prod == JL_REVERSIONARY, rng.uniform(0.5, 1.0, size=n), 0.0)
     pol["age2_m"][prod != JL_REVERSIONARY] = 0
+    return pol
+
+
+def portfolio_two_life(n: int = 10_000, seed: int = 0, age_lo_y: int = 20, age_hi_y: int = 85) -> dict:
+    """Equal shares of the two-life products: joint-life annuities, last-survivor
+    annuities, joint-life term assurances (terms 5-40 y) and joint-life
+    endowments (terms 10-30 y).  Both ages uniform over whole months in
+    [age_lo_y, age_hi_y] years; amounts as in ``portfolio_mix``."""
+    rng = np.random.default_rng([seed, 2])
+    prod = np.resize(np.arange(JOINT_ANNUITY, JOINT_ENDOWMENT + 1, dtype=np.int32), n)
+    rng.shuffle(prod)
+    pol = _policy_arrays(n)
+    pol["product"][:] = prod
+    pol["age1_m"][:] = rng.integers(age_lo_y * 12, age_hi_y * 12 + 1, size=n)
+    pol["age2_m"][:] = rng.integers(age_lo_y * 12, age_hi_y * 12 + 1, size=n)
+    term_y = np.where(prod == JOINT_TERM, rng.integers(5, 41, size=n),
+                      np.where(prod == JOINT_ENDOWMENT, rng.integers(10, 31, size=n), 0))
+    pol["term_m"][:] = term_y * 12
+    ann = rng.lognormal(math.log(1.0e4), 0.5, size=n) / 12.0
+    sums = rng.lognormal(math.log(1.0e5), 0.5, size=n)
+    pol["amount"][:] = np.where(prod <= LAST_SURVIVOR, ann, sums)
     return pol
 
 

@@ -180,3 +180,20 @@ def test_surrogate_mode_gain_over_brute_force(ctx):
     # the node liability is a positive combination of such values and of exact ones
     assert sur_err <= 2e-3
     assert speed > 10
+
+
+def test_nested_two_life_products_against_oracle(ctx):
+    """The nested valuation of the two-life products (joint and last-survivor
+    annuities, joint term assurances and endowments): every (o, n, i) of a
+    small run against the oracle's full-state node liabilities."""
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_two_life(40, seed=14, age_lo_y=50, age_hi_y=80)
+    spec = dict(n_outer=2, n_nodes=4, node_step_m=24, n_inner=40, seed=15)
+    out = nested(ctx, pol, tab, rsv.RSV_FORM_F32_COMP, **spec)
+    worst = 0.0
+    for o in range(2):
+        for n in range(4):
+            L, _, _ = oracle.nested_node(pol, tab, 15, o, n, np.arange(40), node_step=24)
+            worst = max(worst, float(np.max(np.abs(out["L_all"][o, n] - L) / np.abs(L))))
+    print(f"nested two-life products: max rel err {worst:.3e}")
+    assert worst <= 1e-6

@@ -403,3 +403,28 @@ def test_host_outputs_pipelined_equal_device_outputs(ctx, n_scen):
         hV0d = np.zeros((n, n_scen))
         rsv.rsv_compute_reserves(ctx, form, rsv.RSV_OUT_V0, V0d=hV0d)
         assert np.array_equal(hV0d, dV0d.cpu().numpy())
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_two_life_products(ctx, form):
+    """Joint-life and last-survivor annuities, joint term assurances and joint
+    endowments (two tables), mixed with the four single-table products, under
+    ragged Vasicek scenarios: against the oracle's full two-life models."""
+    tab = synth.gm_monthly_survival()
+    tab2 = synth.gm_monthly_survival(A=0.0004, B=0.00002)
+    two = synth.portfolio_two_life(240, seed=3)
+    two["table2"][:] = 1
+    pol = {k: np.concatenate([two[k], synth.portfolio_mix(60, seed=3)[k]]) for k in two}
+    v = synth.vasicek_paths(70, 1200, seed=3)
+    V0, tot = run(ctx, pol, tab, v, form, tables=[tab, tab2])
+    ref, ref_tot = oracle.reserves_batch(pol, np.stack([tab, tab2]), v)
+    err = rel_err(V0, ref, pol["amount"])
+    for p in range(8):
+        m = pol["product"] == p
+        print(f"two-life form {rsv.FORM_NAMES[form]} product {p}: max rel err {err[m].max():.3e}")
+    assert err.max() <= TOL[form]
+    assert np.max(np.abs(tot - ref_tot) / ref_tot) <= TOL[form]
+    if form == rsv.RSV_FORM_F64:   # the time scan and the summation kernel on the same products
+        for var in (rsv.RSV_VARIANT_TIME_SCAN, rsv.RSV_VARIANT_SUMMATION):
+            V0s, _ = run(ctx, pol, tab, v, form, variant=var, tables=[tab, tab2])
+            assert rel_err(V0s, ref, pol["amount"]).max() <= 1e-12
