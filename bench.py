@@ -334,6 +334,85 @@ def cpu_figure1(tab, n_pol=2000):
     return res
 
 
+C5 = dict(n_pol=1_000_000, n_scen=1000, n_steps=600, n_nodes=50, sample_pol=10_000, sample_outer=10)
+C5_WORKLOAD = ("full scale: 1,000,000 single-life annuities (ages 60-90) x 1,000 Vasicek scenarios x 600 monthly "
+               "steps (50 y); nested: 1,000 outer paths x 50 annual nodes x 1,000 inner paths")
+
+
+def bench_full_scale(rsv, torch, tab, sur_epochs=10, reps=3):
+    """(A) The plain batched recurrence at full scale, plain and compensated
+    FP32.  (B) The nested run with the surrogate (all 1,000 outer paths, a
+    policy sample, extrapolated by policies), the brute-force inner loop and
+    the closed-form curve (a sample of outer paths too, extrapolated by outer
+    paths and policies); node-liability errors against the curve on the
+    common sample."""
+    c = C5
+    res = {"workload": C5_WORKLOAD}
+    pol = synth.portfolio_single_life(c["n_pol"], seed=5)
+    v = synth.vasicek_paths(c["n_scen"], c["n_steps"], seed=5)
+    ctx = rsv.rsv_create(torch.cuda.current_device(), torch.cuda.current_stream())
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    V0 = torch.empty((c["n_pol"], c["n_scen"]), dtype=torch.float32, device="cuda")
+    tot = torch.empty(c["n_scen"], dtype=torch.float64, device="cuda")
+    outs = rsv.RSV_OUT_V0 | rsv.RSV_OUT_SCEN_TOTAL
+    for name, form in (("A_plain_f32", rsv.RSV_FORM_F32), ("A_compensated_f32", rsv.RSV_FORM_F32_COMP)):
+        rsv.rsv_tune(ctx, form, horizon=c["n_steps"], reps=1)
+        ms = []
+        for i in range(reps + 1):
+            rsv.rsv_compute_reserves(ctx, form, outs, horizon=c["n_steps"], on_device=True, V0=V0, scen_total=tot)
+            if i:
+                ms.append(rsv.rsv_last_kernel_ms(ctx))
+        t = statistics.median(ms)
+        res[name] = {"kernel_ms": t, "valuations_s": c["n_pol"] * c["n_scen"] / (t / 1e3)}
+    del V0
+    # (B) nested, on the first sample_pol policies
+    sub = synth.take(pol, slice(0, c["sample_pol"]))
+    rsv.rsv_load_portfolio(ctx, sub)
+    NN = c["n_nodes"]
+    t0 = time.perf_counter()
+    rsv.rsv_mlp_init(ctx, 0)
+    rep = rsv.rsv_surrogate_train(ctx, n_train=3_000_000, n_val=300_000, epochs=sur_epochs, batch=8192, lr=2e-3,
+                                  seed=5, max_node_m=(NN - 1) * 12)
+    train_s = time.perf_counter() - t0
+    scale_pol = c["n_pol"] / c["sample_pol"]
+    runs = {}
+    for name, mode, n_outer in (("surrogate", rsv.RSV_NESTED_SURROGATE, c["n_scen"]),
+                                ("surrogate_sample", rsv.RSV_NESTED_SURROGATE, c["sample_outer"]),
+                                ("brute_force", rsv.RSV_NESTED_MC, c["sample_outer"]),
+                                ("curve", rsv.RSV_NESTED_CURVE, c["sample_outer"])):
+        L = torch.empty((n_outer, NN), dtype=torch.float64, device="cuda")
+        q = torch.empty((n_outer, NN), dtype=torch.float64, device="cuda")
+        nfb = np.zeros(1, np.int64)
+        rsv.rsv_compute_nested(ctx, rsv.RSV_FORM_F32_COMP, n_outer=n_outer, n_nodes=NN, node_step_m=12, n_inner=1000,
+                               seed=5, mode=mode, on_device=True, L_mean=L, L_q995=q, n_fallback=nfb)
+        torch.cuda.synchronize()
+        runs[name] = (rsv.rsv_last_kernel_ms(ctx), L.cpu().numpy(), int(nfb[0]))
+    rsv.rsv_destroy(ctx)
+    full_outer = c["n_scen"] / c["sample_outer"]
+    exact = runs["curve"][1]
+    live = exact > 0
+    res["B_surrogate"] = {"measured_ms": runs["surrogate"][0], "measured_on": f"{c['sample_pol']} policies x "
+                          f"{c['n_scen']} outer x {NN} nodes", "fallback_queries": runs["surrogate"][2],
+                          "extrapolated_full_s": runs["surrogate"][0] * scale_pol / 1e3,
+                          "node_liability_max_rel_vs_curve":
+                              float(np.max(np.abs(runs["surrogate_sample"][1] - exact)[live] / exact[live])),
+                          "training_s": train_s, "held_out_median_rel": rep["val_median_rel"],
+                          "served_max_rel": rep["combined_max_rel"], "fallback_share": rep["frac_fallback"]}
+    res["B_brute_force"] = {"measured_ms": runs["brute_force"][0], "measured_on": f"{c['sample_pol']} policies x "
+                            f"{c['sample_outer']} outer x {NN} nodes x 1000 inner",
+                            "extrapolated_full_s": runs["brute_force"][0] * scale_pol * full_outer / 1e3,
+                            "node_liability_max_rel_vs_curve":
+                                float(np.max(np.abs(runs["brute_force"][1] - exact)[live] / exact[live]))}
+    res["B_curve"] = {"measured_ms": runs["curve"][0], "measured_on": f"{c['sample_pol']} policies x "
+                      f"{c['sample_outer']} outer x {NN} nodes",
+                      "extrapolated_full_s": runs["curve"][0] * scale_pol * full_outer / 1e3}
+    res["B_speedup_surrogate_vs_brute_force"] = (res["B_brute_force"]["extrapolated_full_s"] /
+                                                 res["B_surrogate"]["extrapolated_full_s"])
+    return res
+
+
 SURROGATE_WORKLOAD = ("MLP surrogate of the inner-loop expectation: 32->4x256->1 GELU, BF16 weights and activations, "
                       "FP32 accumulation, trained on 10M recurrence labels of the 100,000-policy mix, scored on 1M "
                       "held-out queries")
@@ -406,6 +485,7 @@ def main():
     ap.add_argument("--surrogate-train", type=int, default=10_000_000, help="training labels (profiling runs: fewer)")
     ap.add_argument("--surrogate-val", type=int, default=1_000_000, help="held-out queries")
     ap.add_argument("--nested-outer", type=int, default=NESTED["n_outer"], help="outer paths (profiling runs: fewer)")
+    ap.add_argument("--full-scale", action="store_true", help="also the 1M-policy full-scale configuration")
     ap.add_argument("--nested-surrogate-epochs", type=int, default=10,
                     help="train the surrogate on the nested portfolio and time its mode (0: skip)")
     args = ap.parse_args()
@@ -541,6 +621,14 @@ def main():
         figure1 = bench_figure1(rsv, torch, tab)
         nested = bench_nested(rsv, torch, tab, steps=2, warmup=1, n_outer=args.nested_outer,
                               sur_epochs=args.nested_surrogate_epochs)
+    full = None
+    if args.full_scale and rank == 0:
+        full = bench_full_scale(rsv, torch, tab)
+    peaks = None
+    if rank == 0:
+        peaks = {"fp32_fma_tflops": rsv.rsv_probe_fma_peak(local, None, False),
+                 "fp64_fma_tflops": rsv.rsv_probe_fma_peak(local, None, True),
+                 "how": "independent FMA chains on every SM, best of 5 launches"}
     surrogate = None
     if args.surrogate_epochs > 0 and rank == 0:
         surrogate = bench_surrogate(rsv, torch, tab, args.surrogate_epochs, lr=args.surrogate_lr,
@@ -566,6 +654,8 @@ def main():
             "kernel": f"recur_kernel ({h['variant']})",
             "peak_note": "FP32 FMA pipe, 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal units x max clock)",
             "flops_per_launch": flops}
+    if peaks:
+        roof["frac_of_measured_fma_peak"] = achieved / peaks["fp32_fma_tflops"]
     line = {
         "metric": METRIC, "value": h["valuations_s"], "unit": "valuations/s", "n_gpus": world,
         "steps": h["steps"], "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
@@ -575,6 +665,7 @@ def main():
                    "form": head, "variant": h["variant"], "l2": "flushed between timed steps (256 MiB write)",
                    "scenario_seed": "rank"},
         "roofline": roof,
+        "measured_alu_peaks": peaks,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": 3 * h["steps"],
@@ -582,6 +673,7 @@ def main():
         "forms": results,
         "config1_latency": config1,
         "summation_vs_recurrence": figure1,
+        "full_scale": full,
         "nested": nested,
         "surrogate": surrogate,
     }

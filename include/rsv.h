@@ -409,6 +409,13 @@ enum {
  * network for the network modes), RSV_E_CUDA, RSV_E_NOMEM. */
 rsv_status rsv_surrogate_query(rsv_ctx *ctx, const rsv_query *queries, int64_t n, int32_t how, double *reserve);
 
+/* Measured fused multiply-add throughput of `device` in TFLOP/s (2 flop per
+ * FMA): FP32 (fp64 = 0) or FP64 (fp64 = 1), from a kernel of independent FMA
+ * chains filling every SM, best of five timed launches on `cuda_stream`.  It
+ * is the measured denominator of the ALU rooflines; the paper has no
+ * counterpart.  Blocks until done.  Errors: RSV_E_ARG, RSV_E_CUDA, RSV_E_NOMEM. */
+rsv_status rsv_probe_fma_peak(int32_t device, void *cuda_stream, int32_t fp64, double *tflops);
+
 /* Kernel variants of a form (policies x scenarios per thread, CTA size):
  * how many there are, and a printable description of one. */
 int32_t rsv_variant_count(int32_t form);

@@ -675,42 +675,52 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
                 }
         }
         noff[NN] = (long long)nq.size();
-        const long long Qn = (long long)nq.size(), nq_all = Qn * NO;
-        // device: [V | w | queries | node lists | seg | base]
-        const size_t bytes = (size_t)std::max<long long>(1, nq_all) * (16 + sizeof(rsv_query)) +
+        const long long Qn = (long long)nq.size();
+        // outer paths in batches of at most ~32M queries; device per batch:
+        // [V | w | queries | seg | base], plus the node lists
+        const int Bo = (int)std::max(1LL, std::min<long long>(NO, Qn > 0 ? (32LL << 20) / Qn : NO));
+        const long long nq_b = Qn * Bo;
+        const size_t on_b = (size_t)Bo * NN;
+        const size_t bytes = (size_t)std::max<long long>(1, nq_b) * (16 + sizeof(rsv_query)) +
                              (size_t)std::max<long long>(1, Qn) * (sizeof(rsv_query) + 8) + (NN + 1) * 8 + NN * 8 +
-                             (on_n + 1) * 8 + on_n * 8 + 64;
+                             (on_b + 1) * 8 + on_b * 8 + 64;
         CU(c->d_nest_plane.ensure(bytes));
         char* cur = static_cast<char*>(c->d_nest_plane.p);
         auto take = [&](size_t n) { char* r = cur; cur += (n + 7) / 8 * 8; return r; };
-        double* dV = reinterpret_cast<double*>(take(std::max<long long>(1, nq_all) * 8));
-        double* dw = reinterpret_cast<double*>(take(std::max<long long>(1, nq_all) * 8));
-        rsv_query* dq = reinterpret_cast<rsv_query*>(take(std::max<long long>(1, nq_all) * sizeof(rsv_query)));
+        double* dV = reinterpret_cast<double*>(take(std::max<long long>(1, nq_b) * 8));
+        double* dw = reinterpret_cast<double*>(take(std::max<long long>(1, nq_b) * 8));
+        rsv_query* dq = reinterpret_cast<rsv_query*>(take(std::max<long long>(1, nq_b) * sizeof(rsv_query)));
         rsv_query* dnq = reinterpret_cast<rsv_query*>(take(std::max<long long>(1, Qn) * sizeof(rsv_query)));
         double* dnw = reinterpret_cast<double*>(take(std::max<long long>(1, Qn) * 8));
         long long* dnoff = reinterpret_cast<long long*>(take((NN + 1) * 8));
         double* dnbase = reinterpret_cast<double*>(take(NN * 8));
-        long long* dseg = reinterpret_cast<long long*>(take((on_n + 1) * 8));
-        double* dbase = reinterpret_cast<double*>(take(on_n * 8));
+        long long* dseg = reinterpret_cast<long long*>(take((on_b + 1) * 8));
+        double* dbase = reinterpret_cast<double*>(take(on_b * 8));
         if (Qn > 0) {
             CU(cudaMemcpyAsync(dnq, nq.data(), Qn * sizeof(rsv_query), cudaMemcpyHostToDevice, c->stream));
             CU(cudaMemcpyAsync(dnw, nw.data(), Qn * 8, cudaMemcpyHostToDevice, c->stream));
         }
         CU(cudaMemcpyAsync(dnoff, noff.data(), (NN + 1) * 8, cudaMemcpyHostToDevice, c->stream));
         CU(cudaMemcpyAsync(dnbase, nbase.data(), NN * 8, cudaMemcpyHostToDevice, c->stream));
-        node_segments_kernel<<<(unsigned)((on_n + 256) / 256), 256, 0, c->stream>>>(dnoff, dnbase, Qn, NO, NN, dseg,
-                                                                                  dbase);
-        CU(cudaGetLastError());
         long long nfb = 0;
-        if (nq_all > 0) {
-            expand_node_queries_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(dnq, dnw, Qn, NO, NN, step,
-                                                                               c->d_nest_rn.as<double>(), dq, dw);
+        for (int o0 = 0; o0 < NO; o0 += Bo) {
+            const int Bc = std::min(Bo, NO - o0);
+            const size_t on_c = (size_t)Bc * NN;
+            node_segments_kernel<<<(unsigned)((on_c + 256) / 256), 256, 0, c->stream>>>(dnoff, dnbase, Qn, Bc, NN,
+                                                                                      dseg, dbase);
             CU(cudaGetLastError());
-            st = sur_value_queries(c, dq, nq_all, dseg, (int)on_n, Lmax, dV, &nfb);
-            if (st != RSV_OK) return st;
+            if (Qn > 0) {
+                expand_node_queries_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(
+                    dnq, dnw, Qn, Bc, NN, step, c->d_nest_rn.as<double>() + (size_t)o0 * NN, dq, dw);
+                CU(cudaGetLastError());
+                long long nfb_c = 0;
+                st = sur_value_queries(c, dq, Qn * Bc, dseg, (int)on_c, Lmax, dV, &nfb_c);
+                if (st != RSV_OK) return st;
+                nfb += nfb_c;
+            }
+            segment_wsum_kernel<<<(unsigned)on_c, 256, 0, c->stream>>>(dseg, dw, dV, dbase, Lall + (size_t)o0 * NN);
+            CU(cudaGetLastError());
         }
-        segment_wsum_kernel<<<(unsigned)on_n, 256, 0, c->stream>>>(dseg, dw, dV, dbase, Lall);
-        CU(cudaGetLastError());
         if (out->n_fallback) *out->n_fallback = nfb;
     }
     for (int o0 = 0; o0 < NO && !sur; o0 += B) {

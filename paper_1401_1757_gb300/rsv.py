@@ -96,7 +96,8 @@ EXPORTS = ["rsv_create", "rsv_destroy", "rsv_set_stream", "rsv_load_decrements",
            "rsv_load_scenarios", "rsv_compute_reserves", "rsv_compute_nested", "rsv_variant_count", "rsv_variant_name",
            "rsv_tune", "rsv_synchronize", "rsv_last_error", "rsv_last_kernel_ms", "rsv_device_sm_count",
            "rsv_reserves_noalloc", "rsv_mlp_param_count", "rsv_mlp_init", "rsv_mlp_set_params",
-           "rsv_mlp_get_params", "rsv_mlp_set_backend", "rsv_mlp_forward", "rsv_mlp_gradient", "rsv_surrogate_train", "rsv_surrogate_query"]
+           "rsv_mlp_get_params", "rsv_mlp_set_backend", "rsv_mlp_forward", "rsv_mlp_gradient", "rsv_surrogate_train",
+           "rsv_surrogate_query", "rsv_probe_fma_peak"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -140,6 +141,7 @@ def load_library(path: str = LIB_PATH):
         "rsv_mlp_gradient": ([vp, vp, vp, i64, vp, vp], i32),
         "rsv_surrogate_train": ([vp, C.POINTER(rsv_surrogate_cfg), C.POINTER(rsv_surrogate_report)], i32),
         "rsv_surrogate_query": ([vp, vp, i64, i32, vp], i32),
+        "rsv_probe_fma_peak": ([i32, vp, i32, C.POINTER(C.c_double)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -240,6 +242,16 @@ def rsv_compute_nested(ctx, form: int = RSV_FORM_F32_COMP, *, n_outer: int, n_no
     sp = rsv_nested_spec(n_outer, n_nodes, node_step_m, n_inner, seed, a, b, sigma, r0, mode, batch_outer)
     out = rsv_nested_out(_ptr(L_mean), _ptr(L_q995), _ptr(r_node), _ptr(D0), _ptr(L_all), _ptr(n_fallback))
     _check(ctx, _lib.rsv_compute_nested(ctx, C.byref(o), C.byref(sp), C.byref(out)))
+
+
+def rsv_probe_fma_peak(device: int = 0, stream=None, fp64: bool = False) -> float:
+    """Measured FP32 (or FP64) FMA throughput of the device in TFLOP/s."""
+    lib = load_library()
+    out = C.c_double()
+    st = lib.rsv_probe_fma_peak(device, getattr(stream, "cuda_stream", stream), 1 if fp64 else 0, C.byref(out))
+    if st != RSV_OK:
+        raise RsvError(st, f"rsv_probe_fma_peak failed ({st})")
+    return out.value
 
 
 def rsv_variant_count(form: int) -> int:
