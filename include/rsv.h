@@ -109,6 +109,19 @@ typedef struct {
     double reversion;  /* rho in [0, 1]; RSV_JL_REVERSIONARY only                      */
 } rsv_policy;
 
+/* rsv_opts.payment: the fraction f of Eq. generalForm at which annuity cash
+ * flows are paid within each monthly step,
+ *     r_t = v_t^f W_{t,f} c_t + v_t W_{t,1} r_{t+1}.
+ * RSV_PAY_END: f = 1 (in arrears).  RSV_PAY_START: f = 0 (in advance,
+ * W_{t,0} = I).  RSV_PAY_FRACTION: 0 < f < 1, with the survival over the first
+ * fraction of each month from rsv_load_decrements_fraction (every loaded table
+ * needs one, of the same length) and the discount over it from
+ * rsv_load_scenarios_fraction (the loaded scenario set's shape).  Assurance
+ * benefits stay at the end of the month of death (Section 4.1.3 restricts
+ * them to f = 1).  The scenario-parallel kernels only; V0 and the totals,
+ * not the per-step outputs. */
+enum { RSV_PAY_END = 0, RSV_PAY_START = 1, RSV_PAY_FRACTION = 2 };
+
 /* rsv_opts.variant: the backward recurrence as a parallel-in-time scan.  Each
  * step of Eq. generalForm is an affine map of the next step's reserve vector;
  * one warp takes one chain (policy x scenario), its lanes compose the maps of
@@ -137,7 +150,9 @@ typedef struct {
     int32_t variant;   /* kernel variant index, -1 = the tuned/default one (see
                           rsv_variant_count / rsv_tune), RSV_VARIANT_TIME_SCAN or
                           RSV_VARIANT_SUMMATION                                        */
-    int32_t reserved[3];
+    int32_t payment;   /* RSV_PAY_*: when in each step the annuity cash flows are
+                          paid (0 = at the end, the default)                           */
+    int32_t reserved[2];
 } rsv_opts;
 
 /* Outputs of rsv_compute_reserves.  Any pointer may be NULL when its bit is
@@ -178,6 +193,22 @@ rsv_status rsv_set_stream(rsv_ctx *ctx, void *cuda_stream);
  * RSV_E_ASSUMPTION (an entry outside [0, 1] or not finite, Section 3.7.3). */
 rsv_status rsv_load_decrements(rsv_ctx *ctx, int32_t table_id, const double *p_monthly,
                                int32_t n_ages_m);
+
+/* Survival over the first fraction f of each month of table `table_id`:
+ * p_f[k] = probability of surviving from age k months to k + f months (host
+ * FP64, copied), for RSV_PAY_FRACTION (it populates W_{x,t,f}).  Survival is 0
+ * from age n_ages_m on.
+ * Errors: RSV_E_ARG (bad id, NULL, n_ages_m < 1 or > 4096),
+ * RSV_E_ASSUMPTION (an entry outside [0, 1] or not finite). */
+rsv_status rsv_load_decrements_fraction(rsv_ctx *ctx, int32_t table_id, const double *p_f, int32_t n_ages_m);
+
+/* Discount factors over the first fraction f of each step, v_f[s,t] = v_{s,t}^f
+ * in Eq. generalForm, for RSV_PAY_FRACTION; layout as rsv_load_scenarios
+ * (host FP64, copied).
+ * Errors: RSV_E_ARG (NULL, n_scen < 1, n_steps < 1, bad layout),
+ * RSV_E_ASSUMPTION (a factor not finite or <= 0). */
+rsv_status rsv_load_scenarios_fraction(rsv_ctx *ctx, const double *v_f, int32_t n_scen, int32_t n_steps,
+                                       int32_t layout);
 
 /* Load the portfolio: n records (host, copied).  Validation of the records
  * against the tables happens at compute time.

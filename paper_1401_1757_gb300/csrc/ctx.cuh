@@ -133,6 +133,8 @@ struct rsv_ctx {
 
     std::vector<double> tab[rsv::kMaxTables];
     unsigned long long tab_gen = 1;
+    std::vector<double> tabf[rsv::kMaxTables];   // survival over the first fraction of each month
+    unsigned long long tabf_gen = 1;
 
     std::vector<rsv_policy> pols;
     unsigned long long pol_gen = 1;
@@ -146,6 +148,10 @@ struct rsv_ctx {
     int tab_pad_of[3] = {-1, -1, -1};
     int n_tab_of[3] = {-1, -1, -1};
     unsigned long long tab_gen_of[3] = {0, 0, 0};
+    DevBuf d_tabf[3];                               // [tables | fractional tables] per form
+    unsigned long long tabf_key[3] = {0, 0, 0};
+    int vf_scen = 0, vf_steps = 0;                  // fractional discount planes
+    DevBuf d_vf64, d_vf32, d_vf2;
 
     Layout lay;
     DevBuf d_ctl;       // [0] queue head, [1] status

@@ -128,23 +128,35 @@ __global__ void inner_paths_kernel(VasStep s, uint64_t seed, int o0, int B, int 
     }
 }
 
+// The curve mode with the outer paths on the lanes: every outer path's node
+// rate gives one curve, and all outer paths share the in-force weights, so
+// plane[n][t][o] holds outer path o's curve at node n (one virtual outer
+// path whose "inner paths" are the real outer paths).  Padding lanes get 1.
 template <class VE>
-__global__ void curve_planes_kernel(double a, double b, double sigma, double dt, int o0, int B, int n_nodes,
-                                    int i_pad, int Lmax, const int* __restrict__ Ln,
-                                    const double* __restrict__ r_node, VE* __restrict__ plane) {
-    const size_t total = (size_t)B * n_nodes * Lmax;
+__global__ void curve_planes_lanes_kernel(double a, double b, double sigma, double dt, int n_outer, int n_nodes,
+                                          int o_pad, int Lmax, const int* __restrict__ Ln,
+                                          const double* __restrict__ r_node, VE* __restrict__ plane) {
+    const size_t total = (size_t)n_nodes * Lmax * o_pad;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
-        const int t = (int)(idx % Lmax);
-        const int n = (int)((idx / Lmax) % n_nodes);
-        const int ol = (int)(idx / ((size_t)Lmax * n_nodes));
-        if (t >= Ln[n]) continue;
-        const double r = r_node[(size_t)(o0 + ol) * n_nodes + n];
-        const double v = exp(vasicek_lnP((t + 1) * dt, r, a, b, sigma) - vasicek_lnP(t * dt, r, a, b, sigma));
-        VE* row = plane + (((size_t)ol * n_nodes + n) * Lmax + t) * i_pad;
-        row[0] = to_plane<VE>(v);
-        for (int i = 1; i < 32; ++i) row[i] = to_plane<VE>(1.0);
+        const int o = (int)(idx % o_pad);
+        const int t = (int)((idx / o_pad) % Lmax);
+        const int n = (int)(idx / ((size_t)o_pad * Lmax));
+        double v = 1.0;
+        if (o < n_outer && t < Ln[n]) {
+            const double r = r_node[(size_t)o * n_nodes + n];
+            v = exp(vasicek_lnP((t + 1) * dt, r, a, b, sigma) - vasicek_lnP(t * dt, r, a, b, sigma));
+        }
+        plane[idx] = to_plane<VE>(v);
     }
+}
+
+// L[o][n] = Lt[n][o] (the curve mode's node liabilities back to outer-major)
+__global__ void transpose_on_kernel(const double* __restrict__ Lt, int n_outer, int n_nodes, double* __restrict__ L) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_outer * n_nodes) return;
+    const int o = i / n_nodes, n = i - o * n_nodes;
+    L[i] = Lt[(size_t)n * n_outer + o];
 }
 
 // ------------------------------------------------------- nested recurrence ----
@@ -319,20 +331,27 @@ cudaError_t launch_inner_paths(int form, const VasStep& s, uint64_t seed, int o0
     return cudaGetLastError();
 }
 
-cudaError_t launch_curve_planes(int form, double a, double b, double sigma, int o0, int B, int n_nodes, int i_pad,
-                                int Lmax, const int* Ln, const double* r_node, void* plane, int sm_count,
-                                cudaStream_t st) {
+cudaError_t launch_curve_planes_lanes(int form, double a, double b, double sigma, int n_outer, int n_nodes, int o_pad,
+                                      int Lmax, const int* Ln, const double* r_node, void* plane, int sm_count,
+                                      cudaStream_t st) {
     const int grid = sm_count * 8;
     const double dt = 1.0 / 12.0;
     if (form == F_F64)
-        curve_planes_kernel<double><<<grid, 128, 0, st>>>(a, b, sigma, dt, o0, B, n_nodes, i_pad, Lmax, Ln, r_node,
-                                                           static_cast<double*>(plane));
+        curve_planes_lanes_kernel<double><<<grid, 128, 0, st>>>(a, b, sigma, dt, n_outer, n_nodes, o_pad, Lmax, Ln,
+                                                                 r_node, static_cast<double*>(plane));
     else if (form == F_F32)
-        curve_planes_kernel<float><<<grid, 128, 0, st>>>(a, b, sigma, dt, o0, B, n_nodes, i_pad, Lmax, Ln, r_node,
-                                                          static_cast<float*>(plane));
+        curve_planes_lanes_kernel<float><<<grid, 128, 0, st>>>(a, b, sigma, dt, n_outer, n_nodes, o_pad, Lmax, Ln,
+                                                                r_node, static_cast<float*>(plane));
     else
-        curve_planes_kernel<float2><<<grid, 128, 0, st>>>(a, b, sigma, dt, o0, B, n_nodes, i_pad, Lmax, Ln, r_node,
-                                                           static_cast<float2*>(plane));
+        curve_planes_lanes_kernel<float2><<<grid, 128, 0, st>>>(a, b, sigma, dt, n_outer, n_nodes, o_pad, Lmax, Ln,
+                                                                 r_node, static_cast<float2*>(plane));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_on(const double* Lt, int n_outer, int n_nodes, double* L, cudaStream_t st) {
+    const int n = n_outer * n_nodes;
+    if (n <= 0) return cudaSuccess;
+    transpose_on_kernel<<<(n + 255) / 256, 256, 0, st>>>(Lt, n_outer, n_nodes, L);
     return cudaGetLastError();
 }
 

@@ -33,9 +33,12 @@ cudaError_t launch_outer_paths(const VasStep& s, uint64_t seed, int n_outer, int
 cudaError_t launch_inner_paths(int form, const VasStep& s, uint64_t seed, int o0, int B, int n_nodes, int n_inner,
                                int i_pad, int Lmax, const int* Ln, const double* r_node, void* plane, int sm_count,
                                cudaStream_t st);
-cudaError_t launch_curve_planes(int form, double a, double b, double sigma, int o0, int B, int n_nodes, int i_pad,
-                                int Lmax, const int* Ln, const double* r_node, void* plane, int sm_count,
-                                cudaStream_t st);
+// The curve mode with the outer paths on the lanes (planes [n_nodes][Lmax][o_pad])
+// and the transpose of its [n_nodes][n_outer] liabilities to [n_outer][n_nodes].
+cudaError_t launch_curve_planes_lanes(int form, double a, double b, double sigma, int n_outer, int n_nodes, int o_pad,
+                                      int Lmax, const int* Ln, const double* r_node, void* plane, int sm_count,
+                                      cudaStream_t st);
+cudaError_t launch_transpose_on(const double* Lt, int n_outer, int n_nodes, double* L, cudaStream_t st);
 cudaError_t launch_node_stats(const double* L_all, int n_on, int n_inner, int k, double* mean, double* kth,
                               cudaStream_t st);
 

@@ -13,6 +13,8 @@ static const Variant kComp[] = {
     RSV_VARIANT(F_COMP, 2, 1, 128, 6, false, "comp P2xM1 nt128 min6"),
     RSV_VARIANT(F_COMP, 4, 1, 128, 4, false, "comp P4xM1 nt128 min4"),
     RSV_VARIANT(F_COMP, 2, 1, 256, 1, true, "comp P2xM1 nt256 side-outputs"),
+    RSV_VARIANT_PAY(F_COMP, 2, 1, 256, 2, false, PAY_START, "comp P2xM1 nt256 pay-start"),
+    RSV_VARIANT_PAY(F_COMP, 2, 1, 256, 2, false, PAY_FRACTION, "comp P2xM1 nt256 pay-fraction"),
 };
 const Variant* variants_comp(int* n) {
     *n = (int)(sizeof(kComp) / sizeof(kComp[0]));

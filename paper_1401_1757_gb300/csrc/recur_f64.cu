@@ -9,6 +9,8 @@ static const Variant kF64[] = {
     RSV_VARIANT(F_F64, 4, 1, 128, 1, false, "f64 P4xM1 nt128"),
     RSV_VARIANT(F_F64, 2, 1, 128, 1, false, "f64 P2xM1 nt128"),
     RSV_VARIANT(F_F64, 2, 1, 128, 1, true, "f64 P2xM1 nt128 side-outputs"),
+    RSV_VARIANT_PAY(F_F64, 2, 1, 128, 1, false, PAY_START, "f64 P2xM1 nt128 pay-start"),
+    RSV_VARIANT_PAY(F_F64, 2, 1, 128, 1, false, PAY_FRACTION, "f64 P2xM1 nt128 pay-fraction"),
 };
 const Variant* variants_f64(int* n) {
     *n = (int)(sizeof(kF64) / sizeof(kF64[0]));

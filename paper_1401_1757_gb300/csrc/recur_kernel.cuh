@@ -20,6 +20,8 @@
 // no inter-warp synchronisation after staging).
 #pragma once
 
+#include <type_traits>
+
 #include "rsv_device.cuh"
 
 namespace rsv {
@@ -148,6 +150,37 @@ __device__ __forceinline__ void step_jl(df v, df px, df qx, df py, df qy, df rho
     V10 = A10;
 }
 
+// Annuity-type steps with the payment at the start of the step (f = 0, a = 1)
+// or at the fraction f (a = v^f p^f, the fractional cash-flow term of
+// Eq. generalForm), on unshifted states: r = a + v p r'.  The JL state 10 is
+// carried as r10 / rho: r00 = a0 + v [px py r00' + px qy r01' + qx py rho a10'],
+// r01 = a1 + v px r01', a10 = a2 + v py a10'.
+template <class R>
+__device__ __forceinline__ R step_ann_a(R a, R g, R V) { return p_fma(g, V, a); }
+template <class R>
+__device__ __forceinline__ void step_jl_a(R v, R px, R qx, R py, R qy, R rho, R a0, R a1, R a2, R& V00, R& V01,
+                                          R& V10) {
+    const R gx = p_mul(v, px), gy = p_mul(v, py);
+    R t = p_fma(p_mul(gx, py), V00, a0);
+    t = p_fma(p_mul(gx, qy), V01, t);
+    t = p_fma(p_mul(p_mul(gy, qx), rho), V10, t);
+    V01 = p_fma(gx, V01, a1);
+    V10 = p_fma(gy, V10, a2);
+    V00 = t;
+}
+// Compensated: the one-step cash-flow and death terms in FP32 (they enter once,
+// weighted by their share), the products along the chain in double-float.
+__device__ __forceinline__ df step_ann_a(float a, df g, df V) { return df_float_plus_mul(a, g, V); }
+__device__ __forceinline__ void step_jl_a(df v, df px, df qx, df py, df qy, df rho, float a0, float a1, float a2,
+                                          df& V00, df& V01, df& V10) {
+    const df gx = df_mul(v, px), gy = df_mul(v, py);
+    const float r01 = __fadd_rn(V01.h, V01.l), a10 = __fadd_rn(V10.h, V10.l);
+    const float c = __fmaf_rn(__fmul_rn(__fmul_rn(gy.h, qx.h), rho.h), a10, __fmaf_rn(__fmul_rn(gx.h, qy.h), r01, a0));
+    V00 = df_float_plus_mul(c, df_mul(gx, py), V00);
+    V01 = df_float_plus_mul(a1, gx, V01);
+    V10 = df_float_plus_mul(a2, gy, V10);
+}
+
 // M consecutive scenario-plane elements of one lane, one vector load.
 template <class E, int M>
 struct alignas(sizeof(E) * M) Pack {
@@ -166,9 +199,11 @@ struct TileEnv {
     double* traj;
     double* pt_sum;
     int v0_ld;           // row stride of V0 (the caller's scenario count)
+    const void* vf;      // fractional discount plane (PAY_FRACTION), layout of v
+    int tabf_off;        // entries from the staged tables to the fractional ones (PAY_FRACTION)
 };
 
-template <int FORM, int P, int M, int KIND, bool EXTRA>
+template <int FORM, int P, int M, int KIND, bool EXTRA, int PAY = PAY_END>
 struct Tile {
     using T = Tr<FORM>;
     using Val = typename T::Val;
@@ -220,12 +255,16 @@ struct Tile {
 
     // The compensated form carries annuity-type states shifted (see step_ann):
     // the ANN state and JL states 00 and 01 as 1 + r, JL state 10 as 1 + r / rho.
-    static constexpr bool SHIFTED = FORM == F_COMP && (KIND == K_ANN || KIND == K_ANN2 || KIND == K_JL);
+    static constexpr bool ANNUITY = KIND == K_ANN || KIND == K_ANN2 || KIND == K_JL;
+    static constexpr bool SHIFTED = FORM == F_COMP && ANNUITY && PAY == PAY_END;
+    // payment within the step: unshifted states, JL state 10 carried as r10 / rho
+    static constexpr bool PAYF = ANNUITY && PAY != PAY_END;
 
     // r of state k of policy i, scenario m, in FP64
     __device__ __forceinline__ double dval(int k, int i, int m) const {
         const double x = T::dbl(V[k][i][m]);
         if constexpr (SHIFTED) return k == 2 ? T::dbl(rho[i]) * (x - 1.0) : x - 1.0;
+        if constexpr (PAYF) return k == 2 ? T::dbl(rho[i]) * x : x;
         return x;
     }
 
@@ -261,8 +300,17 @@ struct Tile {
         }
     }
 
+    // the fractional cash-flow terms need v^f of this step (PAY_FRACTION)
+    __device__ __forceinline__ VP loadf(int t) const {
+        return *reinterpret_cast<const VP*>(static_cast<const VE*>(e.vf) + (size_t)t * e.s_pad + s0);
+    }
+
     template <bool CHECK>
     __device__ __forceinline__ void step(int t, const VP& vv) {
+        if constexpr (PAYF) {
+            step_pay<CHECK>(t, vv);
+            return;
+        }
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             if (CHECK && t >= Sp[i]) continue;
@@ -292,6 +340,61 @@ struct Tile {
             if constexpr (EXTRA) record(t, i);
         }
     }
+
+    // Annuity-type step with the payment at the start of the step or at the
+    // fraction f: r = a + v W r' with the cash-flow term a = v^f W_f c.
+    template <bool CHECK>
+    __device__ __forceinline__ void step_pay(int t, const VP& vv) {
+        using A = typename std::conditional<FORM == F_COMP, float, Val>::type;   // the one-step terms
+        VP vf{};
+        if constexpr (PAY == PAY_FRACTION) vf = loadf(t);
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            if (CHECK && t >= Sp[i]) continue;
+            const TabE e1 = tab[idx1[i] + t];
+            const Val px = T::p(e1), qx = T::q(e1);
+            TabE e2{}, f1{}, f2{};
+            if constexpr (KIND != K_ANN) e2 = tab[idx2[i] + t];
+            if constexpr (PAY == PAY_FRACTION) {
+                f1 = tab[e.tabf_off + idx1[i] + t];
+                if constexpr (KIND != K_ANN) f2 = tab[e.tabf_off + idx2[i] + t];
+            }
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const Val v = T::v(vv.e[m]);
+                A vfm = A(1), pxf = A(1), qxf = A(0), pyf = A(1);
+                if constexpr (PAY == PAY_FRACTION) {
+                    vfm = head(T::v(vf.e[m]));
+                    pxf = head(T::p(f1));
+                    qxf = head(T::q(f1));
+                    if constexpr (KIND != K_ANN) pyf = head(T::p(f2));
+                }
+                if constexpr (KIND == K_JL) {
+                    const Val py = T::p(e2), qy = T::q(e2);
+                    // W_f c = (pxf + rho qxf pyf, pxf, rho pyf): state 10 divided by rho
+                    const A a0 = vfm * (pxf + head(rho[i]) * qxf * pyf), a1 = vfm * pxf, a2 = vfm * pyf;
+                    step_jl_a(v, px, qx, py, qy, rho[i], a0, a1, a2, V[0][i][m], V[1][i][m], V[2][i][m]);
+                } else {
+                    Val p = px;
+                    A a = vfm * pxf;
+                    if constexpr (KIND == K_ANN2) {
+                        Val q;
+                        joint_pq(px, qx, T::p(e2), T::q(e2), p, q);
+                        a = a * pyf;
+                    }
+                    if constexpr (FORM == F_COMP) {
+                        V[0][i][m] = step_ann_a(a, df_mul(v, p), V[0][i][m]);
+                    } else {
+                        V[0][i][m] = step_ann_a(a, p_mul(v, p), V[0][i][m]);
+                    }
+                }
+            }
+        }
+    }
+    // the leading part of a value (the head of a double-float), for one-step terms
+    __device__ static __forceinline__ float head(df x) { return x.h; }
+    __device__ static __forceinline__ float head(float x) { return x; }
+    __device__ static __forceinline__ double head(double x) { return x; }
 
     static constexpr int U = 4;   // steps per prefetch group
 
@@ -389,10 +492,10 @@ struct Tile {
 };
 
 // One work item of one reduced model.
-template <int FORM, int P, int M, int KIND, bool EXTRA, class TabE>
+template <int FORM, int P, int M, int KIND, bool EXTRA, int PAY, class TabE>
 __device__ __forceinline__ void run_item(const TileEnv& env, const TabE* tab, int tile, int chunk, int lane,
                                          const RecurArgs& a) {
-    Tile<FORM, P, M, KIND, EXTRA> w(env, tab, tile, chunk, lane);
+    Tile<FORM, P, M, KIND, EXTRA, PAY> w(env, tab, tile, chunk, lane);
     w.run_steps();
     w.epilogue_v0(tile, a.V0f, a.V0d, a.partial);
 }
@@ -400,7 +503,7 @@ __device__ __forceinline__ void run_item(const TileEnv& env, const TabE* tab, in
 // TWO: the portfolio has two-life single-state tiles (K_ANN2, K_ASS2).  The
 // kernel is compiled with and without them: the three hot models alone keep
 // their register allocation free of spills.
-template <int FORM, int P, int M, int NT, int MINB, bool EXTRA, bool TWO>
+template <int FORM, int P, int M, int NT, int MINB, bool EXTRA, bool TWO, int PAY>
 __global__ void __launch_bounds__(NT, MINB) recur_kernel(const RecurArgs a) {
     using TabE = typename Tr<FORM>::TabE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -408,7 +511,8 @@ __global__ void __launch_bounds__(NT, MINB) recur_kernel(const RecurArgs a) {
     TabE* tab = reinterpret_cast<TabE*>(smem_raw);
     if (!stage_to_smem(tab, a.tab, (uint32_t)a.tab_bytes, &bar, a.status)) return;
 
-    const TileEnv env{a.slots, a.v, a.s_pad, a.n_scen, a.n_steps, a.amount, a.traj, a.pt_sum, a.v0_ld};
+    const TileEnv env{a.slots, a.v, a.s_pad, a.n_scen, a.n_steps, a.amount, a.traj, a.pt_sum, a.v0_ld, a.vf,
+                      a.tabf_off};
     const int lane = threadIdx.x & 31;
     for (;;) {
         int item = 0;
@@ -418,12 +522,12 @@ __global__ void __launch_bounds__(NT, MINB) recur_kernel(const RecurArgs a) {
         const int tile = item / a.n_chunks;
         const int chunk = item - tile * a.n_chunks;
         const int kind = a.tile_kind[tile];
-        if (kind == K_JL) run_item<FORM, P, M, K_JL, EXTRA>(env, tab, tile, chunk, lane, a);
-        else if (kind == K_ANN) run_item<FORM, P, M, K_ANN, EXTRA>(env, tab, tile, chunk, lane, a);
-        else if (!TWO || kind == K_ASS) run_item<FORM, P, M, K_ASS, EXTRA>(env, tab, tile, chunk, lane, a);
+        if (kind == K_JL) run_item<FORM, P, M, K_JL, EXTRA, PAY>(env, tab, tile, chunk, lane, a);
+        else if (kind == K_ANN) run_item<FORM, P, M, K_ANN, EXTRA, PAY>(env, tab, tile, chunk, lane, a);
+        else if (!TWO || kind == K_ASS) run_item<FORM, P, M, K_ASS, EXTRA, PAY>(env, tab, tile, chunk, lane, a);
         else if constexpr (TWO) {
-            if (kind == K_ANN2) run_item<FORM, P, M, K_ANN2, EXTRA>(env, tab, tile, chunk, lane, a);
-            else run_item<FORM, P, M, K_ASS2, EXTRA>(env, tab, tile, chunk, lane, a);
+            if (kind == K_ANN2) run_item<FORM, P, M, K_ANN2, EXTRA, PAY>(env, tab, tile, chunk, lane, a);
+            else run_item<FORM, P, M, K_ASS2, EXTRA, PAY>(env, tab, tile, chunk, lane, a);
         }
     }
 }
@@ -432,37 +536,40 @@ __global__ void __launch_bounds__(NT, MINB) recur_kernel(const RecurArgs a) {
 struct Variant {
     int form, P, M, NT;
     bool extra;
+    int pay;   // PAY_END, or the variant that pays annuities within the step
     const char* name;
     // [0]: the three single-table/JL models; [1]: also the two-life single-state ones
     cudaError_t (*launch[2])(const RecurArgs&, int grid, size_t smem, cudaStream_t st);
     cudaError_t (*occupancy[2])(int* blocks_per_sm, size_t smem);
 };
 
-template <int FORM, int P, int M, int NT, int MINB, bool EXTRA, bool TWO>
+template <int FORM, int P, int M, int NT, int MINB, bool EXTRA, bool TWO, int PAY>
 cudaError_t launch_recur(const RecurArgs& a, int grid, size_t smem, cudaStream_t st) {
-    auto k = recur_kernel<FORM, P, M, NT, MINB, EXTRA, TWO>;
+    auto k = recur_kernel<FORM, P, M, NT, MINB, EXTRA, TWO, PAY>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NT, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int FORM, int P, int M, int NT, int MINB, bool EXTRA, bool TWO>
+template <int FORM, int P, int M, int NT, int MINB, bool EXTRA, bool TWO, int PAY>
 cudaError_t occupancy_recur(int* blocks, size_t smem) {
-    auto k = recur_kernel<FORM, P, M, NT, MINB, EXTRA, TWO>;
+    auto k = recur_kernel<FORM, P, M, NT, MINB, EXTRA, TWO, PAY>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, NT, smem);
 }
 
-#define RSV_VARIANT(FORM, P, M, NT, MINB, EXTRA, NAME)                                              \
-    Variant {                                                                                        \
-        FORM, P, M, NT, EXTRA, NAME,                                                                 \
-            {&launch_recur<FORM, P, M, NT, MINB, EXTRA, false>, &launch_recur<FORM, P, M, NT, MINB, EXTRA, true>}, \
-        {                                                                                            \
-            &occupancy_recur<FORM, P, M, NT, MINB, EXTRA, false>, &occupancy_recur<FORM, P, M, NT, MINB, EXTRA, true> \
-        }                                                                                            \
+#define RSV_VARIANT_PAY(FORM, P, M, NT, MINB, EXTRA, PAY, NAME)                                              \
+    Variant {                                                                                                 \
+        FORM, P, M, NT, EXTRA, PAY, NAME,                                                                     \
+            {&launch_recur<FORM, P, M, NT, MINB, EXTRA, false, PAY>, &launch_recur<FORM, P, M, NT, MINB, EXTRA, true, PAY>}, \
+        {                                                                                                     \
+            &occupancy_recur<FORM, P, M, NT, MINB, EXTRA, false, PAY>,                                         \
+                &occupancy_recur<FORM, P, M, NT, MINB, EXTRA, true, PAY>                                       \
+        }                                                                                                     \
     }
+#define RSV_VARIANT(FORM, P, M, NT, MINB, EXTRA, NAME) RSV_VARIANT_PAY(FORM, P, M, NT, MINB, EXTRA, PAY_END, NAME)
 
 // Each form's translation unit defines these.
 const Variant* variants_f64(int* n);

@@ -24,6 +24,19 @@ using namespace rsv;
 
 namespace {
 
+// The tunable variants come first; then the side-output one and those that
+// pay annuities within the step.
+int tunable_count(const Variant* vl, int n) {
+    int k = 0;
+    while (k < n && !vl[k].extra && vl[k].pay == PAY_END) ++k;
+    return k;
+}
+int special_variant(const Variant* vl, int n, bool extra, int pay) {
+    for (int k = 0; k < n; ++k)
+        if (vl[k].extra == extra && vl[k].pay == pay) return k;
+    return 0;
+}
+
 const Variant* variant_list(int form, int* n) {
     switch (form) {
     case F_F64: return variants_f64(n);
@@ -288,6 +301,28 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
     return RSV_OK;
 }
 
+namespace {
+// Entries (p, q) of tables src[0..n_tab) in the format of `form`, pad entries
+// per table, zero survival past each table's end.
+void write_entries(int form, const std::vector<double>* src, int n_tab, int pad, unsigned char* h) {
+    for (int t = 0; t < n_tab; ++t) {
+        for (int k = 0; k < pad; ++k) {
+            const double p = k < (int)src[t].size() ? src[t][k] : 0.0;
+            const double q = 1.0 - p;
+            const size_t i = (size_t)t * pad + k;
+            if (form == F_F64) {
+                reinterpret_cast<double2*>(h)[i] = make_double2(p, q);
+            } else if (form == F_F32) {
+                reinterpret_cast<float2*>(h)[i] = make_float2((float)p, (float)q);
+            } else {
+                const float ph = (float)p, qh = (float)q;
+                reinterpret_cast<float4*>(h)[i] = make_float4(ph, (float)(p - (double)ph), qh, (float)(q - (double)qh));
+            }
+        }
+    }
+}
+}  // namespace
+
 // Decrement tables in the entry format of `form`, zero survival past each
 // table's end, staged per CTA.
 rsv_status rsv::build_tables(rsv_ctx* c, int form, size_t& smem) {
@@ -299,27 +334,36 @@ rsv_status rsv::build_tables(rsv_ctx* c, int form, size_t& smem) {
     if (c->tab_pad_of[form] == pad && c->n_tab_of[form] == n_tab && c->tab_gen_of[form] == c->tab_gen)
         return RSV_OK;
     std::vector<unsigned char> h(smem);
-    for (int t = 0; t < n_tab; ++t) {
-        for (int k = 0; k < pad; ++k) {
-            const double p = k < table_len(c, t) ? c->tab[t][k] : 0.0;
-            const double q = 1.0 - p;
-            const size_t i = (size_t)t * pad + k;
-            if (form == F_F64) {
-                reinterpret_cast<double2*>(h.data())[i] = make_double2(p, q);
-            } else if (form == F_F32) {
-                reinterpret_cast<float2*>(h.data())[i] = make_float2((float)p, (float)q);
-            } else {
-                const float ph = (float)p, qh = (float)q;
-                reinterpret_cast<float4*>(h.data())[i] =
-                    make_float4(ph, (float)(p - (double)ph), qh, (float)(q - (double)qh));
-            }
-        }
-    }
+    write_entries(form, c->tab, n_tab, pad, h.data());
     CU(c->d_tab[form].ensure(smem));
     CU(cudaMemcpyAsync(c->d_tab[form].p, h.data(), smem, cudaMemcpyHostToDevice, c->stream));   // staged
     c->tab_pad_of[form] = pad;
     c->n_tab_of[form] = n_tab;
     c->tab_gen_of[form] = c->tab_gen;
+    return RSV_OK;
+}
+
+// The tables followed by the fractional-survival tables (RSV_PAY_FRACTION),
+// staged together; *tabf_off receives the offset in entries.
+rsv_status build_tables_frac(rsv_ctx* c, int form, size_t& smem, int& tabf_off) {
+    const int pad = c->lay.tab_pad, n_tab = c->lay.n_tab;
+    for (int t = 0; t < n_tab; ++t)
+        if (!c->tab[t].empty() && c->tabf[t].size() != c->tab[t].size())
+            return fail(c, RSV_E_STATE, "table %d has no fractional-survival table of its length", t);
+    const size_t esz = form == F_F32 ? sizeof(float2) : 16, half = (size_t)n_tab * pad * esz;
+    smem = 2 * half;
+    tabf_off = n_tab * pad;
+    if (smem > kMaxSmem)
+        return fail(c, RSV_E_ARG, "tables and fractional tables need %zu bytes of shared memory (max %zu)", smem,
+                    kMaxSmem);
+    const unsigned long long key = c->tab_gen * 1000003ull + c->tabf_gen * 7919ull + (unsigned)pad * 31u + n_tab;
+    if (c->tabf_key[form] == key) return RSV_OK;
+    std::vector<unsigned char> h(smem);
+    write_entries(form, c->tab, n_tab, pad, h.data());
+    write_entries(form, c->tabf, n_tab, pad, h.data() + half);
+    CU(c->d_tabf[form].ensure(smem));
+    CU(cudaMemcpyAsync(c->d_tabf[form].p, h.data(), smem, cudaMemcpyHostToDevice, c->stream));   // staged
+    c->tabf_key[form] = key;
     return RSV_OK;
 }
 
@@ -371,11 +415,18 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
                                                         scan ? "time-scan" : "summation");
     if ((scan || summ) && (outs & RSV_OUT_PT_MEAN))
         return fail(c, RSV_E_ARG, "the %s variant has no per-step means", scan ? "time-scan" : "summation");
+    const int pay = o->payment;
+    if (pay < PAY_END || pay > PAY_FRACTION) return fail(c, RSV_E_ARG, "bad payment %d", pay);
+    if (pay != PAY_END && (extra || scan || summ))
+        return fail(c, RSV_E_ARG, "payment within the step: V0 and totals of the scenario-parallel kernels only");
+    const int nt = tunable_count(vl, nv);
     int vi;
     if (extra || scan || summ) {
-        vi = nv - 1;
+        vi = special_variant(vl, nv, true, PAY_END);
+    } else if (pay != PAY_END) {
+        vi = special_variant(vl, nv, false, pay);
     } else if (o->variant >= 0) {
-        if (o->variant >= nv - 1) return fail(c, RSV_E_ARG, "variant %d out of range", o->variant);
+        if (o->variant >= nt) return fail(c, RSV_E_ARG, "variant %d out of range", o->variant);
         vi = o->variant;
     } else if (o->variant == -1) {
         vi = c->tuned[o->form] >= 0 ? c->tuned[o->form] : 0;
@@ -387,7 +438,14 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     rsv_status st = build_layout(c, (scan || summ) ? 1 : V.P, o->horizon, c->n_steps);
     if (st != RSV_OK) return st;
     size_t smem = 0;
-    if ((st = build_tables(c, o->form, smem)) != RSV_OK) return st;
+    int tabf_off = 0;
+    if (pay == PAY_FRACTION) {
+        if (c->vf_scen != c->n_scen || c->vf_steps != c->n_steps)
+            return fail(c, RSV_E_STATE, "fractional discount factors not loaded for the scenario set's shape");
+        if ((st = build_tables_frac(c, o->form, smem, tabf_off)) != RSV_OK) return st;
+    } else if ((st = build_tables(c, o->form, smem)) != RSV_OK) {
+        return st;
+    }
     if ((st = upload_amounts(c)) != RSV_OK) return st;
 
     const Layout& L = c->lay;
@@ -413,7 +471,10 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     if (tot && L.n_tiles == 0) CU(cudaMemsetAsync(tot, 0, NSc * sizeof(double), c->stream));
 
     RecurArgs a{};
-    a.tab = c->d_tab[o->form].p;
+    a.tab = pay == PAY_FRACTION ? c->d_tabf[o->form].p : c->d_tab[o->form].p;
+    a.tabf_off = tabf_off;
+    a.vf = pay != PAY_FRACTION ? nullptr
+                               : (o->form == F_F64 ? c->d_vf64.p : (o->form == F_F32 ? c->d_vf32.p : c->d_vf2.p));
     a.tab_bytes = (int32_t)smem;
     a.v = o->form == F_F64 ? c->d_v64.p : (o->form == F_F32 ? c->d_v32.p : c->d_v2.p);
     a.s_pad = c->s_pad;
@@ -462,6 +523,7 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
             const int w = std::min(width, NSc - s0);
             RecurArgs b = a;
             b.v = static_cast<const char*>(a.v) + (size_t)s0 * esz_v;
+            b.vf = a.vf ? static_cast<const char*>(a.vf) + (size_t)s0 * esz_v : nullptr;
             b.n_scen = w;
             b.n_chunks = (w + 32 * V.M - 1) / (32 * V.M);
             b.n_items = L.n_tiles * b.n_chunks;
@@ -536,8 +598,8 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
 rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* sp, rsv_nested_out* out) {
     if (!o || !sp || !out) return fail(c, RSV_E_ARG, "opts, spec and out must not be NULL");
     if (o->form < F_F64 || o->form > F_COMP) return fail(c, RSV_E_ARG, "bad form %d", o->form);
-    if (o->outputs != 0 || o->horizon != 0 || (o->on_device != 0 && o->on_device != 1))
-        return fail(c, RSV_E_ARG, "nested runs take outputs = 0, horizon = 0, on_device 0/1");
+    if (o->outputs != 0 || o->horizon != 0 || o->payment != 0 || (o->on_device != 0 && o->on_device != 1))
+        return fail(c, RSV_E_ARG, "nested runs take outputs = 0, horizon = 0, payment 0, on_device 0/1");
     if (sp->n_outer < 1 || sp->n_nodes < 1 || sp->node_step_m < 1 || sp->n_inner < 1 || sp->n_inner > (1 << 20))
         return fail(c, RSV_E_ARG, "bad nested sizes");
     if ((long long)(sp->n_nodes - 1) * sp->node_step_m > kMaxAgeSteps)
@@ -615,7 +677,11 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
     CU(c->d_nest_ln.ensure(NN * sizeof(int)));
     CU(c->d_nest_rn.ensure((size_t)NO * NN * sizeof(double)));
     CU(c->d_nest_d0.ensure((size_t)NO * NN * sizeof(double)));
-    if (!sur) CU(c->d_nest_plane.ensure((size_t)B * per_outer));
+    const bool curve = sp->mode == RSV_NESTED_CURVE;
+    const int o_pad = (NO + 31) / 32 * 32;   // the curve mode: outer paths on the lanes
+    const size_t curve_plane = (size_t)NN * Lmax * o_pad * esz;
+    if (curve) CU(c->d_nest_plane.ensure(curve_plane + (size_t)NN * NO * sizeof(double)));
+    else if (!sur) CU(c->d_nest_plane.ensure((size_t)B * per_outer));
     CU(c->d_nest_mean.ensure((size_t)NO * NN * sizeof(double)));
     CU(c->d_nest_kth.ensure((size_t)NO * NN * sizeof(double)));
     double* Lall = (o->on_device && out->L_all) ? out->L_all : nullptr;
@@ -723,14 +789,29 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
         }
         if (out->n_fallback) *out->n_fallback = nfb;
     }
-    for (int o0 = 0; o0 < NO && !sur; o0 += B) {
+    if (curve) {
+        // one virtual outer path whose "inner paths" are the outer paths: every
+        // lane carries a different outer path's curve, all sharing the weights
+        double* Lt = reinterpret_cast<double*>(static_cast<char*>(c->d_nest_plane.p) + curve_plane);
+        CU(launch_curve_planes_lanes(form, sp->a, sp->b, sp->sigma, NO, NN, o_pad, Lmax, c->d_nest_ln.as<int>(),
+                                     c->d_nest_rn.as<double>(), c->d_nest_plane.p, c->sm_count, c->stream));
+        NestedArgs ac = a;
+        ac.i_pad = o_pad;
+        ac.n_inner = NO;
+        ac.n_chunks = o_pad / 32;
+        ac.B = 1;
+        ac.o0 = 0;
+        ac.n_items = NN * ac.n_chunks;
+        ac.L_all = Lt;
+        CU(cudaMemsetAsync(c->d_ctl.p, 0, sizeof(int32_t), c->stream));
+        if (L.n_tiles > 0) CU(launch_nested(form, ac, c->sm_count, smem, c->stream));
+        else CU(cudaMemsetAsync(Lt, 0, (size_t)NN * NO * sizeof(double), c->stream));
+        CU(launch_transpose_on(Lt, NO, NN, Lall, c->stream));
+    }
+    for (int o0 = 0; o0 < NO && !sur && !curve; o0 += B) {
         const int Bc = std::min(B, NO - o0);
-        if (mc)
-            CU(launch_inner_paths(form, vs, sp->seed, o0, Bc, NN, n_inner, i_pad, Lmax, c->d_nest_ln.as<int>(),
-                                  c->d_nest_rn.as<double>(), c->d_nest_plane.p, c->sm_count, c->stream));
-        else
-            CU(launch_curve_planes(form, sp->a, sp->b, sp->sigma, o0, Bc, NN, i_pad, Lmax, c->d_nest_ln.as<int>(),
-                                   c->d_nest_rn.as<double>(), c->d_nest_plane.p, c->sm_count, c->stream));
+        CU(launch_inner_paths(form, vs, sp->seed, o0, Bc, NN, n_inner, i_pad, Lmax, c->d_nest_ln.as<int>(),
+                              c->d_nest_rn.as<double>(), c->d_nest_plane.p, c->sm_count, c->stream));
         const long long items = (long long)NN * Bc * a.n_chunks;
         if (items > 0x7fffffffLL) return fail(c, RSV_E_ARG, "too many nested work items");
         a.B = Bc;
@@ -795,7 +876,8 @@ rsv_status rsv_destroy(rsv_ctx* c) {
                       &c->d_nest_ln, &c->d_nest_rn, &c->d_nest_d0, &c->d_nest_plane, &c->d_nest_mean,
                       &c->d_nest_kth, &c->d_nest_all, &c->d_pols, &c->sur.d_flag, &c->sur.d_q, &c->sur.d_lab,
                       &c->sur.d_y, &c->sur.d_X, &c->sur.d_pred, &c->sur.d_err, &c->sur.d_aux, &c->sur.d_curve,
-                      &c->sur.d_comm, &c->sur.d_lnb})
+                      &c->sur.d_comm, &c->sur.d_lnb, &c->d_tabf[0], &c->d_tabf[1], &c->d_tabf[2], &c->d_vf64,
+                      &c->d_vf32, &c->d_vf2})
         b->release();
     c->mlp.release();
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -824,6 +906,46 @@ rsv_status rsv_load_decrements(rsv_ctx* c, int32_t table_id, const double* p, in
             return fail(c, RSV_E_ASSUMPTION, "table %d entry %d = %g is not a probability", table_id, k, p[k]);
     c->tab[table_id].assign(p, p + n);
     ++c->tab_gen;
+    return RSV_OK;
+}
+
+rsv_status rsv_load_decrements_fraction(rsv_ctx* c, int32_t table_id, const double* p, int32_t n) {
+    if (!c) return RSV_E_ARG;
+    if (table_id < 0 || table_id >= kMaxTables) return fail(c, RSV_E_ARG, "table id %d outside [0,8)", table_id);
+    if (!p || n < 1 || n > kMaxAgeSteps) return fail(c, RSV_E_ARG, "bad table pointer or length %d", n);
+    for (int k = 0; k < n; ++k)
+        if (!(p[k] >= 0.0 && p[k] <= 1.0))
+            return fail(c, RSV_E_ASSUMPTION, "fractional table %d entry %d = %g is not a probability", table_id, k,
+                        p[k]);
+    c->tabf[table_id].assign(p, p + n);
+    ++c->tabf_gen;
+    return RSV_OK;
+}
+
+rsv_status rsv_load_scenarios_fraction(rsv_ctx* c, const double* v, int32_t n_scen, int32_t n_steps, int32_t layout) {
+    if (!c) return RSV_E_ARG;
+    if (!v || n_scen < 1 || n_steps < 1 || (layout != 0 && layout != 1))
+        return fail(c, RSV_E_ARG, "bad fractional scenario arguments");
+    const size_t n = (size_t)n_scen * n_steps;
+    for (size_t i = 0; i < n; ++i)
+        if (!(std::isfinite(v[i]) && v[i] > 0.0))
+            return fail(c, RSV_E_ASSUMPTION, "fractional discount factor %zu = %g is not finite and positive", i, v[i]);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    const int s_pad = (n_scen + 127) / 128 * 128;
+    const size_t np = (size_t)n_steps * s_pad;
+    CU(c->d_vstage.ensure(n * sizeof(double)));
+    CU(c->d_vf64.ensure(np * sizeof(double)));
+    CU(c->d_vf32.ensure(np * sizeof(float)));
+    CU(c->d_vf2.ensure(np * sizeof(float2)));
+    CU(cudaMemcpyAsync(c->d_vstage.p, v, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    split_planes_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(c->d_vstage.as<double>(), layout, n_scen, n_steps,
+                                                                s_pad, c->d_vf64.as<double>(), c->d_vf32.as<float>(),
+                                                                c->d_vf2.as<float2>());
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(c->stream));
+    c->vf_scen = n_scen;
+    c->vf_steps = n_steps;
     return RSV_OK;
 }
 
@@ -881,8 +1003,8 @@ rsv_status rsv_compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_sp
 
 int32_t rsv_variant_count(int32_t form) {
     int n = 0;
-    variant_list(form, &n);
-    return n > 0 ? n - 1 : 0;
+    const Variant* vl = variant_list(form, &n);
+    return vl ? tunable_count(vl, n) : 0;
 }
 
 const char* rsv_variant_name(int32_t form, int32_t variant) {

@@ -57,7 +57,13 @@ struct RecurArgs {
     double* pt_sum;           // [n_pol][T+1] sums over scenarios or null
     double* traj;             // [n_pol][T+1][n_scen] or null
     int32_t v0_ld;            // row stride of V0 (= n_scen unless a column block is computed)
+    const void* vf;           // fractional discount plane v_t^f, same layout as v (fractional payments)
+    int32_t tabf_off;         // entries from the staged tables to the fractional-survival tables
 };
+
+// When an annuity's cash flow is paid within each step (the fraction f of
+// Eq. generalForm); assurance benefits are always paid at the step's end.
+enum Pay : int32_t { PAY_END = 0, PAY_START = 1, PAY_FRACTION = 2 };
 
 // ------------------------------------------------------------------------
 // double-float ("df") numbers: value = h + l with |l| about ulp(h) or less.
@@ -122,7 +128,7 @@ __device__ __forceinline__ df df_one_plus_mul(df g, df R) {
     return df{h, e};
 }
 
-// c + g R for float c >= 1 and df g, R >= 0: the product as in df_mul, then
+// c + g R for float c >= 0 and df g, R >= 0: the product as in df_mul, then
 // the head sum ordered by magnitude (Fast2Sum) and the tails added.
 __device__ __forceinline__ df df_float_plus_mul(float c, df g, df R) {
     const float p = __fmul_rn(g.h, R.h);

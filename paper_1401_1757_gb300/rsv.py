@@ -23,6 +23,7 @@ RSV_JOINT_ANNUITY, RSV_LAST_SURVIVOR, RSV_JOINT_TERM, RSV_JOINT_ENDOWMENT = 4, 5
 RSV_FORM_F64, RSV_FORM_F32, RSV_FORM_F32_COMP = 0, 1, 2
 RSV_VARIANT_TIME_SCAN = -2   # the FP64 parallel-in-time scan (see include/rsv.h)
 RSV_VARIANT_SUMMATION = -3   # the FP64 O(S^2) summation definition
+RSV_PAY_END, RSV_PAY_START, RSV_PAY_FRACTION = 0, 1, 2
 FORM_NAMES = {0: "f64", 1: "f32", 2: "f32comp"}
 RSV_OUT_V0, RSV_OUT_SCEN_TOTAL, RSV_OUT_PT_MEAN, RSV_OUT_TRAJ = 1, 2, 4, 8
 
@@ -42,7 +43,8 @@ assert POLICY_DTYPE.itemsize == C.sizeof(rsv_policy) == 48
 
 class rsv_opts(C.Structure):
     _fields_ = [("form", C.c_int32), ("outputs", C.c_int32), ("horizon", C.c_int32),
-                ("on_device", C.c_int32), ("variant", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("on_device", C.c_int32), ("variant", C.c_int32), ("payment", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class rsv_out(C.Structure):
@@ -93,6 +95,7 @@ _lib = None
 
 # Exported symbols of librsv.so that include/rsv.h declares.
 EXPORTS = ["rsv_create", "rsv_destroy", "rsv_set_stream", "rsv_load_decrements", "rsv_load_portfolio",
+           "rsv_load_decrements_fraction", "rsv_load_scenarios_fraction",
            "rsv_load_scenarios", "rsv_compute_reserves", "rsv_compute_nested", "rsv_variant_count", "rsv_variant_name",
            "rsv_tune", "rsv_synchronize", "rsv_last_error", "rsv_last_kernel_ms", "rsv_device_sm_count",
            "rsv_reserves_noalloc", "rsv_mlp_param_count", "rsv_mlp_init", "rsv_mlp_set_params",
@@ -121,6 +124,8 @@ def load_library(path: str = LIB_PATH):
         "rsv_load_decrements": ([vp, i32, vp, i32], i32),
         "rsv_load_portfolio": ([vp, vp, i64], i32),
         "rsv_load_scenarios": ([vp, vp, i32, i32, i32], i32),
+        "rsv_load_decrements_fraction": ([vp, i32, vp, i32], i32),
+        "rsv_load_scenarios_fraction": ([vp, vp, i32, i32, i32], i32),
         "rsv_compute_reserves": ([vp, C.POINTER(rsv_opts), C.POINTER(rsv_out)], i32),
         "rsv_compute_nested": ([vp, C.POINTER(rsv_opts), C.POINTER(rsv_nested_spec), C.POINTER(rsv_nested_out)],
                                i32),
@@ -192,6 +197,12 @@ def rsv_load_decrements(ctx, table_id: int, p_monthly):
     _check(ctx, _lib.rsv_load_decrements(ctx, table_id, p.ctypes.data, len(p)))
 
 
+def rsv_load_decrements_fraction(ctx, table_id: int, p_f):
+    """Survival over the first fraction f of each month (RSV_PAY_FRACTION)."""
+    p = np.ascontiguousarray(p_f, dtype=np.float64)
+    _check(ctx, _lib.rsv_load_decrements_fraction(ctx, table_id, p.ctypes.data, len(p)))
+
+
 def policy_records(pol) -> np.ndarray:
     """Policy records in the ABI layout from a dict of arrays (as made by ``synth``)
     or an existing record array."""
@@ -222,12 +233,20 @@ def rsv_load_scenarios(ctx, v, layout: int = 0):
     _check(ctx, _lib.rsv_load_scenarios(ctx, ptr, n_scen, n_steps, layout))
 
 
+def rsv_load_scenarios_fraction(ctx, v_f, layout: int = 0):
+    """Discount factors over the first fraction f of each step (RSV_PAY_FRACTION),
+    shaped as for rsv_load_scenarios."""
+    v = np.ascontiguousarray(v_f, dtype=np.float64)
+    n_scen, n_steps = (v.shape[0], v.shape[1]) if layout == 0 else (v.shape[1], v.shape[0])
+    _check(ctx, _lib.rsv_load_scenarios_fraction(ctx, v.ctypes.data, n_scen, n_steps, layout))
+
+
 def rsv_compute_reserves(ctx, form: int = RSV_FORM_F32_COMP, outputs: int = RSV_OUT_V0, horizon: int = 0,
                          on_device: bool = False, variant: int = -1, V0=None, V0d=None, scen_total=None,
-                         pt_mean=None, traj=None):
+                         pt_mean=None, traj=None, payment: int = 0):
     """Runs the recurrence.  Output buffers (NumPy for on_device=False, CUDA
     torch tensors for on_device=True) are caller-sized; see include/rsv.h."""
-    o = rsv_opts(form, outputs, horizon, 1 if on_device else 0, variant)
+    o = rsv_opts(form, outputs, horizon, 1 if on_device else 0, variant, payment)
     out = rsv_out(_ptr(V0), _ptr(V0d), _ptr(scen_total), _ptr(pt_mean), _ptr(traj))
     _check(ctx, _lib.rsv_compute_reserves(ctx, C.byref(o), C.byref(out)))
 

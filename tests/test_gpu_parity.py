@@ -428,3 +428,64 @@ def test_two_life_products(ctx, form):
         for var in (rsv.RSV_VARIANT_TIME_SCAN, rsv.RSV_VARIANT_SUMMATION):
             V0s, _ = run(ctx, pol, tab, v, form, variant=var, tables=[tab, tab2])
             assert rel_err(V0s, ref, pol["amount"]).max() <= 1e-12
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("payment", [rsv.RSV_PAY_START, rsv.RSV_PAY_FRACTION])
+def test_payment_within_the_step(ctx, form, payment):
+    """Annuities paid at the start of each month (f = 0) or at f = 1/2 (Eq.
+    generalForm with W_{t,f} and v^f): every annuity product and JL state
+    against the oracle's general-f recurrence; assurances stay at f = 1."""
+    tab = synth.gm_monthly_survival()
+    base = synth.portfolio_mix(24, seed=16)
+    two = synth.portfolio_two_life(16, seed=16)
+    jl = np.where(base["product"] == 1)[0]
+    extra = synth.take(base, np.concatenate([jl, jl]))
+    extra["state0"][: len(jl)] = 1
+    extra["state0"][len(jl):] = 2
+    pol = {k: np.concatenate([base[k], extra[k], two[k]]) for k in base}
+    n = len(pol["product"])
+    v = synth.vasicek_paths(40, 1200, seed=16)
+    # f = 1/2 under a constant force and a constant rate within each month
+    tab_f = np.sqrt(tab) if payment == rsv.RSV_PAY_FRACTION else np.ones_like(tab)
+    v_f = np.sqrt(v) if payment == rsv.RSV_PAY_FRACTION else np.ones_like(v)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    if payment == rsv.RSV_PAY_FRACTION:
+        rsv.rsv_load_decrements_fraction(ctx, 0, tab_f)
+        rsv.rsv_load_scenarios_fraction(ctx, v_f)
+    V0 = np.zeros((n, 40))
+    tot = np.zeros(40)
+    rsv.rsv_compute_reserves(ctx, form, V0T, payment=payment, V0d=V0, scen_total=tot)
+    ref = np.zeros((n, 40))
+    for p in range(n):
+        prod = int(pol["product"][p])
+        annuity = prod in (0, 1, 4, 5)
+        for s in range(40):
+            kw = dict(age2=int(pol["age2_m"][p]), term=int(pol["term_m"][p]), rho=float(pol["reversion"][p]))
+            if annuity:
+                kw.update(table_fx=tab_f, table_fy=tab_f, vf=v_f[s])
+            r = oracle.chain(prod, int(pol["age1_m"][p]), float(pol["amount"][p]), tab, v[s], **kw)
+            ref[p, s] = r[0, int(pol["state0"][p])]
+    err = rel_err(V0, ref, pol["amount"])
+    print(f"payment {payment} form {rsv.FORM_NAMES[form]}: max rel err {err.max():.3e}")
+    assert err.max() <= TOL[form]
+    assert np.max(np.abs(tot - ref.sum(axis=0)) / ref.sum(axis=0)) <= TOL[form]
+    with pytest.raises(rsv.RsvError) as e:   # no per-step outputs with payments within the step
+        rsv.rsv_compute_reserves(ctx, form, rsv.RSV_OUT_TRAJ, payment=payment, traj=np.zeros((n, 1201, 40)))
+    assert e.value.status == rsv.RSV_E_ARG
+
+
+def test_payment_fraction_needs_its_inputs(ctx):
+    tab = synth.gm_monthly_survival()
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, synth.portfolio_single_life(10))
+    rsv.rsv_load_scenarios(ctx, synth.vasicek_paths(8, 1200, seed=1))
+    with pytest.raises(rsv.RsvError) as e:
+        rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_V0, payment=rsv.RSV_PAY_FRACTION,
+                                 V0d=np.zeros((10, 8)))
+    assert e.value.status == rsv.RSV_E_STATE
+    with pytest.raises(rsv.RsvError) as e:
+        rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_V0, payment=7, V0d=np.zeros((10, 8)))
+    assert e.value.status == rsv.RSV_E_ARG
