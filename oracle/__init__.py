@@ -71,6 +71,12 @@ def _load(path=None):
                                                i32, i32, dp, i32, i32, dp, i32, i32, dp, dp]
             lib.orc_reserves_batch_method.argtypes = [i64, ip, ip, ip, ip, ip, ip, ip, dp, dp,
                                                       i32, i32, dp, i32, i32, dp, i32, i32, i32, dp, dp]
+            lib.orc_chain_cf.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                         C.c_int, dp, dp, dp, dp, C.c_int, dp, dp, dp, C.c_int, C.c_int, dp]
+            lib.orc_reserves_batch_cf.argtypes = [i64, ip, ip, ip, ip, ip, ip, ip, dp, dp,
+                                                  i32, i32, dp, i32, i32, dp, dp, i32, i32, i32, dp, dp]
+            lib.orc_schedule.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                         C.c_double, dp]
             lib.orc_max_threads.restype = C.c_int
             if hasattr(lib, "orc_nested_node"):
                 _bind_nested(lib)
@@ -128,14 +134,25 @@ def steps(product: int, age1: int, age2: int, term: int, n_ages: int, horizon: i
     return S, rS[: n_states(product)].copy()
 
 
+def schedule(n_steps: int, every: int = 1, first: int = 0, since: int = 0, steps_per_year: int = 12,
+             escalation: float = 0.0, increase: float = 0.0) -> np.ndarray:
+    """Cash-flow multipliers c_t of a payment schedule (see ``orc_schedule``)."""
+    cf = np.zeros(n_steps)
+    st = _load().orc_schedule(n_steps, every, first, since, steps_per_year, escalation, increase, _p(cf))
+    if st != 0:
+        raise ValueError("bad schedule parameters")
+    return cf
+
+
 def chain(product: int, age1: int, amount: float, table_x, v, *, age2: int = 0, term: int = 0,
-          rho: float = 0.0, table_y=None, table_fx=None, table_fy=None, vf=None, horizon: int = 0,
-          method: str = "recurrence") -> np.ndarray:
+          rho: float = 0.0, table_y=None, table_fx=None, table_fy=None, vf=None, cf=None,
+          horizon: int = 0, method: str = "recurrence") -> np.ndarray:
     """Reserve vectors r_t, t = 0..S, of one policy under one discount sequence.
 
     Returns an array [S+1, n] (full state space).  ``table_fx``/``table_fy`` and
     ``vf`` give survival and discounting over the fraction f of a step; they
-    default to the one-step ones (f = 1).
+    default to the one-step ones (f = 1).  ``cf`` (length >= S) scales the
+    nominal cash-flow vector of each step (default: level).
     """
     lib = _load()
     tx = _d(table_x)
@@ -147,20 +164,26 @@ def chain(product: int, age1: int, amount: float, table_x, v, *, age2: int = 0, 
     n = n_states(product)
     out = np.zeros((len(v) + 1) * n)
     m = {"recurrence": 0, "summation": 1}[method]
-    S = lib.orc_chain(product, age1, age2, term, amount, rho, len(tx), _p(tx), _p(ty), _p(tfx),
-                      _p(tfy), len(v), _p(v), _p(vf), horizon, m, _p(out))
+    cfa = None
+    if cf is not None:
+        cfa = np.zeros(len(v))
+        cfa[: min(len(v), len(cf))] = _d(cf)[: len(v)]
+    S = lib.orc_chain_cf(product, age1, age2, term, amount, rho, len(tx), _p(tx), _p(ty), _p(tfx),
+                         _p(tfy), len(v), _p(v), _p(vf), _p(cfa) if cfa is not None else None, horizon, m,
+                         _p(out))
     if S < 0:
         raise ValueError(f"orc_chain failed with code {S}")
     return out[: (S + 1) * n].reshape(S + 1, n)
 
 
 def reserves_batch(pol: dict, tables, v, horizon: int = 0, nthreads: int = 0, totals: bool = True,
-                   method: str = "recurrence"):
+                   method: str = "recurrence", cf=None):
     """V0[p, s] (FP64) of every policy in every scenario, f = 1, by the recurrence
     (or, with ``method="summation"``, by the summation definition at every step).
 
     ``pol`` is a dict of arrays as made by ``synth``; ``tables`` is [n_tables,
-    n_ages] or [n_ages]; ``v`` is [n_scen, n_steps].  Returns (V0, scen_total).
+    n_ages] or [n_ages]; ``v`` is [n_scen, n_steps]; ``cf`` (optional) is
+    [n_pol, n_steps] cash-flow multipliers.  Returns (V0, scen_total).
     """
     lib = _load()
     tables = np.atleast_2d(_d(tables))
@@ -171,12 +194,18 @@ def reserves_batch(pol: dict, tables, v, horizon: int = 0, nthreads: int = 0, to
     a = {k: _i(pol[k]) for k in ("product", "age1_m", "age2_m", "term_m", "state0", "table1", "table2")}
     amount, rho = _d(pol["amount"]), _d(pol["reversion"])
     m = {"recurrence": 0, "summation": 1}[method]
-    st = lib.orc_reserves_batch_method(n, _p(a["product"], C.c_int32), _p(a["age1_m"], C.c_int32),
-                                       _p(a["age2_m"], C.c_int32), _p(a["term_m"], C.c_int32),
-                                       _p(a["state0"], C.c_int32), _p(a["table1"], C.c_int32),
-                                       _p(a["table2"], C.c_int32), _p(amount), _p(rho),
-                                       tables.shape[0], tables.shape[1], _p(tables), v.shape[0], v.shape[1],
-                                       _p(v), horizon, nthreads, m, _p(V0), _p(tot) if totals else None)
+    cfa = None
+    if cf is not None:
+        cfa = _d(cf)
+        if cfa.shape != (n, v.shape[1]):
+            raise ValueError("cf must be [n_pol, n_steps]")
+    st = lib.orc_reserves_batch_cf(n, _p(a["product"], C.c_int32), _p(a["age1_m"], C.c_int32),
+                                   _p(a["age2_m"], C.c_int32), _p(a["term_m"], C.c_int32),
+                                   _p(a["state0"], C.c_int32), _p(a["table1"], C.c_int32),
+                                   _p(a["table2"], C.c_int32), _p(amount), _p(rho),
+                                   tables.shape[0], tables.shape[1], _p(tables), v.shape[0], v.shape[1],
+                                   _p(v), _p(cfa) if cfa is not None else None, horizon, nthreads, m, _p(V0),
+                                   _p(tot) if totals else None)
     if st != 0:
         raise ValueError(f"orc_reserves_batch failed with code {st}")
     return V0, tot

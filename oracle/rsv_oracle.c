@@ -190,22 +190,27 @@ static void matmul(int n, const double *A, const double *B, double *C)
  * life), indexed by age in months; pfx/pfy: survival over the fraction f of
  * the step (equal to p1x/p1y when f = 1).  v[t]: discount factor over step t;
  * vf[t]: discount from t to t+f (v^f; equal to v when f = 1).
+ * cf[t] (NULL: all 1) scales the product's nominal cash-flow vector of
+ * step t: c_t = cf[t] c (Section 4.1.1: increasing, escalating and limited
+ * term annuities differ only in the sequence c_t; Section 4.6: the sequence
+ * carries the timing, e.g. one non-zero step in twelve for annual payments).
+ * The boundary r_S (an endowment's maturity sum) is not scaled.
  * method 0: backward recurrence, Eq. (generalForm); method 1: summation,
  * Eq. (basicReserveSummation).
  * r_out[(S+1) * n] receives r_t for t = 0..S (r_S is the boundary).
  * Returns S, or a negative code: -1 bad product, -2 scenario too short. */
-int orc_chain(int product, int age1, int age2, int term, double amount, double rho,
-              int n_ages, const double *p1x, const double *p1y,
-              const double *pfx, const double *pfy,
-              int n_steps, const double *v, const double *vf,
-              int horizon, int method, double *r_out)
+int orc_chain_cf(int product, int age1, int age2, int term, double amount, double rho,
+                 int n_ages, const double *p1x, const double *p1y,
+                 const double *pfx, const double *pfy,
+                 int n_steps, const double *v, const double *vf, const double *cf,
+                 int horizon, int method, double *r_out)
 {
-    double rS[ORC_MAXN], c[ORC_MAXN];
+    double rS[ORC_MAXN], c0[ORC_MAXN], c[ORC_MAXN];
     int n = orc_n_states(product);
     if (n < 0) return -1;
     int S = orc_steps(product, age1, age2, term, n_ages, horizon, amount, rS);
     if (S > n_steps) return -2;
-    orc_cashflow(product, amount, rho, c);
+    orc_cashflow(product, amount, rho, c0);
     for (int j = 0; j < n; ++j) r_out[S * n + j] = rS[j];
 
     if (method == 0) {
@@ -215,6 +220,7 @@ int orc_chain(int product, int age1, int age2, int term, double amount, double r
                            p1y ? table_at(p1y, n_ages, age2 + t) : 0.0, W1);
             orc_transition(product, table_at(pfx, n_ages, age1 + t),
                            pfy ? table_at(pfy, n_ages, age2 + t) : 0.0, Wf);
+            for (int j = 0; j < n; ++j) c[j] = cf ? cf[t] * c0[j] : c0[j];   /* c_t */
             matvec(n, Wf, c, a);                          /* W_{t,f} c_t     */
             matvec(n, W1, &r_out[(t + 1) * n], b);        /* W_{t,1} r_{t+1} */
             for (int j = 0; j < n; ++j) r_out[t * n + j] = vf[t] * a[j] + v[t] * b[j];
@@ -236,6 +242,7 @@ int orc_chain(int product, int age1, int age2, int term, double amount, double r
             orc_transition(product, table_at(pfx, n_ages, age1 + s),
                            pfy ? table_at(pfy, n_ages, age2 + s) : 0.0, Wf);
             matmul(n, M, Wf, P);                          /* w(t, s+f) */
+            for (int j = 0; j < n; ++j) c[j] = cf ? cf[s] * c0[j] : c0[j];   /* c_s */
             matvec(n, P, c, a);
             for (int j = 0; j < n; ++j) acc[j] += d * vf[s] * a[j];
             matmul(n, M, W1, M2);                         /* w(t, s+1) */
@@ -249,6 +256,45 @@ int orc_chain(int product, int age1, int age2, int term, double amount, double r
     return S;
 }
 
+int orc_chain(int product, int age1, int age2, int term, double amount, double rho,
+              int n_ages, const double *p1x, const double *p1y,
+              const double *pfx, const double *pfy,
+              int n_steps, const double *v, const double *vf,
+              int horizon, int method, double *r_out)
+{
+    return orc_chain_cf(product, age1, age2, term, amount, rho, n_ages, p1x, p1y, pfx, pfy,
+                        n_steps, v, vf, NULL, horizon, method, r_out);
+}
+
+/* Cash-flow multipliers of a payment schedule (Section 4.1.1 and 4.6), for
+ * steps t = 0 .. n_steps-1 from valuation:
+ *   cf[t] = [t >= first and (t - first) mod every == 0] (1 + increase n_t) (1 + escalation)^n_t,
+ *   n_t = floor((t + since) / steps_per_year),
+ * i.e. a payment every `every` steps starting at step `first`, with the level
+ * in force during step t raised at each policy anniversary: by `increase`
+ * times the initial level (arithmetic progression, an increasing annuity) and
+ * by the factor 1 + escalation (geometric progression, an escalating
+ * annuity).  `since` is the number of steps since the last anniversary at
+ * valuation (0 .. steps_per_year-1).  Returns 0, or -1 for bad parameters. */
+int orc_schedule(int n_steps, int every, int first, int since, int steps_per_year,
+                 double escalation, double increase, double *cf)
+{
+    if (n_steps < 0 || every < 1 || first < 0 || steps_per_year < 1 || since < 0 ||
+        since >= steps_per_year || !(escalation > -1.0) || !(increase >= 0.0))
+        return -1;
+    for (int t = 0; t < n_steps; ++t) {
+        if (t < first || (t - first) % every != 0) {
+            cf[t] = 0.0;
+            continue;
+        }
+        int n_t = (t + since) / steps_per_year;
+        double g = 1.0;
+        for (int k = 0; k < n_t; ++k) g *= 1.0 + escalation;
+        cf[t] = (1.0 + increase * n_t) * g;
+    }
+    return 0;
+}
+
 /* Reserves at valuation for a whole portfolio under n_scen scenarios, f = 1,
  * by the backward recurrence (method 0 of orc_chain) or, in
  * orc_reserves_batch_method with method 1, by the summation definition
@@ -260,16 +306,18 @@ int orc_chain(int product, int age1, int age2, int term, double amount, double r
  * receives the reserve of policy p in its valuation state state0[p];
  * scen_total[s] (optional) the sum of V0 over policies, summed in policy
  * order.  nthreads <= 0 uses the OpenMP default; policies are shared among
- * threads with a dynamic schedule.  Returns 0, or -1 bad record, -2 a
- * scenario shorter than a policy's projection. */
-int orc_reserves_batch_method(int64_t n_pol, const int32_t *product, const int32_t *age1,
-                              const int32_t *age2, const int32_t *term, const int32_t *state0,
-                              const int32_t *tab1, const int32_t *tab2,
-                              const double *amount, const double *rho,
-                              int32_t n_tables, int32_t n_ages, const double *tables,
-                              int32_t n_scen, int32_t n_steps, const double *v,
-                              int32_t horizon, int32_t nthreads, int32_t method,
-                              double *V0, double *scen_total)
+ * threads with a dynamic schedule.  cf (orc_reserves_batch_cf; NULL: level)
+ * holds the cash-flow multipliers cf[p * n_steps + t] of every policy (see
+ * orc_chain_cf).  Returns 0, or -1 bad record, -2 a scenario shorter than a
+ * policy's projection. */
+int orc_reserves_batch_cf(int64_t n_pol, const int32_t *product, const int32_t *age1,
+                          const int32_t *age2, const int32_t *term, const int32_t *state0,
+                          const int32_t *tab1, const int32_t *tab2,
+                          const double *amount, const double *rho,
+                          int32_t n_tables, int32_t n_ages, const double *tables,
+                          int32_t n_scen, int32_t n_steps, const double *v,
+                          const double *cf, int32_t horizon, int32_t nthreads, int32_t method,
+                          double *V0, double *scen_total)
 {
     int status = 0;
     (void)nthreads;
@@ -296,8 +344,9 @@ int orc_reserves_batch_method(int64_t n_pol, const int32_t *product, const int32
             const double *ty = tables + (size_t)tab2[p] * n_ages;
             for (int32_t s = 0; s < n_scen; ++s) {
                 const double *vs = v + (size_t)s * n_steps;
-                int S = orc_chain(product[p], age1[p], age2[p], term[p], amount[p], rho[p],
-                                  n_ages, tx, ty, tx, ty, n_steps, vs, vs, horizon, method, r);
+                int S = orc_chain_cf(product[p], age1[p], age2[p], term[p], amount[p], rho[p],
+                                     n_ages, tx, ty, tx, ty, n_steps, vs, vs,
+                                     cf ? cf + (size_t)p * n_steps : NULL, horizon, method, r);
                 if (S < 0) {
 #ifdef _OPENMP
 #pragma omp critical
@@ -317,6 +366,20 @@ int orc_reserves_batch_method(int64_t n_pol, const int32_t *product, const int32
             for (int32_t s = 0; s < n_scen; ++s) scen_total[s] += V0[p * n_scen + s];
     }
     return status;
+}
+
+int orc_reserves_batch_method(int64_t n_pol, const int32_t *product, const int32_t *age1,
+                              const int32_t *age2, const int32_t *term, const int32_t *state0,
+                              const int32_t *tab1, const int32_t *tab2,
+                              const double *amount, const double *rho,
+                              int32_t n_tables, int32_t n_ages, const double *tables,
+                              int32_t n_scen, int32_t n_steps, const double *v,
+                              int32_t horizon, int32_t nthreads, int32_t method,
+                              double *V0, double *scen_total)
+{
+    return orc_reserves_batch_cf(n_pol, product, age1, age2, term, state0, tab1, tab2, amount, rho,
+                                 n_tables, n_ages, tables, n_scen, n_steps, v, NULL, horizon, nthreads,
+                                 method, V0, scen_total);
 }
 
 int orc_reserves_batch(int64_t n_pol, const int32_t *product, const int32_t *age1,

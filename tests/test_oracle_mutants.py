@@ -12,6 +12,7 @@ import subprocess
 import pytest
 
 import oracle
+import tests.test_oracle_cashflows as cfpins
 import tests.test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "rsv_oracle.c")
@@ -31,6 +32,13 @@ MUTANTS = {
     "reversion_cash_flow": ("c[2] = rho * amount;", "c[2] = amount;"),
     "summation_discount_order": ("acc[j] += d * vf[s] * a[j];", "acc[j] += d * a[j];"),
     "summation_matrix_order": ("matmul(n, M, Wf, P);", "matmul(n, Wf, M, P);"),
+    # varying cash-flow sequences
+    "cash_flow_step_index": ("c[j] = cf ? cf[t] * c0[j] : c0[j];", "c[j] = cf ? cf[t > 0 ? t - 1 : 0] * c0[j] : c0[j];"),
+    "summation_cash_flow_index": ("c[j] = cf ? cf[s] * c0[j] : c0[j];", "c[j] = cf ? cf[t] * c0[j] : c0[j];"),
+    "schedule_anniversary_off_by_one": ("int n_t = (t + since) / steps_per_year;",
+                                        "int n_t = (t + since + 1) / steps_per_year;"),
+    "schedule_payment_phase": ("(t - first) % every != 0", "(t + first) % every != 0"),
+    "schedule_arithmetic_increase": ("cf[t] = (1.0 + increase * n_t) * g;", "cf[t] = (1.0 + increase * t) * g;"),
 }
 
 PIN_CHECKS = [
@@ -43,6 +51,12 @@ PIN_CHECKS = [
     lambda: pins.test_printed_assurance_and_endowment_recurrences(),
     lambda: pins.test_transition_rows_sum_to_one_and_upper_triangular(1),
     lambda: pins.test_two_life_matrix_entries(),
+    lambda: cfpins.test_escalating_annuity_geometric_series(0.05),
+    lambda: cfpins.test_increasing_annuity_arithmetic_geometric_series(0.1),
+    lambda: cfpins.test_increasing_annuity_monthly_steps(),
+    lambda: cfpins.test_annual_payments_on_monthly_steps(0.05),
+    lambda: cfpins.test_anniversary_phase_moves_the_escalation(),
+    lambda: cfpins.test_brute_force_with_cash_flows(0),
 ]
 
 
