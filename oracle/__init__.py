@@ -27,6 +27,7 @@ _lib = None
 
 SL_ANNUITY, JL_REVERSIONARY, TERM_ASSURANCE, ENDOWMENT = 0, 1, 2, 3
 JOINT_ANNUITY, LAST_SURVIVOR, JOINT_TERM, JOINT_ENDOWMENT = 4, 5, 6, 7
+LS_TERM, LS_ENDOWMENT = 8, 9
 
 CFLAGS = ["-std=gnu99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp"]
 
@@ -77,6 +78,9 @@ def _load(path=None):
                                                   i32, i32, dp, i32, i32, dp, dp, i32, i32, i32, dp, dp]
             lib.orc_schedule.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                          C.c_double, dp]
+            lib.orc_full_state.argtypes = [C.c_int, C.c_int]
+            lib.orc_mlife_transition.argtypes = [C.c_int, C.c_int, dp, dp]
+            lib.orc_mlife_chain.argtypes = [C.c_int, C.c_int, C.c_int, dp, ip, dp, dp, C.c_int, dp, dp]
             lib.orc_max_threads.restype = C.c_int
             if hasattr(lib, "orc_nested_node"):
                 _bind_nested(lib)
@@ -111,6 +115,11 @@ def n_states(product: int) -> int:
     return _load().orc_n_states(product)
 
 
+def full_state(product: int, state0: int) -> int:
+    """Index in the full state vector of a record's reduced valuation state."""
+    return _load().orc_full_state(product, state0)
+
+
 def transition(product: int, px: float, py: float = 0.0) -> np.ndarray:
     """Full-state W (row = state at the start, column = state at the end)."""
     n = n_states(product)
@@ -129,7 +138,7 @@ def cashflow(product: int, amount: float, rho: float = 0.0) -> np.ndarray:
 def steps(product: int, age1: int, age2: int, term: int, n_ages: int, horizon: int = 0,
           amount: float = 1.0):
     """(S, boundary vector r_S) of a policy."""
-    rS = np.zeros(4)
+    rS = np.zeros(9)
     S = _load().orc_steps(product, age1, age2, term, n_ages, horizon, amount, _p(rS))
     return S, rS[: n_states(product)].copy()
 
@@ -142,6 +151,33 @@ def schedule(n_steps: int, every: int = 1, first: int = 0, since: int = 0, steps
     if st != 0:
         raise ValueError("bad schedule parameters")
     return cf
+
+
+def mlife_transition(m: int, model: int, p) -> np.ndarray:
+    """W^m of m lives (Section 4.3) for survival probabilities p[0..m-1]."""
+    n = model ** m
+    W = np.zeros(81 * 81)
+    pp = _d(np.asarray(p, float).reshape(-1)) if m > 0 else np.zeros(1)
+    if _load().orc_mlife_transition(m, model, _p(pp), _p(W)) != n:
+        raise ValueError("bad m-life model")
+    return W[: n * n].reshape(n, n)
+
+
+def mlife_chain(m: int, model: int, tables, ages, c, rS, S: int, v) -> np.ndarray:
+    """Reserve vectors r_t, t = 0..S, of an m-life contract: [S+1, model^m]."""
+    n = model ** m
+    tabs = np.atleast_2d(_d(tables))
+    if tabs.shape[0] != m:
+        raise ValueError("one table row per life")
+    ag = _i(ages)
+    cc, rr, vv = _d(c), _d(rS), _d(v)
+    if len(cc) != n or len(rr) != n or len(vv) < S:
+        raise ValueError("bad sizes")
+    out = np.zeros((S + 1) * n)
+    if _load().orc_mlife_chain(m, model, tabs.shape[1], _p(tabs), _p(ag, C.c_int32), _p(cc), _p(rr), S,
+                               _p(vv), _p(out)) != n:
+        raise ValueError("orc_mlife_chain failed")
+    return out.reshape(S + 1, n)
 
 
 def chain(product: int, age1: int, amount: float, table_x, v, *, age2: int = 0, term: int = 0,

@@ -41,6 +41,7 @@
 int orc_n_states(int product);
 int orc_transition(int product, double px, double py, double *W);
 int orc_steps(int product, int age1, int age2, int term, int n_ages, int horizon, double amount, double *rS);
+int orc_full_state(int product, int state0);
 int orc_chain(int product, int age1, int age2, int term, double amount, double rho, int n_ages,
               const double *p1x, const double *p1y, const double *pfx, const double *pfy, int n_steps,
               const double *v, const double *vf, int horizon, int method, double *r_out);
@@ -157,13 +158,13 @@ int orc_nested_node(int64_t n_pol, const int32_t *prod, const int32_t *ipol, con
     /* longest remaining projection at the node */
     int Lmax = 0;
     for (int64_t p = 0; p < n_pol; ++p) {
-        double rS[4];
+        double rS[9];
         const int32_t *ip = ipol + 6 * p;
         int S = orc_steps(prod[p], ip[0], ip[1], ip[2], n_ages, 0, 1.0, rS);
         if (S - m > Lmax) Lmax = S - m;
     }
     double *vi = (double *)malloc(sizeof(double) * (Lmax > 0 ? Lmax : 1));
-    double *r = (double *)malloc(sizeof(double) * 4 * ((size_t)Lmax + 2));
+    double *r = (double *)malloc(sizeof(double) * 9 * ((size_t)Lmax + 2));
     if (!vi || !r) { free(vi); free(r); return -3; }
     for (int k = 0; k < n_idx; ++k) {
         path(seed, (uint32_t)idx[k], (uint32_t)n, (3u << 24) | (uint32_t)o, &s, r_node, Lmax, vi, NULL);
@@ -176,15 +177,17 @@ int orc_nested_node(int64_t n_pol, const int32_t *prod, const int32_t *ipol, con
                 free(vi); free(r);
                 return -1;
             }
-            double rS[4];
+            double rS[9];
             int S = orc_steps(product, a1, a2, term, n_ages, 0, 1.0, rS);
             if (S < m) continue;                                  /* ended before the node */
             const int annuity = product == 0 || product == 1 || product == 4 || product == 5;
             if (annuity && term > 0 && term <= m) continue;       /* limited-term annuity over */
             const double *tx = tables + (size_t)ip[4] * n_ages, *ty = tables + (size_t)ip[5] * n_ages;
             /* full-state distribution at the node: e_{state0} times the one-step matrices */
-            double pi[4] = {0, 0, 0, 0}, nx[4], W[16];
-            pi[st0] = 1.0;
+            double pi[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, nx[9], W[81];
+            const int full = orc_full_state(product, st0);
+            if (full < 0 || full >= nst) { free(vi); free(r); return -1; }
+            pi[full] = 1.0;
             for (int u = 0; u < m; ++u) {
                 double px = (a1 + u < n_ages) ? tx[a1 + u] : 0.0;
                 double py = (a2 + u < n_ages) ? ty[a2 + u] : 0.0;

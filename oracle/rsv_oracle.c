@@ -39,7 +39,7 @@
 #include <omp.h>
 #endif
 
-#define ORC_MAXN 4
+#define ORC_MAXN 9
 
 enum {
     ORC_SL_ANNUITY = 0, ORC_JL_REVERSIONARY = 1, ORC_TERM_ASSURANCE = 2, ORC_ENDOWMENT = 3,
@@ -48,8 +48,13 @@ enum {
     ORC_JOINT_ANNUITY = 4,       /* paid while both lives are alive            */
     ORC_LAST_SURVIVOR = 5,       /* paid while at least one life is alive      */
     ORC_JOINT_TERM = 6,          /* sum paid at the end of the step of the first death */
-    ORC_JOINT_ENDOWMENT = 7      /* the same, or at maturity if both are alive */
+    ORC_JOINT_ENDOWMENT = 7,     /* the same, or at maturity if both are alive */
+    /* the two-life assurance model of Section 4.2.3 (nine states) */
+    ORC_LS_TERM = 8,             /* sum paid at the end of the step of the second death */
+    ORC_LS_ENDOWMENT = 9         /* the same, or at maturity if at least one is alive */
 };
+
+static int nine_state(int product) { return product == ORC_LS_TERM || product == ORC_LS_ENDOWMENT; }
 
 static int two_state_life(int product) { return product == ORC_JL_REVERSIONARY || product == ORC_JOINT_ANNUITY || product == ORC_LAST_SURVIVOR; }
 
@@ -68,8 +73,21 @@ int orc_n_states(int product)
     case ORC_ENDOWMENT:
     case ORC_JOINT_TERM:
     case ORC_JOINT_ENDOWMENT: return 3;
+    case ORC_LS_TERM:
+    case ORC_LS_ENDOWMENT: return 9;
     default: return -1;
     }
+}
+
+/* Index in the full state vector of a reduced valuation state (the record's
+ * state0: 0 = every life alive; for the two-life models 1 = only the first
+ * life alive, 2 = only the second).  The nine-state model labels state
+ * 3 i_x + i_y with i = 0 alive, 1 died in the step, 2 dead (Section 4.2.3),
+ * so "only x alive" is (0, 2) = 2 and "only y alive" (2, 0) = 6. */
+int orc_full_state(int product, int state0)
+{
+    if (nine_state(product)) return state0 == 0 ? 0 : (state0 == 1 ? 2 : (state0 == 2 ? 6 : -1));
+    return state0;
 }
 
 /* W_{x,t,g} for survival probabilities px = gp_x (and py = gp_y for two
@@ -89,6 +107,18 @@ int orc_transition(int product, double px, double py, double *W)
         W[1 * 4 + 1] = px; W[1 * 4 + 3] = qx;
         W[2 * 4 + 2] = py; W[2 * 4 + 3] = qy;
         W[3 * 4 + 3] = 1.0;
+    } else if (nine_state(product)) {
+        /* Section 4.2.3: the assurance model of Section 4.1.3 for both lives,
+         * state 3 i_x + i_y; a "died in the step" state moves to "dead" */
+        W[0 * 9 + 0] = px * py; W[0 * 9 + 1] = px * qy; W[0 * 9 + 3] = qx * py; W[0 * 9 + 4] = qx * qy;
+        W[1 * 9 + 2] = px; W[1 * 9 + 5] = qx;
+        W[2 * 9 + 2] = px; W[2 * 9 + 5] = qx;
+        W[3 * 9 + 6] = py; W[3 * 9 + 7] = qy;
+        W[4 * 9 + 8] = 1.0;
+        W[5 * 9 + 8] = 1.0;
+        W[6 * 9 + 6] = py; W[6 * 9 + 7] = qy;
+        W[7 * 9 + 8] = 1.0;
+        W[8 * 9 + 8] = 1.0;
     } else if (product == ORC_JOINT_TERM || product == ORC_JOINT_ENDOWMENT) {
         /* three states of the joint status: both alive / first death in the step / after */
         W[0 * 3 + 0] = px * py; W[0 * 3 + 1] = 1.0 - px * py;
@@ -108,7 +138,9 @@ int orc_transition(int product, double px, double py, double *W)
  *   joint-life annuity:        (A, 0, 0, 0): while both live
  *   last-survivor annuity:     (A, A, A, 0): while either lives
  *   term / endowment (4.1.3) and their joint-status forms:
- *                              (0, A, 0): benefit in the "died in step" state */
+ *                              (0, A, 0): benefit in the "died in step" state
+ *   second-death term / endowment (4.2.3), nine states 3 i_x + i_y:
+ *                              A in (1,1), (1,2), (2,1): the second death in the step */
 int orc_cashflow(int product, double amount, double rho, double *c)
 {
     int n = orc_n_states(product);
@@ -118,6 +150,7 @@ int orc_cashflow(int product, double amount, double rho, double *c)
     else if (product == ORC_JL_REVERSIONARY) { c[0] = amount; c[1] = amount; c[2] = rho * amount; }
     else if (product == ORC_JOINT_ANNUITY) c[0] = amount;
     else if (product == ORC_LAST_SURVIVOR) { c[0] = amount; c[1] = amount; c[2] = amount; }
+    else if (nine_state(product)) { c[4] = amount; c[5] = amount; c[7] = amount; }   /* second death */
     else c[1] = amount;
     return n;
 }
@@ -127,7 +160,8 @@ int orc_cashflow(int product, double amount, double rho, double *c)
  * means p_k = 0 for k >= n_ages, so S = n_ages - (youngest age) (Sections
  * 4.1.1, 4.2.1: sp_120 = 0).  term_m > 0 limits the term.  Assurances run for
  * their term.  An endowment pays its sum at maturity if alive: boundary
- * r_S = (A, 0, 0) (Section 4.1.2, A_{x+n:0} = 1).  A horizon > 0 truncates
+ * r_S = (A, 0, 0) (Section 4.1.2, A_{x+n:0} = 1); the second-death
+ * endowment if either life is alive.  A horizon > 0 truncates
  * the projection with r_horizon = 0, dropping later cash flows. */
 int orc_steps(int product, int age1, int age2, int term, int n_ages, int horizon,
               double amount, double *rS)
@@ -154,6 +188,9 @@ int orc_steps(int product, int age1, int age2, int term, int n_ages, int horizon
         S = horizon;                          /* truncated: r_S = 0 */
     } else if (product == ORC_ENDOWMENT || product == ORC_JOINT_ENDOWMENT) {
         rS[0] = amount;
+    } else if (product == ORC_LS_ENDOWMENT) {
+        /* at maturity, every state with a life alive: (0,0), (0,1), (0,2), (1,0), (2,0) */
+        rS[0] = rS[1] = rS[2] = rS[3] = rS[6] = amount;
     }
     return S;
 }
@@ -295,6 +332,68 @@ int orc_schedule(int n_steps, int every, int first, int since, int steps_per_yea
     return 0;
 }
 
+/* ---- m lives (Section 4.3) ----------------------------------------------
+ * The transition matrix of m independent lives by induction over the lives,
+ *   W^m = W^{m-1} (x) w_m,  W^0 = (1),
+ * with w the single-life matrix of the two-state model [[p, q], [0, 1]]
+ * (model 2: annuities and endowments, states alive/dead) or of the
+ * three-state model [[p, q, 0], [0, 0, 1], [0, 0, 1]] (model 3: assurances,
+ * states alive/died in the step/dead).  The Kronecker product makes life 1
+ * the most significant digit of the state index (base 2 or 3).  p[i] is the
+ * survival probability of life i over the step.  W receives n x n row-major,
+ * n = 2^m or 3^m; returns n, or -1 for m outside 0..4 or a bad model. */
+int orc_mlife_transition(int m, int model, const double *p, double *W)
+{
+    if (m < 0 || m > 4 || (model != 2 && model != 3)) return -1;
+    double A[81 * 81], w[9];
+    int n = 1;
+    W[0] = 1.0;
+    for (int i = 0; i < m; ++i) {
+        const int k = model;
+        for (int e = 0; e < k * k; ++e) w[e] = 0.0;
+        if (k == 2) {
+            w[0] = p[i]; w[1] = 1.0 - p[i]; w[3] = 1.0;
+        } else {
+            w[0] = p[i]; w[1] = 1.0 - p[i]; w[5] = 1.0; w[8] = 1.0;
+        }
+        memcpy(A, W, sizeof(double) * n * n);
+        const int nn = n * k;
+        for (int r1 = 0; r1 < n; ++r1)
+            for (int r2 = 0; r2 < k; ++r2)
+                for (int c1 = 0; c1 < n; ++c1)
+                    for (int c2 = 0; c2 < k; ++c2)
+                        W[(r1 * k + r2) * nn + (c1 * k + c2)] = A[r1 * n + c1] * w[r2 * k + c2];
+        n = nn;
+    }
+    return n;
+}
+
+/* Reserve vectors of an m-life contract under one discount sequence, for
+ * t = 0..S: the backward recurrence of Eq. (generalForm) with f = 1 and a
+ * cash-flow vector c fixed over the steps, r_t = v_t W^m_t (c + r_{t+1}),
+ * from the boundary r_S.  tables holds m rows of n_ages one-step survival
+ * probabilities; life i is aged ages[i] at t = 0 (probability 0 at or beyond
+ * the table's end).  r_out receives (S + 1) x n.  Returns n, or -1. */
+int orc_mlife_chain(int m, int model, int n_ages, const double *tables, const int *ages,
+                    const double *c, const double *rS, int S, const double *v, double *r_out)
+{
+    if (m < 0 || m > 4 || (model != 2 && model != 3) || S < 0) return -1;
+    double p[4], x[81], *W = (double *)malloc(sizeof(double) * 81 * 81);
+    if (!W) return -1;
+    int n = 1;
+    for (int i = 0; i < m; ++i) n *= model;
+    memcpy(&r_out[(size_t)S * n], rS, sizeof(double) * n);
+    for (int t = S - 1; t >= 0; --t) {
+        for (int i = 0; i < m; ++i) p[i] = table_at(tables + (size_t)i * n_ages, n_ages, ages[i] + t);
+        orc_mlife_transition(m, model, p, W);
+        for (int j = 0; j < n; ++j) x[j] = c[j] + r_out[(size_t)(t + 1) * n + j];
+        matvec(n, W, x, &r_out[(size_t)t * n]);
+        for (int j = 0; j < n; ++j) r_out[(size_t)t * n + j] *= v[t];
+    }
+    free(W);
+    return n;
+}
+
 /* Reserves at valuation for a whole portfolio under n_scen scenarios, f = 1,
  * by the backward recurrence (method 0 of orc_chain) or, in
  * orc_reserves_batch_method with method 1, by the summation definition
@@ -332,8 +431,9 @@ int orc_reserves_batch_cf(int64_t n_pol, const int32_t *product, const int32_t *
 #endif
         for (int64_t p = 0; p < n_pol; ++p) {
             int n = orc_n_states(product[p]);
+            int full = orc_full_state(product[p], state0[p]);
             if (!r || n < 0 || tab1[p] < 0 || tab1[p] >= n_tables || tab2[p] < 0 ||
-                tab2[p] >= n_tables || state0[p] < 0 || state0[p] >= n) {
+                tab2[p] >= n_tables || state0[p] < 0 || full < 0 || full >= n) {
 #ifdef _OPENMP
 #pragma omp critical
 #endif
@@ -355,7 +455,7 @@ int orc_reserves_batch_cf(int64_t n_pol, const int32_t *product, const int32_t *
                     V0[p * n_scen + s] = 0.0;
                     continue;
                 }
-                V0[p * n_scen + s] = r[state0[p]];
+                V0[p * n_scen + s] = r[full];
             }
         }
         free(r);

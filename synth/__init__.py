@@ -32,6 +32,8 @@ JOINT_ANNUITY = 4       # paid while both lives are alive
 LAST_SURVIVOR = 5       # paid while at least one life is alive
 JOINT_TERM = 6          # sum at the end of the month of the first death within the term
 JOINT_ENDOWMENT = 7     # joint term assurance + maturity payment if both are alive
+LS_TERM = 8             # sum at the end of the month of the second death within the term
+LS_ENDOWMENT = 9        # second-death term assurance + maturity payment if either is alive
 
 PRODUCT_NAMES = {SL_ANNUITY: "sl_annuity", JL_REVERSIONARY: "jl_reversionary",
                  TERM_ASSURANCE: "term_assurance", ENDOWMENT: "endowment"}
@@ -123,25 +125,48 @@ def portfolio_mix(n: int = 100_000, seed: int = 0, age_lo_y: int = 20, age_hi_y:
     return pol
 
 
-def portfolio_two_life(n: int = 10_000, seed: int = 0, age_lo_y: int = 20, age_hi_y: int = 85) -> dict:
-    """Equal shares of the two-life products: joint-life annuities, last-survivor
-    annuities, joint-life term assurances (terms 5-40 y) and joint-life
-    endowments (terms 10-30 y).  Both ages uniform over whole months in
-    [age_lo_y, age_hi_y] years; amounts as in ``portfolio_mix``."""
+def portfolio_two_life(n: int = 10_000, seed: int = 0, age_lo_y: int = 20, age_hi_y: int = 85,
+                       products=(JOINT_ANNUITY, LAST_SURVIVOR, JOINT_TERM, JOINT_ENDOWMENT)) -> dict:
+    """Equal shares of the two-life products: by default joint-life annuities,
+    last-survivor annuities, joint-life term assurances (terms 5-40 y) and
+    joint-life endowments (terms 10-30 y); the second-death term assurances and
+    endowments (LS_TERM, LS_ENDOWMENT) take the same terms.  Both ages uniform
+    over whole months in [age_lo_y, age_hi_y] years; amounts as in
+    ``portfolio_mix``."""
     rng = np.random.default_rng([seed, 2])
-    prod = np.resize(np.arange(JOINT_ANNUITY, JOINT_ENDOWMENT + 1, dtype=np.int32), n)
+    prod = np.resize(np.asarray(products, dtype=np.int32), n)
     rng.shuffle(prod)
     pol = _policy_arrays(n)
     pol["product"][:] = prod
     pol["age1_m"][:] = rng.integers(age_lo_y * 12, age_hi_y * 12 + 1, size=n)
     pol["age2_m"][:] = rng.integers(age_lo_y * 12, age_hi_y * 12 + 1, size=n)
-    term_y = np.where(prod == JOINT_TERM, rng.integers(5, 41, size=n),
-                      np.where(prod == JOINT_ENDOWMENT, rng.integers(10, 31, size=n), 0))
+    term_y = np.where(np.isin(prod, (JOINT_TERM, LS_TERM)), rng.integers(5, 41, size=n),
+                      np.where(np.isin(prod, (JOINT_ENDOWMENT, LS_ENDOWMENT)), rng.integers(10, 31, size=n), 0))
     pol["term_m"][:] = term_y * 12
     ann = rng.lognormal(math.log(1.0e4), 0.5, size=n) / 12.0
     sums = rng.lognormal(math.log(1.0e5), 0.5, size=n)
     pol["amount"][:] = np.where(prod <= LAST_SURVIVOR, ann, sums)
     return pol
+
+
+def payment_schedules(n: int, seed: int = 0, annual_share: float = 0.2, escalating_share: float = 0.05,
+                      increasing_share: float = 0.0, steps_per_year: int = 12) -> dict:
+    """Payment-schedule parameters per policy (the fields of ``rsv_schedule``),
+    drawn like the paper's cohort of new annuities (Section 5): about 80% paid
+    monthly and the rest annually on the policy anniversary; about 95% level and
+    the rest escalating at 3%, 4.25% or 5% on each anniversary; optionally a
+    share increasing by 5-20% of the initial level per year.  The months since
+    the last anniversary are uniform (inception uniform over the last year).
+    Parameters only: the cash flows themselves are the consumer's to expand."""
+    rng = np.random.default_rng(seed + 7_000_003)
+    since = rng.integers(0, steps_per_year, n).astype(np.int32)
+    annual = rng.uniform(size=n) < annual_share
+    every = np.where(annual, steps_per_year, 1).astype(np.int32)
+    first = np.where(annual, steps_per_year - 1 - since, 0).astype(np.int32)
+    esc = np.where(rng.uniform(size=n) < escalating_share, rng.choice([0.03, 0.0425, 0.05], n), 0.0)
+    inc = np.where(rng.uniform(size=n) < increasing_share, rng.uniform(0.05, 0.2, n), 0.0)
+    return {"every": every, "first": first, "since": since,
+            "steps_per_year": np.full(n, steps_per_year, np.int32), "escalation": esc, "increase": inc}
 
 
 def take(pol: dict, idx) -> dict:

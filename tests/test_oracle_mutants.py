@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 import tests.test_oracle_cashflows as cfpins
+import tests.test_oracle_mlife as mlpins
 import tests.test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "rsv_oracle.c")
@@ -39,6 +40,18 @@ MUTANTS = {
                                         "int n_t = (t + since + 1) / steps_per_year;"),
     "schedule_payment_phase": ("(t - first) % every != 0", "(t + first) % every != 0"),
     "schedule_arithmetic_increase": ("cf[t] = (1.0 + increase * n_t) * g;", "cf[t] = (1.0 + increase * t) * g;"),
+    # the nine-state two-life assurance model and the m-life tensor products
+    "nine_state_entries_swapped": ("W[3 * 9 + 6] = py; W[3 * 9 + 7] = qy;", "W[3 * 9 + 6] = qy; W[3 * 9 + 7] = py;"),
+    "second_death_cash_flow": ("c[4] = amount; c[5] = amount; c[7] = amount;",
+                               "c[4] = amount; c[5] = amount; c[6] = amount;"),
+    "second_death_endowment_boundary": ("rS[0] = rS[1] = rS[2] = rS[3] = rS[6] = amount;",
+                                        "rS[0] = rS[2] = rS[6] = amount;"),
+    "reduced_state_index": ("state0 == 1 ? 2 :", "state0 == 1 ? 1 :"),
+    "kronecker_column_order": ("W[(r1 * k + r2) * nn + (c1 * k + c2)] = A[r1 * n + c1] * w[r2 * k + c2];",
+                               "W[(r1 * k + r2) * nn + (c2 * n + c1)] = A[r1 * n + c1] * w[r2 * k + c2];"),
+    "three_state_factor": ("w[0] = p[i]; w[1] = 1.0 - p[i]; w[5] = 1.0; w[8] = 1.0;",
+                           "w[0] = p[i]; w[1] = 1.0 - p[i]; w[4] = 1.0; w[8] = 1.0;"),
+    "mlife_discount_index": ("r_out[(size_t)t * n + j] *= v[t];", "r_out[(size_t)t * n + j] *= v[t > 0 ? t - 1 : 0];"),
 }
 
 PIN_CHECKS = [
@@ -57,6 +70,13 @@ PIN_CHECKS = [
     lambda: cfpins.test_annual_payments_on_monthly_steps(0.05),
     lambda: cfpins.test_anniversary_phase_moves_the_escalation(),
     lambda: cfpins.test_brute_force_with_cash_flows(0),
+    lambda: mlpins.test_printed_two_life_matrices(0.9, 0.7),
+    lambda: mlpins.test_mlife_nonzero_counts_and_rows(3),
+    lambda: mlpins.test_full_state_of_the_reduced_valuation_states(),
+    lambda: mlpins.test_closed_forms_second_and_first_death(48),
+    lambda: mlpins.test_closed_form_joint_life_of_m_lives(3),
+    lambda: mlpins.test_brute_force_second_death(0),
+    lambda: mlpins.test_brute_force_three_lives(2),
 ]
 
 
