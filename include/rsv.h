@@ -33,6 +33,13 @@
  *   RSV_JOINT_TERM       the sum at the end of the month of the first death
  *                        within the term: r = v ((1 - px py) S + px py r').
  *   RSV_JOINT_ENDOWMENT  RSV_JOINT_TERM plus the sum at maturity if both are alive.
+ *   The nine-state two-life assurance model of Section 4.2.3 (each life
+ *   alive / died in the step / dead) with the benefit on the second death,
+ *   reduced to 3 states: both alive, only the first, only the second:
+ *   RSV_LS_TERM          the sum at the end of the month of the second death
+ *                        within the term: rx = v (qx S + px rx'), likewise ry,
+ *                        r00 = v (qx qy S + px qy rx' + qx py ry' + px py r00').
+ *   RSV_LS_ENDOWMENT     RSV_LS_TERM plus the sum at maturity if either is alive.
  *
  * Conventions shared by every entry point:
  *  - Status codes only; no C++ exception crosses the ABI.  On failure the
@@ -73,7 +80,8 @@ typedef enum {
 
 enum {
     RSV_SL_ANNUITY = 0, RSV_JL_REVERSIONARY = 1, RSV_TERM_ASSURANCE = 2, RSV_ENDOWMENT = 3,
-    RSV_JOINT_ANNUITY = 4, RSV_LAST_SURVIVOR = 5, RSV_JOINT_TERM = 6, RSV_JOINT_ENDOWMENT = 7
+    RSV_JOINT_ANNUITY = 4, RSV_LAST_SURVIVOR = 5, RSV_JOINT_TERM = 6, RSV_JOINT_ENDOWMENT = 7,
+    RSV_LS_TERM = 8, RSV_LS_ENDOWMENT = 9
 };
 
 /* Arithmetic of the recurrence. */
@@ -94,14 +102,14 @@ enum {
 
 /* One policy record (48 bytes). */
 typedef struct {
-    int32_t product;   /* RSV_SL_ANNUITY .. RSV_JOINT_ENDOWMENT                        */
+    int32_t product;   /* RSV_SL_ANNUITY .. RSV_LS_ENDOWMENT                           */
     int32_t age1_m;    /* age of the (first) life at valuation, whole months >= 0      */
     int32_t age2_m;    /* age of the second life; two-life products only               */
     int32_t term_m;    /* term in months; 0 = whole life (annuities only); assurances
                           and endowments need term_m >= 0                              */
-    int32_t state0;    /* reduced state at valuation: 0 for every product; the JL
-                          and last-survivor products also accept 1 (only the first
-                          life alive) and 2 (only the second life alive)               */
+    int32_t state0;    /* reduced state at valuation: 0 for every product; the JL,
+                          last-survivor and second-death products also accept 1
+                          (only the first life alive) and 2 (only the second)          */
     int32_t table1;    /* decrement table of the first life                            */
     int32_t table2;    /* decrement table of the second life (two-life products)       */
     int32_t reserved;  /* must be 0                                                    */
@@ -210,6 +218,56 @@ rsv_status rsv_load_decrements_fraction(rsv_ctx *ctx, int32_t table_id, const do
 rsv_status rsv_load_scenarios_fraction(rsv_ctx *ctx, const double *v_f, int32_t n_scen, int32_t n_steps,
                                        int32_t layout);
 
+/* ---- Varying cash flows ---------------------------------------------------
+ * Section 4.1.1: level, increasing, escalating and limited-term annuities
+ * differ only in the cash-flow sequence c_t; Section 4.6: with monthly steps
+ * the sequence carries the timing and the escalation (for annual payments,
+ * one non-zero step in twelve).  A loaded sequence gives, per policy and step
+ * t from valuation, the multiplier cf_t of the product's nominal cash-flow
+ * vector c (amount, or amount x (1, 1, rho) for the reversionary annuity):
+ * c_t = cf_t c.  It scales annuity payments and assurance death benefits; an
+ * endowment's maturity sum stays the amount.  Once loaded it applies to every
+ * rsv_compute_reserves call (which then runs the general-cash-flow kernels:
+ * unshifted states, V0 and totals; per-step outputs through the time-scan and
+ * summation variants) until rsv_clear_cashflows.  Nested runs value level
+ * cash flows only (RSV_E_STATE while a sequence is loaded), as do the
+ * context-free rsv_reserves_noalloc and the surrogate.  The rows are
+ * indexed like the loaded portfolio: a
+ * compute with another number of policies, or a projection longer than the
+ * rows, fails with RSV_E_STATE. */
+
+/* cf[p * n_steps + t] (host FP64, copied), p < n_pol, t < n_steps.
+ * Errors: RSV_E_ARG (NULL, n_pol < 1, n_steps < 1, more than 2^31 entries),
+ * RSV_E_ASSUMPTION (an entry negative or not finite), RSV_E_NOMEM, RSV_E_CUDA. */
+rsv_status rsv_load_cashflows(rsv_ctx *ctx, const double *cf, int64_t n_pol, int32_t n_steps);
+
+/* A payment schedule (32 bytes): payments every `every` steps from step
+ * `first`; the level in force during step t raised at each policy
+ * anniversary, n_t = floor((t + since) / steps_per_year) anniversaries after
+ * valuation, by the factor 1 + escalation (geometric progression, an
+ * escalating annuity) and by increase x the initial level (arithmetic
+ * progression, an increasing annuity):
+ *   cf_t = [t >= first, (t - first) mod every = 0] (1 + increase n_t) (1 + escalation)^n_t.
+ * A level monthly annuity is {1, 0, 0, 12, 0, 0}; annual payments at the end
+ * of each policy year with 3% escalation {12, 11, 0, 12, 0.03, 0}. */
+typedef struct {
+    int32_t every;          /* >= 1: steps between payments                     */
+    int32_t first;          /* >= 0: step of the first payment                  */
+    int32_t since;          /* 0 .. steps_per_year-1: steps since the last anniversary */
+    int32_t steps_per_year; /* >= 1 (12 for monthly steps)                      */
+    double escalation;      /* > -1, finite                                     */
+    double increase;        /* >= 0, finite                                     */
+} rsv_schedule;
+
+/* Expand one schedule per policy into cash-flow multipliers on the device
+ * (FP64), rows of n_steps as rsv_load_cashflows.
+ * Errors: RSV_E_ARG (NULL, n_pol < 1, n_steps < 1, more than 2^31 entries, a
+ * parameter outside the ranges above), RSV_E_NOMEM, RSV_E_CUDA. */
+rsv_status rsv_load_schedules(rsv_ctx *ctx, const rsv_schedule *sch, int64_t n_pol, int32_t n_steps);
+
+/* Back to level cash flows (cf_t = 1). */
+rsv_status rsv_clear_cashflows(rsv_ctx *ctx);
+
 /* Load the portfolio: n records (host, copied).  Validation of the records
  * against the tables happens at compute time.
  * Errors: RSV_E_ARG (NULL with n > 0, n < 0, n > 2^31 - 1). */
@@ -235,6 +293,48 @@ rsv_status rsv_load_scenarios(rsv_ctx *ctx, const double *v, int32_t n_scen, int
  * exceed 4096), RSV_E_ASSUMPTION (reversion outside [0, 1], amount not
  * finite, a projection longer than n_steps), RSV_E_CUDA, RSV_E_NOMEM. */
 rsv_status rsv_compute_reserves(rsv_ctx *ctx, const rsv_opts *opts, rsv_out *out);
+
+/* ---- m lives (Section 4.3) -------------------------------------------------
+ * Contracts on m = 1..4 independent lives.  The paper builds their transition
+ * matrices by induction, W^m = W^{m-1} (x) w_m, from the single-life two-state
+ * matrix (annuities) or three-state matrix (assurances).  The library keeps
+ * the reduced state "which lives are dead" (2^m states; the three-state
+ * model's "died in the step" states only carry the benefit of that step) and
+ * applies W^m as m one-life passes of the Kronecker factors, m 2^(m-1)
+ * multiply-add pairs per step instead of a dense (2^m)^2 matrix product.
+ *   RSV_MLIFE_ANNUITY    the amount at the end of every month in which at
+ *                        least k of the m lives are alive (k = m: joint life,
+ *                        k = 1: last survivor), to the limiting age of the
+ *                        k-th longest-lived table or the term.
+ *   RSV_MLIFE_ASSURANCE  the amount at the end of the month of the k-th death
+ *                        within the term (term_m >= 1). */
+enum { RSV_MLIFE_ANNUITY = 0, RSV_MLIFE_ASSURANCE = 1 };
+
+typedef struct {     /* 64 bytes */
+    int32_t m;        /* 1..4 lives                                                    */
+    int32_t kind;     /* RSV_MLIFE_ANNUITY or RSV_MLIFE_ASSURANCE                      */
+    int32_t k;        /* 1..m                                                          */
+    int32_t term_m;   /* months; 0 = whole life (annuities only)                       */
+    int32_t age_m[4]; /* ages at valuation in whole months (lives 1..m)                 */
+    int32_t table[4]; /* decrement table of each life                                  */
+    int32_t dead0;    /* lives already dead at valuation: bit i = life i+1; fewer than
+                         k dead for an assurance, at least k alive for an annuity      */
+    int32_t reserved; /* must be 0                                                     */
+    double amount;
+} rsv_mlife_policy;
+
+/* Reserves of n m-life policies under the loaded scenarios (f = 1, level
+ * amounts; the loaded cash-flow sequences do not apply), with the decrement
+ * tables loaded by rsv_load_decrements.  opts: form (any), outputs RSV_OUT_V0
+ * and/or RSV_OUT_SCEN_TOTAL, on_device; horizon, payment and variant 0 / -1.
+ * out->V0 / V0d: [n][n_scen]; out->scen_total: [n_scen], summed over the
+ * policies in order.  The records are copied.
+ * Errors: RSV_E_STATE (tables or scenarios missing), RSV_E_ARG (bad opts or
+ * record, a table not loaded, ages plus steps above 4096), RSV_E_ASSUMPTION
+ * (amount not finite, a projection longer than the scenarios), RSV_E_CUDA,
+ * RSV_E_NOMEM. */
+rsv_status rsv_compute_mlife(rsv_ctx *ctx, const rsv_mlife_policy *pols, int64_t n, const rsv_opts *opts,
+                             rsv_out *out);
 
 /* ---- Nested ("brute force") valuation -------------------------------------
  * Section 2 of the paper: at each future valuation node every policy is

@@ -44,9 +44,9 @@ struct DevBuf {
 // kind, whether it reads a second life, and its number of projection steps
 // from the tables' lengths (the limiting ages) and the term.
 struct ProductModel {
-    int kind;          // K_ANN, K_ASS, K_JL, K_ANN2, K_ASS2
+    int kind;          // K_ANN, K_ASS, K_JL, K_ANN2, K_ASS2, K_LS2
     bool two_life;     // reads the second life's age and table
-    bool multi_state;  // the 3-state JL model (state0 may be 1 or 2)
+    bool multi_state;  // a 3-state model, JL or K_LS2 (state0 may be 1 or 2)
     bool annuity;      // paid while (some) life is alive; term_m 0 = to the limiting age
     float bnd;         // boundary r_S per unit amount at maturity (endowments: 1)
 };
@@ -61,6 +61,8 @@ inline bool product_model(int product, ProductModel& m) {
     case RSV_LAST_SURVIVOR: m = {K_JL, true, true, true, 0.0f}; return true;
     case RSV_JOINT_TERM: m = {K_ASS2, true, false, false, 0.0f}; return true;
     case RSV_JOINT_ENDOWMENT: m = {K_ASS2, true, false, false, 1.0f}; return true;
+    case RSV_LS_TERM: m = {K_LS2, true, true, false, 0.0f}; return true;
+    case RSV_LS_ENDOWMENT: m = {K_LS2, true, true, false, 1.0f}; return true;
     default: return false;
     }
 }
@@ -94,7 +96,7 @@ struct Layout {            // cached tiling for one (P, horizon, data generation
     int n_tiles = 0, tab_pad = 0, n_tab = 0;
     double chain_steps = 0;  // sum over policies of S (per scenario)
     int max_S = 0;           // longest projection
-    bool has_two = false;    // two-life single-state tiles present
+    bool has_two = false;    // tiles of K_ANN2, K_ASS2 or K_LS2 present
     DevBuf slots, kinds;
 };
 
@@ -152,6 +154,10 @@ struct rsv_ctx {
     unsigned long long tabf_key[3] = {0, 0, 0};
     int vf_scen = 0, vf_steps = 0;                  // fractional discount planes
     DevBuf d_vf64, d_vf32, d_vf2;
+    int64_t cf_pol = 0;                             // cash-flow multipliers: rows (0 = level)
+    int cf_steps = 0;                               //   and row length
+    DevBuf d_cf64, d_cf32;                          //   FP64 rows and their FP32 copy
+    DevBuf d_ml_rec, d_ml_amount;                   // m-life records of the last call
 
     Layout lay;
     DevBuf d_ctl;       // [0] queue head, [1] status
@@ -188,6 +194,9 @@ inline rsv_status fail(rsv_ctx* c, rsv_status st, const char* fmt, ...) {
 // entry format (rsv_abi.cu).
 rsv_status build_layout(rsv_ctx* c, int P, int horizon, int max_steps);
 rsv_status build_tables(rsv_ctx* c, int form, size_t& smem);
+// The first n_tab loaded tables, pad entries each, in a form's entry format
+// on the device (cached by shape and table generation); smem = their bytes.
+rsv_status stage_tables(rsv_ctx* c, int form, int pad, int n_tab, size_t& smem);
 
 #define CU(call)                                                                                \
     do {                                                                                        \

@@ -211,6 +211,10 @@ __global__ void __launch_bounds__(NT) nested_kernel(const NestedArgs a) {
                 Tile<FORM, P, 1, K_ASS2, false> w(env, tab, tile, chunk, lane, m);
                 w.run_steps();
                 w.epilogue_weighted(acc, wts, wstride);
+            } else if (kind == K_LS2) {
+                Tile<FORM, P, 1, K_LS2, false> w(env, tab, tile, chunk, lane, m);
+                w.run_steps();
+                w.epilogue_weighted(acc, wts, wstride);
             } else {
                 Tile<FORM, P, 1, K_ASS, false> w(env, tab, tile, chunk, lane, m);
                 w.run_steps();

@@ -15,6 +15,7 @@ static const Variant kComp[] = {
     RSV_VARIANT(F_COMP, 2, 1, 256, 1, true, "comp P2xM1 nt256 side-outputs"),
     RSV_VARIANT_PAY(F_COMP, 2, 1, 256, 2, false, PAY_START, "comp P2xM1 nt256 pay-start"),
     RSV_VARIANT_PAY(F_COMP, 2, 1, 256, 2, false, PAY_FRACTION, "comp P2xM1 nt256 pay-fraction"),
+    RSV_VARIANT_PAY(F_COMP, 2, 1, 256, 2, false, PAY_END_GENERAL, "comp P2xM1 nt256 pay-end-general"),
 };
 const Variant* variants_comp(int* n) {
     *n = (int)(sizeof(kComp) / sizeof(kComp[0]));

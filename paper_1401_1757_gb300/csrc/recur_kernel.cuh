@@ -8,6 +8,12 @@
 //            r01 = v px (1 + r01')          r10 = v py (rho + r10')
 //            r00 = v [px py (1 + r00') + px qy (1 + r01') + qx py (rho + r10')]
 //                = v px py (1 + r00') + qy r01 + qx r10   (r01, r10 of this step)
+//   K_LS2  the nine-state two-life assurance model (Section 4.2.3) with the
+//          benefit on the second death, reduced to the states 00, x only,
+//          y only (the "died in the step" and "dead" states of the other
+//          life share a reserve; both-dead states are zero-reserve states):
+//            rx = v (qx + px rx')           ry = v (qy + py ry')
+//            r00 = v [qx qy + px qy rx' + qx py ry' + px py r00']
 // run backward from the boundary r_S (Section 3.8.2).
 //
 // Mapping.  A work item is one tile of P policies (same kind, similar S) times
@@ -106,6 +112,16 @@ __device__ __forceinline__ void step_jl(R v, R px, R qx, R py, R qy, R rho, R& V
     V01 = n01;
     V10 = n10;
 }
+// Second-death assurance, benefit c per unit amount in this step.
+template <class R>
+__device__ __forceinline__ void step_ls2(R v, R px, R qx, R py, R qy, R c, R& V00, R& Vx, R& Vy) {
+    R t = p_mul(p_mul(qx, py), Vy);             // qx py ry'
+    t = p_fma(p_mul(px, qy), Vx, t);            //   + px qy rx'
+    t = p_fma(p_mul(qx, qy), c, t);             //   + qx qy c
+    V00 = p_mul(v, p_fma(p_mul(px, py), V00, t));
+    Vx = p_mul(v, p_fma(px, Vx, p_mul(qx, c)));
+    Vy = p_mul(v, p_fma(py, Vy, p_mul(qy, c)));
+}
 
 // Compensated form.  Quantities that multiply along the chain (the discount
 // x survival factors and the running reserve) are double-floats built from
@@ -148,6 +164,17 @@ __device__ __forceinline__ void step_jl(df v, df px, df qx, df py, df qy, df rho
     V00 = df_float_plus_mul(__fadd_rn(1.0f, t12), df_mul(gx, py), V00);
     V01 = R01;
     V10 = A10;
+}
+// Second-death assurance: the survival chain px py r00' in double-float; the
+// one-step terms qx qy c + px qy rx' + qx py ry' (non-negative) in FP32.
+__device__ __forceinline__ void step_ls2(df v, df px, df qx, df py, df qy, float c, df& V00, df& Vx, df& Vy) {
+    const float rx = __fadd_rn(Vx.h, Vx.l), ry = __fadd_rn(Vy.h, Vy.l);
+    float t = __fmul_rn(__fmul_rn(qx.h, py.h), ry);
+    t = __fmaf_rn(__fmul_rn(px.h, qy.h), rx, t);
+    t = __fmaf_rn(__fmul_rn(qx.h, qy.h), c, t);
+    V00 = df_mul(v, df_add_float_pos(df_mul(df_mul(px, py), V00), t));
+    Vx = df_mul(v, df_add_float_pos(df_mul(px, Vx), __fmul_rn(qx.h, c)));
+    Vy = df_mul(v, df_add_float_pos(df_mul(py, Vy), __fmul_rn(qy.h, c)));
 }
 
 // Annuity-type steps with the payment at the start of the step (f = 0, a = 1)
@@ -201,6 +228,8 @@ struct TileEnv {
     int v0_ld;           // row stride of V0 (the caller's scenario count)
     const void* vf;      // fractional discount plane (PAY_FRACTION), layout of v
     int tabf_off;        // entries from the staged tables to the fractional ones (PAY_FRACTION)
+    const void* cf;      // cash-flow multipliers [n_pol][cf_ld] or null (variants other than PAY_END)
+    int cf_ld;
 };
 
 template <int FORM, int P, int M, int KIND, bool EXTRA, int PAY = PAY_END>
@@ -210,7 +239,7 @@ struct Tile {
     using TabE = typename T::TabE;
     using VE = typename T::VE;
     using VP = Pack<VE, M>;
-    static constexpr int NS = (KIND == K_JL) ? 3 : 1;
+    static constexpr int NS = (KIND == K_JL || KIND == K_LS2) ? 3 : 1;
 
     const TileEnv& e;
     const TabE* __restrict__ tab;
@@ -244,7 +273,8 @@ struct Tile {
             for (int m = 0; m < M; ++m) {
                 V[0][i][m] = T::cst(SHIFTED ? 1.0f + r.bnd : r.bnd);
 #pragma unroll
-                for (int k = 1; k < NS; ++k) V[k][i][m] = T::cst(SHIFTED ? 1.0f : 0.0f);
+                for (int k = 1; k < NS; ++k)   // the second-death endowment pays if either is alive
+                    V[k][i][m] = T::cst(SHIFTED ? 1.0f : (KIND == K_LS2 ? r.bnd : 0.0f));
             }
         }
     }
@@ -257,8 +287,18 @@ struct Tile {
     // the ANN state and JL states 00 and 01 as 1 + r, JL state 10 as 1 + r / rho.
     static constexpr bool ANNUITY = KIND == K_ANN || KIND == K_ANN2 || KIND == K_JL;
     static constexpr bool SHIFTED = FORM == F_COMP && ANNUITY && PAY == PAY_END;
-    // payment within the step: unshifted states, JL state 10 carried as r10 / rho
+    // payment within the step, or general cash flows: unshifted states, JL
+    // state 10 carried as r10 / rho
     static constexpr bool PAYF = ANNUITY && PAY != PAY_END;
+
+    // the one-step terms: FP32 heads in the compensated form
+    using A = typename std::conditional<FORM == F_COMP, float, Val>::type;
+    using CfE = typename std::conditional<FORM == F_F64, double, float>::type;
+    // c_t / c of policy i (1 for a level cash flow; warp-uniform load)
+    __device__ __forceinline__ A cfac(int i, int t) const {
+        if (PAY == PAY_END || e.cf == nullptr || pol[i] < 0) return A(1);
+        return (A) static_cast<const CfE*>(e.cf)[(size_t)pol[i] * e.cf_ld + t];
+    }
 
     // r of state k of policy i, scenario m, in FP64
     __device__ __forceinline__ double dval(int k, int i, int m) const {
@@ -322,10 +362,18 @@ struct Tile {
 #pragma unroll
                 for (int m = 0; m < M; ++m)
                     step_jl(T::v(vv.e[m]), px, qx, py, qy, rho[i], V[0][i][m], V[1][i][m], V[2][i][m]);
+            } else if constexpr (KIND == K_LS2) {
+                const TabE e2 = tab[idx2[i] + t];
+                const Val py = T::p(e2), qy = T::q(e2);
+                const A c = cfac(i, t);
+#pragma unroll
+                for (int m = 0; m < M; ++m)
+                    step_ls2(T::v(vv.e[m]), px, qx, py, qy, c, V[0][i][m], V[1][i][m], V[2][i][m]);
             } else if constexpr (KIND == K_ANN2 || KIND == K_ASS2) {
                 const TabE e2 = tab[idx2[i] + t];
                 Val p, q;
                 joint_pq(px, qx, T::p(e2), T::q(e2), p, q);
+                if constexpr (KIND == K_ASS2 && PAY != PAY_END) q = scale_q(q, cfac(i, t));
 #pragma unroll
                 for (int m = 0; m < M; ++m)
                     V[0][i][m] = KIND == K_ANN2 ? step_ann(T::v(vv.e[m]), p, V[0][i][m])
@@ -334,18 +382,25 @@ struct Tile {
 #pragma unroll
                 for (int m = 0; m < M; ++m) V[0][i][m] = step_ann(T::v(vv.e[m]), px, V[0][i][m]);
             } else {
+                Val q = qx;   // the death benefit of this step, c_t / c times the level one
+                if constexpr (PAY != PAY_END) q = scale_q(q, cfac(i, t));
 #pragma unroll
-                for (int m = 0; m < M; ++m) V[0][i][m] = step_ass(T::v(vv.e[m]), px, qx, V[0][i][m]);
+                for (int m = 0; m < M; ++m) V[0][i][m] = step_ass(T::v(vv.e[m]), px, q, V[0][i][m]);
             }
             if constexpr (EXTRA) record(t, i);
         }
     }
 
-    // Annuity-type step with the payment at the start of the step or at the
-    // fraction f: r = a + v W r' with the cash-flow term a = v^f W_f c.
+    // q c_t / c: the compensated assurance step takes the death term as an FP32 head
+    __device__ static __forceinline__ df scale_q(df q, float c) { return df{__fmul_rn(q.h, c), 0.0f}; }
+    __device__ static __forceinline__ float scale_q(float q, float c) { return p_mul(q, c); }
+    __device__ static __forceinline__ double scale_q(double q, double c) { return p_mul(q, c); }
+
+    // Annuity-type step with the payment at the start of the step, at the
+    // fraction f, or at the end with a varying cash flow: r = a + v W r' with
+    // the cash-flow term a = v^f W_f c_t.
     template <bool CHECK>
     __device__ __forceinline__ void step_pay(int t, const VP& vv) {
-        using A = typename std::conditional<FORM == F_COMP, float, Val>::type;   // the one-step terms
         VP vf{};
         if constexpr (PAY == PAY_FRACTION) vf = loadf(t);
 #pragma unroll
@@ -358,13 +413,17 @@ struct Tile {
             if constexpr (PAY == PAY_FRACTION) {
                 f1 = tab[e.tabf_off + idx1[i] + t];
                 if constexpr (KIND != K_ANN) f2 = tab[e.tabf_off + idx2[i] + t];
+            } else if constexpr (PAY == PAY_END_GENERAL) {   // W_f = W_1
+                f1 = e1;
+                f2 = e2;
             }
+            const A c = cfac(i, t);
 #pragma unroll
             for (int m = 0; m < M; ++m) {
                 const Val v = T::v(vv.e[m]);
-                A vfm = A(1), pxf = A(1), qxf = A(0), pyf = A(1);
-                if constexpr (PAY == PAY_FRACTION) {
-                    vfm = head(T::v(vf.e[m]));
+                A vfm = c, pxf = A(1), qxf = A(0), pyf = A(1);
+                if constexpr (PAY == PAY_FRACTION || PAY == PAY_END_GENERAL) {
+                    vfm = (PAY == PAY_FRACTION ? head(T::v(vf.e[m])) : head(v)) * c;
                     pxf = head(T::p(f1));
                     qxf = head(T::q(f1));
                     if constexpr (KIND != K_ANN) pyf = head(T::p(f2));
@@ -500,9 +559,9 @@ __device__ __forceinline__ void run_item(const TileEnv& env, const TabE* tab, in
     w.epilogue_v0(tile, a.V0f, a.V0d, a.partial);
 }
 
-// TWO: the portfolio has two-life single-state tiles (K_ANN2, K_ASS2).  The
-// kernel is compiled with and without them: the three hot models alone keep
-// their register allocation free of spills.
+// TWO: the portfolio has tiles of the other two-life models (K_ANN2, K_ASS2,
+// K_LS2).  The kernel is compiled with and without them: the three hot
+// models alone keep their register allocation free of spills.
 template <int FORM, int P, int M, int NT, int MINB, bool EXTRA, bool TWO, int PAY>
 __global__ void __launch_bounds__(NT, MINB) recur_kernel(const RecurArgs a) {
     using TabE = typename Tr<FORM>::TabE;
@@ -512,7 +571,7 @@ __global__ void __launch_bounds__(NT, MINB) recur_kernel(const RecurArgs a) {
     if (!stage_to_smem(tab, a.tab, (uint32_t)a.tab_bytes, &bar, a.status)) return;
 
     const TileEnv env{a.slots, a.v, a.s_pad, a.n_scen, a.n_steps, a.amount, a.traj, a.pt_sum, a.v0_ld, a.vf,
-                      a.tabf_off};
+                      a.tabf_off, a.cf, a.cf_ld};
     const int lane = threadIdx.x & 31;
     for (;;) {
         int item = 0;
@@ -527,7 +586,8 @@ __global__ void __launch_bounds__(NT, MINB) recur_kernel(const RecurArgs a) {
         else if (!TWO || kind == K_ASS) run_item<FORM, P, M, K_ASS, EXTRA, PAY>(env, tab, tile, chunk, lane, a);
         else if constexpr (TWO) {
             if (kind == K_ANN2) run_item<FORM, P, M, K_ANN2, EXTRA, PAY>(env, tab, tile, chunk, lane, a);
-            else run_item<FORM, P, M, K_ASS2, EXTRA, PAY>(env, tab, tile, chunk, lane, a);
+            else if (kind == K_ASS2) run_item<FORM, P, M, K_ASS2, EXTRA, PAY>(env, tab, tile, chunk, lane, a);
+            else run_item<FORM, P, M, K_LS2, EXTRA, PAY>(env, tab, tile, chunk, lane, a);
         }
     }
 }

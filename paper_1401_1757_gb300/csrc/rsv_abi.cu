@@ -37,6 +37,31 @@ int special_variant(const Variant* vl, int n, bool extra, int pay) {
     return 0;
 }
 
+// FP32 copy of the FP64 cash-flow multipliers
+__global__ void cf_to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        b[i] = __double2float_rn(a[i]);
+}
+
+// Cash-flow multipliers of one payment schedule per policy (FP64), rows of
+// n_steps: cf_t = [t >= first, (t - first) mod every = 0] (1 + increase n_t)
+// (1 + escalation)^n_t with n_t = floor((t + since) / steps_per_year).
+__global__ void schedule_kernel(const rsv_schedule* __restrict__ sch, int64_t n_pol, int n_steps,
+                                double* __restrict__ cf64, float* __restrict__ cf32) {
+    const size_t total = (size_t)n_pol * n_steps;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const rsv_schedule s = sch[i / n_steps];
+        const int t = (int)(i % n_steps);
+        double x = 0.0;
+        if (t >= s.first && (t - s.first) % s.every == 0) {
+            const int n = (t + s.since) / s.steps_per_year;
+            x = (1.0 + s.increase * n) * pow(1.0 + s.escalation, (double)n);
+        }
+        cf64[i] = x;
+        cf32[i] = __double2float_rn(x);
+    }
+}
+
 const Variant* variant_list(int form, int* n) {
     switch (form) {
     case F_F64: return variants_f64(n);
@@ -210,10 +235,10 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
     if (st != RSV_OK) return st;
 
     // group by reduced model, longest projection first
-    // JL tiles, then joint and single-life annuities, then assurances
-    static const int kind_rank[5] = {2, 4, 0, 1, 3};
+    // three-state tiles, then joint and single-life annuities, then assurances
+    static const int kind_rank[6] = {3, 5, 0, 2, 4, 1};
     // stable counting sort on (kind rank, S descending): S <= kMaxAgeSteps
-    const int nb = 5 * (kMaxAgeSteps + 1);
+    const int nb = 6 * (kMaxAgeSteps + 1);
     std::vector<int> bucket_start(nb + 1, 0), order(pp.size());
     auto key = [&](const PolPrep& q) { return kind_rank[q.kind] * (kMaxAgeSteps + 1) + (kMaxAgeSteps - q.S); };
     for (const PolPrep& q : pp) ++bucket_start[key(q) + 1];
@@ -247,7 +272,7 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
             slots.push_back(s);
         }
         kinds.push_back(kind);
-        const double w = kind == K_JL ? 4.5 : (kind == K_ANN2 || kind == K_ASS2 ? 1.4 : 1.0);
+        const double w = kind == K_JL ? 4.5 : (kind == K_LS2 ? 4.0 : (kind == K_ANN2 || kind == K_ASS2 ? 1.4 : 1.0));
         cost.push_back(w * slots[slots.size() - P].S);
     }
     // tiles in decreasing cost order (longest-processing-time first): the
@@ -296,7 +321,7 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
     L.has_two = false;
     for (const PolPrep& q : pp) {
         L.max_S = std::max(L.max_S, q.S);
-        L.has_two |= q.kind == K_ANN2 || q.kind == K_ASS2;
+        L.has_two |= q.kind == K_ANN2 || q.kind == K_ASS2 || q.kind == K_LS2;
     }
     return RSV_OK;
 }
@@ -326,7 +351,10 @@ void write_entries(int form, const std::vector<double>* src, int n_tab, int pad,
 // Decrement tables in the entry format of `form`, zero survival past each
 // table's end, staged per CTA.
 rsv_status rsv::build_tables(rsv_ctx* c, int form, size_t& smem) {
-    const int pad = c->lay.tab_pad, n_tab = c->lay.n_tab;
+    return stage_tables(c, form, c->lay.tab_pad, c->lay.n_tab, smem);
+}
+
+rsv_status rsv::stage_tables(rsv_ctx* c, int form, int pad, int n_tab, size_t& smem) {
     const size_t esz = form == F_F32 ? sizeof(float2) : 16;
     smem = (size_t)n_tab * pad * esz;
     if (smem > kMaxSmem)
@@ -419,12 +447,18 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     if (pay < PAY_END || pay > PAY_FRACTION) return fail(c, RSV_E_ARG, "bad payment %d", pay);
     if (pay != PAY_END && (extra || scan || summ))
         return fail(c, RSV_E_ARG, "payment within the step: V0 and totals of the scenario-parallel kernels only");
+    const bool cfl = c->cf_pol > 0;   // varying cash flows loaded
+    if (cfl && c->cf_pol != n_pol)
+        return fail(c, RSV_E_STATE, "cash flows loaded for %lld policies, portfolio has %lld", (long long)c->cf_pol,
+                    (long long)n_pol);
+    if (cfl && extra && !scan && !summ)
+        return fail(c, RSV_E_ARG, "per-step outputs with varying cash flows: use the time-scan or summation variant");
     const int nt = tunable_count(vl, nv);
     int vi;
     if (extra || scan || summ) {
         vi = special_variant(vl, nv, true, PAY_END);
-    } else if (pay != PAY_END) {
-        vi = special_variant(vl, nv, false, pay);
+    } else if (pay != PAY_END || cfl) {
+        vi = special_variant(vl, nv, false, pay == PAY_END ? PAY_END_GENERAL : pay);
     } else if (o->variant >= 0) {
         if (o->variant >= nt) return fail(c, RSV_E_ARG, "variant %d out of range", o->variant);
         vi = o->variant;
@@ -437,6 +471,9 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
 
     rsv_status st = build_layout(c, (scan || summ) ? 1 : V.P, o->horizon, c->n_steps);
     if (st != RSV_OK) return st;
+    if (cfl && c->lay.max_S > c->cf_steps)
+        return fail(c, RSV_E_STATE, "a projection of %d steps is longer than the cash-flow rows (%d)", c->lay.max_S,
+                    c->cf_steps);
     size_t smem = 0;
     int tabf_off = 0;
     if (pay == PAY_FRACTION) {
@@ -498,6 +535,8 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     a.pt_sum = pt;
     a.traj = traj;
     a.v0_ld = NSc;
+    a.cf = !cfl ? nullptr : (o->form == F_F64 ? c->d_cf64.p : c->d_cf32.p);
+    a.cf_ld = c->cf_steps;
     const int two = L.has_two ? 1 : 0;   // kernels compiled with the two-life single-state models
 
     // Host V0 of the scenario-parallel kernels: computed in column blocks of
@@ -600,6 +639,7 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
     if (o->form < F_F64 || o->form > F_COMP) return fail(c, RSV_E_ARG, "bad form %d", o->form);
     if (o->outputs != 0 || o->horizon != 0 || o->payment != 0 || (o->on_device != 0 && o->on_device != 1))
         return fail(c, RSV_E_ARG, "nested runs take outputs = 0, horizon = 0, payment 0, on_device 0/1");
+    if (c->cf_pol > 0) return fail(c, RSV_E_STATE, "nested runs value level cash flows: clear the loaded sequence");
     if (sp->n_outer < 1 || sp->n_nodes < 1 || sp->node_step_m < 1 || sp->n_inner < 1 || sp->n_inner > (1 << 20))
         return fail(c, RSV_E_ARG, "bad nested sizes");
     if ((long long)(sp->n_nodes - 1) * sp->node_step_m > kMaxAgeSteps)
@@ -877,7 +917,8 @@ rsv_status rsv_destroy(rsv_ctx* c) {
                       &c->d_nest_kth, &c->d_nest_all, &c->d_pols, &c->sur.d_flag, &c->sur.d_q, &c->sur.d_lab,
                       &c->sur.d_y, &c->sur.d_X, &c->sur.d_pred, &c->sur.d_err, &c->sur.d_aux, &c->sur.d_curve,
                       &c->sur.d_comm, &c->sur.d_lnb, &c->d_tabf[0], &c->d_tabf[1], &c->d_tabf[2], &c->d_vf64,
-                      &c->d_vf32, &c->d_vf2})
+                      &c->d_vf32, &c->d_vf2, &c->d_cf64, &c->d_cf32, &c->d_ml_rec,
+                      &c->d_ml_amount})
         b->release();
     c->mlp.release();
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -949,6 +990,62 @@ rsv_status rsv_load_scenarios_fraction(rsv_ctx* c, const double* v, int32_t n_sc
     return RSV_OK;
 }
 
+rsv_status rsv_load_cashflows(rsv_ctx* c, const double* cf, int64_t n_pol, int32_t n_steps) {
+    if (!c) return RSV_E_ARG;
+    if (!cf || n_pol < 1 || n_steps < 1 || n_pol * (int64_t)n_steps > 0x7fffffffLL)
+        return fail(c, RSV_E_ARG, "bad cash-flow arguments");
+    const size_t n = (size_t)n_pol * n_steps;
+    for (size_t i = 0; i < n; ++i)
+        if (!(std::isfinite(cf[i]) && cf[i] >= 0.0))
+            return fail(c, RSV_E_ASSUMPTION, "cash-flow multiplier %zu = %g is not finite and non-negative", i, cf[i]);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    c->cf_pol = 0;
+    CU(c->d_cf64.ensure(n * sizeof(double)));
+    CU(c->d_cf32.ensure(n * sizeof(float)));
+    CU(cudaMemcpyAsync(c->d_cf64.p, cf, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    cf_to_f32_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(c->d_cf64.as<double>(), c->d_cf32.as<float>(), n);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(c->stream));
+    c->cf_pol = n_pol;
+    c->cf_steps = n_steps;
+    return RSV_OK;
+}
+
+rsv_status rsv_load_schedules(rsv_ctx* c, const rsv_schedule* sch, int64_t n_pol, int32_t n_steps) {
+    if (!c) return RSV_E_ARG;
+    if (!sch || n_pol < 1 || n_steps < 1 || n_pol * (int64_t)n_steps > 0x7fffffffLL)
+        return fail(c, RSV_E_ARG, "bad schedule arguments");
+    for (int64_t p = 0; p < n_pol; ++p) {
+        const rsv_schedule& s = sch[p];
+        if (s.every < 1 || s.first < 0 || s.steps_per_year < 1 || s.since < 0 || s.since >= s.steps_per_year ||
+            !(std::isfinite(s.escalation) && s.escalation > -1.0) || !(std::isfinite(s.increase) && s.increase >= 0.0))
+            return fail(c, RSV_E_ARG, "schedule %lld has a parameter out of range", (long long)p);
+    }
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    const size_t n = (size_t)n_pol * n_steps;
+    c->cf_pol = 0;
+    CU(c->d_vstage.ensure((size_t)n_pol * sizeof(rsv_schedule)));
+    CU(c->d_cf64.ensure(n * sizeof(double)));
+    CU(c->d_cf32.ensure(n * sizeof(float)));
+    CU(cudaMemcpyAsync(c->d_vstage.p, sch, (size_t)n_pol * sizeof(rsv_schedule), cudaMemcpyHostToDevice, c->stream));
+    schedule_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(c->d_vstage.as<rsv_schedule>(), n_pol, n_steps,
+                                                            c->d_cf64.as<double>(), c->d_cf32.as<float>());
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(c->stream));
+    c->cf_pol = n_pol;
+    c->cf_steps = n_steps;
+    return RSV_OK;
+}
+
+rsv_status rsv_clear_cashflows(rsv_ctx* c) {
+    if (!c) return RSV_E_ARG;
+    c->cf_pol = 0;
+    c->cf_steps = 0;
+    return RSV_OK;
+}
+
 rsv_status rsv_load_portfolio(rsv_ctx* c, const rsv_policy* pols, int64_t n) {
     if (!c) return RSV_E_ARG;
     if (n < 0 || n > 0x7fffffffLL || (n > 0 && !pols)) return fail(c, RSV_E_ARG, "bad portfolio size %lld", (long long)n);
@@ -1017,6 +1114,7 @@ const char* rsv_variant_name(int32_t form, int32_t variant) {
 rsv_status rsv_tune(rsv_ctx* c, const rsv_opts* opts, int32_t reps, int32_t* best, float* ms_out) {
     if (!c) return RSV_E_ARG;
     if (!opts || reps < 1) return fail(c, RSV_E_ARG, "bad tune arguments");
+    if (c->cf_pol > 0) return fail(c, RSV_E_STATE, "tuning ranks the level-cash-flow variants: clear the loaded sequence");
     const int nv = rsv_variant_count(opts->form);
     if (nv < 1) return fail(c, RSV_E_ARG, "bad form %d", opts->form);
     cudaError_t e = cudaSetDevice(c->device);

@@ -14,7 +14,9 @@ enum Kind : int32_t {
     K_ASS = 1,  // 1 state, r = v (q c + p r')          (Section 4.1.3, reduced)
     K_JL = 2,   // 3 states 00, 01, 10 of the two-life model (Section 4.2)
     K_ANN2 = 3, // 1 state, r = v px py (c + r')       (joint-life annuity)
-    K_ASS2 = 4  // 1 state, r = v ((1 - px py) c + px py r')  (joint-status assurance)
+    K_ASS2 = 4, // 1 state, r = v ((1 - px py) c + px py r')  (joint-status assurance)
+    K_LS2 = 5   // 3 states 00, x only, y only of the nine-state two-life assurance
+                // model with the benefit on the second death (Section 4.2.3)
 };
 
 enum Form : int32_t { F_F64 = 0, F_F32 = 1, F_COMP = 2 };
@@ -59,11 +61,16 @@ struct RecurArgs {
     int32_t v0_ld;            // row stride of V0 (= n_scen unless a column block is computed)
     const void* vf;           // fractional discount plane v_t^f, same layout as v (fractional payments)
     int32_t tabf_off;         // entries from the staged tables to the fractional-survival tables
+    const void* cf;           // cash-flow multipliers c_t, [n_pol][cf_ld] (double for FP64, else float), or null
+    int32_t cf_ld;            // row length of cf (steps from valuation)
 };
 
 // When an annuity's cash flow is paid within each step (the fraction f of
 // Eq. generalForm); assurance benefits are always paid at the step's end.
-enum Pay : int32_t { PAY_END = 0, PAY_START = 1, PAY_FRACTION = 2 };
+// PAY_END_GENERAL is f = 1 on unshifted states, for cash flows that vary
+// from step to step (c_t = cf_t c, Section 4.1.1 and 4.6).  The variants
+// other than PAY_END all take the multipliers cf_t when they are given.
+enum Pay : int32_t { PAY_END = 0, PAY_START = 1, PAY_FRACTION = 2, PAY_END_GENERAL = 3 };
 
 // ------------------------------------------------------------------------
 // double-float ("df") numbers: value = h + l with |l| about ulp(h) or less.

@@ -13,8 +13,9 @@
 //
 // This fills a warp with one chain, where the scenario-parallel kernels need
 // 32 scenarios per warp: it is the launch for few scenarios (one flat rate)
-// and for very long projections.  For the 3-state joint-life model B keeps
-// the structure [[b00, b01, b02], [0, b11, 0], [0, 0, b22]] under products.
+// and for very long projections.  For the 3-state models (joint life,
+// second death) B keeps the structure [[b00, b01, b02], [0, b11, 0],
+// [0, 0, b22]] under products.
 #include <algorithm>
 #include <cstdint>
 
@@ -71,6 +72,9 @@ struct StepMaps {
     const double* v;      // scenario column: v[t * s_pad]
     int s_pad, idx1, idx2;
     double rho;
+    const double* cf;     // the policy's cash-flow multipliers c_t / c, or null (level)
+
+    __device__ __forceinline__ double c(int t) const { return cf ? cf[t] : 1.0; }
 
     __device__ __forceinline__ void at(int t, Aff1& m, int kind) const {
         const double vt = v[(size_t)t * s_pad];
@@ -80,15 +84,15 @@ struct StepMaps {
             q = q + p * ey.y;
             p = p * ey.x;
         }
-        if (kind == K_ANN || kind == K_ANN2) {   // r = v p (1 + r')
+        if (kind == K_ANN || kind == K_ANN2) {   // r = v p (c_t + r')
             const double g = vt * p;
-            m = Aff1{g, g};
-        } else {                                 // r = v (q + p r')
-            m = Aff1{vt * q, vt * p};
+            m = Aff1{g * c(t), g};
+        } else {                                 // r = v (q c_t + p r')
+            m = Aff1{vt * q * c(t), vt * p};
         }
     }
-    __device__ __forceinline__ void at(int t, Aff3& m, int) const {
-        // r = v W (c + r'), c = (1, 1, rho), W = [[px py, px qy, qx py], [0, px, 0], [0, 0, py]]
+    __device__ __forceinline__ void at(int t, Aff3& m, int kind) const {
+        // B = v [[px py, px qy, qx py], [0, px, 0], [0, 0, py]] for both three-state models
         const double vt = v[(size_t)t * s_pad];
         const double2 ex = tab[idx1 + t], ey = tab[idx2 + t];
         m.b00 = vt * ex.x * ey.x;
@@ -96,9 +100,16 @@ struct StepMaps {
         m.b02 = vt * ex.y * ey.x;
         m.b11 = vt * ex.x;
         m.b22 = vt * ey.x;
-        m.a0 = m.b00 + m.b01 + m.b02 * rho;
-        m.a1 = m.b11;
-        m.a2 = m.b22 * rho;
+        const double ct = c(t);
+        if (kind == K_JL) {   // r = v W (c_t + r'), c_t = (1, 1, rho) c_t / c
+            m.a0 = (m.b00 + m.b01 + m.b02 * rho) * ct;
+            m.a1 = m.b11 * ct;
+            m.a2 = m.b22 * rho * ct;
+        } else {              // second death in the step: v (qx qy, qx, qy) c_t / c
+            m.a0 = vt * ex.y * ey.y * ct;
+            m.a1 = vt * ex.y * ct;
+            m.a2 = vt * ey.y * ct;
+        }
     }
 };
 
@@ -111,6 +122,13 @@ __device__ __forceinline__ void apply(const Aff3& m, double (&r)[3]) {
     r[0] = r0;
     r[1] = r1;
     r[2] = r2;
+}
+
+// r_S per unit amount: the endowment's maturity sum in state 0, or in every
+// state of the second-death model (a life alive)
+__device__ __forceinline__ void boundary(const SlotRec& rec, int kind, double (&r)[3]) {
+    r[0] = rec.bnd;
+    r[1] = r[2] = kind == K_LS2 ? (double)rec.bnd : 0.0;
 }
 
 // state k of r, selected among compile-time indices (keeps r in registers)
@@ -142,7 +160,8 @@ __device__ double scan_chain(const StepMaps& sm, int kind, const SlotRec& rec, i
         // r at the end of this lane's block: the next lane's suffix applied to r_S
         A next = shfl_down(suf, 1);
         if (lane == 31) next = ident(A{});
-        double r[3] = {rec.bnd, 0.0, 0.0};
+        double r[3];
+        boundary(rec, kind, r);
         apply(next, r);
         const size_t base = (size_t)rec.pol * (a.n_steps + 1);
         // the boundary row t = S, written by the lane whose block ends there
@@ -155,7 +174,8 @@ __device__ double scan_chain(const StepMaps& sm, int kind, const SlotRec& rec, i
             a.traj[(base + t) * a.n_scen + s] = amount * pick(r, k);
         }
     }
-    double r[3] = {rec.bnd, 0.0, 0.0};
+    double r[3];
+    boundary(rec, kind, r);
     apply(suf, r);
     return amount * pick(r, k);
 }
@@ -176,10 +196,11 @@ __global__ void __launch_bounds__(256) scan_kernel(const RecurArgs a) {
         const SlotRec rec = a.slots[tile];
         if (rec.pol < 0) continue;
         const int kind = a.tile_kind[tile];
-        StepMaps sm{tab, plane + s, a.s_pad, rec.idx1, rec.idx2, (double)rec.rho_h + (double)rec.rho_l};
+        const double* cf = a.cf ? static_cast<const double*>(a.cf) + (size_t)rec.pol * a.cf_ld : nullptr;
+        StepMaps sm{tab, plane + s, a.s_pad, rec.idx1, rec.idx2, (double)rec.rho_h + (double)rec.rho_l, cf};
         const double amount = a.amount[rec.pol];
-        const double x = kind == K_JL ? scan_chain<Aff3>(sm, kind, rec, s, amount, a, lane)
-                                      : scan_chain<Aff1>(sm, kind, rec, s, amount, a, lane);
+        const double x = (kind == K_JL || kind == K_LS2) ? scan_chain<Aff3>(sm, kind, rec, s, amount, a, lane)
+                                                         : scan_chain<Aff1>(sm, kind, rec, s, amount, a, lane);
         if (lane == 0) {
             const size_t o = (size_t)rec.pol * a.n_scen + s;
             if (a.V0f) a.V0f[o] = (float)x;

@@ -19,10 +19,11 @@ namespace rsv {
 namespace {
 
 // r_t of chain (slot rec, scenario column v) in the reduced state k
-__device__ double sum_reserve(const double2* tab, const double* v, int s_pad, const SlotRec& rec, int kind, int t) {
+__device__ double sum_reserve(const double2* tab, const double* v, int s_pad, const SlotRec& rec, int kind, int t,
+                              const double* cf) {
     const int S = rec.S;
     const double rho = (double)rec.rho_h + (double)rec.rho_l;
-    if (kind != K_JL) {
+    if (kind != K_JL && kind != K_LS2) {
         const bool joint = kind == K_ANN2 || kind == K_ASS2, ann = kind == K_ANN || kind == K_ANN2;
         double D = 1.0, r = 0.0;   // D = prod_{u=t}^{s-1} v_u p_u
         for (int s = t; s < S; ++s) {
@@ -33,27 +34,33 @@ __device__ double sum_reserve(const double2* tab, const double* v, int s_pad, co
                 q = q + p * ey.y;
                 p = p * ey.x;
             }
-            r += ann ? D * vs * p : D * vs * q;   // annuity: paid if alive at s+1; assurance: death in s
+            const double cs = cf ? cf[s] : 1.0;   // c_s / c
+            r += (ann ? D * vs * p : D * vs * q) * cs;   // annuity: paid if alive at s+1; assurance: death in s
             D *= vs * p;
         }
         return r + D * rec.bnd;
     }
-    // JL: row x = e_k^T prod W over states (00, 01, 10), c = (1, 1, rho), r_S = 0
+    // three-state models: row x = e_k^T prod W over states (00, x only, y only),
+    // W = [[px py, px qy, qx py], [0, px, 0], [0, 0, py]].  JL: c = (1, 1, rho)
+    // on the states at the step's end, r_S = 0.  Second death: the benefit on
+    // the transitions into "both dead", x (qx qy, qx, qy), r_S = bnd in every state.
     double x0 = rec.state0 == 0 ? 1.0 : 0.0, x1 = rec.state0 == 1 ? 1.0 : 0.0, x2 = rec.state0 == 2 ? 1.0 : 0.0;
     double D = 1.0, r = 0.0;
     for (int s = t; s < S; ++s) {
         const double vs = v[(size_t)s * s_pad];
         const double2 ex = tab[rec.idx1 + s], ey = tab[rec.idx2 + s];
-        // x <- x W_s, W = [[px py, px qy, qx py], [0, px, 0], [0, 0, py]]
+        const double cs = cf ? cf[s] : 1.0;
+        D *= vs;
+        if (kind == K_LS2) r += D * (x0 * ex.y * ey.y + x1 * ex.y + x2 * ey.y) * cs;
         const double y0 = x0 * ex.x * ey.x;
         const double y1 = x0 * ex.x * ey.y + x1 * ex.x;
         const double y2 = x0 * ex.y * ey.x + x2 * ey.x;
         x0 = y0;
         x1 = y1;
         x2 = y2;
-        D *= vs;
-        r += D * (x0 + x1 + x2 * rho);
+        if (kind == K_JL) r += D * (x0 + x1 + x2 * rho) * cs;
     }
+    if (kind == K_LS2) r += D * (x0 + x1 + x2) * rec.bnd;
     return r;
 }
 
@@ -79,8 +86,9 @@ __global__ void __launch_bounds__(256) summation_kernel(const RecurArgs a, int w
         if (t > rec.S || (!want_all && t != 0)) continue;
         const int kind = a.tile_kind[tile];
         const double amount = a.amount[rec.pol];
-        const double x = amount * (t == rec.S ? (rec.state0 == 0 ? (double)rec.bnd : 0.0)
-                                              : sum_reserve(tab, plane + s, a.s_pad, rec, kind, t));
+        const double* cf = a.cf ? static_cast<const double*>(a.cf) + (size_t)rec.pol * a.cf_ld : nullptr;
+        const double bnd = (rec.state0 == 0 || kind == K_LS2) ? (double)rec.bnd : 0.0;   // r_S in the state
+        const double x = amount * (t == rec.S ? bnd : sum_reserve(tab, plane + s, a.s_pad, rec, kind, t, cf));
         if (want_all && t <= a.n_steps)
             a.traj[((size_t)rec.pol * (a.n_steps + 1) + t) * a.n_scen + s] = x;
         if (t == 0) {

@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "RSV_OK", -1: "RSV_E_ARG", -2: "RSV_E_NOMEM", -3: "RSV_E_CUDA
                 -5: "RSV_E_TIMEOUT", -6: "RSV_E_ASSUMPTION", -7: "RSV_E_LIMIT"}
 RSV_SL_ANNUITY, RSV_JL_REVERSIONARY, RSV_TERM_ASSURANCE, RSV_ENDOWMENT = 0, 1, 2, 3
 RSV_JOINT_ANNUITY, RSV_LAST_SURVIVOR, RSV_JOINT_TERM, RSV_JOINT_ENDOWMENT = 4, 5, 6, 7
+RSV_LS_TERM, RSV_LS_ENDOWMENT = 8, 9
 RSV_FORM_F64, RSV_FORM_F32, RSV_FORM_F32_COMP = 0, 1, 2
 RSV_VARIANT_TIME_SCAN = -2   # the FP64 parallel-in-time scan (see include/rsv.h)
 RSV_VARIANT_SUMMATION = -3   # the FP64 O(S^2) summation definition
@@ -39,6 +40,23 @@ POLICY_DTYPE = np.dtype([("product", "<i4"), ("age1_m", "<i4"), ("age2_m", "<i4"
                          ("state0", "<i4"), ("table1", "<i4"), ("table2", "<i4"), ("reserved", "<i4"),
                          ("amount", "<f8"), ("reversion", "<f8")])
 assert POLICY_DTYPE.itemsize == C.sizeof(rsv_policy) == 48
+
+
+class rsv_schedule(C.Structure):
+    _fields_ = [("every", C.c_int32), ("first", C.c_int32), ("since", C.c_int32), ("steps_per_year", C.c_int32),
+                ("escalation", C.c_double), ("increase", C.c_double)]
+
+
+SCHEDULE_DTYPE = np.dtype([("every", "<i4"), ("first", "<i4"), ("since", "<i4"), ("steps_per_year", "<i4"),
+                           ("escalation", "<f8"), ("increase", "<f8")])
+assert SCHEDULE_DTYPE.itemsize == C.sizeof(rsv_schedule) == 32
+
+
+RSV_MLIFE_ANNUITY, RSV_MLIFE_ASSURANCE = 0, 1
+
+MLIFE_DTYPE = np.dtype([("m", "<i4"), ("kind", "<i4"), ("k", "<i4"), ("term_m", "<i4"), ("age_m", "<i4", (4,)),
+                        ("table", "<i4", (4,)), ("dead0", "<i4"), ("reserved", "<i4"), ("amount", "<f8")])
+assert MLIFE_DTYPE.itemsize == 64
 
 
 class rsv_opts(C.Structure):
@@ -95,7 +113,8 @@ _lib = None
 
 # Exported symbols of librsv.so that include/rsv.h declares.
 EXPORTS = ["rsv_create", "rsv_destroy", "rsv_set_stream", "rsv_load_decrements", "rsv_load_portfolio",
-           "rsv_load_decrements_fraction", "rsv_load_scenarios_fraction",
+           "rsv_load_decrements_fraction", "rsv_load_scenarios_fraction", "rsv_load_cashflows", "rsv_load_schedules",
+           "rsv_clear_cashflows", "rsv_compute_mlife",
            "rsv_load_scenarios", "rsv_compute_reserves", "rsv_compute_nested", "rsv_variant_count", "rsv_variant_name",
            "rsv_tune", "rsv_synchronize", "rsv_last_error", "rsv_last_kernel_ms", "rsv_device_sm_count",
            "rsv_reserves_noalloc", "rsv_mlp_param_count", "rsv_mlp_init", "rsv_mlp_set_params",
@@ -126,6 +145,10 @@ def load_library(path: str = LIB_PATH):
         "rsv_load_scenarios": ([vp, vp, i32, i32, i32], i32),
         "rsv_load_decrements_fraction": ([vp, i32, vp, i32], i32),
         "rsv_load_scenarios_fraction": ([vp, vp, i32, i32, i32], i32),
+        "rsv_load_cashflows": ([vp, vp, i64, i32], i32),
+        "rsv_load_schedules": ([vp, vp, i64, i32], i32),
+        "rsv_clear_cashflows": ([vp], i32),
+        "rsv_compute_mlife": ([vp, vp, i64, C.POINTER(rsv_opts), C.POINTER(rsv_out)], i32),
         "rsv_compute_reserves": ([vp, C.POINTER(rsv_opts), C.POINTER(rsv_out)], i32),
         "rsv_compute_nested": ([vp, C.POINTER(rsv_opts), C.POINTER(rsv_nested_spec), C.POINTER(rsv_nested_out)],
                                i32),
@@ -241,6 +264,35 @@ def rsv_load_scenarios_fraction(ctx, v_f, layout: int = 0):
     _check(ctx, _lib.rsv_load_scenarios_fraction(ctx, v.ctypes.data, n_scen, n_steps, layout))
 
 
+def rsv_load_cashflows(ctx, cf):
+    """Cash-flow multipliers c_t / c: host FP64 [n_pol, n_steps]."""
+    a = np.ascontiguousarray(cf, dtype=np.float64)
+    if a.ndim != 2:
+        raise ValueError("cf must be [n_pol, n_steps]")
+    _check(ctx, _lib.rsv_load_cashflows(ctx, a.ctypes.data, a.shape[0], a.shape[1]))
+
+
+def schedule_records(sch) -> np.ndarray:
+    """Schedule records in the ABI layout from a dict of arrays or a record array."""
+    if isinstance(sch, np.ndarray) and sch.dtype == SCHEDULE_DTYPE:
+        return np.ascontiguousarray(sch)
+    n = len(sch["every"])
+    rec = np.zeros(n, SCHEDULE_DTYPE)
+    for k in SCHEDULE_DTYPE.names:
+        rec[k] = sch[k]
+    return rec
+
+
+def rsv_load_schedules(ctx, sch, n_steps: int):
+    """One payment schedule per policy, expanded on the device into rows of n_steps."""
+    rec = schedule_records(sch)
+    _check(ctx, _lib.rsv_load_schedules(ctx, rec.ctypes.data if len(rec) else None, len(rec), n_steps))
+
+
+def rsv_clear_cashflows(ctx):
+    _check(ctx, _lib.rsv_clear_cashflows(ctx))
+
+
 def rsv_compute_reserves(ctx, form: int = RSV_FORM_F32_COMP, outputs: int = RSV_OUT_V0, horizon: int = 0,
                          on_device: bool = False, variant: int = -1, V0=None, V0d=None, scen_total=None,
                          pt_mean=None, traj=None, payment: int = 0):
@@ -249,6 +301,30 @@ def rsv_compute_reserves(ctx, form: int = RSV_FORM_F32_COMP, outputs: int = RSV_
     o = rsv_opts(form, outputs, horizon, 1 if on_device else 0, variant, payment)
     out = rsv_out(_ptr(V0), _ptr(V0d), _ptr(scen_total), _ptr(pt_mean), _ptr(traj))
     _check(ctx, _lib.rsv_compute_reserves(ctx, C.byref(o), C.byref(out)))
+
+
+def mlife_records(pol) -> np.ndarray:
+    """m-life records in the ABI layout from a dict of arrays (age_m and table
+    [n, 4]) or an existing record array."""
+    if isinstance(pol, np.ndarray) and pol.dtype == MLIFE_DTYPE:
+        return np.ascontiguousarray(pol)
+    n = len(pol["m"])
+    rec = np.zeros(n, MLIFE_DTYPE)
+    for k in MLIFE_DTYPE.names:
+        if k in pol:
+            rec[k] = pol[k]
+    return rec
+
+
+def rsv_compute_mlife(ctx, pol, form: int = RSV_FORM_F32_COMP, outputs: int = RSV_OUT_V0, on_device: bool = False,
+                      V0=None, V0d=None, scen_total=None):
+    """Reserves of m-life policies (see include/rsv.h) under the loaded tables and
+    scenarios; outputs [n, n_scen] and [n_scen]."""
+    rec = mlife_records(pol)
+    o = rsv_opts(form, outputs, 0, 1 if on_device else 0, -1, 0)
+    out = rsv_out(_ptr(V0), _ptr(V0d), _ptr(scen_total), None, None)
+    _check(ctx, _lib.rsv_compute_mlife(ctx, rec.ctypes.data if len(rec) else None, len(rec), C.byref(o),
+                                       C.byref(out)))
 
 
 def rsv_compute_nested(ctx, form: int = RSV_FORM_F32_COMP, *, n_outer: int, n_nodes: int, node_step_m: int = 12,

@@ -184,10 +184,14 @@ def test_surrogate_mode_gain_over_brute_force(ctx):
 
 def test_nested_two_life_products_against_oracle(ctx):
     """The nested valuation of the two-life products (joint and last-survivor
-    annuities, joint term assurances and endowments): every (o, n, i) of a
-    small run against the oracle's full-state node liabilities."""
+    annuities, joint term assurances and endowments, second-death term
+    assurances and endowments): every (o, n, i) of a small run against the
+    oracle's full-state node liabilities."""
     tab = synth.gm_monthly_survival()
-    pol = synth.portfolio_two_life(40, seed=14, age_lo_y=50, age_hi_y=80)
+    pol = synth.portfolio_two_life(48, seed=14, age_lo_y=50, age_hi_y=80, products=tuple(range(4, 10)))
+    ls = np.where(pol["product"] >= 8)[0]
+    pol["state0"][ls[:4]] = 1     # valued with only the first life alive
+    pol["state0"][ls[4:8]] = 2    # only the second
     spec = dict(n_outer=2, n_nodes=4, node_step_m=24, n_inner=40, seed=15)
     out = nested(ctx, pol, tab, rsv.RSV_FORM_F32_COMP, **spec)
     worst = 0.0

@@ -196,7 +196,7 @@ def test_assumption_and_state_errors(ctx):
         rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F32, rsv.RSV_OUT_SCEN_TOTAL, scen_total=np.zeros(1))
     assert e.value.status == rsv.RSV_E_ASSUMPTION
     pol["reversion"][:] = 0.5
-    pol["product"][0] = 9
+    pol["product"][0] = 10   # no such product
     rsv.rsv_load_portfolio(ctx, pol)
     with pytest.raises(rsv.RsvError) as e:
         rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F32, rsv.RSV_OUT_SCEN_TOTAL, scen_total=np.zeros(1))
@@ -408,18 +408,23 @@ def test_host_outputs_pipelined_equal_device_outputs(ctx, n_scen):
 @pytest.mark.parametrize("form", FORMS)
 def test_two_life_products(ctx, form):
     """Joint-life and last-survivor annuities, joint term assurances and joint
-    endowments (two tables), mixed with the four single-table products, under
-    ragged Vasicek scenarios: against the oracle's full two-life models."""
+    endowments, second-death term assurances and endowments in all three
+    valuation states (two tables), mixed with the four single-table products,
+    under ragged Vasicek scenarios: against the oracle's full two-life models
+    (the nine-state one for the second death)."""
     tab = synth.gm_monthly_survival()
     tab2 = synth.gm_monthly_survival(A=0.0004, B=0.00002)
-    two = synth.portfolio_two_life(240, seed=3)
+    two = synth.portfolio_two_life(300, seed=3, products=tuple(range(4, 10)))
     two["table2"][:] = 1
+    ls = np.where(two["product"] >= 8)[0]
+    two["state0"][ls[:20]] = 1    # second-death products valued with one life alive
+    two["state0"][ls[20:40]] = 2
     pol = {k: np.concatenate([two[k], synth.portfolio_mix(60, seed=3)[k]]) for k in two}
     v = synth.vasicek_paths(70, 1200, seed=3)
     V0, tot = run(ctx, pol, tab, v, form, tables=[tab, tab2])
     ref, ref_tot = oracle.reserves_batch(pol, np.stack([tab, tab2]), v)
     err = rel_err(V0, ref, pol["amount"])
-    for p in range(8):
+    for p in range(10):
         m = pol["product"] == p
         print(f"two-life form {rsv.FORM_NAMES[form]} product {p}: max rel err {err[m].max():.3e}")
     assert err.max() <= TOL[form]
@@ -489,3 +494,152 @@ def test_payment_fraction_needs_its_inputs(ctx):
     with pytest.raises(rsv.RsvError) as e:
         rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_V0, payment=7, V0d=np.zeros((10, 8)))
     assert e.value.status == rsv.RSV_E_ARG
+
+
+def _schedule_rows(sch, n_steps):
+    """The oracle's expansion of each policy's payment schedule."""
+    return np.stack([oracle.schedule(n_steps, every=int(sch["every"][i]), first=int(sch["first"][i]),
+                                     since=int(sch["since"][i]), steps_per_year=int(sch["steps_per_year"][i]),
+                                     escalation=float(sch["escalation"][i]), increase=float(sch["increase"][i]))
+                     for i in range(len(sch["every"]))])
+
+
+def _cf_portfolio(n_single, n_two, seed):
+    base = synth.portfolio_mix(n_single, seed=seed)
+    two = synth.portfolio_two_life(n_two, seed=seed, products=tuple(range(4, 10)))
+    two["table2"][:] = 1
+    jl = np.where(base["product"] == 1)[0][:8]
+    extra = synth.take(base, np.concatenate([jl, jl]))
+    extra["state0"][: len(jl)] = 1
+    extra["state0"][len(jl):] = 2
+    return {k: np.concatenate([base[k], extra[k], two[k]]) for k in base}
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_payment_schedules(ctx, form):
+    """Monthly and annual payments, escalating (3%, 4.25%, 5%) and increasing
+    annuities and assurances (Section 4.1.1, 4.6), every product, expanded on
+    the device from per-policy schedules: against the oracle with its own
+    expansion of the same schedules."""
+    tab = synth.gm_monthly_survival()
+    tab2 = synth.gm_monthly_survival(A=0.0004, B=0.00002)
+    pol = _cf_portfolio(200, 80, seed=21)
+    n, n_scen, T = len(pol["product"]), 70, 1200
+    sch = synth.payment_schedules(n, seed=21, annual_share=0.3, escalating_share=0.3, increasing_share=0.2)
+    v = synth.vasicek_paths(n_scen, T, seed=21)
+    rsv.rsv_load_schedules(ctx, sch, T)
+    V0, tot = run(ctx, pol, tab, v, form, tables=[tab, tab2])
+    cf = _schedule_rows(sch, T)
+    ref, ref_tot = oracle.reserves_batch(pol, np.stack([tab, tab2]), v, cf=cf)
+    err = rel_err(V0, ref, pol["amount"])
+    print(f"schedules form {rsv.FORM_NAMES[form]}: max rel err {err.max():.3e}")
+    assert err.max() <= TOL[form]
+    assert np.max(np.abs(tot - ref_tot) / ref_tot) <= TOL[form]
+    # level schedules reproduce the level valuation of the fast kernels
+    lvl = {k: np.asarray(x).copy() for k, x in sch.items()}
+    lvl["every"][:], lvl["first"][:], lvl["escalation"][:], lvl["increase"][:] = 1, 0, 0.0, 0.0
+    rsv.rsv_load_schedules(ctx, lvl, T)
+    V1, _ = run(ctx, pol, tab, v, form, tables=[tab, tab2])
+    rsv.rsv_clear_cashflows(ctx)
+    V2, _ = run(ctx, pol, tab, v, form, tables=[tab, tab2])
+    assert rel_err(V1, V2, pol["amount"]).max() <= 2 * TOL[form]
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("payment", [rsv.RSV_PAY_START, rsv.RSV_PAY_FRACTION])
+def test_cash_flow_rows_with_payment_within_the_step(ctx, form, payment):
+    """Explicit per-step multipliers (random, a third of them zero, decreasing
+    assurance benefits) with the annuity paid at f = 0 or f = 1/2."""
+    tab = synth.gm_monthly_survival()
+    pol = _cf_portfolio(40, 16, seed=22)
+    pol["table2"][:] = 0
+    n, n_scen, T = len(pol["product"]), 40, 1200
+    rng = np.random.default_rng(22)
+    cf = rng.uniform(0.0, 2.0, (n, T))
+    cf[rng.uniform(size=(n, T)) < 0.33] = 0.0
+    ass = np.isin(pol["product"], (2, 3, 6, 7, 8, 9))
+    cf[ass] = np.maximum(0.0, 1.0 - np.arange(T) / 600.0)[None, :]
+    v = synth.vasicek_paths(n_scen, T, seed=22)
+    tab_f = np.sqrt(tab) if payment == rsv.RSV_PAY_FRACTION else np.ones_like(tab)
+    v_f = np.sqrt(v) if payment == rsv.RSV_PAY_FRACTION else np.ones_like(v)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    rsv.rsv_load_cashflows(ctx, cf)
+    if payment == rsv.RSV_PAY_FRACTION:
+        rsv.rsv_load_decrements_fraction(ctx, 0, tab_f)
+        rsv.rsv_load_scenarios_fraction(ctx, v_f)
+    V0 = np.zeros((n, n_scen))
+    rsv.rsv_compute_reserves(ctx, form, rsv.RSV_OUT_V0, payment=payment, V0d=V0)
+    ref = np.zeros((n, n_scen))
+    for p in range(n):
+        prod = int(pol["product"][p])
+        kw = dict(age2=int(pol["age2_m"][p]), term=int(pol["term_m"][p]), rho=float(pol["reversion"][p]), cf=cf[p])
+        if prod in (0, 1, 4, 5):
+            kw.update(table_fx=tab_f, table_fy=tab_f)
+        for s in range(n_scen):
+            if prod in (0, 1, 4, 5):
+                kw["vf"] = v_f[s]
+            r = oracle.chain(prod, int(pol["age1_m"][p]), float(pol["amount"][p]), tab, v[s], **kw)
+            ref[p, s] = r[0, int(pol["state0"][p])]
+    err = rel_err(V0, ref, pol["amount"])
+    print(f"cash-flow rows payment {payment} form {rsv.FORM_NAMES[form]}: max rel err {err.max():.3e}")
+    assert err.max() <= TOL[form]
+
+
+def test_cash_flows_time_scan_and_summation(ctx):
+    """The FP64 time scan (V0 and the trajectory) and the summation kernel with
+    payment schedules, against the oracle."""
+    tab = synth.gm_monthly_survival()
+    pol = _cf_portfolio(30, 12, seed=23)
+    pol["table2"][:] = 0
+    n, n_scen, T = len(pol["product"]), 6, 1200
+    sch = synth.payment_schedules(n, seed=23, annual_share=0.5, escalating_share=0.5, increasing_share=0.3)
+    v = synth.vasicek_paths(n_scen, T, seed=23)
+    rsv.rsv_load_schedules(ctx, sch, T)
+    cf = _schedule_rows(sch, T)
+    ref, _ = oracle.reserves_batch(pol, tab, v, cf=cf)
+    for var in (rsv.RSV_VARIANT_TIME_SCAN, rsv.RSV_VARIANT_SUMMATION):
+        V0, _ = run(ctx, pol, tab, v, rsv.RSV_FORM_F64, variant=var)
+        assert rel_err(V0, ref, pol["amount"]).max() <= 1e-12, var
+    traj = np.zeros((n, T + 1, n_scen))
+    rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_TRAJ, variant=rsv.RSV_VARIANT_TIME_SCAN, traj=traj)
+    for p in range(0, n, 5):
+        r = oracle.chain(int(pol["product"][p]), int(pol["age1_m"][p]), float(pol["amount"][p]), tab, v[2],
+                         age2=int(pol["age2_m"][p]), term=int(pol["term_m"][p]), rho=float(pol["reversion"][p]),
+                         cf=cf[p])
+        S = r.shape[0] - 1
+        got = traj[p, : S + 1, 2]
+        want = r[:, int(pol["state0"][p])]
+        assert np.max(np.abs(got - want) / np.maximum(np.abs(want), 1e-9 * pol["amount"][p])) <= 1e-12
+
+
+def test_cash_flow_errors(ctx):
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_single_life(10)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, synth.vasicek_paths(8, 1200, seed=1))
+    V0 = np.zeros((10, 8))
+    with pytest.raises(rsv.RsvError) as e:      # negative multiplier
+        rsv.rsv_load_cashflows(ctx, -np.ones((10, 1200)))
+    assert e.value.status == rsv.RSV_E_ASSUMPTION
+    bad = synth.payment_schedules(10, seed=1)
+    bad["since"][3] = 12
+    with pytest.raises(rsv.RsvError) as e:
+        rsv.rsv_load_schedules(ctx, bad, 1200)
+    assert e.value.status == rsv.RSV_E_ARG
+    rsv.rsv_load_cashflows(ctx, np.ones((9, 1200)))   # rows for another portfolio size
+    with pytest.raises(rsv.RsvError) as e:
+        rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_V0, V0d=V0)
+    assert e.value.status == rsv.RSV_E_STATE
+    rsv.rsv_load_cashflows(ctx, np.ones((10, 5)))     # rows shorter than the projections
+    with pytest.raises(rsv.RsvError) as e:
+        rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_V0, V0d=V0)
+    assert e.value.status == rsv.RSV_E_STATE
+    rsv.rsv_load_cashflows(ctx, np.ones((10, 1200)))
+    with pytest.raises(rsv.RsvError) as e:      # per-step outputs need the scan or the summation
+        rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_TRAJ, traj=np.zeros((10, 1201, 8)))
+    assert e.value.status == rsv.RSV_E_ARG
+    rsv.rsv_clear_cashflows(ctx)
+    rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_V0, V0d=V0)
