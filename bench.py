@@ -257,6 +257,97 @@ def bench_nested(rsv, torch, tab, steps, warmup, n_outer=None, sur_epochs=10, su
     return res
 
 
+def bench_cashflows(rsv, torch, ctx, fid, level_ms, steps, warmup, flush):
+    """The main workload with the paper's payment mix (Section 5: about 80%
+    monthly and 20% annual payments, 5% escalating at 3%, 4.25% or 5% on each
+    anniversary), expanded on the device and valued by the general-cash-flow
+    kernel; against the level cash flows of the timed step."""
+    sch = synth.payment_schedules(N_POL, seed=0)
+    rsv.rsv_load_schedules(ctx, sch, N_STEPS)
+    V0 = torch.empty((N_POL, N_SCEN), dtype=torch.float32, device="cuda")
+    tot = torch.empty(N_SCEN, dtype=torch.float64, device="cuda")
+    outs = rsv.RSV_OUT_V0 | rsv.RSV_OUT_SCEN_TOTAL
+    for _ in range(warmup):
+        rsv.rsv_compute_reserves(ctx, fid, outs, on_device=True, V0=V0, scen_total=tot)
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        rsv.rsv_compute_reserves(ctx, fid, outs, on_device=True, V0=V0, scen_total=tot)
+        ms.append(rsv.rsv_last_kernel_ms(ctx))
+    rsv.rsv_clear_cashflows(ctx)
+    t = statistics.mean(ms)
+    return {"workload": WORKLOAD + "; payment schedules: 80% monthly / 20% annual, 5% escalating",
+            "kernel_ms": t, "valuations_s": N_POL * N_SCEN / (t / 1e3), "level_kernel_ms": level_ms,
+            "cost_vs_level": t / level_ms,
+            "variant": "general cash flows (unshifted states, c_t per policy and step)"}
+
+
+# Operations per chain-step of the m-life kernel (m lives; FMA = 2): each of
+# the m 2^(m-1) one-life mixes p a + q b, the scaling by v of the live states,
+# and the cash flow added to the paying states.  Plain forms: mix = FMA + MUL
+# (3), scale 1, add 1.  Compensated: mix = two double-float products (7 each)
+# and an ordered sum (7) = 21, scale 7, add 6.
+def mlife_flops(form, m, assurance, k):
+    n = 1 << m
+    marked = sum(1 for S in range(n) if (bin(S).count("1") >= k if assurance else m - bin(S).count("1") >= k))
+    mix, sc, add = (21, 7, 6) if form == "f32comp" else (3, 1, 1)
+    scaled = n - marked if assurance else n
+    return m * (n // 2) * mix + scaled * sc + (0 if assurance else marked) * add
+
+
+def mlife_bench_portfolio(n, seed=0):
+    """m = 2..4 lives (equal shares) aged 55-85; half annuities paid while k of m
+    are alive (whole life), half k-th death assurances (10-30 y); k uniform."""
+    rng = np.random.default_rng(seed)
+    pol = {"m": rng.integers(2, 5, n), "kind": rng.integers(0, 2, n), "k": np.zeros(n, int),
+           "term_m": np.zeros(n, int), "age_m": np.zeros((n, 4), int), "table": np.zeros((n, 4), int),
+           "dead0": np.zeros(n, int), "amount": rng.lognormal(np.log(1e3), 0.5, n)}
+    for i in range(n):
+        m = pol["m"][i]
+        pol["k"][i] = rng.integers(1, m + 1)
+        pol["age_m"][i, :m] = rng.integers(55 * 12, 85 * 12 + 1, m)
+        if pol["kind"][i] == 1:
+            pol["term_m"][i] = 12 * rng.integers(10, 31)
+    return pol
+
+
+def bench_mlife(rsv, torch, tab, n_pol=20_000, reps=3):
+    """m-life contracts (Section 4.3) under the 1,000 scenarios of 1,200 steps."""
+    pol = mlife_bench_portfolio(n_pol)
+    v = synth.vasicek_paths(N_SCEN, N_STEPS, seed=0)
+    ctx = rsv.rsv_create(torch.cuda.current_device(), torch.cuda.current_stream())
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_scenarios(ctx, v)
+    # steps of each policy (the kernel's rule): annuity to the k-th longest-lived
+    # table, assurance its term
+    S = np.zeros(n_pol, int)
+    for i in range(n_pol):
+        m, k = pol["m"][i], pol["k"][i]
+        if pol["kind"][i] == 1:
+            S[i] = pol["term_m"][i]
+        else:
+            rem = sorted(max(0, len(tab) - a) for a in pol["age_m"][i, :m])
+            S[i] = rem[m - k]
+    V0 = torch.empty((n_pol, N_SCEN), dtype=torch.float32, device="cuda")
+    res = {"workload": f"{n_pol:,} m-life policies (m = 2-4, half k-of-m annuities, half k-th death "
+                       f"assurances 10-30y, ages 55-85) x {N_SCEN:,} Vasicek scenarios x {N_STEPS:,} steps",
+           "chain_steps": int(S.sum()) * N_SCEN}
+    for form in ("f32comp", "f64"):
+        fid = FORMS[form]
+        rsv.rsv_compute_mlife(ctx, pol, fid, rsv.RSV_OUT_V0, on_device=True, V0=V0)
+        ms = []
+        for _ in range(reps):
+            rsv.rsv_compute_mlife(ctx, pol, fid, rsv.RSV_OUT_V0, on_device=True, V0=V0)
+            ms.append(rsv.rsv_last_kernel_ms(ctx))
+        t = statistics.mean(ms) / 1e3
+        flops = sum(mlife_flops(form, int(pol["m"][i]), pol["kind"][i] == 1, int(pol["k"][i])) * int(S[i])
+                    for i in range(n_pol)) * N_SCEN
+        res[form] = {"ms": t * 1e3, "valuations_s": n_pol * N_SCEN / t, "flops_per_launch": flops,
+                     "achieved_tflops": flops / t / 1e12}
+    rsv.rsv_destroy(ctx)
+    return res
+
+
 def bench_config1(rsv, torch, tab, reps=20):
     """Config 1 (1,000 annuities, one flat 4% rate, FP64): a latency-bound run with
     one scenario.  Kernel time of the scenario-parallel FP64 kernel against the
@@ -486,6 +577,8 @@ def main():
     ap.add_argument("--surrogate-val", type=int, default=1_000_000, help="held-out queries")
     ap.add_argument("--nested-outer", type=int, default=NESTED["n_outer"], help="outer paths (profiling runs: fewer)")
     ap.add_argument("--full-scale", action="store_true", help="also the 1M-policy full-scale configuration")
+    ap.add_argument("--mlife-only", action="store_true",
+                    help="time only the m-life contracts (--policies of them) and print their record")
     ap.add_argument("--nested-surrogate-epochs", type=int, default=10,
                     help="train the surrogate on the nested portfolio and time its mode (0: skip)")
     args = ap.parse_args()
@@ -498,6 +591,13 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_arm(args, rank)
+    if args.mlife_only:   # a profiling case of the m-life kernel
+        import torch
+        from paper_1401_1757_gb300 import rsv
+        torch.cuda.set_device(local)
+        print(json.dumps({"mlife": bench_mlife(rsv, torch, synth.gm_monthly_survival(), n_pol=args.policies)}),
+              flush=True)
+        return
 
     import torch
     import torch.distributed as dist
@@ -614,9 +714,14 @@ def main():
                "d2h_bytes_per_step": int(V0_host.numel() * 4 + tot_host.numel() * 8),
                "ms_per_step": 1e3 * tot_s / args.steps}
 
-    rsv.rsv_destroy(ctx)
-    nested = config1 = figure1 = None
+    cashflows = None
     if not args.no_nested and rank == 0:
+        cashflows = bench_cashflows(rsv, torch, ctx, FORMS[head], results[head]["kernel_ms"], args.steps,
+                                    args.warmup, flush)
+    rsv.rsv_destroy(ctx)
+    nested = config1 = figure1 = mlife = None
+    if not args.no_nested and rank == 0:
+        mlife = bench_mlife(rsv, torch, tab)
         config1 = bench_config1(rsv, torch, tab)
         figure1 = bench_figure1(rsv, torch, tab)
         nested = bench_nested(rsv, torch, tab, steps=2, warmup=1, n_outer=args.nested_outer,
@@ -656,6 +761,9 @@ def main():
             "flops_per_launch": flops}
     if peaks:
         roof["frac_of_measured_fma_peak"] = achieved / peaks["fp32_fma_tflops"]
+    if mlife and peaks:
+        mlife["f32comp"]["frac_of_measured_fp32_fma_peak"] = mlife["f32comp"]["achieved_tflops"] / peaks["fp32_fma_tflops"]
+        mlife["f64"]["frac_of_measured_fp64_fma_peak"] = mlife["f64"]["achieved_tflops"] / peaks["fp64_fma_tflops"]
     line = {
         "metric": METRIC, "value": h["valuations_s"], "unit": "valuations/s", "n_gpus": world,
         "steps": h["steps"], "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
@@ -673,6 +781,8 @@ def main():
         "forms": results,
         "config1_latency": config1,
         "summation_vs_recurrence": figure1,
+        "cash_flows": cashflows,
+        "mlife": mlife,
         "full_scale": full,
         "nested": nested,
         "surrogate": surrogate,

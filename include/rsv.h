@@ -517,6 +517,20 @@ typedef struct {
  * Errors: RSV_E_ARG, RSV_E_STATE, RSV_E_CUDA, RSV_E_NOMEM. */
 rsv_status rsv_surrogate_train(rsv_ctx *ctx, const rsv_surrogate_cfg *cfg, rsv_surrogate_report *report);
 
+/* Write the trained surrogate to a file: the network parameters (FP32), the
+ * target normalisation, the fallback map, the tolerance and the Vasicek
+ * parameters of its training, with a 64-bit FNV-1a checksum.  Host byte
+ * order.  The features refer to the loaded decrement tables and portfolio, so
+ * a loaded surrogate is meant for the same tables and policy records.
+ * Errors: RSV_E_ARG (NULL path, the file cannot be written), RSV_E_STATE (not
+ * trained), RSV_E_CUDA. */
+rsv_status rsv_surrogate_save(rsv_ctx *ctx, const char *path);
+
+/* Read a file written by rsv_surrogate_save; the surrogate is then trained.
+ * Errors: RSV_E_ARG (NULL path, unreadable file, wrong magic, size, shape or
+ * checksum), RSV_E_NOMEM, RSV_E_CUDA. */
+rsv_status rsv_surrogate_load(rsv_ctx *ctx, const char *path);
+
 /* A valuation query: policy index (into the loaded portfolio), node month m
  * (0 <= m < the policy's steps), reduced state (0; JL also 1, 2) and the
  * short rate at the node. */

@@ -13,6 +13,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <numeric>
 #include <vector>
 
@@ -756,6 +758,102 @@ rsv_status rsv_mlp_gradient(rsv_ctx* c, const float* X, const float* target, int
     CU(cudaMemcpyAsync(&l, c->mlp.loss, 4, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     if (loss) *loss = l / (float)n;
+    return RSV_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// FNV-1a, 64 bit, over a byte range (the file's integrity check)
+uint64_t fnv1a(const unsigned char* p, size_t n, uint64_t h = 1469598103934665603ull) {
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+const char kSurMagic[8] = {'R', 'S', 'V', 'S', 'U', 'R', '0', '1'};
+constexpr int kSurDoubles = 7;   // y_mean, y_std, tol, a, b, sigma, r0
+}  // namespace
+
+extern "C" {
+
+rsv_status rsv_surrogate_save(rsv_ctx* c, const char* path) {
+    if (!c) return RSV_E_ARG;
+    if (!path) return fail(c, RSV_E_ARG, "path must not be NULL");
+    if (!c->sur.trained || !c->mlp_ready) return fail(c, RSV_E_STATE, "surrogate not trained");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice failed");
+    const SurrogateState& s = c->sur;
+    const int64_t np = (int64_t)mlp_n_params(), nb = SUR_NBUCKETS;
+    std::vector<unsigned char> buf;
+    auto put = [&](const void* x, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(x);
+        buf.insert(buf.end(), b, b + n);
+    };
+    put(kSurMagic, 8);
+    put(&np, 8);
+    put(&nb, 8);
+    const double d[kSurDoubles] = {s.y_mean, s.y_std, s.tol, s.a, s.b, s.sigma, s.r0};
+    put(d, sizeof d);
+    put(s.flag.data(), (size_t)nb);
+    std::vector<float> w((size_t)np);
+    CU(cudaMemcpyAsync(w.data(), c->mlp.params, (size_t)np * 4, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    put(w.data(), w.size() * 4);
+    const uint64_t h = fnv1a(buf.data(), buf.size());
+    put(&h, 8);
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(c, RSV_E_ARG, "cannot open %s for writing", path);
+    const size_t wr = std::fwrite(buf.data(), 1, buf.size(), f);
+    const int cl = std::fclose(f);
+    if (wr != buf.size() || cl != 0) return fail(c, RSV_E_ARG, "writing %s failed", path);
+    return RSV_OK;
+}
+
+rsv_status rsv_surrogate_load(rsv_ctx* c, const char* path) {
+    if (!c) return RSV_E_ARG;
+    if (!path) return fail(c, RSV_E_ARG, "path must not be NULL");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(c, RSV_E_ARG, "cannot open %s", path);
+    std::vector<unsigned char> buf;
+    unsigned char tmp[65536];
+    size_t got;
+    while ((got = std::fread(tmp, 1, sizeof tmp, f)) > 0) buf.insert(buf.end(), tmp, tmp + got);
+    std::fclose(f);
+    const int64_t np = (int64_t)mlp_n_params(), nb = SUR_NBUCKETS;
+    const size_t want = 8 + 16 + kSurDoubles * 8 + (size_t)nb + (size_t)np * 4 + 8;
+    if (buf.size() != want || std::memcmp(buf.data(), kSurMagic, 8) != 0)
+        return fail(c, RSV_E_ARG, "%s is not a surrogate file of this library (%zu bytes)", path, buf.size());
+    int64_t fnp, fnb;
+    std::memcpy(&fnp, buf.data() + 8, 8);
+    std::memcpy(&fnb, buf.data() + 16, 8);
+    uint64_t h;
+    std::memcpy(&h, buf.data() + want - 8, 8);
+    if (fnp != np || fnb != nb || h != fnv1a(buf.data(), want - 8))
+        return fail(c, RSV_E_ARG, "%s: shape or checksum mismatch", path);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice failed");
+    size_t off = 24;
+    double d[kSurDoubles];
+    std::memcpy(d, buf.data() + off, sizeof d);
+    off += sizeof d;
+    SurrogateState& s = c->sur;
+    s.flag.assign(buf.data() + off, buf.data() + off + nb);
+    off += (size_t)nb;
+    std::vector<float> w((size_t)np);
+    std::memcpy(w.data(), buf.data() + off, (size_t)np * 4);
+    rsv_status st = mlp_upload(c, w.data());
+    if (st != RSV_OK) return st;
+    CU(s.d_flag.ensure((size_t)nb));
+    CU(cudaMemcpyAsync(s.d_flag.p, s.flag.data(), (size_t)nb, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    s.y_mean = d[0];
+    s.y_std = d[1];
+    s.tol = d[2];
+    s.a = d[3];
+    s.b = d[4];
+    s.sigma = d[5];
+    s.r0 = d[6];
+    s.trained = true;
     return RSV_OK;
 }
 

@@ -114,7 +114,7 @@ _lib = None
 # Exported symbols of librsv.so that include/rsv.h declares.
 EXPORTS = ["rsv_create", "rsv_destroy", "rsv_set_stream", "rsv_load_decrements", "rsv_load_portfolio",
            "rsv_load_decrements_fraction", "rsv_load_scenarios_fraction", "rsv_load_cashflows", "rsv_load_schedules",
-           "rsv_clear_cashflows", "rsv_compute_mlife",
+           "rsv_clear_cashflows", "rsv_compute_mlife", "rsv_surrogate_save", "rsv_surrogate_load",
            "rsv_load_scenarios", "rsv_compute_reserves", "rsv_compute_nested", "rsv_variant_count", "rsv_variant_name",
            "rsv_tune", "rsv_synchronize", "rsv_last_error", "rsv_last_kernel_ms", "rsv_device_sm_count",
            "rsv_reserves_noalloc", "rsv_mlp_param_count", "rsv_mlp_init", "rsv_mlp_set_params",
@@ -149,6 +149,8 @@ def load_library(path: str = LIB_PATH):
         "rsv_load_schedules": ([vp, vp, i64, i32], i32),
         "rsv_clear_cashflows": ([vp], i32),
         "rsv_compute_mlife": ([vp, vp, i64, C.POINTER(rsv_opts), C.POINTER(rsv_out)], i32),
+        "rsv_surrogate_save": ([vp, C.c_char_p], i32),
+        "rsv_surrogate_load": ([vp, C.c_char_p], i32),
         "rsv_compute_reserves": ([vp, C.POINTER(rsv_opts), C.POINTER(rsv_out)], i32),
         "rsv_compute_nested": ([vp, C.POINTER(rsv_opts), C.POINTER(rsv_nested_spec), C.POINTER(rsv_nested_out)],
                                i32),
@@ -441,6 +443,16 @@ def rsv_mlp_gradient(ctx, X, target):
     _check(ctx, _lib.rsv_mlp_gradient(ctx, X.ctypes.data, t.ctypes.data, X.shape[0], g.ctypes.data,
                                       C.byref(loss)))
     return g, loss.value
+
+
+def rsv_surrogate_save(ctx, path: str):
+    """Write the trained surrogate (network, normalisation, fallback map) to ``path``."""
+    _check(ctx, _lib.rsv_surrogate_save(ctx, os.fsencode(path)))
+
+
+def rsv_surrogate_load(ctx, path: str):
+    """Read a surrogate written by rsv_surrogate_save."""
+    _check(ctx, _lib.rsv_surrogate_load(ctx, os.fsencode(path)))
 
 
 def rsv_surrogate_train(ctx, n_train=10_000_000, n_val=1_000_000, epochs=20, batch=8192, lr=2e-3, seed=0,

@@ -166,3 +166,24 @@ def test_surrogate_learns_and_falls_back(ctx):
     assert np.all(np.isfinite(net)) and np.all(net > 0)
     same = (fb == rec) | (fb == net)
     assert np.all(same)
+    # the trained surrogate saved and loaded into a fresh context serves the same answers
+    import os
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "sur.bin")
+        rsv.rsv_surrogate_save(ctx, path)
+        other = rsv.rsv_create(0, torch.cuda.current_stream())
+        try:
+            rsv.rsv_load_decrements(other, 0, tab)
+            rsv.rsv_load_portfolio(other, pol)
+            rsv.rsv_surrogate_load(other, path)
+            assert np.array_equal(rsv.rsv_surrogate_query(other, q, how=rsv.RSV_QUERY_NETWORK), net)
+            assert np.array_equal(rsv.rsv_surrogate_query(other, q, how=rsv.RSV_QUERY_FALLBACK), fb)
+            raw = bytearray(open(path, "rb").read())
+            raw[100] ^= 1                                   # one flipped bit: the checksum fails
+            open(path, "wb").write(bytes(raw))
+            with pytest.raises(rsv.RsvError) as e:
+                rsv.rsv_surrogate_load(other, path)
+            assert e.value.status == rsv.RSV_E_ARG
+        finally:
+            rsv.rsv_destroy(other)
