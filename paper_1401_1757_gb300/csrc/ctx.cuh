@@ -90,10 +90,17 @@ struct PolPrep {
     double rho;
 };
 
-struct Layout {            // cached tiling for one (P, horizon, data generation)
-    int P = -1, horizon = -1;
+// Cached tiling for one (P, P_general, horizon, data generation).  Tiles come
+// in up to two groups, each in decreasing cost order: group 0 of P policies,
+// then group 1 of P_general policies whose loaded cash flows are not level
+// (only when P_general > 0), valued by the general-cash-flow kernel.
+struct Layout {
+    int P = -1, P_general = -1, horizon = -1;
     unsigned long long gen = ~0ull;
     int n_tiles = 0, tab_pad = 0, n_tab = 0;
+    int grp_tiles[2] = {0, 0};       // tiles per group
+    size_t grp_slot0[2] = {0, 0};    // first slot of each group
+    bool grp_two[2] = {false, false};
     double chain_steps = 0;  // sum over policies of S (per scenario)
     int max_S = 0;           // longest projection
     bool has_two = false;    // tiles of K_ANN2, K_ASS2 or K_LS2 present
@@ -157,6 +164,8 @@ struct rsv_ctx {
     int64_t cf_pol = 0;                             // cash-flow multipliers: rows (0 = level)
     int cf_steps = 0;                               //   and row length
     DevBuf d_cf64, d_cf32;                          //   FP64 rows and their FP32 copy
+    std::vector<unsigned char> cf_level;            //   per policy: 1 = the row is all ones
+    unsigned long long cf_gen = 1;
     DevBuf d_ml_rec, d_ml_amount;                   // m-life records of the last call
 
     Layout lay;
@@ -192,7 +201,7 @@ inline rsv_status fail(rsv_ctx* c, rsv_status st, const char* fmt, ...) {
 
 // Cached device work layout (policy tiles) and decrement tables in a form's
 // entry format (rsv_abi.cu).
-rsv_status build_layout(rsv_ctx* c, int P, int horizon, int max_steps);
+rsv_status build_layout(rsv_ctx* c, int P, int horizon, int max_steps, int P_general = 0);
 rsv_status build_tables(rsv_ctx* c, int form, size_t& smem);
 // The first n_tab loaded tables, pad entries each, in a form's entry format
 // on the device (cached by shape and table generation); smem = their bytes.

@@ -62,6 +62,19 @@ __global__ void schedule_kernel(const rsv_schedule* __restrict__ sch, int64_t n_
     }
 }
 
+// Per policy: 1 if its cash-flow row is all ones (level), one warp per row.
+__global__ void cf_level_kernel(const double* __restrict__ cf, int64_t n_pol, int n_steps,
+                                unsigned char* __restrict__ level) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; p < n_pol; p += warps) {
+        bool one = true;
+        for (int t = lane; t < n_steps; t += 32) one &= cf[(size_t)p * n_steps + t] == 1.0;
+        one = __all_sync(0xffffffffu, one);
+        if (lane == 0) level[p] = one ? 1 : 0;
+    }
+}
+
 const Variant* variant_list(int form, int* n) {
     switch (form) {
     case F_F64: return variants_f64(n);
@@ -224,36 +237,47 @@ rsv_status prep_policies(rsv_ctx* c, int horizon, int max_steps, std::vector<Pol
 
 }  // namespace
 
-rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
+rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps, int P_general) {
     Layout& L = c->lay;
-    const unsigned long long gen = c->pol_gen * 1000003ull + c->tab_gen * 7919ull + (unsigned)max_steps;
-    if (L.P == P && L.horizon == horizon && L.gen == gen) return RSV_OK;
+    // the general group exists only while cash flows are loaded for this portfolio
+    const bool split = P_general > 0 && c->cf_pol > 0 && c->cf_pol == (int64_t)c->pols.size();
+    if (!split) P_general = 0;
+    const unsigned long long gen = c->pol_gen * 1000003ull + c->tab_gen * 7919ull + (unsigned)max_steps +
+                                   (split ? c->cf_gen * 104729ull : 0ull);
+    if (L.P == P && L.P_general == P_general && L.horizon == horizon && L.gen == gen) return RSV_OK;
     std::vector<PolPrep> pp;
     int tab_pad, n_tab;
     double cs;
     rsv_status st = prep_policies(c, horizon, max_steps, pp, tab_pad, n_tab, cs);
     if (st != RSV_OK) return st;
+    auto group = [&](const PolPrep& q) { return split && !c->cf_level[q.pol] ? 1 : 0; };
 
-    // group by reduced model, longest projection first
+    // group by (cash-flow group, reduced model), longest projection first:
     // three-state tiles, then joint and single-life annuities, then assurances
     static const int kind_rank[6] = {3, 5, 0, 2, 4, 1};
-    // stable counting sort on (kind rank, S descending): S <= kMaxAgeSteps
-    const int nb = 6 * (kMaxAgeSteps + 1);
+    // stable counting sort on the key: S <= kMaxAgeSteps
+    const int per_group = 6 * (kMaxAgeSteps + 1);
+    const int nb = 2 * per_group;
     std::vector<int> bucket_start(nb + 1, 0), order(pp.size());
-    auto key = [&](const PolPrep& q) { return kind_rank[q.kind] * (kMaxAgeSteps + 1) + (kMaxAgeSteps - q.S); };
+    auto key = [&](const PolPrep& q) {
+        return group(q) * per_group + kind_rank[q.kind] * (kMaxAgeSteps + 1) + (kMaxAgeSteps - q.S);
+    };
     for (const PolPrep& q : pp) ++bucket_start[key(q) + 1];
     for (int b = 0; b < nb; ++b) bucket_start[b + 1] += bucket_start[b];
     for (size_t i = 0; i < pp.size(); ++i) order[bucket_start[key(pp[i])]++] = (int)i;
     std::vector<SlotRec> slots;
-    std::vector<int> kinds;
+    std::vector<int> kinds, grps;
+    std::vector<size_t> first;   // first slot of each tile
     std::vector<double> cost;
     size_t i = 0;
     while (i < order.size()) {
-        const int kind = pp[order[i]].kind;
+        const int kind = pp[order[i]].kind, g = group(pp[order[i]]);
+        const int Pg = g ? P_general : P;
+        first.push_back(slots.size());
         SlotRec last{};
-        for (int k = 0; k < P; ++k) {
+        for (int k = 0; k < Pg; ++k) {
             SlotRec s;
-            if (i < order.size() && pp[order[i]].kind == kind) {
+            if (i < order.size() && pp[order[i]].kind == kind && group(pp[order[i]]) == g) {
                 const PolPrep& q = pp[order[i]];
                 s.idx1 = q.table1 * tab_pad + q.idx_age1;
                 s.idx2 = q.table2 * tab_pad + q.idx_age2;
@@ -272,35 +296,50 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
             slots.push_back(s);
         }
         kinds.push_back(kind);
+        grps.push_back(g);
         const double w = kind == K_JL ? 4.5 : (kind == K_LS2 ? 4.0 : (kind == K_ANN2 || kind == K_ASS2 ? 1.4 : 1.0));
-        cost.push_back(w * slots[slots.size() - P].S);
+        cost.push_back(w * slots[first.back()].S);
     }
-    // tiles in decreasing cost order (longest-processing-time first): the
-    // tiles of each kind are already in decreasing cost, so merge the runs
-    // (ties keep creation order)
+    // tiles in decreasing cost order within each group (longest-processing-time
+    // first): the tiles of each (group, kind) run are already in decreasing
+    // cost, so merge the runs (ties keep creation order)
     const int n_tiles = (int)kinds.size();
-    std::vector<int> to(n_tiles);
-    {
+    std::vector<int> to;
+    to.reserve(n_tiles);
+    int grp_tiles[2] = {0, 0};
+    for (int g = 0; g < 2; ++g) {
         std::vector<int> head, end;
-        for (int t = 0; t < n_tiles; ++t)
-            if (t == 0 || kinds[t] != kinds[t - 1]) {
-                if (t) end.push_back(t);
+        for (int t = 0; t < n_tiles; ++t) {
+            if (grps[t] != g) continue;
+            if (head.empty() || kinds[t] != kinds[t - 1] || grps[t - 1] != g) {
+                if (!head.empty()) end.push_back(t);
                 head.push_back(t);
             }
-        if (n_tiles) end.push_back(n_tiles);
-        for (int out = 0; out < n_tiles; ++out) {
+        }
+        if (!head.empty()) {
+            int last_t = -1;
+            for (int t = 0; t < n_tiles; ++t)
+                if (grps[t] == g) last_t = t;
+            end.push_back(last_t + 1);
+        }
+        int cnt = 0;
+        for (int t = 0; t < n_tiles; ++t) cnt += grps[t] == g;
+        for (int out = 0; out < cnt; ++out) {
             int best = -1;
             for (size_t r = 0; r < head.size(); ++r)
                 if (head[r] < end[r] && (best < 0 || cost[head[r]] > cost[head[best]])) best = (int)r;
-            to[out] = head[best]++;
+            to.push_back(head[best]++);
         }
+        grp_tiles[g] = cnt;
     }
-    std::vector<SlotRec> s2((size_t)n_tiles * P);
+    std::vector<SlotRec> s2;
+    s2.reserve(slots.size());
     std::vector<int> k2(n_tiles);
     for (int t = 0; t < n_tiles; ++t) {
-        k2[t] = kinds[to[t]];
-        std::copy(slots.begin() + (size_t)to[t] * P, slots.begin() + (size_t)(to[t] + 1) * P,
-                  s2.begin() + (size_t)t * P);
+        const int src = to[t];
+        const size_t n = (size_t)(grps[src] ? P_general : P);
+        k2[t] = kinds[src];
+        s2.insert(s2.end(), slots.begin() + first[src], slots.begin() + first[src] + n);
     }
     CU(L.slots.ensure(std::max<size_t>(1, s2.size()) * sizeof(SlotRec)));
     CU(L.kinds.ensure(std::max<size_t>(1, k2.size()) * sizeof(int)));
@@ -311,17 +350,25 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps) {
         CU(cudaMemcpyAsync(L.kinds.p, k2.data(), k2.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     }
     L.P = P;
+    L.P_general = P_general;
     L.horizon = horizon;
     L.gen = gen;
     L.n_tiles = n_tiles;
+    L.grp_tiles[0] = grp_tiles[0];
+    L.grp_tiles[1] = grp_tiles[1];
+    L.grp_slot0[0] = 0;
+    L.grp_slot0[1] = (size_t)grp_tiles[0] * P;
     L.tab_pad = tab_pad;
     L.n_tab = n_tab;
     L.chain_steps = cs;
     L.max_S = 0;
     L.has_two = false;
+    L.grp_two[0] = L.grp_two[1] = false;
     for (const PolPrep& q : pp) {
         L.max_S = std::max(L.max_S, q.S);
-        L.has_two |= q.kind == K_ANN2 || q.kind == K_ASS2 || q.kind == K_LS2;
+        const bool two = q.kind == K_ANN2 || q.kind == K_ASS2 || q.kind == K_LS2;
+        L.has_two |= two;
+        L.grp_two[group(q)] |= two;
     }
     return RSV_OK;
 }
@@ -454,11 +501,15 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     if (cfl && extra && !scan && !summ)
         return fail(c, RSV_E_ARG, "per-step outputs with varying cash flows: use the time-scan or summation variant");
     const int nt = tunable_count(vl, nv);
-    int vi;
+    // With cash flows loaded and f = 1, the policies whose sequence is level
+    // keep the fast kernel (tile group 0) and the others take the
+    // general-cash-flow kernel (group 1).
+    const bool split = cfl && pay == PAY_END && !extra && !scan && !summ;
+    int vi, vg = -1;
     if (extra || scan || summ) {
         vi = special_variant(vl, nv, true, PAY_END);
-    } else if (pay != PAY_END || cfl) {
-        vi = special_variant(vl, nv, false, pay == PAY_END ? PAY_END_GENERAL : pay);
+    } else if (pay != PAY_END) {
+        vi = special_variant(vl, nv, false, pay);
     } else if (o->variant >= 0) {
         if (o->variant >= nt) return fail(c, RSV_E_ARG, "variant %d out of range", o->variant);
         vi = o->variant;
@@ -467,9 +518,10 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     } else {
         return fail(c, RSV_E_ARG, "variant %d out of range", o->variant);
     }
+    if (split) vg = special_variant(vl, nv, false, PAY_END_GENERAL);
     const Variant& V = vl[vi];
 
-    rsv_status st = build_layout(c, (scan || summ) ? 1 : V.P, o->horizon, c->n_steps);
+    rsv_status st = build_layout(c, (scan || summ) ? 1 : V.P, o->horizon, c->n_steps, split ? vl[vg].P : 0);
     if (st != RSV_OK) return st;
     if (cfl && c->lay.max_S > c->cf_steps)
         return fail(c, RSV_E_STATE, "a projection of %d steps is longer than the cash-flow rows (%d)", c->lay.max_S,
@@ -537,7 +589,33 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     a.v0_ld = NSc;
     a.cf = !cfl ? nullptr : (o->form == F_F64 ? c->d_cf64.p : c->d_cf32.p);
     a.cf_ld = c->cf_steps;
-    const int two = L.has_two ? 1 : 0;   // kernels compiled with the two-life single-state models
+    // One launch per non-empty tile group on the scenario columns of `base`:
+    // group 0 by V (with the cash flows unless they are split off), group 1
+    // by the general-cash-flow variant; each with its own zeroed queue head.
+    auto launch_groups = [&](const RecurArgs& base) -> rsv_status {
+        for (int g = 0; g < 2; ++g) {
+            const int n_t = L.grp_tiles[g];
+            if (n_t == 0) continue;
+            const Variant& VV = g ? vl[vg] : V;
+            const int two = L.grp_two[g] ? 1 : 0;   // kernels compiled with the other two-life models
+            RecurArgs b = base;
+            b.slots = L.slots.as<SlotRec>() + L.grp_slot0[g];
+            b.tile_kind = L.kinds.as<int32_t>() + (g ? L.grp_tiles[0] : 0);
+            b.n_tiles = n_t;
+            b.n_chunks = (b.n_scen + 32 * VV.M - 1) / (32 * VV.M);
+            b.n_items = n_t * b.n_chunks;
+            b.partial = base.partial ? base.partial + (size_t)(g ? L.grp_tiles[0] : 0) * c->s_pad : nullptr;
+            b.cf = (split && g == 0) ? nullptr : base.cf;
+            int bps = 0;
+            CU(VV.occupancy[two](&bps, smem));
+            if (bps < 1) return fail(c, RSV_E_CUDA, "variant %s cannot be resident with %zu B smem", VV.name, smem);
+            long long grid = (long long)c->sm_count * bps;
+            grid = std::max(1LL, std::min(grid, ((long long)b.n_items * 32 + VV.NT - 1) / VV.NT));
+            CU(cudaMemsetAsync(c->d_ctl.p, 0, sizeof(int32_t), c->stream));
+            CU(VV.launch[two](b, (int)grid, smem, c->stream));
+        }
+        return RSV_OK;
+    };
 
     // Host V0 of the scenario-parallel kernels: computed in column blocks of
     // scenarios, each block's V0 copied to the host on a second stream while
@@ -550,9 +628,6 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
         const int width = ((NSc + blocks - 1) / blocks + 127) / 128 * 128;   // multiple of 128 scenario columns
         if (!c->copy_stream) CU(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
         if (!c->ev_block) CU(cudaEventCreateWithFlags(&c->ev_block, cudaEventDisableTiming));
-        int bps = 0;
-        CU(V.occupancy[two](&bps, smem));
-        if (bps < 1) return fail(c, RSV_E_CUDA, "variant %s cannot be resident with %zu B smem", V.name, smem);
         const size_t esz_v = o->form == F_F64 ? sizeof(double) : (o->form == F_F32 ? sizeof(float) : sizeof(float2));
         const size_t esz_o = hV0f ? sizeof(float) : sizeof(double);
         char* dV0 = hV0f ? reinterpret_cast<char*>(V0f) : reinterpret_cast<char*>(V0d);
@@ -564,15 +639,10 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
             b.v = static_cast<const char*>(a.v) + (size_t)s0 * esz_v;
             b.vf = a.vf ? static_cast<const char*>(a.vf) + (size_t)s0 * esz_v : nullptr;
             b.n_scen = w;
-            b.n_chunks = (w + 32 * V.M - 1) / (32 * V.M);
-            b.n_items = L.n_tiles * b.n_chunks;
             b.V0f = a.V0f ? a.V0f + s0 : nullptr;
             b.V0d = a.V0d ? a.V0d + s0 : nullptr;
             b.partial = a.partial ? a.partial + s0 : nullptr;
-            long long grid = (long long)c->sm_count * bps;
-            grid = std::max(1LL, std::min(grid, ((long long)b.n_items * 32 + V.NT - 1) / V.NT));
-            CU(cudaMemsetAsync(c->d_ctl.p, 0, sizeof(int32_t), c->stream));
-            CU(V.launch[two](b, (int)grid, smem, c->stream));
+            if ((st = launch_groups(b)) != RSV_OK) return st;
             CU(cudaEventRecord(c->ev_block, c->stream));
             CU(cudaStreamWaitEvent(c->copy_stream, c->ev_block, 0));
             CU(cudaMemcpy2DAsync(hV0 + (size_t)s0 * esz_o, (size_t)NSc * esz_o, dV0 + (size_t)s0 * esz_o,
@@ -593,14 +663,8 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
             else CU(launch_summation(a, wpc, c->sm_count, smem, c->stream));
             CU(cudaEventRecord(c->ev1, c->stream));
         } else {
-            int bps = 0;
-            CU(V.occupancy[two](&bps, smem));
-            if (bps < 1) return fail(c, RSV_E_CUDA, "variant %s cannot be resident with %zu B smem", V.name, smem);
-            const long long warps_needed = items;
-            long long grid = (long long)c->sm_count * bps;
-            grid = std::max(1LL, std::min(grid, (warps_needed * 32 + V.NT - 1) / V.NT));
             CU(cudaEventRecord(c->ev0, c->stream));
-            CU(V.launch[two](a, (int)grid, smem, c->stream));
+            if ((st = launch_groups(a)) != RSV_OK) return st;
             CU(cudaEventRecord(c->ev1, c->stream));
         }
         c->ev_recorded = true;
@@ -990,6 +1054,21 @@ rsv_status rsv_load_scenarios_fraction(rsv_ctx* c, const double* v, int32_t n_sc
     return RSV_OK;
 }
 
+// The level flags of freshly written rows (device FP64) and the new generation.
+static rsv_status finish_cashflows(rsv_ctx* c, int64_t n_pol, int32_t n_steps) {
+    CU(c->d_vstage.ensure((size_t)n_pol));
+    cf_level_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(c->d_cf64.as<double>(), n_pol, n_steps,
+                                                            c->d_vstage.as<unsigned char>());
+    CU(cudaGetLastError());
+    c->cf_level.resize((size_t)n_pol);
+    CU(cudaMemcpyAsync(c->cf_level.data(), c->d_vstage.p, (size_t)n_pol, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->cf_pol = n_pol;
+    c->cf_steps = n_steps;
+    ++c->cf_gen;
+    return RSV_OK;
+}
+
 rsv_status rsv_load_cashflows(rsv_ctx* c, const double* cf, int64_t n_pol, int32_t n_steps) {
     if (!c) return RSV_E_ARG;
     if (!cf || n_pol < 1 || n_steps < 1 || n_pol * (int64_t)n_steps > 0x7fffffffLL)
@@ -1006,10 +1085,7 @@ rsv_status rsv_load_cashflows(rsv_ctx* c, const double* cf, int64_t n_pol, int32
     CU(cudaMemcpyAsync(c->d_cf64.p, cf, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     cf_to_f32_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(c->d_cf64.as<double>(), c->d_cf32.as<float>(), n);
     CU(cudaGetLastError());
-    CU(cudaStreamSynchronize(c->stream));
-    c->cf_pol = n_pol;
-    c->cf_steps = n_steps;
-    return RSV_OK;
+    return finish_cashflows(c, n_pol, n_steps);
 }
 
 rsv_status rsv_load_schedules(rsv_ctx* c, const rsv_schedule* sch, int64_t n_pol, int32_t n_steps) {
@@ -1033,16 +1109,16 @@ rsv_status rsv_load_schedules(rsv_ctx* c, const rsv_schedule* sch, int64_t n_pol
     schedule_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(c->d_vstage.as<rsv_schedule>(), n_pol, n_steps,
                                                             c->d_cf64.as<double>(), c->d_cf32.as<float>());
     CU(cudaGetLastError());
-    CU(cudaStreamSynchronize(c->stream));
-    c->cf_pol = n_pol;
-    c->cf_steps = n_steps;
-    return RSV_OK;
+    CU(cudaStreamSynchronize(c->stream));   // the staged schedules are read before d_vstage is reused
+    return finish_cashflows(c, n_pol, n_steps);
 }
 
 rsv_status rsv_clear_cashflows(rsv_ctx* c) {
     if (!c) return RSV_E_ARG;
     c->cf_pol = 0;
     c->cf_steps = 0;
+    c->cf_level.clear();
+    ++c->cf_gen;
     return RSV_OK;
 }
 

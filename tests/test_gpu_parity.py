@@ -643,3 +643,32 @@ def test_cash_flow_errors(ctx):
     assert e.value.status == rsv.RSV_E_ARG
     rsv.rsv_clear_cashflows(ctx)
     rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_V0, V0d=V0)
+
+
+def test_cash_flows_split_launch_host_and_device_outputs(ctx):
+    """Level and varying cash flows in one portfolio: the level policies run on
+    the fast kernel and the others on the general one, in column blocks when
+    the outputs go to the host.  Host and device outputs are bit-identical, and
+    the level policies equal a run without cash flows."""
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_mix(400, seed=24)
+    n, n_scen, T = 400, 300, 1200
+    v = synth.vasicek_paths(n_scen, T, seed=24)
+    sch = synth.payment_schedules(n, seed=24)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    V_level = np.zeros((n, n_scen))
+    rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F32_COMP, rsv.RSV_OUT_V0, V0d=V_level)
+    rsv.rsv_load_schedules(ctx, sch, T)
+    host = np.zeros((n, n_scen))
+    rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F32_COMP, rsv.RSV_OUT_V0, V0d=host)
+    dev = torch.zeros((n, n_scen), dtype=torch.float64, device="cuda")
+    rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F32_COMP, rsv.RSV_OUT_V0, on_device=True, V0d=dev)
+    torch.cuda.synchronize()
+    assert np.array_equal(host, dev.cpu().numpy())
+    level = (sch["every"] == 1) & (sch["escalation"] == 0) & (sch["increase"] == 0)
+    assert 0 < level.sum() < n
+    assert np.array_equal(host[level], V_level[level])
+    ref, _ = oracle.reserves_batch(pol, tab, v[:20], cf=_schedule_rows(sch, T))
+    assert rel_err(host[:, :20], ref, pol["amount"]).max() <= TOL[rsv.RSV_FORM_F32_COMP]
