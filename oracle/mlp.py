@@ -1,7 +1,9 @@
 """FP64 CPU reference of the surrogate perceptron (TEST INFRASTRUCTURE).
 
 Only tests/ may import this.  The network: 32 -> 256 -> 256 -> 256 -> 256 -> 1
-with exact-erf GELU, flat parameters W1 [32][256], b1, W2, b2, W3, b3, W4, b4
+with GELU in its tanh form (Hendrycks & Gimpel, "Gaussian Error Linear Units",
+2016: x Phi(x) ~ x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))) / 2), flat
+parameters W1 [32][256], b1, W2, b2, W3, b3, W4, b4
 (each W row-major [in][out]), w5 [256], b5 [1]; loss = mean squared error.
 Backward pass written out by the chain rule.
 
@@ -20,7 +22,8 @@ import math
 import numpy as np
 
 IN, H = 32, 256
-_erf = np.vectorize(math.erf)
+_C = math.sqrt(2.0 / math.pi)   # the tanh form's scale
+_K = 0.044715                   # and its cubic coefficient
 
 
 def dims():
@@ -55,11 +58,12 @@ def bf16(x):
 
 
 def gelu(z):
-    return 0.5 * z * (1.0 + _erf(z / math.sqrt(2.0)))
+    return 0.5 * z * (1.0 + np.tanh(_C * (z + _K * z ** 3)))
 
 
 def gelu_grad(z):
-    return 0.5 * (1.0 + _erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+    t = np.tanh(_C * (z + _K * z ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * _C * (1.0 + 3.0 * _K * z * z)
 
 
 def forward(p, X, bf16_storage=False):
