@@ -1,5 +1,5 @@
 // mlp.cu -- the reserve surrogate network on sm_103a: a 32 -> 256 -> 256 ->
-// 256 -> 256 -> 1 perceptron with exact-erf GELU, BF16 weights and
+// 256 -> 256 -> 1 perceptron with GELU (tanh form), BF16 weights and
 // activations, FP32 accumulation, FP32 master weights and Adam.
 //
 // Forward per layer l = 1..4:  Z_l = A_{l-1} W_l + b_l,  A_l = gelu(Z_l)

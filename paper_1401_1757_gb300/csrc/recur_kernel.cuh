@@ -6,8 +6,15 @@
 //   K_ASS  r_t = v_t (q_t + p_t r_{t+1})                        (Section 4.1.3)
 //   K_JL   three states of the two-life model (Section 4.2), c = (1, 1, rho):
 //            r01 = v px (1 + r01')          r10 = v py (rho + r10')
-//            r00 = v [px py (1 + r00') + px qy (1 + r01') + qx py (rho + r10')]
-//                = v px py (1 + r00') + qy r01 + qx r10   (r01, r10 of this step)
+//            r00 = v [px py (1 + r00') + px qy (1 + r01') + qx py (rho + r10')].
+//          With independent lives the reduced vector is, at every step, a
+//          combination of three single-state annuities (the reversionary
+//          annuity a_{x|y} = a_y - a_xy of Section 4.2.1):
+//            r00 = a_x + rho (a_y - a_xy),  r01 = a_x,  r10 = rho a_y,
+//            a_x = v px (1 + a_x'),  a_y = v py (1 + a_y'),  a_xy = v px py (1 + a_xy'),
+//          which is the recurrence above regrouped (substitute and use
+//          px + qx = 1).  The kernel runs the three annuity chains; the
+//          payment-within-the-step variants keep the vector form.
 //   K_LS2  the nine-state two-life assurance model (Section 4.2.3) with the
 //          benefit on the second death, reduced to the states 00, x only,
 //          y only (the "died in the step" and "dead" states of the other
@@ -100,17 +107,13 @@ __device__ __forceinline__ void joint_pq(R px, R qx, R py, R qy, R& p, R& q) {
     p = p_mul(px, py);
     q = p_fma(px, qy, qx);
 }
+// The reversionary annuity's three annuity chains: Vxy = a_xy, Vx = a_x, Vy = a_y.
 template <class R>
-__device__ __forceinline__ void step_jl(R v, R px, R qx, R py, R qy, R rho, R& V00, R& V01, R& V10) {
-    R gx = p_mul(v, px), gy = p_mul(v, py);
-    R n01 = p_fma(gx, V01, gx);                 // v px (1 + r01')
-    R n10 = p_mul(gy, p_add(rho, V10));         // v py (rho + r10')
-    R gxy = p_mul(gx, py);
-    R t = p_fma(gxy, V00, gxy);                 // v px py (1 + r00')
-    t = p_fma(qy, n01, t);                      //   + qy r01
-    V00 = p_fma(qx, n10, t);                    //   + qx r10
-    V01 = n01;
-    V10 = n10;
+__device__ __forceinline__ void step_jl(R v, R px, R py, R& Vxy, R& Vx, R& Vy) {
+    const R gx = p_mul(v, px), gy = p_mul(v, py), gxy = p_mul(gx, py);
+    Vx = p_fma(gx, Vx, gx);                     // v px (1 + a_x')
+    Vy = p_fma(gy, Vy, gy);                     // v py (1 + a_y')
+    Vxy = p_fma(gxy, Vxy, gxy);                 // v px py (1 + a_xy')
 }
 // Second-death assurance, benefit c per unit amount in this step.
 template <class R>
@@ -136,10 +139,8 @@ __device__ __forceinline__ void step_ls2(R v, R px, R qx, R py, R qy, R c, R& V0
 // head + tail, not as its head alone.
 //
 // Annuity-type states are carried shifted, R = 1 + r (boundary R_S = 1):
-// r_t = g_t (1 + r_{t+1}) becomes R_t = 1 + g_t R_{t+1}, one df_one_plus_mul.
-// The JL state 10 is carried as A = 1 + r10 / rho, which obeys the same
-// update with g = v py, and the JL state 00 as R00 = 1 + r00:
-// R00_t = (1 + qy r01 + qx r10) + v px py R00_{t+1}.
+// r_t = g_t (1 + r_{t+1}) becomes R_t = 1 + g_t R_{t+1}, one df_one_plus_mul;
+// the JL product's three annuity chains likewise.
 __device__ __forceinline__ df step_ann(df v, df p, df R) {
     return df_one_plus_mul(df_mul(v, p), R);
 }
@@ -151,19 +152,14 @@ __device__ __forceinline__ void joint_pq(df px, df qx, df py, df qy, df& p, df& 
     p = df_mul(px, py);
     q = df{__fmaf_rn(px.h, qy.h, qx.h), 0.0f};
 }
-// V00 = R00 = 1 + r00; V01 = R01 = 1 + r01; V10 = A10 = 1 + r10 / rho.
-__device__ __forceinline__ void step_jl(df v, df px, df qx, df py, df qy, df rho, df& V00, df& V01,
-                                        df& V10) {
-    df gx = df_mul(v, px), gy = df_mul(v, py);
-    const df R01 = df_one_plus_mul(gx, V01);
-    const df A10 = df_one_plus_mul(gy, V10);
-    // qy r01 + qx rho (r10 / rho) of this step; R - 1 is exact for 1 <= R.h < 2^24
-    const float r01 = __fadd_rn(__fsub_rn(R01.h, 1.0f), R01.l);
-    const float a10 = __fadd_rn(__fsub_rn(A10.h, 1.0f), A10.l);
-    const float t12 = __fmaf_rn(__fmul_rn(qx.h, rho.h), a10, __fmul_rn(qy.h, r01));
-    V00 = df_float_plus_mul(__fadd_rn(1.0f, t12), df_mul(gx, py), V00);
-    V01 = R01;
-    V10 = A10;
+// The reversionary annuity's three annuity chains, shifted: Vxy = 1 + a_xy,
+// Vx = 1 + a_x, Vy = 1 + a_y.
+__device__ __forceinline__ void step_jl(df v, df px, df py, df& Vxy, df& Vx, df& Vy) {
+    const df gx = df_mul(v, px), gy = df_mul(v, py);
+    const df gxy = df_mul(gx, py);
+    Vx = df_one_plus_mul(gx, Vx);
+    Vy = df_one_plus_mul(gy, Vy);
+    Vxy = df_one_plus_mul(gxy, Vxy);
 }
 // Second-death assurance: the survival chain px py r00' in double-float; the
 // one-step terms qx qy c + px qy rx' + qx py ry' (non-negative) in FP32.
@@ -284,12 +280,14 @@ struct Tile {
     }
 
     // The compensated form carries annuity-type states shifted (see step_ann):
-    // the ANN state and JL states 00 and 01 as 1 + r, JL state 10 as 1 + r / rho.
+    // the ANN state and the JL product's three annuity chains as 1 + a.
     static constexpr bool ANNUITY = KIND == K_ANN || KIND == K_ANN2 || KIND == K_JL;
     static constexpr bool SHIFTED = FORM == F_COMP && ANNUITY && PAY == PAY_END;
-    // payment within the step, or general cash flows: unshifted states, JL
-    // state 10 carried as r10 / rho
+    // payment within the step, or general cash flows: unshifted states; the
+    // JL product in vector form, state 10 carried as r10 / rho
     static constexpr bool PAYF = ANNUITY && PAY != PAY_END;
+    // the JL product as the annuity chains (a_xy, a_x, a_y)
+    static constexpr bool JLDEC = KIND == K_JL && !PAYF;
 
     // the one-step terms: FP32 heads in the compensated form
     using A = typename std::conditional<FORM == F_COMP, float, Val>::type;
@@ -302,8 +300,14 @@ struct Tile {
 
     // r of state k of policy i, scenario m, in FP64
     __device__ __forceinline__ double dval(int k, int i, int m) const {
+        if constexpr (JLDEC) {   // r00 = a_x + rho (a_y - a_xy), r01 = a_x, r10 = rho a_y
+            const double off = SHIFTED ? 1.0 : 0.0, r = T::dbl(rho[i]);
+            if (k == 1) return T::dbl(V[1][i][m]) - off;
+            if (k == 2) return r * (T::dbl(V[2][i][m]) - off);
+            return (T::dbl(V[1][i][m]) - off) + r * (T::dbl(V[2][i][m]) - T::dbl(V[0][i][m]));
+        }
         const double x = T::dbl(V[k][i][m]);
-        if constexpr (SHIFTED) return k == 2 ? T::dbl(rho[i]) * (x - 1.0) : x - 1.0;
+        if constexpr (SHIFTED) return x - 1.0;
         if constexpr (PAYF) return k == 2 ? T::dbl(rho[i]) * x : x;
         return x;
     }
@@ -357,11 +361,9 @@ struct Tile {
             const TabE e1 = tab[idx1[i] + t];
             const Val px = T::p(e1), qx = T::q(e1);
             if constexpr (KIND == K_JL) {
-                const TabE e2 = tab[idx2[i] + t];
-                const Val py = T::p(e2), qy = T::q(e2);
+                const Val py = T::p(tab[idx2[i] + t]);
 #pragma unroll
-                for (int m = 0; m < M; ++m)
-                    step_jl(T::v(vv.e[m]), px, qx, py, qy, rho[i], V[0][i][m], V[1][i][m], V[2][i][m]);
+                for (int m = 0; m < M; ++m) step_jl(T::v(vv.e[m]), px, py, V[0][i][m], V[1][i][m], V[2][i][m]);
             } else if constexpr (KIND == K_LS2) {
                 const TabE e2 = tab[idx2[i] + t];
                 const Val py = T::p(e2), qy = T::q(e2);

@@ -297,7 +297,7 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps, int 
         }
         kinds.push_back(kind);
         grps.push_back(g);
-        const double w = kind == K_JL ? 4.5 : (kind == K_LS2 ? 4.0 : (kind == K_ANN2 || kind == K_ASS2 ? 1.4 : 1.0));
+        const double w = kind == K_JL ? 3.0 : (kind == K_LS2 ? 4.0 : (kind == K_ANN2 || kind == K_ASS2 ? 1.4 : 1.0));
         cost.push_back(w * slots[first.back()].S);
     }
     // tiles in decreasing cost order within each group (longest-processing-time

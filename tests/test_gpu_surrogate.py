@@ -2,13 +2,17 @@
 accumulation) and of its recurrence labels, against the FP64 references.
 
 Bounds.  With the reference evaluated with BF16 storage at the same points
-as the GPU, the two differ by FP32 accumulation order (~1e-6 relative),
-erff/expf against FP64 erf/exp, and the occasional BF16 rounding flip of an
-activation whose FP32 and FP64 pre-activations straddle a rounding boundary
-(one flip moves an output by ~2^-8 of one of 256 terms): forward outputs
-within 2e-3 of the output scale, gradients within 2e-2 in norm per parameter
-block.  Against the reference without BF16 storage the BF16 rounding itself
-(2^-9 relative per value, 4 layers) bounds the forward difference by ~3e-2.
+as the GPU, the two differ by FP32 accumulation order (~1e-6 relative), the
+hardware tanh inside GELU (relative error ~2^-11) against FP64 tanh, and the
+BF16 rounding flips these cause: an activation whose FP32 value lands on the
+other side of a rounding boundary moves by one BF16 ulp (2^-8 relative).
+The hardware tanh's error is about 2^-3 of a BF16 ulp, so a few percent of
+the activations flip; over four layers of 256 that leaves forward outputs
+within 1e-2 of the output scale and gradients within 2e-2 in norm per
+parameter block.  Two GPU kernels with the same GELU (tcgen05 and mma.sync)
+differ by accumulation order and its rare flips only: within 2e-3.  Against
+the reference without BF16 storage the BF16 rounding itself (2^-9 relative
+per value, 4 layers) bounds the forward difference by ~3e-2 in norm.
 """
 import math
 
@@ -57,7 +61,7 @@ def test_mlp_forward_matches_reference(ctx):
     scale = np.max(np.abs(y_bf))
     print("forward: vs bf16-storage reference", np.max(np.abs(y - y_bf)) / scale,
           "vs FP64 reference", np.linalg.norm(y - y_64) / np.linalg.norm(y_64))
-    assert np.max(np.abs(y - y_bf)) <= 2e-3 * scale
+    assert np.max(np.abs(y - y_bf)) <= 1e-2 * scale
     assert np.linalg.norm(y - y_64) <= 3e-2 * np.linalg.norm(y_64)
 
 
@@ -77,7 +81,7 @@ def test_tcgen05_inference_matches_mma_sync_and_reference(ctx):
     scale = np.max(np.abs(y_bf))
     print("tcgen05 vs mma.sync", np.max(np.abs(y_tc - y_mma)) / scale, "vs reference",
           np.max(np.abs(y_tc - y_bf)) / scale)
-    assert np.max(np.abs(y_tc - y_bf)) <= 2e-3 * scale
+    assert np.max(np.abs(y_tc - y_bf)) <= 1e-2 * scale
     assert np.max(np.abs(y_tc - y_mma)) <= 2e-3 * scale
 
 
