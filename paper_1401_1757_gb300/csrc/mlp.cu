@@ -201,8 +201,22 @@ cudaError_t Mlp::ensure(int batch) {
     return cudaSuccess;
 }
 
+cudaError_t Mlp::ensure_infer(int batch) {
+    if (batch <= cap_i) return cudaSuccess;
+    if (Xi) cudaFree(Xi);
+    if (yi) cudaFree(yi);
+    Xi = nullptr;
+    yi = nullptr;
+    cap_i = 0;
+    cudaError_t e = cudaMalloc((void**)&Xi, (size_t)batch * MLP_XW * 2);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&yi, (size_t)batch * 4)) != cudaSuccess) return e;
+    cap_i = batch;
+    return cudaSuccess;
+}
+
 void Mlp::release() {
-    void* ps[] = {params, grads, adam_m, adam_v, wbf, dW1, A4f, X, y, t, dy, sq, loss, wt, part};
+    void* ps[] = {params, grads, adam_m, adam_v, wbf, dW1, A4f, X, y, t, dy, sq, loss, wt, part, Xi, yi};
     for (void* p : ps)
         if (p) cudaFree(p);
     for (int l = 0; l < 4; ++l) {

@@ -40,8 +40,12 @@ struct Mlp {
     float* part = nullptr;          // column-sum partials [cap / 128 + 1][MLP_H]
     __nv_bfloat16* wt = nullptr;    // W_l^T (K-major) BF16 copies for the tcgen05 inference kernel
     bool use_tc = true;             // inference on tcgen05 (else the mma.sync kernels)
+    __nv_bfloat16* Xi = nullptr;    // inference-only features [cap_i][MLP_XW] (tcgen05 path)
+    float* yi = nullptr;            // and outputs [cap_i]
+    int cap_i = 0;
 
     cudaError_t ensure(int batch);
+    cudaError_t ensure_infer(int batch);   // Xi, yi only: the tcgen05 path needs no activation buffers
     void release();
     __nv_bfloat16* wb(int l) const;
     cudaError_t refresh_bf16(cudaStream_t st);

@@ -475,24 +475,34 @@ rsv_status sur_predict(rsv_ctx* c, const SurQuery* q, long long n, double* V, bo
     SurTables T;
     rsv_status st = sur_tables(c, T);
     if (st != RSV_OK) return st;
-    CU(c->mlp.ensure(batch));
+    // the tcgen05 path needs only features and outputs: large batches keep
+    // the feature kernel's dependent loads in flight
+    const bool tc = c->mlp.use_tc;
+    if (tc) {
+        batch = std::max(batch, 1 << 19);
+        CU(c->mlp.ensure_infer(batch));
+    } else {
+        CU(c->mlp.ensure(batch));
+    }
+    __nv_bfloat16* X = tc ? c->mlp.Xi : c->mlp.X;
+    float* y = tc ? c->mlp.yi : c->mlp.y;
     batch = batch / 128 * 128;
     CU(s.d_lnb.ensure((size_t)batch * sizeof(double)));
     for (long long o = 0; o < n; o += batch) {
         const int nb = (int)std::min<long long>(batch, n - o);
         const int nb_pad = (nb + 127) / 128 * 128;
-        if (nb_pad != nb) CU(cudaMemsetAsync(c->mlp.X, 0, (size_t)nb_pad * MLP_XW * 2, c->stream));
-        sur_features_kernel<<<c->sm_count * 4, 256, 0, c->stream>>>(c->d_pols.as<PolSur>(), T, q + o, nb, c->mlp.X,
-                                                                    s.d_lnb.as<double>());
+        if (nb_pad != nb) CU(cudaMemsetAsync(X, 0, (size_t)nb_pad * MLP_XW * 2, c->stream));
+        const int grid = (int)std::min<long long>((nb + 255) / 256, (long long)c->sm_count * 16);
+        sur_features_kernel<<<grid, 256, 0, c->stream>>>(c->d_pols.as<PolSur>(), T, q + o, nb, X,
+                                                         s.d_lnb.as<double>());
         CU(cudaGetLastError());
-        if (c->mlp.use_tc) {
+        if (tc) {
             CU(c->d_ctl.ensure(2 * sizeof(int32_t)));
-            CU(c->mlp.forward_tc(c->mlp.X, nb_pad, c->mlp.y, c->sm_count, c->d_ctl.as<int32_t>() + 1, c->stream));
+            CU(c->mlp.forward_tc(X, nb_pad, y, c->sm_count, c->d_ctl.as<int32_t>() + 1, c->stream));
         } else {
-            CU(c->mlp.forward(c->mlp.X, nb_pad, c->mlp.y, nullptr, c->stream));
+            CU(c->mlp.forward(X, nb_pad, y, nullptr, c->stream));
         }
-        sur_to_reserve_kernel<<<c->sm_count * 4, 256, 0, c->stream>>>(c->mlp.y, s.d_lnb.as<double>(), nb, s.y_mean,
-                                                                      s.y_std, V + o);
+        sur_to_reserve_kernel<<<grid, 256, 0, c->stream>>>(y, s.d_lnb.as<double>(), nb, s.y_mean, s.y_std, V + o);
         CU(cudaGetLastError());
     }
     if (fallback) {
