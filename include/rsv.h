@@ -444,7 +444,7 @@ rsv_status rsv_reserves_noalloc(int device, void *cuda_stream, const rsv_policy 
  * exactly the recurrence (Eq. generalForm) on the forward curve
  * P(t+1|r)/P(t|r), because the reserve is linear in the discount products
  * (Eq. basicReserveSummation).  The surrogate is a perceptron
- * 32 -> 256 -> 256 -> 256 -> 256 -> 1 with exact-erf GELU, BF16 weights and
+ * 32 -> 256 -> 256 -> 256 -> 256 -> 1 with GELU (tanh form), BF16 weights and
  * activations and FP32 accumulation on the tensor cores, FP32 master weights
  * and Adam; it predicts ln(reserve per unit amount) from 16 features (product
  * and state one-hot, ages, reversion, remaining term, rate, ln amount and
