@@ -135,3 +135,30 @@ def test_mlife_errors(ctx):
     with pytest.raises(rsv.RsvError) as e:
         rsv.rsv_compute_mlife(ctx, ass, rsv.RSV_FORM_F64, rsv.RSV_OUT_V0, V0d=V0)
     assert e.value.status == rsv.RSV_E_ARG
+
+
+def test_mlife_empty_and_single_life(ctx):
+    """No policies: the totals are zero.  m = 1 annuity and assurance against
+    the single-life products of the scenario-parallel kernels."""
+    tab = synth.gm_monthly_survival()
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    v = synth.vasicek_paths(40, 1200, seed=8)
+    rsv.rsv_load_scenarios(ctx, v)
+    tot = np.full(40, 7.0)
+    empty = {k: [] for k in ("m", "kind", "k", "term_m", "dead0", "amount")}
+    empty.update(age_m=np.zeros((0, 4), int), table=np.zeros((0, 4), int))
+    rsv.rsv_compute_mlife(ctx, empty, rsv.RSV_FORM_F64, rsv.RSV_OUT_SCEN_TOTAL, scen_total=tot)
+    assert np.all(tot == 0.0)
+    pol = synth.portfolio_mix(40, seed=8)
+    sl = np.isin(pol["product"], (0, 2))
+    pol = synth.take(pol, np.where(sl)[0])
+    n = len(pol["product"])
+    ml = {"m": np.ones(n, int), "kind": (pol["product"] == 2).astype(int), "k": np.ones(n, int),
+          "term_m": pol["term_m"], "age_m": np.stack([pol["age1_m"]] + [0 * pol["age1_m"]] * 3, axis=1),
+          "table": np.zeros((n, 4), int), "dead0": np.zeros(n, int), "amount": pol["amount"]}
+    V0 = np.zeros((n, 40))
+    rsv.rsv_compute_mlife(ctx, ml, rsv.RSV_FORM_F64, rsv.RSV_OUT_V0, V0d=V0)
+    rsv.rsv_load_portfolio(ctx, pol)
+    V1 = np.zeros((n, 40))
+    rsv.rsv_compute_reserves(ctx, rsv.RSV_FORM_F64, rsv.RSV_OUT_V0, V0d=V1)
+    assert np.max(np.abs(V0 - V1) / np.abs(V1)) <= 1e-12

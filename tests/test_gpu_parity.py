@@ -672,3 +672,25 @@ def test_cash_flows_split_launch_host_and_device_outputs(ctx):
     assert np.array_equal(host[level], V_level[level])
     ref, _ = oracle.reserves_batch(pol, tab, v[:20], cf=_schedule_rows(sch, T))
     assert rel_err(host[:, :20], ref, pol["amount"]).max() <= TOL[rsv.RSV_FORM_F32_COMP]
+
+
+@pytest.mark.parametrize("form", [rsv.RSV_FORM_F64, rsv.RSV_FORM_F32_COMP])
+def test_cash_flows_with_horizon(ctx, form):
+    """A horizon truncates the projection (r_h = 0) with varying cash flows as
+    well: the rows beyond it are never read."""
+    tab = synth.gm_monthly_survival()
+    pol = _cf_portfolio(60, 24, seed=25)
+    pol["table2"][:] = 0
+    n, n_scen, T, h = len(pol["product"]), 33, 1200, 300
+    sch = synth.payment_schedules(n, seed=25, annual_share=0.4, escalating_share=0.4, increasing_share=0.2)
+    v = synth.vasicek_paths(n_scen, T, seed=25)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    rsv.rsv_load_schedules(ctx, sch, h)   # rows only as long as the horizon
+    V0 = np.zeros((n, n_scen))
+    rsv.rsv_compute_reserves(ctx, form, rsv.RSV_OUT_V0, horizon=h, V0d=V0)
+    cf = np.zeros((n, T))
+    cf[:, :h] = _schedule_rows(sch, h)
+    ref, _ = oracle.reserves_batch(pol, tab, v, horizon=h, cf=cf)
+    assert rel_err(V0, ref, pol["amount"]).max() <= TOL[form]
