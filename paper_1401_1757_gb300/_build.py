@@ -17,7 +17,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "librsv.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread",
               "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 
 
@@ -65,7 +65,7 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
             print(log)
     if todo or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
+        cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lpthread",
                "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

@@ -105,6 +105,11 @@ struct Layout {
     int max_S = 0;           // longest projection
     bool has_two = false;    // tiles of K_ANN2, K_ASS2 or K_LS2 present
     DevBuf slots, kinds;
+    // host scratch of the rebuild, kept between calls
+    std::vector<PolPrep> h_pp;
+    std::vector<int> h_order, h_bucket, h_first, h_kinds, h_grps, h_to, h_k2;
+    std::vector<double> h_cost;
+    std::vector<SlotRec> h_s2;
 };
 
 // The trained surrogate: target normalisation, the per-bucket fallback map

@@ -7,6 +7,7 @@
 // paper's dynamic OpenMP schedule did, Section 5.1.1), and the scratch of the
 // per-scenario totals.
 #include <algorithm>
+#include <thread>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -177,58 +178,115 @@ namespace {
 
 int table_len(const rsv_ctx* c, int id) { return (int)c->tab[id].size(); }
 
-// Validate every record against the tables and the scenario length and
-// derive its reduced model (Section 3.6.4), steps and boundary.
+// One record against the tables and the scenario length: its reduced model
+// (Section 3.6.4), steps and boundary; on failure the message goes to msg.
+rsv_status prep_one(const rsv_ctx* c, int64_t i, int horizon, int max_steps, PolPrep& q, int& need, int& n_tab,
+                    char (&msg)[160]) {
+    const rsv_policy& r = c->pols[i];
+    ProductModel pm;
+    if (!product_model(r.product, pm) || r.reserved != 0) {
+        snprintf(msg, sizeof msg, "policy %lld: bad product %d", (long long)i, r.product);
+        return RSV_E_ARG;
+    }
+    const bool two = pm.two_life;
+    if (r.table1 < 0 || r.table1 >= kMaxTables || c->tab[r.table1].empty() ||
+        (two && (r.table2 < 0 || r.table2 >= kMaxTables || c->tab[r.table2].empty()))) {
+        snprintf(msg, sizeof msg, "policy %lld: decrement table not loaded", (long long)i);
+        return RSV_E_ARG;
+    }
+    if (r.age1_m < 0 || (two && r.age2_m < 0) || r.term_m < 0) {
+        snprintf(msg, sizeof msg, "policy %lld: negative age or term", (long long)i);
+        return RSV_E_ARG;
+    }
+    if (r.state0 < 0 || r.state0 > (pm.multi_state ? 2 : 0)) {
+        snprintf(msg, sizeof msg, "policy %lld: bad state0 %d", (long long)i, r.state0);
+        return RSV_E_ARG;
+    }
+    if (!std::isfinite(r.amount)) {
+        snprintf(msg, sizeof msg, "policy %lld: amount not finite", (long long)i);
+        return RSV_E_ASSUMPTION;
+    }
+    if (r.product == RSV_JL_REVERSIONARY && !(r.reversion >= 0.0 && r.reversion <= 1.0)) {
+        snprintf(msg, sizeof msg, "policy %lld: reversion outside [0,1]", (long long)i);
+        return RSV_E_ASSUMPTION;
+    }
+    int S = product_steps(r, table_len(c, r.table1), two ? table_len(c, r.table2) : 0);
+    float bnd = pm.bnd;
+    if (horizon > 0 && horizon < S) {
+        S = horizon;
+        bnd = 0.0f;   // truncated projection: r_horizon = 0
+    }
+    if (S > max_steps) {
+        snprintf(msg, sizeof msg, "policy %lld: %d steps but scenarios have %d", (long long)i, S, max_steps);
+        return RSV_E_ASSUMPTION;
+    }
+    const int top = std::max(r.age1_m + S, two ? r.age2_m + S : 0);
+    if (top > kMaxAgeSteps) {
+        snprintf(msg, sizeof msg, "policy %lld: age + steps %d exceeds %d", (long long)i, top, kMaxAgeSteps);
+        return RSV_E_ARG;
+    }
+    need = std::max(need, top);
+    n_tab = std::max(n_tab, std::max(r.table1, two ? r.table2 : 0) + 1);
+    q.kind = pm.kind;
+    q.S = S;
+    q.idx_age1 = r.age1_m;
+    q.idx_age2 = two ? r.age2_m : 0;
+    q.table1 = r.table1;
+    q.table2 = two ? r.table2 : 0;
+    q.state0 = r.state0;
+    q.pol = (int)i;
+    q.bnd = bnd;
+    q.rho = r.product == RSV_JL_REVERSIONARY ? r.reversion : (r.product == RSV_LAST_SURVIVOR ? 1.0 : 0.0);
+    return RSV_OK;
+}
+
+// Validate every record and derive its reduced model, steps and boundary,
+// on several host threads for large portfolios.  The error reported is the
+// first bad record in portfolio order.
 rsv_status prep_policies(rsv_ctx* c, int horizon, int max_steps, std::vector<PolPrep>& out, int& tab_pad,
                          int& n_tab, double& chain_steps) {
     const int64_t n = (int64_t)c->pols.size();
     out.resize(n);
+    struct Part {
+        int need = 1, n_tab = 1;
+        double steps = 0.0;
+        int64_t bad = -1;
+        rsv_status st = RSV_OK;
+        char msg[160] = {0};
+    };
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(hw, 16), n / 16384));
+    std::vector<Part> part(T);
+    auto run = [&](int k) {
+        Part& pr = part[k];
+        const int64_t lo = n * k / T, hi = n * (k + 1) / T;
+        for (int64_t i = lo; i < hi; ++i) {
+            const rsv_status st = prep_one(c, i, horizon, max_steps, out[i], pr.need, pr.n_tab, pr.msg);
+            if (st != RSV_OK) {
+                pr.st = st;
+                pr.bad = i;
+                return;
+            }
+            pr.steps += out[i].S;
+        }
+    };
+    if (T == 1) {
+        run(0);
+    } else {
+        std::vector<std::thread> th;
+        th.reserve(T - 1);
+        for (int k = 1; k < T; ++k) th.emplace_back(run, k);
+        run(0);
+        for (auto& t : th) t.join();
+    }
     int need = 1;
     n_tab = 1;
     chain_steps = 0;
-    for (int64_t i = 0; i < n; ++i) {
-        const rsv_policy& r = c->pols[i];
-        PolPrep& q = out[i];
-        ProductModel pm;
-        if (!product_model(r.product, pm) || r.reserved != 0)
-            return fail(c, RSV_E_ARG, "policy %lld: bad product %d", (long long)i, r.product);
-        const bool two = pm.two_life;
-        if (r.table1 < 0 || r.table1 >= kMaxTables || c->tab[r.table1].empty() ||
-            (two && (r.table2 < 0 || r.table2 >= kMaxTables || c->tab[r.table2].empty())))
-            return fail(c, RSV_E_ARG, "policy %lld: decrement table not loaded", (long long)i);
-        if (r.age1_m < 0 || (two && r.age2_m < 0) || r.term_m < 0)
-            return fail(c, RSV_E_ARG, "policy %lld: negative age or term", (long long)i);
-        if (r.state0 < 0 || r.state0 > (pm.multi_state ? 2 : 0))
-            return fail(c, RSV_E_ARG, "policy %lld: bad state0 %d", (long long)i, r.state0);
-        if (!std::isfinite(r.amount))
-            return fail(c, RSV_E_ASSUMPTION, "policy %lld: amount not finite", (long long)i);
-        if (r.product == RSV_JL_REVERSIONARY && !(r.reversion >= 0.0 && r.reversion <= 1.0))
-            return fail(c, RSV_E_ASSUMPTION, "policy %lld: reversion outside [0,1]", (long long)i);
-        int S = product_steps(r, table_len(c, r.table1), two ? table_len(c, r.table2) : 0);
-        float bnd = pm.bnd;
-        if (horizon > 0 && horizon < S) {
-            S = horizon;
-            bnd = 0.0f;   // truncated projection: r_horizon = 0
-        }
-        if (S > max_steps)
-            return fail(c, RSV_E_ASSUMPTION, "policy %lld: %d steps but scenarios have %d", (long long)i, S,
-                        max_steps);
-        const int top = std::max(r.age1_m + S, two ? r.age2_m + S : 0);
-        if (top > kMaxAgeSteps)
-            return fail(c, RSV_E_ARG, "policy %lld: age + steps %d exceeds %d", (long long)i, top, kMaxAgeSteps);
-        need = std::max(need, top);
-        n_tab = std::max(n_tab, std::max(r.table1, two ? r.table2 : 0) + 1);
-        q.kind = pm.kind;
-        q.S = S;
-        q.idx_age1 = r.age1_m;
-        q.idx_age2 = two ? r.age2_m : 0;
-        q.table1 = r.table1;
-        q.table2 = two ? r.table2 : 0;
-        q.state0 = r.state0;
-        q.pol = (int)i;
-        q.bnd = bnd;
-        q.rho = r.product == RSV_JL_REVERSIONARY ? r.reversion : (r.product == RSV_LAST_SURVIVOR ? 1.0 : 0.0);
-        chain_steps += S;
+    for (const Part& pr : part) {   // parts in portfolio order: the first failure is the earliest record
+        if (pr.st != RSV_OK) return fail(c, pr.st, "%s", pr.msg);
+        need = std::max(need, pr.need);
+        n_tab = std::max(n_tab, pr.n_tab);
+        chain_steps += pr.steps;
     }
     for (int t = 0; t < n_tab; ++t) need = std::max(need, table_len(c, t));
     tab_pad = (need + 31) / 32 * 32;
@@ -245,7 +303,8 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps, int 
     const unsigned long long gen = c->pol_gen * 1000003ull + c->tab_gen * 7919ull + (unsigned)max_steps +
                                    (split ? c->cf_gen * 104729ull : 0ull);
     if (L.P == P && L.P_general == P_general && L.horizon == horizon && L.gen == gen) return RSV_OK;
-    std::vector<PolPrep> pp;
+    // host scratch kept across rebuilds: no allocation or first-touch cost per call
+    std::vector<PolPrep>& pp = L.h_pp;
     int tab_pad, n_tab;
     double cs;
     rsv_status st = prep_policies(c, horizon, max_steps, pp, tab_pad, n_tab, cs);
@@ -254,92 +313,126 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps, int 
 
     // group by (cash-flow group, reduced model), longest projection first:
     // three-state tiles, then joint and single-life annuities, then assurances
-    static const int kind_rank[6] = {3, 5, 0, 2, 4, 1};
+    static const int kind_rank[6] = {3, 5, 0, 2, 4, 1};   // by kind
+    static const int rank_kind[6] = {K_JL, K_LS2, K_ANN2, K_ANN, K_ASS2, K_ASS};
     // stable counting sort on the key: S <= kMaxAgeSteps
-    const int per_group = 6 * (kMaxAgeSteps + 1);
+    const int span = kMaxAgeSteps + 1, per_group = 6 * span;
     const int nb = 2 * per_group;
-    std::vector<int> bucket_start(nb + 1, 0), order(pp.size());
+    std::vector<int>& bucket_start = L.h_bucket;
+    std::vector<int>& order = L.h_order;
+    bucket_start.assign(nb + 1, 0);
+    order.resize(pp.size());
     auto key = [&](const PolPrep& q) {
-        return group(q) * per_group + kind_rank[q.kind] * (kMaxAgeSteps + 1) + (kMaxAgeSteps - q.S);
+        return group(q) * per_group + kind_rank[q.kind] * span + (kMaxAgeSteps - q.S);
     };
     for (const PolPrep& q : pp) ++bucket_start[key(q) + 1];
     for (int b = 0; b < nb; ++b) bucket_start[b + 1] += bucket_start[b];
-    for (size_t i = 0; i < pp.size(); ++i) order[bucket_start[key(pp[i])]++] = (int)i;
-    std::vector<SlotRec> slots;
-    std::vector<int> kinds, grps;
-    std::vector<size_t> first;   // first slot of each tile
-    std::vector<double> cost;
-    size_t i = 0;
-    while (i < order.size()) {
-        const int kind = pp[order[i]].kind, g = group(pp[order[i]]);
-        const int Pg = g ? P_general : P;
-        first.push_back(slots.size());
-        SlotRec last{};
-        for (int k = 0; k < Pg; ++k) {
-            SlotRec s;
-            if (i < order.size() && pp[order[i]].kind == kind && group(pp[order[i]]) == g) {
-                const PolPrep& q = pp[order[i]];
-                s.idx1 = q.table1 * tab_pad + q.idx_age1;
-                s.idx2 = q.table2 * tab_pad + q.idx_age2;
-                s.S = q.S;
-                s.pol = q.pol;
-                s.rho_h = (float)q.rho;
-                s.rho_l = (float)(q.rho - (double)s.rho_h);
-                s.state0 = q.state0;
-                s.bnd = q.bnd;
-                ++i;
-            } else {
-                s = last;       // padding: same shape, never written out
-                s.pol = -1;
-            }
-            last = s;
-            slots.push_back(s);
-        }
-        kinds.push_back(kind);
-        grps.push_back(g);
-        const double w = kind == K_JL ? 3.0 : (kind == K_LS2 ? 4.0 : (kind == K_ANN2 || kind == K_ASS2 ? 1.4 : 1.0));
-        cost.push_back(w * slots[first.back()].S);
+    int run_lo[12], run_hi[12];   // sorted ranges of the (group, kind rank) runs
+    for (int r = 0; r < 12; ++r) {
+        run_lo[r] = bucket_start[r * span];
+        run_hi[r] = bucket_start[(r + 1) * span];
     }
-    // tiles in decreasing cost order within each group (longest-processing-time
-    // first): the tiles of each (group, kind) run are already in decreasing
-    // cost, so merge the runs (ties keep creation order)
+    for (size_t i = 0; i < pp.size(); ++i) order[bucket_start[key(pp[i])]++] = (int)i;
+
+    // Tiles: each run is cut into tiles of Pg policies (the last one padded).
+    // A tile's cost is its model's weight times the S of its first, longest
+    // policy.
+    std::vector<int>& t_start = L.h_first;
+    std::vector<int>& kinds = L.h_kinds;
+    std::vector<int>& grps = L.h_grps;
+    std::vector<double>& cost = L.h_cost;
+    t_start.clear();
+    kinds.clear();
+    grps.clear();
+    cost.clear();
+    int run_t0[13];               // first tile of each run
+    for (int r = 0; r < 12; ++r) {
+        run_t0[r] = (int)kinds.size();
+        const int g = r / 6, kind = rank_kind[r % 6], Pg = g ? P_general : P;
+        if (run_hi[r] > run_lo[r] && Pg <= 0) return fail(c, RSV_E_ARG, "internal: empty tile width");
+        const double w = kind == K_JL ? 3.0 : (kind == K_LS2 ? 4.0 : (kind == K_ANN2 || kind == K_ASS2 ? 1.4 : 1.0));
+        for (int st0 = run_lo[r]; st0 < run_hi[r]; st0 += Pg) {
+            t_start.push_back(st0);
+            kinds.push_back(kind);
+            grps.push_back(g);
+            cost.push_back(w * pp[order[st0]].S);
+        }
+    }
+    run_t0[12] = (int)kinds.size();
     const int n_tiles = (int)kinds.size();
-    std::vector<int> to;
+
+    // tiles in decreasing cost order within each group (longest-processing-time
+    // first): the tiles of each run are already in decreasing cost, so merge
+    // the runs (ties keep creation order)
+    std::vector<int>& to = L.h_to;
+    to.clear();
     to.reserve(n_tiles);
     int grp_tiles[2] = {0, 0};
     for (int g = 0; g < 2; ++g) {
-        std::vector<int> head, end;
-        for (int t = 0; t < n_tiles; ++t) {
-            if (grps[t] != g) continue;
-            if (head.empty() || kinds[t] != kinds[t - 1] || grps[t - 1] != g) {
-                if (!head.empty()) end.push_back(t);
-                head.push_back(t);
-            }
+        int head[6], end[6];
+        for (int r = 0; r < 6; ++r) {
+            head[r] = run_t0[g * 6 + r];
+            end[r] = run_t0[g * 6 + r + 1];
         }
-        if (!head.empty()) {
-            int last_t = -1;
-            for (int t = 0; t < n_tiles; ++t)
-                if (grps[t] == g) last_t = t;
-            end.push_back(last_t + 1);
-        }
-        int cnt = 0;
-        for (int t = 0; t < n_tiles; ++t) cnt += grps[t] == g;
+        const int cnt = run_t0[g * 6 + 6] - run_t0[g * 6];
         for (int out = 0; out < cnt; ++out) {
             int best = -1;
-            for (size_t r = 0; r < head.size(); ++r)
-                if (head[r] < end[r] && (best < 0 || cost[head[r]] > cost[head[best]])) best = (int)r;
+            for (int r = 0; r < 6; ++r)
+                if (head[r] < end[r] && (best < 0 || cost[head[r]] > cost[head[best]])) best = r;
             to.push_back(head[best]++);
         }
         grp_tiles[g] = cnt;
     }
-    std::vector<SlotRec> s2;
-    s2.reserve(slots.size());
-    std::vector<int> k2(n_tiles);
-    for (int t = 0; t < n_tiles; ++t) {
-        const int src = to[t];
-        const size_t n = (size_t)(grps[src] ? P_general : P);
-        k2[t] = kinds[src];
-        s2.insert(s2.end(), slots.begin() + first[src], slots.begin() + first[src] + n);
+
+    // the slots, written in their final places (several host threads for
+    // large portfolios): policy records gathered in sorted order, padding
+    // slots repeating the last policy of their tile with pol = -1
+    std::vector<SlotRec>& s2 = L.h_s2;
+    std::vector<int>& k2 = L.h_k2;
+    const size_t n_slots = (size_t)grp_tiles[0] * P + (size_t)grp_tiles[1] * (P_general > 0 ? P_general : 0);
+    s2.resize(n_slots);
+    k2.resize(n_tiles);
+    auto fill = [&](int f0, int f1) {
+        for (int f = f0; f < f1; ++f) {
+            const int src = to[f], g = grps[src], Pg = g ? P_general : P;
+            const size_t o = f < grp_tiles[0] ? (size_t)f * P
+                                                : (size_t)grp_tiles[0] * P + (size_t)(f - grp_tiles[0]) * P_general;
+            const int r = (g ? 6 : 0) + kind_rank[kinds[src]];
+            const int st0 = t_start[src], len = std::min(Pg, run_hi[r] - st0);
+            k2[f] = kinds[src];
+            for (int k = 0; k < Pg; ++k) {
+                SlotRec sl;
+                if (k < len) {
+                    const PolPrep& q = pp[order[st0 + k]];
+                    sl.idx1 = q.table1 * tab_pad + q.idx_age1;
+                    sl.idx2 = q.table2 * tab_pad + q.idx_age2;
+                    sl.S = q.S;
+                    sl.pol = q.pol;
+                    sl.rho_h = (float)q.rho;
+                    sl.rho_l = (float)(q.rho - (double)sl.rho_h);
+                    sl.state0 = q.state0;
+                    sl.bnd = q.bnd;
+                } else {
+                    sl = s2[o + k - 1];   // padding: same shape, never written out
+                    sl.pol = -1;
+                }
+                s2[o + k] = sl;
+            }
+        }
+    };
+    {
+        const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+        const int T = std::max(1, std::min(std::min(hw, 16), n_tiles / 4096));
+        if (T == 1) {
+            fill(0, n_tiles);
+        } else {
+            std::vector<std::thread> th;
+            th.reserve(T - 1);
+            for (int k = 1; k < T; ++k) th.emplace_back(fill, (int)((long long)n_tiles * k / T),
+                                                        (int)((long long)n_tiles * (k + 1) / T));
+            fill(0, (int)((long long)n_tiles / T));
+            for (auto& t : th) t.join();
+        }
     }
     CU(L.slots.ensure(std::max<size_t>(1, s2.size()) * sizeof(SlotRec)));
     CU(L.kinds.ensure(std::max<size_t>(1, k2.size()) * sizeof(int)));
