@@ -13,8 +13,8 @@
 //            r00 = a_x + rho (a_y - a_xy),  r01 = a_x,  r10 = rho a_y,
 //            a_x = v px (1 + a_x'),  a_y = v py (1 + a_y'),  a_xy = v px py (1 + a_xy'),
 //          which is the recurrence above regrouped (substitute and use
-//          px + qx = 1).  The kernel runs the three annuity chains; the
-//          payment-within-the-step variants keep the vector form.
+//          px + qx = 1), for any payment time within the step and any
+//          cash-flow sequence.  The kernel runs the three annuity chains.
 //   K_LS2  the nine-state two-life assurance model (Section 4.2.3) with the
 //          benefit on the second death, reduced to the states 00, x only,
 //          y only (the "died in the step" and "dead" states of the other
@@ -173,36 +173,15 @@ __device__ __forceinline__ void step_ls2(df v, df px, df qx, df py, df qy, float
     Vy = df_mul(v, df_add_float_pos(df_mul(py, Vy), __fmul_rn(qy.h, c)));
 }
 
-// Annuity-type steps with the payment at the start of the step (f = 0, a = 1)
-// or at the fraction f (a = v^f p^f, the fractional cash-flow term of
-// Eq. generalForm), on unshifted states: r = a + v p r'.  The JL state 10 is
-// carried as r10 / rho: r00 = a0 + v [px py r00' + px qy r01' + qx py rho a10'],
-// r01 = a1 + v px r01', a10 = a2 + v py a10'.
+// Annuity-type steps with the payment at the start of the step (f = 0, a = 1),
+// at the fraction f (a = v^f p^f, the fractional cash-flow term of
+// Eq. generalForm) or with a varying cash flow, on unshifted states:
+// r = a + v p r'.  The JL product runs its three annuity chains this way too.
 template <class R>
 __device__ __forceinline__ R step_ann_a(R a, R g, R V) { return p_fma(g, V, a); }
-template <class R>
-__device__ __forceinline__ void step_jl_a(R v, R px, R qx, R py, R qy, R rho, R a0, R a1, R a2, R& V00, R& V01,
-                                          R& V10) {
-    const R gx = p_mul(v, px), gy = p_mul(v, py);
-    R t = p_fma(p_mul(gx, py), V00, a0);
-    t = p_fma(p_mul(gx, qy), V01, t);
-    t = p_fma(p_mul(p_mul(gy, qx), rho), V10, t);
-    V01 = p_fma(gx, V01, a1);
-    V10 = p_fma(gy, V10, a2);
-    V00 = t;
-}
-// Compensated: the one-step cash-flow and death terms in FP32 (they enter once,
-// weighted by their share), the products along the chain in double-float.
+// Compensated: the one-step cash-flow term in FP32 (it enters once, weighted
+// by its share), the products along the chain in double-float.
 __device__ __forceinline__ df step_ann_a(float a, df g, df V) { return df_float_plus_mul(a, g, V); }
-__device__ __forceinline__ void step_jl_a(df v, df px, df qx, df py, df qy, df rho, float a0, float a1, float a2,
-                                          df& V00, df& V01, df& V10) {
-    const df gx = df_mul(v, px), gy = df_mul(v, py);
-    const float r01 = __fadd_rn(V01.h, V01.l), a10 = __fadd_rn(V10.h, V10.l);
-    const float c = __fmaf_rn(__fmul_rn(__fmul_rn(gy.h, qx.h), rho.h), a10, __fmaf_rn(__fmul_rn(gx.h, qy.h), r01, a0));
-    V00 = df_float_plus_mul(c, df_mul(gx, py), V00);
-    V01 = df_float_plus_mul(a1, gx, V01);
-    V10 = df_float_plus_mul(a2, gy, V10);
-}
 
 // M consecutive scenario-plane elements of one lane, one vector load.
 template <class E, int M>
@@ -283,11 +262,10 @@ struct Tile {
     // the ANN state and the JL product's three annuity chains as 1 + a.
     static constexpr bool ANNUITY = KIND == K_ANN || KIND == K_ANN2 || KIND == K_JL;
     static constexpr bool SHIFTED = FORM == F_COMP && ANNUITY && PAY == PAY_END;
-    // payment within the step, or general cash flows: unshifted states; the
-    // JL product in vector form, state 10 carried as r10 / rho
+    // payment within the step, or general cash flows: unshifted states
     static constexpr bool PAYF = ANNUITY && PAY != PAY_END;
     // the JL product as the annuity chains (a_xy, a_x, a_y)
-    static constexpr bool JLDEC = KIND == K_JL && !PAYF;
+    static constexpr bool JLDEC = KIND == K_JL;
 
     // the one-step terms: FP32 heads in the compensated form
     using A = typename std::conditional<FORM == F_COMP, float, Val>::type;
@@ -308,7 +286,6 @@ struct Tile {
         }
         const double x = T::dbl(V[k][i][m]);
         if constexpr (SHIFTED) return x - 1.0;
-        if constexpr (PAYF) return k == 2 ? T::dbl(rho[i]) * x : x;
         return x;
     }
 
@@ -423,18 +400,26 @@ struct Tile {
 #pragma unroll
             for (int m = 0; m < M; ++m) {
                 const Val v = T::v(vv.e[m]);
-                A vfm = c, pxf = A(1), qxf = A(0), pyf = A(1);
+                A vfm = c, pxf = A(1), pyf = A(1);
                 if constexpr (PAY == PAY_FRACTION || PAY == PAY_END_GENERAL) {
                     vfm = (PAY == PAY_FRACTION ? head(T::v(vf.e[m])) : head(v)) * c;
                     pxf = head(T::p(f1));
-                    qxf = head(T::q(f1));
                     if constexpr (KIND != K_ANN) pyf = head(T::p(f2));
                 }
-                if constexpr (KIND == K_JL) {
-                    const Val py = T::p(e2), qy = T::q(e2);
-                    // W_f c = (pxf + rho qxf pyf, pxf, rho pyf): state 10 divided by rho
-                    const A a0 = vfm * (pxf + head(rho[i]) * qxf * pyf), a1 = vfm * pxf, a2 = vfm * pyf;
-                    step_jl_a(v, px, qx, py, qy, rho[i], a0, a1, a2, V[0][i][m], V[1][i][m], V[2][i][m]);
+                if constexpr (KIND == K_JL) {   // the chains a_x, a_y, a_xy
+                    const Val py = T::p(e2);
+                    const A ax = vfm * pxf, ay = vfm * pyf, axy = ax * pyf;
+                    if constexpr (FORM == F_COMP) {
+                        const df gx = df_mul(v, px);
+                        V[1][i][m] = step_ann_a(ax, gx, V[1][i][m]);
+                        V[2][i][m] = step_ann_a(ay, df_mul(v, py), V[2][i][m]);
+                        V[0][i][m] = step_ann_a(axy, df_mul(gx, py), V[0][i][m]);
+                    } else {
+                        const Val gx = p_mul(v, px);
+                        V[1][i][m] = step_ann_a(ax, gx, V[1][i][m]);
+                        V[2][i][m] = step_ann_a(ay, p_mul(v, py), V[2][i][m]);
+                        V[0][i][m] = step_ann_a(axy, p_mul(gx, py), V[0][i][m]);
+                    }
                 } else {
                     Val p = px;
                     A a = vfm * pxf;
