@@ -554,6 +554,18 @@ enum {
  * network for the network modes), RSV_E_CUDA, RSV_E_NOMEM. */
 rsv_status rsv_surrogate_query(rsv_ctx *ctx, const rsv_query *queries, int64_t n, int32_t how, double *reserve);
 
+/* Self-test of the bounded device-side wait that every kernel's bulk-copy
+ * staging of the decrement tables relies on (failure detection without a GPU
+ * fault): one CTA stages 16 KiB into shared memory with the same bulk-copy and
+ * mbarrier primitives.  never_completes = 0: a normal staging; RSV_OK if the
+ * bytes round-trip.  never_completes = 1: the barrier is told to expect 16
+ * bytes more than are copied, so its phase cannot complete; the bounded wait
+ * runs out (65,536 polls), the kernel records the timeout, lets its copies
+ * land and returns, and the call returns RSV_E_TIMEOUT with the device and any
+ * context on it still usable.  Blocks until done.
+ * Errors: RSV_E_TIMEOUT (as described), RSV_E_NOMEM, RSV_E_CUDA. */
+rsv_status rsv_selftest_bounded_wait(int32_t device, void *cuda_stream, int32_t never_completes);
+
 /* Measured fused multiply-add throughput of `device` in TFLOP/s (2 flop per
  * FMA): FP32 (fp64 = 0) or FP64 (fp64 = 1), from a kernel of independent FMA
  * chains filling every SM, best of five timed launches on `cuda_stream`.  It

@@ -115,6 +115,7 @@ _lib = None
 EXPORTS = ["rsv_create", "rsv_destroy", "rsv_set_stream", "rsv_load_decrements", "rsv_load_portfolio",
            "rsv_load_decrements_fraction", "rsv_load_scenarios_fraction", "rsv_load_cashflows", "rsv_load_schedules",
            "rsv_clear_cashflows", "rsv_compute_mlife", "rsv_surrogate_save", "rsv_surrogate_load",
+           "rsv_selftest_bounded_wait",
            "rsv_load_scenarios", "rsv_compute_reserves", "rsv_compute_nested", "rsv_variant_count", "rsv_variant_name",
            "rsv_tune", "rsv_synchronize", "rsv_last_error", "rsv_last_kernel_ms", "rsv_device_sm_count",
            "rsv_reserves_noalloc", "rsv_mlp_param_count", "rsv_mlp_init", "rsv_mlp_set_params",
@@ -150,6 +151,7 @@ def load_library(path: str = LIB_PATH):
         "rsv_clear_cashflows": ([vp], i32),
         "rsv_compute_mlife": ([vp, vp, i64, C.POINTER(rsv_opts), C.POINTER(rsv_out)], i32),
         "rsv_surrogate_save": ([vp, C.c_char_p], i32),
+        "rsv_selftest_bounded_wait": ([i32, vp, i32], i32),
         "rsv_surrogate_load": ([vp, C.c_char_p], i32),
         "rsv_compute_reserves": ([vp, C.POINTER(rsv_opts), C.POINTER(rsv_out)], i32),
         "rsv_compute_nested": ([vp, C.POINTER(rsv_opts), C.POINTER(rsv_nested_spec), C.POINTER(rsv_nested_out)],
@@ -339,6 +341,12 @@ def rsv_compute_nested(ctx, form: int = RSV_FORM_F32_COMP, *, n_outer: int, n_no
     sp = rsv_nested_spec(n_outer, n_nodes, node_step_m, n_inner, seed, a, b, sigma, r0, mode, batch_outer)
     out = rsv_nested_out(_ptr(L_mean), _ptr(L_q995), _ptr(r_node), _ptr(D0), _ptr(L_all), _ptr(n_fallback))
     _check(ctx, _lib.rsv_compute_nested(ctx, C.byref(o), C.byref(sp), C.byref(out)))
+
+
+def rsv_selftest_bounded_wait(device: int = 0, stream=None, never_completes: bool = False) -> int:
+    """Run the bounded-wait self-test; returns the status code (RSV_OK or RSV_E_TIMEOUT)."""
+    return load_library().rsv_selftest_bounded_wait(device, getattr(stream, "cuda_stream", stream),
+                                                    1 if never_completes else 0)
 
 
 def rsv_probe_fma_peak(device: int = 0, stream=None, fp64: bool = False) -> float:

@@ -694,3 +694,19 @@ def test_cash_flows_with_horizon(ctx, form):
     cf[:, :h] = _schedule_rows(sch, h)
     ref, _ = oracle.reserves_batch(pol, tab, v, horizon=h, cf=cf)
     assert rel_err(V0, ref, pol["amount"]).max() <= TOL[form]
+
+
+def test_bounded_wait_times_out_and_the_context_survives(ctx):
+    """Failure detection without a GPU fault: a staging wait whose barrier can
+    never complete runs out, the kernel reports RSV_E_TIMEOUT and returns, and
+    the same device and context keep working."""
+    stream = torch.cuda.current_stream()
+    assert rsv.rsv_selftest_bounded_wait(0, stream, never_completes=False) == rsv.RSV_OK
+    assert rsv.rsv_selftest_bounded_wait(0, stream, never_completes=True) == rsv.RSV_E_TIMEOUT
+    assert rsv.rsv_selftest_bounded_wait(0, stream, never_completes=False) == rsv.RSV_OK
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_single_life(50)
+    v = synth.vasicek_paths(40, 720, seed=1)
+    V0, _ = run(ctx, pol, tab, v, rsv.RSV_FORM_F64)
+    ref, _ = oracle.reserves_batch(pol, tab, v)
+    assert rel_err(V0, ref, pol["amount"]).max() <= 1e-12
