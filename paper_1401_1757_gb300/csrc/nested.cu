@@ -73,23 +73,76 @@ __device__ __forceinline__ double vasicek_path(const VasStep& s, uint64_t seed, 
     return r;
 }
 
+// Outer paths, one warp each.  The draws of a step depend only on its
+// counter, so the lanes take 32 consecutive steps at once; the rate update
+// r_{t+1} = e r_t + c_t (c_t = b (1 - e) + l11 z1_t) is affine with a common
+// multiplier, so a warp scan of the maps gives every lane the rate at the
+// start of its step, and a product scan the discount to its end.  The same
+// path as the serial recursion up to the order of rounding.
 __global__ void outer_paths_kernel(VasStep s, uint64_t seed, int n_outer, int n_nodes, int node_step, double r0,
                                    double* __restrict__ r_node, double* __restrict__ d0) {
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= n_outer) return;
-    r_node[(size_t)o * n_nodes] = r0;
-    d0[(size_t)o * n_nodes] = 1.0;
-    int next = 1;
-    double D = 1.0;
-    vasicek_path(s, seed, (uint32_t)o, 0u, 2u << 24, r0, (n_nodes - 1) * node_step,
-                 [&](int t, double v, double r_after) {
-                     D *= v;
-                     if (t + 1 == next * node_step) {
-                         r_node[(size_t)o * n_nodes + next] = r_after;
-                         d0[(size_t)o * n_nodes + next] = D;
-                         ++next;
-                     }
-                 });
+    const int lane = threadIdx.x & 31;
+    const int o = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (o >= n_outer) return;   // whole warps leave together
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const double inv32 = 2.3283064365386963e-10;   // 2^-32
+    const int n_steps = (n_nodes - 1) * node_step;
+    if (lane == 0) {
+        r_node[(size_t)o * n_nodes] = r0;
+        d0[(size_t)o * n_nodes] = 1.0;
+    }
+    double r = r0, D = 1.0;   // at the start of the block of 32 steps
+    for (int t0 = 0; t0 < n_steps; t0 += 32) {
+        const int t = t0 + lane;
+        const bool live = t < n_steps;
+        double z1 = 0.0, z2 = 0.0;
+        if (live) {   // the serial generator's draw for step t
+            uint32_t w[4];
+            philox4x32_10((uint32_t)(t >> 1), (uint32_t)o, 0u, 2u << 24, k0, k1, w);
+            const int h = t & 1;
+            const double u1 = ((double)w[2 * h] + 0.5) * inv32;
+            const double u2 = ((double)w[2 * h + 1] + 0.5) * inv32;
+            const double R = sqrt(-2.0 * log(u1));
+            double sn, cs;
+            sincospi(2.0 * u2, &sn, &cs);
+            z1 = R * cs;
+            z2 = R * sn;
+        }
+        // inclusive scan of the maps x -> A x + B over the lanes: A = e^(lane+1)
+        double A = s.e, B = live ? s.b * (1.0 - s.e) + s.l11 * z1 : 0.0;
+        if (!live) A = 1.0;   // identity past the end
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const double Au = __shfl_up_sync(0xffffffffu, A, d), Bu = __shfl_up_sync(0xffffffffu, B, d);
+            if (lane >= d) {   // this map after the lower lanes' composition
+                B = A * Bu + B;
+                A = A * Au;
+            }
+        }
+        // the rate at the start of step t: the exclusive prefix applied to r
+        double Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+        if (lane == 0) {
+            Ae = 1.0;
+            Be = 0.0;
+        }
+        const double rt = Ae * r + Be;
+        const double I = s.b * s.dt + (rt - s.b) * s.k1 + s.l21 * z1 + s.l22 * z2;
+        double v = live ? exp(-I) : 1.0;
+        // inclusive product scan of the discount factors
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const double vu = __shfl_up_sync(0xffffffffu, v, d);
+            if (lane >= d) v *= vu;
+        }
+        const double r_after = A * r + B, D_after = D * v;
+        if (live && (t + 1) % node_step == 0) {
+            const int nd = (t + 1) / node_step;
+            r_node[(size_t)o * n_nodes + nd] = r_after;
+            d0[(size_t)o * n_nodes + nd] = D_after;
+        }
+        r = __shfl_sync(0xffffffffu, r_after, 31);
+        D = __shfl_sync(0xffffffffu, D_after, 31);
+    }
 }
 
 template <class VE>
@@ -315,7 +368,7 @@ cudaError_t launch_nested(int form, const NestedArgs& a, int sm_count, size_t sm
 
 cudaError_t launch_outer_paths(const VasStep& s, uint64_t seed, int n_outer, int n_nodes, int node_step, double r0,
                                double* r_node, double* d0, cudaStream_t st) {
-    outer_paths_kernel<<<(n_outer + 63) / 64, 64, 0, st>>>(s, seed, n_outer, n_nodes, node_step, r0, r_node, d0);
+    outer_paths_kernel<<<(n_outer + 3) / 4, 128, 0, st>>>(s, seed, n_outer, n_nodes, node_step, r0, r_node, d0);
     return cudaGetLastError();
 }
 
