@@ -191,25 +191,59 @@ __global__ void sur_label_kernel(const PolSur* __restrict__ pols, const SurTable
     }
 }
 
+// The same reserve in the compensated form of the valuation kernels
+// (double-float chains, shifted annuity states, the reversionary annuity as
+// three annuity chains): the FP32 pipes instead of the FP64 one, to about
+// 1e-8, far inside the surrogate's tolerance.  vc: the discount factors as
+// hi/lo pairs; tab: the compensated decrement entries (p_hi, p_lo, q_hi, q_lo).
+__device__ __forceinline__ double sur_recurrence_df(const PolSur& P, const float4* __restrict__ tab, int tab_pad,
+                                                    const SurQuery& Q, const float2* vc) {
+    const int Sn = P.S - Q.m;
+    const float4* tx = tab + (size_t)P.tab1 * tab_pad + P.age1 + Q.m;
+    if (P.product == RSV_SL_ANNUITY) {
+        df R{1.0f, 0.0f};
+        for (int t = Sn - 1; t >= 0; --t) R = step_ann(df{vc[t].x, vc[t].y}, df{tx[t].x, tx[t].y}, R);
+        return df_to_double(R) - 1.0;
+    }
+    if (P.product == RSV_JL_REVERSIONARY) {
+        const float4* ty = tab + (size_t)P.tab2 * tab_pad + P.age2 + Q.m;
+        df Rxy{1.0f, 0.0f}, Rx{1.0f, 0.0f}, Ry{1.0f, 0.0f};
+        for (int t = Sn - 1; t >= 0; --t)
+            step_jl(df{vc[t].x, vc[t].y}, df{tx[t].x, tx[t].y}, df{ty[t].x, ty[t].y}, Rxy, Rx, Ry);
+        const double ax = df_to_double(Rx) - 1.0;
+        if (Q.state == 1) return ax;
+        if (Q.state == 2) return P.rho * (df_to_double(Ry) - 1.0);
+        return ax + P.rho * (df_to_double(Ry) - df_to_double(Rxy));
+    }
+    df V{P.product == RSV_ENDOWMENT ? 1.0f : 0.0f, 0.0f};   // term assurance or endowment
+    for (int t = Sn - 1; t >= 0; --t)
+        V = step_ass(df{vc[t].x, vc[t].y}, df{tx[t].x, tx[t].y}, df{tx[t].z, tx[t].w}, V);
+    return df_to_double(V);
+}
+
 // The fallback of the nested valuation: the queries of one (outer path, node)
 // share its short rate, so each block builds that curve once in shared memory
-// (Lmax months) and values the segment's flagged queries from it.
-__global__ void sur_fallback_nodes_kernel(const PolSur* __restrict__ pols, const SurTables T,
+// (Lmax months, FP64 then split hi/lo) and values the segment's flagged
+// queries from it in the compensated form.
+__global__ void sur_fallback_nodes_kernel(const PolSur* __restrict__ pols, const float4* __restrict__ tab,
+                                          int tab_pad, const double2* __restrict__ curve,
                                           const SurQuery* __restrict__ qs, const long long* __restrict__ seg, int Lmax,
                                           const unsigned char* __restrict__ flag, double* __restrict__ V) {
-    extern __shared__ double vcur[];
+    extern __shared__ float2 vcur[];
     const long long b = seg[blockIdx.x], e = seg[blockIdx.x + 1];
     if (b == e) return;
     const double r = qs[b].r;
     for (int t = threadIdx.x; t < Lmax; t += blockDim.x) {
-        const double2 dc = T.curve[t];
-        vcur[t] = exp(dc.x - dc.y * r);
+        const double2 dc = curve[t];
+        const double x = exp(dc.x - dc.y * r);
+        const float h = __double2float_rn(x);
+        vcur[t] = make_float2(h, __double2float_rn(x - (double)h));
     }
     __syncthreads();
     for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
         const SurQuery Q = qs[i];
         if (Q.state < 0 || !flag[Q.bucket]) continue;
-        V[i] = sur_recurrence(pols[Q.pol], T, Q, [&](int t) { return vcur[t]; });
+        V[i] = sur_recurrence_df(pols[Q.pol], tab, tab_pad, Q, vcur);
     }
 }
 
@@ -630,8 +664,11 @@ rsv_status sur_value_queries(rsv_ctx* c, const rsv_query* dq, long long n, const
     if (st != RSV_OK) return st;
     SurTables T;
     if ((st = sur_tables(c, T)) != RSV_OK) return st;
-    sur_fallback_nodes_kernel<<<n_seg, 256, (size_t)Lmax * sizeof(double), c->stream>>>(
-        c->d_pols.as<PolSur>(), T, q, seg, Lmax, s.d_flag.as<unsigned char>(), V);
+    size_t smem_c;
+    if ((st = build_tables(c, F_COMP, smem_c)) != RSV_OK) return st;   // the compensated entries, same padding
+    sur_fallback_nodes_kernel<<<n_seg, 256, (size_t)Lmax * sizeof(float2), c->stream>>>(
+        c->d_pols.as<PolSur>(), c->d_tab[F_COMP].as<float4>(), c->tab_pad_of[F_COMP], T.curve, q, seg, Lmax,
+        s.d_flag.as<unsigned char>(), V);
     CU(cudaGetLastError());
     long long cnt[2] = {0, 0};
     CU(cudaMemcpyAsync(cnt, s.d_err.p, 16, cudaMemcpyDeviceToHost, c->stream));
