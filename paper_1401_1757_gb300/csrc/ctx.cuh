@@ -200,7 +200,12 @@ inline rsv_status fail(rsv_ctx* c, rsv_status st, const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
-    if (c) c->err = buf;
+    if (c) {
+        try {
+            c->err = buf;
+        } catch (...) {   // no room for the message: the status still reports the failure
+        }
+    }
     return st;
 }
 

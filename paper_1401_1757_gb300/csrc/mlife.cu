@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "abi_guard.cuh"
 
 namespace rsv {
 namespace {
@@ -165,7 +166,7 @@ cudaError_t launch_form(int m, const MlArgs& a, int sm_count, size_t smem, cudaS
 using namespace rsv;
 
 extern "C" rsv_status rsv_compute_mlife(rsv_ctx* c, const rsv_mlife_policy* pols, int64_t n, const rsv_opts* o,
-                                        rsv_out* out) {
+                                        rsv_out* out) try {
     if (!c) return RSV_E_ARG;
     if (!o || !out || n < 0 || n > 0x7fffffffLL || (n > 0 && !pols)) return fail(c, RSV_E_ARG, "bad m-life arguments");
     if (o->form < F_F64 || o->form > F_COMP) return fail(c, RSV_E_ARG, "bad form %d", o->form);
@@ -320,4 +321,6 @@ extern "C" rsv_status rsv_compute_mlife(rsv_ctx* c, const rsv_mlife_policy* pols
         return rsv_synchronize(c);
     }
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }

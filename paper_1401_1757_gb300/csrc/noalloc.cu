@@ -28,6 +28,7 @@
 #include <mutex>
 
 #include "rsv.h"
+#include "abi_guard.cuh"
 #include "recur_kernel.cuh"
 
 namespace rsv {
@@ -234,7 +235,7 @@ using namespace rsv;
 
 extern "C" rsv_status rsv_reserves_noalloc(int device, void* cuda_stream, const rsv_policy* pols, int32_t n_pol,
                                            const double* p_monthly, int32_t n_ages, const double* v, int32_t n_scen,
-                                           int32_t n_steps, double* V0, double* scen_total) {
+                                           int32_t n_steps, double* V0, double* scen_total) try {
     if (device < 0 || device >= kMaxDevices || n_pol < 0 || (n_pol > 0 && (!pols || !V0)) || !p_monthly ||
         n_ages < 1 || n_ages > kTabEntries || !v || n_scen < 1 || n_steps < 1)
         return RSV_E_ARG;
@@ -275,4 +276,6 @@ extern "C" rsv_status rsv_reserves_noalloc(int device, void* cuda_stream, const 
     if (ctl[CTL_STATUS] == NA_BAD_INPUT) return RSV_E_ASSUMPTION;
     if (ctl[CTL_BAD] > 0) return RSV_E_ARG;
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(nullptr);
 }

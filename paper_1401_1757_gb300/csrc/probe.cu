@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "rsv.h"
+#include "abi_guard.cuh"
 #include "rsv_device.cuh"
 
 namespace {
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(128) wait_selftest_kernel(const uint4* __restr
 
 }  // namespace
 
-extern "C" rsv_status rsv_selftest_bounded_wait(int32_t device, void* cuda_stream, int32_t never_completes) {
+extern "C" rsv_status rsv_selftest_bounded_wait(int32_t device, void* cuda_stream, int32_t never_completes) try {
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (cudaSetDevice(device) != cudaSuccess) return RSV_E_CUDA;
     constexpr int n16 = 1024;   // 16 KiB
@@ -148,10 +149,14 @@ extern "C" rsv_status rsv_selftest_bounded_wait(int32_t device, void* cuda_strea
     cudaFree(dst);
     cudaFree(status);
     return rc;
+} catch (...) {
+    return rsv::host_error(nullptr);
 }
 
-extern "C" rsv_status rsv_probe_fma_peak(int32_t device, void* cuda_stream, int32_t fp64, double* tflops) {
+extern "C" rsv_status rsv_probe_fma_peak(int32_t device, void* cuda_stream, int32_t fp64, double* tflops) try {
     if (!tflops) return RSV_E_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     return fp64 ? probe<double>(device, st, tflops) : probe<float>(device, st, tflops);
+} catch (...) {
+    return rsv::host_error(nullptr);
 }

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "rsv.h"
+#include "abi_guard.cuh"
 #include "ctx.cuh"
 #include "nested.cuh"
 #include "scan.cuh"
@@ -178,6 +179,27 @@ namespace {
 
 int table_len(const rsv_ctx* c, int id) { return (int)c->tab[id].size(); }
 
+// Run part(k) for k = 0 .. T-1, on T - 1 helper threads and this one; the
+// parts whose thread cannot start run here.
+template <class F>
+void run_parts(int T, F&& part) {
+    std::vector<std::thread> th;
+    int started = 1;
+    if (T > 1) {
+        try {
+            th.reserve(T - 1);
+            for (int k = 1; k < T; ++k) {
+                th.emplace_back(part, k);
+                ++started;
+            }
+        } catch (...) {   // no more threads: the rest runs serially below
+        }
+    }
+    part(0);
+    for (int k = started; k < T; ++k) part(k);
+    for (auto& t : th) t.join();
+}
+
 // One record against the tables and the scenario length: its reduced model
 // (Section 3.6.4), steps and boundary; on failure the message goes to msg.
 rsv_status prep_one(const rsv_ctx* c, int64_t i, int horizon, int max_steps, PolPrep& q, int& need, int& n_tab,
@@ -270,15 +292,7 @@ rsv_status prep_policies(rsv_ctx* c, int horizon, int max_steps, std::vector<Pol
             pr.steps += out[i].S;
         }
     };
-    if (T == 1) {
-        run(0);
-    } else {
-        std::vector<std::thread> th;
-        th.reserve(T - 1);
-        for (int k = 1; k < T; ++k) th.emplace_back(run, k);
-        run(0);
-        for (auto& t : th) t.join();
-    }
+    run_parts(T, run);
     int need = 1;
     n_tab = 1;
     chain_steps = 0;
@@ -423,16 +437,9 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps, int 
     {
         const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
         const int T = std::max(1, std::min(std::min(hw, 16), n_tiles / 4096));
-        if (T == 1) {
-            fill(0, n_tiles);
-        } else {
-            std::vector<std::thread> th;
-            th.reserve(T - 1);
-            for (int k = 1; k < T; ++k) th.emplace_back(fill, (int)((long long)n_tiles * k / T),
-                                                        (int)((long long)n_tiles * (k + 1) / T));
-            fill(0, (int)((long long)n_tiles / T));
-            for (auto& t : th) t.join();
-        }
+        run_parts(T, [&](int k) {
+            fill((int)((long long)n_tiles * k / T), (int)((long long)n_tiles * (k + 1) / T));
+        });
     }
     CU(L.slots.ensure(std::max<size_t>(1, s2.size()) * sizeof(SlotRec)));
     CU(L.kinds.ensure(std::max<size_t>(1, k2.size()) * sizeof(int)));
@@ -490,6 +497,8 @@ void write_entries(int form, const std::vector<double>* src, int n_tab, int pad,
 
 // Decrement tables in the entry format of `form`, zero survival past each
 // table's end, staged per CTA.
+rsv_status rsv::fail_msg(rsv_ctx* c, rsv_status st, const char* msg) noexcept { return fail(c, st, "%s", msg); }
+
 rsv_status rsv::build_tables(rsv_ctx* c, int form, size_t& smem) {
     return stage_tables(c, form, c->lay.tab_pad, c->lay.n_tab, smem);
 }
@@ -1044,7 +1053,7 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
 
 extern "C" {
 
-rsv_status rsv_create(rsv_ctx** out, int device, void* cuda_stream) {
+rsv_status rsv_create(rsv_ctx** out, int device, void* cuda_stream) try {
     if (!out) return RSV_E_ARG;
     *out = nullptr;
     rsv_ctx* c = new (std::nothrow) rsv_ctx();
@@ -1061,9 +1070,11 @@ rsv_status rsv_create(rsv_ctx** out, int device, void* cuda_stream) {
     }
     *out = c;
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(nullptr);
 }
 
-rsv_status rsv_destroy(rsv_ctx* c) {
+rsv_status rsv_destroy(rsv_ctx* c) try {
     if (!c) return RSV_OK;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
@@ -1087,15 +1098,19 @@ rsv_status rsv_destroy(rsv_ctx* c) {
     }
     delete c;
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_set_stream(rsv_ctx* c, void* cuda_stream) {
+rsv_status rsv_set_stream(rsv_ctx* c, void* cuda_stream) try {
     if (!c) return RSV_E_ARG;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_load_decrements(rsv_ctx* c, int32_t table_id, const double* p, int32_t n) {
+rsv_status rsv_load_decrements(rsv_ctx* c, int32_t table_id, const double* p, int32_t n) try {
     if (!c) return RSV_E_ARG;
     if (table_id < 0 || table_id >= kMaxTables) return fail(c, RSV_E_ARG, "table id %d outside [0,8)", table_id);
     if (!p || n < 1 || n > kMaxAgeSteps) return fail(c, RSV_E_ARG, "bad table pointer or length %d", n);
@@ -1105,9 +1120,11 @@ rsv_status rsv_load_decrements(rsv_ctx* c, int32_t table_id, const double* p, in
     c->tab[table_id].assign(p, p + n);
     ++c->tab_gen;
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_load_decrements_fraction(rsv_ctx* c, int32_t table_id, const double* p, int32_t n) {
+rsv_status rsv_load_decrements_fraction(rsv_ctx* c, int32_t table_id, const double* p, int32_t n) try {
     if (!c) return RSV_E_ARG;
     if (table_id < 0 || table_id >= kMaxTables) return fail(c, RSV_E_ARG, "table id %d outside [0,8)", table_id);
     if (!p || n < 1 || n > kMaxAgeSteps) return fail(c, RSV_E_ARG, "bad table pointer or length %d", n);
@@ -1118,9 +1135,11 @@ rsv_status rsv_load_decrements_fraction(rsv_ctx* c, int32_t table_id, const doub
     c->tabf[table_id].assign(p, p + n);
     ++c->tabf_gen;
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_load_scenarios_fraction(rsv_ctx* c, const double* v, int32_t n_scen, int32_t n_steps, int32_t layout) {
+rsv_status rsv_load_scenarios_fraction(rsv_ctx* c, const double* v, int32_t n_scen, int32_t n_steps, int32_t layout) try {
     if (!c) return RSV_E_ARG;
     if (!v || n_scen < 1 || n_steps < 1 || (layout != 0 && layout != 1))
         return fail(c, RSV_E_ARG, "bad fractional scenario arguments");
@@ -1145,6 +1164,8 @@ rsv_status rsv_load_scenarios_fraction(rsv_ctx* c, const double* v, int32_t n_sc
     c->vf_scen = n_scen;
     c->vf_steps = n_steps;
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
 // The level flags of freshly written rows (device FP64) and the new generation.
@@ -1162,7 +1183,7 @@ static rsv_status finish_cashflows(rsv_ctx* c, int64_t n_pol, int32_t n_steps) {
     return RSV_OK;
 }
 
-rsv_status rsv_load_cashflows(rsv_ctx* c, const double* cf, int64_t n_pol, int32_t n_steps) {
+rsv_status rsv_load_cashflows(rsv_ctx* c, const double* cf, int64_t n_pol, int32_t n_steps) try {
     if (!c) return RSV_E_ARG;
     if (!cf || n_pol < 1 || n_steps < 1 || n_pol * (int64_t)n_steps > 0x7fffffffLL)
         return fail(c, RSV_E_ARG, "bad cash-flow arguments");
@@ -1179,9 +1200,11 @@ rsv_status rsv_load_cashflows(rsv_ctx* c, const double* cf, int64_t n_pol, int32
     cf_to_f32_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(c->d_cf64.as<double>(), c->d_cf32.as<float>(), n);
     CU(cudaGetLastError());
     return finish_cashflows(c, n_pol, n_steps);
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_load_schedules(rsv_ctx* c, const rsv_schedule* sch, int64_t n_pol, int32_t n_steps) {
+rsv_status rsv_load_schedules(rsv_ctx* c, const rsv_schedule* sch, int64_t n_pol, int32_t n_steps) try {
     if (!c) return RSV_E_ARG;
     if (!sch || n_pol < 1 || n_steps < 1 || n_pol * (int64_t)n_steps > 0x7fffffffLL)
         return fail(c, RSV_E_ARG, "bad schedule arguments");
@@ -1204,27 +1227,33 @@ rsv_status rsv_load_schedules(rsv_ctx* c, const rsv_schedule* sch, int64_t n_pol
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(c->stream));   // the staged schedules are read before d_vstage is reused
     return finish_cashflows(c, n_pol, n_steps);
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_clear_cashflows(rsv_ctx* c) {
+rsv_status rsv_clear_cashflows(rsv_ctx* c) try {
     if (!c) return RSV_E_ARG;
     c->cf_pol = 0;
     c->cf_steps = 0;
     c->cf_level.clear();
     ++c->cf_gen;
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_load_portfolio(rsv_ctx* c, const rsv_policy* pols, int64_t n) {
+rsv_status rsv_load_portfolio(rsv_ctx* c, const rsv_policy* pols, int64_t n) try {
     if (!c) return RSV_E_ARG;
     if (n < 0 || n > 0x7fffffffLL || (n > 0 && !pols)) return fail(c, RSV_E_ARG, "bad portfolio size %lld", (long long)n);
     c->pols.assign(pols, pols + n);
     ++c->pol_gen;
     c->amount_dirty = true;
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_load_scenarios(rsv_ctx* c, const double* v, int32_t n_scen, int32_t n_steps, int32_t layout) {
+rsv_status rsv_load_scenarios(rsv_ctx* c, const double* v, int32_t n_scen, int32_t n_steps, int32_t layout) try {
     if (!c) return RSV_E_ARG;
     if (!v || n_scen < 1 || n_steps < 1 || (layout != 0 && layout != 1))
         return fail(c, RSV_E_ARG, "bad scenario arguments");
@@ -1251,20 +1280,26 @@ rsv_status rsv_load_scenarios(rsv_ctx* c, const double* v, int32_t n_scen, int32
     c->s_pad = s_pad;
     c->lay.gen = ~0ull;   // scenario length changes validation
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_compute_reserves(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
+rsv_status rsv_compute_reserves(rsv_ctx* c, const rsv_opts* o, rsv_out* out) try {
     if (!c) return RSV_E_ARG;
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
     return compute(c, o, out);
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* sp, rsv_nested_out* out) {
+rsv_status rsv_compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* sp, rsv_nested_out* out) try {
     if (!c) return RSV_E_ARG;
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
     return compute_nested(c, o, sp, out);
+} catch (...) {
+    return rsv::host_error(c);
 }
 
 int32_t rsv_variant_count(int32_t form) {
@@ -1280,7 +1315,7 @@ const char* rsv_variant_name(int32_t form, int32_t variant) {
     return v[variant].name;
 }
 
-rsv_status rsv_tune(rsv_ctx* c, const rsv_opts* opts, int32_t reps, int32_t* best, float* ms_out) {
+rsv_status rsv_tune(rsv_ctx* c, const rsv_opts* opts, int32_t reps, int32_t* best, float* ms_out) try {
     if (!c) return RSV_E_ARG;
     if (!opts || reps < 1) return fail(c, RSV_E_ARG, "bad tune arguments");
     if (c->cf_pol > 0) return fail(c, RSV_E_STATE, "tuning ranks the level-cash-flow variants: clear the loaded sequence");
@@ -1318,9 +1353,11 @@ rsv_status rsv_tune(rsv_ctx* c, const rsv_opts* opts, int32_t reps, int32_t* bes
     c->tuned[opts->form] = arg;
     if (best) *best = arg;
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_synchronize(rsv_ctx* c) {
+rsv_status rsv_synchronize(rsv_ctx* c) try {
     if (!c) return RSV_E_ARG;
     CU(cudaStreamSynchronize(c->stream));
     if (c->d_ctl.p) {
@@ -1329,6 +1366,8 @@ rsv_status rsv_synchronize(rsv_ctx* c) {
         if (ctl[1] == DEV_TIMEOUT) return fail(c, RSV_E_TIMEOUT, "a bounded device wait ran out (table staging)");
     }
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
 const char* rsv_last_error(const rsv_ctx* c) { return c ? c->err.c_str() : "NULL context"; }

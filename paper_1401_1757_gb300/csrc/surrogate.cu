@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "abi_guard.cuh"
 #include "philox.cuh"
 #include "surrogate.cuh"
 
@@ -684,7 +685,7 @@ using namespace rsv;
 
 extern "C" {
 
-rsv_status rsv_surrogate_query(rsv_ctx* c, const rsv_query* queries, int64_t n, int32_t how, double* reserve) {
+rsv_status rsv_surrogate_query(rsv_ctx* c, const rsv_query* queries, int64_t n, int32_t how, double* reserve) try {
     if (!c) return RSV_E_ARG;
     if (!queries || !reserve || n < 1 || n > (int64_t(1) << 31) || how < RSV_QUERY_NETWORK || how > RSV_QUERY_FALLBACK)
         return fail(c, RSV_E_ARG, "bad query arguments");
@@ -732,44 +733,54 @@ rsv_status rsv_surrogate_query(rsv_ctx* c, const rsv_query* queries, int64_t n, 
     CU(cudaStreamSynchronize(c->stream));
     if (bad) return fail(c, RSV_E_ARG, "%d queries name a bad policy, state or month", bad);
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
 int64_t rsv_mlp_param_count(void) { return (int64_t)mlp_n_params(); }
 
-rsv_status rsv_mlp_init(rsv_ctx* c, uint64_t seed) {
+rsv_status rsv_mlp_init(rsv_ctx* c, uint64_t seed) try {
     if (!c) return RSV_E_ARG;
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice failed");
     std::vector<float> p;
     he_init(p, seed);
     c->sur.trained = false;
     return mlp_upload(c, p.data());
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_mlp_set_params(rsv_ctx* c, const float* params, int64_t n) {
+rsv_status rsv_mlp_set_params(rsv_ctx* c, const float* params, int64_t n) try {
     if (!c) return RSV_E_ARG;
     if (!params || n != (int64_t)mlp_n_params()) return fail(c, RSV_E_ARG, "expected %zu parameters", mlp_n_params());
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice failed");
     c->sur.trained = false;
     return mlp_upload(c, params);
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_mlp_get_params(rsv_ctx* c, float* params, int64_t n) {
+rsv_status rsv_mlp_get_params(rsv_ctx* c, float* params, int64_t n) try {
     if (!c) return RSV_E_ARG;
     if (!params || n != (int64_t)mlp_n_params()) return fail(c, RSV_E_ARG, "expected %zu parameters", mlp_n_params());
     if (!c->mlp_ready) return fail(c, RSV_E_STATE, "network not initialised");
     CU(cudaMemcpyAsync(params, c->mlp.params, mlp_n_params() * 4, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_mlp_set_backend(rsv_ctx* c, int32_t backend) {
+rsv_status rsv_mlp_set_backend(rsv_ctx* c, int32_t backend) try {
     if (!c) return RSV_E_ARG;
     if (backend != RSV_MLP_MMA_SYNC && backend != RSV_MLP_TCGEN05) return fail(c, RSV_E_ARG, "bad backend");
     c->mlp.use_tc = backend == RSV_MLP_TCGEN05;
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_mlp_forward(rsv_ctx* c, const float* X, int64_t n, float* y) {
+rsv_status rsv_mlp_forward(rsv_ctx* c, const float* X, int64_t n, float* y) try {
     if (!c) return RSV_E_ARG;
     if (!X || !y || n < 1 || n > (1 << 20)) return fail(c, RSV_E_ARG, "bad forward arguments");
     if (!c->mlp_ready) return fail(c, RSV_E_STATE, "network not initialised");
@@ -787,9 +798,11 @@ rsv_status rsv_mlp_forward(rsv_ctx* c, const float* X, int64_t n, float* y) {
     CU(cudaMemcpyAsync(y, c->mlp.y, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_mlp_gradient(rsv_ctx* c, const float* X, const float* target, int64_t n, float* grads, float* loss) {
+rsv_status rsv_mlp_gradient(rsv_ctx* c, const float* X, const float* target, int64_t n, float* grads, float* loss) try {
     if (!c) return RSV_E_ARG;
     if (!X || !target || !grads || n < 64 || n % 64 || n > (1 << 20))
         return fail(c, RSV_E_ARG, "bad gradient arguments (n a multiple of 64)");
@@ -806,6 +819,8 @@ rsv_status rsv_mlp_gradient(rsv_ctx* c, const float* X, const float* target, int
     CU(cudaStreamSynchronize(c->stream));
     if (loss) *loss = l / (float)n;
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
 }  // extern "C"
@@ -825,7 +840,7 @@ constexpr int kSurDoubles = 7;   // y_mean, y_std, tol, a, b, sigma, r0
 
 extern "C" {
 
-rsv_status rsv_surrogate_save(rsv_ctx* c, const char* path) {
+rsv_status rsv_surrogate_save(rsv_ctx* c, const char* path) try {
     if (!c) return RSV_E_ARG;
     if (!path) return fail(c, RSV_E_ARG, "path must not be NULL");
     if (!c->sur.trained || !c->mlp_ready) return fail(c, RSV_E_STATE, "surrogate not trained");
@@ -855,9 +870,11 @@ rsv_status rsv_surrogate_save(rsv_ctx* c, const char* path) {
     const int cl = std::fclose(f);
     if (wr != buf.size() || cl != 0) return fail(c, RSV_E_ARG, "writing %s failed", path);
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_surrogate_load(rsv_ctx* c, const char* path) {
+rsv_status rsv_surrogate_load(rsv_ctx* c, const char* path) try {
     if (!c) return RSV_E_ARG;
     if (!path) return fail(c, RSV_E_ARG, "path must not be NULL");
     FILE* f = std::fopen(path, "rb");
@@ -902,9 +919,11 @@ rsv_status rsv_surrogate_load(rsv_ctx* c, const char* path) {
     s.r0 = d[6];
     s.trained = true;
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
-rsv_status rsv_surrogate_train(rsv_ctx* c, const rsv_surrogate_cfg* cfg, rsv_surrogate_report* rep) {
+rsv_status rsv_surrogate_train(rsv_ctx* c, const rsv_surrogate_cfg* cfg, rsv_surrogate_report* rep) try {
     if (!c) return RSV_E_ARG;
     if (!cfg || !rep) return fail(c, RSV_E_ARG, "cfg and report must not be NULL");
     if (cfg->n_train < 1024 || cfg->n_val < 1024 || cfg->epochs < 0 || cfg->batch < 64 || cfg->batch % 64 ||
@@ -1081,6 +1100,8 @@ rsv_status rsv_surrogate_train(rsv_ctx* c, const rsv_surrogate_cfg* cfg, rsv_sur
     rep->y_mean = s.y_mean;
     rep->y_std = s.y_std;
     return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
 }
 
 }  // extern "C"
