@@ -590,10 +590,20 @@ struct Variant {
     cudaError_t (*occupancy[2])(int* blocks_per_sm, size_t smem);
 };
 
+// Every CTA stages its own copy of the decrement tables: the largest
+// shared-memory carveout lets the register-bound number of small CTAs fit.
+template <int FORM, int P, int M, int NT, int MINB, bool EXTRA, bool TWO, int PAY>
+cudaError_t set_recur_attributes(size_t smem) {
+    auto k = recur_kernel<FORM, P, M, NT, MINB, EXTRA, TWO, PAY>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+}
+
 template <int FORM, int P, int M, int NT, int MINB, bool EXTRA, bool TWO, int PAY>
 cudaError_t launch_recur(const RecurArgs& a, int grid, size_t smem, cudaStream_t st) {
     auto k = recur_kernel<FORM, P, M, NT, MINB, EXTRA, TWO, PAY>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_recur_attributes<FORM, P, M, NT, MINB, EXTRA, TWO, PAY>(smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NT, smem, st>>>(a);
     return cudaGetLastError();
@@ -602,7 +612,7 @@ cudaError_t launch_recur(const RecurArgs& a, int grid, size_t smem, cudaStream_t
 template <int FORM, int P, int M, int NT, int MINB, bool EXTRA, bool TWO, int PAY>
 cudaError_t occupancy_recur(int* blocks, size_t smem) {
     auto k = recur_kernel<FORM, P, M, NT, MINB, EXTRA, TWO, PAY>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_recur_attributes<FORM, P, M, NT, MINB, EXTRA, TWO, PAY>(smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, NT, smem);
 }
