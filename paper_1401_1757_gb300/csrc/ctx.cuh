@@ -129,6 +129,7 @@ struct SurrogateState {
     std::vector<unsigned char> flag;    // per bucket: 1 = value by the recurrence
     DevBuf d_flag, d_q, d_lab, d_y, d_X, d_pred, d_err, d_aux;
     DevBuf d_curve, d_comm, d_lnb;      // forward-curve increments, commutation columns, ln base values
+    DevBuf d_cnt, d_q2, d_idx, d_v2;    // compaction of the served queries (nested surrogate mode)
     double curve_key[3] = {0.0, 0.0, -1.0};
     int comm_pad = -1, comm_ntab = -1;
     unsigned long long comm_gen = 0;

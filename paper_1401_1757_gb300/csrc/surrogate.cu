@@ -640,6 +640,75 @@ __global__ void scale_by_amount_kernel(const PolSur* __restrict__ pols, const Su
         V[i] = q[i].state < 0 ? 0.0 : V[i] * pols[q[i].pol].amount;
 }
 
+// Compaction of the queries the network serves (valid and in an unflagged
+// bucket), in query order: per-block counts, one block's exclusive scan of
+// the counts, then each block writes its served queries at its offset plus
+// their rank within the block.
+constexpr int kCompactBlock = 1024;
+
+__device__ __forceinline__ bool sur_served(const SurQuery& Q, const unsigned char* __restrict__ flag) {
+    return Q.state >= 0 && !flag[Q.bucket];
+}
+
+__global__ void __launch_bounds__(kCompactBlock) served_count_kernel(const SurQuery* __restrict__ q, long long n,
+                                                                     const unsigned char* __restrict__ flag,
+                                                                     int* __restrict__ counts) {
+    const long long i = blockIdx.x * (long long)kCompactBlock + threadIdx.x;
+    const bool on = i < n && sur_served(q[i], flag);
+    const int c = __syncthreads_count(on);
+    if (threadIdx.x == 0) counts[blockIdx.x] = c;
+}
+
+// Exclusive scan of counts[0 .. nb) in place (one block); total -> counts[nb].
+__global__ void __launch_bounds__(1024) exclusive_scan_kernel(int* __restrict__ counts, int nb) {
+    __shared__ long long part[1024];
+    const int per = (nb + 1023) / 1024, lo = threadIdx.x * per, hi = min(nb, lo + per);
+    long long sum = 0;
+    for (int k = lo; k < hi; ++k) sum += counts[k];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {   // inclusive scan of the thread sums
+        const long long y = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+        __syncthreads();
+        part[threadIdx.x] += y;
+        __syncthreads();
+    }
+    long long run = part[threadIdx.x] - sum;   // exclusive start of this thread's range
+    for (int k = lo; k < hi; ++k) {
+        const int c = counts[k];
+        counts[k] = (int)run;
+        run += c;
+    }
+    if (threadIdx.x == 1023) counts[nb] = (int)part[1023];
+}
+
+__global__ void __launch_bounds__(kCompactBlock) served_gather_kernel(const SurQuery* __restrict__ q, long long n,
+                                                                      const unsigned char* __restrict__ flag,
+                                                                      const int* __restrict__ offsets,
+                                                                      SurQuery* __restrict__ q2, int* __restrict__ idx) {
+    __shared__ int wsum[kCompactBlock / 32];
+    const long long i = blockIdx.x * (long long)kCompactBlock + threadIdx.x;
+    SurQuery Q{};
+    const bool on = i < n && sur_served(Q = q[i], flag);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned m = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) wsum[warp] = __popc(m);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    if (on) {
+        const int pos = offsets[blockIdx.x] + before + __popc(m & ((1u << lane) - 1u));
+        q2[pos] = Q;
+        idx[pos] = (int)i;
+    }
+}
+
+__global__ void scatter_served_kernel(const double* __restrict__ v2, const int* __restrict__ idx, long long n2,
+                                      double* __restrict__ V) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n2; k += (long long)gridDim.x * blockDim.x)
+        V[idx[k]] = v2[k];
+}
+
 }  // namespace
 
 // Per-unit expected reserves (device, n values) of device queries by the
@@ -661,8 +730,31 @@ rsv_status sur_value_queries(rsv_ctx* c, const rsv_query* dq, long long n, const
         c->d_pols.as<PolSur>(), (int)c->pols.size(), dq, n, s.a, s.b, s.sigma, s.r0, q,
         s.d_err.as<int>(), s.d_flag.as<unsigned char>(), reinterpret_cast<unsigned long long*>(s.d_err.as<char>() + 8));
     CU(cudaGetLastError());
-    rsv_status st = sur_predict(c, q, n, V, false, 65536);
-    if (st != RSV_OK) return st;
+    // only the served queries go through features and the network
+    if (n > 0x7fffffffLL) return fail(c, RSV_E_ARG, "too many nested surrogate queries (%lld)", n);
+    const int nb = (int)((n + kCompactBlock - 1) / kCompactBlock);
+    CU(s.d_cnt.ensure(((size_t)nb + 1) * sizeof(int)));
+    CU(s.d_q2.ensure((size_t)std::max(1LL, n) * sizeof(SurQuery)));
+    CU(s.d_idx.ensure((size_t)std::max(1LL, n) * sizeof(int)));
+    CU(s.d_v2.ensure((size_t)std::max(1LL, n) * sizeof(double)));
+    int n_served = 0;
+    if (nb > 0) {
+        served_count_kernel<<<nb, kCompactBlock, 0, c->stream>>>(q, n, s.d_flag.as<unsigned char>(), s.d_cnt.as<int>());
+        exclusive_scan_kernel<<<1, 1024, 0, c->stream>>>(s.d_cnt.as<int>(), nb);
+        served_gather_kernel<<<nb, kCompactBlock, 0, c->stream>>>(q, n, s.d_flag.as<unsigned char>(), s.d_cnt.as<int>(),
+                                                                  s.d_q2.as<SurQuery>(), s.d_idx.as<int>());
+        CU(cudaGetLastError());
+        CU(cudaMemcpyAsync(&n_served, s.d_cnt.as<int>() + nb, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    rsv_status st = RSV_OK;
+    if (n_served > 0) {
+        if ((st = sur_predict(c, s.d_q2.as<SurQuery>(), n_served, s.d_v2.as<double>(), false, 65536)) != RSV_OK)
+            return st;
+        scatter_served_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(s.d_v2.as<double>(), s.d_idx.as<int>(), n_served,
+                                                                      V);
+        CU(cudaGetLastError());
+    }
     SurTables T;
     if ((st = sur_tables(c, T)) != RSV_OK) return st;
     size_t smem_c;
