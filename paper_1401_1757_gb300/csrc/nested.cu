@@ -217,7 +217,7 @@ __global__ void transpose_on_kernel(const double* __restrict__ Lt, int n_outer, 
 // policy tiles, each lane accumulates the pi-weighted reserves of its path,
 // and the CTA adds the warps' sums in a fixed order (deterministic).
 template <int FORM, int P, int NT>
-__global__ void __launch_bounds__(NT) nested_kernel(const NestedArgs a) {
+__global__ void __launch_bounds__(NT, NT == 128 ? 3 : 1) nested_kernel(const NestedArgs a) {
     using TabE = typename Tr<FORM>::TabE;
     using VE = typename Tr<FORM>::VE;
     constexpr int NW = NT / 32;
@@ -356,13 +356,13 @@ cudaError_t launch_nested_t(const NestedArgs& a, int sm_count, size_t smem, cuda
     return cudaGetLastError();
 }
 
-int nested_tile_width(int form) { return form == F_F32 ? 4 : 2; }
+int nested_tile_width(int form) { return form == F_F32 ? 4 : (form == F_COMP ? 6 : 2); }
 
 cudaError_t launch_nested(int form, const NestedArgs& a, int sm_count, size_t smem, cudaStream_t st) {
     switch (form) {
     case F_F64: return launch_nested_t<F_F64, 2, 256>(a, sm_count, smem, st);
     case F_F32: return launch_nested_t<F_F32, 4, 256>(a, sm_count, smem, st);
-    default: return launch_nested_t<F_COMP, 2, 256>(a, sm_count, smem, st);
+    default: return launch_nested_t<F_COMP, 6, 128>(a, sm_count, smem, st);
     }
 }
 
