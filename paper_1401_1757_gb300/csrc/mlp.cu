@@ -235,6 +235,7 @@ __nv_bfloat16* Mlp::wb(int l) const {   // BF16 copy of W_l as the GEMM reads it
 }
 
 cudaError_t Mlp::refresh_bf16(cudaStream_t st) {
+    wt_fresh = false;
     tied_w1_kernel<<<32, 256, 0, st>>>(params + mlp_w_off(1), wb(1));
     for (int l = 2; l <= 4; ++l) {
         const size_t n = (size_t)MLP_H * MLP_H;

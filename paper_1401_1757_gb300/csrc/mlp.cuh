@@ -39,6 +39,7 @@ struct Mlp {
     float *y = nullptr, *t = nullptr, *dy = nullptr, *sq = nullptr, *loss = nullptr;
     float* part = nullptr;          // column-sum partials [cap / 128 + 1][MLP_H]
     __nv_bfloat16* wt = nullptr;    // W_l^T (K-major) BF16 copies for the tcgen05 inference kernel
+    bool wt_fresh = false;          // wt matches params (cleared whenever the BF16 weights are refreshed)
     bool use_tc = true;             // inference on tcgen05 (else the mma.sync kernels)
     __nv_bfloat16* Xi = nullptr;    // inference-only features [cap_i][MLP_XW] (tcgen05 path)
     float* yi = nullptr;            // and outputs [cap_i]

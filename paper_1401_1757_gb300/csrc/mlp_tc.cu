@@ -1,18 +1,25 @@
 // mlp_tc.cu -- surrogate inference on the 5th-generation tensor cores
-// (tcgen05.mma, accumulators in TMEM, operands staged by TMA).
+// (tcgen05.mma, accumulators and activations in TMEM, operands staged by TMA).
 //
-// One CTA (16 warps) runs the whole network on 128-row tiles of queries:
-//   for l = 1..4:  D = A_{l-1} . W_l  (tcgen05.mma m128 n256 k16, FP32 in TMEM)
-//                  A_l = gelu(D + b_l) (BF16, written back into shared memory as
-//                  the next layer's A operand)
-//   y = gelu(D_4 + b_4) . w5 + b5     (FP32 head from the TMEM accumulator)
-// A and W^T are K-major BF16 tiles in shared memory with the 128-byte swizzle
-// (TMA writes them; the epilogue writes A_l with the same pattern).  A warp
-// may only read its own quarter of the TMEM lanes, so warp w reads lanes
-// 32 (w % 4) .. +31 (rows of the tile) and columns 64 (w / 4) .. +63: four
-// warps per lane quarter share the epilogue.  Thread 0 issues the TMA copies
-// and the MMAs.  Every mbarrier wait is bounded; on a timeout the kernel
-// records it in the status word, frees its TMEM and returns.
+// One CTA runs the whole network on 128-row tiles of queries.  Every layer is
+// split into two N = 128 halves, h = 0, 1:
+//   D_h = A_{l-1} . W_l[:, half h]   (tcgen05.mma m128 n128 k16, FP32 in TMEM)
+//   A_l[:, half h] = gelu(D_h + b_l)  (BF16, written back into TMEM by tcgen05.st
+//                                     as the next layer's A operand)
+//   y = gelu(D_4 + b_4) . w5 + b5      (FP32 head from the TMEM accumulators)
+// The first layer reads its A operand (the query features X) from shared
+// memory; the later ones read A from TMEM, two BF16 values per 32-bit column,
+// the even K index in the low half.  TMEM holds D_0, D_1 (columns 0-255) and
+// two activation buffers (256-383, 384-511), so the epilogue of half 0 runs
+// while the tensor cores compute half 1, and the next layer's first K half
+// starts as soon as the epilogue of half 0 is done.  Warp 16 (one thread)
+// issues the TMA copies and the products; warps 0-15 run the epilogue: warp w
+// may only touch TMEM lanes 32 (w % 4) .. +31 (the rows of the tile), and takes
+// columns 32 (w / 4) .. +31 of each half.  W_l^T is staged per half
+// (K-major, 128-byte swizzle); the next layer's half is fetched as soon as the
+// products of the current half are done.  Every mbarrier wait is bounded; on a
+// timeout the kernel records it in the status word, skips the later waits,
+// lets the copies and products in flight land, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -27,15 +34,19 @@ namespace rsv {
 namespace {
 
 constexpr int TM = 128;                         // rows per tile (MMA M)
-constexpr int TN = MLP_H;                       // MMA N = 256
+constexpr int TN = MLP_H;                       // layer width 256
+constexpr int NH = TN / 2;                      // MMA N = 128 (one half of a layer)
 constexpr int SLAB_K = 64;                      // K elements per 128-byte swizzle row
-constexpr int A_SLAB = TM * 128;                // 16 KiB
-constexpr int W_SLAB = TN * 128;                // 32 KiB
-constexpr int A_BYTES = 4 * A_SLAB;             // 64 KiB (K = 256)
-constexpr int W_BYTES = 4 * W_SLAB;             // 128 KiB
+constexpr int X_BYTES = TM * 128;               // 16 KiB: the features, K = 64
+constexpr int WH_SLAB = NH * 128;               // 16 KiB: one K slab of one half of W_l^T
+constexpr int W_SLAB = 2 * WH_SLAB;             // 32 KiB: both halves of one K slab
+constexpr int W_BYTES = 4 * W_SLAB;             // 128 KiB (K = 256)
 constexpr uint32_t kPoll = 1u << 24;
-constexpr int kThreads = 512;                   // 16 warps: 4 lane quarters x 4 column groups
-constexpr int kColsPerWarp = TN / 4;            // 64
+constexpr int kEpiWarps = 16;                   // 4 lane quarters x 4 column groups
+constexpr int kThreads = 32 * (kEpiWarps + 1);  // + the issuing warp
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kAcol0 = 256u;                // activation buffers in TMEM: columns 256 and 384
+__device__ __forceinline__ uint32_t acol_of(int i) { return kAcol0 + 128u * (uint32_t)i; }
 
 struct TcArgs {
     const float* bias[4];
@@ -66,15 +77,24 @@ __device__ __forceinline__ uint64_t sw128_desc(const void* smem) {
 }
 
 // kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both
-// K-major, M = 128, N = 256.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+// K-major, M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NH >> 3) << 17) |
                             ((uint32_t)(TM >> 4) << 24);
 
-__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accum) {
+// D (TMEM) [+]= A . B with A from shared memory
+__device__ __forceinline__ void mma_ss(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accum) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
         "l"(a), "l"(b), "r"(kIdesc), "r"(accum)
+        : "memory");
+}
+// D (TMEM) [+]= A . B with A from tensor memory
+__device__ __forceinline__ void mma_ts(uint32_t tmem, uint32_t a_tmem, uint64_t b, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem),
+        "r"(a_tmem), "l"(b), "r"(kIdesc), "r"(accum)
         : "memory");
 }
 
@@ -104,17 +124,24 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// 16 columns of this warp's 32 lanes from registers into TMEM; waits for completion
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// Byte offset of element (row, k) in a K-major, 128-byte-swizzled operand made
-// of 64-column slabs of `rows` rows.
-__device__ __forceinline__ uint32_t sw128_off(int row, int k, int rows) {
-    const int slab = k >> 6, kc = k & 63;
-    const int chunk = (kc >> 3) ^ (row & 7);
-    return slab * rows * 128 + row * 128 + chunk * 16 + (kc & 7) * 2;
-}
 
 // ---- the kernel -------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads, 1)
@@ -124,26 +151,29 @@ __global__ void __launch_bounds__(kThreads, 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment for the swizzle atoms
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char* Abuf = base;
-    unsigned char* Wbuf = base + A_BYTES;
-    __shared__ uint64_t bar_x, bar_w, bar_mma;
+    unsigned char* Xbuf = base;
+    unsigned char* Wbuf = base + X_BYTES;   // K slab s, half h at s * W_SLAB + h * WH_SLAB
+    __shared__ uint64_t bar_x, bar_w[2], bar_mma[2], bar_epi[2];
     __shared__ uint32_t tmem_slot;
-    __shared__ float head_part[4][TM];   // partial head sums per column group
-    __shared__ float bias_s[4][TN];      // b_1..b_4
-    __shared__ float w5_s[TN + 1];       // head weights and bias
+    __shared__ float head_part[4][TM];                 // partial head sums per column group
+    __shared__ __align__(16) float bias_s[4][TN];      // b_1..b_4
+    __shared__ __align__(16) float w5_s[TN + 4];       // head weights and bias
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < 4 * TN; i += kThreads) bias_s[i / TN][i % TN] = a.bias[i / TN][i % TN];
     for (int i = tid; i <= TN; i += kThreads) w5_s[i] = a.w5[i];
     if (tid == 0) {
         mbar_init(&bar_x, 1);
-        mbar_init(&bar_w, 1);
-        mbar_init(&bar_mma, 1);
+        for (int h = 0; h < 2; ++h) {
+            mbar_init(&bar_w[h], 1);
+            mbar_init(&bar_mma[h], 1);
+            mbar_init(&bar_epi[h], kEpiWarps);   // one arrival per epilogue warp
+        }
         fence_barrier_init();
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(TN)
+                     "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -151,89 +181,162 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = tmem_slot;
-    const CUtensorMap* maps[4] = {&mapW1, &mapW2, &mapW3, &mapW4};
-    uint32_t ph_x = 0, ph_w = 0, ph_m = 0;
+    // tiles of this CTA; layer g = 4 it + l - 1 over them (every barrier below
+    // completes once per layer, so phase parities follow g)
+    const int n_my = (int)blockIdx.x < a.n_tiles ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     bool failed = false;
 
-    auto wait = [&](uint64_t* bar, uint32_t& ph) {
-        bool ok = mbar_wait_bounded(bar, ph, kPoll);
-        ph ^= 1u;
-        ok = __syncthreads_and(ok);
-        return ok;
-    };
-
-    for (int tile = blockIdx.x; tile < a.n_tiles && !failed; tile += gridDim.x) {
-        if (tid == 0) {
-            mbar_arrive_expect_tx(&bar_x, TM * 128);
-            tma_load_2d(Abuf, &mapX, 0, tile * TM, &bar_x);
-            mbar_arrive_expect_tx(&bar_w, TN * 128);
-            tma_load_2d(Wbuf, &mapW1, 0, 0, &bar_w);
-        }
-        if (!wait(&bar_x, ph_x)) { failed = true; break; }
-        for (int l = 0; l < 4; ++l) {
-            if (!wait(&bar_w, ph_w)) { failed = true; break; }
-            const int kslabs = l == 0 ? 1 : 4;
-            if (tid == 0) {
-                fence_after();
-                for (int s = 0; s < kslabs; ++s)
-                    for (int kk = 0; kk < 4; ++kk)   // 4 x k16 per 64-wide slab: +32 bytes each
-                        mma_f16(tmem, sw128_desc(Abuf + s * A_SLAB + kk * 32), sw128_desc(Wbuf + s * W_SLAB + kk * 32),
-                                (s | kk) != 0);
-                mma_commit(&bar_mma);
+    if (warp == kEpiWarps) {
+        if (lane == 0) {
+            const CUtensorMap* maps[4] = {&mapW1, &mapW2, &mapW3, &mapW4};
+            // in flight: copies on bar_x / bar_w[h], products on bar_mma[h] (with the parity they complete)
+            bool pend_x = false, pend_w[2] = {false, false}, pend_m[2] = {false, false};
+            uint32_t par_x = 0, par_w[2] = {0, 0}, par_m[2] = {0, 0};
+            auto wait = [&](uint64_t* bar, uint32_t parity) {
+                if (failed) return;
+                if (!mbar_wait_bounded(bar, parity, kPoll)) {
+                    failed = true;
+                    atomicExch(a.status, DEV_TIMEOUT);
+                }
+            };
+            auto load_w = [&](int h, int layer, uint32_t parity) {   // half h of W_layer
+                const int ns = layer == 1 ? 1 : 4;
+                mbar_arrive_expect_tx(&bar_w[h], ns * WH_SLAB);
+                for (int s = 0; s < ns; ++s)
+                    tma_load_2d(Wbuf + s * W_SLAB + h * WH_SLAB, maps[layer - 1], s * SLAB_K, h * NH, &bar_w[h]);
+                pend_w[h] = true;
+                par_w[h] = parity;
+            };
+            auto load_x = [&](int tile, uint32_t parity) {
+                mbar_arrive_expect_tx(&bar_x, X_BYTES);
+                tma_load_2d(Xbuf, &mapX, 0, tile * TM, &bar_x);
+                pend_x = true;
+                par_x = parity;
+            };
+            if (n_my > 0) {
+                load_x(blockIdx.x, 0);
+                load_w(0, 1, 0);
+                load_w(1, 1, 0);
             }
-            if (!wait(&bar_mma, ph_m)) { failed = true; break; }
-            fence_after();
-            if (tid == 0 && l < 3) {   // the MMAs are done with Wbuf: fetch the next layer's weights
-                mbar_arrive_expect_tx(&bar_w, 4 * W_SLAB);
-                for (int s = 0; s < 4; ++s) tma_load_2d(Wbuf + s * W_SLAB, maps[l + 1], s * SLAB_K, 0, &bar_w);
-            }
-            // epilogue: row = 32 (warp % 4) + lane, columns 64 (warp / 4) .. +63 in chunks of 32
-            const int quarter = warp & 3, cgrp = warp >> 2;
-            const int row = quarter * 32 + lane;
-            const float* bias = bias_s[l];
-            float ysum = 0.0f;
-            for (int c0 = cgrp * kColsPerWarp; c0 < (cgrp + 1) * kColsPerWarp; c0 += 32) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + c0, v);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = gelu_f(v[i] + bias[c0 + i]);
-                if (l < 3) {
-#pragma unroll
-                    for (int i = 0; i < 32; i += 8) {
-                        const uint4 pk = make_uint4(pack_bf16x2(v[i], v[i + 1]), pack_bf16x2(v[i + 2], v[i + 3]),
-                                                    pack_bf16x2(v[i + 4], v[i + 5]), pack_bf16x2(v[i + 6], v[i + 7]));
-                        *reinterpret_cast<uint4*>(Abuf + sw128_off(row, c0 + i, TM)) = pk;
+            for (int it = 0; it < n_my && !failed; ++it) {
+                const bool more = it + 1 < n_my;
+                for (int l = 1; l <= 4 && !failed; ++l) {
+                    const int g = it * 4 + l - 1;
+                    const uint32_t ph = g & 1, php = (g - 1) & 1;
+                    if (l == 1) {
+                        wait(&bar_x, it & 1);
+                        pend_x = false;
                     }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) ysum += v[i] * w5_s[c0 + i];
+                    for (int h = 0; h < 2 && !failed; ++h) {
+                        wait(&bar_w[h], ph);
+                        pend_w[h] = false;
+                        if (g > 0) wait(&bar_epi[h], php);   // D_h read out; A half h of this layer written
+                        if (failed) break;
+                        fence_after();
+                        const uint32_t d = tmem + h * NH;
+                        const unsigned char* wh = Wbuf + h * WH_SLAB;
+                        if (l == 1) {
+                            for (int kk = 0; kk < 4; ++kk)   // 4 x k16 per 64-wide slab: +32 bytes each
+                                mma_ss(d, sw128_desc(Xbuf + kk * 32), sw128_desc(wh + kk * 32), kk != 0);
+                        } else {
+                            const uint32_t acol = tmem + acol_of((l - 2) & 1);
+                            // A column 8 j holds K = 16 j .. 16 j + 15
+                            const int jsplit = h == 0 ? 8 : 0;
+                            for (int j = 0; j < jsplit; ++j)
+                                mma_ts(d, acol + 8 * j, sw128_desc(wh + (j >> 2) * W_SLAB + (j & 3) * 32), j != 0);
+                            if (h == 0) {
+                                wait(&bar_epi[1], php);   // K 128..255 written by the epilogue of half 1
+                                if (failed) break;
+                                fence_after();
+                            }
+                            for (int j = jsplit; j < 16; ++j)
+                                mma_ts(d, acol + 8 * j, sw128_desc(wh + (j >> 2) * W_SLAB + (j & 3) * 32), j != 0);
+                        }
+                        mma_commit(&bar_mma[h]);
+                        pend_m[h] = true;
+                        par_m[h] = ph;
+                    }
+                    // refill each half once its products are done: the next layer's
+                    // weights (the next tile's W_1 after the last layer), and after
+                    // the first layer the next tile's features
+                    for (int h = 0; h < 2 && !failed; ++h) {
+                        wait(&bar_mma[h], ph);
+                        if (failed) break;
+                        pend_m[h] = false;
+                        if (l < 4) load_w(h, l + 1, (g + 1) & 1);
+                        else if (more) load_w(h, 1, (g + 1) & 1);
+                        if (h == 1 && l == 1 && more) load_x(blockIdx.x + (it + 1) * gridDim.x, (it + 1) & 1);
+                    }
                 }
             }
-            if (l == 3) {   // uniform across the block
-                head_part[cgrp][row] = ysum;
-                __syncthreads();
-                if (cgrp == 0)
-                    a.y[tile * TM + row] =
-                        ((head_part[0][row] + head_part[1][row]) + (head_part[2][row] + head_part[3][row])) + w5_s[TN];
+            if (failed) {   // let the copies and products in flight land before the memory is released
+                if (pend_x) mbar_wait_bounded(&bar_x, par_x, kPoll);
+                for (int h = 0; h < 2; ++h) {
+                    if (pend_w[h]) mbar_wait_bounded(&bar_w[h], par_w[h], kPoll);
+                    if (pend_m[h]) mbar_wait_bounded(&bar_mma[h], par_m[h], kPoll);
+                }
             }
-            fence_before();
-            fence_async_smem();   // A_l written by the generic proxy, read next by the tensor cores
-            __syncthreads();
-            fence_after();
         }
-    }
-    if (failed) {
-        // let copies and products still in flight land before the memory is released
-        if (tid == 0) atomicExch(a.status, DEV_TIMEOUT);
-        mbar_wait_bounded(&bar_x, ph_x, kPoll);
-        mbar_wait_bounded(&bar_w, ph_w, kPoll);
-        mbar_wait_bounded(&bar_mma, ph_m, kPoll);
+        __syncwarp();
+    } else {
+        // epilogue: row = 32 (warp % 4) + lane, columns 32 (warp / 4) .. +31 of each half
+        const int quarter = warp & 3, cgrp = warp >> 2, row = quarter * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+        for (int it = 0; it < n_my; ++it) {
+            const int tile = blockIdx.x + it * gridDim.x;
+            float ysum = 0.0f;
+            for (int l = 1; l <= 4; ++l) {
+                const int g = it * 4 + l - 1;
+                for (int h = 0; h < 2; ++h) {
+                    // a timeout is recorded and the later waits skipped, so that every
+                    // warp still reaches the block-wide barriers below
+                    bool ok = true;
+                    if (lane == 0 && !failed) ok = mbar_wait_bounded(&bar_mma[h], g & 1, kPoll);
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (!ok && !failed) {
+                        failed = true;
+                        if (lane == 0) atomicExch(a.status, DEV_TIMEOUT);
+                    }
+                    fence_after();
+                    const int c0 = h * NH + cgrp * 32;
+                    float v[32];
+                    tmem_ld32(tmem + lane_base + c0, v);
+                    const float4* b4 = reinterpret_cast<const float4*>(&bias_s[l - 1][c0]);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float4 b = b4[i];
+                        v[4 * i] = gelu_f(v[4 * i] + b.x);
+                        v[4 * i + 1] = gelu_f(v[4 * i + 1] + b.y);
+                        v[4 * i + 2] = gelu_f(v[4 * i + 2] + b.z);
+                        v[4 * i + 3] = gelu_f(v[4 * i + 3] + b.w);
+                    }
+                    if (l < 4) {
+                        uint32_t r[16];
+#pragma unroll
+                        for (int m = 0; m < 16; ++m) r[m] = pack_bf16x2(v[2 * m], v[2 * m + 1]);
+                        tmem_st16(tmem + lane_base + acol_of((l - 1) & 1) + c0 / 2, r);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) ysum += v[i] * w5_s[c0 + i];
+                    }
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bar_epi[h]);
+                }
+            }
+            head_part[cgrp][row] = ysum;
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+            if (cgrp == 0)
+                a.y[tile * TM + row] =
+                    ((head_part[0][row] + head_part[1][row]) + (head_part[2][row] + head_part[3][row])) + w5_s[TN];
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+        }
     }
     fence_before();
     __syncthreads();
     fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
 // ---- host: tensor maps through the driver entry point ---------------------
@@ -288,18 +391,21 @@ cudaError_t Mlp::forward_tc(const __nv_bfloat16* Xin, int n, float* yout, int sm
     cudaError_t e;
     if (!wt) {
         if ((e = cudaMalloc((void**)&wt, (size_t)(MLP_XW + 3 * MLP_H) * MLP_H * 2)) != cudaSuccess) return e;
+        wt_fresh = false;
     }
-    // refresh the transposed weights (cheap: 200k elements)
-    transpose_w_kernel<<<64, 256, 0, st>>>(params + mlp_w_off(1), MLP_XW, wt, true);
-    for (int l = 2; l <= 4; ++l)
-        transpose_w_kernel<<<128, 256, 0, st>>>(params + mlp_w_off(l), MLP_H,
-                                                wt + (size_t)(MLP_XW + (l - 2) * MLP_H) * MLP_H, false);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    CUtensorMap mx, mw[4];
-    if (!make_map(&mx, Xin, MLP_XW, n, TM) || !make_map(&mw[0], wt, MLP_XW, MLP_H, MLP_H))
+    if (!wt_fresh) {   // the transposed weights, once per change of the parameters (200k elements)
+        transpose_w_kernel<<<64, 256, 0, st>>>(params + mlp_w_off(1), MLP_XW, wt, true);
+        for (int l = 2; l <= 4; ++l)
+            transpose_w_kernel<<<128, 256, 0, st>>>(params + mlp_w_off(l), MLP_H,
+                                                    wt + (size_t)(MLP_XW + (l - 2) * MLP_H) * MLP_H, false);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        wt_fresh = true;
+    }
+    CUtensorMap mx, mw[4];   // weight boxes are one N half (128 rows of W_l^T)
+    if (!make_map(&mx, Xin, MLP_XW, n, TM) || !make_map(&mw[0], wt, MLP_XW, MLP_H, NH))
         return cudaErrorNotSupported;
     for (int l = 1; l < 4; ++l)
-        if (!make_map(&mw[l], wt + (size_t)(MLP_XW + (l - 1) * MLP_H) * MLP_H, MLP_H, MLP_H, MLP_H))
+        if (!make_map(&mw[l], wt + (size_t)(MLP_XW + (l - 1) * MLP_H) * MLP_H, MLP_H, MLP_H, NH))
             return cudaErrorNotSupported;
     TcArgs a;
     for (int l = 0; l < 4; ++l) a.bias[l] = params + mlp_b_off(l + 1);
@@ -307,7 +413,7 @@ cudaError_t Mlp::forward_tc(const __nv_bfloat16* Xin, int n, float* yout, int sm
     a.y = yout;
     a.n_tiles = n / TM;
     a.status = status;
-    const size_t smem = A_BYTES + W_BYTES + 1024;
+    const size_t smem = X_BYTES + W_BYTES + 1024;
     if ((e = cudaFuncSetAttribute(mlp_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
         return e;

@@ -115,33 +115,41 @@ __global__ void sur_curve_kernel(double a, double b, double sigma, int n, double
 // Commutation columns of each decrement table at each flat reference rate
 // delta (one thread per (table, rate)): l_k = prod_{j<k} p_j from month 0,
 // D_k = v^k l_k, N_k = sum_{j>=k} D_j, C_k = v^{k+1} l_k q_k, M_k = sum_{j>=k} C_j,
-// v = exp(-delta/12); survival is zero past the table's end.
-__global__ void sur_comm_kernel(const double2* __restrict__ tab, int tab_pad, int n_tab, double* __restrict__ comm) {
+// v = exp(-delta/12); survival is zero past the table's end.  Computed in FP64
+// and stored as FP32 head + tail pairs (about 48 bits), so that the
+// differences N_a - N_b of the base values keep their precision in FP32.
+__device__ __forceinline__ float2 sur_split(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ double sur_join(float2 x) { return (double)x.x + (double)x.y; }
+
+__global__ void sur_comm_kernel(const double2* __restrict__ tab, int tab_pad, int n_tab, float2* __restrict__ comm) {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= n_tab * SUR_COMM_N) return;
     const int t = id / SUR_COMM_N, g = id % SUR_COMM_N;
     const int CL = sur_comm_len(tab_pad);
-    double* D = comm + (size_t)id * 3 * CL;
-    double* N = D + CL;
-    double* M = N + CL;
+    float2* D = comm + (size_t)id * 3 * CL;
+    float2* N = D + CL;
+    float2* M = N + CL;
     const double v = exp(-(SUR_COMM_LO + g * SUR_COMM_STEP) / 12.0);
     double l = 1.0, vk = 1.0;
     for (int k = 0; k <= tab_pad; ++k) {
         const double p = k < tab_pad ? tab[(size_t)t * tab_pad + k].x : 0.0;
-        D[k] = vk * l;
-        M[k] = vk * v * l * (1.0 - p);   // C_k, summed below
+        D[k] = sur_split(vk * l);
+        M[k] = sur_split(vk * v * l * (1.0 - p));   // C_k, summed below
         l *= p;
         vk *= v;
     }
-    D[tab_pad + 1] = 0.0;
+    D[tab_pad + 1] = make_float2(0.0f, 0.0f);
     double sn = 0.0, sm = 0.0;
-    N[tab_pad + 1] = 0.0;
-    M[tab_pad + 1] = 0.0;
+    N[tab_pad + 1] = make_float2(0.0f, 0.0f);
+    M[tab_pad + 1] = make_float2(0.0f, 0.0f);
     for (int k = tab_pad; k >= 0; --k) {
-        sn += D[k];
-        sm += M[k];
-        N[k] = sn;
-        M[k] = sm;
+        sn += sur_join(D[k]);
+        sm += sur_join(M[k]);
+        N[k] = sur_split(sn);
+        M[k] = sur_split(sm);
     }
 }
 
@@ -256,56 +264,54 @@ __global__ void sur_fallback_nodes_kernel(const PolSur* __restrict__ pols, const
 // two single-life values: for constant monthly forces a monthly annuity in
 // arrears satisfies ln(1 + 1/a) = (delta + mu)/12, and the joint life's force
 // is the sum of the two, so ln(1 + 1/a_xy) = ln(1 + 1/a_x) + ln(1 + 1/a_y) - delta/12.
-__device__ double sur_base_value(const PolSur& P, const SurTables& T, int g, int m, int state) {
+__device__ float sur_base_value(const PolSur& P, const SurTables& T, int g, int m, int state) {
     const int CL = sur_comm_len(T.tab_pad), n = P.S - m;
     auto col = [&](int tab) { return T.comm + ((size_t)tab * SUR_COMM_N + g) * 3 * CL; };
+    // a - b of two head + tail pairs: the heads first (exact when they are close), then the tails
+    auto diff = [](float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); };
     auto ann = [&](int tab, int x) {
-        const double* D = col(tab);
+        const float2* D = col(tab);
         const int e = min(x + n, T.tab_pad);
-        return D[x] > 0.0 ? (D[CL + x + 1] - D[CL + e + 1]) / D[x] : 0.0;
+        return D[x].x > 0.0f ? diff(D[CL + x + 1], D[CL + e + 1]) / D[x].x : 0.0f;
     };
     const int x = P.age1 + m;
     if (P.product == RSV_SL_ANNUITY) return ann(P.tab1, x);
     if (P.product == RSV_JL_REVERSIONARY) {
         const int y = P.age2 + m;
+        const float rho = (float)P.rho;
         if (state == 1) return ann(P.tab1, x);
-        if (state == 2) return P.rho * ann(P.tab2, y);
-        const double ax = ann(P.tab1, x), ay = ann(P.tab2, y);
-        if (!(ax > 0.0) || !(ay > 0.0)) return ax + P.rho * ay;
-        // an estimate: FP32 is ample (train and inference use the same function)
-        const float e = log1pf((float)(1.0 / ax)) + log1pf((float)(1.0 / ay)) -
-                        (float)((SUR_COMM_LO + g * SUR_COMM_STEP) / 12.0);
-        const double axy = e > 0.0f ? fmin((double)(1.0f / expm1f(e)), fmin(ax, ay)) : fmin(ax, ay);
-        return ax + P.rho * (ay - axy);
+        if (state == 2) return rho * ann(P.tab2, y);
+        const float ax = ann(P.tab1, x), ay = ann(P.tab2, y);
+        if (!(ax > 0.0f) || !(ay > 0.0f)) return ax + rho * ay;
+        const float e = log1pf(1.0f / ax) + log1pf(1.0f / ay) - (SUR_COMM_LO_F + g * SUR_COMM_STEP_F) / 12.0f;
+        const float axy = e > 0.0f ? fminf(1.0f / expm1f(e), fminf(ax, ay)) : fminf(ax, ay);
+        return ax + rho * (ay - axy);
     }
-    const double* D = col(P.tab1);
-    if (!(D[x] > 0.0)) return 1.0;   // past the table: death in the first month
+    const float2* D = col(P.tab1);
+    if (!(D[x].x > 0.0f)) return 1.0f;   // past the table: death in the first month
     const int e = min(x + n, T.tab_pad + 1);
-    const double A1 = (D[2 * CL + x] - D[2 * CL + e]) / D[x];
-    return P.product == RSV_TERM_ASSURANCE ? A1 : A1 + D[e] / D[x];
+    const float A1 = diff(D[2 * CL + x], D[2 * CL + e]) / D[x].x;
+    return P.product == RSV_TERM_ASSURANCE ? A1 : A1 + D[e].x / D[x].x;
 }
 
 // ln of the base value at the query's own flat rate: the Vasicek yield to
 // half the remaining term (between one month and 15 years), interpolated
-// linearly in ln between the two neighbouring grid rates.  Returns the yield
-// through *delta.  0 where the base value is not positive.  The yield and the
-// logarithms are FP32 (the same deterministic function at training and at
-// inference; its rounding, ~1e-7, is far below the network's error); the
-// commutation ratios stay FP64.
-__device__ double sur_ln_base(const PolSur& P, const SurTables& T, const SurQuery& Q, double* delta) {
+// linearly in ln(base value) between the two nearest grid rates.  FP32
+// throughout (GB300's FP64 pipe is narrow, and the value is only an offset
+// that training and inference share).
+__device__ float sur_ln_base(const PolSur& P, const SurTables& T, const SurQuery& Q, float* delta) {
     const int n = P.S - Q.m;
     const float h = min(max(n / 2, 1), 180) / 12.0f;
-    const float a = (float)T.a, B = -expm1f(-a * h) / a;
-    const float lnP = (B - h) * (float)((T.a * T.a * T.b - 0.5 * T.sigma * T.sigma) / (T.a * T.a)) -
-                      (float)(T.sigma * T.sigma / (4.0 * T.a)) * B * B - B * (float)Q.r;
-    const double d = (double)(-lnP / h);
+    const float B = -expm1f(-T.af * h) / T.af;
+    const float lnP = (B - h) * T.k1 - T.k2 * B * B - B * (float)Q.r;
+    const float d = -lnP / h;
     *delta = d;
-    const double u = fmin(fmax((d - SUR_COMM_LO) / SUR_COMM_STEP, 0.0), (double)(SUR_COMM_N - 1));
+    const float u = fminf(fmaxf((d - SUR_COMM_LO_F) * SUR_COMM_INV_STEP_F, 0.0f), (float)(SUR_COMM_N - 1));
     const int g0 = min((int)u, SUR_COMM_N - 2);
-    const double f = u - g0;
-    const double b0 = sur_base_value(P, T, g0, Q.m, Q.state), b1 = sur_base_value(P, T, g0 + 1, Q.m, Q.state);
-    if (!(b0 > 0.0) || !(b1 > 0.0)) return 0.0;
-    return (1.0 - f) * (double)logf((float)b0) + f * (double)logf((float)b1);
+    const float f = u - g0;
+    const float b0 = sur_base_value(P, T, g0, Q.m, Q.state), b1 = sur_base_value(P, T, g0 + 1, Q.m, Q.state);
+    if (!(b0 > 0.0f) || !(b1 > 0.0f)) return 0.0f;
+    return (1.0f - f) * logf(b0) + f * logf(b1);
 }
 
 // A feature row as exact hi + lo BF16 halves (the first layer's weights are
@@ -332,48 +338,49 @@ __device__ __forceinline__ void sur_store_features(const float (&f)[MLP_IN], __n
 // Features of a query (zero-padded to MLP_IN, hi + lo BF16) and the ln base
 // value the network's output is added to.
 __global__ void sur_features_kernel(const PolSur* __restrict__ pols, const SurTables T, const SurQuery* __restrict__ qs,
-                                    long long n, __nv_bfloat16* __restrict__ X, double* __restrict__ lnb) {
+                                    long long n, __nv_bfloat16* __restrict__ X, float* __restrict__ lnb) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const SurQuery Q = qs[i];
         const PolSur P = pols[Q.pol];
         float f[MLP_IN];
 #pragma unroll
         for (int k = 0; k < MLP_IN; ++k) f[k] = 0.0f;
-        double base = 0.0, delta = 0.0;
+        float base = 0.0f, delta = 0.0f;
         if (Q.state >= 0) base = sur_ln_base(P, T, Q, &delta);
         f[P.product] = 1.0f;
         f[4 + max(0, Q.state)] = 1.0f;
         const bool jl = P.product == RSV_JL_REVERSIONARY;
         const float age1 = ((P.age1 + Q.m) / 12.0f - 60.0f) / 25.0f;
         const float rem = (P.S - Q.m) / 12.0f / 40.0f;
-        const float rr = (float)((Q.r - 0.04) / 0.02);
+        const float rr = ((float)Q.r - 0.04f) * 50.0f;
         f[7] = age1;
         f[8] = jl ? ((P.age2 + Q.m) / 12.0f - 60.0f) / 25.0f : 0.0f;
         f[9] = jl ? (float)P.rho : 0.0f;
         f[10] = rem;
         f[11] = rr;
-        f[12] = (logf((float)fmax(P.amount, 1e-30)) - 9.0f) / 2.0f;
+        f[12] = (logf(fmaxf((float)P.amount, 1e-30f)) - 9.0f) / 2.0f;
         f[13] = age1 * age1;
         f[14] = rem * rem;
         f[15] = rr * rem;
         f[16] = log1pf((float)(P.S - Q.m)) / 7.0f;
-        f[17] = (float)(base / 4.0);
-        f[18] = (float)((delta - 0.04) / 0.02);
+        f[17] = base * 0.25f;
+        f[18] = (delta - 0.04f) * 50.0f;
         sur_store_features(f, X + i * MLP_XW);
         lnb[i] = base;
     }
 }
 
-// reserve per unit = exp(network output, denormalised, + ln base value)
-__global__ void sur_to_reserve_kernel(const float* __restrict__ yhat, const double* __restrict__ lnb, long long n,
-                                      double mu, double sd, double* __restrict__ V) {
+// reserve per unit = exp(network output, denormalised, + ln base value), in
+// FP32 (about 3e-7 relative for arguments below 8 in magnitude)
+__global__ void sur_to_reserve_kernel(const float* __restrict__ yhat, const float* __restrict__ lnb, long long n,
+                                      float mu, float sd, double* __restrict__ V) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        V[i] = exp((double)yhat[i] * sd + mu + lnb[i]);
+        V[i] = (double)expf(fmaf(yhat[i], sd, mu) + lnb[i]);
 }
 
 namespace {
 
-__global__ void targets_kernel(const double* __restrict__ V, const double* __restrict__ lnb, long long n, double mu,
+__global__ void targets_kernel(const double* __restrict__ V, const float* __restrict__ lnb, long long n, double mu,
                                double sd, float* __restrict__ y) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] = (float)((log(V[i]) - lnb[i] - mu) / sd);
@@ -402,7 +409,7 @@ __global__ void rel_err_kernel(const double* __restrict__ pred, const double* __
 }
 
 // moments of ln(label / base value) (FP64, fixed order per block, then on the host)
-__global__ void log_moments_kernel(const double* __restrict__ V, const double* __restrict__ lnb, long long n,
+__global__ void log_moments_kernel(const double* __restrict__ V, const float* __restrict__ lnb, long long n,
                                    double* __restrict__ part) {
     __shared__ double s1[256], s2[256];
     double a = 0.0, b2 = 0.0;
@@ -449,9 +456,9 @@ rsv_status sur_tables(rsv_ctx* c, SurTables& T) {
     }
     if (s.comm_pad != pad || s.comm_ntab != n_tab || s.comm_gen != c->tab_gen) {
         const int jobs = n_tab * SUR_COMM_N;
-        CU(s.d_comm.ensure((size_t)jobs * 3 * sur_comm_len(pad) * sizeof(double)));
+        CU(s.d_comm.ensure((size_t)jobs * 3 * sur_comm_len(pad) * sizeof(float2)));
         sur_comm_kernel<<<(jobs + 63) / 64, 64, 0, c->stream>>>(c->d_tab[F_F64].as<double2>(), pad, n_tab,
-                                                               s.d_comm.as<double>());
+                                                               s.d_comm.as<float2>());
         CU(cudaGetLastError());
         s.comm_pad = pad;
         s.comm_ntab = n_tab;
@@ -460,10 +467,13 @@ rsv_status sur_tables(rsv_ctx* c, SurTables& T) {
     T.tab = c->d_tab[F_F64].as<double2>();
     T.tab_pad = pad;
     T.curve = s.d_curve.as<double2>();
-    T.comm = s.d_comm.as<double>();
+    T.comm = s.d_comm.as<float2>();
     T.a = s.a;
     T.b = s.b;
     T.sigma = s.sigma;
+    T.af = (float)s.a;
+    T.k1 = (float)((s.a * s.a * s.b - 0.5 * s.sigma * s.sigma) / (s.a * s.a));
+    T.k2 = (float)(s.sigma * s.sigma / (4.0 * s.a));
     return RSV_OK;
 }
 
@@ -522,14 +532,14 @@ rsv_status sur_predict(rsv_ctx* c, const SurQuery* q, long long n, double* V, bo
     __nv_bfloat16* X = tc ? c->mlp.Xi : c->mlp.X;
     float* y = tc ? c->mlp.yi : c->mlp.y;
     batch = batch / 128 * 128;
-    CU(s.d_lnb.ensure((size_t)batch * sizeof(double)));
+    CU(s.d_lnb.ensure((size_t)batch * sizeof(float)));
     for (long long o = 0; o < n; o += batch) {
         const int nb = (int)std::min<long long>(batch, n - o);
         const int nb_pad = (nb + 127) / 128 * 128;
         if (nb_pad != nb) CU(cudaMemsetAsync(X, 0, (size_t)nb_pad * MLP_XW * 2, c->stream));
         const int grid = (int)std::min<long long>((nb + 255) / 256, (long long)c->sm_count * 16);
         sur_features_kernel<<<grid, 256, 0, c->stream>>>(c->d_pols.as<PolSur>(), T, q + o, nb, X,
-                                                         s.d_lnb.as<double>());
+                                                         s.d_lnb.as<float>());
         CU(cudaGetLastError());
         if (tc) {
             CU(c->d_ctl.ensure(2 * sizeof(int32_t)));
@@ -537,7 +547,8 @@ rsv_status sur_predict(rsv_ctx* c, const SurQuery* q, long long n, double* V, bo
         } else {
             CU(c->mlp.forward(X, nb_pad, y, nullptr, c->stream));
         }
-        sur_to_reserve_kernel<<<grid, 256, 0, c->stream>>>(y, s.d_lnb.as<double>(), nb, s.y_mean, s.y_std, V + o);
+        sur_to_reserve_kernel<<<grid, 256, 0, c->stream>>>(y, s.d_lnb.as<float>(), nb, (float)s.y_mean, (float)s.y_std,
+                                                           V + o);
         CU(cudaGetLastError());
     }
     if (fallback) {
@@ -1060,19 +1071,19 @@ rsv_status rsv_surrogate_train(rsv_ctx* c, const rsv_surrogate_cfg* cfg, rsv_sur
     CU(cudaGetLastError());
     SurTables T;
     if ((st = sur_tables(c, T)) != RSV_OK) return st;
-    CU(s.d_lnb.ensure((size_t)n * sizeof(double)));
+    CU(s.d_lnb.ensure((size_t)n * sizeof(float)));
     CU(cudaEventRecord(e0, c->stream));
     sur_label_kernel<<<grid, 128, 0, c->stream>>>(c->d_pols.as<PolSur>(), T, q, n, nullptr, s.d_lab.as<double>());
     CU(cudaGetLastError());
     CU(cudaEventRecord(e1, c->stream));
     sur_features_kernel<<<grid, 256, 0, c->stream>>>(c->d_pols.as<PolSur>(), T, q, n, s.d_X.as<__nv_bfloat16>(),
-                                                     s.d_lnb.as<double>());
+                                                     s.d_lnb.as<float>());
     CU(cudaGetLastError());
     // target normalisation from the training labels
     const int mb = 256;
     DevBuf part;
     CU(part.ensure(mb * 2 * 8));
-    log_moments_kernel<<<mb, 256, 0, c->stream>>>(s.d_lab.as<double>(), s.d_lnb.as<double>(), nt, part.as<double>());
+    log_moments_kernel<<<mb, 256, 0, c->stream>>>(s.d_lab.as<double>(), s.d_lnb.as<float>(), nt, part.as<double>());
     std::vector<double> hpart(mb * 2);
     CU(cudaMemcpyAsync(hpart.data(), part.p, mb * 2 * 8, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
@@ -1085,7 +1096,7 @@ rsv_status rsv_surrogate_train(rsv_ctx* c, const rsv_surrogate_cfg* cfg, rsv_sur
     s.y_mean = s1 / nt;
     s.y_std = std::sqrt(std::max(s2 / nt - s.y_mean * s.y_mean, 1e-12));
     if (!std::isfinite(s.y_mean)) return fail(c, RSV_E_ASSUMPTION, "a training label is not positive");
-    targets_kernel<<<grid, 256, 0, c->stream>>>(s.d_lab.as<double>(), s.d_lnb.as<double>(), n, s.y_mean, s.y_std,
+    targets_kernel<<<grid, 256, 0, c->stream>>>(s.d_lab.as<double>(), s.d_lnb.as<float>(), n, s.y_mean, s.y_std,
                                                 s.d_y.as<float>());
     CU(cudaGetLastError());
 
@@ -1116,8 +1127,9 @@ rsv_status rsv_surrogate_train(rsv_ctx* c, const rsv_surrogate_cfg* cfg, rsv_sur
     cudaEventElapsedTime(&label_ms, e0, e1);
     cudaEventElapsedTime(&train_ms, e2, e3);
 
-    // held-out scoring against the recurrence
+    // held-out scoring against the recurrence (buffers allocated before the timed region)
     CU(s.d_pred.ensure((size_t)nv * 8));
+    if (c->mlp.use_tc) CU(c->mlp.ensure_infer(1 << 19));
     CU(cudaEventRecord(e0, c->stream));
     if ((st = sur_predict(c, q + nt, nv, s.d_pred.as<double>(), false, 65536)) != RSV_OK) return st;
     CU(cudaEventRecord(e1, c->stream));

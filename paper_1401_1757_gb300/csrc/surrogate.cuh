@@ -24,12 +24,15 @@ struct SurTables {
     const double2* tab;    // F64 decrement table entries (p, q), tab_pad per table
     int tab_pad;
     const double2* curve;  // per month t: (dA_t, dB_t), ln P((t+1)/12 | r) - ln P(t/12 | r) = dA_t - dB_t r
-    const double* comm;    // commutation columns D, N, M per (table, grid rate), sur_comm_len(tab_pad) entries each
+    const float2* comm;    // commutation columns D, N, M per (table, grid rate), sur_comm_len(tab_pad) entries
+                           // each, as FP32 head + tail pairs of the FP64 values
     double a, b, sigma;    // the Vasicek model
+    float af, k1, k2;      // a, (a^2 b - sigma^2/2)/a^2 and sigma^2/(4a) in FP32 for the base value's yield
 };
 
 // Flat reference rates of the commutation columns (continuous, per year).
 constexpr double SUR_COMM_LO = -0.10, SUR_COMM_STEP = 0.0025;
+constexpr float SUR_COMM_LO_F = -0.10f, SUR_COMM_STEP_F = 0.0025f, SUR_COMM_INV_STEP_F = 400.0f;
 constexpr int SUR_COMM_N = 141;
 __host__ __device__ constexpr int sur_comm_len(int tab_pad) { return tab_pad + 2; }
 
