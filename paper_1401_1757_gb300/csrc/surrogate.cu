@@ -27,14 +27,19 @@ namespace rsv {
 
 // z-score of a node rate under the Vasicek model at month m from r0 (the
 // rate at month 0 is r0 itself: anything else is out of the model's range).
-__device__ __forceinline__ double sur_rate_z(int m, double r, double a, double b, double sigma, double r0) {
-    const double t = m / 12.0;
-    const double mean = b + (r0 - b) * exp(-a * t);
-    const double sd = sigma * sqrt(-expm1(-2.0 * a * t) / (2.0 * a));
-    if (sd > 0.0) return (r - mean) / sd;
-    return r == mean ? 0.0 : 1e30;
+// FP32: it only picks a bucket, and calibration and use share this function.
+__device__ __forceinline__ float sur_rate_z(int m, double r, double a, double b, double sigma, double r0) {
+    const float t = m / 12.0f, af = (float)a, bf = (float)b;
+    const float mean = bf + ((float)r0 - bf) * expf(-af * t);
+    const float sd = (float)sigma * sqrtf(-expm1f(-2.0f * af * t) / (2.0f * af));
+    const float rf = (float)r;
+    if (sd > 0.0f) return (rf - mean) / sd;
+    return rf == mean ? 0.0f : 1e30f;
 }
 
+// Gate bucket of a query: product and state, 10-year age band of the life the
+// value depends on (from age 20), 10-year band of the remaining term, and the
+// node rate's z-score in half standard deviations (beyond 4 in the last band).
 __device__ __forceinline__ int sur_bucket(const PolSur& P, int m, int state, double r, double a, double b,
                                           double sigma, double r0) {
     const int ps = P.product == RSV_SL_ANNUITY ? 0
@@ -42,10 +47,10 @@ __device__ __forceinline__ int sur_bucket(const PolSur& P, int m, int state, dou
                    : P.product == RSV_TERM_ASSURANCE ? 4 : 5;
     int age = P.age1;   // the life (or for state 00 the older life) the value depends on
     if (P.product == RSV_JL_REVERSIONARY) age = state == 2 ? P.age2 : (state == 1 ? P.age1 : max(P.age1, P.age2));
-    const int ab = min(SUR_NB_AGE - 1, max(0, (int)(((age + m) / 12.0 - 20.0) / 10.0)));
-    const int tb = min(SUR_NB_TERM - 1, max(0, (int)((P.S - m) / 120.0)));
-    const double z = sur_rate_z(m, r, a, b, sigma, r0);
-    const int rb = fabs(z) < 4.0 ? min(SUR_NB_R - 2, max(0, (int)floor(2.0 * z + 8.0))) : SUR_NB_R - 1;
+    const int ab = min(SUR_NB_AGE - 1, max(0, (age + m - 240) / 120));   // months; truncation as the clamp wants
+    const int tb = min(SUR_NB_TERM - 1, max(0, (P.S - m) / 120));
+    const float z = sur_rate_z(m, r, a, b, sigma, r0);
+    const int rb = fabsf(z) < 4.0f ? min(SUR_NB_R - 2, max(0, (int)floorf(2.0f * z + 8.0f))) : SUR_NB_R - 1;
     return ((ps * SUR_NB_AGE + ab) * SUR_NB_TERM + tb) * SUR_NB_R + rb;
 }
 
@@ -633,14 +638,19 @@ __global__ void query_prep_kernel(const PolSur* __restrict__ pols, int n_pol, co
         const bool ok = r.pol >= 0 && r.pol < n_pol && r.m >= 0 && isfinite(r.r) && r.state >= 0 &&
                         r.state <= (pols[r.pol >= 0 && r.pol < n_pol ? r.pol : 0].product == RSV_JL_REVERSIONARY ? 2 : 0) &&
                         r.m < pols[r.pol >= 0 && r.pol < n_pol ? r.pol : 0].S;
+        bool flagged = false;
         if (!ok) {
             atomicAdd(bad, 1);
             Q.pol = 0;
             Q.state = -1;
         } else {
             Q.bucket = sur_bucket(pols[r.pol], r.m, r.state, r.r, a, b, sigma, r0);
-            if (flag && flag[Q.bucket]) atomicAdd(n_flag, 1ull);
+            flagged = flag && flag[Q.bucket];
         }
+        // one atomic per warp for the flagged count
+        const unsigned active = __activemask();
+        const unsigned fm = __ballot_sync(active, flagged);
+        if (fm && (threadIdx.x & 31) == __ffs(active) - 1) atomicAdd(n_flag, (unsigned long long)__popc(fm));
         out[i] = Q;
     }
 }
