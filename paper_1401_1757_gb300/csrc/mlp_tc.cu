@@ -4,9 +4,10 @@
 // One CTA runs the whole network on 128-row tiles of queries.  Every layer is
 // split into two N = 128 halves, h = 0, 1:
 //   D_h = A_{l-1} . W_l[:, half h]   (tcgen05.mma m128 n128 k16, FP32 in TMEM)
-//   A_l[:, half h] = gelu(D_h + b_l)  (BF16, written back into TMEM by tcgen05.st
-//                                     as the next layer's A operand)
-//   y = gelu(D_4 + b_4) . w5 + b5      (FP32 head from the TMEM accumulators)
+//   A_l[:, half h] = 2 gelu(D_h + b_l) (BF16, written back into TMEM by tcgen05.st
+//                                     as the next layer's A operand; the next
+//                                     layer's weights are staged as W / 2)
+//   y = 2 gelu(D_4 + b_4) . (w5 / 2) + b5  (FP32 head from the TMEM accumulators)
 // The first layer reads its A operand (the query features X) from shared
 // memory; the later ones read A from TMEM, two BF16 values per 32-bit column,
 // the even K index in the low half.  TMEM holds D_0, D_1 (columns 0-255) and
@@ -124,6 +125,14 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// 2 gelu(z) in the tanh form: z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).  The
+// factor 1/2 of gelu is carried by the next layer's weights (and the head's),
+// which saves a multiply per element; powers of two scale BF16 and FP32 exactly.
+__device__ __forceinline__ float gelu2_f(float z) {
+    const float t = tanh_hw(z * __fmaf_rn(kGeluCK, z * z, kGeluC));
+    return __fmaf_rn(z, t, z);
+}
+
 // 16 columns of this warp's 32 lanes from registers into TMEM; waits for completion
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
     asm volatile(
@@ -161,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < 4 * TN; i += kThreads) bias_s[i / TN][i % TN] = a.bias[i / TN][i % TN];
-    for (int i = tid; i <= TN; i += kThreads) w5_s[i] = a.w5[i];
+    for (int i = tid; i <= TN; i += kThreads) w5_s[i] = i < TN ? 0.5f * a.w5[i] : a.w5[i];   // w5 / 2, then b5
     if (tid == 0) {
         mbar_init(&bar_x, 1);
         for (int h = 0; h < 2; ++h) {
@@ -305,10 +314,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const float4 b = b4[i];
-                        v[4 * i] = gelu_f(v[4 * i] + b.x);
-                        v[4 * i + 1] = gelu_f(v[4 * i + 1] + b.y);
-                        v[4 * i + 2] = gelu_f(v[4 * i + 2] + b.z);
-                        v[4 * i + 3] = gelu_f(v[4 * i + 3] + b.w);
+                        v[4 * i] = gelu2_f(v[4 * i] + b.x);
+                        v[4 * i + 1] = gelu2_f(v[4 * i + 1] + b.y);
+                        v[4 * i + 2] = gelu2_f(v[4 * i + 2] + b.z);
+                        v[4 * i + 3] = gelu2_f(v[4 * i + 3] + b.w);
                     }
                     if (l < 4) {
                         uint32_t r[16];
@@ -317,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tmem_st16(tmem + lane_base + acol_of((l - 1) & 1) + c0 / 2, r);
                     } else {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) ysum += v[i] * w5_s[c0 + i];
+                        for (int i = 0; i < 32; ++i) ysum = __fmaf_rn(v[i], w5_s[c0 + i], ysum);
                     }
                     fence_before();
                     __syncwarp();
@@ -370,13 +379,15 @@ bool make_map(CUtensorMap* m, const void* ptr, uint64_t cols, uint64_t rows, uin
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// W_l^T (K-major, [256][K]) BF16 copies for the tensor cores
-__global__ void transpose_w_kernel(const float* __restrict__ W, int K, __nv_bfloat16* __restrict__ Wt, bool tied) {
+// W_l^T (K-major, [256][K]) BF16 copies for the tensor cores, times `scale`
+// (a power of two, so the BF16 value is the scaled BF16 of the weight)
+__global__ void transpose_w_kernel(const float* __restrict__ W, int K, __nv_bfloat16* __restrict__ Wt, bool tied,
+                                   float scale) {
     // W [K_in][256] FP32 (K_in = 32 for the tied first layer) -> Wt [256][K]
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K * MLP_H; i += gridDim.x * blockDim.x) {
         const int n = i / K, k = i % K;
         const int kin = tied ? (k % MLP_IN) : k;
-        Wt[i] = __float2bfloat16_rn(W[(size_t)kin * MLP_H + n]);
+        Wt[i] = __float2bfloat16_rn(W[(size_t)kin * MLP_H + n] * scale);
     }
 }
 
@@ -394,10 +405,11 @@ cudaError_t Mlp::forward_tc(const __nv_bfloat16* Xin, int n, float* yout, int sm
         wt_fresh = false;
     }
     if (!wt_fresh) {   // the transposed weights, once per change of the parameters (200k elements)
-        transpose_w_kernel<<<64, 256, 0, st>>>(params + mlp_w_off(1), MLP_XW, wt, true);
+        // layers 2-4 read 2 gelu(z) (see the epilogue): their weights carry the 1/2
+        transpose_w_kernel<<<64, 256, 0, st>>>(params + mlp_w_off(1), MLP_XW, wt, true, 1.0f);
         for (int l = 2; l <= 4; ++l)
             transpose_w_kernel<<<128, 256, 0, st>>>(params + mlp_w_off(l), MLP_H,
-                                                    wt + (size_t)(MLP_XW + (l - 2) * MLP_H) * MLP_H, false);
+                                                    wt + (size_t)(MLP_XW + (l - 2) * MLP_H) * MLP_H, false, 0.5f);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         wt_fresh = true;
     }
