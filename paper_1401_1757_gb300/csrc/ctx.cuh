@@ -179,6 +179,8 @@ struct rsv_ctx {
     DevBuf d_partial, d_part2;
     DevBuf d_o_v0f, d_o_v0d, d_o_tot, d_o_pt, d_o_traj;   // staging for host outputs
     DevBuf d_nest_w, d_nest_ln, d_nest_rn, d_nest_d0, d_nest_plane, d_nest_mean, d_nest_kth, d_nest_all;
+    DevBuf d_nest_bm;            // Box-Muller tables of the inner-path generator (staged once)
+    bool nest_bm_ready = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaStream_t copy_stream = nullptr;   // device-to-host copies of V0 column blocks
     cudaEvent_t ev_block = nullptr;

@@ -16,7 +16,9 @@
 //
 // Random numbers: Philox4x32-10 (Salmon et al., SC'11), counter (k, c1, c2,
 // c3), key (seed lo, seed hi); step 2k takes words 0,1 and step 2k+1 words
-// 2,3 as uniforms (w + 1/2) 2^-32, Box-Muller in FP64.  Outer path o:
+// 2,3 as uniforms (w + 1/2) 2^-32, Box-Muller in FP64 (the inner paths
+// with table-driven logarithm, sine and cosine, and a series for the
+// month's discount factor: below.  Outer path o:
 // (k, o, 0, 2 << 24); inner path (o, n, i): (k, i, n, (3 << 24) | o).
 // Vasicek exact monthly step of (r, integral of r) (Glasserman 2004 3.3.1);
 // v = exp(-integral), FP64, stored in the form's plane format.
@@ -47,27 +49,103 @@ VasStep vasicek_step_constants(double a, double b, double sigma, double dt) {
     return s;
 }
 
-// One path: n_steps monthly steps from rate r; calls `emit(t, v_t)`.
+// Host tables of the Box-Muller step (see nested.cuh).
+const double2* bm_tables_host() {
+    static const std::vector<double2> t = [] {
+        std::vector<double2> v(BM_SC + BM_LG);
+        const long double two_pi = 6.283185307179586476925286766559005768L;
+        for (int j = 0; j < BM_SC; ++j) {
+            const long double x = two_pi * j / BM_SC;
+            v[j] = make_double2((double)std::sin(x), (double)std::cos(x));
+        }
+        for (int j = 0; j < BM_LG; ++j) {
+            const double c = 1.0 + (j + 0.5) / BM_LG;
+            const double inv = std::ldexp(std::nearbyint(std::ldexp(1.0 / c, 18)), -18);
+            const int k = j >= BM_LG_K0 ? 1 : 0;
+            v[BM_SC + j] = make_double2(inv, (double)(-std::log(std::ldexp((long double)inv, k))));
+        }
+        return v;
+    }();
+    return t.data();
+}
+
+constexpr double kLn2 = 0.6931471805599453094;
+constexpr double kTwoPi32 = 6.283185307179586477 / 4294967296.0;   // 2 pi 2^-32 (a power-of-two scaling of 2 pi)
+
+// ln u for the uniform u = (w + 1/2) 2^-32 by Tang's table-driven method in
+// FP64: w + 1/2 = 2^e y with y in [1, 2); interval j = the top 7 bits of y's
+// mantissa; r = y inv_j - 1 is exact (inv_j has 18 significant bits, y at
+// most 33) and |r| < 2^-8; ln u = (e + k_j - 32) ln 2 + L_j + log1p(r) with
+// L_j = -ln(2^k_j inv_j), k_j = 1 above sqrt 2, and log1p by its Taylor
+// series to r^7 (remainder below 2^-60 r).  For u >= 1 - 2^-8, where L_j and
+// log1p(r) would cancel, r = u - 1 (exact) and ln u = log1p(r).
+__device__ __forceinline__ double bm_log_u(uint32_t w, const double2* __restrict__ lg) {
+    const double m = (double)w + 0.5;
+    const int e = w ? 31 - __clz((int)w) : -1;
+    const double y = m * __longlong_as_double((long long)(1023 - e) << 52);
+    const int j = (int)((__double_as_longlong(y) >> 45) & (BM_LG - 1));
+    const double2 t = lg[j];
+    const bool near1 = w >= 0xFF000000u;
+    const double r = near1 ? __dmul_rn(__dadd_rn(m, -4294967296.0), 0x1.0p-32) : __fma_rn(y, t.x, -1.0);
+    double q = __fma_rn(r, 1.0 / 7.0, -1.0 / 6.0);
+    q = __fma_rn(r, q, 1.0 / 5.0);
+    q = __fma_rn(r, q, -0.25);
+    q = __fma_rn(r, q, 1.0 / 3.0);
+    q = __fma_rn(r, q, -0.5);
+    const double p = __fma_rn(__dmul_rn(r, r), q, r);
+    const int k = j >= BM_LG_K0 ? 1 : 0;
+    return near1 ? p : __fma_rn((double)(e + k - 32), kLn2, __dadd_rn(t.y, p));
+}
+
+// (sin, cos)(2 pi u) for u = (w + 1/2) 2^-32: the top 10 bits of w pick
+// alpha = 2 pi j / 1024 from the table, the rest give beta = 2 pi f with
+// 0 <= beta < 2 pi / 1024; sin beta and cos beta - 1 by their Taylor series
+// (to beta^5 and beta^6: remainders below 1e-19), then the addition theorems.
+__device__ __forceinline__ void bm_sincos_2pi_u(uint32_t w, const double2* __restrict__ sc, double& sn, double& cs) {
+    const double2 t = sc[w >> 22];
+    const double b = __dmul_rn(__dadd_rn((double)(w & 0x3FFFFFu), 0.5), kTwoPi32);
+    const double b2 = __dmul_rn(b, b);
+    const double sb = __fma_rn(__dmul_rn(b2, b), __fma_rn(b2, 1.0 / 120.0, -1.0 / 6.0), b);
+    const double cm1 = __dmul_rn(b2, __fma_rn(b2, __fma_rn(b2, -1.0 / 720.0, 1.0 / 24.0), -0.5));
+    sn = __fma_rn(t.y, sb, __fma_rn(t.x, cm1, t.x));
+    cs = __fma_rn(-t.x, sb, __fma_rn(t.y, cm1, t.y));
+}
+
+// e^x: |x| < 1/16 by its Taylor series to x^8 (remainder below 5e-17 relative;
+// a month's integrated rate is far inside), exp() beyond.
+__device__ __forceinline__ double bm_exp_small(double x) {
+    if (!(fabs(x) < 0.0625)) return exp(x);
+    double p = __fma_rn(x, 1.0 / 40320.0, 1.0 / 5040.0);
+    p = __fma_rn(x, p, 1.0 / 720.0);
+    p = __fma_rn(x, p, 1.0 / 120.0);
+    p = __fma_rn(x, p, 1.0 / 24.0);
+    p = __fma_rn(x, p, 1.0 / 6.0);
+    p = __fma_rn(x, p, 0.5);
+    p = __fma_rn(x, p, 1.0);
+    return __fma_rn(x, p, 1.0);
+}
+
+// One path: n_steps monthly steps from rate r; calls `emit(t, v_t)`.  `bm`
+// holds the Box-Muller tables (BM_SC sine/cosine entries, then BM_LG
+// logarithm entries).
 template <class Emit>
 __device__ __forceinline__ double vasicek_path(const VasStep& s, uint64_t seed, uint32_t c1, uint32_t c2,
-                                               uint32_t c3, double r, int n_steps, Emit emit) {
+                                               uint32_t c3, double r, int n_steps, const double2* __restrict__ bm,
+                                               Emit emit) {
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const double inv32 = 2.3283064365386963e-10;   // 2^-32
     for (int t = 0; t < n_steps; t += 2) {
         uint32_t w[4];
         philox4x32_10((uint32_t)(t >> 1), c1, c2, c3, k0, k1, w);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             if (t + h >= n_steps) break;
-            const double u1 = ((double)w[2 * h] + 0.5) * inv32;
-            const double u2 = ((double)w[2 * h + 1] + 0.5) * inv32;
-            const double R = sqrt(-2.0 * log(u1));
+            const double R = sqrt(-2.0 * bm_log_u(w[2 * h], bm + BM_SC));
             double sn, cs;
-            sincospi(2.0 * u2, &sn, &cs);
+            bm_sincos_2pi_u(w[2 * h + 1], bm, sn, cs);
             const double z1 = R * cs, z2 = R * sn;
             const double I = s.b * s.dt + (r - s.b) * s.k1 + s.l21 * z1 + s.l22 * z2;
             r = s.b + (r - s.b) * s.e + s.l11 * z1;
-            emit(t + h, exp(-I), r);
+            emit(t + h, bm_exp_small(-I), r);
         }
     }
     return r;
@@ -162,7 +240,10 @@ __device__ __forceinline__ float2 to_plane<float2>(double x) {
 template <class VE>
 __global__ void inner_paths_kernel(VasStep s, uint64_t seed, int o0, int B, int n_nodes, int n_inner, int i_pad,
                                    int Lmax, const int* __restrict__ Ln, const double* __restrict__ r_node,
-                                   VE* __restrict__ plane) {
+                                   const double2* __restrict__ bm_g, VE* __restrict__ plane) {
+    __shared__ double2 bm[BM_SC + BM_LG];   // 18 KiB: the Box-Muller tables
+    for (int k = threadIdx.x; k < BM_SC + BM_LG; k += blockDim.x) bm[k] = bm_g[k];
+    __syncthreads();
     const size_t total = (size_t)B * n_nodes * i_pad;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
@@ -177,7 +258,7 @@ __global__ void inner_paths_kernel(VasStep s, uint64_t seed, int o0, int B, int 
             continue;
         }
         vasicek_path(s, seed, (uint32_t)i, (uint32_t)n, (3u << 24) | (uint32_t)o, r_node[(size_t)o * n_nodes + n],
-                     L, [&](int t, double v, double) { base[(size_t)t * i_pad] = to_plane<VE>(v); });
+                     L, bm, [&](int t, double v, double) { base[(size_t)t * i_pad] = to_plane<VE>(v); });
     }
 }
 
@@ -373,18 +454,18 @@ cudaError_t launch_outer_paths(const VasStep& s, uint64_t seed, int n_outer, int
 }
 
 cudaError_t launch_inner_paths(int form, const VasStep& s, uint64_t seed, int o0, int B, int n_nodes, int n_inner,
-                               int i_pad, int Lmax, const int* Ln, const double* r_node, void* plane, int sm_count,
-                               cudaStream_t st) {
+                               int i_pad, int Lmax, const int* Ln, const double* r_node, const double2* bm,
+                               void* plane, int sm_count, cudaStream_t st) {
     const int grid = sm_count * 8;
     if (form == F_F64)
         inner_paths_kernel<double><<<grid, 128, 0, st>>>(s, seed, o0, B, n_nodes, n_inner, i_pad, Lmax, Ln, r_node,
-                                                          static_cast<double*>(plane));
+                                                          bm, static_cast<double*>(plane));
     else if (form == F_F32)
         inner_paths_kernel<float><<<grid, 128, 0, st>>>(s, seed, o0, B, n_nodes, n_inner, i_pad, Lmax, Ln, r_node,
-                                                         static_cast<float*>(plane));
+                                                         bm, static_cast<float*>(plane));
     else
         inner_paths_kernel<float2><<<grid, 128, 0, st>>>(s, seed, o0, B, n_nodes, n_inner, i_pad, Lmax, Ln, r_node,
-                                                          static_cast<float2*>(plane));
+                                                          bm, static_cast<float2*>(plane));
     return cudaGetLastError();
 }
 

@@ -30,9 +30,15 @@ int nested_tile_width(int form);
 cudaError_t launch_nested(int form, const NestedArgs& a, int sm_count, size_t smem, cudaStream_t st);
 cudaError_t launch_outer_paths(const VasStep& s, uint64_t seed, int n_outer, int n_nodes, int node_step, double r0,
                                double* r_node, double* d0, cudaStream_t st);
+// Tables of the inner-path generator's Box-Muller step (FP64): (sin, cos) of
+// 2 pi j / BM_SC for j < BM_SC, then for the BM_LG intervals of the logarithm
+// (1/c_j to 18 significant bits, -ln(2^k_j / c_j)); built once on the host.
+constexpr int BM_SC = 1024, BM_LG = 128;
+constexpr int BM_LG_K0 = 53;   // first interval whose centre 1 + (j + 1/2)/128 exceeds sqrt 2
+const double2* bm_tables_host();   // BM_SC + BM_LG entries
 cudaError_t launch_inner_paths(int form, const VasStep& s, uint64_t seed, int o0, int B, int n_nodes, int n_inner,
-                               int i_pad, int Lmax, const int* Ln, const double* r_node, void* plane, int sm_count,
-                               cudaStream_t st);
+                               int i_pad, int Lmax, const int* Ln, const double* r_node, const double2* bm,
+                               void* plane, int sm_count, cudaStream_t st);
 // The curve mode with the outer paths on the lanes (planes [n_nodes][Lmax][o_pad])
 // and the transpose of its [n_nodes][n_outer] liabilities to [n_outer][n_nodes].
 cudaError_t launch_curve_planes_lanes(int form, double a, double b, double sigma, int n_outer, int n_nodes, int o_pad,

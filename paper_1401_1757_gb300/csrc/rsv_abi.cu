@@ -1014,10 +1014,17 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
         else CU(cudaMemsetAsync(Lt, 0, (size_t)NN * NO * sizeof(double), c->stream));
         CU(launch_transpose_on(Lt, NO, NN, Lall, c->stream));
     }
+    if (!sur && !curve && !c->nest_bm_ready) {   // the generator's tables: once per context (static host copy)
+        CU(c->d_nest_bm.ensure((size_t)(BM_SC + BM_LG) * sizeof(double2)));
+        CU(cudaMemcpyAsync(c->d_nest_bm.p, bm_tables_host(), (size_t)(BM_SC + BM_LG) * sizeof(double2),
+                           cudaMemcpyHostToDevice, c->stream));
+        c->nest_bm_ready = true;
+    }
     for (int o0 = 0; o0 < NO && !sur && !curve; o0 += B) {
         const int Bc = std::min(B, NO - o0);
         CU(launch_inner_paths(form, vs, sp->seed, o0, Bc, NN, n_inner, i_pad, Lmax, c->d_nest_ln.as<int>(),
-                              c->d_nest_rn.as<double>(), c->d_nest_plane.p, c->sm_count, c->stream));
+                              c->d_nest_rn.as<double>(), c->d_nest_bm.as<double2>(), c->d_nest_plane.p, c->sm_count,
+                              c->stream));
         const long long items = (long long)NN * Bc * a.n_chunks;
         if (items > 0x7fffffffLL) return fail(c, RSV_E_ARG, "too many nested work items");
         a.B = Bc;
@@ -1086,7 +1093,7 @@ rsv_status rsv_destroy(rsv_ctx* c) try {
                       &c->sur.d_y, &c->sur.d_X, &c->sur.d_pred, &c->sur.d_err, &c->sur.d_aux, &c->sur.d_curve,
                       &c->sur.d_comm, &c->sur.d_lnb, &c->d_tabf[0], &c->d_tabf[1], &c->d_tabf[2], &c->d_vf64,
                       &c->d_vf32, &c->d_vf2, &c->d_cf64, &c->d_cf32, &c->d_ml_rec,
-                      &c->d_ml_amount, &c->sur.d_cnt, &c->sur.d_q2, &c->sur.d_idx, &c->sur.d_v2})
+                      &c->d_ml_amount, &c->sur.d_cnt, &c->sur.d_q2, &c->sur.d_idx, &c->sur.d_v2, &c->d_nest_bm})
         b->release();
     c->mlp.release();
     if (c->ev0) cudaEventDestroy(c->ev0);
