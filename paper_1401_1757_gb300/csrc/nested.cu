@@ -133,6 +133,7 @@ __device__ __forceinline__ double vasicek_path(const VasStep& s, uint64_t seed, 
                                                uint32_t c3, double r, int n_steps, const double2* __restrict__ bm,
                                                Emit emit) {
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const double bdt = s.b * s.dt;
     for (int t = 0; t < n_steps; t += 2) {
         uint32_t w[4];
         philox4x32_10((uint32_t)(t >> 1), c1, c2, c3, k0, k1, w);
@@ -143,8 +144,9 @@ __device__ __forceinline__ double vasicek_path(const VasStep& s, uint64_t seed, 
             double sn, cs;
             bm_sincos_2pi_u(w[2 * h + 1], bm, sn, cs);
             const double z1 = R * cs, z2 = R * sn;
-            const double I = s.b * s.dt + (r - s.b) * s.k1 + s.l21 * z1 + s.l22 * z2;
-            r = s.b + (r - s.b) * s.e + s.l11 * z1;
+            const double dr = r - s.b;
+            const double I = __fma_rn(s.l22, z2, __fma_rn(s.l21, z1, __fma_rn(dr, s.k1, bdt)));
+            r = __fma_rn(s.l11, z1, __fma_rn(dr, s.e, s.b));
             emit(t + h, bm_exp_small(-I), r);
         }
     }
