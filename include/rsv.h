@@ -566,6 +566,20 @@ rsv_status rsv_surrogate_query(rsv_ctx *ctx, const rsv_query *queries, int64_t n
  * Errors: RSV_E_TIMEOUT (as described), RSV_E_NOMEM, RSV_E_CUDA. */
 rsv_status rsv_selftest_bounded_wait(int32_t device, void *cuda_stream, int32_t never_completes);
 
+/* The nested valuation's inner-path generator evaluates its FP64 functions by
+ * its own table-driven methods (Tang's logarithm; sine and cosine from a
+ * 1,024-entry table and the addition theorems; a series for e^x with
+ * |x| < 1/16, exp() beyond).  This entry point runs those device functions on
+ * given draws so that tests can compare them with a reference library: for
+ * i < n, with u_i = (w[i] + 1/2) 2^-32, out[4 i] = ln u_i,
+ * out[4 i + 1] = sin(2 pi u_i), out[4 i + 2] = cos(2 pi u_i) and
+ * out[4 i + 3] = e^{x[i]}.  w: n 32-bit draws, x: n doubles, out: 4 n doubles;
+ * all host memory owned by the caller.  Blocks until done.
+ * Errors: RSV_E_ARG (n < 0, or a null pointer with n > 0), RSV_E_NOMEM,
+ * RSV_E_CUDA. */
+rsv_status rsv_selftest_generator_math(int32_t device, void *cuda_stream, const uint32_t *w, const double *x,
+                                       int64_t n, double *out);
+
 /* Measured fused multiply-add throughput of `device` in TFLOP/s (2 flop per
  * FMA): FP32 (fp64 = 0) or FP64 (fp64 = 1), from a kernel of independent FMA
  * chains filling every SM, best of five timed launches on `cuda_stream`.  It

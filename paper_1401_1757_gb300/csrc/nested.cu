@@ -29,6 +29,8 @@
 
 #include "nested.cuh"
 #include "philox.cuh"
+#include "rsv.h"
+#include "abi_guard.cuh"
 
 namespace rsv {
 
@@ -471,6 +473,22 @@ cudaError_t launch_inner_paths(int form, const VasStep& s, uint64_t seed, int o0
     return cudaGetLastError();
 }
 
+// The generator's functions on given draws (a test entry point).
+__global__ void generator_math_kernel(const uint32_t* __restrict__ w, const double* __restrict__ x, long long n,
+                                      const double2* __restrict__ bm_g, double* __restrict__ out) {
+    __shared__ double2 bm[BM_SC + BM_LG];
+    for (int k = threadIdx.x; k < BM_SC + BM_LG; k += blockDim.x) bm[k] = bm_g[k];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double sn, cs;
+        bm_sincos_2pi_u(w[i], bm, sn, cs);
+        out[4 * i] = bm_log_u(w[i], bm + BM_SC);
+        out[4 * i + 1] = sn;
+        out[4 * i + 2] = cs;
+        out[4 * i + 3] = bm_exp_small(x[i]);
+    }
+}
+
 cudaError_t launch_curve_planes_lanes(int form, double a, double b, double sigma, int n_outer, int n_nodes, int o_pad,
                                       int Lmax, const int* Ln, const double* r_node, void* plane, int sm_count,
                                       cudaStream_t st) {
@@ -503,3 +521,38 @@ cudaError_t launch_node_stats(const double* L_all, int n_on, int n_inner, int k,
 }
 
 }  // namespace rsv
+
+extern "C" rsv_status rsv_selftest_generator_math(int32_t device, void* cuda_stream, const uint32_t* w, const double* x,
+                                                  int64_t n, double* out) try {
+    if (n < 0 || (n > 0 && (!w || !x || !out))) return RSV_E_ARG;
+    if (n == 0) return RSV_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaSetDevice(device) != cudaSuccess) return RSV_E_CUDA;
+    uint32_t* dw = nullptr;
+    double *dx = nullptr, *dout = nullptr;
+    double2* dbm = nullptr;
+    const size_t nb = (size_t)(rsv::BM_SC + rsv::BM_LG) * sizeof(double2);
+    rsv_status rc = RSV_OK;
+    if (cudaMalloc(&dw, (size_t)n * 4) != cudaSuccess || cudaMalloc(&dx, (size_t)n * 8) != cudaSuccess ||
+        cudaMalloc(&dout, (size_t)n * 32) != cudaSuccess || cudaMalloc(&dbm, nb) != cudaSuccess) {
+        rc = RSV_E_NOMEM;
+    } else if (cudaMemcpyAsync(dw, w, (size_t)n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+               cudaMemcpyAsync(dx, x, (size_t)n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+               cudaMemcpyAsync(dbm, rsv::bm_tables_host(), nb, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        rc = RSV_E_CUDA;
+    } else {
+        const int grid = (int)std::min<long long>((n + 127) / 128, 1024);
+        rsv::generator_math_kernel<<<grid, 128, 0, st>>>(dw, dx, n, dbm, dout);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(out, dout, (size_t)n * 32, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = RSV_E_CUDA;
+    }
+    cudaFree(dw);
+    cudaFree(dx);
+    cudaFree(dout);
+    cudaFree(dbm);
+    return rc;
+} catch (...) {
+    return rsv::host_error(nullptr);
+}

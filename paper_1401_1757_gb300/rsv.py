@@ -115,7 +115,7 @@ _lib = None
 EXPORTS = ["rsv_create", "rsv_destroy", "rsv_set_stream", "rsv_load_decrements", "rsv_load_portfolio",
            "rsv_load_decrements_fraction", "rsv_load_scenarios_fraction", "rsv_load_cashflows", "rsv_load_schedules",
            "rsv_clear_cashflows", "rsv_compute_mlife", "rsv_surrogate_save", "rsv_surrogate_load",
-           "rsv_selftest_bounded_wait",
+           "rsv_selftest_bounded_wait", "rsv_selftest_generator_math",
            "rsv_load_scenarios", "rsv_compute_reserves", "rsv_compute_nested", "rsv_variant_count", "rsv_variant_name",
            "rsv_tune", "rsv_synchronize", "rsv_last_error", "rsv_last_kernel_ms", "rsv_device_sm_count",
            "rsv_reserves_noalloc", "rsv_mlp_param_count", "rsv_mlp_init", "rsv_mlp_set_params",
@@ -152,6 +152,7 @@ def load_library(path: str = LIB_PATH):
         "rsv_compute_mlife": ([vp, vp, i64, C.POINTER(rsv_opts), C.POINTER(rsv_out)], i32),
         "rsv_surrogate_save": ([vp, C.c_char_p], i32),
         "rsv_selftest_bounded_wait": ([i32, vp, i32], i32),
+        "rsv_selftest_generator_math": ([i32, vp, vp, vp, i64, vp], i32),
         "rsv_surrogate_load": ([vp, C.c_char_p], i32),
         "rsv_compute_reserves": ([vp, C.POINTER(rsv_opts), C.POINTER(rsv_out)], i32),
         "rsv_compute_nested": ([vp, C.POINTER(rsv_opts), C.POINTER(rsv_nested_spec), C.POINTER(rsv_nested_out)],
@@ -347,6 +348,21 @@ def rsv_selftest_bounded_wait(device: int = 0, stream=None, never_completes: boo
     """Run the bounded-wait self-test; returns the status code (RSV_OK or RSV_E_TIMEOUT)."""
     return load_library().rsv_selftest_bounded_wait(device, getattr(stream, "cuda_stream", stream),
                                                     1 if never_completes else 0)
+
+
+def rsv_selftest_generator_math(w, x, device: int = 0, stream=None):
+    """The inner-path generator's ln u, sin 2 pi u, cos 2 pi u (u = (w + 1/2) 2^-32)
+    and e^x on the device; returns an (n, 4) float64 array."""
+    w = np.ascontiguousarray(w, dtype=np.uint32)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if w.shape != x.shape or w.ndim != 1:
+        raise ValueError("w and x must be 1-D arrays of the same length")
+    out = np.empty((len(w), 4), dtype=np.float64)
+    st = load_library().rsv_selftest_generator_math(device, getattr(stream, "cuda_stream", stream), w.ctypes.data,
+                                                    x.ctypes.data, len(w), out.ctypes.data)
+    if st != RSV_OK:
+        raise RsvError(st, f"rsv_selftest_generator_math failed ({st})")
+    return out
 
 
 def rsv_probe_fma_peak(device: int = 0, stream=None, fp64: bool = False) -> float:

@@ -201,3 +201,31 @@ def test_nested_two_life_products_against_oracle(ctx):
             worst = max(worst, float(np.max(np.abs(out["L_all"][o, n] - L) / np.abs(L))))
     print(f"nested two-life products: max rel err {worst:.3e}")
     assert worst <= 1e-6
+
+
+def test_generator_math_against_libm():
+    """The inner-path generator's own FP64 logarithm, sine, cosine (table-driven)
+    and exponential series against NumPy's libm: random draws plus both ends of
+    (0, 1), the table boundaries and the switch to log1p(u - 1) near u = 1."""
+    rng = np.random.default_rng(11)
+    w = np.concatenate([rng.integers(0, 2**32, 200_000, dtype=np.uint64),
+                        np.arange(2**32 - 4096, 2**32), np.arange(0xFF000000 - 2048, 0xFF000000 + 2048),
+                        np.arange(0, 4096), np.arange(2**22 - 8, 2**22 + 8), (np.arange(1024) << 22),
+                        (np.arange(1024) << 22) + 0x3FFFFF]).astype(np.uint32)
+    x = np.concatenate([rng.uniform(-0.0625, 0.0625, len(w) - 4000), rng.uniform(-3.0, 3.0, 4000)])
+    out = rsv.rsv_selftest_generator_math(w, x)
+    u = (w.astype(np.float64) + 0.5) / 2.0**32
+    ln_ref = np.log(u)
+    rel_ln = np.abs(out[:, 0] - ln_ref) / np.abs(ln_ref)
+    ang = 2.0 * np.pi * u   # rounded angle: the reference itself is off by up to ~4 pi 2^-53
+    err_sin = np.abs(out[:, 1] - np.sin(ang))
+    err_cos = np.abs(out[:, 2] - np.cos(ang))
+    rel_exp = np.abs(out[:, 3] - np.exp(x)) / np.exp(x)
+    print(f"generator math: ln {rel_ln.max():.2e} rel, sin {err_sin.max():.2e}, cos {err_cos.max():.2e} abs, "
+          f"exp {rel_exp.max():.2e} rel")
+    assert rel_ln.max() <= 1e-15
+    assert max(err_sin.max(), err_cos.max()) <= 2e-15
+    assert rel_exp.max() <= 1e-15
+    assert np.allclose(out[:, 1] ** 2 + out[:, 2] ** 2, 1.0, rtol=0, atol=1e-15)
+    assert rsv.load_library().rsv_selftest_generator_math(0, None, None, None, 5, None) == rsv.RSV_E_ARG
+    assert rsv.rsv_selftest_generator_math(np.zeros(0, np.uint32), np.zeros(0)).shape == (0, 4)
