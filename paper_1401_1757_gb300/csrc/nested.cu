@@ -113,20 +113,6 @@ __device__ __forceinline__ void bm_sincos_2pi_u(uint32_t w, const double2* __res
     cs = __fma_rn(-t.x, sb, __fma_rn(t.y, cm1, t.y));
 }
 
-// e^x: |x| < 1/16 by its Taylor series to x^8 (remainder below 5e-17 relative;
-// a month's integrated rate is far inside), exp() beyond.
-__device__ __forceinline__ double bm_exp_small(double x) {
-    if (!(fabs(x) < 0.0625)) return exp(x);
-    double p = __fma_rn(x, 1.0 / 40320.0, 1.0 / 5040.0);
-    p = __fma_rn(x, p, 1.0 / 720.0);
-    p = __fma_rn(x, p, 1.0 / 120.0);
-    p = __fma_rn(x, p, 1.0 / 24.0);
-    p = __fma_rn(x, p, 1.0 / 6.0);
-    p = __fma_rn(x, p, 0.5);
-    p = __fma_rn(x, p, 1.0);
-    return __fma_rn(x, p, 1.0);
-}
-
 // One path: n_steps monthly steps from rate r; calls `emit(t, v_t)`.  `bm`
 // holds the Box-Muller tables (BM_SC sine/cosine entries, then BM_LG
 // logarithm entries).
@@ -149,7 +135,7 @@ __device__ __forceinline__ double vasicek_path(const VasStep& s, uint64_t seed, 
             const double dr = r - s.b;
             const double I = __fma_rn(s.l22, z2, __fma_rn(s.l21, z1, __fma_rn(dr, s.k1, bdt)));
             r = __fma_rn(s.l11, z1, __fma_rn(dr, s.e, s.b));
-            emit(t + h, bm_exp_small(-I), r);
+            emit(t + h, exp_small(-I), r);
         }
     }
     return r;
@@ -485,7 +471,7 @@ __global__ void generator_math_kernel(const uint32_t* __restrict__ w, const doub
         out[4 * i] = bm_log_u(w[i], bm + BM_SC);
         out[4 * i + 1] = sn;
         out[4 * i + 2] = cs;
-        out[4 * i + 3] = bm_exp_small(x[i]);
+        out[4 * i + 3] = exp_small(x[i]);
     }
 }
 

@@ -235,6 +235,8 @@ __device__ __forceinline__ double sur_recurrence_df(const PolSur& P, const float
     return df_to_double(V);
 }
 
+constexpr int kFallbackChunk = 4096;   // queries compacted per pass of the fallback kernel
+
 // The fallback of the nested valuation: the queries of one (outer path, node)
 // share its short rate, so each block builds that curve once in shared memory
 // (Lmax months, FP64 then split hi/lo) and values the segment's flagged
@@ -243,21 +245,54 @@ __global__ void sur_fallback_nodes_kernel(const PolSur* __restrict__ pols, const
                                           int tab_pad, const double2* __restrict__ curve,
                                           const SurQuery* __restrict__ qs, const long long* __restrict__ seg, int Lmax,
                                           const unsigned char* __restrict__ flag, double* __restrict__ V) {
-    extern __shared__ float2 vcur[];
+    extern __shared__ float2 fb_smem[];
+    float2* vcur = fb_smem;                                     // the segment's curve, Lmax months
+    int* list = reinterpret_cast<int*>(fb_smem + Lmax);         // flagged queries of a chunk
+    __shared__ int n_list, warp_off[32];
     const long long b = seg[blockIdx.x], e = seg[blockIdx.x + 1];
     if (b == e) return;
     const double r = qs[b].r;
     for (int t = threadIdx.x; t < Lmax; t += blockDim.x) {
         const double2 dc = curve[t];
-        const double x = exp(dc.x - dc.y * r);
+        const double x = exp_small(dc.x - dc.y * r);
         const float h = __double2float_rn(x);
         vcur[t] = make_float2(h, __double2float_rn(x - (double)h));
     }
-    __syncthreads();
-    for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
-        const SurQuery Q = qs[i];
-        if (Q.state < 0 || !flag[Q.bucket]) continue;
-        V[i] = sur_recurrence_df(pols[Q.pol], tab, tab_pad, Q, vcur);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // Only the flagged queries (a fifth or so) run a recurrence: compact them
+    // first (in query order, kFallbackChunk at a time), so that every lane has one.
+    for (long long c0 = b; c0 < e; c0 += kFallbackChunk) {
+        const long long c1 = c0 + kFallbackChunk < e ? c0 + kFallbackChunk : e;
+        if (threadIdx.x == 0) n_list = 0;
+        __syncthreads();
+        for (long long base = c0; base < c1; base += blockDim.x) {
+            const long long i = base + threadIdx.x;
+            bool f = false;
+            if (i < c1) {
+                const SurQuery Q = qs[i];
+                f = Q.state >= 0 && flag[Q.bucket];
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, f);
+            if (lane == 0) warp_off[wid] = __popc(m);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int acc = n_list;
+                for (int w = 0; w < nw; ++w) {
+                    const int c = warp_off[w];
+                    warp_off[w] = acc;
+                    acc += c;
+                }
+                n_list = acc;
+            }
+            __syncthreads();
+            if (f) list[warp_off[wid] + __popc(m & ((1u << lane) - 1u))] = (int)(i - c0);
+            __syncthreads();
+        }
+        for (int k = threadIdx.x; k < n_list; k += blockDim.x) {
+            const long long i = c0 + list[k];
+            V[i] = sur_recurrence_df(pols[qs[i].pol], tab, tab_pad, qs[i], vcur);
+        }
+        __syncthreads();
     }
 }
 
@@ -780,7 +815,7 @@ rsv_status sur_value_queries(rsv_ctx* c, const rsv_query* dq, long long n, const
     if ((st = sur_tables(c, T)) != RSV_OK) return st;
     size_t smem_c;
     if ((st = build_tables(c, F_COMP, smem_c)) != RSV_OK) return st;   // the compensated entries, same padding
-    sur_fallback_nodes_kernel<<<n_seg, 256, (size_t)Lmax * sizeof(float2), c->stream>>>(
+    sur_fallback_nodes_kernel<<<n_seg, 256, (size_t)Lmax * sizeof(float2) + kFallbackChunk * sizeof(int), c->stream>>>(
         c->d_pols.as<PolSur>(), c->d_tab[F_COMP].as<float4>(), c->tab_pad_of[F_COMP], T.curve, q, seg, Lmax,
         s.d_flag.as<unsigned char>(), V);
     CU(cudaGetLastError());
