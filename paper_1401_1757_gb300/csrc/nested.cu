@@ -27,6 +27,7 @@
 #include <cstring>
 #include <vector>
 
+#include "fp64_series.cuh"
 #include "nested.cuh"
 #include "philox.cuh"
 #include "rsv.h"

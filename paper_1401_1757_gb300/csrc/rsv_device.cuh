@@ -232,18 +232,4 @@ __device__ __forceinline__ bool stage_to_smem(void* dst, const void* src, uint32
     return ok;
 }
 
-// e^x in FP64: |x| < 1/16 by its Taylor series to x^8 (remainder below 5e-17
-// relative; a month's integrated rate is far inside), exp() beyond.
-__device__ __forceinline__ double exp_small(double x) {
-    if (!(fabs(x) < 0.0625)) return exp(x);
-    double p = __fma_rn(x, 1.0 / 40320.0, 1.0 / 5040.0);
-    p = __fma_rn(x, p, 1.0 / 720.0);
-    p = __fma_rn(x, p, 1.0 / 120.0);
-    p = __fma_rn(x, p, 1.0 / 24.0);
-    p = __fma_rn(x, p, 1.0 / 6.0);
-    p = __fma_rn(x, p, 0.5);
-    p = __fma_rn(x, p, 1.0);
-    return __fma_rn(x, p, 1.0);
-}
-
 }  // namespace rsv

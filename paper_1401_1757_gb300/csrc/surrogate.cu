@@ -22,6 +22,7 @@
 #include "abi_guard.cuh"
 #include "philox.cuh"
 #include "surrogate.cuh"
+#include "fp64_series.cuh"
 
 namespace rsv {
 
