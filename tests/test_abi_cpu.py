@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_1401_1757_gb300 import _build, rsv
@@ -61,3 +62,19 @@ def test_null_arguments_are_rejected_without_gpu(lib_path):
     assert lib.rsv_destroy(None) == rsv.RSV_OK
     assert lib.rsv_load_portfolio(None, None, 0) == rsv.RSV_E_ARG
     assert lib.rsv_compute_reserves(None, None, None) == rsv.RSV_E_ARG
+
+
+def test_generator_math_selftest_arguments_without_gpu(lib_path):
+    """The generator-math test entry point checks its arguments before any CUDA
+    call: a negative count or missing buffers are RSV_E_ARG, an empty call is a
+    no-op (the device functions themselves are checked in the GPU tests)."""
+    lib = rsv.load_library(lib_path)
+    buf = np.zeros(8)
+    w = np.zeros(2, np.uint32)
+    assert lib.rsv_selftest_generator_math(0, None, None, None, -1, None) == rsv.RSV_E_ARG
+    assert lib.rsv_selftest_generator_math(0, None, None, buf.ctypes.data, 2, buf.ctypes.data) == rsv.RSV_E_ARG
+    assert lib.rsv_selftest_generator_math(0, None, w.ctypes.data, None, 2, buf.ctypes.data) == rsv.RSV_E_ARG
+    assert lib.rsv_selftest_generator_math(0, None, w.ctypes.data, buf.ctypes.data, 2, None) == rsv.RSV_E_ARG
+    assert lib.rsv_selftest_generator_math(0, None, None, None, 0, None) == rsv.RSV_OK
+    with pytest.raises(ValueError):
+        rsv.rsv_selftest_generator_math(np.zeros(3, np.uint32), np.zeros(2))
