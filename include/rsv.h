@@ -446,9 +446,12 @@ rsv_status rsv_reserves_noalloc(int device, void *cuda_stream, const rsv_policy 
  * (Eq. basicReserveSummation).  The surrogate is a perceptron
  * 32 -> 256 -> 256 -> 256 -> 256 -> 1 with GELU (tanh form), BF16 weights and
  * activations and FP32 accumulation on the tensor cores, FP32 master weights
- * and Adam; it predicts ln(reserve per unit amount) from 16 features (product
- * and state one-hot, ages, reversion, remaining term, rate, ln amount and
- * three products of them; zero-padded to 32).  The parameters are one flat
+ * and Adam; it predicts ln(reserve per unit amount) minus the ln of a
+ * commutation-function base value, from 19 feature slots zero-padded to 32:
+ * product one-hot (4), state one-hot (3), the two ages, the reversion, the
+ * remaining term, the node rate, ln amount, age^2, term^2, rate x term,
+ * ln(1 + remaining months), the ln base value and the flat yield it is taken
+ * at.  The parameters are one flat
  * FP32 vector: W1 [32][256], b1 [256], W2 [256][256], b2, W3, b3, W4, b4
  * (each W row-major [in][out]), w5 [256], b5 [1]. */
 int64_t rsv_mlp_param_count(void);
