@@ -88,9 +88,30 @@ enum {
 enum {
     RSV_FORM_F64 = 0,      /* plain FP64 on the GPU                                  */
     RSV_FORM_F32 = 1,      /* plain FP32                                              */
-    RSV_FORM_F32_COMP = 2  /* FP32 with compensated (double-float) accumulation and
+    RSV_FORM_F32_COMP = 2, /* FP32 with compensated (double-float) accumulation and
                               hi/lo-split inputs                                      */
+    RSV_FORM_F32_DEFLATED = 3 /* the recurrence in deflated units, compensated FP32:
+                              see below                                               */
 };
+
+/* RSV_FORM_F32_DEFLATED.  Eq. (generalForm) multiplied at step t by the
+ * deflator G_t = D_t l_{x+t} / l_x (D_t = v_0 ... v_{t-1}, the discount-factor
+ * product to the start of step t; l the life table {l_{x+t}} of Section 5)
+ * becomes U_t = U_{t+1} + G_{t+1} c_t with U = G r: the same backward
+ * substitution (Section 3.8.2) whose multiplicative factor is 1 at every
+ * step, and r_0 = U_0.  The discount products D are FP64 running products, one
+ * per scenario, computed on the device in every call; the life tables are
+ * built once in FP64 on the host; each chain-step is one FP32 fused
+ * multiply-add, summed in FP32 over 8 steps and folded every 16 steps into a
+ * double-float.  Every reserve is within about 14 x 2^-24 (8.3e-7) relative
+ * of its value on the FP64 inputs, whatever the projection length.  Products
+ * RSV_SL_ANNUITY .. RSV_LAST_SURVIVOR (the reversionary and last-survivor
+ * annuities through the reversionary identity of Section 4.2.1, every
+ * valuation state); outputs RSV_OUT_V0 and RSV_OUT_SCEN_TOTAL; payment at the
+ * end of the step; level cash flows.  Other requests return RSV_E_ARG (a
+ * product, output or payment it does not take; tables whose survival falls
+ * below 2^-220 or that need more shared memory than the device has) or
+ * RSV_E_STATE (a cash-flow sequence loaded). */
 
 /* rsv_opts.outputs bits */
 enum {

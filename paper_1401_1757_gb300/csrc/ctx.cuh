@@ -185,7 +185,11 @@ struct rsv_ctx {
     cudaStream_t copy_stream = nullptr;   // device-to-host copies of V0 column blocks
     cudaEvent_t ev_block = nullptr;
     bool ev_recorded = false;
-    int tuned[3] = {-1, -1, -1};
+    int tuned[4] = {-1, -1, -1, -1};
+    // the deflated form: super-tile slots, life tables, deflator plane
+    DevBuf d_defl_slots, d_defl_kinds, d_defl_tab, d_defl_plane;
+    unsigned long long defl_lay_key = 0, defl_tab_key = 0;
+    int defl_W = -1, defl_n_st = 0, defl_dpad = 0, defl_n_tab = 0;
     // surrogate network and its data
     rsv::Mlp mlp;
     bool mlp_ready = false;
@@ -219,6 +223,11 @@ rsv_status build_tables(rsv_ctx* c, int form, size_t& smem);
 // The first n_tab loaded tables, pad entries each, in a form's entry format
 // on the device (cached by shape and table generation); smem = their bytes.
 rsv_status stage_tables(rsv_ctx* c, int form, int pad, int n_tab, size_t& smem);
+// rsv_compute_reserves in the deflated form (defl_abi.cu); opts checked by the caller
+rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out);
+// Per-scenario totals from per-tile (row) partial sums [n_rows][s_pad], in a
+// fixed order (rsv_abi.cu).
+rsv_status scenario_totals(rsv_ctx* c, const double* partial, int n_rows, int s_pad, int n_scen, double* tot);
 
 #define CU(call)                                                                                \
     do {                                                                                        \

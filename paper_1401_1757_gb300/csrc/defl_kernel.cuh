@@ -1,0 +1,514 @@
+// defl_kernel.cuh -- the backward recurrence in deflated units (compensated FP32).
+//
+// Multiply the reserve of Eq. (generalForm) at step t by the deflator
+// G_t = D_t l_{x+t} / l_x, the product of the discount factors of the steps
+// before t (D_t = v_0 ... v_{t-1}) and the survival to t.  For the reduced
+// one-state models (Section 3.6.4, Section 4.1) r_t = v_t p_t (c + r_{t+1})
+// becomes
+//     U_t = U_{t+1} + c G_{t+1},        U = G r,  U_S = G_S r_S,
+// the same backward substitution (Section 3.8.2) with the multiplicative
+// factor of every step equal to 1.  The reserve at valuation is r_0 = U_0.
+// G splits into a scenario part and a policy part: D_{t+1} is one FP64
+// running product per scenario (the discount-factor products over long
+// terms, computed once per scenario by defl_plane_kernel) and l_{x+t+1} /
+// l_x comes from the life table {l_k} (Section 5 computes it per policy; here
+// it is one table, built once in FP64).  A chain-step is one FP32 fused
+// multiply-add of the two; no rounding compounds along the chain, because no
+// rounded value is ever multiplied by the next step's factor.
+//
+// The weights w_t = D_{t+1} E_t, with E_t the policy's expected cash flow at
+// the end of step t per unit amount:
+//   K_ANN   l_{x+t+1}                                     (Section 4.1.1)
+//   K_ASS   l_{x+t} q_{x+t}  (deaths in the step),  U_S = D_S l_{x+S} bnd
+//                                                          (Sections 4.1.2-4.1.3)
+//   K_ANN2  P^x P^y, P^x = l^x_{x+t+1}/l^x_x, P^y = l^y_{y+t+1}/l^y_y  (joint life, Section 4.2)
+//   K_JL    P^x + P^y (1 - P^x) with P^x = l^x_{x+t+1}/l^x_x, P^y = rho l^y_{y+t+1}/l^y_y
+//           in state 00; P^y = 0 in state 01 and P^x = 0 in state 10
+//           (c = (1, 1, rho) of the reversionary annuity, Section 4.2.1:
+//           r00 = a_x + rho (a_y - a_xy) is the sum of these weights).
+// K_ANN and K_ASS carry the factor 1 / l_x in the per-policy scale applied at
+// the end.  The tables are normalised to l_0 = 2^100, so that every ratio
+// down to 2^-220 stays in FP32's normal range.
+//
+// Accumulation.  Terms are added in FP32 by fused multiply-adds into two
+// accumulators (alternate steps), each taking 8 terms; every 16 steps their
+// sum is folded into a double-float (h, l) by an ordered Fast2Sum, whose
+// error term is exact.  An FP32 sum of 8 positive terms is within 8 u of its
+// value (u = 2^-24), the two-accumulator add adds u, the inputs D and E are
+// rounded once each (and E of the JL product up to 3 u), so every reserve is
+// within about 14 u = 8.3e-7 of the value the exact arithmetic gives on the
+// FP64 inputs, whatever the projection length; the errors are independent
+// roundings, so typical errors are far smaller.
+//
+// Mapping.  A work item is a super-tile of NW tiles of P policies (the tiles
+// of one reduced model, consecutive in decreasing-length order) times one
+// chunk of 32 M scenarios; a CTA of NW warps takes one item, warp w the
+// policies [w P, (w+1) P) of the super-tile, lane l the scenarios
+// chunk + m 32 + l (m < M).  The deflator plane is read in blocks of 32
+// steps: each block of the chunk is staged into shared memory by TMA bulk
+// copies, NBUF blocks in flight, completing on one mbarrier per buffer
+// (bounded waits, agreed on by the whole CTA).  The life tables are staged
+// once per CTA, as four copies shifted by one entry, so that four
+// consecutive steps of any policy are one aligned 16-byte shared-memory load.
+// Items come from an atomic queue in decreasing-cost order; thread 0 claims
+// them ahead of use, so the staging of the next item overlaps this one.
+#pragma once
+
+#include "rsv_device.cuh"
+
+namespace rsv {
+
+constexpr int DEFL_KB = 32;        // steps per staged block of the deflator plane
+constexpr int DEFL_G = DEFL_KB / 4; // float4 rows (groups of four steps) per block
+
+// One policy slot of a deflated super-tile (64 bytes).  All lanes of a warp
+// read the same slot.
+struct DeflSlot {
+    int32_t off1;    // float4 index of life 1's run in the staged main array (A or deaths)
+    int32_t off2;    // float4 index of life 2's run in A (K_JL, K_ANN2)
+    int32_t S;       // steps; padding slots repeat a shape with pol = -1
+    int32_t pol;     // portfolio index, -1 = padding
+    float ix, iy;    // K_JL: 1/l_x and rho/l_y of the valuation state (0 where a life is dead);
+                     // K_ANN2: 1/l_x and 1/l_y
+    float mat;       // deflated boundary weight bnd * l_{x+S} (endowments), else 0
+    int32_t kind;
+    double scale;    // V0 = scale * U: amount / l_x (K_ANN, K_ASS) or amount (K_JL, K_ANN2)
+    float sc_h, sc_l;// scale as an FP32 head and tail
+    int32_t pad[4];
+};
+static_assert(sizeof(DeflSlot) == 64, "DeflSlot layout");
+
+struct DeflArgs {
+    const float* tab;        // staged tables: [2 arrays (A, deaths)][n_tab][4 shifted copies][dpad]
+    int32_t tab_bytes;       // bytes to stage (multiple of 16)
+    const float4* D;         // deflator plane [n_groups][s_pad]: D_{t+1} for t = 4g .. 4g+3
+    int32_t s_pad;           // row length of the plane (scenarios, multiple of 128)
+    int32_t n_scen;          // valid scenario columns from the plane's first column
+    int32_t n_groups;        // rows of the plane (a multiple of DEFL_G)
+    const DeflSlot* slots;   // [n_st][W] (W = NW * P), super-tiles in decreasing cost order
+    const int32_t* st_kind;  // [n_st]
+    int32_t n_st;
+    int32_t n_chunks;        // scenario chunks of 32 M
+    int32_t n_items;         // n_st * n_chunks
+    int32_t* counter;        // work-queue head, zero before the launch
+    int32_t* status;         // DEV_* error word
+    float* V0f;              // [n_pol][v0_ld] or null
+    double* V0d;             // [n_pol][v0_ld] or null
+    int32_t v0_ld;
+    double* partial;         // [n_st][part_ld] per-super-tile scenario sums or null
+    int32_t part_ld;
+};
+
+// Sum b >= 0 into the double-float (h, l), h >= 0: Fast2Sum on the heads
+// ordered by size (exact error term), the tail accumulates it.
+__device__ __forceinline__ void defl_fold(float& h, float& l, float b) {
+    const float hi = fmaxf(h, b), lo = fminf(h, b);
+    const float s = __fadd_rn(hi, lo);
+    const float e = __fsub_rn(lo, __fsub_rn(s, hi));
+    h = s;
+    l = __fadd_rn(l, e);
+}
+
+// Header of a staged block: which item and block it holds.
+struct DeflBlock {
+    int32_t item;   // -1: no more work
+    int32_t j;      // block index (steps j*32 .. j*32+31)
+    int32_t first;  // first block of the item (its longest block)
+    int32_t q;      // the item's number in this CTA's sequence (its partial-sum slot is q & 1);
+                    // bit 30 set: block 0, the item's epilogue follows
+};
+
+template <int P, int M, int NW, int NBUF>
+struct DeflSmem {
+    static constexpr int CH = 32 * M;                      // scenarios per chunk
+    static constexpr size_t ring = (size_t)NBUF * DEFL_G * CH * sizeof(float4);
+    static constexpr size_t red = (size_t)2 * NW * CH * sizeof(float2);
+    static constexpr size_t hdr = (size_t)NBUF * sizeof(DeflBlock);
+    static constexpr size_t bars = (size_t)2 * NBUF * sizeof(uint64_t);
+    // layout after the tables (tab_bytes, a multiple of 16): ring | red | hdr | bars
+    static size_t bytes(size_t tab_bytes) { return tab_bytes + ring + red + hdr + bars; }
+};
+
+__device__ __forceinline__ void defl_mbar_arrive(uint64_t* bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Per-lane state of one item: P policies x M scenarios.
+template <int P, int M>
+struct DeflLane {
+    float a0[P][M], a1[P][M];   // the current 16 steps' two FP32 accumulators
+    float h[P][M], l[P][M];     // double-float sums of the folded spans
+};
+
+// What a block needs of a warp's P slots.
+template <int P>
+struct DeflPol {
+    int off1[P], off2[P], S[P];
+    float ix[P], iy[P];
+};
+
+// The expected cash flows E of four steps t = 4g .. 4g+3 of policy i
+// (per unit amount; for K_ANN and K_ASS unscaled), zero past its end.
+template <int KIND, int P>
+__device__ __forceinline__ float4 defl_weights(const DeflPol<P>& pp, int i, const float4* __restrict__ tab, int g,
+                                               bool check) {
+    float4 e;
+    if constexpr (KIND == K_ANN || KIND == K_ASS) {
+        e = tab[pp.off1[i] + g];
+    } else if constexpr (KIND == K_ANN2) {   // E = P^x P^y
+        const float4 x = tab[pp.off1[i] + g], y = tab[pp.off2[i] + g];
+        const float ix = pp.ix[i], iy = pp.iy[i];
+        e.x = __fmul_rn(__fmul_rn(x.x, ix), __fmul_rn(y.x, iy));
+        e.y = __fmul_rn(__fmul_rn(x.y, ix), __fmul_rn(y.y, iy));
+        e.z = __fmul_rn(__fmul_rn(x.z, ix), __fmul_rn(y.z, iy));
+        e.w = __fmul_rn(__fmul_rn(x.w, ix), __fmul_rn(y.w, iy));
+    } else {   // K_JL: E = P^x (1 - P^y) + P^y
+        const float4 x = tab[pp.off1[i] + g], y = tab[pp.off2[i] + g];
+        const float ix = pp.ix[i], iy = pp.iy[i];
+        float px = __fmul_rn(x.x, ix), py = __fmul_rn(y.x, iy);
+        e.x = __fmaf_rn(px, __fsub_rn(1.0f, py), py);
+        px = __fmul_rn(x.y, ix); py = __fmul_rn(y.y, iy);
+        e.y = __fmaf_rn(px, __fsub_rn(1.0f, py), py);
+        px = __fmul_rn(x.z, ix); py = __fmul_rn(y.z, iy);
+        e.z = __fmaf_rn(px, __fsub_rn(1.0f, py), py);
+        px = __fmul_rn(x.w, ix); py = __fmul_rn(y.w, iy);
+        e.w = __fmaf_rn(px, __fsub_rn(1.0f, py), py);
+    }
+    if (check) {   // steps at or past the end contribute nothing
+        const int t0 = 4 * g, S = pp.S[i];
+        if (t0 >= S) e.x = 0.0f;
+        if (t0 + 1 >= S) e.y = 0.0f;
+        if (t0 + 2 >= S) e.z = 0.0f;
+        if (t0 + 3 >= S) e.w = 0.0f;
+    }
+    return e;
+}
+
+// One group of four steps (descending t) of the warp's P x M chains: the
+// weights of every policy first, then the fused multiply-adds step by step
+// across all chains (the two accumulators take alternate steps).  FIRST: the
+// group opens a 16-step span, whose products start the accumulators.
+template <int KIND, int P, int M, bool FIRST>
+__device__ __forceinline__ void defl_group(DeflLane<P, M>& st, const DeflPol<P>& pp, const float4* __restrict__ tab,
+                                           const float4 (&d)[M], int g, bool check) {
+    float4 e[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        // a group wholly past the policy's end reads nothing (its table entries
+        // may lie beyond what was staged for it)
+        if (check && 4 * g >= pp.S[i]) e[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        else e[i] = defl_weights<KIND, P>(pp, i, tab, g, check);
+    }
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+            st.a1[i][m] = FIRST ? __fmul_rn(d[m].w, e[i].w) : __fmaf_rn(d[m].w, e[i].w, st.a1[i][m]);
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+            st.a0[i][m] = FIRST ? __fmul_rn(d[m].z, e[i].z) : __fmaf_rn(d[m].z, e[i].z, st.a0[i][m]);
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+        for (int m = 0; m < M; ++m) st.a1[i][m] = __fmaf_rn(d[m].y, e[i].y, st.a1[i][m]);
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+        for (int m = 0; m < M; ++m) st.a0[i][m] = __fmaf_rn(d[m].x, e[i].x, st.a0[i][m]);
+}
+
+// After the steps of one 16-step span: fold the two accumulators into (h, l).
+template <int P, int M>
+__device__ __forceinline__ void defl_fold_all(DeflLane<P, M>& st) {
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+        for (int m = 0; m < M; ++m) defl_fold(st.h[i][m], st.l[i][m], __fadd_rn(st.a0[i][m], st.a1[i][m]));
+}
+
+// One 16-step span (four groups, descending) from the staged rows r0+3 .. r0.
+template <int KIND, int P, int M>
+__device__ __forceinline__ void defl_span(DeflLane<P, M>& st, const DeflPol<P>& pp, const float4* __restrict__ tab,
+                                          const float4* __restrict__ ring_b, int g0, int lane, bool check) {
+#pragma unroll
+    for (int u = 3; u >= 0; --u) {
+        float4 d[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) d[m] = ring_b[u * (32 * M) + m * 32 + lane];
+        if (u == 3) defl_group<KIND, P, M, true>(st, pp, tab, d, g0 + u, check);
+        else defl_group<KIND, P, M, false>(st, pp, tab, d, g0 + u, check);
+    }
+    defl_fold_all(st);
+}
+
+// One staged block (two spans, descending) of one item.
+template <int KIND, int P, int M>
+__device__ __forceinline__ void defl_block(DeflLane<P, M>& st, const DeflPol<P>& pp, const float4* __restrict__ tab,
+                                           const float4* __restrict__ ring_b, int j, int lane, int smin, int smax) {
+    const int t_lo = j * DEFL_KB;
+    if (t_lo >= smax) return;                       // every policy of this warp has ended before the block
+    const int g_lo = j * DEFL_G;
+    if (t_lo + DEFL_KB > smin) {                    // some policy ends within or before the block
+#pragma unroll 1
+        for (int h = 1; h >= 0; --h) defl_span<KIND, P, M>(st, pp, tab, ring_b + h * 4 * (32 * M), g_lo + 4 * h, lane, true);
+    } else {
+#pragma unroll 1
+        for (int h = 1; h >= 0; --h) defl_span<KIND, P, M>(st, pp, tab, ring_b + h * 4 * (32 * M), g_lo + 4 * h, lane, false);
+    }
+}
+
+// Roles: warps 0 .. NW-1 value chains; warp NW stages the deflator blocks.
+// The warps are not synchronised with each other after the table staging:
+// each consumes the staged blocks in order, releasing each buffer with an
+// mbarrier arrival; the producer refills a buffer once all NW warps have
+// released it.  The per-scenario sums of an item are joined by the warp that
+// finishes the item last (a shared-memory counter), in warp order.
+template <int P, int M, int NW, int NBUF, int MINB>
+__global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArgs a) {
+    using SM = DeflSmem<P, M, NW, NBUF>;
+    constexpr int CH = SM::CH, W = NW * P;
+    constexpr int kLast = 1 << 30;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint64_t tbar;
+    __shared__ int red_cnt[2];
+    __shared__ volatile int done_items, abort_flag;
+    unsigned char* base = smem_raw + a.tab_bytes;
+    float4* ring = reinterpret_cast<float4*>(base);
+    float2* red = reinterpret_cast<float2*>(base + SM::ring);
+    DeflBlock* hdr = reinterpret_cast<DeflBlock*>(base + SM::ring + SM::red);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + SM::ring + SM::red + SM::hdr);
+    uint64_t* empty = full + NBUF;
+
+    if (!stage_to_smem(smem_raw, a.tab, (uint32_t)a.tab_bytes, &tbar, a.status)) return;
+    const float4* tab = reinterpret_cast<const float4*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr uint32_t row_bytes = CH * sizeof(float4), blk_bytes = DEFL_G * row_bytes;
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], NW);
+        }
+        fence_barrier_init();
+        red_cnt[0] = red_cnt[1] = 0;
+        done_items = 0;
+        abort_flag = 0;
+    }
+    __syncthreads();
+
+    if (warp == NW) {
+        // ---------------- producer: lane 0 claims items and stages their blocks
+        if (lane != 0) return;
+        int k = 0;
+        for (int q = 0;; ++q) {
+            const int it = atomicAdd(a.counter, 1);
+            const bool more = it < a.n_items;
+            int jmax = 0, chunk = 0;
+            if (more) {
+                const int stt = it / a.n_chunks;
+                chunk = it - stt * a.n_chunks;
+                const int Smax = a.slots[(size_t)stt * W].S;
+                jmax = Smax > 0 ? (Smax - 1) / DEFL_KB : 0;
+                // item q writes partial-sum slot q & 1, last used by item q - 2
+                if (q >= 2) {
+                    uint32_t n = 0;
+                    while (done_items < q - 1 && !abort_flag && ++n < kWaitLimit) __nanosleep(64);
+                    if (done_items < q - 1) abort_flag = 1;
+                    __threadfence_block();   // the slot's reset is seen before its reuse is released
+                }
+            }
+            for (int j = jmax; j >= 0 && !abort_flag; --j, ++k) {
+                const int b = k % NBUF;
+                if (k >= NBUF && !mbar_wait_bounded(&empty[b], (uint32_t)(((k / NBUF) - 1) & 1), kWaitLimit)) {
+                    abort_flag = 1;
+                    break;
+                }
+                if (!more) {   // no more work: a closing header, no copy
+                    hdr[b] = DeflBlock{-1, 0, 0, 0};
+                    defl_mbar_arrive(&full[b]);
+                    break;
+                }
+                hdr[b] = DeflBlock{it, j, j == jmax ? 1 : 0, q | (j == 0 ? kLast : 0)};
+                mbar_arrive_expect_tx(&full[b], blk_bytes);
+                const float4* src = a.D + (size_t)j * DEFL_G * a.s_pad + (size_t)chunk * CH;
+                for (int r = 0; r < DEFL_G; ++r)
+                    bulk_g2s(ring + ((size_t)b * DEFL_G + r) * CH, src + (size_t)r * a.s_pad, row_bytes, &full[b]);
+            }
+            if (!more || abort_flag) break;
+        }
+        if (abort_flag) {
+            atomicExch(a.status, DEV_TIMEOUT);
+            // let the copies still in flight land before the CTA exits
+            for (int q = 1; q <= NBUF && k - q >= 0; ++q)
+                mbar_wait_bounded(&full[(k - q) % NBUF], (uint32_t)(((k - q) / NBUF) & 1), kWaitLimit);
+        }
+        return;
+    }
+
+    // -------------------- consumers
+    DeflLane<P, M> st;
+    DeflPol<P> pp;
+    int smin = 0, smax = 0, kind = K_ANN, stt = 0, chunk = 0;
+    for (int k = 0;; ++k) {
+        const int b = k % NBUF;
+        if (!mbar_wait_bounded(&full[b], (uint32_t)((k / NBUF) & 1), kWaitLimit)) {
+            abort_flag = 1;
+            if (lane == 0) atomicExch(a.status, DEV_TIMEOUT);
+            break;
+        }
+        const DeflBlock hb = hdr[b];
+        if (hb.item < 0) break;
+        const DeflSlot* rec = nullptr;
+        if (hb.first) {   // a new item: this warp's P policies
+            stt = hb.item / a.n_chunks;
+            chunk = hb.item - stt * a.n_chunks;
+            kind = a.st_kind[stt];
+            rec = a.slots + (size_t)stt * W + warp * P;
+            smin = 1 << 30;
+            smax = 0;
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                const int4 q4 = *reinterpret_cast<const int4*>(&rec[i].off1);
+                const float4 f4 = *reinterpret_cast<const float4*>(&rec[i].ix);   // ix, iy, mat, kind
+                const int S = q4.w < 0 ? 0 : q4.z;
+                const float mat = f4.z;
+                pp.off1[i] = q4.x;
+                pp.off2[i] = q4.y;
+                pp.S[i] = S;
+                pp.ix[i] = f4.x;
+                pp.iy[i] = f4.y;
+                smin = min(smin, S);
+                smax = max(smax, S);
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    st.l[i][m] = 0.0f;
+                    float h0 = 0.0f;
+                    if (mat != 0.0f && q4.w >= 0) {   // U_S = D_S l_{x+S} bnd
+                        float dS = 1.0f;
+                        if (S > 0) {
+                            const int t = S - 1, s = chunk * CH + m * 32 + lane;
+                            dS = reinterpret_cast<const float*>(a.D + (size_t)(t >> 2) * a.s_pad + s)[t & 3];
+                        }
+                        h0 = __fmul_rn(dS, mat);
+                    }
+                    st.h[i][m] = h0;
+                }
+            }
+        }
+        rec = a.slots + (size_t)stt * W + warp * P;
+        const float4* ring_b = ring + (size_t)b * DEFL_G * CH;
+        if (kind == K_ANN) defl_block<K_ANN, P, M>(st, pp, tab, ring_b, hb.j, lane, smin, smax);
+        else if (kind == K_ASS) defl_block<K_ASS, P, M>(st, pp, tab, ring_b, hb.j, lane, smin, smax);
+        else if (kind == K_JL) defl_block<K_JL, P, M>(st, pp, tab, ring_b, hb.j, lane, smin, smax);
+        else defl_block<K_ANN2, P, M>(st, pp, tab, ring_b, hb.j, lane, smin, smax);
+        __syncwarp();
+        if (lane == 0) defl_mbar_arrive(&empty[b]);   // this warp is done with buffer b
+
+        if (hb.q & kLast) {   // epilogue: scale, write V0, join the per-scenario sums
+            float ph[M], pl[M];
+#pragma unroll
+            for (int m = 0; m < M; ++m) ph[m] = pl[m] = 0.0f;
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                const int pol = rec[i].pol;
+                if (pol < 0) continue;
+                const float sh = rec[i].sc_h, sl = rec[i].sc_l;
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    const int s = chunk * CH + m * 32 + lane;
+                    if (s >= a.n_scen) continue;
+                    const float H = st.h[i][m], L = st.l[i][m];
+                    const size_t o = (size_t)pol * a.v0_ld + s;
+                    // (H + L)(sh + sl) as a double-float, for V0 and the sums
+                    const float p = __fmul_rn(H, sh);
+                    float e = __fmaf_rn(H, sh, -p);
+                    e = __fmaf_rn(H, sl, e);
+                    e = __fmaf_rn(L, sh, e);
+                    if (a.V0f) a.V0f[o] = __fadd_rn(p, e);
+                    if (a.V0d) a.V0d[o] = ((double)H + (double)L) * rec[i].scale;
+                    defl_fold(ph[m], pl[m], p);
+                    pl[m] = __fadd_rn(pl[m], e);
+                }
+            }
+            if (a.partial) {
+                const int slot = hb.q & 1;
+                float2* rs = red + (size_t)slot * NW * CH;
+#pragma unroll
+                for (int m = 0; m < M; ++m) rs[warp * CH + m * 32 + lane] = make_float2(ph[m], pl[m]);
+                __threadfence_block();
+                __syncwarp();
+                int old = 0;
+                if (lane == 0) old = atomicAdd(&red_cnt[slot], 1);
+                old = __shfl_sync(0xffffffffu, old, 0);
+                if (old == NW - 1) {   // the last warp of this item: fixed order over the warps, FP64
+                    __threadfence_block();
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        const int c = m * 32 + lane;
+                        double x = 0.0;
+                        for (int w = 0; w < NW; ++w) {
+                            const float2 v = rs[w * CH + c];
+                            x += (double)v.x + (double)v.y;
+                        }
+                        a.partial[(size_t)stt * a.part_ld + chunk * CH + c] = x;
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        red_cnt[slot] = 0;
+                        __threadfence_block();
+                        atomicAdd((int*)&done_items, 1);
+                    }
+                }
+            } else if (lane == 0 && warp == 0) {
+                atomicAdd((int*)&done_items, 1);
+            }
+        }
+        if (abort_flag) break;
+    }
+}
+
+// ------------------------------------------------------ variant registry ----
+struct DeflVariant {
+    int P, M, NW, NBUF;
+    const char* name;
+    cudaError_t (*launch)(const DeflArgs&, int grid, size_t smem, cudaStream_t st);
+    cudaError_t (*occupancy)(int* blocks_per_sm, size_t smem);
+};
+
+template <int P, int M, int NW, int NBUF, int MINB>
+cudaError_t set_defl_attributes(size_t smem) {
+    auto k = defl_kernel<P, M, NW, NBUF, MINB>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+}
+
+template <int P, int M, int NW, int NBUF, int MINB>
+cudaError_t launch_defl(const DeflArgs& a, int grid, size_t smem, cudaStream_t st) {
+    cudaError_t e = set_defl_attributes<P, M, NW, NBUF, MINB>(smem);
+    if (e != cudaSuccess) return e;
+    defl_kernel<P, M, NW, NBUF, MINB><<<grid, (NW + 1) * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int P, int M, int NW, int NBUF, int MINB>
+cudaError_t occupancy_defl(int* blocks, size_t smem) {
+    cudaError_t e = set_defl_attributes<P, M, NW, NBUF, MINB>(smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, defl_kernel<P, M, NW, NBUF, MINB>, (NW + 1) * 32,
+                                                         smem);
+}
+
+#define RSV_DEFL_VARIANT(P, M, NW, NBUF, MINB, NAME)                                                  \
+    DeflVariant {                                                                                     \
+        P, M, NW, NBUF, NAME, &launch_defl<P, M, NW, NBUF, MINB>, &occupancy_defl<P, M, NW, NBUF, MINB> \
+    }
+
+const DeflVariant* variants_defl(int* n);
+// smem bytes of a variant beyond its staged tables
+size_t defl_smem_extra(const DeflVariant& v);
+
+}  // namespace rsv

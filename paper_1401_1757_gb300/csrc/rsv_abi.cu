@@ -21,6 +21,7 @@
 #include "nested.cuh"
 #include "scan.cuh"
 #include "summation.cuh"
+#include "defl_kernel.cuh"
 
 using namespace rsv;
 
@@ -520,6 +521,18 @@ rsv_status rsv::stage_tables(rsv_ctx* c, int form, int pad, int n_tab, size_t& s
     return RSV_OK;
 }
 
+rsv_status rsv::scenario_totals(rsv_ctx* c, const double* partial, int n_rows, int s_pad, int n_scen, double* tot) {
+    const int G = 256, groups = (n_rows + G - 1) / G;
+    CU(c->d_part2.ensure((size_t)groups * s_pad * sizeof(double)));
+    dim3 g1((s_pad + 127) / 128, groups);
+    reduce_tiles_kernel<<<g1, 128, 0, c->stream>>>(partial, n_rows, s_pad, G, c->d_part2.as<double>());
+    CU(cudaGetLastError());
+    reduce_groups_kernel<<<(n_scen + 127) / 128, 128, 0, c->stream>>>(c->d_part2.as<double>(), groups, s_pad, n_scen,
+                                                                     tot);
+    CU(cudaGetLastError());
+    return RSV_OK;
+}
+
 // The tables followed by the fractional-survival tables (RSV_PAY_FRACTION),
 // staged together; *tabf_off receives the offset in entries.
 rsv_status build_tables_frac(rsv_ctx* c, int form, size_t& smem, int& tabf_off) {
@@ -561,7 +574,7 @@ rsv_status upload_amounts(rsv_ctx* c) {
 rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     if (!c) return RSV_E_ARG;
     if (!o || !out) return fail(c, RSV_E_ARG, "opts and out must not be NULL");
-    if (o->form < F_F64 || o->form > F_COMP) return fail(c, RSV_E_ARG, "bad form %d", o->form);
+    if (o->form < F_F64 || o->form > F_DEFL) return fail(c, RSV_E_ARG, "bad form %d", o->form);
     if (o->horizon < 0 || (o->on_device != 0 && o->on_device != 1))
         return fail(c, RSV_E_ARG, "bad horizon or on_device");
     if (c->pols.empty() && c->n_scen == 0) return fail(c, RSV_E_STATE, "no portfolio and no scenarios loaded");
@@ -575,6 +588,7 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     if ((outs & RSV_OUT_SCEN_TOTAL) && !out->scen_total) return fail(c, RSV_E_ARG, "scen_total NULL");
     if ((outs & RSV_OUT_PT_MEAN) && !out->pt_mean) return fail(c, RSV_E_ARG, "pt_mean NULL");
     if ((outs & RSV_OUT_TRAJ) && !out->traj) return fail(c, RSV_E_ARG, "traj NULL");
+    if (o->form == F_DEFL) return compute_deflated(c, o, out);
 
     const int64_t n_pol = (int64_t)c->pols.size();
     const int T = c->n_steps, NSc = c->n_scen;
@@ -772,16 +786,7 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
         c->ev_recorded = true;
     }
     if (L.n_tiles > 0) {
-        if (tot) {
-            const int G = 256, groups = (L.n_tiles + G - 1) / G;
-            CU(c->d_part2.ensure((size_t)groups * c->s_pad * sizeof(double)));
-            dim3 g1((c->s_pad + 127) / 128, groups);
-            reduce_tiles_kernel<<<g1, 128, 0, c->stream>>>(a.partial, L.n_tiles, c->s_pad, G, c->d_part2.as<double>());
-            CU(cudaGetLastError());
-            reduce_groups_kernel<<<(NSc + 127) / 128, 128, 0, c->stream>>>(c->d_part2.as<double>(), groups, c->s_pad,
-                                                                          NSc, tot);
-            CU(cudaGetLastError());
-        }
+        if (tot && (st = scenario_totals(c, a.partial, L.n_tiles, c->s_pad, NSc, tot)) != RSV_OK) return st;
         if (pt) {
             scale_kernel<<<c->sm_count * 4, 256, 0, c->stream>>>(pt, n_pt, 1.0 / NSc);
             CU(cudaGetLastError());
@@ -1093,7 +1098,8 @@ rsv_status rsv_destroy(rsv_ctx* c) try {
                       &c->sur.d_y, &c->sur.d_X, &c->sur.d_pred, &c->sur.d_err, &c->sur.d_aux, &c->sur.d_curve,
                       &c->sur.d_comm, &c->sur.d_lnb, &c->d_tabf[0], &c->d_tabf[1], &c->d_tabf[2], &c->d_vf64,
                       &c->d_vf32, &c->d_vf2, &c->d_cf64, &c->d_cf32, &c->d_ml_rec,
-                      &c->d_ml_amount, &c->sur.d_cnt, &c->sur.d_q2, &c->sur.d_idx, &c->sur.d_v2, &c->d_nest_bm})
+                      &c->d_ml_amount, &c->sur.d_cnt, &c->sur.d_q2, &c->sur.d_idx, &c->sur.d_v2, &c->d_nest_bm,
+                      &c->d_defl_slots, &c->d_defl_kinds, &c->d_defl_tab, &c->d_defl_plane})
         b->release();
     c->mlp.release();
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -1311,12 +1317,17 @@ rsv_status rsv_compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_sp
 
 int32_t rsv_variant_count(int32_t form) {
     int n = 0;
+    if (form == F_DEFL) return variants_defl(&n) ? n : 0;
     const Variant* vl = variant_list(form, &n);
     return vl ? tunable_count(vl, n) : 0;
 }
 
 const char* rsv_variant_name(int32_t form, int32_t variant) {
     int n = 0;
+    if (form == F_DEFL) {
+        const DeflVariant* dv = variants_defl(&n);
+        return (variant < 0 || variant >= n) ? "" : dv[variant].name;
+    }
     const Variant* v = variant_list(form, &n);
     if (!v || variant < 0 || variant >= n) return "";
     return v[variant].name;

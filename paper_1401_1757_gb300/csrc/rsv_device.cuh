@@ -19,7 +19,8 @@ enum Kind : int32_t {
                 // model with the benefit on the second death (Section 4.2.3)
 };
 
-enum Form : int32_t { F_F64 = 0, F_F32 = 1, F_COMP = 2 };
+// F_DEFL: the recurrence in deflated units, compensated FP32 (defl_kernel.cuh)
+enum Form : int32_t { F_F64 = 0, F_F32 = 1, F_COMP = 2, F_DEFL = 3 };
 
 // Device status word values.
 enum : int32_t { DEV_OK = 0, DEV_TIMEOUT = 1 };

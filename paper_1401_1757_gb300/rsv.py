@@ -21,11 +21,11 @@ STATUS_NAMES = {0: "RSV_OK", -1: "RSV_E_ARG", -2: "RSV_E_NOMEM", -3: "RSV_E_CUDA
 RSV_SL_ANNUITY, RSV_JL_REVERSIONARY, RSV_TERM_ASSURANCE, RSV_ENDOWMENT = 0, 1, 2, 3
 RSV_JOINT_ANNUITY, RSV_LAST_SURVIVOR, RSV_JOINT_TERM, RSV_JOINT_ENDOWMENT = 4, 5, 6, 7
 RSV_LS_TERM, RSV_LS_ENDOWMENT = 8, 9
-RSV_FORM_F64, RSV_FORM_F32, RSV_FORM_F32_COMP = 0, 1, 2
+RSV_FORM_F64, RSV_FORM_F32, RSV_FORM_F32_COMP, RSV_FORM_F32_DEFLATED = 0, 1, 2, 3
 RSV_VARIANT_TIME_SCAN = -2   # the FP64 parallel-in-time scan (see include/rsv.h)
 RSV_VARIANT_SUMMATION = -3   # the FP64 O(S^2) summation definition
 RSV_PAY_END, RSV_PAY_START, RSV_PAY_FRACTION = 0, 1, 2
-FORM_NAMES = {0: "f64", 1: "f32", 2: "f32comp"}
+FORM_NAMES = {0: "f64", 1: "f32", 2: "f32comp", 3: "f32defl"}
 RSV_OUT_V0, RSV_OUT_SCEN_TOTAL, RSV_OUT_PT_MEAN, RSV_OUT_TRAJ = 1, 2, 4, 8
 
 

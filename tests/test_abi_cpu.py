@@ -43,6 +43,9 @@ def test_library_loads_without_gpu(lib_path):
     # pure host queries need no device
     assert lib.rsv_variant_count(2) >= 2
     assert b"comp" in lib.rsv_variant_name(2, 0)
+    assert lib.rsv_variant_count(3) >= 4
+    assert b"deflated" in lib.rsv_variant_name(3, 0)
+    assert lib.rsv_variant_name(3, 99) == b""
     assert lib.rsv_variant_count(7) == 0
     assert lib.rsv_last_error(None) == b"NULL context"
 
