@@ -1,23 +1,38 @@
 #!/usr/bin/env python
 """Benchmark: policy-scenario reserve valuations per second on one GB300 (or N).
 
-Workload (one "step"): the 100,000-policy four-product mix (40% single-life
-annuities, 20% joint-life reversionary annuities with 3 states and reversion
-50-100%, 20% term assurances 5-40 y, 20% endowments 10-30 y; ages 20-85) under
-1,000 exact-step Vasicek scenarios (a=0.1, b=0.04, sigma=0.01, r0=0.03) of
-1,200 monthly discount factors: 1e8 policy-scenario chains, the backward
-vector reserve recurrence of every chain to t = 0, the reserves written out
-and the per-scenario portfolio totals summed in FP64.
+Headline workload (one "step"): the full-scale configuration, part (A): 1,000,000
+single-life monthly level annuities (ages 60-90, Gompertz-Makeham mortality)
+under 1,000 exact-step Vasicek scenarios (a=0.1, b=0.04, sigma=0.01, r0=0.03)
+of 600 monthly discount factors (50 years; projections are truncated there):
+1e9 policy-scenario chains, each valued by the backward recurrence to t = 0,
+the reserves written out (4 GB FP32) and the per-scenario portfolio totals
+summed in FP64.  The chosen form is the recurrence in deflated units
+(RSV_FORM_F32_DEFLATED, compensated FP32); the plain FP32 recurrence, the
+double-float recurrence and FP64 run on the same data beside it, each with
+its relative error against the FP64 oracle on sampled policies.
+
+Also measured (rank 0): the 100,000-policy four-product mix (configuration 2)
+in every form; part (B) of the full-scale configuration (the nested run with
+the surrogate and recurrence fallback against the brute-force inner loop and
+the closed-form curve); the surrogate trained on 10M recurrence labels and
+scored on 1M held-out queries (configuration 4); the nested brute force
+(configuration 3); configuration 1's latency; the paper's summation against
+recurrence comparison; varying cash flows; m-life contracts.
 
 Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
-launching stream, with a 256 MiB write between steps to flush L2 (the inputs
-are L2-sized).  ``value`` = chains of all ranks / (sum of step times, max over
-ranks).  ``e2e`` times the same step through the C ABI with host buffers: the
-scenario, portfolio and table uploads and the device-to-host copy of every
-reserve are inside the timed region.
+launching stream, with a 256 MiB write between steps to flush L2 (the
+scenario inputs are L2-sized; the 4 GB of reserves are not).  ``value`` = the
+chains of all ranks / (sum of step times, max over ranks).  With N ranks the
+portfolio is partitioned by policy (balanced by projection steps), every rank
+values its share under the same scenarios, and the per-scenario FP64 totals
+are summed over the ranks inside each timed step (strong scaling).  ``e2e``
+times the same step through the C ABI with host buffers: the scenario,
+portfolio and table uploads and the device-to-host copy of every reserve are
+inside the timed region.
 
 ``--impl reference`` times the FP64 CPU oracle instead (rank 0, host cores,
-a bounded sample of the same workload per step).
+a bounded sample of the headline workload per step).
 """
 from __future__ import annotations
 
@@ -25,6 +40,8 @@ import argparse
 import hashlib
 import json
 import os
+import platform
+import re
 import statistics
 import subprocess
 import sys
@@ -37,67 +54,97 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
+from paper_1401_1757_gb300.shard import PolicyPartition, projection_steps  # noqa: E402
 
 METRIC = "policy-scenario reserve valuations/s (plain vs surrogate) at stated error"
-N_POL, N_SCEN, N_STEPS = 100_000, 1000, 1200
-N_POL_MIX = 100_000
-WORKLOAD = ("100,000-policy mix (40% SL annuities, 20% JL reversionary 3-state, 20% term 5-40y, "
-            "20% endowments 10-30y, ages 20-85) x 1,000 Vasicek scenarios x 1,200 monthly steps")
+C5 = dict(n_pol=1_000_000, n_scen=1000, n_steps=600, horizon=600, seed=5, n_nodes=50, sample_pol=10_000,
+          sample_outer=10)
+HEAD_WORKLOAD = ("full scale (A): 1,000,000 single-life monthly level annuities (ages 60-90, Gompertz-Makeham) x "
+                 "1,000 Vasicek scenarios x 600 monthly steps (50 y, projections truncated there); V0 of every chain "
+                 "and FP64 per-scenario totals")
+C5B_WORKLOAD = ("full scale (B): the same annuities; nested run on the 1,000 outer Vasicek paths x 50 annual nodes x "
+                "1,000 inner paths")
+C2 = dict(n_pol=100_000, n_scen=1000, n_steps=1200, seed=0)
+C2_WORKLOAD = ("100,000-policy mix (40% SL annuities, 20% JL reversionary 3-state, 20% term 5-40y, "
+               "20% endowments 10-30y, ages 20-85) x 1,000 Vasicek scenarios x 1,200 monthly steps")
 
-# FP32 (FP64 for f64) operations per chain-step of each form and product
-# (add/sub/mul/min/max = 1, FMA = 2), counted from the formulas the kernels
-# evaluate: plain annuity v*p then an FMA; compensated annuity a double-float
-# product (7) and the shifted update 1 + g R (9); compensated assurance two
-# double-float products and an ordered sum (20); the JL product as three
-# annuity chains a_x, a_y, a_xy: plain three products and three FMAs (9),
-# compensated three double-float products (21) and three shifted updates
-# (27): 48.
-FLOPS = {"f32": {0: 3, 1: 9, 2: 3, 3: 3},
-         "f32comp": {0: 16, 1: 48, 2: 20, 3: 20},
-         "f64": {0: 3, 1: 9, 2: 3, 3: 3}}
+FORMS = {"f64": 0, "f32": 1, "f32comp": 2, "f32defl": 3}
+HEAD = "f32defl"
+DTYPE = {"f32defl": "f32-deflated-compensated", "f32comp": "f32-compensated", "f32": "f32", "f64": "f64"}
+
+# Algorithmic work of the method per chain-step (the same for every form):
+# 3 flop for a one-state step (v p (c + r'): one multiply and one fused
+# multiply-add), 16 for the three-state reversionary step (five products of
+# the 3x3 upper-triangular W, three adds, three scalings, px py shared).
+ALGO_FLOPS = {0: 3, 1: 16, 2: 3, 3: 3}
+# FP32 (FP64 for f64) operations each form's kernels issue per chain-step
+# (FMA = 2, add/sub/mul/min/max = 1): plain v p then an FMA; the double-float
+# forms' products and ordered sums; the deflated form per 16 steps two
+# products and 14 FMAs (30), the join of its two partial sums (1) and the
+# ordered fold (6), plus for the reversionary annuity the expected cash flow
+# (two products, one subtraction, one FMA: 5) per policy-step shared by the M
+# scenarios of a lane.
+ISSUED_FLOPS = {"f32": {0: 3, 1: 9, 2: 3, 3: 3},
+                "f32comp": {0: 16, 1: 48, 2: 20, 3: 20},
+                "f64": {0: 3, 1: 9, 2: 3, 3: 3},
+                "f32defl": {0: 37 / 16, 1: 37 / 16, 2: 37 / 16, 3: 37 / 16}}
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = 2 * FP32_LANES * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 at 2070 MHz
 
-FORMS = {"f64": 0, "f32": 1, "f32comp": 2}
+
+def chain_steps_by_product(pol, horizon=0):
+    S = projection_steps(pol, horizon=horizon)
+    return {p: int(S[pol["product"] == p].sum()) for p in range(4)}
 
 
-def policy_steps(pol, n_ages=1440, horizon=0):
-    """Projection length of each policy (the same rules as the library applies)."""
-    prod, a1, a2, term = pol["product"], pol["age1_m"], pol["age2_m"], pol["term_m"]
-    S = np.where(prod == 0, np.maximum(0, n_ages - a1),
-                 np.where(prod == 1, np.maximum(0, n_ages - np.minimum(a1, a2)), term))
-    S = np.where((prod <= 1) & (term > 0), np.minimum(S, term), S)
-    if horizon > 0:
-        S = np.minimum(S, horizon)
-    return S.astype(np.int64)
+def algorithmic_flops(pol, n_scen, horizon=0):
+    cs = chain_steps_by_product(pol, horizon)
+    return float(sum(ALGO_FLOPS[p] * cs[p] for p in cs) * n_scen)
 
 
-def algorithmic_flops(pol, form, n_scen):
-    S = policy_steps(pol)
-    return float(sum(FLOPS[form][p] * S[pol["product"] == p].sum() for p in range(4)) * n_scen)
+def issued_flops(pol, form, n_scen, horizon=0, variant_name=""):
+    cs = chain_steps_by_product(pol, horizon)
+    per = dict(ISSUED_FLOPS[form])
+    if form == "f32defl":   # the JL expected cash flow, amortised over the lane's M scenarios
+        m = re.search(r"xM(\d+)", variant_name)
+        per[1] += 5.0 / (int(m.group(1)) if m else 4)
+    return float(sum(per[p] * cs[p] for p in cs) * n_scen)
 
 
-def kernel_source_hash():
-    """Hash of the sources the valuation recurrence kernel is built from."""
+def kernel_source_hash(form=HEAD):
+    """Hash of the sources a form's valuation kernel is built from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1401_1757_gb300", "csrc")
-    for f in ("rsv_device.cuh", "recur_kernel.cuh", "recur_comp.cu", "recur_f32.cu", "recur_f64.cu"):
+    files = (("rsv_device.cuh", "defl_kernel.cuh", "recur_defl.cu") if form == "f32defl" else
+             ("rsv_device.cuh", "recur_kernel.cuh", "recur_comp.cu", "recur_f32.cu", "recur_f64.cu"))
+    for f in files:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def measured_traffic(form):
-    """DRAM bytes per launch of the recurrence kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
+def measured_traffic(form, workload_key):
+    """DRAM bytes per launch of a form's kernel on a workload, from the
+    committed ncu summary, if it was taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "recur_traffic.json")
     try:
         d = json.load(open(path))
     except Exception:
         return None
-    e = d.get(form)
-    if not e or e.get("kernel_hash") != kernel_source_hash():
+    e = d.get(f"{form}:{workload_key}")
+    if not e or e.get("kernel_hash") != kernel_source_hash(form):
         return None
     return e.get("dram_bytes_per_launch")
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
 
 
 class ClockSampler:
@@ -149,37 +196,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def reference_arm(args, rank):
-    """The FP64 CPU oracle on the host cores, a bounded sample of the workload per step."""
-    if rank != 0:
-        return
-    import oracle
-    oracle.build()
-    pol = synth.portfolio_mix(N_POL, seed=0)
-    tab = synth.gm_monthly_survival()
-    v = synth.vasicek_paths(N_SCEN, N_STEPS, seed=0)
-    n_sample = args.ref_policies
-    sub = synth.take(pol, slice(0, n_sample))
-    threads = os.cpu_count() or 1
-    times = []
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        oracle.reserves_batch(sub, tab, v, nthreads=threads)
-        dt = time.perf_counter() - t0
-        if i >= args.warmup:
-            times.append(dt)
-    per = sum(times) / len(times)
-    value = n_sample * N_SCEN / per
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "valuations/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"first {n_sample} policies x {N_SCEN} scenarios per step"},
-            "cpu_baseline": {"value": value, "unit": "valuations/s", "cores": threads, "kind": "oracle",
-                             "sample": f"first {n_sample} of {N_POL} policies x all {N_SCEN} scenarios"},
-            "e2e": {"value": value, "unit": "valuations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
 NESTED = dict(n_pol=2000, n_outer=100, n_nodes=40, node_step=12, n_inner=1000)
 NESTED_WORKLOAD = ("nested brute force: 2,000 single-life annuities (ages 60-90) x 100 outer Vasicek paths x "
                    "40 annual nodes x 1,000 inner paths, compensated FP32")
@@ -193,7 +209,7 @@ def bench_nested(rsv, torch, tab, steps, warmup, n_outer=None, sur_epochs=10, su
     if n_outer:
         cfg["n_outer"] = n_outer
     pol = synth.portfolio_single_life(cfg["n_pol"], seed=0)
-    S = policy_steps(pol)
+    S = projection_steps(pol)
     live = chain_steps = 0
     for n in range(cfg["n_nodes"]):
         rem = S - n * cfg["node_step"]
@@ -263,10 +279,11 @@ def bench_cashflows(rsv, torch, ctx, fid, level_ms, steps, warmup, flush):
     monthly and 20% annual payments, 5% escalating at 3%, 4.25% or 5% on each
     anniversary), expanded on the device and valued by the general-cash-flow
     kernel; against the level cash flows of the timed step."""
-    sch = synth.payment_schedules(N_POL, seed=0)
-    rsv.rsv_load_schedules(ctx, sch, N_STEPS)
-    V0 = torch.empty((N_POL, N_SCEN), dtype=torch.float32, device="cuda")
-    tot = torch.empty(N_SCEN, dtype=torch.float64, device="cuda")
+    n_pol, n_scen, n_steps = C2["n_pol"], C2["n_scen"], C2["n_steps"]
+    sch = synth.payment_schedules(n_pol, seed=0)
+    rsv.rsv_load_schedules(ctx, sch, n_steps)
+    V0 = torch.empty((n_pol, n_scen), dtype=torch.float32, device="cuda")
+    tot = torch.empty(n_scen, dtype=torch.float64, device="cuda")
     outs = rsv.RSV_OUT_V0 | rsv.RSV_OUT_SCEN_TOTAL
     for _ in range(warmup):
         rsv.rsv_compute_reserves(ctx, fid, outs, on_device=True, V0=V0, scen_total=tot)
@@ -277,8 +294,8 @@ def bench_cashflows(rsv, torch, ctx, fid, level_ms, steps, warmup, flush):
         ms.append(rsv.rsv_last_kernel_ms(ctx))
     rsv.rsv_clear_cashflows(ctx)
     t = statistics.mean(ms)
-    return {"workload": WORKLOAD + "; payment schedules: 80% monthly / 20% annual, 5% escalating",
-            "kernel_ms": t, "valuations_s": N_POL * N_SCEN / (t / 1e3), "level_kernel_ms": level_ms,
+    return {"workload": C2_WORKLOAD + "; payment schedules: 80% monthly / 20% annual, 5% escalating",
+            "kernel_ms": t, "valuations_s": n_pol * n_scen / (t / 1e3), "level_kernel_ms": level_ms,
             "cost_vs_level": t / level_ms,
             "variant": "general cash flows (unshifted states, c_t per policy and step)"}
 
@@ -315,7 +332,7 @@ def mlife_bench_portfolio(n, seed=0):
 def bench_mlife(rsv, torch, tab, n_pol=20_000, reps=3):
     """m-life contracts (Section 4.3) under the 1,000 scenarios of 1,200 steps."""
     pol = mlife_bench_portfolio(n_pol)
-    v = synth.vasicek_paths(N_SCEN, N_STEPS, seed=0)
+    v = synth.vasicek_paths(C2["n_scen"], C2["n_steps"], seed=0)
     ctx = rsv.rsv_create(torch.cuda.current_device(), torch.cuda.current_stream())
     rsv.rsv_load_decrements(ctx, 0, tab)
     rsv.rsv_load_scenarios(ctx, v)
@@ -329,10 +346,10 @@ def bench_mlife(rsv, torch, tab, n_pol=20_000, reps=3):
         else:
             rem = sorted(max(0, len(tab) - a) for a in pol["age_m"][i, :m])
             S[i] = rem[m - k]
-    V0 = torch.empty((n_pol, N_SCEN), dtype=torch.float32, device="cuda")
+    V0 = torch.empty((n_pol, C2["n_scen"]), dtype=torch.float32, device="cuda")
     res = {"workload": f"{n_pol:,} m-life policies (m = 2-4, half k-of-m annuities, half k-th death "
-                       f"assurances 10-30y, ages 55-85) x {N_SCEN:,} Vasicek scenarios x {N_STEPS:,} steps",
-           "chain_steps": int(S.sum()) * N_SCEN}
+                       f"assurances 10-30y, ages 55-85) x {C2['n_scen']:,} Vasicek scenarios x {C2['n_steps']:,} steps",
+           "chain_steps": int(S.sum()) * C2["n_scen"]}
     for form in ("f32comp", "f64"):
         fid = FORMS[form]
         rsv.rsv_compute_mlife(ctx, pol, fid, rsv.RSV_OUT_V0, on_device=True, V0=V0)
@@ -342,8 +359,8 @@ def bench_mlife(rsv, torch, tab, n_pol=20_000, reps=3):
             ms.append(rsv.rsv_last_kernel_ms(ctx))
         t = statistics.mean(ms) / 1e3
         flops = sum(mlife_flops(form, int(pol["m"][i]), pol["kind"][i] == 1, int(pol["k"][i])) * int(S[i])
-                    for i in range(n_pol)) * N_SCEN
-        res[form] = {"ms": t * 1e3, "valuations_s": n_pol * N_SCEN / t, "flops_per_launch": flops,
+                    for i in range(n_pol)) * C2["n_scen"]
+        res[form] = {"ms": t * 1e3, "valuations_s": n_pol * C2["n_scen"] / t, "flops_per_launch": flops,
                      "achieved_tflops": flops / t / 1e12}
     rsv.rsv_destroy(ctx)
     return res
@@ -426,42 +443,229 @@ def cpu_figure1(tab, n_pol=2000):
     return res
 
 
-C5 = dict(n_pol=1_000_000, n_scen=1000, n_steps=600, n_nodes=50, sample_pol=10_000, sample_outer=10)
-C5_WORKLOAD = ("full scale: 1,000,000 single-life annuities (ages 60-90) x 1,000 Vasicek scenarios x 600 monthly "
-               "steps (50 y); nested: 1,000 outer paths x 50 annual nodes x 1,000 inner paths")
+SURROGATE_WORKLOAD = ("MLP surrogate of the inner-loop expectation: 32->4x256->1 GELU, BF16 weights and activations, "
+                      "FP32 accumulation, trained on 10M recurrence labels of the 100,000-policy mix, scored on 1M "
+                      "held-out queries")
 
 
-def bench_full_scale(rsv, torch, tab, sur_epochs=10, reps=3):
-    """(A) The plain batched recurrence at full scale, plain and compensated
-    FP32.  (B) The nested run with the surrogate (all 1,000 outer paths, a
-    policy sample, extrapolated by policies), the brute-force inner loop and
-    the closed-form curve (a sample of outer paths too, extrapolated by outer
-    paths and policies); node-liability errors against the curve on the
-    common sample."""
-    c = C5
-    res = {"workload": C5_WORKLOAD}
-    pol = synth.portfolio_single_life(c["n_pol"], seed=5)
-    v = synth.vasicek_paths(c["n_scen"], c["n_steps"], seed=5)
+def bench_surrogate(rsv, torch, tab, epochs, lr=2e-3, n_train=10_000_000, n_val=1_000_000):
+    """Train the surrogate on recurrence labels of the four-product portfolio and
+    score it; throughput of the network against the recurrence it replaces."""
+    pol = synth.portfolio_mix(C2["n_pol"], seed=0)
     ctx = rsv.rsv_create(torch.cuda.current_device(), torch.cuda.current_stream())
     rsv.rsv_load_decrements(ctx, 0, tab)
     rsv.rsv_load_portfolio(ctx, pol)
-    rsv.rsv_load_scenarios(ctx, v)
-    V0 = torch.empty((c["n_pol"], c["n_scen"]), dtype=torch.float32, device="cuda")
-    tot = torch.empty(c["n_scen"], dtype=torch.float64, device="cuda")
+    rsv.rsv_mlp_init(ctx, 0)
+    rep = rsv.rsv_surrogate_train(ctx, n_train=n_train, n_val=n_val, epochs=epochs, batch=8192, lr=lr, seed=0)
+    rsv.rsv_destroy(ctx)
+    flops_q = 2 * (32 * 256 + 3 * 256 * 256 + 256)
+    return {
+        "workload": SURROGATE_WORKLOAD if (n_train, n_val) == (10_000_000, 1_000_000) else
+        f"profiling case: {n_train} labels, {n_val} held-out queries", "epochs": epochs, "lr": lr,
+        "held_out": {k: rep[k] for k in ("val_max_rel", "val_p99_rel", "val_median_rel", "val_rms_rel")},
+        "tol": 1e-3, "margin": 0.3, "frac_fallback": rep["frac_fallback"], "combined_max_rel": rep["combined_max_rel"],
+        "buckets_flagged": f"{rep['n_flagged']} of {rep['n_buckets']}",
+        "residual_target_sd": rep["y_std"],
+        "network_queries_s": rep["n_infer"] / (rep["infer_ms"] / 1e3),
+        "network_tflops": rep["n_infer"] * flops_q / (rep["infer_ms"] / 1e3) / 1e12,
+        "recurrence_fp64_queries_s": rep["n_label"] / (rep["label_ms"] / 1e3),
+        "train_s": rep["train_ms"] / 1e3,
+        "train_samples_s": epochs * (n_train // 8192) * 8192 / max(rep["train_ms"] / 1e3, 1e-9),
+    }
+
+
+def head_inputs(n_pol=None, n_scen=None):
+    c = C5
+    pol = synth.portfolio_single_life(n_pol or c["n_pol"], seed=c["seed"])
+    v = synth.vasicek_paths(n_scen or c["n_scen"], c["n_steps"], seed=c["seed"])
+    return pol, v
+
+
+def oracle_runs(pol, tab, v, horizon, runs, warm=1):
+    """Time the FP64 oracle on all host cores: ``warm`` untimed runs, then ``runs`` timed ones."""
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    times = []
+    for i in range(warm + runs):
+        t0 = time.perf_counter()
+        oracle.reserves_batch(pol, tab, v, horizon=horizon, nthreads=threads)
+        if i >= warm:
+            times.append(time.perf_counter() - t0)
+    return times, threads
+
+
+def reference_arm(args, rank):
+    """The FP64 CPU oracle on the host cores, a bounded sample of the headline
+    workload per step (the same policies, all scenarios, the same horizon)."""
+    if rank != 0:
+        return
+    pol, v = head_inputs(args.policies, args.scenarios)
+    tab = synth.gm_monthly_survival()
+    n_sample = min(args.ref_policies, len(pol["product"]))
+    sub = synth.take(pol, slice(0, n_sample))
+    times, threads = oracle_runs(sub, tab, v, C5["horizon"], args.steps, warm=args.warmup)
+    per = sum(times) / len(times)
+    value = n_sample * v.shape[0] / per
+    sample = (f"first {n_sample} of {len(pol['product'])} policies x all {v.shape[0]} scenarios x "
+              f"{C5['horizon']} steps per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "valuations/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": HEAD_WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "valuations/s", "cores": threads, "kind": "oracle",
+                             "sample": sample, "cpu_model": cpu_model()},
+            "e2e": {"value": value, "unit": "valuations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(pol, tab, v, horizon, n_sample, runs=7):
+    """The oracle on the host cores, the paper's timing method (Section 5.1:
+    the minimum of repeated runs; the median beside it): one warm-up and
+    ``runs`` timed runs of the first n_sample policies x all scenarios."""
+    sub = synth.take(pol, slice(0, n_sample))
+    times, threads = oracle_runs(sub, tab, v, horizon, runs)
+    vals = n_sample * v.shape[0]
+    return {"value": vals / min(times), "unit": "valuations/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {n_sample} of {len(pol['product'])} policies x all {v.shape[0]} scenarios"
+                      + (f" x {horizon} steps" if horizon else "") + f", min of {runs} runs",
+            "runs": runs, "min_s": min(times), "median_s": statistics.median(times),
+            "median_value": vals / statistics.median(times), "cpu_model": cpu_model()}
+
+
+def rel_errors(got, ref, amount):
+    scale = np.maximum(np.abs(ref), 1e-9 * np.abs(amount)[:, None])
+    e = np.abs(got - ref) / scale
+    return {"max_rel_err": float(e.max()), "p99_rel_err": float(np.quantile(e, 0.99)),
+            "median_rel_err": float(np.median(e))}
+
+
+def time_form(rsv, torch, ctx, form, V0, tot, horizon, steps, warmup, flush, stream, part=None, dist=None,
+              sampler=None, tune=True):
+    """K timed steps of one form (tuned first), CUDA events on the launching
+    stream around each step; with a partition, the FP64 sum of the totals over
+    the ranks is inside the step."""
+    fid = FORMS[form]
     outs = rsv.RSV_OUT_V0 | rsv.RSV_OUT_SCEN_TOTAL
-    for name, form in (("A_plain_f32", rsv.RSV_FORM_F32), ("A_compensated_f32", rsv.RSV_FORM_F32_COMP)):
-        rsv.rsv_tune(ctx, form, horizon=c["n_steps"], reps=1)
-        ms = []
-        for i in range(reps + 1):
-            rsv.rsv_compute_reserves(ctx, form, outs, horizon=c["n_steps"], on_device=True, V0=V0, scen_total=tot)
-            if i:
-                ms.append(rsv.rsv_last_kernel_ms(ctx))
-        t = statistics.median(ms)
-        res[name] = {"kernel_ms": t, "valuations_s": c["n_pol"] * c["n_scen"] / (t / 1e3)}
+    tune_ms = None
+    if tune:
+        best, tune_ms = rsv.rsv_tune(ctx, fid, horizon=horizon, reps=1)
+    else:
+        best = 0
+    world = part.world if part else 1
+    for _ in range(warmup):
+        rsv.rsv_compute_reserves(ctx, fid, outs, horizon=horizon, on_device=True, V0=V0, scen_total=tot)
+        if part:
+            part.reduce_totals(tot, dist)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.5)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs, kern = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rsv.rsv_compute_reserves(ctx, fid, outs, horizon=horizon, on_device=True, V0=V0, scen_total=tot)
+        if part:
+            part.reduce_totals(tot, dist)
+        e1.record(stream)
+        evs.append((e0, e1))
+        kern.append(rsv.rsv_last_kernel_ms(ctx))   # waits for this step's kernel
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    r = {"ms_per_step": total_ms / steps, "median_ms": statistics.median(step_ms), "best_ms": min(step_ms),
+         "kernel_ms": statistics.mean(kern), "steps": steps, "variant": rsv.rsv_variant_name(fid, best)}
+    if tune_ms:
+        r["tune_ms"] = {rsv.rsv_variant_name(fid, i): round(m, 3) for i, m in enumerate(tune_ms)}
+    return r, clocks
+
+
+def sampled_rows(rsv, torch, ctx, form, n_pol, n_scen, horizon, idx):
+    """The same launch writing FP64 reserves; the rows of the sampled policies."""
+    V0d = torch.empty((n_pol, n_scen), dtype=torch.float64, device="cuda")
+    rsv.rsv_compute_reserves(ctx, FORMS[form], rsv.RSV_OUT_V0, horizon=horizon, on_device=True, V0d=V0d)
+    torch.cuda.synchronize()
+    rows = V0d[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    del V0d
+    return rows
+
+
+def bench_forms(rsv, torch, ctx, pol, tab, v, forms, horizon, steps, warmup, flush, stream, n_sample, seed,
+                part=None, dist=None, head_sampler=None):
+    """Every form on one loaded workload: timing, algorithmic and issued
+    throughput, and the error of each against the oracle on sampled policies."""
+    import oracle
+    n_pol, n_scen = len(pol["product"]), v.shape[0]
+    V0 = torch.empty((n_pol, n_scen), dtype=torch.float32, device="cuda")
+    tot = torch.empty(n_scen, dtype=torch.float64, device="cuda")
+    world = part.world if part else 1
+    cs = float(projection_steps(pol, horizon=horizon).sum()) * n_scen
+    results, clocks = {}, None
+    for form in forms:
+        slow = form == "f64"
+        r, ck = time_form(rsv, torch, ctx, form, V0, tot, horizon, min(steps, 2) if slow else steps,
+                          1 if slow else warmup, flush, stream, part, dist,
+                          head_sampler if form == forms[0] else None, tune=not slow)
+        if ck:
+            clocks = ck
+        t = r["ms_per_step"] / 1e3
+        r["valuations_s"] = world * n_pol * n_scen / t
+        r["chain_steps_s"] = world * cs / t
+        kt = r["kernel_ms"] / 1e3
+        r["algorithmic_tflops"] = algorithmic_flops(pol, n_scen, horizon) / kt / 1e12
+        r["issued_tflops"] = issued_flops(pol, form, n_scen, horizon, r["variant"]) / kt / 1e12
+        results[form] = r
     del V0
-    # (B) nested, on the first sample_pol policies
-    sub = synth.take(pol, slice(0, c["sample_pol"]))
-    rsv.rsv_load_portfolio(ctx, sub)
+    if n_sample > 0:
+        rng = np.random.default_rng(seed)
+        idx = np.sort(rng.choice(n_pol, min(n_sample, n_pol), replace=False))
+        sub = synth.take(pol, idx)
+        ref, _ = oracle.reserves_batch(sub, tab, v, horizon=horizon)
+        for form in forms:
+            rows = sampled_rows(rsv, torch, ctx, form, n_pol, n_scen, horizon, idx)
+            results[form].update(rel_errors(rows, ref, sub["amount"]))
+            results[form]["error_sample"] = f"{len(idx)} random policies x all {n_scen} scenarios, FP64 output"
+    return results, clocks
+
+
+def bench_config2(rsv, torch, tab, forms, steps, warmup, flush, stream):
+    """Configuration 2 (the four-product mix) in every form."""
+    c = C2
+    pol = synth.portfolio_mix(c["n_pol"], seed=c["seed"])
+    v = synth.vasicek_paths(c["n_scen"], c["n_steps"], seed=c["seed"])
+    ctx = rsv.rsv_create(torch.cuda.current_device(), stream)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    res, _ = bench_forms(rsv, torch, ctx, pol, tab, v, forms, 0, steps, warmup, flush, stream, 300, seed=0)
+    res["workload"] = C2_WORKLOAD
+    return res, ctx, pol
+
+
+def bench_c5_nested(rsv, torch, tab, sur_epochs=10):
+    """Part (B) of the full-scale configuration: the nested run with the
+    surrogate (all 1,000 outer paths, a policy sample, extrapolated by
+    policies), the brute-force inner loop and the closed-form curve (a sample
+    of outer paths too, extrapolated by outer paths and policies);
+    node-liability errors against the curve on the common sample."""
+    c = C5
+    res = {"workload": C5B_WORKLOAD}
+    pol = synth.take(synth.portfolio_single_life(c["n_pol"], seed=c["seed"]), slice(0, c["sample_pol"]))
+    ctx = rsv.rsv_create(torch.cuda.current_device(), torch.cuda.current_stream())
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
     NN = c["n_nodes"]
     t0 = time.perf_counter()
     rsv.rsv_mlp_init(ctx, 0)
@@ -505,91 +709,79 @@ def bench_full_scale(rsv, torch, tab, sur_epochs=10, reps=3):
                                                             / exact[live]))}
     res["B_speedup_surrogate_vs_brute_force"] = (res["B_brute_force"]["extrapolated_full_s"] /
                                                  res["B_surrogate"]["extrapolated_full_s"])
+    res["extrapolation"] = ("times measured on the stated samples on one GB300, scaled linearly by policies (and by "
+                            "outer paths for the brute force) to 1,000,000 policies x 1,000 outer paths")
     return res
 
 
-SURROGATE_WORKLOAD = ("MLP surrogate of the inner-loop expectation: 32->4x256->1 GELU, BF16 weights and activations, "
-                      "FP32 accumulation, trained on 10M recurrence labels of the 100,000-policy mix, scored on 1M "
-                      "held-out queries")
+def bench_e2e(rsv, torch, ctx, pol, tab, v, form, horizon, steps, warmup, world, dist):
+    """The head step through the C ABI with host buffers: uploads of the table,
+    scenarios and portfolio from pinned memory and the device-to-host copy of
+    every reserve inside the timed region."""
+    fid = FORMS[form]
+    outs = rsv.RSV_OUT_V0 | rsv.RSV_OUT_SCEN_TOTAL
+    n_pol, n_scen = len(pol["product"]), v.shape[0]
+    v_host = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+    recs = torch.from_numpy(rsv.policy_records(pol).view(np.uint8)).pin_memory()
+    V0_host = torch.empty((n_pol, n_scen), dtype=torch.float32).pin_memory()
+    tot_host = torch.empty(n_scen, dtype=torch.float64).pin_memory()
+    V0n, totn = V0_host.numpy(), tot_host.numpy()
+    recn = recs.numpy().view(rsv.POLICY_DTYPE)
 
+    def step():
+        rsv.rsv_load_decrements(ctx, 0, tab)
+        rsv.rsv_load_scenarios(ctx, v_host)
+        rsv.rsv_load_portfolio(ctx, recn)
+        rsv.rsv_compute_reserves(ctx, fid, outs, horizon=horizon, on_device=False, V0=V0n, scen_total=totn)
 
-def bench_surrogate(rsv, torch, tab, epochs, lr=2e-3, n_train=10_000_000, n_val=1_000_000):
-    """Train the surrogate on recurrence labels of the four-product portfolio and
-    score it; throughput of the network against the recurrence it replaces."""
-    pol = synth.portfolio_mix(N_POL_MIX, seed=0)
-    ctx = rsv.rsv_create(torch.cuda.current_device(), torch.cuda.current_stream())
-    rsv.rsv_load_decrements(ctx, 0, tab)
-    rsv.rsv_load_portfolio(ctx, pol)
-    rsv.rsv_mlp_init(ctx, 0)
-    rep = rsv.rsv_surrogate_train(ctx, n_train=n_train, n_val=n_val, epochs=epochs, batch=8192, lr=lr, seed=0)
-    rsv.rsv_destroy(ctx)
-    flops_q = 2 * (32 * 256 + 3 * 256 * 256 + 256)
-    return {
-        "workload": SURROGATE_WORKLOAD if (n_train, n_val) == (10_000_000, 1_000_000) else
-        f"profiling case: {n_train} labels, {n_val} held-out queries", "epochs": epochs, "lr": lr,
-        "held_out": {k: rep[k] for k in ("val_max_rel", "val_p99_rel", "val_median_rel", "val_rms_rel")},
-        "tol": 1e-3, "margin": 0.3, "frac_fallback": rep["frac_fallback"], "combined_max_rel": rep["combined_max_rel"],
-        "buckets_flagged": f"{rep['n_flagged']} of {rep['n_buckets']}",
-        "residual_target_sd": rep["y_std"],
-        "network_queries_s": rep["n_infer"] / (rep["infer_ms"] / 1e3),
-        "network_tflops": rep["n_infer"] * flops_q / (rep["infer_ms"] / 1e3) / 1e12,
-        "recurrence_fp64_queries_s": rep["n_label"] / (rep["label_ms"] / 1e3),
-        "train_s": rep["train_ms"] / 1e3,
-        "train_samples_s": epochs * (n_train // 8192) * 8192 / max(rep["train_ms"] / 1e3, 1e-9),
-    }
-
-
-def cpu_baseline(pol, tab, v, n_sample, gpu_rows):
-    """Oracle timed on the host cores on the first n_sample policies x all
-    scenarios; also the max relative error of each GPU form on that sample."""
-    import oracle
-    oracle.build()
-    sub = synth.take(pol, slice(0, n_sample))
-    threads = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    ref, _ = oracle.reserves_batch(sub, tab, v, nthreads=threads)
-    dt = time.perf_counter() - t0
-    errs = {}
-    scale = np.maximum(np.abs(ref), 1e-9 * np.abs(sub["amount"])[:, None])
-    for form, rows in gpu_rows.items():
-        e = np.abs(rows.astype(np.float64) - ref) / scale
-        errs[form] = {"max_rel_err": float(e.max()), "p99_rel_err": float(np.quantile(e, 0.99)),
-                      "median_rel_err": float(np.median(e))}
-    return {"value": n_sample * v.shape[0] / dt, "unit": "valuations/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {n_sample} of {len(pol['product'])} policies x all {v.shape[0]} scenarios "
-                      f"({dt:.1f} s wall)"}, errs
+    for _ in range(max(1, warmup)):
+        step()
+    if world > 1:
+        dist.barrier()
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+    tot_s = sum(times)
+    if world > 1:
+        t = torch.tensor([tot_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_s = float(t.item())
+    return {"value": world * n_pol * n_scen * steps / tot_s, "unit": "valuations/s",
+            "h2d_bytes_per_step": int(v.nbytes + recn.nbytes + tab.nbytes),
+            "d2h_bytes_per_step": int(V0_host.numel() * 4 + tot_host.numel() * 8),
+            "ms_per_step": 1e3 * tot_s / steps,
+            "note": "per rank: uploads of its portfolio share, the scenarios and the table; its V0 and totals back"}
 
 
 def main():
-    global N_POL, N_SCEN, WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="f32comp,f32,f64")
-    ap.add_argument("--cpu-sample", type=int, default=1500, help="policies in the CPU oracle sample")
-    ap.add_argument("--policies", type=int, default=100_000, help="smaller portfolios for profiling runs")
-    ap.add_argument("--scenarios", type=int, default=1000, help="smaller scenario sets for profiling runs")
+    ap.add_argument("--forms", default="f32defl,f32comp,f32,f64", help="the first is the headline form")
+    ap.add_argument("--policies", type=int, default=C5["n_pol"], help="smaller portfolios for profiling runs")
+    ap.add_argument("--scenarios", type=int, default=C5["n_scen"], help="smaller scenario sets for profiling runs")
+    ap.add_argument("--sample-policies", type=int, default=200, help="policies in each form's oracle error sample")
+    ap.add_argument("--cpu-sample", type=int, default=2000, help="policies in each CPU oracle run")
+    ap.add_argument("--cpu-runs", type=int, default=7)
     ap.add_argument("--ref-policies", type=int, default=1000, help="policies per reference-arm step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="only the headline workload")
     ap.add_argument("--no-nested", action="store_true")
-    ap.add_argument("--surrogate-epochs", type=int, default=0, help="train and score the surrogate (0: skip)")
+    ap.add_argument("--surrogate-epochs", type=int, default=30, help="configuration 4 (0: skip)")
     ap.add_argument("--surrogate-lr", type=float, default=2e-3)
     ap.add_argument("--surrogate-train", type=int, default=10_000_000, help="training labels (profiling runs: fewer)")
     ap.add_argument("--surrogate-val", type=int, default=1_000_000, help="held-out queries")
     ap.add_argument("--nested-outer", type=int, default=NESTED["n_outer"], help="outer paths (profiling runs: fewer)")
-    ap.add_argument("--full-scale", action="store_true", help="also the 1M-policy full-scale configuration")
-    ap.add_argument("--mlife-only", action="store_true",
-                    help="time only the m-life contracts (--policies of them) and print their record")
     ap.add_argument("--nested-surrogate-epochs", type=int, default=10,
                     help="train the surrogate on the nested portfolio and time its mode (0: skip)")
+    ap.add_argument("--mlife-only", action="store_true",
+                    help="time only the m-life contracts (--policies of them) and print their record")
     args = ap.parse_args()
-    if (args.policies, args.scenarios) != (N_POL, N_SCEN):
-        N_POL, N_SCEN = args.policies, args.scenarios
-        WORKLOAD = f"profiling case: {N_POL}-policy mix x {N_SCEN} Vasicek scenarios x {N_STEPS} monthly steps"
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -610,194 +802,112 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    # weak scaling: every rank values the full portfolio under its own scenario set
-    pol = synth.portfolio_mix(N_POL, seed=0)
+    full = (args.policies, args.scenarios) == (C5["n_pol"], C5["n_scen"])
+    workload = HEAD_WORKLOAD if full else (f"profiling case: {args.policies} single-life annuities x "
+                                           f"{args.scenarios} Vasicek scenarios x 600 steps")
+    pol_all, v = head_inputs(args.policies, args.scenarios)
     tab = synth.gm_monthly_survival()
-    v = synth.vasicek_paths(N_SCEN, N_STEPS, seed=rank)
+    horizon = C5["horizon"]
+    part = PolicyPartition(projection_steps(pol_all, horizon=horizon), world, rank)
+    pol = part.take(pol_all)
     stream = torch.cuda.current_stream()
     ctx = rsv.rsv_create(local, stream)
     rsv.rsv_load_decrements(ctx, 0, tab)
     rsv.rsv_load_portfolio(ctx, pol)
     rsv.rsv_load_scenarios(ctx, v)
-
-    V0 = torch.empty((N_POL, N_SCEN), dtype=torch.float32, device="cuda")
-    tot = torch.empty(N_SCEN, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    outs = rsv.RSV_OUT_V0 | rsv.RSV_OUT_SCEN_TOTAL
     forms = [f for f in args.forms.split(",") if f]
     head = forms[0]
-    results, sample_rows = {}, {}
-    clocks = None
-    for form in forms:
-        fid = FORMS[form]
-        best, tune_ms = rsv.rsv_tune(ctx, fid, reps=1)
-        K = args.steps if form != "f64" else min(args.steps, 3)
-        for _ in range(args.warmup):
-            rsv.rsv_compute_reserves(ctx, fid, outs, on_device=True, V0=V0, scen_total=tot)
-        torch.cuda.synchronize()
-        sampler = None
-        if form == head:
-            sampler = ClockSampler(local)
-            sampler.start()
-            time.sleep(0.5)
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        evs = []
-        kern_ms = []
-        t_wall = time.perf_counter()
-        for _ in range(K):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            rsv.rsv_compute_reserves(ctx, fid, outs, on_device=True, V0=V0, scen_total=tot)
-            e1.record(stream)
-            evs.append((e0, e1))
-            kern_ms.append(rsv.rsv_last_kernel_ms(ctx))   # waits for this step's kernel
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t_wall
-        if world > 1:
-            dist.barrier()
-        if sampler:
-            clocks = sampler.stop()
-        step_ms = [a.elapsed_time(b) for a, b in evs]
-        total_ms = sum(step_ms)
-        if world > 1:
-            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
-        per_ms = total_ms / K
-        chains = N_POL * N_SCEN
-        results[form] = {
-            "valuations_s": world * chains / (per_ms / 1e3),
-            "chain_steps_s": world * float(policy_steps(pol).sum()) * N_SCEN / (per_ms / 1e3),
-            "ms_per_step": per_ms, "median_ms": statistics.median(step_ms), "best_ms": min(step_ms),
-            "kernel_ms": statistics.mean(kern_ms), "steps": K,
-            "variant": rsv.rsv_variant_name(fid, best),
-            "tune_ms": {rsv.rsv_variant_name(fid, i): round(m, 3) for i, m in enumerate(tune_ms)},
-            "wall_s_incl_flush": wall,
-        }
-        # accuracy sample: the same launch writing FP64 reserves for the first policies
-        V0d = torch.empty((N_POL, N_SCEN), dtype=torch.float64, device="cuda")
-        rsv.rsv_compute_reserves(ctx, fid, rsv.RSV_OUT_V0, on_device=True, V0d=V0d)
-        torch.cuda.synchronize()
-        sample_rows[form] = V0d[: args.cpu_sample].cpu().numpy()
-        del V0d
-
-    # end to end through the C ABI with host buffers (head form)
+    sampler = ClockSampler(local)
+    results, clocks = bench_forms(rsv, torch, ctx, pol, tab, v, forms, horizon, args.steps, args.warmup, flush,
+                                  stream, args.sample_policies if rank == 0 else 0, seed=C5["seed"], part=part,
+                                  dist=dist, head_sampler=sampler)
     e2e = None
     if not args.no_e2e:
-        fid = FORMS[head]
-        v_host = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
-        recs = rsv.policy_records(pol)
-        V0_host = torch.empty((N_POL, N_SCEN), dtype=torch.float32).pin_memory()
-        tot_host = torch.empty(N_SCEN, dtype=torch.float64).pin_memory()
-        V0n, totn = V0_host.numpy(), tot_host.numpy()
-
-        def e2e_step():
-            rsv.rsv_load_decrements(ctx, 0, tab)
-            rsv.rsv_load_scenarios(ctx, v_host)
-            rsv.rsv_load_portfolio(ctx, recs)
-            rsv.rsv_compute_reserves(ctx, fid, outs, on_device=False, V0=V0n, scen_total=totn)
-
-        for _ in range(max(1, args.warmup)):
-            e2e_step()
-        if world > 1:
-            dist.barrier()
-        times = []
-        for _ in range(args.steps):
-            t0 = time.perf_counter()
-            e2e_step()
-            times.append(time.perf_counter() - t0)
-        tot_s = sum(times)
-        if world > 1:
-            t = torch.tensor([tot_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot_s = float(t.item())
-        e2e = {"value": world * N_POL * N_SCEN * args.steps / tot_s, "unit": "valuations/s",
-               "h2d_bytes_per_step": int(v.nbytes + recs.nbytes + tab.nbytes),
-               "d2h_bytes_per_step": int(V0_host.numel() * 4 + tot_host.numel() * 8),
-               "ms_per_step": 1e3 * tot_s / args.steps}
-
-    cashflows = None
-    if not args.no_nested and rank == 0:
-        cashflows = bench_cashflows(rsv, torch, ctx, FORMS[head], results[head]["kernel_ms"], args.steps,
-                                    args.warmup, flush)
+        e2e = bench_e2e(rsv, torch, ctx, pol, tab, v, head, horizon, args.steps, args.warmup, world, dist)
     rsv.rsv_destroy(ctx)
-    nested = config1 = figure1 = mlife = None
-    if not args.no_nested and rank == 0:
-        mlife = bench_mlife(rsv, torch, tab)
-        config1 = bench_config1(rsv, torch, tab)
-        figure1 = bench_figure1(rsv, torch, tab)
-        nested = bench_nested(rsv, torch, tab, steps=2, warmup=1, n_outer=args.nested_outer,
-                              sur_epochs=args.nested_surrogate_epochs)
-    full = None
-    if args.full_scale and rank == 0:
-        full = bench_full_scale(rsv, torch, tab)
+    torch.cuda.empty_cache()
+
+    extras = {}
     peaks = None
     if rank == 0:
         peaks = {"fp32_fma_tflops": rsv.rsv_probe_fma_peak(local, None, False),
                  "fp64_fma_tflops": rsv.rsv_probe_fma_peak(local, None, True),
                  "how": "independent FMA chains on every SM, best of 5 launches"}
-    surrogate = None
-    if args.surrogate_epochs > 0 and rank == 0:
-        surrogate = bench_surrogate(rsv, torch, tab, args.surrogate_epochs, lr=args.surrogate_lr,
-                                    n_train=args.surrogate_train, n_val=args.surrogate_val)
+    if rank == 0 and not args.no_extras:
+        c2, c2ctx, c2pol = bench_config2(rsv, torch, tab, forms, args.steps, args.warmup, flush, stream)
+        extras["config2"] = c2
+        extras["cash_flows"] = bench_cashflows(rsv, torch, c2ctx, FORMS["f32comp"], c2["f32comp"]["kernel_ms"],
+                                               args.steps, args.warmup, flush) if "f32comp" in c2 else None
+        rsv.rsv_destroy(c2ctx)
+        torch.cuda.empty_cache()
+        extras["mlife"] = bench_mlife(rsv, torch, tab)
+        extras["config1_latency"] = bench_config1(rsv, torch, tab)
+        extras["summation_vs_recurrence"] = bench_figure1(rsv, torch, tab)
+        if not args.no_nested:
+            extras["nested"] = bench_nested(rsv, torch, tab, steps=2, warmup=1, n_outer=args.nested_outer,
+                                            sur_epochs=args.nested_surrogate_epochs)
+            extras["full_scale_nested"] = bench_c5_nested(rsv, torch, tab)
+        if args.surrogate_epochs > 0:
+            extras["surrogate"] = bench_surrogate(rsv, torch, tab, args.surrogate_epochs, lr=args.surrogate_lr,
+                                                  n_train=args.surrogate_train, n_val=args.surrogate_val)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    cpu, errs = (None, {})
+    cpu = None
     if not args.no_cpu:
-        cpu, errs = cpu_baseline(pol, tab, v, args.cpu_sample, sample_rows)
-        if figure1 is not None:
-            figure1["cpu_oracle"] = cpu_figure1(tab)
-    for f in results:
-        results[f].update(errs.get(f, {}))
+        cpu = cpu_baseline(pol_all, tab, v, horizon, min(args.cpu_sample, len(pol_all["product"])), args.cpu_runs)
+        if "summation_vs_recurrence" in extras:
+            extras["summation_vs_recurrence"]["cpu_oracle"] = cpu_figure1(tab)
+    for f, r in results.items():
+        pk = peaks["fp64_fma_tflops"] if f == "f64" else peaks["fp32_fma_tflops"]
+        r["algorithmic_frac_of_measured_peak"] = r["algorithmic_tflops"] / pk
+        r["issued_frac_of_measured_peak"] = r["issued_tflops"] / pk
+    if "mlife" in extras:
+        m = extras["mlife"]
+        m["f32comp"]["frac_of_measured_fp32_fma_peak"] = m["f32comp"]["achieved_tflops"] / peaks["fp32_fma_tflops"]
+        m["f64"]["frac_of_measured_fp64_fma_peak"] = m["f64"]["achieved_tflops"] / peaks["fp64_fma_tflops"]
+    if "config2" in extras:
+        for f, r in extras["config2"].items():
+            if isinstance(r, dict) and "algorithmic_tflops" in r:
+                pk = peaks["fp64_fma_tflops"] if f == "f64" else peaks["fp32_fma_tflops"]
+                r["algorithmic_frac_of_measured_peak"] = r["algorithmic_tflops"] / pk
 
     h = results[head]
-    flops = algorithmic_flops(pol, head, N_SCEN)
-    achieved = flops / (h["kernel_ms"] / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": measured_traffic(head),
-            "kernel": f"recur_kernel ({h['variant']})",
+    n_scen = v.shape[0]
+    flops = algorithmic_flops(pol, n_scen, horizon)
+    ifl = issued_flops(pol, head, n_scen, horizon, h["variant"])
+    kt = h["kernel_ms"] / 1e3
+    roof = {"bound": "alu", "achieved": flops / kt / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": flops / kt / 1e12 / FP32_PEAK_TFLOPS,
+            "traffic": measured_traffic(head, "c5A") if full else None,
+            "kernel": f"defl_kernel ({h['variant']}) with its deflator-plane pass" if head == "f32defl" else
+                      f"recur_kernel ({h['variant']})",
+            "flops_per_launch": flops,
+            "count": "algorithmic: 3 flop per one-state chain-step, 16 per three-state chain-step",
             "peak_note": "FP32 FMA pipe, 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal units x max clock)",
-            "flops_per_launch": flops}
-    if peaks:
-        roof["frac_of_measured_fma_peak"] = achieved / peaks["fp32_fma_tflops"]
-    for f, r in results.items():   # every form against the measured peak of its arithmetic
-        fl = algorithmic_flops(pol, f, N_SCEN)
-        r["achieved_tflops"] = fl / (r["kernel_ms"] / 1e3) / 1e12
-        if peaks:
-            pk = peaks["fp64_fma_tflops"] if f == "f64" else peaks["fp32_fma_tflops"]
-            r["frac_of_measured_fma_peak"] = r["achieved_tflops"] / pk
-    if mlife and peaks:
-        mlife["f32comp"]["frac_of_measured_fp32_fma_peak"] = mlife["f32comp"]["achieved_tflops"] / peaks["fp32_fma_tflops"]
-        mlife["f64"]["frac_of_measured_fp64_fma_peak"] = mlife["f64"]["achieved_tflops"] / peaks["fp64_fma_tflops"]
+            "frac_of_measured_fma_peak": flops / kt / 1e12 / peaks["fp32_fma_tflops"],
+            "issued_flops_per_launch": ifl, "issued_frac": ifl / kt / 1e12 / FP32_PEAK_TFLOPS,
+            "issued_count": "FP32 operations the kernel issues per chain-step (FMA 2, others 1)"}
     line = {
         "metric": METRIC, "value": h["valuations_s"], "unit": "valuations/s", "n_gpus": world,
         "steps": h["steps"], "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32-compensated" if head == "f32comp" else head,
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "policies": N_POL, "scenarios": N_SCEN, "steps": N_STEPS,
-                   "form": head, "variant": h["variant"], "l2": "flushed between timed steps (256 MiB write)",
-                   "scenario_seed": "rank"},
+        "scaling": "strong", "vs_baseline": None, "dtype": DTYPE[head], "data": "synthetic",
+        "config": {"workload": workload, "policies": len(pol_all["product"]), "scenarios": n_scen,
+                   "steps": C5["n_steps"], "horizon": horizon, "form": head, "variant": h["variant"],
+                   "max_rel_err_vs_oracle": h.get("max_rel_err"),
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"policy partition over {world} GPU(s), FP64 sum of per-scenario totals"},
         "roofline": roof,
-        "measured_alu_peaks": peaks,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": 3 * h["steps"],
+        "gpu_launches": (4 if head == "f32defl" else 3) * h["steps"],
         "clocks": clocks,
         "forms": results,
-        "config1_latency": config1,
-        "summation_vs_recurrence": figure1,
-        "cash_flows": cashflows,
-        "mlife": mlife,
-        "full_scale": full,
-        "nested": nested,
-        "surrogate": surrogate,
+        "measured_alu_peaks": peaks,
+        **extras,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

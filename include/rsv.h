@@ -620,7 +620,10 @@ const char *rsv_variant_name(int32_t form, int32_t variant);
  * outputs as `opts`), keep the fastest as the context's default for that
  * form and return its index in *best (may be NULL).  reps >= 1 timed runs
  * per variant after one warm-up run; best of reps is compared.
- * ms_out (optional) receives rsv_variant_count(form) times in ms.
+ * ms_out (optional) receives rsv_variant_count(form) times in ms; -1 for a
+ * RSV_FORM_F32_DEFLATED variant whose staging does not fit in shared memory
+ * beside the loaded tables (it is skipped; without a tuned variant the
+ * deflated form falls back to the first that fits).
  * Errors: as rsv_compute_reserves. */
 rsv_status rsv_tune(rsv_ctx *ctx, const rsv_opts *opts, int32_t reps, int32_t *best,
                     float *ms_out);

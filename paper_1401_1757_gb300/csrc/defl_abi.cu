@@ -54,22 +54,50 @@ rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     } else {
         return fail(c, RSV_E_ARG, "variant %d out of range (the deflated form has no scan or summation)", o->variant);
     }
+    // The staged tables: the survivors array A (annuities) and the deaths
+    // array (assurances), each only if a product needs it, for the tables in
+    // use.  A variant whose staging ring does not fit beside them is replaced
+    // by the first that does, unless it was asked for by index.
+    int W = 0;
+    rsv_status st = RSV_OK;
+    bool use_a = false, use_d = false;
+    size_t tab_bytes = 0, smem = 0;
+    int n_tab = 0, dpad = 0;
+    const long long smem_max = defl_smem_limit(c->device);
+    for (int pass = 0;; ++pass) {
+        const DeflVariant& V = vl[vi];
+        W = V.NW * V.P;
+        if ((st = build_layout(c, W, o->horizon, c->n_steps)) != RSV_OK) return st;
+        const Layout& L = c->lay;
+        use_a = use_d = false;
+        for (int k : L.h_k2) {
+            if (k != K_ANN && k != K_ASS && k != K_JL && k != K_ANN2)
+                return fail(c, RSV_E_ARG,
+                            "the deflated form values products 0-5 (single-life, reversionary, joint and last-survivor "
+                            "annuities, term and endowment assurances); use RSV_FORM_F32_COMP for the others");
+            (k == K_ASS ? use_d : use_a) = true;
+        }
+        // a copy holds every entry up to the end of the longest table used,
+        // then zeros: at least one whole group of four past each table's end
+        n_tab = L.n_tab;
+        int max_len = 1;
+        for (int t = 0; t < n_tab; ++t) max_len = std::max(max_len, (int)c->tab[t].size());
+        dpad = (max_len + 8 + 3) / 4 * 4 + 8;   // the last two groups: a unit group, then zeros
+        tab_bytes = (size_t)(use_a + use_d) * n_tab * 4 * dpad * sizeof(float);
+        smem = tab_bytes + defl_smem_extra(V);
+        if ((long long)smem <= smem_max) break;
+        int alt = -1;
+        for (int k = 0; k < nv && alt < 0; ++k)
+            if ((long long)(tab_bytes + defl_smem_extra(vl[k])) <= smem_max) alt = k;
+        if (o->variant >= 0 || alt < 0 || pass > 0)
+            return fail(c, RSV_E_ARG, "variant %s needs %zu bytes of shared memory for %d tables (%lld available)",
+                        V.name, smem, n_tab, smem_max);
+        vi = alt;
+    }
     const DeflVariant& V = vl[vi];
-    const int W = V.NW * V.P, CH = 32 * V.M;
-
-    rsv_status st = build_layout(c, W, o->horizon, c->n_steps);
-    if (st != RSV_OK) return st;
+    const int CH = 32 * V.M;
     const Layout& L = c->lay;
-    for (int k : L.h_k2)
-        if (k != K_ANN && k != K_ASS && k != K_JL && k != K_ANN2)
-            return fail(c, RSV_E_ARG,
-                        "the deflated form values products 0-5 (single-life, reversionary, joint and last-survivor "
-                        "annuities, term and endowment assurances); use RSV_FORM_F32_COMP for the others");
-    const int n_tab = L.n_tab, dpad = L.tab_pad + 4;
-    const size_t tab_bytes = (size_t)2 * n_tab * 4 * dpad * sizeof(float);
-    const size_t smem = tab_bytes + defl_smem_extra(V);
-    if ((long long)smem > defl_smem_limit(c->device))
-        return fail(c, RSV_E_ARG, "the deflated form needs %zu bytes of shared memory for %d tables", smem, n_tab);
+    const int arr_d = use_a ? 1 : 0;   // index of the deaths array among the staged ones
 
     // life tables: [A | deaths][table][4 copies shifted by c][dpad], A_k = l_{k+1}, deaths_k = l_k q_k
     std::vector<std::vector<double>> ell(n_tab);
@@ -80,9 +108,10 @@ rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
                 return fail(c, RSV_E_ARG, "table %d: survival to age %d months is below 2^-220, out of the "
                                           "deflated form's range", t, k + 1);
     }
-    const unsigned long long tkey = c->tab_gen * 1000003ull + (unsigned)dpad * 131ull + (unsigned)n_tab;
+    const unsigned long long tkey = c->tab_gen * 1000003ull + (unsigned)dpad * 131ull + (unsigned)n_tab * 7ull +
+                                    (use_a ? 1ull : 0ull) + (use_d ? 2ull : 0ull);
     if (c->defl_tab_key != tkey) {
-        std::vector<float> h((size_t)2 * n_tab * 4 * dpad, 0.0f);
+        std::vector<float> h((size_t)(use_a + use_d) * n_tab * 4 * dpad, 0.0f);
         for (int t = 0; t < n_tab; ++t) {
             const std::vector<double>& l = ell[t];
             const std::vector<double>& p = c->tab[t];
@@ -90,9 +119,10 @@ rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
                 for (int q = 0; q < dpad; ++q) {
                     const int k = q + cpy;
                     const double pk = k < (int)p.size() ? p[k] : 0.0;
-                    h[(((size_t)0 * n_tab + t) * 4 + cpy) * dpad + q] = (float)l[k + 1];
-                    h[(((size_t)1 * n_tab + t) * 4 + cpy) * dpad + q] = (float)(l[k] * (1.0 - pk));
+                    if (use_a) h[(((size_t)0 * n_tab + t) * 4 + cpy) * dpad + q] = (float)l[k + 1];
+                    if (use_d) h[(((size_t)arr_d * n_tab + t) * 4 + cpy) * dpad + q] = (float)(l[k] * (1.0 - pk));
                 }
+            if (use_d) h[(((size_t)arr_d * n_tab + t) * 4 + 0) * dpad + dpad - 8] = 1.0f;   // the unit group
         }
         CU(c->d_defl_tab.ensure(h.size() * sizeof(float)));
         CU(cudaMemcpyAsync(c->d_defl_tab.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice,
@@ -101,12 +131,26 @@ rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     }
 
     // slot records of the super-tiles
-    const unsigned long long lkey = L.gen * 31ull + (unsigned long long)dpad * 7ull + (unsigned)L.horizon;
+    const unsigned long long lkey = L.gen * 31ull + (unsigned long long)dpad * 7ull + (unsigned)L.horizon * 3ull +
+                                    (unsigned long long)arr_d;
     if (c->defl_lay_key != lkey || c->defl_W != W || c->defl_dpad != dpad || c->defl_n_st != L.n_tiles) {
         std::vector<DeflSlot> ds((size_t)L.n_tiles * W);
         auto off = [&](int arr, int tb, int age) {
             const int cp = age & 3;
             return (int)(((((size_t)arr * n_tab + tb) * 4 + cp) * dpad + (age - cp)) / 4);
+        };
+        // A life's float4 run and its first all-zero group: entries are zero
+        // from z on (z = the table's length for survivors, one more for deaths).
+        // A life already at or past z reads one zero group of copy 0 for every
+        // step.  Every read then stays below z + 7 <= dpad.
+        auto run = [&](int arr, int tb, int age, int z, int& o, int& gz) {
+            if (age >= z) {
+                o = off(arr, tb, (z + 3) / 4 * 4);
+                gz = 0;
+            } else {
+                o = off(arr, tb, age);
+                gz = (z - age + 3) / 4;
+            }
         };
         for (int f = 0; f < L.n_tiles; ++f) {
             const int kind = L.h_k2[f];
@@ -115,18 +159,34 @@ rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
                 DeflSlot d{};
                 const int tb1 = r.idx1 / L.tab_pad, a1 = r.idx1 % L.tab_pad;
                 const int tb2 = r.idx2 / L.tab_pad, a2 = r.idx2 % L.tab_pad;
-                d.off1 = off(kind == K_ASS ? 1 : 0, tb1, a1);
-                d.off2 = off(0, tb2, a2);
+                // survivors are zero from the table's length on, deaths one step
+                // later (everyone left dies in the month at the limiting age)
+                const int z1 = (int)c->tab[tb1].size() + (kind == K_ASS ? 1 : 0), z2 = (int)c->tab[tb2].size();
+                run(kind == K_ASS ? arr_d : 0, tb1, a1, z1, d.off1, d.gz1);
+                run(0, tb2, a2, z2, d.off2, d.gz2);
                 d.S = r.S;
                 d.pol = r.pol;
                 d.kind = kind;
-                const double lx = ell[tb1][a1], ly = ell[tb2][a2];
+                auto ell_at = [&](int tb, int k) { return k < (int)ell[tb].size() ? ell[tb][k] : 0.0; };
+                const double lx = ell_at(tb1, a1), ly = ell_at(tb2, a2);
                 const double amount = r.pol >= 0 ? c->pols[r.pol].amount : 0.0;
                 const double rho = (double)r.rho_h + (double)r.rho_l;
                 double scale = 0.0;
                 if (kind == K_ANN || kind == K_ASS) {
                     scale = lx > 0.0 ? amount / lx : 0.0;
-                    if (kind == K_ASS && r.bnd != 0.0f) d.mat = (float)((double)r.bnd * ell[tb1][a1 + r.S]);
+                    if (kind == K_ASS && r.bnd != 0.0f) d.mat = (float)((double)r.bnd * ell_at(tb1, a1 + r.S));
+                    if (kind == K_ASS && r.S == 0) {   // at maturity: r_0 = bnd, whatever the survival
+                        scale = amount;
+                        d.mat = r.bnd;
+                    } else if (kind == K_ASS && !(lx > 0.0)) {
+                        // alive at an age the table gives no survival to: death in
+                        // the first month is certain; the run is the unit group
+                        // (1, 0, 0, 0) followed by zeros
+                        scale = amount;
+                        d.mat = 0.0f;
+                        d.off1 = off(arr_d, tb1, dpad - 8);
+                        d.gz1 = 1;
+                    }
                 } else {
                     scale = amount;
                     const double ix = lx > 0.0 ? 1.0 / lx : 0.0;

@@ -74,7 +74,9 @@ struct DeflSlot {
     int32_t kind;
     double scale;    // V0 = scale * U: amount / l_x (K_ANN, K_ASS) or amount (K_JL, K_ANN2)
     float sc_h, sc_l;// scale as an FP32 head and tail
-    int32_t pad[4];
+    int32_t gz1, gz2;// first group of four steps whose table entries are all zero (past the
+                     // table's end), life 1 and life 2: reads of later groups read that one
+    int32_t pad[2];
 };
 static_assert(sizeof(DeflSlot) == 64, "DeflSlot layout");
 
@@ -144,7 +146,7 @@ struct DeflLane {
 // What a block needs of a warp's P slots.
 template <int P>
 struct DeflPol {
-    int off1[P], off2[P], S[P];
+    int off1[P], off2[P], S[P], gz1[P], gz2[P];
     float ix[P], iy[P];
 };
 
@@ -153,18 +155,24 @@ struct DeflPol {
 template <int KIND, int P>
 __device__ __forceinline__ float4 defl_weights(const DeflPol<P>& pp, int i, const float4* __restrict__ tab, int g,
                                                bool check) {
+    // A policy's steps run past its table's end where a term assurance outlives
+    // the limiting age or where the other life of a two-life product lives
+    // longer; those entries are zero, and the staged tables hold one zero group
+    // past each table's end, which the reads of later groups are clamped to.
     float4 e;
-    if constexpr (KIND == K_ANN || KIND == K_ASS) {
+    if constexpr (KIND == K_ANN) {   // S never runs past the table's end
         e = tab[pp.off1[i] + g];
+    } else if constexpr (KIND == K_ASS) {
+        e = tab[pp.off1[i] + min(g, pp.gz1[i])];
     } else if constexpr (KIND == K_ANN2) {   // E = P^x P^y
-        const float4 x = tab[pp.off1[i] + g], y = tab[pp.off2[i] + g];
+        const float4 x = tab[pp.off1[i] + min(g, pp.gz1[i])], y = tab[pp.off2[i] + min(g, pp.gz2[i])];
         const float ix = pp.ix[i], iy = pp.iy[i];
         e.x = __fmul_rn(__fmul_rn(x.x, ix), __fmul_rn(y.x, iy));
         e.y = __fmul_rn(__fmul_rn(x.y, ix), __fmul_rn(y.y, iy));
         e.z = __fmul_rn(__fmul_rn(x.z, ix), __fmul_rn(y.z, iy));
         e.w = __fmul_rn(__fmul_rn(x.w, ix), __fmul_rn(y.w, iy));
     } else {   // K_JL: E = P^x (1 - P^y) + P^y
-        const float4 x = tab[pp.off1[i] + g], y = tab[pp.off2[i] + g];
+        const float4 x = tab[pp.off1[i] + min(g, pp.gz1[i])], y = tab[pp.off2[i] + min(g, pp.gz2[i])];
         const float ix = pp.ix[i], iy = pp.iy[i];
         float px = __fmul_rn(x.x, ix), py = __fmul_rn(y.x, iy);
         e.x = __fmaf_rn(px, __fsub_rn(1.0f, py), py);
@@ -373,10 +381,13 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
             for (int i = 0; i < P; ++i) {
                 const int4 q4 = *reinterpret_cast<const int4*>(&rec[i].off1);
                 const float4 f4 = *reinterpret_cast<const float4*>(&rec[i].ix);   // ix, iy, mat, kind
+                const int2 z2 = *reinterpret_cast<const int2*>(&rec[i].gz1);
                 const int S = q4.w < 0 ? 0 : q4.z;
                 const float mat = f4.z;
                 pp.off1[i] = q4.x;
                 pp.off2[i] = q4.y;
+                pp.gz1[i] = z2.x;
+                pp.gz2[i] = z2.y;
                 pp.S[i] = S;
                 pp.ix[i] = f4.x;
                 pp.iy[i] = f4.y;

@@ -1352,22 +1352,33 @@ rsv_status rsv_tune(rsv_ctx* c, const rsv_opts* opts, int32_t reps, int32_t* bes
     out.scen_total = c->d_o_tot.as<double>();
     int arg = -1;
     float best_ms = 0.0f;
+    rsv_status last = RSV_OK;
     for (int v = 0; v < nv; ++v) {
         o.variant = v;
         float vbest = -1.0f;
-        for (int r = 0; r <= reps; ++r) {
+        bool skip = false;
+        for (int r = 0; r <= reps && !skip; ++r) {
             rsv_status st = compute(c, &o, &out);
+            // a deflated variant whose staging does not fit beside the loaded
+            // tables is skipped (time -1); the others decide
+            if (st == RSV_E_ARG && opts->form == F_DEFL) {
+                last = st;
+                skip = true;
+                break;
+            }
             if (st != RSV_OK) return st;
             if ((st = rsv_synchronize(c)) != RSV_OK) return st;
             const float ms = rsv_last_kernel_ms(c);
             if (r > 0 && (vbest < 0 || ms < vbest)) vbest = ms;
         }
         if (ms_out) ms_out[v] = vbest;
+        if (skip) continue;
         if (arg < 0 || vbest < best_ms) {
             arg = v;
             best_ms = vbest;
         }
     }
+    if (arg < 0) return last;
     c->tuned[opts->form] = arg;
     if (best) *best = arg;
     return RSV_OK;

@@ -160,6 +160,32 @@ def test_edge_cases(ctx):
     assert tot[0] == 0.0
 
 
+def test_lives_at_and_past_the_limiting_age(ctx):
+    """Term assurances that run past the limiting age (the benefit is then
+    certain in the month the table ends), a life already past the table's end
+    (death within the first month certain), an endowment at maturity past it,
+    and reversionary annuities with one life past the limit (the other life's
+    annuity, or the reversion from the first month)."""
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_mix(12, seed=6)
+    spec = [(2, 1438, 0, 60), (2, 1440, 0, 12), (2, 1450, 0, 12), (3, 1450, 0, 0), (3, 1420, 0, 120),
+            (1, 900, 1445, 0), (1, 1445, 700, 0), (1, 1300, 1300, 0), (0, 1440, 0, 0), (2, 30, 0, 480),
+            (3, 1000, 0, 600), (1, 240, 1020, 0)]
+    for i, (p, a1, a2, term) in enumerate(spec):
+        pol["product"][i], pol["age1_m"][i], pol["age2_m"][i], pol["term_m"][i] = p, a1, a2, term
+        pol["reversion"][i] = 0.8 if p == 1 else 0.0
+    v = synth.vasicek_paths(40, 1500, seed=6)
+    V0, tot = run(ctx, pol, [tab], v)
+    ref, ref_tot = oracle.reserves_batch(pol, tab, v)
+    err = rel_err(V0, ref, pol["amount"])
+    print("limiting-age cases:", " ".join(f"{e:.1e}" for e in err.max(axis=1)))
+    assert err.max() <= TOL
+    assert np.max(np.abs(tot - ref_tot) / ref_tot) <= TOL
+    # past the table's end: the whole sum at the end of the first month
+    assert np.allclose(V0[2], pol["amount"][2] * v[:, 0], rtol=1e-7, atol=0)
+    assert np.allclose(V0[3], pol["amount"][3], rtol=1e-7, atol=0)
+
+
 def test_joint_and_last_survivor_annuities(ctx):
     """Joint-life and last-survivor annuities (two tables) beside the mix; the
     two-life assurances are not taken by this form (RSV_E_ARG)."""

@@ -1,8 +1,10 @@
 """Multi-rank logic on CPU: world_size-2 gloo process groups.
 
-Each rank values its shard with the FP64 oracle standing in for its GPU; the
-shards put back together must equal the single-process result, and the
-max-over-ranks timing reduction the benchmark uses must pick the slowest rank.
+Each rank values its shard with the FP64 oracle standing in for its GPU.  The
+policy mode uses the partition and the FP64 reduction of the totals that the
+benchmark's multi-GPU path runs (``PolicyPartition``); the shards put back
+together must equal the single-process result, and the max-over-ranks timing
+reduction the benchmark uses must pick the slowest rank.
 """
 import os
 import socket
@@ -14,7 +16,7 @@ import torch.multiprocessing as mp
 
 import oracle
 import synth
-from paper_1401_1757_gb300.shard import policy_shard, scenario_shard
+from paper_1401_1757_gb300.shard import PolicyPartition, policy_shard, projection_steps, scenario_shard
 
 
 def free_port():
@@ -39,12 +41,9 @@ def _worker(rank, world, port, mode, out):
         full[lo:hi] = torch.from_numpy(tot)
         dist.all_reduce(full)            # gather for the check only
     else:
-        S = np.array([oracle.steps(int(p), int(a1), int(a2), int(t), 1440)[0] for p, a1, a2, t in
-                      zip(pol["product"], pol["age1_m"], pol["age2_m"], pol["term_m"])])
-        mine = policy_shard(S, world)[rank]
-        V0, tot = oracle.reserves_batch(synth.take(pol, mine), tab, v, nthreads=1)
-        full = torch.from_numpy(tot)
-        dist.all_reduce(full)            # partial per-scenario sums
+        part = PolicyPartition(projection_steps(pol), world, rank)
+        V0, tot = oracle.reserves_batch(part.take(pol), tab, v, nthreads=1)
+        full = part.reduce_totals(torch.from_numpy(tot), dist)   # partial per-scenario sums
     t = torch.tensor([float(rank + 1)], dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     if rank == 0:
@@ -77,6 +76,12 @@ def test_shard_helpers():
         assert parts[0][0] == 0 and parts[-1][1] == n
         assert all(a[1] == b[0] for a, b in zip(parts, parts[1:]))
         assert max(h - l for l, h in parts) - min(h - l for l, h in parts) <= 1
+    pol = synth.portfolio_mix(300, seed=4)
+    S = projection_steps(pol)
+    want = [oracle.steps(int(p), int(a1), int(a2), int(t), 1440)[0] for p, a1, a2, t in
+            zip(pol["product"], pol["age1_m"], pol["age2_m"], pol["term_m"])]
+    assert S.tolist() == want
+    assert projection_steps(pol, horizon=100).max() <= 100
     steps = np.random.default_rng(0).integers(60, 1200, 1001)
     shards = policy_shard(steps, 4)
     assert sorted(np.concatenate(shards).tolist()) == list(range(1001))
