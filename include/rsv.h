@@ -444,15 +444,21 @@ rsv_status rsv_compute_nested(rsv_ctx *ctx, const rsv_opts *opts, const rsv_nest
  * up to 256 B); larger calls return RSV_E_LIMIT before any GPU work (100,000
  * policies x 1,000 scenarios x 1,200 steps needs 17.4 MB).
  * The first call on a device looks up the array's device address (with that
- * device current) and keeps it; make that first call before any stream
- * capture.  Every call shares the array and leaves its contents behind; each
- * call re-initialises what it reads, but calls whose GPU work overlaps (other
- * streams or host threads) race on it: serialise them.  The call is issued on
- * `cuda_stream` (NULL = legacy default) and blocks until it has finished.
- * It takes the single-table products RSV_SL_ANNUITY .. RSV_ENDOWMENT.
- * Errors: RSV_E_ARG (NULL pointer, bad size, a record the main entry point
- * would reject, a two-life product other than RSV_JL_REVERSIONARY), RSV_E_LIMIT, RSV_E_ASSUMPTION (a table entry outside [0, 1], a
- * discount factor not finite and positive), RSV_E_CUDA, RSV_E_TIMEOUT; on an
+ * device current) and keeps it.  Every call shares the array and leaves its
+ * contents behind; each call re-initialises what it reads, but calls whose
+ * GPU work overlaps (other streams or host threads) race on it: serialise
+ * them.  The call is issued on `cuda_stream` (NULL = legacy default) and
+ * blocks until its work is done (it reads its status back to the host), so it
+ * cannot be issued inside a stream capture.
+ * It takes the products RSV_SL_ANNUITY .. RSV_ENDOWMENT on decrement table 0.
+ * Errors: RSV_E_ARG (NULL pointer, bad size, a record that breaks an argument
+ * rule of the main entry point: product, table, age, term, state, reserved
+ * field, age plus steps above 4096), RSV_E_LIMIT (sizes beyond the scratch,
+ * refused before any GPU work), RSV_E_ASSUMPTION (a table entry outside
+ * [0, 1], a discount factor not finite and positive, or a record with an
+ * amount not finite, a reversion outside [0, 1] or more steps than the
+ * scenarios; with several bad records, the status of the first in portfolio
+ * order, as the main entry point reports), RSV_E_CUDA, RSV_E_TIMEOUT; on an
  * error the outputs are unspecified. */
 rsv_status rsv_reserves_noalloc(int device, void *cuda_stream, const rsv_policy *pols, int32_t n_pol,
                                 const double *p_monthly, int32_t n_ages, const double *v, int32_t n_scen,
@@ -501,6 +507,26 @@ rsv_status rsv_mlp_forward(rsv_ctx *ctx, const float *X, int64_t n, float *y);
  * receives the mean squared error.  Uses the network's current parameters. */
 rsv_status rsv_mlp_gradient(rsv_ctx *ctx, const float *X, const float *target, int64_t n, float *grads,
                             float *loss);
+
+/* Test entry point (the paper has no counterpart): one pass of the network on
+ * n rows of 32 host FP32 features (n a multiple of 128, at most 4096) with
+ * every layer's values, so that each layer can be checked on its own against
+ * a reference fed the same inputs.  All outputs are host buffers owned by the
+ * caller.  Xb [n][64]: the BF16 bits of the features as the first layer reads
+ * them (hi halves, then lo halves; may be NULL).  y [n]: the outputs.
+ * backend RSV_MLP_MMA_SYNC (the training kernels): Z [4][n][256] the FP32
+ * pre-activations z_l = A_{l-1} W_l + b_l, A [4][n][256] the BF16 bits of
+ * gelu(z_l) as stored for the next product (the head reads layer 4 in FP32);
+ * with a target [n] also the backward pass of the mean squared error:
+ * dZ [4][n][256] the FP32 gradients with respect to z_l, dZb the BF16 bits the
+ * products read, grads [rsv_mlp_param_count()] the parameter gradients.
+ * backend RSV_MLP_TCGEN05 (the inference kernel): Z as above and in A the
+ * first three layers' BF16 operands as the kernel stores them in tensor
+ * memory, 2 gelu(z_l) (its next layer's weights are staged halved); target,
+ * dZ, dZb and grads must be NULL.  Blocks until done.
+ * Errors: RSV_E_ARG, RSV_E_STATE (no network), RSV_E_CUDA, RSV_E_TIMEOUT. */
+rsv_status rsv_mlp_trace(rsv_ctx *ctx, int32_t backend, const float *X, const float *target, int64_t n,
+                         uint16_t *Xb, float *Z, uint16_t *A, float *y, float *dZ, uint16_t *dZb, float *grads);
 
 typedef struct {
     int64_t n_train;     /* labelled training queries (>= 1024)                       */

@@ -196,6 +196,7 @@ struct rsv_ctx {
     DevBuf d_pols;                  // policy records on the device (surrogate queries)
     unsigned long long pols_dev_gen = 0;
     rsv::SurrogateState sur;
+    DevBuf d_mlp_trace;             // layer-by-layer outputs of rsv_mlp_trace (tcgen05 path)
 };
 
 

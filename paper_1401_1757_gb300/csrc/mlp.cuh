@@ -55,7 +55,11 @@ struct Mlp {
     cudaError_t adam_step(float lr, cudaStream_t st);
     // inference only: X [n][MLP_XW], n a multiple of 128, all four layers and
     // the head in one tcgen05 kernel (mlp_tc.cu)
-    cudaError_t forward_tc(const __nv_bfloat16* X, int n, float* y, int sm_count, int32_t* status, cudaStream_t st);
+    // trace_z / trace_a (optional, device): every layer's pre-activations
+    // [4][n][256] FP32 and the BF16 operands of the next layer [3][n][256]
+    // (2 gelu(z): the next layer's weights are staged halved)
+    cudaError_t forward_tc(const __nv_bfloat16* X, int n, float* y, int sm_count, int32_t* status, cudaStream_t st,
+                           float* trace_z = nullptr, void* trace_a = nullptr);
 };
 
 }  // namespace rsv

@@ -55,6 +55,11 @@ struct TcArgs {
     float* y;             // [n_rows]
     int n_tiles;
     int32_t* status;
+    // layer-by-layer test output, or null: pre-activations z = D + b of every
+    // layer [4][n_rows][256] and the BF16 operands written to TMEM for the next
+    // layer, 2 gelu(z), [3][n_rows][256]
+    float* trace_z;
+    uint32_t* trace_a;    // BF16 pairs
 };
 
 // ---- PTX wrappers ---------------------------------------------------------
@@ -311,6 +316,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float v[32];
                     tmem_ld32(tmem + lane_base + c0, v);
                     const float4* b4 = reinterpret_cast<const float4*>(&bias_s[l - 1][c0]);
+                    const size_t trow = (size_t)tile * TM + row;   // the row in the traced outputs
+                    if (a.trace_z) {
+                        float* tz = a.trace_z + (((size_t)(l - 1) * a.n_tiles * TM + trow) * TN + c0);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const float4 b = b4[i];
+                            tz[4 * i] = v[4 * i] + b.x;
+                            tz[4 * i + 1] = v[4 * i + 1] + b.y;
+                            tz[4 * i + 2] = v[4 * i + 2] + b.z;
+                            tz[4 * i + 3] = v[4 * i + 3] + b.w;
+                        }
+                    }
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const float4 b = b4[i];
@@ -324,6 +341,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int m = 0; m < 16; ++m) r[m] = pack_bf16x2(v[2 * m], v[2 * m + 1]);
                         tmem_st16(tmem + lane_base + acol_of((l - 1) & 1) + c0 / 2, r);
+                        if (a.trace_a) {
+                            uint32_t* ta = a.trace_a + (((size_t)(l - 1) * a.n_tiles * TM + trow) * TN + c0) / 2;
+#pragma unroll
+                            for (int m = 0; m < 16; ++m) ta[m] = r[m];
+                        }
                     } else {
 #pragma unroll
                         for (int i = 0; i < 32; ++i) ysum = __fmaf_rn(v[i], w5_s[c0 + i], ysum);
@@ -397,7 +419,7 @@ __global__ void transpose_w_kernel(const float* __restrict__ W, int K, __nv_bflo
 // y (FP32 [n]) on the tensor cores.  Returns cudaErrorNotSupported when the
 // tensor-map encoder is unavailable.
 cudaError_t Mlp::forward_tc(const __nv_bfloat16* Xin, int n, float* yout, int sm_count, int32_t* status,
-                            cudaStream_t st) {
+                            cudaStream_t st, float* trace_z, void* trace_a) {
     if (n % TM) return cudaErrorInvalidValue;
     cudaError_t e;
     if (!wt) {
@@ -425,6 +447,8 @@ cudaError_t Mlp::forward_tc(const __nv_bfloat16* Xin, int n, float* yout, int sm
     a.y = yout;
     a.n_tiles = n / TM;
     a.status = status;
+    a.trace_z = trace_z;
+    a.trace_a = static_cast<uint32_t*>(trace_a);
     const size_t smem = X_BYTES + W_BYTES + 1024;
     if ((e = cudaFuncSetAttribute(mlp_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)

@@ -42,7 +42,11 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_rsv_noalloc_scratch[kScratchBytes];
 
-enum { CTL_COUNTER = 0, CTL_STATUS = 1, CTL_BAD = 2 };
+// Control words.  CTL_BAD_ARG / CTL_BAD_ASM: the smallest index of a record
+// that breaks an argument rule (RSV_E_ARG) / an assumption of Section 3.7
+// (RSV_E_ASSUMPTION), INT32_MAX if none; the call reports the first bad record
+// in portfolio order, as rsv_compute_reserves does.
+enum { CTL_COUNTER = 0, CTL_STATUS = 1, CTL_BAD_ARG = 2, CTL_BAD_ASM = 3 };
 enum : int32_t { NA_OK = 0, NA_TIMEOUT = DEV_TIMEOUT, NA_BAD_INPUT = 3 };
 
 struct NaLayout {
@@ -57,7 +61,7 @@ struct NaLayout {
 };
 
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }
-__host__ __device__ inline int scen_pad(int n_scen) { return (n_scen + 127) / 128 * 128; }
+__host__ __device__ inline size_t scen_pad(int n_scen) { return ((size_t)n_scen + 127) / 128 * 128; }
 
 __host__ __device__ inline NaLayout carve(unsigned char* base, int n_pol, int n_scen, int n_steps) {
     NaLayout L;
@@ -102,7 +106,7 @@ __global__ void na_prepare_kernel(unsigned char* scratch, const rsv_policy* __re
         const float ph = __double2float_rn(p), qh = __double2float_rn(q);
         L.tab[k] = make_float4(ph, __double2float_rn(p - (double)ph), qh, __double2float_rn(q - (double)qh));
     }
-    const int sp = scen_pad(n_scen);
+    const size_t sp = scen_pad(n_scen);
     for (size_t i = tid; i < (size_t)n_steps * sp; i += nth) {
         const int t = (int)(i / sp), s = (int)(i % sp);
         double x = 1.0;   // padding scenarios: any finite factor, never written out
@@ -116,10 +120,13 @@ __global__ void na_prepare_kernel(unsigned char* scratch, const rsv_policy* __re
     for (size_t i = tid; i < (size_t)n_pol; i += nth) {
         const rsv_policy r = pols[i];
         const bool jl = r.product == RSV_JL_REVERSIONARY;
+        // the checks of rsv_compute_reserves, in its order: argument rules,
+        // then the assumptions (amount, reversion, scenario length), then the
+        // table bound on age + steps
         bool ok = r.product >= RSV_SL_ANNUITY && r.product <= RSV_ENDOWMENT && r.reserved == 0 && r.table1 == 0 &&
                   (!jl || r.table2 == 0) && r.age1_m >= 0 && (!jl || r.age2_m >= 0) && r.term_m >= 0 &&
-                  r.state0 >= 0 && r.state0 <= (jl ? 2 : 0) && isfinite(r.amount) &&
-                  (!jl || (r.reversion >= 0.0 && r.reversion <= 1.0));
+                  r.state0 >= 0 && r.state0 <= (jl ? 2 : 0);
+        bool assumption = false;
         int S = 0;
         if (ok) {
             if (r.product == RSV_SL_ANNUITY) {
@@ -131,7 +138,9 @@ __global__ void na_prepare_kernel(unsigned char* scratch, const rsv_policy* __re
             } else {
                 S = r.term_m;
             }
-            ok = S <= n_steps && r.age1_m + S <= kTabEntries && (!jl || r.age2_m + S <= kTabEntries);
+            assumption = !isfinite(r.amount) || (jl && !(r.reversion >= 0.0 && r.reversion <= 1.0)) || S > n_steps;
+            ok = !assumption && (long long)r.age1_m + S <= kTabEntries &&
+                 (!jl || (long long)r.age2_m + S <= kTabEntries);
         }
         SlotRec s;
         s.idx1 = ok ? r.age1_m : 0;
@@ -146,7 +155,16 @@ __global__ void na_prepare_kernel(unsigned char* scratch, const rsv_policy* __re
         L.slots[i] = s;
         L.kinds[i] = jl ? K_JL : (r.product == RSV_SL_ANNUITY ? K_ANN : K_ASS);
         L.amount[i] = ok ? r.amount : 0.0;
-        if (!ok) atomicAdd(&L.ctl[CTL_BAD], 1);
+        if (!ok) atomicMin(&L.ctl[assumption ? CTL_BAD_ASM : CTL_BAD_ARG], (int)i);
+    }
+}
+
+__global__ void na_init_ctl_kernel(int32_t* ctl) {
+    if (threadIdx.x == 0) {
+        ctl[CTL_COUNTER] = 0;
+        ctl[CTL_STATUS] = NA_OK;
+        ctl[CTL_BAD_ARG] = INT32_MAX;
+        ctl[CTL_BAD_ASM] = INT32_MAX;
     }
 }
 
@@ -239,7 +257,11 @@ extern "C" rsv_status rsv_reserves_noalloc(int device, void* cuda_stream, const 
     if (device < 0 || device >= kMaxDevices || n_pol < 0 || (n_pol > 0 && (!pols || !V0)) || !p_monthly ||
         n_ages < 1 || n_ages > kTabEntries || !v || n_scen < 1 || n_steps < 1)
         return RSV_E_ARG;
-    if (na_bytes(n_pol, n_scen, n_steps) > kScratchBytes) return RSV_E_LIMIT;
+    // every size term is computed in 64-bit; a dimension that alone exceeds the
+    // scratch is refused before the sum is formed
+    if ((size_t)n_scen > kScratchBytes / sizeof(double) || (size_t)n_steps > kScratchBytes / sizeof(double) ||
+        (size_t)n_pol > kScratchBytes / sizeof(SlotRec) || na_bytes(n_pol, n_scen, n_steps) > kScratchBytes)
+        return RSV_E_LIMIT;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (cudaSetDevice(device) != cudaSuccess) return RSV_E_CUDA;
     unsigned char* scratch = nullptr;
@@ -251,7 +273,8 @@ extern "C" rsv_status rsv_reserves_noalloc(int device, void* cuda_stream, const 
         return RSV_E_CUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, na_recur_kernel, 256, smem) != cudaSuccess || bps < 1)
         return RSV_E_CUDA;
-    if (cudaMemsetAsync(scratch, 0, kCtlBytes, st) != cudaSuccess) return RSV_E_CUDA;
+    na_init_ctl_kernel<<<1, 32, 0, st>>>(reinterpret_cast<int32_t*>(scratch));
+    if (cudaGetLastError() != cudaSuccess) return RSV_E_CUDA;
     na_prepare_kernel<<<sms * 4, 256, 0, st>>>(scratch, pols, n_pol, p_monthly, n_ages, v, n_scen, n_steps);
     if (cudaGetLastError() != cudaSuccess) return RSV_E_CUDA;
     if (n_pol > 0) {
@@ -269,12 +292,13 @@ extern "C" rsv_status rsv_reserves_noalloc(int device, void* cuda_stream, const 
         na_total_kernel<<<(n_scen + 127) / 128, 128, 0, st>>>(scratch, n_pol, n_scen, n_steps, scen_total);
         if (cudaGetLastError() != cudaSuccess) return RSV_E_CUDA;
     }
-    int32_t ctl[3] = {0, 0, 0};
+    int32_t ctl[4] = {0, 0, 0, 0};
     if (cudaMemcpyAsync(ctl, scratch, sizeof ctl, cudaMemcpyDeviceToHost, st) != cudaSuccess) return RSV_E_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return RSV_E_CUDA;
     if (ctl[CTL_STATUS] == NA_TIMEOUT) return RSV_E_TIMEOUT;
-    if (ctl[CTL_STATUS] == NA_BAD_INPUT) return RSV_E_ASSUMPTION;
-    if (ctl[CTL_BAD] > 0) return RSV_E_ARG;
+    if (ctl[CTL_STATUS] == NA_BAD_INPUT) return RSV_E_ASSUMPTION;   // a table entry or discount factor
+    if (ctl[CTL_BAD_ARG] != INT32_MAX || ctl[CTL_BAD_ASM] != INT32_MAX)
+        return ctl[CTL_BAD_ARG] < ctl[CTL_BAD_ASM] ? RSV_E_ARG : RSV_E_ASSUMPTION;
     return RSV_OK;
 } catch (...) {
     return rsv::host_error(nullptr);

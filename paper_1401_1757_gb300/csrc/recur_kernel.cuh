@@ -315,9 +315,12 @@ struct Tile {
             }
         }
         if (e.pt_sum) {
+            // a fixed order: a butterfly over the lanes, then the tile's warp
+            // adds its scenario chunks one after the other (recur_kernel gives
+            // every chunk of a tile to one warp when side outputs are on)
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            if ((threadIdx.x & 31) == 0) atomicAdd(&e.pt_sum[row], sum);
+            if ((threadIdx.x & 31) == 0) e.pt_sum[row] += sum;
         }
     }
 
@@ -560,11 +563,29 @@ __global__ void __launch_bounds__(NT, MINB) recur_kernel(const RecurArgs a) {
     const TileEnv env{a.slots, a.v, a.s_pad, a.n_scen, a.n_steps, a.amount, a.traj, a.pt_sum, a.v0_ld, a.vf,
                       a.tabf_off, a.cf, a.cf_ld};
     const int lane = threadIdx.x & 31;
+    // With side outputs a work item is a whole tile, its scenario chunks run
+    // in order by one warp, so that the per-step sums over scenarios are added
+    // in a fixed order; otherwise an item is one (tile, chunk).
+    const int n_work = EXTRA ? a.n_tiles : a.n_items;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(a.counter, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= a.n_items) break;
+        if (item >= n_work) break;
+        if constexpr (EXTRA) {
+            const int kind = a.tile_kind[item];
+            for (int chunk = 0; chunk < a.n_chunks; ++chunk) {
+                if (kind == K_JL) run_item<FORM, P, M, K_JL, EXTRA, PAY>(env, tab, item, chunk, lane, a);
+                else if (kind == K_ANN) run_item<FORM, P, M, K_ANN, EXTRA, PAY>(env, tab, item, chunk, lane, a);
+                else if (!TWO || kind == K_ASS) run_item<FORM, P, M, K_ASS, EXTRA, PAY>(env, tab, item, chunk, lane, a);
+                else if constexpr (TWO) {
+                    if (kind == K_ANN2) run_item<FORM, P, M, K_ANN2, EXTRA, PAY>(env, tab, item, chunk, lane, a);
+                    else if (kind == K_ASS2) run_item<FORM, P, M, K_ASS2, EXTRA, PAY>(env, tab, item, chunk, lane, a);
+                    else run_item<FORM, P, M, K_LS2, EXTRA, PAY>(env, tab, item, chunk, lane, a);
+                }
+            }
+            continue;
+        }
         const int tile = item / a.n_chunks;
         const int chunk = item - tile * a.n_chunks;
         const int kind = a.tile_kind[tile];

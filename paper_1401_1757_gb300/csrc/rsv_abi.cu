@@ -1099,7 +1099,7 @@ rsv_status rsv_destroy(rsv_ctx* c) try {
                       &c->sur.d_comm, &c->sur.d_lnb, &c->d_tabf[0], &c->d_tabf[1], &c->d_tabf[2], &c->d_vf64,
                       &c->d_vf32, &c->d_vf2, &c->d_cf64, &c->d_cf32, &c->d_ml_rec,
                       &c->d_ml_amount, &c->sur.d_cnt, &c->sur.d_q2, &c->sur.d_idx, &c->sur.d_v2, &c->d_nest_bm,
-                      &c->d_defl_slots, &c->d_defl_kinds, &c->d_defl_tab, &c->d_defl_plane})
+                      &c->d_defl_slots, &c->d_defl_kinds, &c->d_defl_tab, &c->d_defl_plane, &c->d_mlp_trace})
         b->release();
     c->mlp.release();
     if (c->ev0) cudaEventDestroy(c->ev0);

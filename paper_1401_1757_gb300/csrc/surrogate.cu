@@ -972,6 +972,56 @@ rsv_status rsv_mlp_gradient(rsv_ctx* c, const float* X, const float* target, int
     return rsv::host_error(c);
 }
 
+rsv_status rsv_mlp_trace(rsv_ctx* c, int32_t backend, const float* X, const float* target, int64_t n, uint16_t* Xb,
+                         float* Z, uint16_t* A, float* y, float* dZ, uint16_t* dZb, float* grads) try {
+    if (!c) return RSV_E_ARG;
+    const bool tc = backend == RSV_MLP_TCGEN05;
+    if ((backend != RSV_MLP_MMA_SYNC && !tc) || !X || !Z || !A || !y || n < 128 || n % 128 || n > 4096)
+        return fail(c, RSV_E_ARG, "bad trace arguments (n a multiple of 128, at most 4096)");
+    if (tc && (target || dZ || dZb || grads)) return fail(c, RSV_E_ARG, "the tcgen05 path traces the forward pass only");
+    if (!tc && (target != nullptr) != (dZ != nullptr && dZb != nullptr && grads != nullptr))
+        return fail(c, RSV_E_ARG, "a target needs dZ, dZb and grads (and they need a target)");
+    if (!c->mlp_ready) return fail(c, RSV_E_STATE, "network not initialised");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, RSV_E_CUDA, "cudaSetDevice failed");
+    rsv_status st = mlp_stage_inputs(c, X, n, n);
+    if (st != RSV_OK) return st;
+    const size_t L = (size_t)n * MLP_H;   // one layer's values
+    if (tc) {
+        CU(c->d_ctl.ensure(2 * sizeof(int32_t)));
+        CU(cudaMemsetAsync(c->d_ctl.p, 0, 2 * sizeof(int32_t), c->stream));
+        CU(c->d_mlp_trace.ensure(4 * L * 4 + 3 * L * 2));
+        float* tz = c->d_mlp_trace.as<float>();
+        uint16_t* ta = reinterpret_cast<uint16_t*>(tz + 4 * L);
+        CU(c->mlp.forward_tc(c->mlp.X, (int)n, c->mlp.y, c->sm_count, c->d_ctl.as<int32_t>() + 1, c->stream, tz, ta));
+        CU(cudaMemcpyAsync(Z, tz, 4 * L * 4, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(A, ta, 3 * L * 2, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        if (target) CU(cudaMemcpyAsync(c->mlp.t, target, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
+        CU(c->mlp.forward(c->mlp.X, (int)n, c->mlp.y, target ? c->mlp.t : nullptr, c->stream));
+        if (target) CU(c->mlp.backward(c->mlp.X, (int)n, c->stream));
+        for (int l = 0; l < 4; ++l) {
+            CU(cudaMemcpyAsync(Z + l * L, c->mlp.Z[l], L * 4, cudaMemcpyDeviceToHost, c->stream));
+            CU(cudaMemcpyAsync(A + l * L, c->mlp.A[l], L * 2, cudaMemcpyDeviceToHost, c->stream));
+            if (target) {
+                CU(cudaMemcpyAsync(dZ + l * L, c->mlp.dZf[l], L * 4, cudaMemcpyDeviceToHost, c->stream));
+                CU(cudaMemcpyAsync(dZb + l * L, c->mlp.dZb[l], L * 2, cudaMemcpyDeviceToHost, c->stream));
+            }
+        }
+        if (target) CU(cudaMemcpyAsync(grads, c->mlp.grads, mlp_n_params() * 4, cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (Xb) CU(cudaMemcpyAsync(Xb, c->mlp.X, (size_t)n * MLP_XW * 2, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(y, c->mlp.y, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (tc) {
+        int32_t ctl[2] = {0, 0};
+        CU(cudaMemcpy(ctl, c->d_ctl.p, sizeof ctl, cudaMemcpyDeviceToHost));
+        if (ctl[1] == DEV_TIMEOUT) return fail(c, RSV_E_TIMEOUT, "a bounded device wait ran out (tcgen05 inference)");
+    }
+    return RSV_OK;
+} catch (...) {
+    return rsv::host_error(c);
+}
+
 }  // extern "C"
 
 namespace {

@@ -120,7 +120,7 @@ EXPORTS = ["rsv_create", "rsv_destroy", "rsv_set_stream", "rsv_load_decrements",
            "rsv_tune", "rsv_synchronize", "rsv_last_error", "rsv_last_kernel_ms", "rsv_device_sm_count",
            "rsv_reserves_noalloc", "rsv_mlp_param_count", "rsv_mlp_init", "rsv_mlp_set_params",
            "rsv_mlp_get_params", "rsv_mlp_set_backend", "rsv_mlp_forward", "rsv_mlp_gradient", "rsv_surrogate_train",
-           "rsv_surrogate_query", "rsv_probe_fma_peak"]
+           "rsv_surrogate_query", "rsv_probe_fma_peak", "rsv_mlp_trace"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -175,6 +175,7 @@ def load_library(path: str = LIB_PATH):
         "rsv_surrogate_train": ([vp, C.POINTER(rsv_surrogate_cfg), C.POINTER(rsv_surrogate_report)], i32),
         "rsv_surrogate_query": ([vp, vp, i64, i32, vp], i32),
         "rsv_probe_fma_peak": ([i32, vp, i32, C.POINTER(C.c_double)], i32),
+        "rsv_mlp_trace": ([vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -467,6 +468,40 @@ def rsv_mlp_gradient(ctx, X, target):
     _check(ctx, _lib.rsv_mlp_gradient(ctx, X.ctypes.data, t.ctypes.data, X.shape[0], g.ctypes.data,
                                       C.byref(loss)))
     return g, loss.value
+
+
+def bf16_bits_to_f64(bits):
+    """BF16 values given by their 16-bit patterns, as FP64 (exact)."""
+    b = np.ascontiguousarray(bits, dtype=np.uint16)
+    return (b.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def rsv_mlp_trace(ctx, X, backend: int = RSV_MLP_MMA_SYNC, target=None):
+    """One pass of the network with every layer's values (see include/rsv.h).
+    Returns a dict: Xb [n][64], Z [4][n][256], A [4][n][256] (FP64 of the BF16
+    values; the tcgen05 path fills A[0..2] with 2 gelu), y [n]; with a target
+    (mma.sync only) also dZ, dZb [4][n][256] and grads."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    n = X.shape[0]
+    L = n * 256
+    Xb = np.zeros((n, 64), np.uint16)
+    Z = np.zeros((4, n, 256), np.float32)
+    A = np.zeros((4, n, 256), np.uint16)
+    y = np.zeros(n, np.float32)
+    dZ = dZb = grads = t = None
+    if target is not None:
+        t = np.ascontiguousarray(target, dtype=np.float32)
+        dZ = np.zeros((4, n, 256), np.float32)
+        dZb = np.zeros((4, n, 256), np.uint16)
+        grads = np.zeros(rsv_mlp_param_count(), np.float32)
+    _check(ctx, _lib.rsv_mlp_trace(ctx, backend, X.ctypes.data, _ptr(t), n, Xb.ctypes.data, Z.ctypes.data,
+                                   A.ctypes.data, y.ctypes.data, _ptr(dZ), _ptr(dZb), _ptr(grads)))
+    out = {"Xb": bf16_bits_to_f64(Xb), "Z": Z.astype(np.float64), "A": bf16_bits_to_f64(A).reshape(4, n, 256),
+           "y": y.astype(np.float64)}
+    if target is not None:
+        out.update(dZ=dZ.astype(np.float64), dZb=bf16_bits_to_f64(dZb).reshape(4, n, 256),
+                   grads=grads.astype(np.float64))
+    return out
 
 
 def rsv_surrogate_save(ctx, path: str):

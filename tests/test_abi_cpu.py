@@ -81,3 +81,16 @@ def test_generator_math_selftest_arguments_without_gpu(lib_path):
     assert lib.rsv_selftest_generator_math(0, None, None, None, 0, None) == rsv.RSV_OK
     with pytest.raises(ValueError):
         rsv.rsv_selftest_generator_math(np.zeros(3, np.uint32), np.zeros(2))
+
+
+def test_noalloc_refuses_oversized_calls_without_gpu(lib_path):
+    """rsv_reserves_noalloc checks its sizes in 64-bit arithmetic before any CUDA
+    call: a scenario or step count near 2^31, or a portfolio beyond the scratch,
+    is RSV_E_LIMIT (the pointers are never read, so placeholders serve)."""
+    lib = rsv.load_library(lib_path)
+    fake = C.c_void_p(4096)
+    big = 2 ** 31 - 100
+    for n_pol, n_scen, n_steps in [(1, big, 1), (1, 1, big), (1, big, big), (10 ** 9, 1000, 1200), (100_000, 1000, 20_000)]:
+        st = lib.rsv_reserves_noalloc(0, None, fake, n_pol, fake, 1440, fake, n_scen, n_steps, fake, None)
+        assert st == rsv.RSV_E_LIMIT, (n_pol, n_scen, n_steps)
+    assert lib.rsv_reserves_noalloc(0, None, fake, 1, fake, 1440, fake, 0, 1, fake, None) == rsv.RSV_E_ARG

@@ -176,9 +176,12 @@ def test_surrogate_mode_gain_over_brute_force(ctx):
     print(f"surrogate mode: max rel err vs exact {sur_err:.2e} (fallback queries "
           f"{res[rsv.RSV_NESTED_SURROGATE][1]}), brute force {mc_err:.2e}; speed-up over brute force {speed:.1f}x; "
           f"held-out median {rep['val_median_rel']:.2e}, fallback share {rep['frac_fallback']:.2f}")
-    # every query the network serves was in a bucket whose held-out error stayed under 1e-3;
-    # the node liability is a positive combination of such values and of exact ones
-    assert sur_err <= 2e-3
+    # every query the network serves was in a bucket whose held-out error stayed
+    # under 0.3 x 1e-3; the node liability is a positive combination of such
+    # values and of exact ones, so it stays within the 1e-3 target
+    assert sur_err <= 1e-3
+    # the recurrence fallback (compacted per segment) ran for the flagged buckets
+    assert res[rsv.RSV_NESTED_SURROGATE][1] > 0
     assert speed > 10
 
 

@@ -212,6 +212,35 @@ def test_deterministic_reruns(ctx):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+@pytest.mark.parametrize("form", [rsv.RSV_FORM_F64, rsv.RSV_FORM_F32_COMP])
+def test_per_step_means_reproducible(ctx, form):
+    """The per-(policy, step) means over scenarios are summed in a fixed order
+    (a warp's lanes by a butterfly, its scenario chunks one after another): two
+    runs give the same bits, with many chunks per policy."""
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_mix(40, seed=12)
+    v = synth.vasicek_paths(600, 1200, seed=12)
+    rsv.rsv_load_decrements(ctx, 0, tab)
+    rsv.rsv_load_portfolio(ctx, pol)
+    rsv.rsv_load_scenarios(ctx, v)
+    runs = []
+    for _ in range(3):
+        pt = np.zeros((40, 1201))
+        rsv.rsv_compute_reserves(ctx, form, rsv.RSV_OUT_PT_MEAN, pt_mean=pt)
+        runs.append(pt)
+    assert np.array_equal(runs[0], runs[1]) and np.array_equal(runs[0], runs[2])
+    for p in range(3):   # the mean of the oracle's r_t over all 600 scenarios
+        rows = []
+        for s in range(600):
+            r = oracle.chain(int(pol["product"][p]), int(pol["age1_m"][p]), float(pol["amount"][p]), tab, v[s],
+                             age2=int(pol["age2_m"][p]), term=int(pol["term_m"][p]),
+                             rho=float(pol["reversion"][p]))[:, 0]
+            rows.append(np.concatenate([r, np.zeros(1201 - len(r))]))
+        ref = np.mean(rows, axis=0)
+        scale = np.maximum(np.abs(ref), 1e-9 * pol["amount"][p])
+        assert np.max(np.abs(runs[0][p] - ref) / scale) <= TOL[form]
+
+
 def test_config2_full_size_sampled(ctx):
     """100,000-policy mix x 1,000 Vasicek scenarios x 1,200 steps, the benchmark's
     launch configuration (tuned variant, device outputs): sampled policies

@@ -1,18 +1,23 @@
 """GPU tests of the surrogate network (BF16 tensor-core kernels, FP32
 accumulation) and of its recurrence labels, against the FP64 references.
 
-Bounds.  With the reference evaluated with BF16 storage at the same points
-as the GPU, the two differ by FP32 accumulation order (~1e-6 relative), the
-hardware tanh inside GELU (relative error ~2^-11) against FP64 tanh, and the
-BF16 rounding flips these cause: an activation whose FP32 value lands on the
-other side of a rounding boundary moves by one BF16 ulp (2^-8 relative).
-The hardware tanh's error is about 2^-3 of a BF16 ulp, so a few percent of
-the activations flip; over four layers of 256 that leaves forward outputs
-within 1e-2 of the output scale and gradients within 2e-2 in norm per
-parameter block.  Two GPU kernels with the same GELU (tcgen05 and mma.sync)
-differ by accumulation order and its rare flips only: within 2e-3.  Against
-the reference without BF16 storage the BF16 rounding itself (2^-9 relative
-per value, 4 layers) bounds the forward difference by ~3e-2 in norm.
+Each layer is pinned on its own in test_gpu_mlp_layers.py (FP32-accumulation
+and hardware-tanh bounds on the GPU's own BF16 inputs).  These end-to-end
+checks compare whole passes with the reference evaluated in BF16 storage from
+the same parameters and features, so the per-layer differences compound: a
+BF16 activation whose FP32 value lands on the other side of a rounding
+boundary moves by one BF16 ulp (2^-7 relative, against half an ulp per value
+for the rounding itself), the hardware tanh's error (about 2^-11) moves a few
+percent of the activations that way, and four layers of 256 carry those moves
+to the output.  Taking the flips of one layer as correlated, each layer adds
+at most about 2^-8 of the output scale, 1.6e-2 over four layers; the forward
+bound 1e-2 sits below that worst case (measured: 7e-4 to 3e-3), and the
+gradient bound 2e-2 in norm per parameter block allows the same for the
+backward pass (measured 2e-3).  Two GPU kernels with the same GELU (tcgen05
+and mma.sync) differ by accumulation order and its rare flips only: within
+2e-3.  Against the reference without BF16 storage the BF16 rounding itself
+(2^-9 relative per value, 4 layers) bounds the forward difference by ~3e-2 in
+norm.
 """
 import math
 

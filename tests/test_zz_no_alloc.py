@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 from paper_1401_1757_gb300 import rsv
 
@@ -56,6 +57,12 @@ def test_noalloc_matches_main_entry_point_on_two_calls():
         terr = float(np.max(np.abs(got_tot - want_tot) / np.abs(want_tot)))
         print(f"call {call}: max rel diff to rsv_compute_reserves {err:.3e}, totals {terr:.3e}")
         assert err <= TOL and terr <= TOL
+        # and against the FP64 oracle directly, on a sample of the policies
+        idx = np.arange(0, n, 29)
+        ref, _ = oracle.reserves_batch(synth.take(pol, idx), tab, v)
+        oerr = float(np.max(np.abs(got[idx] - ref) / np.maximum(np.abs(ref), 1e-9 * pol["amount"][idx, None])))
+        print(f"call {call}: max rel err against the oracle {oerr:.3e}")
+        assert oerr <= TOL
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch_and_bad_records():
@@ -76,3 +83,20 @@ def test_noalloc_rejects_sizes_beyond_its_scratch_and_bad_records():
     with pytest.raises(rsv.RsvError) as e:
         rsv.rsv_reserves_noalloc(0, torch.cuda.current_stream(), bad, d_tab, d_v[:, :4].contiguous(), out)
     assert e.value.status == rsv.RSV_E_ARG
+    # the assumptions of Section 3.7 give the status rsv_compute_reserves gives:
+    # an amount not finite, a reversion outside [0, 1]; with two bad records,
+    # the first one's
+    out2 = torch.empty((2, 4), dtype=torch.float64, device="cuda")
+    mix = synth.portfolio_mix(2, seed=1)
+    mix["product"][:] = [0, 1]
+    mix["age2_m"][1], mix["reversion"][1] = 700, 0.6
+    for change, want in ((("amount", 0, np.inf), rsv.RSV_E_ASSUMPTION), (("reversion", 1, 1.5), rsv.RSV_E_ASSUMPTION),
+                         (("table1", 0, 3), rsv.RSV_E_ARG)):
+        p2 = {k: a.copy() for k, a in mix.items()}
+        p2[change[0]][change[1]] = change[2]
+        if change[0] == "table1":
+            p2["amount"][1] = np.nan        # a later record with an assumption broken: the first decides
+        d2 = torch.from_numpy(rsv.policy_records(p2).view(np.uint8).copy()).cuda()
+        with pytest.raises(rsv.RsvError) as e:
+            rsv.rsv_reserves_noalloc(0, torch.cuda.current_stream(), d2, d_tab, d_v[:, :4].contiguous(), out2)
+        assert e.value.status == want, change
