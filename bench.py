@@ -198,7 +198,7 @@ class ClockSampler:
 
 NESTED = dict(n_pol=2000, n_outer=100, n_nodes=40, node_step=12, n_inner=1000)
 NESTED_WORKLOAD = ("nested brute force: 2,000 single-life annuities (ages 60-90) x 100 outer Vasicek paths x "
-                   "40 annual nodes x 1,000 inner paths, compensated FP32")
+                   "40 annual nodes x 1,000 inner paths, deflated FP32 (and the double-float recurrence)")
 
 
 def bench_nested(rsv, torch, tab, steps, warmup, n_outer=None, sur_epochs=10, sur_train=3_000_000):
@@ -224,7 +224,9 @@ def bench_nested(rsv, torch, tab, steps, warmup, n_outer=None, sur_epochs=10, su
     q = torch.empty((NO, NN), dtype=torch.float64, device="cuda")
     spec = dict(n_outer=NO, n_nodes=NN, node_step_m=cfg["node_step"], seed=0, on_device=True, L_mean=mean, L_q995=q)
     res = {}
-    modes = [(rsv.RSV_NESTED_MC, "brute_force", NI), (rsv.RSV_NESTED_CURVE, "curve", 1)]
+    # the brute force in the chosen (deflated) form and in the double-float recurrence
+    modes = [(rsv.RSV_NESTED_MC, "brute_force", NI), (rsv.RSV_NESTED_MC, "brute_force_compensated", NI),
+             (rsv.RSV_NESTED_CURVE, "curve", 1)]
     if sur_epochs > 0:
         # the surrogate, trained on this portfolio's own recurrence labels up to the last node
         t0 = time.perf_counter()
@@ -239,13 +241,14 @@ def bench_nested(rsv, torch, tab, steps, warmup, n_outer=None, sur_epochs=10, su
     means = {}
     for mode, name, ni in modes:
         nfb = np.zeros(1, np.int64)
+        form = rsv.RSV_FORM_F32_COMP if name == "brute_force_compensated" else rsv.RSV_FORM_F32_DEFLATED
         for _ in range(warmup):
-            rsv.rsv_compute_nested(ctx, rsv.RSV_FORM_F32_COMP, n_inner=NI, mode=mode, n_fallback=nfb, **spec)
+            rsv.rsv_compute_nested(ctx, form, n_inner=NI, mode=mode, n_fallback=nfb, **spec)
         torch.cuda.synchronize()
         ms, walls = [], []
         for _ in range(steps):
             w0 = time.perf_counter()
-            rsv.rsv_compute_nested(ctx, rsv.RSV_FORM_F32_COMP, n_inner=NI, mode=mode, n_fallback=nfb, **spec)
+            rsv.rsv_compute_nested(ctx, form, n_inner=NI, mode=mode, n_fallback=nfb, **spec)
             ms.append(rsv.rsv_last_kernel_ms(ctx))
             torch.cuda.synchronize()
             walls.append(time.perf_counter() - w0)
@@ -262,7 +265,10 @@ def bench_nested(rsv, torch, tab, steps, warmup, n_outer=None, sur_epochs=10, su
         exact = means["curve"]
         live_m = exact > 0
         res["node_liability_max_rel_vs_exact"] = {
-            k: float(np.max(np.abs(means[k] - exact)[live_m] / exact[live_m])) for k in ("brute_force", "surrogate")}
+            k: float(np.max(np.abs(means[k] - exact)[live_m] / exact[live_m]))
+            for k in ("brute_force", "brute_force_compensated", "surrogate")}
+        res["brute_force_forms_max_rel_diff"] = float(np.max(np.abs(means["brute_force"] - means["brute_force_compensated"])
+                                                             [live_m] / np.abs(means["brute_force_compensated"])[live_m]))
         res["surrogate_speedup_vs_brute_force"] = res["brute_force"]["ms"] / res["surrogate"]["ms"]
     rsv.rsv_destroy(ctx)
     res["workload"] = NESTED_WORKLOAD if cfg["n_outer"] == NESTED["n_outer"] else \
@@ -682,8 +688,8 @@ def bench_c5_nested(rsv, torch, tab, sur_epochs=10):
         L = torch.empty((n_outer, NN), dtype=torch.float64, device="cuda")
         q = torch.empty((n_outer, NN), dtype=torch.float64, device="cuda")
         nfb = np.zeros(1, np.int64)
-        rsv.rsv_compute_nested(ctx, rsv.RSV_FORM_F32_COMP, n_outer=n_outer, n_nodes=NN, node_step_m=12, n_inner=1000,
-                               seed=5, mode=mode, on_device=True, L_mean=L, L_q995=q, n_fallback=nfb)
+        rsv.rsv_compute_nested(ctx, rsv.RSV_FORM_F32_DEFLATED, n_outer=n_outer, n_nodes=NN, node_step_m=12,
+                               n_inner=1000, seed=5, mode=mode, on_device=True, L_mean=L, L_q995=q, n_fallback=nfb)
         torch.cuda.synchronize()
         runs[name] = (rsv.rsv_last_kernel_ms(ctx), L.cpu().numpy(), int(nfb[0]))
     rsv.rsv_destroy(ctx)

@@ -411,7 +411,13 @@ typedef struct {
 
 /* Nested valuation of the loaded portfolio (tables and portfolio needed, no
  * scenario set).  opts->form selects the arithmetic, opts->outputs and
- * opts->horizon must be 0.  Blocking unless opts->on_device.
+ * opts->horizon must be 0.  With RSV_FORM_F32_DEFLATED the brute-force mode
+ * runs in deflated units (products 0-5): each inner path's deflators are the
+ * FP64 running products of its discount factors from the node, and
+ * L_{o,n,i} = sum_p scale_p sum_{t >= m} D_i(m, t+1) E_p(t) with the policies'
+ * expected cash flows E_p of rsv_compute_reserves' deflated form (the in-force
+ * weighting at the node is part of them); the curve and surrogate modes then
+ * run compensated.  Blocking unless opts->on_device.
  * Errors: RSV_E_STATE, RSV_E_ARG (bad spec, NULL L_mean/L_q995, a record as
  * in rsv_compute_reserves), RSV_E_ASSUMPTION, RSV_E_CUDA, RSV_E_NOMEM. */
 rsv_status rsv_compute_nested(rsv_ctx *ctx, const rsv_opts *opts, const rsv_nested_spec *spec,

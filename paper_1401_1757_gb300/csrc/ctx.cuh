@@ -226,6 +226,17 @@ rsv_status build_tables(rsv_ctx* c, int form, size_t& smem);
 rsv_status stage_tables(rsv_ctx* c, int form, int pad, int n_tab, size_t& smem);
 // rsv_compute_reserves in the deflated form (defl_abi.cu); opts checked by the caller
 rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out);
+// The deflated kernels' staged life tables (defl_abi.cu): their shape from the
+// layout's kinds (RSV_E_ARG for a product the form does not take), then the
+// FP64 life tables {l_k} (l_0 = 2^100) and the staged FP32 arrays.
+struct DeflTabs {
+    int n_tab = 0, dpad = 0, arr_d = 0;
+    bool use_a = false, use_d = false;
+    size_t bytes = 0;
+    std::vector<std::vector<double>> ell;
+};
+rsv_status defl_table_shape(rsv_ctx* c, const Layout& L, DeflTabs& T);
+rsv_status defl_table_stage(rsv_ctx* c, DeflTabs& T);
 // Per-scenario totals from per-tile (row) partial sums [n_rows][s_pad], in a
 // fixed order (rsv_abi.cu).
 rsv_status scenario_totals(rsv_ctx* c, const double* partial, int n_rows, int s_pad, int n_scen, double* tot);

@@ -36,6 +36,66 @@ int defl_smem_limit(int device) {
 
 }  // namespace
 
+// The staged tables of the deflated kernels: the survivors array A
+// (annuities) and the deaths array (assurances), each only if a product needs
+// it, for the tables in use, as four copies shifted by one entry.  A copy
+// holds every entry up to the end of the longest table used, then zeros (at
+// least one whole group of four past each table's end), a unit group and a
+// last zero group.
+rsv_status defl_table_shape(rsv_ctx* c, const Layout& L, DeflTabs& T) {
+    T.use_a = T.use_d = false;
+    for (int k : L.h_k2) {
+        if (k != K_ANN && k != K_ASS && k != K_JL && k != K_ANN2)
+            return fail(c, RSV_E_ARG,
+                        "the deflated form values products 0-5 (single-life, reversionary, joint and last-survivor "
+                        "annuities, term and endowment assurances); use RSV_FORM_F32_COMP for the others");
+        (k == K_ASS ? T.use_d : T.use_a) = true;
+    }
+    T.n_tab = L.n_tab;
+    int max_len = 1;
+    for (int t = 0; t < T.n_tab; ++t) max_len = std::max(max_len, (int)c->tab[t].size());
+    T.dpad = (max_len + 8 + 3) / 4 * 4 + 8;   // the last two groups: a unit group, then zeros
+    T.arr_d = T.use_a ? 1 : 0;                 // index of the deaths array among the staged ones
+    T.bytes = (size_t)(T.use_a + T.use_d) * T.n_tab * 4 * T.dpad * sizeof(float);
+    return RSV_OK;
+}
+
+rsv_status defl_table_stage(rsv_ctx* c, DeflTabs& T) {
+    const int n_tab = T.n_tab, dpad = T.dpad, arr_d = T.arr_d;
+    const bool use_a = T.use_a, use_d = T.use_d;
+    // life tables: [A | deaths][table][4 copies shifted by c][dpad], A_k = l_{k+1}, deaths_k = l_k q_k
+    T.ell.assign(n_tab, {});
+    for (int t = 0; t < n_tab; ++t) {
+        T.ell[t] = life_table(c->tab[t], dpad + 4);
+        for (int k = 0; k < (int)c->tab[t].size(); ++k)
+            if (T.ell[t][k + 1] > 0.0 && T.ell[t][k + 1] < kEllMinRatio * kEllScale)
+                return fail(c, RSV_E_ARG, "table %d: survival to age %d months is below 2^-220, out of the "
+                                          "deflated form's range", t, k + 1);
+    }
+    const unsigned long long tkey = c->tab_gen * 1000003ull + (unsigned)dpad * 131ull + (unsigned)n_tab * 7ull +
+                                    (use_a ? 1ull : 0ull) + (use_d ? 2ull : 0ull);
+    if (c->defl_tab_key != tkey) {
+        std::vector<float> h((size_t)(use_a + use_d) * n_tab * 4 * dpad, 0.0f);
+        for (int t = 0; t < n_tab; ++t) {
+            const std::vector<double>& l = T.ell[t];
+            const std::vector<double>& p = c->tab[t];
+            for (int cpy = 0; cpy < 4; ++cpy)
+                for (int q = 0; q < dpad; ++q) {
+                    const int k = q + cpy;
+                    const double pk = k < (int)p.size() ? p[k] : 0.0;
+                    if (use_a) h[(((size_t)0 * n_tab + t) * 4 + cpy) * dpad + q] = (float)l[k + 1];
+                    if (use_d) h[(((size_t)arr_d * n_tab + t) * 4 + cpy) * dpad + q] = (float)(l[k] * (1.0 - pk));
+                }
+            if (use_d) h[(((size_t)arr_d * n_tab + t) * 4 + 0) * dpad + dpad - 8] = 1.0f;   // the unit group
+        }
+        CU(c->d_defl_tab.ensure(h.size() * sizeof(float)));
+        CU(cudaMemcpyAsync(c->d_defl_tab.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice,
+                           c->stream));   // staged (pageable source)
+        c->defl_tab_key = tkey;
+    }
+    return RSV_OK;
+}
+
 rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     const int outs = o->outputs;
     if (outs & (RSV_OUT_PT_MEAN | RSV_OUT_TRAJ))
@@ -54,81 +114,35 @@ rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     } else {
         return fail(c, RSV_E_ARG, "variant %d out of range (the deflated form has no scan or summation)", o->variant);
     }
-    // The staged tables: the survivors array A (annuities) and the deaths
-    // array (assurances), each only if a product needs it, for the tables in
-    // use.  A variant whose staging ring does not fit beside them is replaced
+    // A variant whose staging ring does not fit beside the tables is replaced
     // by the first that does, unless it was asked for by index.
     int W = 0;
     rsv_status st = RSV_OK;
-    bool use_a = false, use_d = false;
-    size_t tab_bytes = 0, smem = 0;
-    int n_tab = 0, dpad = 0;
+    DeflTabs T;
+    size_t smem = 0;
     const long long smem_max = defl_smem_limit(c->device);
     for (int pass = 0;; ++pass) {
         const DeflVariant& V = vl[vi];
         W = V.NW * V.P;
         if ((st = build_layout(c, W, o->horizon, c->n_steps)) != RSV_OK) return st;
-        const Layout& L = c->lay;
-        use_a = use_d = false;
-        for (int k : L.h_k2) {
-            if (k != K_ANN && k != K_ASS && k != K_JL && k != K_ANN2)
-                return fail(c, RSV_E_ARG,
-                            "the deflated form values products 0-5 (single-life, reversionary, joint and last-survivor "
-                            "annuities, term and endowment assurances); use RSV_FORM_F32_COMP for the others");
-            (k == K_ASS ? use_d : use_a) = true;
-        }
-        // a copy holds every entry up to the end of the longest table used,
-        // then zeros: at least one whole group of four past each table's end
-        n_tab = L.n_tab;
-        int max_len = 1;
-        for (int t = 0; t < n_tab; ++t) max_len = std::max(max_len, (int)c->tab[t].size());
-        dpad = (max_len + 8 + 3) / 4 * 4 + 8;   // the last two groups: a unit group, then zeros
-        tab_bytes = (size_t)(use_a + use_d) * n_tab * 4 * dpad * sizeof(float);
-        smem = tab_bytes + defl_smem_extra(V);
+        if ((st = defl_table_shape(c, c->lay, T)) != RSV_OK) return st;
+        smem = T.bytes + defl_smem_extra(V);
         if ((long long)smem <= smem_max) break;
         int alt = -1;
         for (int k = 0; k < nv && alt < 0; ++k)
-            if ((long long)(tab_bytes + defl_smem_extra(vl[k])) <= smem_max) alt = k;
+            if ((long long)(T.bytes + defl_smem_extra(vl[k])) <= smem_max) alt = k;
         if (o->variant >= 0 || alt < 0 || pass > 0)
             return fail(c, RSV_E_ARG, "variant %s needs %zu bytes of shared memory for %d tables (%lld available)",
-                        V.name, smem, n_tab, smem_max);
+                        V.name, smem, T.n_tab, smem_max);
         vi = alt;
     }
     const DeflVariant& V = vl[vi];
     const int CH = 32 * V.M;
     const Layout& L = c->lay;
-    const int arr_d = use_a ? 1 : 0;   // index of the deaths array among the staged ones
-
-    // life tables: [A | deaths][table][4 copies shifted by c][dpad], A_k = l_{k+1}, deaths_k = l_k q_k
-    std::vector<std::vector<double>> ell(n_tab);
-    for (int t = 0; t < n_tab; ++t) {
-        ell[t] = life_table(c->tab[t], dpad + 4);
-        for (int k = 0; k < (int)c->tab[t].size(); ++k)
-            if (ell[t][k + 1] > 0.0 && ell[t][k + 1] < kEllMinRatio * kEllScale)
-                return fail(c, RSV_E_ARG, "table %d: survival to age %d months is below 2^-220, out of the "
-                                          "deflated form's range", t, k + 1);
-    }
-    const unsigned long long tkey = c->tab_gen * 1000003ull + (unsigned)dpad * 131ull + (unsigned)n_tab * 7ull +
-                                    (use_a ? 1ull : 0ull) + (use_d ? 2ull : 0ull);
-    if (c->defl_tab_key != tkey) {
-        std::vector<float> h((size_t)(use_a + use_d) * n_tab * 4 * dpad, 0.0f);
-        for (int t = 0; t < n_tab; ++t) {
-            const std::vector<double>& l = ell[t];
-            const std::vector<double>& p = c->tab[t];
-            for (int cpy = 0; cpy < 4; ++cpy)
-                for (int q = 0; q < dpad; ++q) {
-                    const int k = q + cpy;
-                    const double pk = k < (int)p.size() ? p[k] : 0.0;
-                    if (use_a) h[(((size_t)0 * n_tab + t) * 4 + cpy) * dpad + q] = (float)l[k + 1];
-                    if (use_d) h[(((size_t)arr_d * n_tab + t) * 4 + cpy) * dpad + q] = (float)(l[k] * (1.0 - pk));
-                }
-            if (use_d) h[(((size_t)arr_d * n_tab + t) * 4 + 0) * dpad + dpad - 8] = 1.0f;   // the unit group
-        }
-        CU(c->d_defl_tab.ensure(h.size() * sizeof(float)));
-        CU(cudaMemcpyAsync(c->d_defl_tab.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice,
-                           c->stream));   // staged (pageable source)
-        c->defl_tab_key = tkey;
-    }
+    if ((st = defl_table_stage(c, T)) != RSV_OK) return st;
+    const int n_tab = T.n_tab, dpad = T.dpad, arr_d = T.arr_d;
+    const size_t tab_bytes = T.bytes;
+    const std::vector<std::vector<double>>& ell = T.ell;
 
     // slot records of the super-tiles
     const unsigned long long lkey = L.gen * 31ull + (unsigned long long)dpad * 7ull + (unsigned)L.horizon * 3ull +

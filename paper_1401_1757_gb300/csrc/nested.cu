@@ -29,6 +29,7 @@
 
 #include "fp64_series.cuh"
 #include "nested.cuh"
+#include "defl_kernel.cuh"
 #include "philox.cuh"
 #include "rsv.h"
 #include "abi_guard.cuh"
@@ -413,7 +414,242 @@ __global__ void node_stats_kernel(const double* __restrict__ L_all, int n_inner,
     }
 }
 
+// ------------------------------------------- deflated brute-force mode ----
+// Inner paths as deflator planes: D_i(m, m+tau+1), the FP64 running product
+// of the path's monthly discount factors from the node, rounded to FP32, in
+// rows of four steps [B][n_nodes][G4][i_pad]; zeros from the node's remaining
+// length to the end of its last group of four.  One thread per path.
+__global__ void inner_paths_defl_kernel(VasStep s, uint64_t seed, int o0, int B, int n_nodes, int n_inner, int i_pad,
+                                        int G4, const int* __restrict__ Ln, const double* __restrict__ r_node,
+                                        const double2* __restrict__ bm_g, float* __restrict__ plane) {
+    __shared__ double2 bm[BM_SC + BM_LG];   // 18 KiB: the Box-Muller tables
+    for (int k = threadIdx.x; k < BM_SC + BM_LG; k += blockDim.x) bm[k] = bm_g[k];
+    __syncthreads();
+    const size_t total = (size_t)B * n_nodes * i_pad;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % i_pad);
+        const int n = (int)((idx / i_pad) % n_nodes);
+        const int ol = (int)(idx / ((size_t)i_pad * n_nodes));
+        const int o = o0 + ol;
+        // element (tau, i) at ((ol n_nodes + n) G4 + tau / 4) i_pad 4 + 4 i + tau % 4
+        float* base = plane + ((size_t)ol * n_nodes + n) * G4 * i_pad * 4 + 4 * (size_t)i;
+        const int L = Ln[n], Lr = (L + 3) / 4 * 4;
+        auto at = [&](int tau) -> float& { return base[(size_t)(tau >> 2) * i_pad * 4 + (tau & 3)]; };
+        if (i >= n_inner) {   // padding lanes: finite factors, never written out
+            for (int tau = 0; tau < Lr; ++tau) at(tau) = 1.0f;
+            continue;
+        }
+        double D = 1.0;
+        vasicek_path(s, seed, (uint32_t)i, (uint32_t)n, (3u << 24) | (uint32_t)o, r_node[(size_t)o * n_nodes + n], L,
+                     bm, [&](int t, double v, double) {
+                         D = __dmul_rn(D, v);
+                         at(t) = __double2float_rn(D);
+                     });
+        for (int tau = L; tau < Lr; ++tau) at(tau) = 0.0f;
+    }
+}
+
+// Node liabilities by the deflated recurrence.  One CTA per item (node n,
+// outer path of the batch, chunk of 32 M inner paths); its NW warps share the
+// policy tiles, lane l holds inner paths chunk + m 32 + l of every policy of
+// its tile (P x M chains).  Per chain-step one FP32 fused multiply-add of the
+// path's deflator and the policy's expected cash flow (two accumulators on
+// alternate steps, folded into a double-float every 16 steps); per tile the
+// scaled sums are added into each path's double-float liability, and the
+// CTA adds its warps' liabilities in a fixed order in FP64.
+template <int P, int M, int NW>
+__global__ void __launch_bounds__(NW * 32, 2) nested_defl_kernel(const NestDeflArgs a) {
+    constexpr int CH = 32 * M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint64_t bar;
+    __shared__ int s_item;
+    __shared__ float2 red[NW][CH];
+    if (!stage_to_smem(smem_raw, a.tab, (uint32_t)a.tab_bytes, &bar, a.status)) return;
+    const float4* tab = reinterpret_cast<const float4*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int dpad4 = a.dpad / 4;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= a.n_items) break;
+        // node-major: the early nodes (longest projections) first
+        const int chunk = item % a.n_chunks;
+        const int ol = (item / a.n_chunks) % a.B;
+        const int n = item / (a.n_chunks * a.B);
+        const int m = n * a.node_step;
+        const float4* plane = a.D + ((size_t)ol * a.n_nodes + n) * a.G4 * a.i_pad + (size_t)chunk * CH + lane;
+        float acc_h[M], acc_l[M];
+#pragma unroll
+        for (int q = 0; q < M; ++q) acc_h[q] = acc_l[q] = 0.0f;
+        for (int tile = warp; tile < a.n_tiles; tile += NW) {
+            const NestSlot* rec = a.slots + (size_t)tile * P;
+            if (rec[0].S < m) continue;   // the tile's longest policy ended before the node
+            const int kind = a.tile_kind[tile];
+            // the runs of the tile's policies from the node
+            int off1[P], off2[P], gz1[P], gz2[P], Sr[P];
+            float ix[P], iy[P];
+            int smin = 1 << 30, smax = 0;
+            DeflLane<P, M> st;
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                const NestSlot r = rec[i];
+                int S = r.S - m;
+                const bool live = r.pol >= 0 && S >= 0 && !(r.unit && m > 0);
+                if (!live) S = 0;
+                Sr[i] = S;
+                smin = min(smin, S);
+                smax = max(smax, S);
+                ix[i] = r.ix;
+                iy[i] = r.iy;
+                // life 1: aligned run at age + m, or a zero group; the unit group at node 0
+                const int a1 = r.age1 + m;
+                if (r.unit) {
+                    off1[i] = r.base1 + (a.dpad - 8) / 4;
+                    gz1[i] = 1;
+                } else if (a1 >= r.z1) {
+                    off1[i] = r.base1 + (r.z1 + 3) / 4;
+                    gz1[i] = 0;
+                } else {
+                    off1[i] = r.base1 + (a1 & 3) * dpad4 + (a1 >> 2);
+                    gz1[i] = (r.z1 - a1 + 3) / 4;
+                }
+                const int a2 = r.age2 + m;
+                if (a2 >= r.z2) {
+                    off2[i] = r.base2 + (r.z2 + 3) / 4;
+                    gz2[i] = 0;
+                } else {
+                    off2[i] = r.base2 + (a2 & 3) * dpad4 + (a2 >> 2);
+                    gz2[i] = (r.z2 - a2 + 3) / 4;
+                }
+#pragma unroll
+                for (int q = 0; q < M; ++q) {   // the boundary D(m, S) mat
+                    st.a0[i][q] = st.a1[i][q] = st.l[i][q] = 0.0f;
+                    float h0 = 0.0f;
+                    if (live && r.mat != 0.0f) {
+                        float dS = 1.0f;
+                        if (S > 0) dS = reinterpret_cast<const float*>(plane + (size_t)((S - 1) >> 2) * a.i_pad + q * 32)[(S - 1) & 3];
+                        h0 = __fmul_rn(dS, r.mat);
+                    }
+                    st.h[i][q] = h0;
+                }
+            }
+            if (smax > 0) {
+                const int g_top = (smax - 1) >> 2;
+#pragma unroll 1
+                for (int g = g_top; g >= 0; --g) {
+                    float4 d[M];
+#pragma unroll
+                    for (int q = 0; q < M; ++q) d[q] = plane[(size_t)g * a.i_pad + q * 32];
+                    const bool check = 4 * g + 3 >= smin;
+                    float4 e[P];
+#pragma unroll
+                    for (int i = 0; i < P; ++i) {
+                        const int t0 = 4 * g, S = Sr[i];
+                        if (t0 >= S) {
+                            e[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                            continue;
+                        }
+                        const float4 x = tab[off1[i] + min(g, gz1[i])];
+                        if (kind == K_ANN || kind == K_ASS) {
+                            e[i] = x;
+                        } else {
+                            const float4 y = tab[off2[i] + min(g, gz2[i])];
+                            const float fx[4] = {x.x, x.y, x.z, x.w}, fy[4] = {y.x, y.y, y.z, y.w};
+                            float fe[4];
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const float px = __fmul_rn(fx[c], ix[i]), py = __fmul_rn(fy[c], iy[i]);
+                                fe[c] = kind == K_JL ? __fmaf_rn(px, __fsub_rn(1.0f, py), py) : __fmul_rn(px, py);
+                            }
+                            e[i] = make_float4(fe[0], fe[1], fe[2], fe[3]);
+                        }
+                        if (check && t0 + 3 >= S) {
+                            if (t0 + 1 >= S) e[i].y = 0.0f;
+                            if (t0 + 2 >= S) e[i].z = 0.0f;
+                            if (t0 + 3 >= S) e[i].w = 0.0f;
+                        }
+                    }
+                    const bool first = (g & 3) == 3;   // the first group of a 16-step span
+#pragma unroll
+                    for (int i = 0; i < P; ++i)
+#pragma unroll
+                        for (int q = 0; q < M; ++q) {
+                            st.a1[i][q] = first ? __fmul_rn(d[q].w, e[i].w) : __fmaf_rn(d[q].w, e[i].w, st.a1[i][q]);
+                            st.a0[i][q] = first ? __fmul_rn(d[q].z, e[i].z) : __fmaf_rn(d[q].z, e[i].z, st.a0[i][q]);
+                        }
+#pragma unroll
+                    for (int i = 0; i < P; ++i)
+#pragma unroll
+                        for (int q = 0; q < M; ++q) {
+                            st.a1[i][q] = __fmaf_rn(d[q].y, e[i].y, st.a1[i][q]);
+                            st.a0[i][q] = __fmaf_rn(d[q].x, e[i].x, st.a0[i][q]);
+                        }
+                    if ((g & 3) == 0) defl_fold_all(st);   // 16-step spans aligned at the node
+                }
+            }
+            // this tile's scaled sums into the paths' liabilities
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                const float sh = rec[i].sc_h, sl = rec[i].sc_l;
+#pragma unroll
+                for (int q = 0; q < M; ++q) {
+                    const float H = st.h[i][q], L = st.l[i][q];
+                    const float p = __fmul_rn(H, sh);
+                    float e = __fmaf_rn(H, sh, -p);
+                    e = __fmaf_rn(H, sl, e);
+                    e = __fmaf_rn(L, sh, e);
+                    defl_fold(acc_h[q], acc_l[q], p);
+                    acc_l[q] = __fadd_rn(acc_l[q], e);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < M; ++q) red[warp][q * 32 + lane] = make_float2(acc_h[q], acc_l[q]);
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int q = 0; q < M; ++q) {
+                double x = 0.0;
+                for (int w = 0; w < NW; ++w) {
+                    const float2 v = red[w][q * 32 + lane];
+                    x += (double)v.x + (double)v.y;
+                }
+                const int i = chunk * CH + q * 32 + lane;
+                if (i < a.n_inner) a.L_all[((size_t)(a.o0 + ol) * a.n_nodes + n) * a.n_inner + i] = x;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------- launchers ----
+cudaError_t launch_inner_paths_defl(const VasStep& s, uint64_t seed, int o0, int B, int n_nodes, int n_inner,
+                                    int i_pad, int G4, const int* Ln, const double* r_node, const double2* bm,
+                                    float4* plane, int sm_count, cudaStream_t st) {
+    inner_paths_defl_kernel<<<sm_count * 8, 128, 0, st>>>(s, seed, o0, B, n_nodes, n_inner, i_pad, G4, Ln, r_node, bm,
+                                                          reinterpret_cast<float*>(plane));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nested_defl(const NestDeflArgs& a, int sm_count, cudaStream_t st) {
+    constexpr int P = kNestDeflP, M = 2, NW = 8;
+    auto k = nested_defl_kernel<P, M, NW>;
+    const size_t smem = (size_t)a.tab_bytes;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, NW * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) return cudaErrorInvalidConfiguration;
+    const long long grid = std::min<long long>((long long)sm_count * bps, std::max(1, a.n_items));
+    k<<<(int)grid, NW * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int FORM, int P, int NT>
 cudaError_t launch_nested_t(const NestedArgs& a, int sm_count, size_t smem, cudaStream_t st) {
     auto k = nested_kernel<FORM, P, NT>;

@@ -45,6 +45,44 @@ cudaError_t launch_curve_planes_lanes(int form, double a, double b, double sigma
                                       int Lmax, const int* Ln, const double* r_node, void* plane, int sm_count,
                                       cudaStream_t st);
 cudaError_t launch_transpose_on(const double* Lt, int n_outer, int n_nodes, double* L, cudaStream_t st);
+
+// ---- the brute-force mode in deflated units (RSV_FORM_F32_DEFLATED) ---------
+// The node liability is the policies' expected cash flows E_p(t) at valuation
+// (the weights of the deflated valuation kernel, scaled by amount / l_x or
+// amount) discounted along the inner path from the node:
+//   L_{o,n,i} = sum_p scale_p [ sum_{t >= m} D_i(m, t+1) E_p(t) + D_i(m, S_p) mat_p ],
+// D_i(m, t+1) = v_m ... v_t on inner path i, since sum_j pi_{p,n,j} r_{p,j}(node)
+// is the expected value at the node of the cash flows after it.
+struct NestSlot {   // 64 bytes, one policy slot of a tile
+    int32_t base1, age1, z1;   // life 1: float4 index of copy 0 of its staged array, its age at valuation,
+                               // the first table entry that is zero (the table's end, +1 for deaths)
+    int32_t base2, age2, z2;   // life 2 (K_JL, K_ANN2)
+    int32_t S, pol;            // steps from valuation; pol -1 = padding
+    float ix, iy, mat;         // as DeflSlot
+    int32_t kind;
+    float sc_h, sc_l;          // the scale as an FP32 head and tail
+    int32_t unit;              // 1: alive past its table's end at valuation (death in the first month)
+    int32_t pad;
+};
+static_assert(sizeof(NestSlot) == 64, "NestSlot layout");
+
+struct NestDeflArgs {
+    const float* tab;          // the deflated form's staged tables
+    int32_t tab_bytes, dpad;
+    const float4* D;           // [B][n_nodes][G4][i_pad]: D_i(m, m+tau+1) for tau = 4g .. 4g+3
+    int32_t i_pad, n_inner, G4, n_nodes, node_step, B, o0;
+    const NestSlot* slots;     // [n_tiles * P]
+    const int32_t* tile_kind;
+    int32_t n_tiles, n_chunks, n_items;
+    int32_t* counter;
+    int32_t* status;
+    double* L_all;
+};
+constexpr int kNestDeflP = 4;   // policies per tile of the deflated nested kernel
+cudaError_t launch_inner_paths_defl(const VasStep& s, uint64_t seed, int o0, int B, int n_nodes, int n_inner,
+                                    int i_pad, int G4, const int* Ln, const double* r_node, const double2* bm,
+                                    float4* plane, int sm_count, cudaStream_t st);
+cudaError_t launch_nested_defl(const NestDeflArgs& a, int sm_count, cudaStream_t st);
 cudaError_t launch_node_stats(const double* L_all, int n_on, int n_inner, int k, double* mean, double* kth,
                               cudaStream_t st);
 

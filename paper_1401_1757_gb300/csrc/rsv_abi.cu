@@ -807,7 +807,7 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
 // remaining projection length per node, and the nested launch sequence.
 rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* sp, rsv_nested_out* out) {
     if (!o || !sp || !out) return fail(c, RSV_E_ARG, "opts, spec and out must not be NULL");
-    if (o->form < F_F64 || o->form > F_COMP) return fail(c, RSV_E_ARG, "bad form %d", o->form);
+    if (o->form < F_F64 || o->form > F_DEFL) return fail(c, RSV_E_ARG, "bad form %d", o->form);
     if (o->outputs != 0 || o->horizon != 0 || o->payment != 0 || (o->on_device != 0 && o->on_device != 1))
         return fail(c, RSV_E_ARG, "nested runs take outputs = 0, horizon = 0, payment 0, on_device 0/1");
     if (c->cf_pol > 0) return fail(c, RSV_E_STATE, "nested runs value level cash flows: clear the loaded sequence");
@@ -830,17 +830,28 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
     for (auto& t : c->tab) any_tab |= !t.empty();
     if (!any_tab) return fail(c, RSV_E_STATE, "no decrement table loaded");
 
-    const int form = o->form, P = nested_tile_width(form);
+    // The deflated form values the brute-force mode in deflated units; the
+    // curve and surrogate modes run it compensated.
+    const bool mc = sp->mode == RSV_NESTED_MC;
+    const bool defl = o->form == F_DEFL && mc;
+    const int form = o->form == F_DEFL && !mc ? F_COMP : o->form;
+    const int P = defl ? kNestDeflP : nested_tile_width(form);
     rsv_status st = build_layout(c, P, 0, kMaxAgeSteps);
     if (st != RSV_OK) return st;
     size_t smem = 0;
-    if ((st = build_tables(c, form, smem)) != RSV_OK) return st;
+    DeflTabs T;
+    if (defl) {
+        if ((st = defl_table_shape(c, c->lay, T)) != RSV_OK) return st;
+        if ((st = defl_table_stage(c, T)) != RSV_OK) return st;
+        smem = T.bytes;
+    } else if ((st = build_tables(c, form, smem)) != RSV_OK) {
+        return st;
+    }
     const Layout& L = c->lay;
     const int n_pol = (int)c->pols.size(), NN = sp->n_nodes, NO = sp->n_outer, step = sp->node_step_m;
-    const bool mc = sp->mode == RSV_NESTED_MC;
     const bool sur = sp->mode == RSV_NESTED_SURROGATE;
     const int n_inner = mc ? sp->n_inner : 1;
-    const int i_pad = (n_inner + 31) / 32 * 32;
+    const int i_pad = defl ? (n_inner + 63) / 64 * 64 : (n_inner + 31) / 32 * 32;
 
     // weights and remaining lengths
     std::vector<double> w((size_t)std::max(1, n_pol) * NN * 3, 0.0);
@@ -879,8 +890,9 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
         }
     }
     const int Lmax = std::max(1, *std::max_element(Ln.begin(), Ln.end()));
+    const int G4 = (Lmax + 3) / 4;   // the deflated planes' rows of four steps
     const size_t esz = form == F_F32 ? sizeof(float) : 8;
-    const size_t per_outer = (size_t)NN * Lmax * i_pad * esz;
+    const size_t per_outer = defl ? (size_t)NN * G4 * i_pad * sizeof(float4) : (size_t)NN * Lmax * i_pad * esz;
     int B = sp->batch_outer > 0 ? sp->batch_outer : (int)std::max<size_t>(1, (size_t(4) << 30) / per_outer);
     B = std::min(B, NO);
 
@@ -1025,8 +1037,104 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
                            cudaMemcpyHostToDevice, c->stream));
         c->nest_bm_ready = true;
     }
+    NestDeflArgs da{};
+    if (defl) {   // policy slots of the deflated tiles: runs, scales, boundary weights
+        std::vector<NestSlot> ns(L.h_s2.size());
+        for (int f = 0; f < L.n_tiles; ++f) {
+            const int kind = L.h_k2[f];
+            for (int k = 0; k < P; ++k) {
+                const SlotRec& r = L.h_s2[(size_t)f * P + k];
+                NestSlot d{};
+                const int tb1 = r.idx1 / L.tab_pad, a1 = r.idx1 % L.tab_pad;
+                const int tb2 = r.idx2 / L.tab_pad, a2 = r.idx2 % L.tab_pad;
+                const int arr1 = kind == K_ASS ? T.arr_d : 0;
+                d.base1 = (arr1 * T.n_tab + tb1) * T.dpad;   // float4 index of copy 0: 4 dpad floats per copy
+                d.base2 = (0 * T.n_tab + tb2) * T.dpad;
+                d.age1 = a1;
+                d.age2 = a2;
+                d.z1 = (int)c->tab[tb1].size() + (kind == K_ASS ? 1 : 0);
+                d.z2 = (int)c->tab[tb2].size();
+                d.S = r.S;
+                d.pol = r.pol;
+                d.kind = kind;
+                auto ell_at = [&](int tb, int a) { return a < (int)T.ell[tb].size() ? T.ell[tb][a] : 0.0; };
+                const double lx = ell_at(tb1, a1), ly = ell_at(tb2, a2);
+                const double amount = r.pol >= 0 ? c->pols[r.pol].amount : 0.0;
+                const double rho = (double)r.rho_h + (double)r.rho_l;
+                double scale = 0.0;
+                if (kind == K_ANN || kind == K_ASS) {
+                    scale = lx > 0.0 ? amount / lx : 0.0;
+                    if (kind == K_ASS && r.bnd != 0.0f) d.mat = (float)((double)r.bnd * ell_at(tb1, a1 + r.S));
+                    if (kind == K_ASS && r.S == 0) {
+                        scale = amount;
+                        d.mat = r.bnd;
+                    } else if (kind == K_ASS && !(lx > 0.0)) {
+                        scale = amount;
+                        d.mat = 0.0f;
+                        d.unit = 1;
+                    }
+                } else {
+                    scale = amount;
+                    const double ix = lx > 0.0 ? 1.0 / lx : 0.0, iy = ly > 0.0 ? 1.0 / ly : 0.0;
+                    if (kind == K_ANN2) {
+                        d.ix = (float)ix;
+                        d.iy = (float)iy;
+                    } else {
+                        d.ix = r.state0 == 2 ? 0.0f : (float)ix;
+                        d.iy = r.state0 == 1 ? 0.0f : (float)(rho * iy);
+                    }
+                }
+                d.sc_h = (float)scale;
+                d.sc_l = (float)(scale - (double)d.sc_h);
+                ns[(size_t)f * P + k] = d;
+            }
+        }
+        CU(c->d_defl_slots.ensure(std::max<size_t>(1, ns.size()) * sizeof(NestSlot)));
+        CU(c->d_defl_kinds.ensure(std::max<size_t>(1, L.h_k2.size()) * sizeof(int32_t)));
+        if (!ns.empty()) {
+            CU(cudaMemcpyAsync(c->d_defl_slots.p, ns.data(), ns.size() * sizeof(NestSlot), cudaMemcpyHostToDevice,
+                               c->stream));
+            CU(cudaMemcpyAsync(c->d_defl_kinds.p, L.h_k2.data(), L.h_k2.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, c->stream));
+        }
+        c->defl_lay_key = 0;   // the valuation's slot records were overwritten
+        da.tab = c->d_defl_tab.as<float>();
+        da.tab_bytes = (int32_t)T.bytes;
+        da.dpad = T.dpad;
+        da.D = c->d_nest_plane.as<float4>();
+        da.i_pad = i_pad;
+        da.n_inner = n_inner;
+        da.G4 = G4;
+        da.n_nodes = NN;
+        da.node_step = step;
+        da.slots = c->d_defl_slots.as<NestSlot>();
+        da.tile_kind = c->d_defl_kinds.as<int32_t>();
+        da.n_tiles = L.n_tiles;
+        da.n_chunks = i_pad / 64;
+        da.counter = c->d_ctl.as<int32_t>();
+        da.status = c->d_ctl.as<int32_t>() + 1;
+        da.L_all = Lall;
+    }
     for (int o0 = 0; o0 < NO && !sur && !curve; o0 += B) {
         const int Bc = std::min(B, NO - o0);
+        if (defl) {
+            CU(launch_inner_paths_defl(vs, sp->seed, o0, Bc, NN, n_inner, i_pad, G4, c->d_nest_ln.as<int>(),
+                                       c->d_nest_rn.as<double>(), c->d_nest_bm.as<double2>(),
+                                       c->d_nest_plane.as<float4>(), c->sm_count, c->stream));
+            const long long items = (long long)NN * Bc * da.n_chunks;
+            if (items > 0x7fffffffLL) return fail(c, RSV_E_ARG, "too many nested work items");
+            da.B = Bc;
+            da.o0 = o0;
+            da.n_items = (int32_t)items;
+            CU(cudaMemsetAsync(c->d_ctl.p, 0, sizeof(int32_t), c->stream));
+            if (L.n_tiles > 0) {
+                CU(launch_nested_defl(da, c->sm_count, c->stream));
+            } else {
+                CU(cudaMemsetAsync(Lall + (size_t)o0 * NN * n_inner, 0, (size_t)Bc * NN * n_inner * sizeof(double),
+                                   c->stream));
+            }
+            continue;
+        }
         CU(launch_inner_paths(form, vs, sp->seed, o0, Bc, NN, n_inner, i_pad, Lmax, c->d_nest_ln.as<int>(),
                               c->d_nest_rn.as<double>(), c->d_nest_bm.as<double2>(), c->d_nest_plane.p, c->sm_count,
                               c->stream));

@@ -16,7 +16,7 @@ from paper_1401_1757_gb300 import rsv
 
 pytestmark = pytest.mark.gpu
 
-TOL = {rsv.RSV_FORM_F64: 1e-11, rsv.RSV_FORM_F32_COMP: 1e-6, rsv.RSV_FORM_F32: 2e-4}
+TOL = {rsv.RSV_FORM_F64: 1e-11, rsv.RSV_FORM_F32_COMP: 1e-6, rsv.RSV_FORM_F32: 2e-4, rsv.RSV_FORM_F32_DEFLATED: 1e-6}
 
 
 @pytest.fixture
@@ -44,7 +44,7 @@ def mixed_portfolio(n=40, seed=12):
     return pol
 
 
-@pytest.mark.parametrize("form", [rsv.RSV_FORM_F64, rsv.RSV_FORM_F32_COMP, rsv.RSV_FORM_F32])
+@pytest.mark.parametrize("form", [rsv.RSV_FORM_F64, rsv.RSV_FORM_F32_COMP, rsv.RSV_FORM_F32, rsv.RSV_FORM_F32_DEFLATED])
 def test_nested_small_against_oracle(ctx, form):
     """3 outer paths (in batches of 2 and 1) x 5 nodes 24 months apart x 70 inner
     paths (ragged against the 32-path chunks), four-product mix with JL
@@ -66,6 +66,36 @@ def test_nested_small_against_oracle(ctx, form):
     srt = np.sort(out["L_all"], axis=2)
     assert np.allclose(out["L_mean"], out["L_all"].mean(axis=2), rtol=1e-13, atol=0)
     assert np.array_equal(out["L_q995"], srt[:, :, -1])          # ceil(0.005 * 70) = 1: the largest
+
+
+def test_nested_deflated_unaligned_nodes_and_edges(ctx):
+    """The deflated brute force with nodes 7 months apart (table runs start at
+    every offset within a group of four), assurances that run past the
+    limiting age or start past it, endowments maturing at a node, joint-life
+    and last-survivor annuities (two tables), the reversionary annuity from
+    every state: every (o, n, i) against the oracle; reruns bit-identical."""
+    tab = synth.gm_monthly_survival()
+    tab2 = synth.gm_monthly_survival(A=0.0004, B=0.00002)
+    pol = mixed_portfolio(36, seed=17)
+    two = synth.portfolio_two_life(8, seed=3, age_lo_y=55, age_hi_y=85, products=(4, 5))
+    two["table2"][:] = 1
+    pol = {k: np.concatenate([pol[k], two[k]]) for k in pol}
+    spec_rows = [(2, 1430, 60), (2, 1445, 24), (3, 900, 21), (3, 1000, 7), (0, 1430, 0)]
+    for i, (prod, age, term) in enumerate(spec_rows):
+        pol["product"][i], pol["age1_m"][i], pol["term_m"][i] = prod, age, term
+        pol["age2_m"][i], pol["reversion"][i], pol["state0"][i] = 0, 0.0, 0
+    rsv.rsv_load_decrements(ctx, 1, tab2)
+    spec = dict(n_outer=2, n_nodes=6, node_step_m=7, n_inner=70, seed=41)
+    out = nested(ctx, pol, tab, rsv.RSV_FORM_F32_DEFLATED, **spec)
+    worst = 0.0
+    for o in range(2):
+        for n in range(6):
+            L, _, _ = oracle.nested_node(pol, np.stack([tab, tab2]), 41, o, n, np.arange(70), node_step=7)
+            worst = max(worst, float(np.max(np.abs(out["L_all"][o, n] - L) / np.abs(L))))
+    print(f"deflated nested, unaligned nodes: max rel err {worst:.3e}")
+    assert worst <= 1e-6
+    again = nested(ctx, pol, tab, rsv.RSV_FORM_F32_DEFLATED, **spec)
+    assert np.array_equal(again["L_all"], out["L_all"])
 
 
 def test_node_statistics_fifth_largest(ctx):
@@ -93,10 +123,11 @@ def test_inner_mean_matches_curve_mode(ctx):
     assert np.allclose(mc["r_node"], cv["r_node"], rtol=0, atol=0)
 
 
-def test_config3_full_size_sampled(ctx):
+@pytest.mark.parametrize("form", [rsv.RSV_FORM_F32_COMP, rsv.RSV_FORM_F32_DEFLATED])
+def test_config3_full_size_sampled(ctx, form):
     """2,000 single-life annuities (ages 60-90) x 100 outer paths x 40 annual
-    nodes x 1,000 inner paths, compensated FP32: sampled (o, n, i) against the
-    oracle, statistics against the returned liabilities."""
+    nodes x 1,000 inner paths, compensated FP32 and deflated: sampled (o, n, i)
+    against the oracle, statistics against the returned liabilities."""
     tab = synth.gm_monthly_survival()
     pol = synth.portfolio_single_life(2000, seed=0)
     NO, NN, NI = 100, 40, 1000
@@ -105,7 +136,7 @@ def test_config3_full_size_sampled(ctx):
     L_all = torch.empty((NO, NN, NI), dtype=torch.float64, device="cuda")
     mean = torch.empty((NO, NN), dtype=torch.float64, device="cuda")
     q = torch.empty((NO, NN), dtype=torch.float64, device="cuda")
-    rsv.rsv_compute_nested(ctx, rsv.RSV_FORM_F32_COMP, n_outer=NO, n_nodes=NN, node_step_m=12, n_inner=NI, seed=0,
+    rsv.rsv_compute_nested(ctx, form, n_outer=NO, n_nodes=NN, node_step_m=12, n_inner=NI, seed=0,
                            on_device=True, L_mean=mean, L_q995=q, L_all=L_all)
     rsv.rsv_synchronize(ctx)
     L = L_all.cpu().numpy()
@@ -115,7 +146,7 @@ def test_config3_full_size_sampled(ctx):
         idx = np.sort(rng.choice(NI, 3, replace=False))
         ref, _, _ = oracle.nested_node(pol, tab, 0, o, n, idx, node_step=12)
         worst = max(worst, float(np.max(np.abs(L[o, n, idx] - ref) / np.abs(ref))))
-    print(f"config-3 sampled: max rel err {worst:.3e}")
+    print(f"config-3 sampled, form {rsv.FORM_NAMES[form]}: max rel err {worst:.3e}")
     assert worst <= 1e-6
     srt = np.sort(L, axis=2)
     assert np.array_equal(q.cpu().numpy(), srt[:, :, -5])
