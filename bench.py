@@ -81,9 +81,9 @@ ALGO_FLOPS = {0: 3, 1: 16, 2: 3, 3: 3}
 # (FMA = 2, add/sub/mul/min/max = 1): plain v p then an FMA; the double-float
 # forms' products and ordered sums; the deflated form per 16 steps two
 # products and 14 FMAs (30), the join of its two partial sums (1) and the
-# ordered fold (6), plus for the reversionary annuity the expected cash flow
-# (two products, one subtraction, one FMA: 5) per policy-step shared by the M
-# scenarios of a lane.
+# ordered fold (6; the packed-pair variants' TwoSum 7), plus for the
+# reversionary annuity the expected cash flow (two products, one subtraction,
+# one FMA: 5) per policy-step shared by the M scenarios of a lane.
 ISSUED_FLOPS = {"f32": {0: 3, 1: 9, 2: 3, 3: 3},
                 "f32comp": {0: 16, 1: 48, 2: 20, 3: 20},
                 "f64": {0: 3, 1: 9, 2: 3, 3: 3},
@@ -108,6 +108,8 @@ def issued_flops(pol, form, n_scen, horizon=0, variant_name=""):
     if form == "f32defl":   # the JL expected cash flow, amortised over the lane's M scenarios
         m = re.search(r"xM(\d+)", variant_name)
         per[1] += 5.0 / (int(m.group(1)) if m else 4)
+        if variant_name.endswith(" x2"):   # TwoSum fold: one operation more per span
+            per = {p: f + 1.0 / 16 for p, f in per.items()}
     return float(sum(per[p] * cs[p] for p in cs) * n_scen)
 
 
@@ -397,7 +399,7 @@ def bench_config1(rsv, torch, tab, reps=20):
 
 
 FIG1_STEPS = (60, 120, 240, 360, 480, 600, 720)
-FIG1_WORKLOAD = ("the paper's algorithm comparison (Section 5.2): single-life annuities from age 60 with a term of "
+FIG1_WORKLOAD = ("the paper's algorithm comparison (Section 5.1.2, Fig. 1): single-life annuities from age 60 with a term of "
                  "S months, one flat 4% scenario, FP64, the reserve at every step; time per policy")
 
 
@@ -463,8 +465,18 @@ def bench_surrogate(rsv, torch, tab, epochs, lr=2e-3, n_train=10_000_000, n_val=
     rsv.rsv_load_portfolio(ctx, pol)
     rsv.rsv_mlp_init(ctx, 0)
     rep = rsv.rsv_surrogate_train(ctx, n_train=n_train, n_val=n_val, epochs=epochs, batch=8192, lr=lr, seed=0)
-    rsv.rsv_destroy(ctx)
     flops_q = 2 * (32 * 256 + 3 * 256 * 256 + 256)
+    # the tcgen05 inference kernel alone on batches of 2^19 queries (features
+    # already on the device; CUDA events around the kernel, best of 5)
+    Xq = np.random.default_rng(1).normal(0, 1, (1 << 19, 32)).astype(np.float32)
+    Xq[:, 20:] = 0.0
+    ks = []
+    for _ in range(6):
+        rsv.rsv_mlp_forward(ctx, Xq)
+        ks.append(rsv.rsv_last_kernel_ms(ctx))
+    k_ms = min(ks[1:])
+    rsv.rsv_destroy(ctx)
+    peaks = measured_peaks()
     return {
         "workload": SURROGATE_WORKLOAD if (n_train, n_val) == (10_000_000, 1_000_000) else
         f"profiling case: {n_train} labels, {n_val} held-out queries", "epochs": epochs, "lr": lr,
@@ -472,12 +484,25 @@ def bench_surrogate(rsv, torch, tab, epochs, lr=2e-3, n_train=10_000_000, n_val=
         "tol": 1e-3, "margin": 0.3, "frac_fallback": rep["frac_fallback"], "combined_max_rel": rep["combined_max_rel"],
         "buckets_flagged": f"{rep['n_flagged']} of {rep['n_buckets']}",
         "residual_target_sd": rep["y_std"],
-        "network_queries_s": rep["n_infer"] / (rep["infer_ms"] / 1e3),
-        "network_tflops": rep["n_infer"] * flops_q / (rep["infer_ms"] / 1e3) / 1e12,
+        "scoring_queries_s": rep["n_infer"] / (rep["infer_ms"] / 1e3),
+        "scoring_note": "held-out scoring: features, the network and the reserve, batches of 524,288",
+        "network_kernel": {
+            "kernel": "mlp_fwd_tc_kernel (tcgen05, TMEM accumulators)", "queries": 1 << 19, "kernel_ms": k_ms,
+            "flops_per_query": flops_q, "tflops": (1 << 19) * flops_q / (k_ms / 1e3) / 1e12,
+            "frac_of_measured_bf16_burst_peak": (1 << 19) * flops_q / (k_ms / 1e3) / 1e12 / peaks["bf16_tflops"]
+            if peaks else None,
+            "peak": peaks["bf16_tflops"] if peaks else None},
         "recurrence_fp64_queries_s": rep["n_label"] / (rep["label_ms"] / 1e3),
         "train_s": rep["train_ms"] / 1e3,
         "train_samples_s": epochs * (n_train // 8192) * 8192 / max(rep["train_ms"] / 1e3, 1e-9),
     }
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
 
 
 def head_inputs(n_pol=None, n_scen=None):
@@ -526,8 +551,8 @@ def reference_arm(args, rank):
 
 
 def cpu_baseline(pol, tab, v, horizon, n_sample, runs=7):
-    """The oracle on the host cores, the paper's timing method (Section 5.1:
-    the minimum of repeated runs; the median beside it): one warm-up and
+    """The oracle on the host cores, the paper's timing method (Section 5.2.1:
+    the minimum of seven runs; the median beside it): one warm-up and
     ``runs`` timed runs of the first n_sample policies x all scenarios."""
     sub = synth.take(pol, slice(0, n_sample))
     times, threads = oracle_runs(sub, tab, v, horizon, runs)
@@ -787,6 +812,10 @@ def main():
                     help="train the surrogate on the nested portfolio and time its mode (0: skip)")
     ap.add_argument("--mlife-only", action="store_true",
                     help="time only the m-life contracts (--policies of them) and print their record")
+    ap.add_argument("--nested-only", action="store_true",
+                    help="time only the nested valuation (--nested-outer paths) and print its record")
+    ap.add_argument("--surrogate-only", action="store_true",
+                    help="train and score only the surrogate (--surrogate-* sizes) and print its record")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -799,6 +828,22 @@ def main():
         torch.cuda.set_device(local)
         print(json.dumps({"mlife": bench_mlife(rsv, torch, synth.gm_monthly_survival(), n_pol=args.policies)}),
               flush=True)
+        return
+    if args.surrogate_only:   # a profiling case of the network kernels
+        import torch
+        from paper_1401_1757_gb300 import rsv
+        torch.cuda.set_device(local)
+        print(json.dumps({"surrogate": bench_surrogate(rsv, torch, synth.gm_monthly_survival(), args.surrogate_epochs,
+                                                       lr=args.surrogate_lr, n_train=args.surrogate_train,
+                                                       n_val=args.surrogate_val)}), flush=True)
+        return
+    if args.nested_only:   # a profiling case of the nested kernels
+        import torch
+        from paper_1401_1757_gb300 import rsv
+        torch.cuda.set_device(local)
+        print(json.dumps({"nested": bench_nested(rsv, torch, synth.gm_monthly_survival(), steps=1, warmup=1,
+                                                 n_outer=args.nested_outer,
+                                                 sur_epochs=args.nested_surrogate_epochs)}), flush=True)
         return
 
     import torch

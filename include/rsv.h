@@ -505,7 +505,8 @@ enum { RSV_MLP_MMA_SYNC = 0, RSV_MLP_TCGEN05 = 1 };
 rsv_status rsv_mlp_set_backend(rsv_ctx *ctx, int32_t backend);
 
 /* Network output for n rows of 32 host FP32 features (rounded to BF16 on the
- * way in), 1 <= n <= 2^20; y (host) receives n outputs. */
+ * way in), 1 <= n <= 2^20; y (host) receives n outputs.  The device time of
+ * the network's kernels (not the copies) is available from rsv_last_kernel_ms. */
 rsv_status rsv_mlp_forward(rsv_ctx *ctx, const float *X, int64_t n, float *y);
 
 /* Gradient of the mean squared error (1/n) sum (y - target)^2 over n rows
@@ -668,9 +669,10 @@ rsv_status rsv_synchronize(rsv_ctx *ctx);
  * call).  Never NULL. */
 const char *rsv_last_error(const rsv_ctx *ctx);
 
-/* Device time in ms of the last recurrence kernel issued by
- * rsv_compute_reserves on ctx (CUDA events on the context stream; valid after
- * the call has completed).  Returns -1 if unknown. */
+/* Device time in ms of the last timed kernel work on ctx: the recurrence
+ * kernel of rsv_compute_reserves, or the kernels named by the other calls that
+ * say so (CUDA events on the context stream; valid after the call has
+ * completed).  Returns -1 if unknown. */
 float rsv_last_kernel_ms(rsv_ctx *ctx);
 
 /* Number of streaming multiprocessors of the context's device. */

@@ -52,7 +52,19 @@
 // consecutive steps of any policy are one aligned 16-byte shared-memory load.
 // Items come from an atomic queue in decreasing-cost order; thread 0 claims
 // them ahead of use, so the staging of the next item overlaps this one.
+//
+// Packed pairs (X2 variants).  sm_100 and later issue fma/mul/add/sub on two
+// FP32 values held in one 64-bit register pair (.f32x2), each half rounded
+// exactly as the scalar instruction rounds.  The two accumulators of a chain
+// are one pair {even steps, odd steps}, and four consecutive steps of a
+// deflator row and of a weight row are two pairs, so a pair instruction does
+// the work of two chain-steps.  The fold of a span into (h, l) runs on pairs
+// of chains (scenarios m and m + 1) as Knuth's branch-free TwoSum, whose error
+// term is exact like the ordered Fast2Sum's: the X2 variants give the same
+// bits as the scalar ones.
 #pragma once
+
+#include <type_traits>
 
 #include "rsv_device.cuh"
 
@@ -139,8 +151,47 @@ __device__ __forceinline__ void defl_mbar_arrive(uint64_t* bar) {
 // Per-lane state of one item: P policies x M scenarios.
 template <int P, int M>
 struct DeflLane {
+    static constexpr bool packed = false;
     float a0[P][M], a1[P][M];   // the current 16 steps' two FP32 accumulators
     float h[P][M], l[P][M];     // double-float sums of the folded spans
+    __device__ __forceinline__ void start(int i, const float (&h0)[M]) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            h[i][m] = h0[m];
+            l[i][m] = 0.0f;
+        }
+    }
+    __device__ __forceinline__ void sum(int i, float (&H)[M], float (&L)[M]) const {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            H[m] = h[i][m];
+            L[m] = l[i][m];
+        }
+    }
+};
+
+// The same state in packed pairs (M even): acc = {a0, a1} of each chain,
+// (h, l) of scenarios 2k (x) and 2k + 1 (y).
+template <int P, int M>
+struct DeflLaneX2 {
+    static constexpr bool packed = true;
+    static_assert(M % 2 == 0, "pairs of scenarios");
+    f32x2 acc[P][M];
+    f32x2 h[P][M / 2], l[P][M / 2];
+    __device__ __forceinline__ void start(int i, const float (&h0)[M]) {
+#pragma unroll
+        for (int k = 0; k < M / 2; ++k) {
+            h[i][k] = x2_pack(h0[2 * k], h0[2 * k + 1]);
+            l[i][k] = 0ull;
+        }
+    }
+    __device__ __forceinline__ void sum(int i, float (&H)[M], float (&L)[M]) const {
+#pragma unroll
+        for (int k = 0; k < M / 2; ++k) {
+            x2_unpack(h[i][k], H[2 * k], H[2 * k + 1]);
+            x2_unpack(l[i][k], L[2 * k], L[2 * k + 1]);
+        }
+    }
 };
 
 // What a block needs of a warp's P slots.
@@ -197,8 +248,8 @@ __device__ __forceinline__ float4 defl_weights(const DeflPol<P>& pp, int i, cons
 // weights of every policy first, then the fused multiply-adds step by step
 // across all chains (the two accumulators take alternate steps).  FIRST: the
 // group opens a 16-step span, whose products start the accumulators.
-template <int KIND, int P, int M, bool FIRST>
-__device__ __forceinline__ void defl_group(DeflLane<P, M>& st, const DeflPol<P>& pp, const float4* __restrict__ tab,
+template <int KIND, int P, int M, bool FIRST, class Lane>
+__device__ __forceinline__ void defl_group(Lane& st, const DeflPol<P>& pp, const float4* __restrict__ tab,
                                            const float4 (&d)[M], int g, bool check) {
     float4 e[P];
 #pragma unroll
@@ -208,24 +259,45 @@ __device__ __forceinline__ void defl_group(DeflLane<P, M>& st, const DeflPol<P>&
         if (check && 4 * g >= pp.S[i]) e[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         else e[i] = defl_weights<KIND, P>(pp, i, tab, g, check);
     }
+    if constexpr (Lane::packed) {   // steps {4g+2, 4g+3}, then {4g, 4g+1}
+        f32x2 dl[M], dh[M];
 #pragma unroll
-    for (int i = 0; i < P; ++i)
+        for (int m = 0; m < M; ++m) {
+            dl[m] = x2_pack(d[m].x, d[m].y);
+            dh[m] = x2_pack(d[m].z, d[m].w);
+        }
 #pragma unroll
-        for (int m = 0; m < M; ++m)
-            st.a1[i][m] = FIRST ? __fmul_rn(d[m].w, e[i].w) : __fmaf_rn(d[m].w, e[i].w, st.a1[i][m]);
+        for (int i = 0; i < P; ++i) {
+            const f32x2 eh = x2_pack(e[i].z, e[i].w);
 #pragma unroll
-    for (int i = 0; i < P; ++i)
+            for (int m = 0; m < M; ++m) st.acc[i][m] = FIRST ? x2_mul(dh[m], eh) : x2_fma(dh[m], eh, st.acc[i][m]);
+        }
 #pragma unroll
-        for (int m = 0; m < M; ++m)
-            st.a0[i][m] = FIRST ? __fmul_rn(d[m].z, e[i].z) : __fmaf_rn(d[m].z, e[i].z, st.a0[i][m]);
+        for (int i = 0; i < P; ++i) {
+            const f32x2 el = x2_pack(e[i].x, e[i].y);
 #pragma unroll
-    for (int i = 0; i < P; ++i)
+            for (int m = 0; m < M; ++m) st.acc[i][m] = x2_fma(dl[m], el, st.acc[i][m]);
+        }
+    } else {
 #pragma unroll
-        for (int m = 0; m < M; ++m) st.a1[i][m] = __fmaf_rn(d[m].y, e[i].y, st.a1[i][m]);
+        for (int i = 0; i < P; ++i)
 #pragma unroll
-    for (int i = 0; i < P; ++i)
+            for (int m = 0; m < M; ++m)
+                st.a1[i][m] = FIRST ? __fmul_rn(d[m].w, e[i].w) : __fmaf_rn(d[m].w, e[i].w, st.a1[i][m]);
 #pragma unroll
-        for (int m = 0; m < M; ++m) st.a0[i][m] = __fmaf_rn(d[m].x, e[i].x, st.a0[i][m]);
+        for (int i = 0; i < P; ++i)
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                st.a0[i][m] = FIRST ? __fmul_rn(d[m].z, e[i].z) : __fmaf_rn(d[m].z, e[i].z, st.a0[i][m]);
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+#pragma unroll
+            for (int m = 0; m < M; ++m) st.a1[i][m] = __fmaf_rn(d[m].y, e[i].y, st.a1[i][m]);
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+#pragma unroll
+            for (int m = 0; m < M; ++m) st.a0[i][m] = __fmaf_rn(d[m].x, e[i].x, st.a0[i][m]);
+    }
 }
 
 // After the steps of one 16-step span: fold the two accumulators into (h, l).
@@ -236,10 +308,30 @@ __device__ __forceinline__ void defl_fold_all(DeflLane<P, M>& st) {
 #pragma unroll
         for (int m = 0; m < M; ++m) defl_fold(st.h[i][m], st.l[i][m], __fadd_rn(st.a0[i][m], st.a1[i][m]));
 }
+// Packed: b = a0 + a1 of two chains, then TwoSum (s, e) = h + b on the pair
+// (exact e for any order of magnitude, so no ordering is needed) and l += e.
+template <int P, int M>
+__device__ __forceinline__ void defl_fold_all(DeflLaneX2<P, M>& st) {
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+        for (int k = 0; k < M / 2; ++k) {
+            float x0, y0, x1, y1;
+            x2_unpack(st.acc[i][2 * k], x0, y0);
+            x2_unpack(st.acc[i][2 * k + 1], x1, y1);
+            const f32x2 b = x2_pack(__fadd_rn(x0, y0), __fadd_rn(x1, y1));
+            const f32x2 h = st.h[i][k];
+            const f32x2 s = x2_add(h, b);
+            const f32x2 bb = x2_sub(s, h);
+            const f32x2 e = x2_add(x2_sub(h, x2_sub(s, bb)), x2_sub(b, bb));
+            st.h[i][k] = s;
+            st.l[i][k] = x2_add(st.l[i][k], e);
+        }
+}
 
 // One 16-step span (four groups, descending) from the staged rows r0+3 .. r0.
-template <int KIND, int P, int M>
-__device__ __forceinline__ void defl_span(DeflLane<P, M>& st, const DeflPol<P>& pp, const float4* __restrict__ tab,
+template <int KIND, int P, int M, class Lane>
+__device__ __forceinline__ void defl_span(Lane& st, const DeflPol<P>& pp, const float4* __restrict__ tab,
                                           const float4* __restrict__ ring_b, int g0, int lane, bool check) {
 #pragma unroll
     for (int u = 3; u >= 0; --u) {
@@ -253,8 +345,8 @@ __device__ __forceinline__ void defl_span(DeflLane<P, M>& st, const DeflPol<P>& 
 }
 
 // One staged block (two spans, descending) of one item.
-template <int KIND, int P, int M>
-__device__ __forceinline__ void defl_block(DeflLane<P, M>& st, const DeflPol<P>& pp, const float4* __restrict__ tab,
+template <int KIND, int P, int M, class Lane>
+__device__ __forceinline__ void defl_block(Lane& st, const DeflPol<P>& pp, const float4* __restrict__ tab,
                                            const float4* __restrict__ ring_b, int j, int lane, int smin, int smax) {
     const int t_lo = j * DEFL_KB;
     if (t_lo >= smax) return;                       // every policy of this warp has ended before the block
@@ -274,7 +366,7 @@ __device__ __forceinline__ void defl_block(DeflLane<P, M>& st, const DeflPol<P>&
 // mbarrier arrival; the producer refills a buffer once all NW warps have
 // released it.  The per-scenario sums of an item are joined by the warp that
 // finishes the item last (a shared-memory counter), in warp order.
-template <int P, int M, int NW, int NBUF, int MINB>
+template <int P, int M, int NW, int NBUF, int MINB, bool X2>
 __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArgs a) {
     using SM = DeflSmem<P, M, NW, NBUF>;
     constexpr int CH = SM::CH, W = NW * P;
@@ -357,7 +449,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
     }
 
     // -------------------- consumers
-    DeflLane<P, M> st;
+    using Lane = typename std::conditional<X2, DeflLaneX2<P, M>, DeflLane<P, M>>::type;
+    Lane st;
     DeflPol<P> pp;
     int smin = 0, smax = 0, kind = K_ANN, stt = 0, chunk = 0;
     for (int k = 0;; ++k) {
@@ -393,9 +486,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
                 pp.iy[i] = f4.y;
                 smin = min(smin, S);
                 smax = max(smax, S);
+                float h0s[M];
 #pragma unroll
                 for (int m = 0; m < M; ++m) {
-                    st.l[i][m] = 0.0f;
                     float h0 = 0.0f;
                     if (mat != 0.0f && q4.w >= 0) {   // U_S = D_S l_{x+S} bnd
                         float dS = 1.0f;
@@ -405,8 +498,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
                         }
                         h0 = __fmul_rn(dS, mat);
                     }
-                    st.h[i][m] = h0;
+                    h0s[m] = h0;
                 }
+                st.start(i, h0s);
             }
         }
         rec = a.slots + (size_t)stt * W + warp * P;
@@ -427,11 +521,13 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
                 const int pol = rec[i].pol;
                 if (pol < 0) continue;
                 const float sh = rec[i].sc_h, sl = rec[i].sc_l;
+                float Hs[M], Ls[M];
+                st.sum(i, Hs, Ls);
 #pragma unroll
                 for (int m = 0; m < M; ++m) {
                     const int s = chunk * CH + m * 32 + lane;
                     if (s >= a.n_scen) continue;
-                    const float H = st.h[i][m], L = st.l[i][m];
+                    const float H = Hs[m], L = Ls[m];
                     const size_t o = (size_t)pol * a.v0_ld + s;
                     // (H + L)(sh + sl) as a double-float, for V0 and the sums
                     const float p = __fmul_rn(H, sh);
@@ -489,33 +585,33 @@ struct DeflVariant {
     cudaError_t (*occupancy)(int* blocks_per_sm, size_t smem);
 };
 
-template <int P, int M, int NW, int NBUF, int MINB>
+template <int P, int M, int NW, int NBUF, int MINB, bool X2>
 cudaError_t set_defl_attributes(size_t smem) {
-    auto k = defl_kernel<P, M, NW, NBUF, MINB>;
+    auto k = defl_kernel<P, M, NW, NBUF, MINB, X2>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
 }
 
-template <int P, int M, int NW, int NBUF, int MINB>
+template <int P, int M, int NW, int NBUF, int MINB, bool X2>
 cudaError_t launch_defl(const DeflArgs& a, int grid, size_t smem, cudaStream_t st) {
-    cudaError_t e = set_defl_attributes<P, M, NW, NBUF, MINB>(smem);
+    cudaError_t e = set_defl_attributes<P, M, NW, NBUF, MINB, X2>(smem);
     if (e != cudaSuccess) return e;
-    defl_kernel<P, M, NW, NBUF, MINB><<<grid, (NW + 1) * 32, smem, st>>>(a);
+    defl_kernel<P, M, NW, NBUF, MINB, X2><<<grid, (NW + 1) * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int P, int M, int NW, int NBUF, int MINB>
+template <int P, int M, int NW, int NBUF, int MINB, bool X2>
 cudaError_t occupancy_defl(int* blocks, size_t smem) {
-    cudaError_t e = set_defl_attributes<P, M, NW, NBUF, MINB>(smem);
+    cudaError_t e = set_defl_attributes<P, M, NW, NBUF, MINB, X2>(smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, defl_kernel<P, M, NW, NBUF, MINB>, (NW + 1) * 32,
-                                                         smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, defl_kernel<P, M, NW, NBUF, MINB, X2>,
+                                                         (NW + 1) * 32, smem);
 }
 
-#define RSV_DEFL_VARIANT(P, M, NW, NBUF, MINB, NAME)                                                  \
-    DeflVariant {                                                                                     \
-        P, M, NW, NBUF, NAME, &launch_defl<P, M, NW, NBUF, MINB>, &occupancy_defl<P, M, NW, NBUF, MINB> \
+#define RSV_DEFL_VARIANT(P, M, NW, NBUF, MINB, X2, NAME)                                              \
+    DeflVariant {                                                                                         \
+        P, M, NW, NBUF, NAME, &launch_defl<P, M, NW, NBUF, MINB, X2>, &occupancy_defl<P, M, NW, NBUF, MINB, X2> \
     }
 
 const DeflVariant* variants_defl(int* n);

@@ -130,12 +130,17 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// 2 gelu(z) in the tanh form: z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).  The
-// factor 1/2 of gelu is carried by the next layer's weights (and the head's),
-// which saves a multiply per element; powers of two scale BF16 and FP32 exactly.
-__device__ __forceinline__ float gelu2_f(float z) {
-    const float t = tanh_hw(z * __fmaf_rn(kGeluCK, z * z, kGeluC));
-    return __fmaf_rn(z, t, z);
+// 2 gelu(z) in the tanh form, z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))), of
+// z = acc + bias for two columns at once.  The factor 1/2 of gelu is carried
+// by the next layer's weights (and the head's), which saves a multiply per
+// element; powers of two scale BF16 and FP32 exactly.  The arithmetic runs in
+// packed FP32 pairs (each half rounded as the scalar instruction rounds, in
+// half the issue slots); tanh.approx stays scalar.
+__device__ __forceinline__ void bias_gelu2_x2(float& z0, float& z1, float b0, float b1, f32x2 cK, f32x2 cC) {
+    const f32x2 z = x2_add(x2_pack(z0, z1), x2_pack(b0, b1));
+    float u0, u1;
+    x2_unpack(x2_mul(z, x2_fma(cK, x2_mul(z, z), cC)), u0, u1);
+    x2_unpack(x2_fma(z, x2_pack(tanh_hw(u0), tanh_hw(u1)), z), z0, z1);
 }
 
 // 16 columns of this warp's 32 lanes from registers into TMEM; waits for completion
@@ -158,6 +163,8 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // ---- the kernel -------------------------------------------------------------
+// TRACE: also write the traced layer values (a.trace_z, a.trace_a).
+template <bool TRACE>
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_fwd_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapW1,
                       const __grid_constant__ CUtensorMap mapW2, const __grid_constant__ CUtensorMap mapW3,
@@ -296,9 +303,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         // epilogue: row = 32 (warp % 4) + lane, columns 32 (warp / 4) .. +31 of each half
         const int quarter = warp & 3, cgrp = warp >> 2, row = quarter * 32 + lane;
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+        const f32x2 cK = x2_pack(kGeluCK, kGeluCK), cC = x2_pack(kGeluC, kGeluC);
         for (int it = 0; it < n_my; ++it) {
             const int tile = blockIdx.x + it * gridDim.x;
-            float ysum = 0.0f;
+            f32x2 ysum = 0ull;   // the head's dot product: even and odd columns in the two halves
             for (int l = 1; l <= 4; ++l) {
                 const int g = it * 4 + l - 1;
                 for (int h = 0; h < 2; ++h) {
@@ -317,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tmem_ld32(tmem + lane_base + c0, v);
                     const float4* b4 = reinterpret_cast<const float4*>(&bias_s[l - 1][c0]);
                     const size_t trow = (size_t)tile * TM + row;   // the row in the traced outputs
-                    if (a.trace_z) {
+                    if constexpr (TRACE) {
                         float* tz = a.trace_z + (((size_t)(l - 1) * a.n_tiles * TM + trow) * TN + c0);
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
@@ -331,31 +339,32 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const float4 b = b4[i];
-                        v[4 * i] = gelu2_f(v[4 * i] + b.x);
-                        v[4 * i + 1] = gelu2_f(v[4 * i + 1] + b.y);
-                        v[4 * i + 2] = gelu2_f(v[4 * i + 2] + b.z);
-                        v[4 * i + 3] = gelu2_f(v[4 * i + 3] + b.w);
+                        bias_gelu2_x2(v[4 * i], v[4 * i + 1], b.x, b.y, cK, cC);
+                        bias_gelu2_x2(v[4 * i + 2], v[4 * i + 3], b.z, b.w, cK, cC);
                     }
                     if (l < 4) {
                         uint32_t r[16];
 #pragma unroll
                         for (int m = 0; m < 16; ++m) r[m] = pack_bf16x2(v[2 * m], v[2 * m + 1]);
                         tmem_st16(tmem + lane_base + acol_of((l - 1) & 1) + c0 / 2, r);
-                        if (a.trace_a) {
+                        if constexpr (TRACE) {
                             uint32_t* ta = a.trace_a + (((size_t)(l - 1) * a.n_tiles * TM + trow) * TN + c0) / 2;
 #pragma unroll
                             for (int m = 0; m < 16; ++m) ta[m] = r[m];
                         }
                     } else {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) ysum = __fmaf_rn(v[i], w5_s[c0 + i], ysum);
+                        for (int i = 0; i < 32; i += 2)
+                            ysum = x2_fma(x2_pack(v[i], v[i + 1]), x2_pack(w5_s[c0 + i], w5_s[c0 + i + 1]), ysum);
                     }
                     fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&bar_epi[h]);
                 }
             }
-            head_part[cgrp][row] = ysum;
+            float y_even, y_odd;
+            x2_unpack(ysum, y_even, y_odd);
+            head_part[cgrp][row] = y_even + y_odd;
             asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
             if (cgrp == 0)
                 a.y[tile * TM + row] =
@@ -450,11 +459,11 @@ cudaError_t Mlp::forward_tc(const __nv_bfloat16* Xin, int n, float* yout, int sm
     a.trace_z = trace_z;
     a.trace_a = static_cast<uint32_t*>(trace_a);
     const size_t smem = X_BYTES + W_BYTES + 1024;
-    if ((e = cudaFuncSetAttribute(mlp_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
+    auto kern = trace_z || trace_a ? mlp_fwd_tc_kernel<true> : mlp_fwd_tc_kernel<false>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     const int grid = std::min(a.n_tiles, sm_count);
-    mlp_fwd_tc_kernel<<<grid, kThreads, smem, st>>>(mx, mw[0], mw[1], mw[2], mw[3], a);
+    kern<<<grid, kThreads, smem, st>>>(mx, mw[0], mw[1], mw[2], mw[3], a);
     return cudaGetLastError();
 }
 

@@ -3,9 +3,9 @@
 // Loads copy the caller's host data; compute builds (and caches) the device
 // work layout: the decrement tables in the form's entry format, the policy
 // tiles grouped by reduced model and sorted by decreasing projection length
-// (so the persistent kernel's queue hands out the longest work first, as the
-// paper's dynamic OpenMP schedule did, Section 5.1.1), and the scratch of the
-// per-scenario totals.
+// (so the persistent kernel's queue hands out the longest work first; the
+// paper spreads policies over OpenMP threads, Section 6.2), and the scratch of
+// the per-scenario totals.
 #include <algorithm>
 #include <thread>
 #include <cmath>

@@ -111,6 +111,24 @@ def test_every_variant_agrees(ctx):
         assert np.max(np.abs(tot - ref_tot) / ref_tot) <= TOL
 
 
+def test_packed_variants_give_the_scalar_bits(ctx):
+    """The packed-pair (f32x2) variants round every operation as the scalar
+    ones do, and their TwoSum fold has the same exact error term as the
+    ordered Fast2Sum: their reserves are bit-identical to the scalar variant
+    of the same shape, on the whole mix with every state."""
+    tab = synth.gm_monthly_survival()
+    pol = with_jl_states(synth.portfolio_mix(300, seed=8))
+    v = synth.vasicek_paths(201, 1200, seed=8)
+    names = {rsv.rsv_variant_name(DEFL, i): i for i in range(rsv.rsv_variant_count(DEFL))}
+    pairs = [(names[n[:-3]], i) for n, i in names.items() if n.endswith(" x2") and n[:-3] in names]
+    assert pairs
+    for scalar, packed in pairs:
+        a, ta = run(ctx, pol, [tab], v, variant=scalar)
+        b, tb = run(ctx, pol, [tab], v, variant=packed)
+        assert np.array_equal(a, b), rsv.rsv_variant_name(DEFL, packed)
+        assert np.array_equal(ta, tb)
+
+
 def test_negative_rates_and_steep_weights(ctx):
     """Scenarios with negative rates (discount factors above 1, so the weights
     can grow along the chain) and a steep constant-force table: the ordered
