@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "rsv.h"
@@ -35,6 +36,64 @@ struct DevBuf {
         if (p) cudaFree(p);
         p = nullptr;
         n = 0;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+// Run part(k) for k = 0 .. T-1, on T - 1 helper threads and this one; the
+// parts whose thread cannot start run here.
+template <class F>
+inline void run_parts(int T, F&& part) {
+    std::vector<std::thread> th;
+    int started = 1;
+    if (T > 1) {
+        try {
+            th.reserve(T - 1);
+            for (int k = 1; k < T; ++k) {
+                th.emplace_back(part, k);
+                ++started;
+            }
+        } catch (...) {   // no more threads: the rest runs serially below
+        }
+    }
+    part(0);
+    for (int k = started; k < T; ++k) part(k);
+    for (auto& t : th) t.join();
+}
+
+// Pinned host staging for uploads built on the host: written in place, copied
+// with one asynchronous copy at full link speed.  `ready` is recorded after
+// the copy; the next writer waits for it, so a buffer is never rewritten while
+// a copy from it may still run.
+struct HostStage {
+    void* p = nullptr;
+    size_t n = 0;
+    cudaEvent_t ready = nullptr;
+    cudaError_t acquire(size_t bytes) {
+        cudaError_t e;
+        if (ready && (e = cudaEventSynchronize(ready)) != cudaSuccess) return e;
+        if (bytes <= n && p) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+        if ((e = cudaHostAlloc(&p, bytes ? bytes : 16, cudaHostAllocDefault)) != cudaSuccess) return e;
+        n = bytes;
+        return cudaSuccess;
+    }
+    cudaError_t upload(void* dst, size_t bytes, cudaStream_t st) {
+        cudaError_t e;
+        if (!ready && (e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if (bytes && (e = cudaMemcpyAsync(dst, p, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+        return cudaEventRecord(ready, st);
+    }
+    void release() {
+        if (ready) cudaEventSynchronize(ready);
+        if (p) cudaFreeHost(p);
+        if (ready) cudaEventDestroy(ready);
+        p = nullptr;
+        n = 0;
+        ready = nullptr;
     }
     template <class T>
     T* as() const { return static_cast<T*>(p); }
@@ -138,6 +197,7 @@ struct SurrogateState {
 }  // namespace rsv
 
 using rsv::DevBuf;
+using rsv::HostStage;
 
 struct rsv_ctx {
     using Layout = rsv::Layout;
@@ -188,6 +248,7 @@ struct rsv_ctx {
     int tuned[4] = {-1, -1, -1, -1};
     // the deflated form: super-tile slots, life tables, deflator plane
     DevBuf d_defl_slots, d_defl_kinds, d_defl_tab, d_defl_plane;
+    HostStage h_defl_stage;   // the deflated slot records, built here and uploaded
     unsigned long long defl_lay_key = 0, defl_tab_key = 0;
     int defl_W = -1, defl_n_st = 0, defl_dpad = 0, defl_n_tab = 0;
     // surrogate network and its data

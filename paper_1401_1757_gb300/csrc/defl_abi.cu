@@ -2,6 +2,7 @@
 // (RSV_FORM_F32_DEFLATED): life tables, super-tile slot records, the
 // deflator plane and the launches.
 #include <algorithm>
+#include <thread>
 #include <cmath>
 #include <vector>
 
@@ -148,7 +149,10 @@ rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     const unsigned long long lkey = L.gen * 31ull + (unsigned long long)dpad * 7ull + (unsigned)L.horizon * 3ull +
                                     (unsigned long long)arr_d;
     if (c->defl_lay_key != lkey || c->defl_W != W || c->defl_dpad != dpad || c->defl_n_st != L.n_tiles) {
-        std::vector<DeflSlot> ds((size_t)L.n_tiles * W);
+        // written in place into pinned memory by several host threads
+        const size_t n_slots = (size_t)L.n_tiles * W;
+        CU(c->h_defl_stage.acquire(std::max<size_t>(1, n_slots) * sizeof(DeflSlot)));
+        DeflSlot* ds = c->h_defl_stage.as<DeflSlot>();
         auto off = [&](int arr, int tb, int age) {
             const int cp = age & 3;
             return (int)(((((size_t)arr * n_tab + tb) * 4 + cp) * dpad + (age - cp)) / 4);
@@ -166,7 +170,8 @@ rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
                 gz = (z - age + 3) / 4;
             }
         };
-        for (int f = 0; f < L.n_tiles; ++f) {
+        auto fill = [&](int f0, int f1) {
+        for (int f = f0; f < f1; ++f) {
             const int kind = L.h_k2[f];
             for (int k = 0; k < W; ++k) {
                 const SlotRec& r = L.h_s2[(size_t)f * W + k];
@@ -219,11 +224,19 @@ rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
                 ds[(size_t)f * W + k] = d;
             }
         }
-        CU(c->d_defl_slots.ensure(std::max<size_t>(1, ds.size()) * sizeof(DeflSlot)));
+        };
+        {
+            const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+            const int T = std::max(1, std::min(std::min(hw, 16), L.n_tiles / 512));
+            run_parts(T, [&](int k) {
+                fill((int)((long long)L.n_tiles * k / T), (int)((long long)L.n_tiles * (k + 1) / T));
+            });
+        }
+        CU(c->d_defl_slots.ensure(std::max<size_t>(1, n_slots) * sizeof(DeflSlot)));
         CU(c->d_defl_kinds.ensure(std::max<size_t>(1, L.h_k2.size()) * sizeof(int32_t)));
-        if (!ds.empty()) {
-            CU(cudaMemcpyAsync(c->d_defl_slots.p, ds.data(), ds.size() * sizeof(DeflSlot), cudaMemcpyHostToDevice,
-                               c->stream));
+        if (n_slots) {
+            CU(c->h_defl_stage.upload(c->d_defl_slots.p, n_slots * sizeof(DeflSlot), c->stream));
+            // pageable source: staged before the call returns
             CU(cudaMemcpyAsync(c->d_defl_kinds.p, L.h_k2.data(), L.h_k2.size() * sizeof(int32_t),
                                cudaMemcpyHostToDevice, c->stream));
         }
@@ -301,8 +314,9 @@ rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     bool copied_v0 = false;
     if (L.n_tiles > 0 && pipelined) {
         // V0 in column blocks, each copied to the host on a second stream
-        // while the next block computes
-        const int blocks = std::min(4, NSc / 128);
+        // while the next block computes (the last block's copy is the tail
+        // left after the last kernel: eight blocks keep it short)
+        const int blocks = std::min(8, NSc / 128);
         const int width = ((NSc + blocks - 1) / blocks + 127) / 128 * 128;
         if (!c->copy_stream) CU(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
         if (!c->ev_block) CU(cudaEventCreateWithFlags(&c->ev_block, cudaEventDisableTiming));

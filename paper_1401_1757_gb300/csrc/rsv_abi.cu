@@ -180,26 +180,6 @@ namespace {
 
 int table_len(const rsv_ctx* c, int id) { return (int)c->tab[id].size(); }
 
-// Run part(k) for k = 0 .. T-1, on T - 1 helper threads and this one; the
-// parts whose thread cannot start run here.
-template <class F>
-void run_parts(int T, F&& part) {
-    std::vector<std::thread> th;
-    int started = 1;
-    if (T > 1) {
-        try {
-            th.reserve(T - 1);
-            for (int k = 1; k < T; ++k) {
-                th.emplace_back(part, k);
-                ++started;
-            }
-        } catch (...) {   // no more threads: the rest runs serially below
-        }
-    }
-    part(0);
-    for (int k = started; k < T; ++k) part(k);
-    for (auto& t : th) t.join();
-}
 
 // One record against the tables and the scenario length: its reduced model
 // (Section 3.6.4), steps and boundary; on failure the message goes to msg.
@@ -1212,6 +1192,7 @@ rsv_status rsv_destroy(rsv_ctx* c) try {
     c->mlp.release();
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    c->h_defl_stage.release();
     if (c->ev_block) cudaEventDestroy(c->ev_block);
     if (c->copy_stream) {
         cudaStreamSynchronize(c->copy_stream);
