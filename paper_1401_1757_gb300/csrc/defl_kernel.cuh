@@ -137,10 +137,11 @@ struct DeflSmem {
     static constexpr int CH = 32 * M;                      // scenarios per chunk
     static constexpr size_t ring = (size_t)NBUF * DEFL_G * CH * sizeof(float4);
     static constexpr size_t red = (size_t)2 * NW * CH * sizeof(float2);
+    static constexpr size_t slots = (size_t)2 * NW * P * sizeof(DeflSlot);   // two items' slot records
     static constexpr size_t hdr = (size_t)NBUF * sizeof(DeflBlock);
     static constexpr size_t bars = (size_t)2 * NBUF * sizeof(uint64_t);
-    // layout after the tables (tab_bytes, a multiple of 16): ring | red | hdr | bars
-    static size_t bytes(size_t tab_bytes) { return tab_bytes + ring + red + hdr + bars; }
+    // layout after the tables (tab_bytes, a multiple of 16): ring | red | slots | hdr | bars
+    static size_t bytes(size_t tab_bytes) { return tab_bytes + ring + red + slots + hdr + bars; }
 };
 
 __device__ __forceinline__ void defl_mbar_arrive(uint64_t* bar) {
@@ -378,8 +379,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
     unsigned char* base = smem_raw + a.tab_bytes;
     float4* ring = reinterpret_cast<float4*>(base);
     float2* red = reinterpret_cast<float2*>(base + SM::ring);
-    DeflBlock* hdr = reinterpret_cast<DeflBlock*>(base + SM::ring + SM::red);
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + SM::ring + SM::red + SM::hdr);
+    DeflSlot* sslot = reinterpret_cast<DeflSlot*>(base + SM::ring + SM::red);
+    DeflBlock* hdr = reinterpret_cast<DeflBlock*>(base + SM::ring + SM::red + SM::slots);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + SM::ring + SM::red + SM::slots + SM::hdr);
     uint64_t* empty = full + NBUF;
 
     if (!stage_to_smem(smem_raw, a.tab, (uint32_t)a.tab_bytes, &tbar, a.status)) return;
@@ -432,7 +434,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
                     break;
                 }
                 hdr[b] = DeflBlock{it, j, j == jmax ? 1 : 0, q | (j == 0 ? kLast : 0)};
-                mbar_arrive_expect_tx(&full[b], blk_bytes);
+                constexpr uint32_t slot_bytes = (uint32_t)(W * sizeof(DeflSlot));
+                mbar_arrive_expect_tx(&full[b], blk_bytes + (j == jmax ? slot_bytes : 0u));
+                if (j == jmax)   // the item's slot records, with its first block, into area q & 1
+                    bulk_g2s(sslot + (size_t)(q & 1) * W, a.slots + (size_t)(it / a.n_chunks) * W, slot_bytes,
+                             &full[b]);
                 const float4* src = a.D + (size_t)j * DEFL_G * a.s_pad + (size_t)chunk * CH;
                 for (int r = 0; r < DEFL_G; ++r)
                     bulk_g2s(ring + ((size_t)b * DEFL_G + r) * CH, src + (size_t)r * a.s_pad, row_bytes, &full[b]);
@@ -462,12 +468,12 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
         }
         const DeflBlock hb = hdr[b];
         if (hb.item < 0) break;
-        const DeflSlot* rec = nullptr;
+        // this warp's P slot records of the item, staged with its first block
+        const DeflSlot* rec = sslot + (size_t)(hb.q & 1) * W + warp * P;
         if (hb.first) {   // a new item: this warp's P policies
             stt = hb.item / a.n_chunks;
             chunk = hb.item - stt * a.n_chunks;
-            kind = a.st_kind[stt];
-            rec = a.slots + (size_t)stt * W + warp * P;
+            kind = rec[0].kind;
             smin = 1 << 30;
             smax = 0;
 #pragma unroll
@@ -503,7 +509,6 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
                 st.start(i, h0s);
             }
         }
-        rec = a.slots + (size_t)stt * W + warp * P;
         const float4* ring_b = ring + (size_t)b * DEFL_G * CH;
         if (kind == K_ANN) defl_block<K_ANN, P, M>(st, pp, tab, ring_b, hb.j, lane, smin, smax);
         else if (kind == K_ASS) defl_block<K_ASS, P, M>(st, pp, tab, ring_b, hb.j, lane, smin, smax);
@@ -540,37 +545,47 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
                     pl[m] = __fadd_rn(pl[m], e);
                 }
             }
+            // every warp reports; the last one joins the sums and releases the
+            // item's areas (partial sums and slot records) for item q + 2
+            const int slot = hb.q & 1;
+            float2* rs = red + (size_t)slot * NW * CH;
             if (a.partial) {
-                const int slot = hb.q & 1;
-                float2* rs = red + (size_t)slot * NW * CH;
 #pragma unroll
                 for (int m = 0; m < M; ++m) rs[warp * CH + m * 32 + lane] = make_float2(ph[m], pl[m]);
-                __threadfence_block();
-                __syncwarp();
-                int old = 0;
-                if (lane == 0) old = atomicAdd(&red_cnt[slot], 1);
-                old = __shfl_sync(0xffffffffu, old, 0);
-                if (old == NW - 1) {   // the last warp of this item: fixed order over the warps, FP64
+            }
+            __threadfence_block();
+            __syncwarp();
+            int old = 0;
+            if (lane == 0) old = atomicAdd(&red_cnt[slot], 1);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            if (old == NW - 1) {
+                if (a.partial) {
+                    // the last warp of this item joins the NW double-floats in a
+                    // fixed order (warp 0 first) with an exact TwoSum on the heads,
+                    // in FP32: GB300's narrow FP64 pipe took a warp-instruction per
+                    // 64 cycles here; only the result is widened to FP64
                     __threadfence_block();
 #pragma unroll
                     for (int m = 0; m < M; ++m) {
                         const int c = m * 32 + lane;
-                        double x = 0.0;
+                        float h = 0.0f, l = 0.0f;
                         for (int w = 0; w < NW; ++w) {
                             const float2 v = rs[w * CH + c];
-                            x += (double)v.x + (double)v.y;
+                            const float s = __fadd_rn(h, v.x);
+                            const float bb = __fsub_rn(s, h);
+                            const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(v.x, bb));
+                            h = s;
+                            l = __fadd_rn(l, __fadd_rn(e, v.y));
                         }
-                        a.partial[(size_t)stt * a.part_ld + chunk * CH + c] = x;
-                    }
-                    __syncwarp();
-                    if (lane == 0) {
-                        red_cnt[slot] = 0;
-                        __threadfence_block();
-                        atomicAdd((int*)&done_items, 1);
+                        a.partial[(size_t)stt * a.part_ld + chunk * CH + c] = (double)h + (double)l;
                     }
                 }
-            } else if (lane == 0 && warp == 0) {
-                atomicAdd((int*)&done_items, 1);
+                __syncwarp();
+                if (lane == 0) {
+                    red_cnt[slot] = 0;
+                    __threadfence_block();
+                    atomicAdd((int*)&done_items, 1);
+                }
             }
         }
         if (abort_flag) break;

@@ -29,7 +29,8 @@ const DeflVariant* variants_defl(int* n) {
 size_t defl_smem_extra(const DeflVariant& v) {
     const size_t CH = 32 * (size_t)v.M;
     return (size_t)v.NBUF * DEFL_G * CH * sizeof(float4) + (size_t)2 * v.NW * CH * sizeof(float2) +
-           (size_t)v.NBUF * sizeof(DeflBlock) + (size_t)2 * v.NBUF * sizeof(uint64_t);
+           (size_t)2 * v.NW * v.P * sizeof(DeflSlot) + (size_t)v.NBUF * sizeof(DeflBlock) +
+           (size_t)2 * v.NBUF * sizeof(uint64_t);
 }
 
 // The deflator plane: D_{t+1} = v_0 v_1 ... v_t of every scenario column as an
