@@ -1,26 +1,24 @@
 // mlp_tc.cu -- surrogate inference on the 5th-generation tensor cores
 // (tcgen05.mma, accumulators and activations in TMEM, operands staged by TMA).
 //
-// One CTA runs the whole network on 128-row tiles of queries.  Every layer is
-// split into two N = 128 halves, h = 0, 1:
-//   D_h = A_{l-1} . W_l[:, half h]   (tcgen05.mma m128 n128 k16, FP32 in TMEM)
-//   A_l[:, half h] = 2 gelu(D_h + b_l) (BF16, written back into TMEM by tcgen05.st
-//                                     as the next layer's A operand; the next
-//                                     layer's weights are staged as W / 2)
+// One CTA runs the whole network on 128-row tiles of queries, two tiles at a
+// time.  Every layer is split into two N = 128 halves, h = 0, 1:
+//   D = A_{l-1} . W_l[:, half h]   (tcgen05.mma m128 n128 k16, FP32 in TMEM)
+//   A_l[:, half h] = 2 gelu(D + b_l) (BF16, written back into TMEM by tcgen05.st
+//                                   as the next layer's A operand; the next
+//                                   layer's weights are staged as W / 2)
 //   y = 2 gelu(D_4 + b_4) . (w5 / 2) + b5  (FP32 head from the TMEM accumulators)
 // The first layer reads its A operand (the query features X) from shared
 // memory; the later ones read A from TMEM, two BF16 values per 32-bit column,
-// the even K index in the low half.  TMEM holds D_0, D_1 (columns 0-255) and
-// two activation buffers (256-383, 384-511), so the epilogue of half 0 runs
-// while the tensor cores compute half 1, and the next layer's first K half
-// starts as soon as the epilogue of half 0 is done.  Warp 16 (one thread)
-// issues the TMA copies and the products; warps 0-15 run the epilogue: warp w
-// may only touch TMEM lanes 32 (w % 4) .. +31 (the rows of the tile), and takes
-// columns 32 (w / 4) .. +31 of each half.  W_l^T is staged per half
-// (K-major, 128-byte swizzle); the next layer's half is fetched as soon as the
-// products of the current half are done.  Every mbarrier wait is bounded; on a
-// timeout the kernel records it in the status word, skips the later waits,
-// lets the copies and products in flight land, frees its TMEM and returns.
+// the even K index in the low half.  Each of the two tiles in flight (slots)
+// owns 128 accumulator columns and 128 activation columns of TMEM, so the
+// tensor cores work on one slot while the epilogue drains the other (see the
+// kernel).  Warp 16 (one thread) issues the TMA copies and the products;
+// warps 0-15 run the epilogue: warp w may only touch TMEM lanes 32 (w % 4) ..
+// +31 (the rows of the tile), and takes columns 32 (w / 4) .. +31 of each
+// half.  Every mbarrier wait is bounded; on a timeout the kernel records it in
+// the status word, skips the later waits, lets the copies and products in
+// flight land, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -46,8 +44,9 @@ constexpr uint32_t kPoll = 1u << 24;
 constexpr int kEpiWarps = 16;                   // 4 lane quarters x 4 column groups
 constexpr int kThreads = 32 * (kEpiWarps + 1);  // + the issuing warp
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kAcol0 = 256u;                // activation buffers in TMEM: columns 256 and 384
-__device__ __forceinline__ uint32_t acol_of(int i) { return kAcol0 + 128u * (uint32_t)i; }
+// TMEM columns of slot s: its accumulator at 256 s, its activation buffer at 256 s + 128
+__device__ __forceinline__ uint32_t dcol_of(int s) { return 256u * (uint32_t)s; }
+__device__ __forceinline__ uint32_t acol_of(int s) { return 256u * (uint32_t)s + 128u; }
 
 struct TcArgs {
     const float* bias[4];
@@ -109,20 +108,21 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// 16 columns of this warp's 32 lanes from TMEM, without waiting: the values
+// may be used only after tmem_wait_ld.
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-          "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+}
+// Wait for this thread's TMEM loads; the registers pass through an empty asm
+// after the wait, so that no use of them is scheduled before it.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) asm volatile("" : "+r"(r[i]));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
@@ -143,16 +143,15 @@ __device__ __forceinline__ void bias_gelu2_x2(float& z0, float& z1, float b0, fl
     x2_unpack(x2_fma(z, x2_pack(tanh_hw(u0), tanh_hw(u1)), z), z0, z1);
 }
 
-// 16 columns of this warp's 32 lanes from registers into TMEM; waits for completion
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-            taddr),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
-        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
-        : "memory");
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+// 8 columns of this warp's 32 lanes from registers into TMEM; with WAIT, waits for completion
+template <bool WAIT = true>
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+    if (WAIT) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
@@ -163,6 +162,23 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // ---- the kernel -------------------------------------------------------------
+// Two tiles in flight per CTA (slots s = 0, 1): slot s has one accumulator of
+// 128 TMEM columns (dcol_of(s)) and one activation buffer of 128 columns
+// (acol_of(s): K = 256 BF16).  The products run step by step in the order
+// (s, h) = (0, 0), (1, 0), (0, 1), (1, 1) of every layer, so that the epilogue
+// of one slot runs while the other slot's products run:
+//   products (s, l, 0): D_s = A_s(l-1) . W_l[:, 0:128]
+//   epilogue (s, l, 0): D_s into registers as the BF16 of 2 gelu(z + b), held;
+//                       D_s is released
+//   products (s, l, 1): D_s = A_s(l-1) . W_l[:, 128:256]
+//   epilogue (s, l, 1): D_s into registers; A_s(l-1) is read no more, so both
+//                       halves of A_s(l) are written into TMEM; the slot is
+//                       released for layer l + 1
+// Layer 4's epilogue feeds the head.  W_l is staged per half (K-major,
+// 128-byte swizzle); half h is refilled with the next layer's once both
+// slots' products on it are done, which the issuing thread checks only after
+// it has queued the next step's products.  A pair's second tile may lie past
+// the last one: its features load as zeros and it writes nothing.
 // TRACE: also write the traced layer values (a.trace_z, a.trace_a).
 template <bool TRACE>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -172,11 +188,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment for the swizzle atoms
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char* Xbuf = base;
-    unsigned char* Wbuf = base + X_BYTES;   // K slab s, half h at s * W_SLAB + h * WH_SLAB
-    __shared__ uint64_t bar_x, bar_w[2], bar_mma[2], bar_epi[2];
+    unsigned char* Xbuf = base;                  // slot s at s * X_BYTES
+    unsigned char* Wbuf = base + 2 * X_BYTES;    // K slab k, half h at k * W_SLAB + h * WH_SLAB
+    // bar_mma[s]: the products of one step of slot s are done; bar_dfree[s]: the
+    // epilogue (s, l, 0) has read D_s; bar_act[s]: the epilogue (s, l, 1) is done
+    __shared__ uint64_t bar_x[2], bar_w[2], bar_mma[2], bar_dfree[2], bar_act[2];
     __shared__ uint32_t tmem_slot;
-    __shared__ float head_part[4][TM];                 // partial head sums per column group
+    __shared__ float head_part[2][4][TM];              // partial head sums per slot and column group
     __shared__ __align__(16) float bias_s[4][TN];      // b_1..b_4
     __shared__ __align__(16) float w5_s[TN + 4];       // head weights and bias
 
@@ -184,11 +202,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = tid; i < 4 * TN; i += kThreads) bias_s[i / TN][i % TN] = a.bias[i / TN][i % TN];
     for (int i = tid; i <= TN; i += kThreads) w5_s[i] = i < TN ? 0.5f * a.w5[i] : a.w5[i];   // w5 / 2, then b5
     if (tid == 0) {
-        mbar_init(&bar_x, 1);
-        for (int h = 0; h < 2; ++h) {
-            mbar_init(&bar_w[h], 1);
-            mbar_init(&bar_mma[h], 1);
-            mbar_init(&bar_epi[h], kEpiWarps);   // one arrival per epilogue warp
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar_x[i], 1);
+            mbar_init(&bar_w[i], 1);
+            mbar_init(&bar_mma[i], 1);
+            mbar_init(&bar_dfree[i], kEpiWarps);   // one arrival per epilogue warp
+            mbar_init(&bar_act[i], kEpiWarps);
         }
         fence_barrier_init();
     }
@@ -202,17 +221,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = tmem_slot;
-    // tiles of this CTA; layer g = 4 it + l - 1 over them (every barrier below
-    // completes once per layer, so phase parities follow g)
-    const int n_my = (int)blockIdx.x < a.n_tiles ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    // pairs of tiles: this CTA takes pairs blockIdx.x + p gridDim.x, pair P holding
+    // tiles 2P and 2P + 1; step g = 4 p + l - 1 (every barrier below completes a
+    // fixed number of times per step, so phase parities follow g)
+    const int n_pairs = (a.n_tiles + 1) / 2;
+    const int n_my = (int)blockIdx.x < n_pairs ? (n_pairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     bool failed = false;
 
     if (warp == kEpiWarps) {
         if (lane == 0) {
             const CUtensorMap* maps[4] = {&mapW1, &mapW2, &mapW3, &mapW4};
-            // in flight: copies on bar_x / bar_w[h], products on bar_mma[h] (with the parity they complete)
-            bool pend_x = false, pend_w[2] = {false, false}, pend_m[2] = {false, false};
-            uint32_t par_x = 0, par_w[2] = {0, 0}, par_m[2] = {0, 0};
+            // in flight: copies on bar_x / bar_w, products on bar_mma (with the parity they complete)
+            bool pend_x[2] = {false, false}, pend_w[2] = {false, false}, pend_m[2] = {false, false};
+            uint32_t par_x[2] = {0, 0}, par_w[2] = {0, 0}, par_m[2] = {0, 0};
             auto wait = [&](uint64_t* bar, uint32_t parity) {
                 if (failed) return;
                 if (!mbar_wait_bounded(bar, parity, kPoll)) {
@@ -223,152 +244,204 @@ __global__ void __launch_bounds__(kThreads, 1)
             auto load_w = [&](int h, int layer, uint32_t parity) {   // half h of W_layer
                 const int ns = layer == 1 ? 1 : 4;
                 mbar_arrive_expect_tx(&bar_w[h], ns * WH_SLAB);
-                for (int s = 0; s < ns; ++s)
-                    tma_load_2d(Wbuf + s * W_SLAB + h * WH_SLAB, maps[layer - 1], s * SLAB_K, h * NH, &bar_w[h]);
+                for (int k = 0; k < ns; ++k)
+                    tma_load_2d(Wbuf + k * W_SLAB + h * WH_SLAB, maps[layer - 1], k * SLAB_K, h * NH, &bar_w[h]);
                 pend_w[h] = true;
                 par_w[h] = parity;
             };
-            auto load_x = [&](int tile, uint32_t parity) {
-                mbar_arrive_expect_tx(&bar_x, X_BYTES);
-                tma_load_2d(Xbuf, &mapX, 0, tile * TM, &bar_x);
-                pend_x = true;
-                par_x = parity;
+            auto load_x = [&](int p, uint32_t parity) {   // both slots' features of this CTA's pair p
+                const int pair = (int)blockIdx.x + p * (int)gridDim.x;
+                for (int sl = 0; sl < 2; ++sl) {
+                    mbar_arrive_expect_tx(&bar_x[sl], X_BYTES);
+                    tma_load_2d(Xbuf + sl * X_BYTES, &mapX, 0, (2 * pair + sl) * TM, &bar_x[sl]);
+                    pend_x[sl] = true;
+                    par_x[sl] = parity;
+                }
+            };
+            // the refill deferred from the previous half step: W half rh for
+            // step rg + 1 (or the next pair's layer 1), once slot 1's products
+            // of (rg, rh) are done (slot 0's were committed before them)
+            int rg = -1, rh = 0;
+            auto refill = [&]() {
+                if (rg < 0 || failed) return;
+                wait(&bar_mma[1], (uint32_t)rh);
+                if (failed) return;
+                const int l = rg % 4 + 1, p = rg / 4;
+                if (l < 4) load_w(rh, l + 1, (uint32_t)((rg + 1) & 1));
+                else if (p + 1 < n_my) load_w(rh, 1, (uint32_t)((rg + 1) & 1));
+                if (l == 1 && rh == 1 && p + 1 < n_my) load_x(p + 1, (uint32_t)((p + 1) & 1));
+                rg = -1;
             };
             if (n_my > 0) {
-                load_x(blockIdx.x, 0);
+                load_x(0, 0);
                 load_w(0, 1, 0);
                 load_w(1, 1, 0);
             }
-            for (int it = 0; it < n_my && !failed; ++it) {
-                const bool more = it + 1 < n_my;
+            for (int p = 0; p < n_my && !failed; ++p) {
                 for (int l = 1; l <= 4 && !failed; ++l) {
-                    const int g = it * 4 + l - 1;
-                    const uint32_t ph = g & 1, php = (g - 1) & 1;
-                    if (l == 1) {
-                        wait(&bar_x, it & 1);
-                        pend_x = false;
-                    }
+                    const int g = p * 4 + l - 1;
                     for (int h = 0; h < 2 && !failed; ++h) {
-                        wait(&bar_w[h], ph);
+                        wait(&bar_w[h], (uint32_t)(g & 1));
+                        if (failed) break;
                         pend_w[h] = false;
-                        if (g > 0) wait(&bar_epi[h], php);   // D_h read out; A half h of this layer written
-                        if (failed) break;
-                        fence_after();
-                        const uint32_t d = tmem + h * NH;
-                        const unsigned char* wh = Wbuf + h * WH_SLAB;
-                        if (l == 1) {
-                            for (int kk = 0; kk < 4; ++kk)   // 4 x k16 per 64-wide slab: +32 bytes each
-                                mma_ss(d, sw128_desc(Xbuf + kk * 32), sw128_desc(wh + kk * 32), kk != 0);
-                        } else {
-                            const uint32_t acol = tmem + acol_of((l - 2) & 1);
-                            // A column 8 j holds K = 16 j .. 16 j + 15
-                            const int jsplit = h == 0 ? 8 : 0;
-                            for (int j = 0; j < jsplit; ++j)
-                                mma_ts(d, acol + 8 * j, sw128_desc(wh + (j >> 2) * W_SLAB + (j & 3) * 32), j != 0);
+                        for (int sl = 0; sl < 2; ++sl) {
                             if (h == 0) {
-                                wait(&bar_epi[1], php);   // K 128..255 written by the epilogue of half 1
-                                if (failed) break;
-                                fence_after();
+                                // A_s(l-1) written and D_s free
+                                if (g > 0) wait(&bar_act[sl], (uint32_t)((g - 1) & 1));
+                                if (l == 1) {
+                                    wait(&bar_x[sl], (uint32_t)(p & 1));
+                                    pend_x[sl] = false;
+                                }
+                            } else {
+                                wait(&bar_dfree[sl], (uint32_t)(g & 1));   // the epilogue (s, l, 0) has read D_s
                             }
-                            for (int j = jsplit; j < 16; ++j)
-                                mma_ts(d, acol + 8 * j, sw128_desc(wh + (j >> 2) * W_SLAB + (j & 3) * 32), j != 0);
+                            if (failed) break;
+                            fence_after();
+                            const uint32_t d = tmem + dcol_of(sl);
+                            const unsigned char* wh = Wbuf + h * WH_SLAB;
+                            if (l == 1) {
+                                const unsigned char* xs = Xbuf + sl * X_BYTES;
+                                for (int kk = 0; kk < 4; ++kk)   // 4 x k16 per 64-wide slab: +32 bytes each
+                                    mma_ss(d, sw128_desc(xs + kk * 32), sw128_desc(wh + kk * 32), kk != 0);
+                            } else {
+                                const uint32_t ac = tmem + acol_of(sl);   // A column 8 j holds K = 16 j .. 16 j + 15
+                                for (int j = 0; j < 16; ++j)
+                                    mma_ts(d, ac + 8 * j, sw128_desc(wh + (j >> 2) * W_SLAB + (j & 3) * 32), j != 0);
+                            }
+                            mma_commit(&bar_mma[sl]);
+                            pend_m[sl] = true;
+                            par_m[sl] = (uint32_t)h;
+                            // with the first product of this half queued, take the
+                            // deferred refill of the previous half
+                            if (sl == 0) refill();
                         }
-                        mma_commit(&bar_mma[h]);
-                        pend_m[h] = true;
-                        par_m[h] = ph;
-                    }
-                    // refill each half once its products are done: the next layer's
-                    // weights (the next tile's W_1 after the last layer), and after
-                    // the first layer the next tile's features
-                    for (int h = 0; h < 2 && !failed; ++h) {
-                        wait(&bar_mma[h], ph);
-                        if (failed) break;
-                        pend_m[h] = false;
-                        if (l < 4) load_w(h, l + 1, (g + 1) & 1);
-                        else if (more) load_w(h, 1, (g + 1) & 1);
-                        if (h == 1 && l == 1 && more) load_x(blockIdx.x + (it + 1) * gridDim.x, (it + 1) & 1);
+                        rg = g;
+                        rh = h;
                     }
                 }
             }
+            refill();
             if (failed) {   // let the copies and products in flight land before the memory is released
-                if (pend_x) mbar_wait_bounded(&bar_x, par_x, kPoll);
-                for (int h = 0; h < 2; ++h) {
-                    if (pend_w[h]) mbar_wait_bounded(&bar_w[h], par_w[h], kPoll);
-                    if (pend_m[h]) mbar_wait_bounded(&bar_mma[h], par_m[h], kPoll);
+                for (int i = 0; i < 2; ++i) {
+                    if (pend_x[i]) mbar_wait_bounded(&bar_x[i], par_x[i], kPoll);
+                    if (pend_w[i]) mbar_wait_bounded(&bar_w[i], par_w[i], kPoll);
+                    if (pend_m[i]) mbar_wait_bounded(&bar_mma[i], par_m[i], kPoll);
                 }
             }
         }
         __syncwarp();
     } else {
-        // epilogue: row = 32 (warp % 4) + lane, columns 32 (warp / 4) .. +31 of each half
+        // epilogue: row = 32 (warp % 4) + lane; columns 32 (warp / 4) .. +31 of
+        // each half, in two sub-chunks of 16
         const int quarter = warp & 3, cgrp = warp >> 2, row = quarter * 32 + lane;
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         const f32x2 cK = x2_pack(kGeluCK, kGeluCK), cC = x2_pack(kGeluC, kGeluC);
-        for (int it = 0; it < n_my; ++it) {
-            const int tile = blockIdx.x + it * gridDim.x;
-            f32x2 ysum = 0ull;   // the head's dot product: even and odd columns in the two halves
+        for (int p = 0; p < n_my; ++p) {
+            const int pair = (int)blockIdx.x + p * (int)gridDim.x;
+            f32x2 ysum[2] = {0ull, 0ull};   // the head's dot products: even and odd columns
+            uint32_t hold[2][16];           // the BF16 pairs of half 0 of each slot, until half 1 is done
             for (int l = 1; l <= 4; ++l) {
-                const int g = it * 4 + l - 1;
+                const int g = p * 4 + l - 1;
+#pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    // a timeout is recorded and the later waits skipped, so that every
-                    // warp still reaches the block-wide barriers below
-                    bool ok = true;
-                    if (lane == 0 && !failed) ok = mbar_wait_bounded(&bar_mma[h], g & 1, kPoll);
-                    ok = __shfl_sync(0xffffffffu, ok, 0);
-                    if (!ok && !failed) {
-                        failed = true;
-                        if (lane == 0) atomicExch(a.status, DEV_TIMEOUT);
-                    }
-                    fence_after();
-                    const int c0 = h * NH + cgrp * 32;
-                    float v[32];
-                    tmem_ld32(tmem + lane_base + c0, v);
-                    const float4* b4 = reinterpret_cast<const float4*>(&bias_s[l - 1][c0]);
-                    const size_t trow = (size_t)tile * TM + row;   // the row in the traced outputs
-                    if constexpr (TRACE) {
-                        float* tz = a.trace_z + (((size_t)(l - 1) * a.n_tiles * TM + trow) * TN + c0);
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const float4 b = b4[i];
-                            tz[4 * i] = v[4 * i] + b.x;
-                            tz[4 * i + 1] = v[4 * i + 1] + b.y;
-                            tz[4 * i + 2] = v[4 * i + 2] + b.z;
-                            tz[4 * i + 3] = v[4 * i + 3] + b.w;
+                    for (int sl = 0; sl < 2; ++sl) {
+                        const int tile = 2 * pair + sl;
+                        // a timeout is recorded and the later waits skipped, so that
+                        // every warp still reaches the block-wide barriers below
+                        bool ok = true;
+                        if (lane == 0 && !failed) ok = mbar_wait_bounded(&bar_mma[sl], (uint32_t)h, kPoll);
+                        ok = __shfl_sync(0xffffffffu, ok, 0);
+                        if (!ok && !failed) {
+                            failed = true;
+                            if (lane == 0) atomicExch(a.status, DEV_TIMEOUT);
                         }
-                    }
+                        fence_after();
+                        const size_t trow = (size_t)tile * TM + row;   // the row in the traced outputs
+                        const bool traced = TRACE && tile < a.n_tiles;
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float4 b = b4[i];
-                        bias_gelu2_x2(v[4 * i], v[4 * i + 1], b.x, b.y, cK, cC);
-                        bias_gelu2_x2(v[4 * i + 2], v[4 * i + 3], b.z, b.w, cK, cC);
-                    }
-                    if (l < 4) {
-                        uint32_t r[16];
+                        for (int c = 0; c < 2; ++c) {
+                            const int col = h * NH + cgrp * 32 + c * 16;   // column of the layer
+                            uint32_t r[16];
+                            tmem_ld16_async(tmem + lane_base + dcol_of(sl) + cgrp * 32 + c * 16, r);
+                            tmem_wait_ld(r);
+                            float v[16];
 #pragma unroll
-                        for (int m = 0; m < 16; ++m) r[m] = pack_bf16x2(v[2 * m], v[2 * m + 1]);
-                        tmem_st16(tmem + lane_base + acol_of((l - 1) & 1) + c0 / 2, r);
-                        if constexpr (TRACE) {
-                            uint32_t* ta = a.trace_a + (((size_t)(l - 1) * a.n_tiles * TM + trow) * TN + c0) / 2;
+                            for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+                            const float4* b4 = reinterpret_cast<const float4*>(&bias_s[l - 1][col]);
+                            if constexpr (TRACE) {
+                                if (traced) {
+                                    float* tz = a.trace_z + (((size_t)(l - 1) * a.n_tiles * TM + trow) * TN + col);
 #pragma unroll
-                            for (int m = 0; m < 16; ++m) ta[m] = r[m];
+                                    for (int i = 0; i < 4; ++i) {
+                                        const float4 b = b4[i];
+                                        tz[4 * i] = v[4 * i] + b.x;
+                                        tz[4 * i + 1] = v[4 * i + 1] + b.y;
+                                        tz[4 * i + 2] = v[4 * i + 2] + b.z;
+                                        tz[4 * i + 3] = v[4 * i + 3] + b.w;
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const float4 b = b4[i];
+                                bias_gelu2_x2(v[4 * i], v[4 * i + 1], b.x, b.y, cK, cC);
+                                bias_gelu2_x2(v[4 * i + 2], v[4 * i + 3], b.z, b.w, cK, cC);
+                            }
+                            if (l < 4) {
+                                uint32_t q[8];
+#pragma unroll
+                                for (int m = 0; m < 8; ++m) q[m] = pack_bf16x2(v[2 * m], v[2 * m + 1]);
+                                if (h == 0) {
+#pragma unroll
+                                    for (int m = 0; m < 8; ++m) hold[sl][c * 8 + m] = q[m];
+                                } else {
+                                    // both halves of A_s(l) for these 16 + 16 columns
+                                    const uint32_t ac = tmem + lane_base + acol_of(sl);
+                                    uint32_t q0[8];
+#pragma unroll
+                                    for (int m = 0; m < 8; ++m) q0[m] = hold[sl][c * 8 + m];
+                                    tmem_st8<false>(ac + (cgrp * 32 + c * 16) / 2, q0);
+                                    tmem_st8<false>(ac + (NH + cgrp * 32 + c * 16) / 2, q);
+                                    if constexpr (TRACE) {
+                                        if (traced) {
+                                            uint32_t* ta = a.trace_a + ((size_t)(l - 1) * a.n_tiles * TM + trow) * TN / 2;
+#pragma unroll
+                                            for (int m = 0; m < 8; ++m) {
+                                                ta[(cgrp * 32 + c * 16) / 2 + m] = q0[m];
+                                                ta[(NH + cgrp * 32 + c * 16) / 2 + m] = q[m];
+                                            }
+                                        }
+                                    }
+                                }
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 16; i += 2)
+                                    ysum[sl] = x2_fma(x2_pack(v[i], v[i + 1]),
+                                                      x2_pack(w5_s[col + i], w5_s[col + i + 1]), ysum[sl]);
+                            }
                         }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 32; i += 2)
-                            ysum = x2_fma(x2_pack(v[i], v[i + 1]), x2_pack(w5_s[c0 + i], w5_s[c0 + i + 1]), ysum);
+                        if (h == 1 && l < 4) tmem_wait_st();
+                        fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(h == 0 ? &bar_dfree[sl] : &bar_act[sl]);
                     }
-                    fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&bar_epi[h]);
                 }
             }
-            float y_even, y_odd;
-            x2_unpack(ysum, y_even, y_odd);
-            head_part[cgrp][row] = y_even + y_odd;
+#pragma unroll
+            for (int sl = 0; sl < 2; ++sl) {
+                float y_even, y_odd;
+                x2_unpack(ysum[sl], y_even, y_odd);
+                head_part[sl][cgrp][row] = y_even + y_odd;
+            }
             asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
-            if (cgrp == 0)
-                a.y[tile * TM + row] =
-                    ((head_part[0][row] + head_part[1][row]) + (head_part[2][row] + head_part[3][row])) + w5_s[TN];
+            if (cgrp < 2) {   // column groups 0 and 1 finish slots 0 and 1
+                const int sl = cgrp, tile = 2 * pair + sl;
+                if (tile < a.n_tiles)
+                    a.y[(size_t)tile * TM + row] = ((head_part[sl][0][row] + head_part[sl][1][row]) +
+                                                    (head_part[sl][2][row] + head_part[sl][3][row])) +
+                                                   w5_s[TN];
+            }
             asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
         }
     }
@@ -458,11 +531,11 @@ cudaError_t Mlp::forward_tc(const __nv_bfloat16* Xin, int n, float* yout, int sm
     a.status = status;
     a.trace_z = trace_z;
     a.trace_a = static_cast<uint32_t*>(trace_a);
-    const size_t smem = X_BYTES + W_BYTES + 1024;
+    const size_t smem = 2 * X_BYTES + W_BYTES + 1024;
     auto kern = trace_z || trace_a ? mlp_fwd_tc_kernel<true> : mlp_fwd_tc_kernel<false>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    const int grid = std::min(a.n_tiles, sm_count);
+    const int grid = std::min((a.n_tiles + 1) / 2, sm_count);
     kern<<<grid, kThreads, smem, st>>>(mx, mw[0], mw[1], mw[2], mw[3], a);
     return cudaGetLastError();
 }
