@@ -108,7 +108,7 @@ def issued_flops(pol, form, n_scen, horizon=0, variant_name=""):
     if form == "f32defl":   # the JL expected cash flow, amortised over the lane's M scenarios
         m = re.search(r"xM(\d+)", variant_name)
         per[1] += 5.0 / (int(m.group(1)) if m else 4)
-        if variant_name.endswith(" x2"):   # TwoSum fold: one operation more per span
+        if " x2" in variant_name:   # TwoSum fold: one operation more per span
             per = {p: f + 1.0 / 16 for p, f in per.items()}
     return float(sum(per[p] * cs[p] for p in cs) * n_scen)
 
