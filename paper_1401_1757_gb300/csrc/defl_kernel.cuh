@@ -169,6 +169,12 @@ struct DeflLane {
             L[m] = l[i][m];
         }
     }
+    __device__ __forceinline__ void clear_acc() {   // a span that opens mid-way starts from zero
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+#pragma unroll
+            for (int m = 0; m < M; ++m) a0[i][m] = a1[i][m] = 0.0f;
+    }
 };
 
 // The same state in packed pairs (M even): acc = {a0, a1} of each chain,
@@ -192,6 +198,12 @@ struct DeflLaneX2 {
             x2_unpack(h[i][k], H[2 * k], H[2 * k + 1]);
             x2_unpack(l[i][k], L[2 * k], L[2 * k + 1]);
         }
+    }
+    __device__ __forceinline__ void clear_acc() {   // a span that opens mid-way starts from zero
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+#pragma unroll
+            for (int m = 0; m < M; ++m) acc[i][m] = 0ull;
     }
 };
 

@@ -458,8 +458,27 @@ __global__ void inner_paths_defl_kernel(VasStep s, uint64_t seed, int o0, int B,
 // alternate steps, folded into a double-float every 16 steps); per tile the
 // scaled sums are added into each path's double-float liability, and the
 // CTA adds its warps' liabilities in a fixed order in FP64.
+// One whole 16-step span from the node, groups g0 .. g0 - 3 (g0 = 3 mod 4),
+// the inner paths' deflator rows read from the plane (row stride i_pad).
+template <int KIND, int P, int M, bool CHECK, class Lane>
+__device__ __forceinline__ void nest_span(Lane& st, const DeflPol<P>& pp, const float4* __restrict__ tab,
+                                          const float4* __restrict__ plane, int i_pad, int g0) {
+    const float4* row = plane + (size_t)g0 * i_pad;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        float4 d[M];
+#pragma unroll
+        for (int q = 0; q < M; ++q) d[q] = row[q * 32];
+        row -= i_pad;
+        if (u == 0) defl_group<KIND, P, M, true>(st, pp, tab, d, g0 - u, CHECK);
+        else defl_group<KIND, P, M, false>(st, pp, tab, d, g0 - u, CHECK);
+    }
+    defl_fold_all(st);
+}
+
 template <int P, int M, int NW>
 __global__ void __launch_bounds__(NW * 32, 2) nested_defl_kernel(const NestDeflArgs a) {
+    using Lane = DeflLaneX2<P, M>;   // packed pairs, as the valuation kernel
     constexpr int CH = 32 * M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint64_t bar;
@@ -490,114 +509,92 @@ __global__ void __launch_bounds__(NW * 32, 2) nested_defl_kernel(const NestDeflA
             if (rec[0].S < m) continue;   // the tile's longest policy ended before the node
             const int kind = a.tile_kind[tile];
             // the runs of the tile's policies from the node
-            int off1[P], off2[P], gz1[P], gz2[P], Sr[P];
-            float ix[P], iy[P];
+            DeflPol<P> pp;
             int smin = 1 << 30, smax = 0;
-            DeflLane<P, M> st;
+            Lane st;
+            float h0s[P][M];
 #pragma unroll
             for (int i = 0; i < P; ++i) {
                 const NestSlot r = rec[i];
                 int S = r.S - m;
                 const bool live = r.pol >= 0 && S >= 0 && !(r.unit && m > 0);
                 if (!live) S = 0;
-                Sr[i] = S;
+                pp.S[i] = S;
                 smin = min(smin, S);
                 smax = max(smax, S);
-                ix[i] = r.ix;
-                iy[i] = r.iy;
+                pp.ix[i] = r.ix;
+                pp.iy[i] = r.iy;
                 // life 1: aligned run at age + m, or a zero group; the unit group at node 0
                 const int a1 = r.age1 + m;
                 if (r.unit) {
-                    off1[i] = r.base1 + (a.dpad - 8) / 4;
-                    gz1[i] = 1;
+                    pp.off1[i] = r.base1 + (a.dpad - 8) / 4;
+                    pp.gz1[i] = 1;
                 } else if (a1 >= r.z1) {
-                    off1[i] = r.base1 + (r.z1 + 3) / 4;
-                    gz1[i] = 0;
+                    pp.off1[i] = r.base1 + (r.z1 + 3) / 4;
+                    pp.gz1[i] = 0;
                 } else {
-                    off1[i] = r.base1 + (a1 & 3) * dpad4 + (a1 >> 2);
-                    gz1[i] = (r.z1 - a1 + 3) / 4;
+                    pp.off1[i] = r.base1 + (a1 & 3) * dpad4 + (a1 >> 2);
+                    pp.gz1[i] = (r.z1 - a1 + 3) / 4;
                 }
                 const int a2 = r.age2 + m;
                 if (a2 >= r.z2) {
-                    off2[i] = r.base2 + (r.z2 + 3) / 4;
-                    gz2[i] = 0;
+                    pp.off2[i] = r.base2 + (r.z2 + 3) / 4;
+                    pp.gz2[i] = 0;
                 } else {
-                    off2[i] = r.base2 + (a2 & 3) * dpad4 + (a2 >> 2);
-                    gz2[i] = (r.z2 - a2 + 3) / 4;
+                    pp.off2[i] = r.base2 + (a2 & 3) * dpad4 + (a2 >> 2);
+                    pp.gz2[i] = (r.z2 - a2 + 3) / 4;
                 }
 #pragma unroll
                 for (int q = 0; q < M; ++q) {   // the boundary D(m, S) mat
-                    st.a0[i][q] = st.a1[i][q] = st.l[i][q] = 0.0f;
                     float h0 = 0.0f;
                     if (live && r.mat != 0.0f) {
                         float dS = 1.0f;
                         if (S > 0) dS = reinterpret_cast<const float*>(plane + (size_t)((S - 1) >> 2) * a.i_pad + q * 32)[(S - 1) & 3];
                         h0 = __fmul_rn(dS, r.mat);
                     }
-                    st.h[i][q] = h0;
+                    h0s[i][q] = h0;
                 }
             }
+#pragma unroll
+            for (int i = 0; i < P; ++i) st.start(i, h0s[i]);
+            st.clear_acc();
             if (smax > 0) {
+                // groups of four steps from the node, descending; 16-step spans
+                // aligned at the node (a span opens at g = 3 mod 4 and is folded at
+                // g = 0 mod 4; the top span may be partial and starts from zero)
                 const int g_top = (smax - 1) >> 2;
+                auto run = [&](auto kind_c) {
+                    constexpr int KIND = decltype(kind_c)::value;
+                    int g = g_top;
 #pragma unroll 1
-                for (int g = g_top; g >= 0; --g) {
-                    float4 d[M];
+                    for (; g >= 0 && (g & 3) != 3; --g) {   // the partial top span
+                        float4 d[M];
 #pragma unroll
-                    for (int q = 0; q < M; ++q) d[q] = plane[(size_t)g * a.i_pad + q * 32];
-                    const bool check = 4 * g + 3 >= smin;
-                    float4 e[P];
-#pragma unroll
-                    for (int i = 0; i < P; ++i) {
-                        const int t0 = 4 * g, S = Sr[i];
-                        if (t0 >= S) {
-                            e[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                            continue;
-                        }
-                        const float4 x = tab[off1[i] + min(g, gz1[i])];
-                        if (kind == K_ANN || kind == K_ASS) {
-                            e[i] = x;
-                        } else {
-                            const float4 y = tab[off2[i] + min(g, gz2[i])];
-                            const float fx[4] = {x.x, x.y, x.z, x.w}, fy[4] = {y.x, y.y, y.z, y.w};
-                            float fe[4];
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) {
-                                const float px = __fmul_rn(fx[c], ix[i]), py = __fmul_rn(fy[c], iy[i]);
-                                fe[c] = kind == K_JL ? __fmaf_rn(px, __fsub_rn(1.0f, py), py) : __fmul_rn(px, py);
-                            }
-                            e[i] = make_float4(fe[0], fe[1], fe[2], fe[3]);
-                        }
-                        if (check && t0 + 3 >= S) {
-                            if (t0 + 1 >= S) e[i].y = 0.0f;
-                            if (t0 + 2 >= S) e[i].z = 0.0f;
-                            if (t0 + 3 >= S) e[i].w = 0.0f;
-                        }
+                        for (int q = 0; q < M; ++q) d[q] = plane[(size_t)g * a.i_pad + q * 32];
+                        defl_group<KIND, P, M, false>(st, pp, tab, d, g, true);
+                        if ((g & 3) == 0) defl_fold_all(st);
                     }
-                    const bool first = (g & 3) == 3;   // the first group of a 16-step span
-#pragma unroll
-                    for (int i = 0; i < P; ++i)
-#pragma unroll
-                        for (int q = 0; q < M; ++q) {
-                            st.a1[i][q] = first ? __fmul_rn(d[q].w, e[i].w) : __fmaf_rn(d[q].w, e[i].w, st.a1[i][q]);
-                            st.a0[i][q] = first ? __fmul_rn(d[q].z, e[i].z) : __fmaf_rn(d[q].z, e[i].z, st.a0[i][q]);
-                        }
-#pragma unroll
-                    for (int i = 0; i < P; ++i)
-#pragma unroll
-                        for (int q = 0; q < M; ++q) {
-                            st.a1[i][q] = __fmaf_rn(d[q].y, e[i].y, st.a1[i][q]);
-                            st.a0[i][q] = __fmaf_rn(d[q].x, e[i].x, st.a0[i][q]);
-                        }
-                    if ((g & 3) == 0) defl_fold_all(st);   // 16-step spans aligned at the node
-                }
+                    // whole spans g .. g - 3; only those reaching a policy's end check
+#pragma unroll 1
+                    for (; g >= 3; g -= 4) {
+                        if (4 * g + 3 >= smin) nest_span<KIND, P, M, true>(st, pp, tab, plane, a.i_pad, g);
+                        else nest_span<KIND, P, M, false>(st, pp, tab, plane, a.i_pad, g);
+                    }
+                };
+                if (kind == K_ANN) run(std::integral_constant<int, K_ANN>{});
+                else if (kind == K_ASS) run(std::integral_constant<int, K_ASS>{});
+                else if (kind == K_JL) run(std::integral_constant<int, K_JL>{});
+                else run(std::integral_constant<int, K_ANN2>{});
             }
             // this tile's scaled sums into the paths' liabilities
 #pragma unroll
             for (int i = 0; i < P; ++i) {
                 const float sh = rec[i].sc_h, sl = rec[i].sc_l;
+                float Hs[M], Ls[M];
+                st.sum(i, Hs, Ls);
 #pragma unroll
                 for (int q = 0; q < M; ++q) {
-                    const float H = st.h[i][q], L = st.l[i][q];
+                    const float H = Hs[q], L = Ls[q];
                     const float p = __fmul_rn(H, sh);
                     float e = __fmaf_rn(H, sh, -p);
                     e = __fmaf_rn(H, sl, e);
