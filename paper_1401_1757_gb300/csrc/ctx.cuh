@@ -243,6 +243,10 @@ struct rsv_ctx {
     bool nest_bm_ready = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaStream_t copy_stream = nullptr;   // device-to-host copies of V0 column blocks
+    // the deflated brute force's two pipelines: valuation (high priority) and the
+    // FP64 inner-path generator (low priority), with their ordering events
+    cudaStream_t nest_val = nullptr, nest_gen = nullptr;
+    cudaEvent_t nest_ev[5] = {};   // start, generated[2], valued[2]
     cudaEvent_t ev_block = nullptr;
     bool ev_recorded = false;
     int tuned[4] = {-1, -1, -1, -1};

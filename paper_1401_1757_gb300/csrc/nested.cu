@@ -626,13 +626,13 @@ __global__ void __launch_bounds__(NW * 32, 2) nested_defl_kernel(const NestDeflA
 // ------------------------------------------------------------- launchers ----
 cudaError_t launch_inner_paths_defl(const VasStep& s, uint64_t seed, int o0, int B, int n_nodes, int n_inner,
                                     int i_pad, int G4, const int* Ln, const double* r_node, const double2* bm,
-                                    float4* plane, int sm_count, cudaStream_t st) {
-    inner_paths_defl_kernel<<<sm_count * 8, 128, 0, st>>>(s, seed, o0, B, n_nodes, n_inner, i_pad, G4, Ln, r_node, bm,
+                                    float4* plane, int sm_count, int ctas_per_sm, cudaStream_t st) {
+    inner_paths_defl_kernel<<<sm_count * ctas_per_sm, 128, 0, st>>>(s, seed, o0, B, n_nodes, n_inner, i_pad, G4, Ln, r_node, bm,
                                                           reinterpret_cast<float*>(plane));
     return cudaGetLastError();
 }
 
-cudaError_t launch_nested_defl(const NestDeflArgs& a, int sm_count, cudaStream_t st) {
+cudaError_t launch_nested_defl(const NestDeflArgs& a, int sm_count, int max_per_sm, cudaStream_t st) {
     constexpr int P = kNestDeflP, M = 2, NW = 8;
     auto k = nested_defl_kernel<P, M, NW>;
     const size_t smem = (size_t)a.tab_bytes;
@@ -642,7 +642,7 @@ cudaError_t launch_nested_defl(const NestDeflArgs& a, int sm_count, cudaStream_t
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, NW * 32, smem);
     if (e != cudaSuccess) return e;
     if (bps < 1) return cudaErrorInvalidConfiguration;
-    const long long grid = std::min<long long>((long long)sm_count * bps, std::max(1, a.n_items));
+    const long long grid = std::min<long long>((long long)sm_count * std::min(bps, max_per_sm), std::max(1, a.n_items));
     k<<<(int)grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }

@@ -79,10 +79,13 @@ struct NestDeflArgs {
     double* L_all;
 };
 constexpr int kNestDeflP = 4;   // policies per tile of the deflated nested kernel
+// The generator runs ctas_per_sm CTAs of 128 threads per SM (grid-stride);
+// the valuation kernel at most max_per_sm CTAs per SM, so that both fit on
+// every SM when they run concurrently on two streams.
 cudaError_t launch_inner_paths_defl(const VasStep& s, uint64_t seed, int o0, int B, int n_nodes, int n_inner,
                                     int i_pad, int G4, const int* Ln, const double* r_node, const double2* bm,
-                                    float4* plane, int sm_count, cudaStream_t st);
-cudaError_t launch_nested_defl(const NestDeflArgs& a, int sm_count, cudaStream_t st);
+                                    float4* plane, int sm_count, int ctas_per_sm, cudaStream_t st);
+cudaError_t launch_nested_defl(const NestDeflArgs& a, int sm_count, int max_per_sm, cudaStream_t st);
 cudaError_t launch_node_stats(const double* L_all, int n_on, int n_inner, int k, double* mean, double* kth,
                               cudaStream_t st);
 

@@ -874,6 +874,10 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
     const size_t esz = form == F_F32 ? sizeof(float) : 8;
     const size_t per_outer = defl ? (size_t)NN * G4 * i_pad * sizeof(float4) : (size_t)NN * Lmax * i_pad * esz;
     int B = sp->batch_outer > 0 ? sp->batch_outer : (int)std::max<size_t>(1, (size_t(4) << 30) / per_outer);
+    // the deflated brute force pipelines the generator of batch i + 1 with the
+    // valuation of batch i: two plane buffers, and at least eight batches so
+    // that the first and last stages are short
+    if (defl && sp->batch_outer <= 0) B = std::max(1, std::min(B / 2, (NO + 7) / 8));
     B = std::min(B, NO);
 
     CU(c->d_nest_w.ensure(w.size() * sizeof(double)));
@@ -884,7 +888,7 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
     const int o_pad = (NO + 31) / 32 * 32;   // the curve mode: outer paths on the lanes
     const size_t curve_plane = (size_t)NN * Lmax * o_pad * esz;
     if (curve) CU(c->d_nest_plane.ensure(curve_plane + (size_t)NN * NO * sizeof(double)));
-    else if (!sur) CU(c->d_nest_plane.ensure((size_t)B * per_outer));
+    else if (!sur) CU(c->d_nest_plane.ensure((size_t)(defl ? 2 : 1) * B * per_outer));
     CU(c->d_nest_mean.ensure((size_t)NO * NN * sizeof(double)));
     CU(c->d_nest_kth.ensure((size_t)NO * NN * sizeof(double)));
     double* Lall = (o->on_device && out->L_all) ? out->L_all : nullptr;
@@ -1095,26 +1099,56 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
         da.status = c->d_ctl.as<int32_t>() + 1;
         da.L_all = Lall;
     }
-    for (int o0 = 0; o0 < NO && !sur && !curve; o0 += B) {
-        const int Bc = std::min(B, NO - o0);
-        if (defl) {
+    if (defl && !sur && !curve) {
+        // generator (FP64 pipe) and valuation (FP32 pipes) of consecutive batches
+        // run concurrently: the generator of batch i + 1 on a low-priority stream
+        // into the other plane buffer, the valuation of batch i on a
+        // high-priority stream at one CTA per SM, so that both fit on every SM
+        if (!c->nest_val) {
+            int lo = 0, hi = 0;
+            CU(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            CU(cudaStreamCreateWithPriority(&c->nest_val, cudaStreamNonBlocking, hi));
+            CU(cudaStreamCreateWithPriority(&c->nest_gen, cudaStreamNonBlocking, lo));
+            for (cudaEvent_t& e : c->nest_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        cudaEvent_t ev_start = c->nest_ev[0], *ev_gen = c->nest_ev + 1, *ev_val = c->nest_ev + 3;
+        CU(cudaEventRecord(ev_start, c->stream));   // the outer paths, weights and queue word are ready
+        CU(cudaStreamWaitEvent(c->nest_gen, ev_start, 0));
+        CU(cudaStreamWaitEvent(c->nest_val, ev_start, 0));
+        const size_t buf4 = (size_t)B * per_outer / sizeof(float4);
+        int i = 0;
+        for (int o0 = 0; o0 < NO; o0 += B, ++i) {
+            const int Bc = std::min(B, NO - o0), bi = i & 1;
+            float4* plane = c->d_nest_plane.as<float4>() + bi * buf4;
+            if (i >= 2) CU(cudaStreamWaitEvent(c->nest_gen, ev_val[bi], 0));   // the buffer's last reader
             CU(launch_inner_paths_defl(vs, sp->seed, o0, Bc, NN, n_inner, i_pad, G4, c->d_nest_ln.as<int>(),
-                                       c->d_nest_rn.as<double>(), c->d_nest_bm.as<double2>(),
-                                       c->d_nest_plane.as<float4>(), c->sm_count, c->stream));
+                                       c->d_nest_rn.as<double>(), c->d_nest_bm.as<double2>(), plane, c->sm_count, 4,
+                                       c->nest_gen));
+            CU(cudaEventRecord(ev_gen[bi], c->nest_gen));
+            CU(cudaStreamWaitEvent(c->nest_val, ev_gen[bi], 0));
             const long long items = (long long)NN * Bc * da.n_chunks;
             if (items > 0x7fffffffLL) return fail(c, RSV_E_ARG, "too many nested work items");
+            da.D = plane;
             da.B = Bc;
             da.o0 = o0;
             da.n_items = (int32_t)items;
-            CU(cudaMemsetAsync(c->d_ctl.p, 0, sizeof(int32_t), c->stream));
+            CU(cudaMemsetAsync(c->d_ctl.p, 0, sizeof(int32_t), c->nest_val));
             if (L.n_tiles > 0) {
-                CU(launch_nested_defl(da, c->sm_count, c->stream));
+                CU(launch_nested_defl(da, c->sm_count, 1, c->nest_val));
             } else {
                 CU(cudaMemsetAsync(Lall + (size_t)o0 * NN * n_inner, 0, (size_t)Bc * NN * n_inner * sizeof(double),
-                                   c->stream));
+                                   c->nest_val));
             }
-            continue;
+            CU(cudaEventRecord(ev_val[bi], c->nest_val));
         }
+        // the call's stream continues once both pipelines are done
+        CU(cudaEventRecord(ev_gen[0], c->nest_gen));
+        CU(cudaStreamWaitEvent(c->stream, ev_gen[0], 0));
+        CU(cudaEventRecord(ev_val[0], c->nest_val));
+        CU(cudaStreamWaitEvent(c->stream, ev_val[0], 0));
+    }
+    for (int o0 = 0; o0 < NO && !sur && !curve && !defl; o0 += B) {
+        const int Bc = std::min(B, NO - o0);
         CU(launch_inner_paths(form, vs, sp->seed, o0, Bc, NN, n_inner, i_pad, Lmax, c->d_nest_ln.as<int>(),
                               c->d_nest_rn.as<double>(), c->d_nest_bm.as<double2>(), c->d_nest_plane.p, c->sm_count,
                               c->stream));
@@ -1193,6 +1227,10 @@ rsv_status rsv_destroy(rsv_ctx* c) try {
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     c->h_defl_stage.release();
+    for (cudaEvent_t& e : c->nest_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->nest_val) cudaStreamDestroy(c->nest_val);
+    if (c->nest_gen) cudaStreamDestroy(c->nest_gen);
     if (c->ev_block) cudaEventDestroy(c->ev_block);
     if (c->copy_stream) {
         cudaStreamSynchronize(c->copy_stream);
