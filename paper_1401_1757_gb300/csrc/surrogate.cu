@@ -1250,7 +1250,7 @@ rsv_status rsv_surrogate_train(rsv_ctx* c, const rsv_surrogate_cfg* cfg, rsv_sur
     cudaEventDestroy(e2);
     cudaEventDestroy(e3);
 
-    // statistics; fallback map calibrated on the first half, judged on the second
+    // statistics; fallback map calibrated on the first half, scored on the second
     std::vector<double> ae;
     ae.reserve(nv);
     for (long long i = 0; i < nv; ++i)
