@@ -98,6 +98,23 @@ def test_nested_deflated_unaligned_nodes_and_edges(ctx):
     assert np.array_equal(again["L_all"], out["L_all"])
 
 
+def test_nested_deflated_batching_gives_the_same_bits(ctx):
+    """The deflated brute force runs its generator and its valuation on two
+    streams, batch i + 1's inner paths being generated into the second plane
+    buffer while batch i is valued; the inner paths are counter-based, so the
+    liabilities must not depend on the batching: one outer path per batch
+    (nine batches, both buffers reused four times) against one batch."""
+    tab = synth.gm_monthly_survival()
+    pol = mixed_portfolio(60, seed=23)
+    spec = dict(n_outer=9, n_nodes=7, node_step_m=12, n_inner=200, seed=29)
+    one = nested(ctx, pol, tab, rsv.RSV_FORM_F32_DEFLATED, batch_outer=9, **spec)
+    many = nested(ctx, pol, tab, rsv.RSV_FORM_F32_DEFLATED, batch_outer=1, **spec)
+    default = nested(ctx, pol, tab, rsv.RSV_FORM_F32_DEFLATED, **spec)
+    assert np.array_equal(one["L_all"], many["L_all"])
+    assert np.array_equal(one["L_all"], default["L_all"])
+    assert np.array_equal(one["L_q995"], many["L_q995"])
+
+
 def test_node_statistics_fifth_largest(ctx):
     tab = synth.gm_monthly_survival()
     pol = synth.portfolio_single_life(50, seed=4)
