@@ -391,6 +391,11 @@ typedef struct {
     double r0;            /* short rate at month 0                                     */
     int32_t mode;         /* RSV_NESTED_MC or RSV_NESTED_CURVE                         */
     int32_t batch_outer;  /* outer paths per inner-path batch; 0 = fit 4 GiB           */
+    int32_t outer_first;  /* global index of the first outer path: the call values the
+                             paths outer_first .. outer_first + n_outer - 1, whose random
+                             streams are keyed by that index (below 2^24), so that the
+                             outer paths can be split across calls or GPUs with no
+                             exchange; the outputs are indexed from 0                    */
 } rsv_nested_spec;
 
 /* Outputs (caller-sized; host or device pointers per rsv_opts.on_device):

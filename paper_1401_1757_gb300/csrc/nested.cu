@@ -149,8 +149,8 @@ __device__ __forceinline__ double vasicek_path(const VasStep& s, uint64_t seed, 
 // multiplier, so a warp scan of the maps gives every lane the rate at the
 // start of its step, and a product scan the discount to its end.  The same
 // path as the serial recursion up to the order of rounding.
-__global__ void outer_paths_kernel(VasStep s, uint64_t seed, int n_outer, int n_nodes, int node_step, double r0,
-                                   double* __restrict__ r_node, double* __restrict__ d0) {
+__global__ void outer_paths_kernel(VasStep s, uint64_t seed, int o_first, int n_outer, int n_nodes, int node_step,
+                                   double r0, double* __restrict__ r_node, double* __restrict__ d0) {
     const int lane = threadIdx.x & 31;
     const int o = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     if (o >= n_outer) return;   // whole warps leave together
@@ -168,7 +168,7 @@ __global__ void outer_paths_kernel(VasStep s, uint64_t seed, int n_outer, int n_
         double z1 = 0.0, z2 = 0.0;
         if (live) {   // the serial generator's draw for step t
             uint32_t w[4];
-            philox4x32_10((uint32_t)(t >> 1), (uint32_t)o, 0u, 2u << 24, k0, k1, w);
+            philox4x32_10((uint32_t)(t >> 1), (uint32_t)(o_first + o), 0u, 2u << 24, k0, k1, w);
             const int h = t & 1;
             const double u1 = ((double)w[2 * h] + 0.5) * inv32;
             const double u2 = ((double)w[2 * h + 1] + 0.5) * inv32;
@@ -230,7 +230,7 @@ __device__ __forceinline__ float2 to_plane<float2>(double x) {
 // Inner paths of outer paths [o0, o0 + B), every node: one thread per path.
 // Plane layout [B][n_nodes][Lmax][i_pad]; node n fills rows 0 .. Ln[n]-1.
 template <class VE>
-__global__ void inner_paths_kernel(VasStep s, uint64_t seed, int o0, int B, int n_nodes, int n_inner, int i_pad,
+__global__ void inner_paths_kernel(VasStep s, uint64_t seed, int o_first, int o0, int B, int n_nodes, int n_inner, int i_pad,
                                    int Lmax, const int* __restrict__ Ln, const double* __restrict__ r_node,
                                    const double2* __restrict__ bm_g, VE* __restrict__ plane) {
     __shared__ double2 bm[BM_SC + BM_LG];   // 18 KiB: the Box-Muller tables
@@ -249,8 +249,9 @@ __global__ void inner_paths_kernel(VasStep s, uint64_t seed, int o0, int B, int 
             for (int t = 0; t < L; ++t) base[(size_t)t * i_pad] = to_plane<VE>(1.0);
             continue;
         }
-        vasicek_path(s, seed, (uint32_t)i, (uint32_t)n, (3u << 24) | (uint32_t)o, r_node[(size_t)o * n_nodes + n],
-                     L, bm, [&](int t, double v, double) { base[(size_t)t * i_pad] = to_plane<VE>(v); });
+        vasicek_path(s, seed, (uint32_t)i, (uint32_t)n, (3u << 24) | (uint32_t)(o_first + o),
+                     r_node[(size_t)o * n_nodes + n], L, bm,
+                     [&](int t, double v, double) { base[(size_t)t * i_pad] = to_plane<VE>(v); });
     }
 }
 
@@ -419,7 +420,7 @@ __global__ void node_stats_kernel(const double* __restrict__ L_all, int n_inner,
 // of the path's monthly discount factors from the node, rounded to FP32, in
 // rows of four steps [B][n_nodes][G4][i_pad]; zeros from the node's remaining
 // length to the end of its last group of four.  One thread per path.
-__global__ void inner_paths_defl_kernel(VasStep s, uint64_t seed, int o0, int B, int n_nodes, int n_inner, int i_pad,
+__global__ void inner_paths_defl_kernel(VasStep s, uint64_t seed, int o_first, int o0, int B, int n_nodes, int n_inner, int i_pad,
                                         int G4, const int* __restrict__ Ln, const double* __restrict__ r_node,
                                         const double2* __restrict__ bm_g, float* __restrict__ plane) {
     __shared__ double2 bm[BM_SC + BM_LG];   // 18 KiB: the Box-Muller tables
@@ -441,8 +442,8 @@ __global__ void inner_paths_defl_kernel(VasStep s, uint64_t seed, int o0, int B,
             continue;
         }
         double D = 1.0;
-        vasicek_path(s, seed, (uint32_t)i, (uint32_t)n, (3u << 24) | (uint32_t)o, r_node[(size_t)o * n_nodes + n], L,
-                     bm, [&](int t, double v, double) {
+        vasicek_path(s, seed, (uint32_t)i, (uint32_t)n, (3u << 24) | (uint32_t)(o_first + o),
+                     r_node[(size_t)o * n_nodes + n], L, bm, [&](int t, double v, double) {
                          D = __dmul_rn(D, v);
                          at(t) = __double2float_rn(D);
                      });
@@ -624,10 +625,10 @@ __global__ void __launch_bounds__(NW * 32, 2) nested_defl_kernel(const NestDeflA
 }
 
 // ------------------------------------------------------------- launchers ----
-cudaError_t launch_inner_paths_defl(const VasStep& s, uint64_t seed, int o0, int B, int n_nodes, int n_inner,
+cudaError_t launch_inner_paths_defl(const VasStep& s, uint64_t seed, int o_first, int o0, int B, int n_nodes, int n_inner,
                                     int i_pad, int G4, const int* Ln, const double* r_node, const double2* bm,
                                     float4* plane, int sm_count, int ctas_per_sm, cudaStream_t st) {
-    inner_paths_defl_kernel<<<sm_count * ctas_per_sm, 128, 0, st>>>(s, seed, o0, B, n_nodes, n_inner, i_pad, G4, Ln, r_node, bm,
+    inner_paths_defl_kernel<<<sm_count * ctas_per_sm, 128, 0, st>>>(s, seed, o_first, o0, B, n_nodes, n_inner, i_pad, G4, Ln, r_node, bm,
                                                           reinterpret_cast<float*>(plane));
     return cudaGetLastError();
 }
@@ -671,24 +672,24 @@ cudaError_t launch_nested(int form, const NestedArgs& a, int sm_count, size_t sm
     }
 }
 
-cudaError_t launch_outer_paths(const VasStep& s, uint64_t seed, int n_outer, int n_nodes, int node_step, double r0,
+cudaError_t launch_outer_paths(const VasStep& s, uint64_t seed, int o_first, int n_outer, int n_nodes, int node_step, double r0,
                                double* r_node, double* d0, cudaStream_t st) {
-    outer_paths_kernel<<<(n_outer + 3) / 4, 128, 0, st>>>(s, seed, n_outer, n_nodes, node_step, r0, r_node, d0);
+    outer_paths_kernel<<<(n_outer + 3) / 4, 128, 0, st>>>(s, seed, o_first, n_outer, n_nodes, node_step, r0, r_node, d0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_inner_paths(int form, const VasStep& s, uint64_t seed, int o0, int B, int n_nodes, int n_inner,
+cudaError_t launch_inner_paths(int form, const VasStep& s, uint64_t seed, int o_first, int o0, int B, int n_nodes, int n_inner,
                                int i_pad, int Lmax, const int* Ln, const double* r_node, const double2* bm,
                                void* plane, int sm_count, cudaStream_t st) {
     const int grid = sm_count * 8;
     if (form == F_F64)
-        inner_paths_kernel<double><<<grid, 128, 0, st>>>(s, seed, o0, B, n_nodes, n_inner, i_pad, Lmax, Ln, r_node,
+        inner_paths_kernel<double><<<grid, 128, 0, st>>>(s, seed, o_first, o0, B, n_nodes, n_inner, i_pad, Lmax, Ln, r_node,
                                                           bm, static_cast<double*>(plane));
     else if (form == F_F32)
-        inner_paths_kernel<float><<<grid, 128, 0, st>>>(s, seed, o0, B, n_nodes, n_inner, i_pad, Lmax, Ln, r_node,
+        inner_paths_kernel<float><<<grid, 128, 0, st>>>(s, seed, o_first, o0, B, n_nodes, n_inner, i_pad, Lmax, Ln, r_node,
                                                          bm, static_cast<float*>(plane));
     else
-        inner_paths_kernel<float2><<<grid, 128, 0, st>>>(s, seed, o0, B, n_nodes, n_inner, i_pad, Lmax, Ln, r_node,
+        inner_paths_kernel<float2><<<grid, 128, 0, st>>>(s, seed, o_first, o0, B, n_nodes, n_inner, i_pad, Lmax, Ln, r_node,
                                                           bm, static_cast<float2*>(plane));
     return cudaGetLastError();
 }

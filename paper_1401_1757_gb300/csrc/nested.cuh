@@ -28,7 +28,9 @@ struct VasStep {
 VasStep vasicek_step_constants(double a, double b, double sigma, double dt);
 int nested_tile_width(int form);
 cudaError_t launch_nested(int form, const NestedArgs& a, int sm_count, size_t smem, cudaStream_t st);
-cudaError_t launch_outer_paths(const VasStep& s, uint64_t seed, int n_outer, int n_nodes, int node_step, double r0,
+// o_first: the global index of the first outer path (the key of its random
+// streams); outputs and r_node are indexed from 0.
+cudaError_t launch_outer_paths(const VasStep& s, uint64_t seed, int o_first, int n_outer, int n_nodes, int node_step, double r0,
                                double* r_node, double* d0, cudaStream_t st);
 // Tables of the inner-path generator's Box-Muller step (FP64): (sin, cos) of
 // 2 pi j / BM_SC for j < BM_SC, then for the BM_LG intervals of the logarithm
@@ -36,7 +38,7 @@ cudaError_t launch_outer_paths(const VasStep& s, uint64_t seed, int n_outer, int
 constexpr int BM_SC = 1024, BM_LG = 128;
 constexpr int BM_LG_K0 = 53;   // first interval whose centre 1 + (j + 1/2)/128 exceeds sqrt 2
 const double2* bm_tables_host();   // BM_SC + BM_LG entries
-cudaError_t launch_inner_paths(int form, const VasStep& s, uint64_t seed, int o0, int B, int n_nodes, int n_inner,
+cudaError_t launch_inner_paths(int form, const VasStep& s, uint64_t seed, int o_first, int o0, int B, int n_nodes, int n_inner,
                                int i_pad, int Lmax, const int* Ln, const double* r_node, const double2* bm,
                                void* plane, int sm_count, cudaStream_t st);
 // The curve mode with the outer paths on the lanes (planes [n_nodes][Lmax][o_pad])
@@ -82,7 +84,7 @@ constexpr int kNestDeflP = 4;   // policies per tile of the deflated nested kern
 // The generator runs ctas_per_sm CTAs of 128 threads per SM (grid-stride);
 // the valuation kernel at most max_per_sm CTAs per SM, so that both fit on
 // every SM when they run concurrently on two streams.
-cudaError_t launch_inner_paths_defl(const VasStep& s, uint64_t seed, int o0, int B, int n_nodes, int n_inner,
+cudaError_t launch_inner_paths_defl(const VasStep& s, uint64_t seed, int o_first, int o0, int B, int n_nodes, int n_inner,
                                     int i_pad, int G4, const int* Ln, const double* r_node, const double2* bm,
                                     float4* plane, int sm_count, int ctas_per_sm, cudaStream_t st);
 cudaError_t launch_nested_defl(const NestDeflArgs& a, int sm_count, int max_per_sm, cudaStream_t st);

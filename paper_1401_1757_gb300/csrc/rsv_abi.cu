@@ -805,6 +805,9 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
     if (!(sp->a > 0.0) || !(sp->sigma >= 0.0) || !std::isfinite(sp->a) || !std::isfinite(sp->b) ||
         !std::isfinite(sp->sigma) || !std::isfinite(sp->r0) || sp->batch_outer < 0)
         return fail(c, RSV_E_ARG, "bad Vasicek parameters");
+    // the outer index keys 24 bits of the random streams' counters
+    if (sp->outer_first < 0 || (long long)sp->outer_first + sp->n_outer > (1LL << 24))
+        return fail(c, RSV_E_ARG, "outer paths outer_first .. outer_first + n_outer - 1 must lie in [0, 2^24)");
     if (!out->L_mean || !out->L_q995) return fail(c, RSV_E_ARG, "L_mean and L_q995 are required");
     bool any_tab = false;
     for (auto& t : c->tab) any_tab |= !t.empty();
@@ -903,7 +906,7 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
 
     const VasStep vs = vasicek_step_constants(sp->a, sp->b, sp->sigma, 1.0 / 12.0);
     CU(cudaEventRecord(c->ev0, c->stream));
-    CU(launch_outer_paths(vs, sp->seed, NO, NN, step, sp->r0, c->d_nest_rn.as<double>(), c->d_nest_d0.as<double>(),
+    CU(launch_outer_paths(vs, sp->seed, sp->outer_first, NO, NN, step, sp->r0, c->d_nest_rn.as<double>(), c->d_nest_d0.as<double>(),
                           c->stream));
     NestedArgs a{};
     a.tab = c->d_tab[form].p;
@@ -1121,7 +1124,7 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
             const int Bc = std::min(B, NO - o0), bi = i & 1;
             float4* plane = c->d_nest_plane.as<float4>() + bi * buf4;
             if (i >= 2) CU(cudaStreamWaitEvent(c->nest_gen, ev_val[bi], 0));   // the buffer's last reader
-            CU(launch_inner_paths_defl(vs, sp->seed, o0, Bc, NN, n_inner, i_pad, G4, c->d_nest_ln.as<int>(),
+            CU(launch_inner_paths_defl(vs, sp->seed, sp->outer_first, o0, Bc, NN, n_inner, i_pad, G4, c->d_nest_ln.as<int>(),
                                        c->d_nest_rn.as<double>(), c->d_nest_bm.as<double2>(), plane, c->sm_count, 4,
                                        c->nest_gen));
             CU(cudaEventRecord(ev_gen[bi], c->nest_gen));
@@ -1149,7 +1152,7 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
     }
     for (int o0 = 0; o0 < NO && !sur && !curve && !defl; o0 += B) {
         const int Bc = std::min(B, NO - o0);
-        CU(launch_inner_paths(form, vs, sp->seed, o0, Bc, NN, n_inner, i_pad, Lmax, c->d_nest_ln.as<int>(),
+        CU(launch_inner_paths(form, vs, sp->seed, sp->outer_first, o0, Bc, NN, n_inner, i_pad, Lmax, c->d_nest_ln.as<int>(),
                               c->d_nest_rn.as<double>(), c->d_nest_bm.as<double2>(), c->d_nest_plane.p, c->sm_count,
                               c->stream));
         const long long items = (long long)NN * Bc * a.n_chunks;

@@ -76,7 +76,8 @@ RSV_NESTED_MC, RSV_NESTED_SURROGATE, RSV_NESTED_CURVE = 0, 1, 2
 class rsv_nested_spec(C.Structure):
     _fields_ = [("n_outer", C.c_int32), ("n_nodes", C.c_int32), ("node_step_m", C.c_int32),
                 ("n_inner", C.c_int32), ("seed", C.c_uint64), ("a", C.c_double), ("b", C.c_double),
-                ("sigma", C.c_double), ("r0", C.c_double), ("mode", C.c_int32), ("batch_outer", C.c_int32)]
+                ("sigma", C.c_double), ("r0", C.c_double), ("mode", C.c_int32), ("batch_outer", C.c_int32),
+                ("outer_first", C.c_int32)]
 
 
 class rsv_nested_out(C.Structure):
@@ -335,12 +336,13 @@ def rsv_compute_mlife(ctx, pol, form: int = RSV_FORM_F32_COMP, outputs: int = RS
 
 def rsv_compute_nested(ctx, form: int = RSV_FORM_F32_COMP, *, n_outer: int, n_nodes: int, node_step_m: int = 12,
                        n_inner: int = 1000, seed: int = 0, a: float = 0.1, b: float = 0.04, sigma: float = 0.01,
-                       r0: float = 0.03, mode: int = RSV_NESTED_MC, batch_outer: int = 0, on_device: bool = False,
-                       L_mean=None, L_q995=None, r_node=None, D0=None, L_all=None, n_fallback=None):
+                       r0: float = 0.03, mode: int = RSV_NESTED_MC, batch_outer: int = 0, outer_first: int = 0,
+                       on_device: bool = False, L_mean=None, L_q995=None, r_node=None, D0=None, L_all=None,
+                       n_fallback=None):
     """Nested valuation (see include/rsv.h).  Output buffers are caller-sized
     ([n_outer, n_nodes] and [n_outer, n_nodes, n_inner])."""
     o = rsv_opts(form, 0, 0, 1 if on_device else 0, -1)
-    sp = rsv_nested_spec(n_outer, n_nodes, node_step_m, n_inner, seed, a, b, sigma, r0, mode, batch_outer)
+    sp = rsv_nested_spec(n_outer, n_nodes, node_step_m, n_inner, seed, a, b, sigma, r0, mode, batch_outer, outer_first)
     out = rsv_nested_out(_ptr(L_mean), _ptr(L_q995), _ptr(r_node), _ptr(D0), _ptr(L_all), _ptr(n_fallback))
     _check(ctx, _lib.rsv_compute_nested(ctx, C.byref(o), C.byref(sp), C.byref(out)))
 

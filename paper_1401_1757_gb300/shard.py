@@ -9,7 +9,10 @@ Chains are independent (the paper's own decomposition is by policy, Section
   per-scenario FP64 portfolio totals over the ranks (``reduce_totals``).
 * ``scenario_shard``: contiguous scenario ranges; every rank values the whole
   portfolio under its own scenarios, so per-scenario totals are complete on
-  the owning rank and nothing is reduced.
+  the owning rank and nothing is reduced.  The same split serves the outer
+  paths of a nested valuation: each rank passes its range's first index as
+  ``outer_first`` (the paths' random streams are keyed by the global index),
+  and every node statistic is complete on the rank that owns the path.
 """
 from __future__ import annotations
 

@@ -115,6 +115,23 @@ def test_nested_deflated_batching_gives_the_same_bits(ctx):
     assert np.array_equal(one["L_q995"], many["L_q995"])
 
 
+@pytest.mark.parametrize("form", [rsv.RSV_FORM_F32_COMP, rsv.RSV_FORM_F32_DEFLATED])
+def test_outer_paths_split_across_calls(ctx, form):
+    """Outer paths keyed by their global index: two calls on outer paths 0-2
+    and 3-5 (outer_first = 3) give the rows of one call on all six, bit for
+    bit, so ranks can split the outer paths with no exchange."""
+    tab = synth.gm_monthly_survival()
+    pol = mixed_portfolio(30, seed=31)
+    spec = dict(n_nodes=5, node_step_m=12, n_inner=96, seed=37)
+    whole = nested(ctx, pol, tab, form, n_outer=6, **spec)
+    lo = nested(ctx, pol, tab, form, n_outer=3, **spec)
+    hi = nested(ctx, pol, tab, form, n_outer=3, outer_first=3, **spec)
+    for key in ("L_all", "L_mean", "L_q995", "r_node", "D0"):
+        assert np.array_equal(np.concatenate([lo[key], hi[key]]), whole[key]), key
+    with pytest.raises(rsv.RsvError):
+        nested(ctx, pol, tab, form, n_outer=3, outer_first=(1 << 24) - 2, **spec)
+
+
 def test_node_statistics_fifth_largest(ctx):
     tab = synth.gm_monthly_survival()
     pol = synth.portfolio_single_life(50, seed=4)
