@@ -81,7 +81,7 @@ ALGO_FLOPS = {0: 3, 1: 16, 2: 3, 3: 3}
 # (FMA = 2, add/sub/mul/min/max = 1): plain v p then an FMA; the double-float
 # forms' products and ordered sums; the deflated form per 16 steps two
 # products and 14 FMAs (30), the join of its two partial sums (1) and the
-# ordered fold (6; the packed-pair variants' TwoSum 7), plus for the
+# ordered fold (6: max, min, three adds, one more into l), plus for the
 # reversionary annuity the expected cash flow (two products, one subtraction,
 # one FMA: 5) per policy-step shared by the M scenarios of a lane.
 ISSUED_FLOPS = {"f32": {0: 3, 1: 9, 2: 3, 3: 3},
@@ -108,8 +108,6 @@ def issued_flops(pol, form, n_scen, horizon=0, variant_name=""):
     if form == "f32defl":   # the JL expected cash flow, amortised over the lane's M scenarios
         m = re.search(r"xM(\d+)", variant_name)
         per[1] += 5.0 / (int(m.group(1)) if m else 4)
-        if " x2" in variant_name:   # TwoSum fold: one operation more per span
-            per = {p: f + 1.0 / 16 for p, f in per.items()}
     return float(sum(per[p] * cs[p] for p in cs) * n_scen)
 
 

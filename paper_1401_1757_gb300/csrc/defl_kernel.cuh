@@ -59,9 +59,9 @@
 // are one pair {even steps, odd steps}, and four consecutive steps of a
 // deflator row and of a weight row are two pairs, so a pair instruction does
 // the work of two chain-steps.  The fold of a span into (h, l) runs on pairs
-// of chains (scenarios m and m + 1) as Knuth's branch-free TwoSum, whose error
-// term is exact like the ordered Fast2Sum's: the X2 variants give the same
-// bits as the scalar ones.
+// of chains (scenarios m and m + 1): the ordering by max and min per chain (the
+// terms are non-negative), then the ordered Fast2Sum on the pair, so the X2
+// variants give the same bits as the scalar ones.
 #pragma once
 
 #include <type_traits>
@@ -321,24 +321,25 @@ __device__ __forceinline__ void defl_fold_all(DeflLane<P, M>& st) {
 #pragma unroll
         for (int m = 0; m < M; ++m) defl_fold(st.h[i][m], st.l[i][m], __fadd_rn(st.a0[i][m], st.a1[i][m]));
 }
-// Packed: b = a0 + a1 of two chains, then TwoSum (s, e) = h + b on the pair
-// (exact e for any order of magnitude, so no ordering is needed) and l += e.
+// Packed: b = a0 + a1 of two chains, ordered against h by max and min per
+// chain (both non-negative), then the ordered Fast2Sum on the pair and l += e:
+// the scalar fold's operations, so the same bits.
 template <int P, int M>
 __device__ __forceinline__ void defl_fold_all(DeflLaneX2<P, M>& st) {
 #pragma unroll
     for (int i = 0; i < P; ++i)
 #pragma unroll
         for (int k = 0; k < M / 2; ++k) {
-            float x0, y0, x1, y1;
+            float x0, y0, x1, y1, h0, h1;
             x2_unpack(st.acc[i][2 * k], x0, y0);
             x2_unpack(st.acc[i][2 * k + 1], x1, y1);
-            const f32x2 b = x2_pack(__fadd_rn(x0, y0), __fadd_rn(x1, y1));
-            const f32x2 h = st.h[i][k];
-            const f32x2 s = x2_add(h, b);
-            const f32x2 bb = x2_sub(s, h);
-            const f32x2 e = x2_add(x2_sub(h, x2_sub(s, bb)), x2_sub(b, bb));
+            x2_unpack(st.h[i][k], h0, h1);
+            const float b0 = __fadd_rn(x0, y0), b1 = __fadd_rn(x1, y1);
+            const f32x2 hi = x2_pack(fmaxf(h0, b0), fmaxf(h1, b1));
+            const f32x2 lo = x2_pack(fminf(h0, b0), fminf(h1, b1));
+            const f32x2 s = x2_add(hi, lo);
             st.h[i][k] = s;
-            st.l[i][k] = x2_add(st.l[i][k], e);
+            st.l[i][k] = x2_add(st.l[i][k], x2_sub(lo, x2_sub(s, hi)));
         }
 }
 

@@ -359,15 +359,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                         fence_after();
                         const size_t trow = (size_t)tile * TM + row;   // the row in the traced outputs
                         const bool traced = TRACE && tile < a.n_tiles;
+                        // both column chunks into registers first; after half 0 the
+                        // accumulator is released before the arithmetic, so that the
+                        // products of half 1 need not wait for it
+                        uint32_t r2[2][16];
+                        tmem_ld16_async(tmem + lane_base + dcol_of(sl) + cgrp * 32, r2[0]);
+                        tmem_ld16_async(tmem + lane_base + dcol_of(sl) + cgrp * 32 + 16, r2[1]);
+                        tmem_wait_ld(r2[0]);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) asm volatile("" : "+r"(r2[1][i]));
+                        if (h == 0) {
+                            fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&bar_dfree[sl]);
+                        }
 #pragma unroll
                         for (int c = 0; c < 2; ++c) {
                             const int col = h * NH + cgrp * 32 + c * 16;   // column of the layer
-                            uint32_t r[16];
-                            tmem_ld16_async(tmem + lane_base + dcol_of(sl) + cgrp * 32 + c * 16, r);
-                            tmem_wait_ld(r);
                             float v[16];
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+                            for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r2[c][i]);
                             const float4* b4 = reinterpret_cast<const float4*>(&bias_s[l - 1][col]);
                             if constexpr (TRACE) {
                                 if (traced) {
@@ -421,10 +432,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                       x2_pack(w5_s[col + i], w5_s[col + i + 1]), ysum[sl]);
                             }
                         }
-                        if (h == 1 && l < 4) tmem_wait_st();
-                        fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(h == 0 ? &bar_dfree[sl] : &bar_act[sl]);
+                        if (h == 1) {
+                            if (l < 4) tmem_wait_st();
+                            fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&bar_act[sl]);
+                        }
                     }
                 }
             }

@@ -113,9 +113,9 @@ def test_every_variant_agrees(ctx):
 
 def test_packed_variants_give_the_scalar_bits(ctx):
     """The packed-pair (f32x2) variants round every operation as the scalar
-    ones do, and their TwoSum fold has the same exact error term as the
-    ordered Fast2Sum: their reserves are bit-identical to the scalar variant
-    of the same shape, on the whole mix with every state."""
+    ones do, and their fold is the same ordered Fast2Sum on pairs of chains:
+    their reserves are bit-identical to the scalar variant of the same shape,
+    on the whole mix with every state."""
     tab = synth.gm_monthly_survival()
     pol = with_jl_states(synth.portfolio_mix(300, seed=8))
     v = synth.vasicek_paths(201, 1200, seed=8)
