@@ -175,7 +175,9 @@ typedef struct {
                           r_horizon = 0 (later cash flows dropped); 0 = none           */
     int32_t on_device; /* 1: output pointers are device pointers and the call is
                           asynchronous on the context stream; 0: host pointers, the
-                          call blocks until the results are in host memory            */
+                          call blocks until the results are in host memory (in the
+                          deflated form a page-locked, device-mapped V0 is written
+                          by the kernel itself, any other is staged and copied)      */
     int32_t variant;   /* kernel variant index, -1 = the tuned/default one (see
                           rsv_variant_count / rsv_tune), RSV_VARIANT_TIME_SCAN or
                           RSV_VARIANT_SUMMATION                                        */

@@ -254,9 +254,38 @@ rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     double* tot = (outs & RSV_OUT_SCEN_TOTAL) ? out->scen_total : nullptr;
     float* hV0f = V0f;
     double *hV0d = V0d, *htot = tot;
+    // A page-locked host V0 that is mapped into the device's address space is
+    // written by the kernel itself (coherent stores over the CPU-GPU link, at
+    // a small fraction of the link's bandwidth for this kernel), so its 4 or 8
+    // bytes per valuation are not staged in device memory and copied after.
+    // Both ends of each buffer must lie in mapped page-locked memory, else the
+    // staged copy is used.
+    auto mapped = [](const void* p, size_t bytes) -> char* {
+        cudaPointerAttributes a0{}, a1{};
+        const char* q = static_cast<const char*>(p);
+        if (cudaPointerGetAttributes(&a0, q) != cudaSuccess ||
+            cudaPointerGetAttributes(&a1, q + bytes - 1) != cudaSuccess) {
+            cudaGetLastError();   // not a CUDA allocation
+            return nullptr;
+        }
+        if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+            return nullptr;
+        char* d = static_cast<char*>(a0.devicePointer);
+        return static_cast<char*>(a1.devicePointer) == d + bytes - 1 ? d : nullptr;
+    };
+    bool direct_v0 = false;
+    if (!o->on_device && (V0f || V0d) && n_v0 > 0) {
+        char* df = V0f ? mapped(V0f, n_v0 * sizeof(float)) : nullptr;
+        char* dd = V0d ? mapped(V0d, n_v0 * sizeof(double)) : nullptr;
+        if ((!V0f || df) && (!V0d || dd)) {
+            direct_v0 = true;
+            if (V0f) V0f = reinterpret_cast<float*>(df);
+            if (V0d) V0d = reinterpret_cast<double*>(dd);
+        }
+    }
     if (!o->on_device) {
-        if (V0f) { CU(c->d_o_v0f.ensure(n_v0 * sizeof(float))); V0f = c->d_o_v0f.as<float>(); }
-        if (V0d) { CU(c->d_o_v0d.ensure(n_v0 * sizeof(double))); V0d = c->d_o_v0d.as<double>(); }
+        if (V0f && !direct_v0) { CU(c->d_o_v0f.ensure(n_v0 * sizeof(float))); V0f = c->d_o_v0f.as<float>(); }
+        if (V0d && !direct_v0) { CU(c->d_o_v0d.ensure(n_v0 * sizeof(double))); V0d = c->d_o_v0d.as<double>(); }
         if (tot) { CU(c->d_o_tot.ensure(NSc * sizeof(double))); tot = c->d_o_tot.as<double>(); }
     }
     CU(c->d_ctl.ensure(2 * sizeof(int32_t)));
@@ -307,11 +336,12 @@ rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
         return RSV_OK;
     };
 
-    const bool pipelined = !o->on_device && ((hV0f != nullptr) != (hV0d != nullptr)) && L.n_tiles > 0 && NSc >= 256;
+    const bool pipelined =
+        !o->on_device && !direct_v0 && ((hV0f != nullptr) != (hV0d != nullptr)) && L.n_tiles > 0 && NSc >= 256;
     CU(cudaEventRecord(c->ev0, c->stream));
     CU(launch_defl_plane(c->d_v64.as<double>(), c->n_steps, s_pad, n_groups, c->d_defl_plane.as<float4>(),
                          c->stream));
-    bool copied_v0 = false;
+    bool copied_v0 = direct_v0;
     if (L.n_tiles > 0 && pipelined) {
         // V0 in column blocks, each copied to the host on a second stream
         // while the next block computes (the last block's copy is the tail

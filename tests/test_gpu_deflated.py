@@ -333,3 +333,30 @@ def test_config5_full_size_sampled(ctx):
     host_sum = V0.double().sum(dim=0).cpu().numpy()
     assert np.max(np.abs(tot.cpu().numpy() - host_sum) / host_sum) <= 1e-8
     del V0
+
+
+def test_pinned_host_v0_written_by_the_kernel(ctx):
+    """A page-locked host V0 (FP32 or FP64) is written by the kernel itself; a
+    pageable one is staged on the device and copied.  Both give the bits of
+    the device-resident call."""
+    tab = synth.gm_monthly_survival()
+    pol = synth.portfolio_mix(700, seed=13)
+    v = synth.vasicek_paths(300, 1200, seed=13)
+    load(ctx, pol, [tab], v)
+    n, S = len(pol["product"]), v.shape[0]
+    Vd = torch.empty((n, S), device="cuda")
+    Vdd = torch.empty((n, S), dtype=torch.float64, device="cuda")
+    td = torch.empty(S, dtype=torch.float64, device="cuda")
+    rsv.rsv_compute_reserves(ctx, DEFL, V0T, on_device=True, V0=Vd, V0d=Vdd, scen_total=td)
+    ref, refd, reft = Vd.cpu().numpy(), Vdd.cpu().numpy(), td.cpu().numpy()
+    for pinned in (True, False):
+        Vh = torch.full((n, S), np.nan, dtype=torch.float32)
+        Vhd = torch.full((n, S), np.nan, dtype=torch.float64)
+        if pinned:
+            Vh, Vhd = Vh.pin_memory(), Vhd.pin_memory()
+        th = np.zeros(S)
+        rsv.rsv_compute_reserves(ctx, DEFL, V0T, V0=Vh.numpy(), scen_total=th)
+        assert np.array_equal(Vh.numpy(), ref), pinned
+        assert np.array_equal(th, reft)
+        rsv.rsv_compute_reserves(ctx, DEFL, rsv.RSV_OUT_V0, V0=Vh.numpy(), V0d=Vhd.numpy())
+        assert np.array_equal(Vh.numpy(), ref) and np.array_equal(Vhd.numpy(), refd), pinned
