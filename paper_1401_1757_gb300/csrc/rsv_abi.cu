@@ -320,14 +320,36 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps, int 
     auto key = [&](const PolPrep& q) {
         return group(q) * per_group + kind_rank[q.kind] * span + (kMaxAgeSteps - q.S);
     };
-    for (const PolPrep& q : pp) ++bucket_start[key(q) + 1];
-    for (int b = 0; b < nb; ++b) bucket_start[b + 1] += bucket_start[b];
+    // in parallel for large portfolios: each part counts its contiguous range,
+    // the parts' starts per bucket follow part order, and each part scatters
+    // its range in order, so the sort stays stable
+    const int64_t n_pp = (int64_t)pp.size();
+    const int hw_s = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int TS = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(hw_s, 16), n_pp / 65536));
+    std::vector<int>& cnt = L.h_cnt;
+    cnt.assign((size_t)TS * nb, 0);
+    run_parts(TS, [&](int k) {
+        int* h = cnt.data() + (size_t)k * nb;
+        for (int64_t i = n_pp * k / TS, e = n_pp * (k + 1) / TS; i < e; ++i) ++h[key(pp[i])];
+    });
+    for (int b = 0, run = 0; b < nb; ++b) {
+        bucket_start[b] = run;
+        for (int k = 0; k < TS; ++k) {
+            const int v = cnt[(size_t)k * nb + b];
+            cnt[(size_t)k * nb + b] = run;
+            run += v;
+        }
+        bucket_start[b + 1] = run;
+    }
     int run_lo[12], run_hi[12];   // sorted ranges of the (group, kind rank) runs
     for (int r = 0; r < 12; ++r) {
         run_lo[r] = bucket_start[r * span];
         run_hi[r] = bucket_start[(r + 1) * span];
     }
-    for (size_t i = 0; i < pp.size(); ++i) order[bucket_start[key(pp[i])]++] = (int)i;
+    run_parts(TS, [&](int k) {
+        int* h = cnt.data() + (size_t)k * nb;
+        for (int64_t i = n_pp * k / TS, e = n_pp * (k + 1) / TS; i < e; ++i) order[h[key(pp[i])]++] = (int)i;
+    });
 
     // Tiles: each run is cut into tiles of Pg policies (the last one padded).
     // A tile's cost is its model's weight times the S of its first, longest
@@ -422,14 +444,7 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps, int 
             fill((int)((long long)n_tiles * k / T), (int)((long long)n_tiles * (k + 1) / T));
         });
     }
-    CU(L.slots.ensure(std::max<size_t>(1, s2.size()) * sizeof(SlotRec)));
-    CU(L.kinds.ensure(std::max<size_t>(1, k2.size()) * sizeof(int)));
-    if (n_tiles) {
-        CU(cudaMemcpyAsync(L.slots.p, s2.data(), s2.size() * sizeof(SlotRec), cudaMemcpyHostToDevice, c->stream));
-        // pageable sources: each copy is staged before the call returns, so the
-        // vectors may go out of scope without a stream synchronisation
-        CU(cudaMemcpyAsync(L.kinds.p, k2.data(), k2.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    }
+    L.dev_ok = false;
     L.P = P;
     L.P_general = P_general;
     L.horizon = horizon;
@@ -445,12 +460,43 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps, int 
     L.max_S = 0;
     L.has_two = false;
     L.grp_two[0] = L.grp_two[1] = false;
-    for (const PolPrep& q : pp) {
-        L.max_S = std::max(L.max_S, q.S);
-        const bool two = q.kind == K_ANN2 || q.kind == K_ASS2 || q.kind == K_LS2;
-        L.has_two |= two;
-        L.grp_two[group(q)] |= two;
+    {
+        struct Scan {
+            int max_S = 0;
+            bool two[2] = {false, false};
+        };
+        std::vector<Scan> sc(TS);
+        run_parts(TS, [&](int k) {
+            Scan& r = sc[k];
+            for (int64_t i = n_pp * k / TS, e = n_pp * (k + 1) / TS; i < e; ++i) {
+                const PolPrep& q = pp[i];
+                r.max_S = std::max(r.max_S, q.S);
+                if (q.kind == K_ANN2 || q.kind == K_ASS2 || q.kind == K_LS2) r.two[group(q)] = true;
+            }
+        });
+        for (const Scan& r : sc) {
+            L.max_S = std::max(L.max_S, r.max_S);
+            L.grp_two[0] |= r.two[0];
+            L.grp_two[1] |= r.two[1];
+        }
+        L.has_two = L.grp_two[0] || L.grp_two[1];
     }
+    return RSV_OK;
+}
+
+rsv_status rsv::layout_to_device(rsv_ctx* c) {
+    Layout& L = c->lay;
+    if (L.dev_ok) return RSV_OK;
+    CU(L.slots.ensure(std::max<size_t>(1, L.h_s2.size()) * sizeof(SlotRec)));
+    CU(L.kinds.ensure(std::max<size_t>(1, L.h_k2.size()) * sizeof(int)));
+    if (L.n_tiles) {
+        // pageable sources: each copy is staged before the call returns
+        CU(cudaMemcpyAsync(L.slots.p, L.h_s2.data(), L.h_s2.size() * sizeof(SlotRec), cudaMemcpyHostToDevice,
+                           c->stream));
+        CU(cudaMemcpyAsync(L.kinds.p, L.h_k2.data(), L.h_k2.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           c->stream));
+    }
+    L.dev_ok = true;
     return RSV_OK;
 }
 
@@ -618,6 +664,7 @@ rsv_status compute(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
     const Variant& V = vl[vi];
 
     rsv_status st = build_layout(c, (scan || summ) ? 1 : V.P, o->horizon, c->n_steps, split ? vl[vg].P : 0);
+    if (st == RSV_OK) st = layout_to_device(c);
     if (st != RSV_OK) return st;
     if (cfl && c->lay.max_S > c->cf_steps)
         return fail(c, RSV_E_STATE, "a projection of %d steps is longer than the cash-flow rows (%d)", c->lay.max_S,
@@ -820,6 +867,7 @@ rsv_status compute_nested(rsv_ctx* c, const rsv_opts* o, const rsv_nested_spec* 
     const int form = o->form == F_DEFL && !mc ? F_COMP : o->form;
     const int P = defl ? kNestDeflP : nested_tile_width(form);
     rsv_status st = build_layout(c, P, 0, kMaxAgeSteps);
+    if (st == RSV_OK) st = layout_to_device(c);
     if (st != RSV_OK) return st;
     size_t smem = 0;
     DeflTabs T;
@@ -1388,7 +1436,14 @@ rsv_status rsv_clear_cashflows(rsv_ctx* c) try {
 rsv_status rsv_load_portfolio(rsv_ctx* c, const rsv_policy* pols, int64_t n) try {
     if (!c) return RSV_E_ARG;
     if (n < 0 || n > 0x7fffffffLL || (n > 0 && !pols)) return fail(c, RSV_E_ARG, "bad portfolio size %lld", (long long)n);
-    c->pols.assign(pols, pols + n);
+    // copied by several host threads for large portfolios (no zero fill first)
+    c->pols.resize((size_t)n);
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(hw, 16), n / 65536));
+    run_parts(T, [&](int k) {
+        const int64_t lo = n * k / T, hi = n * (k + 1) / T;
+        if (hi > lo) memcpy(c->pols.data() + lo, pols + lo, (size_t)(hi - lo) * sizeof(rsv_policy));
+    });
     ++c->pol_gen;
     c->amount_dirty = true;
     return RSV_OK;
