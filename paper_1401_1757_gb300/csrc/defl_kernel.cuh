@@ -214,6 +214,32 @@ struct DeflPol {
     float ix[P], iy[P];
 };
 
+// The fields of a warp's P slot records that product kind KIND reads, loaded
+// from shared memory at each staged block, so that no other kind's fields
+// stay live in registers across the block loop.
+template <int KIND, int P>
+__device__ __forceinline__ DeflPol<P> defl_pol(const DeflSlot* __restrict__ rec) {
+    DeflPol<P> pp;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        const int4 q4 = *reinterpret_cast<const int4*>(&rec[i].off1);   // off1, off2, S, pol
+        pp.off1[i] = q4.x;
+        pp.S[i] = q4.w < 0 ? 0 : q4.z;
+        if constexpr (KIND != K_ANN) {
+            const int2 z2 = *reinterpret_cast<const int2*>(&rec[i].gz1);
+            pp.gz1[i] = z2.x;
+            pp.gz2[i] = z2.y;
+        }
+        if constexpr (KIND == K_JL || KIND == K_ANN2) {
+            const float2 f2 = *reinterpret_cast<const float2*>(&rec[i].ix);
+            pp.off2[i] = q4.y;
+            pp.ix[i] = f2.x;
+            pp.iy[i] = f2.y;
+        }
+    }
+    return pp;
+}
+
 // The expected cash flows E of four steps t = 4g .. 4g+3 of policy i
 // (per unit amount; for K_ANN and K_ASS unscaled), zero past its end.
 template <int KIND, int P>
@@ -358,7 +384,9 @@ __device__ __forceinline__ void defl_span(Lane& st, const DeflPol<P>& pp, const 
     defl_fold_all(st);
 }
 
-// One staged block (two spans, descending) of one item.
+// One staged block (two spans, descending) of one item.  The packed lanes
+// unroll the two spans of a block that no policy ends in, so that the
+// scheduler can overlap the first span's fold with the second span's loads.
 template <int KIND, int P, int M, class Lane>
 __device__ __forceinline__ void defl_block(Lane& st, const DeflPol<P>& pp, const float4* __restrict__ tab,
                                            const float4* __restrict__ ring_b, int j, int lane, int smin, int smax) {
@@ -368,6 +396,9 @@ __device__ __forceinline__ void defl_block(Lane& st, const DeflPol<P>& pp, const
     if (t_lo + DEFL_KB > smin) {                    // some policy ends within or before the block
 #pragma unroll 1
         for (int h = 1; h >= 0; --h) defl_span<KIND, P, M>(st, pp, tab, ring_b + h * 4 * (32 * M), g_lo + 4 * h, lane, true);
+    } else if constexpr (Lane::packed) {
+        defl_span<KIND, P, M>(st, pp, tab, ring_b + 4 * (32 * M), g_lo + 4, lane, false);
+        defl_span<KIND, P, M>(st, pp, tab, ring_b, g_lo, lane, false);
     } else {
 #pragma unroll 1
         for (int h = 1; h >= 0; --h) defl_span<KIND, P, M>(st, pp, tab, ring_b + h * 4 * (32 * M), g_lo + 4 * h, lane, false);
@@ -470,7 +501,6 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
     // -------------------- consumers
     using Lane = typename std::conditional<X2, DeflLaneX2<P, M>, DeflLane<P, M>>::type;
     Lane st;
-    DeflPol<P> pp;
     int smin = 0, smax = 0, kind = K_ANN, stt = 0, chunk = 0;
     for (int k = 0;; ++k) {
         const int b = k % NBUF;
@@ -491,18 +521,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
             smax = 0;
 #pragma unroll
             for (int i = 0; i < P; ++i) {
-                const int4 q4 = *reinterpret_cast<const int4*>(&rec[i].off1);
-                const float4 f4 = *reinterpret_cast<const float4*>(&rec[i].ix);   // ix, iy, mat, kind
-                const int2 z2 = *reinterpret_cast<const int2*>(&rec[i].gz1);
+                const int4 q4 = *reinterpret_cast<const int4*>(&rec[i].off1);   // off1, off2, S, pol
                 const int S = q4.w < 0 ? 0 : q4.z;
-                const float mat = f4.z;
-                pp.off1[i] = q4.x;
-                pp.off2[i] = q4.y;
-                pp.gz1[i] = z2.x;
-                pp.gz2[i] = z2.y;
-                pp.S[i] = S;
-                pp.ix[i] = f4.x;
-                pp.iy[i] = f4.y;
+                const float mat = rec[i].mat;
                 smin = min(smin, S);
                 smax = max(smax, S);
                 float h0s[M];
@@ -523,10 +544,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
             }
         }
         const float4* ring_b = ring + (size_t)b * DEFL_G * CH;
-        if (kind == K_ANN) defl_block<K_ANN, P, M>(st, pp, tab, ring_b, hb.j, lane, smin, smax);
-        else if (kind == K_ASS) defl_block<K_ASS, P, M>(st, pp, tab, ring_b, hb.j, lane, smin, smax);
-        else if (kind == K_JL) defl_block<K_JL, P, M>(st, pp, tab, ring_b, hb.j, lane, smin, smax);
-        else defl_block<K_ANN2, P, M>(st, pp, tab, ring_b, hb.j, lane, smin, smax);
+        if (kind == K_ANN) defl_block<K_ANN, P, M>(st, defl_pol<K_ANN, P>(rec), tab, ring_b, hb.j, lane, smin, smax);
+        else if (kind == K_ASS) defl_block<K_ASS, P, M>(st, defl_pol<K_ASS, P>(rec), tab, ring_b, hb.j, lane, smin, smax);
+        else if (kind == K_JL) defl_block<K_JL, P, M>(st, defl_pol<K_JL, P>(rec), tab, ring_b, hb.j, lane, smin, smax);
+        else defl_block<K_ANN2, P, M>(st, defl_pol<K_ANN2, P>(rec), tab, ring_b, hb.j, lane, smin, smax);
         __syncwarp();
         if (lane == 0) defl_mbar_arrive(&empty[b]);   // this warp is done with buffer b
 
