@@ -745,8 +745,10 @@ def bench_c5_nested(rsv, torch, tab, sur_epochs=10):
 
 def bench_e2e(rsv, torch, ctx, pol, tab, v, form, horizon, steps, warmup, world, dist):
     """The head step through the C ABI with host buffers: uploads of the table,
-    scenarios and portfolio from pinned memory and the device-to-host copy of
-    every reserve inside the timed region."""
+    scenarios and portfolio from pinned memory, the host rebuild of the layout
+    after the portfolio reload, and every reserve written to page-locked host
+    memory (by the kernel itself in the deflated form, else by a copy), all
+    inside the timed region."""
     fid = FORMS[form]
     outs = rsv.RSV_OUT_V0 | rsv.RSV_OUT_SCEN_TOTAL
     n_pol, n_scen = len(pol["product"]), v.shape[0]
@@ -781,7 +783,8 @@ def bench_e2e(rsv, torch, ctx, pol, tab, v, form, horizon, steps, warmup, world,
             "h2d_bytes_per_step": int(v.nbytes + recn.nbytes + tab.nbytes),
             "d2h_bytes_per_step": int(V0_host.numel() * 4 + tot_host.numel() * 8),
             "ms_per_step": 1e3 * tot_s / steps,
-            "note": "per rank: uploads of its portfolio share, the scenarios and the table; its V0 and totals back"}
+            "note": "per rank: uploads of its portfolio share, the scenarios and the table, and the layout "
+                    "rebuilt on the host; its V0 (written to page-locked host memory) and totals back"}
 
 
 def main():
