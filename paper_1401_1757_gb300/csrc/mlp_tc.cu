@@ -231,6 +231,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == kEpiWarps) {
         if (lane == 0) {
             const CUtensorMap* maps[4] = {&mapW1, &mapW2, &mapW3, &mapW4};
+            // shared-memory descriptors of the operand buffers, built once: the
+            // issuing thread runs alone, so every instruction of its address
+            // arithmetic would sit on the products' issue path
+            const uint64_t wdesc0 = sw128_desc(Wbuf), xdesc0 = sw128_desc(Xbuf);
             // in flight: copies on bar_x / bar_w, products on bar_mma (with the parity they complete)
             bool pend_x[2] = {false, false}, pend_w[2] = {false, false}, pend_m[2] = {false, false};
             uint32_t par_x[2] = {0, 0}, par_w[2] = {0, 0}, par_m[2] = {0, 0};
@@ -298,15 +302,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (failed) break;
                             fence_after();
                             const uint32_t d = tmem + dcol_of(sl);
-                            const unsigned char* wh = Wbuf + h * WH_SLAB;
+                            // descriptors advance by the byte offset / 16 in their start
+                            // address field (shared addresses stay below 2^18, so the
+                            // field cannot carry); every offset is a constant
+                            const uint64_t wd = wdesc0 + (uint64_t)((h * WH_SLAB) >> 4);
                             if (l == 1) {
-                                const unsigned char* xs = Xbuf + sl * X_BYTES;
+                                const uint64_t xd = xdesc0 + (uint64_t)((sl * X_BYTES) >> 4);
+#pragma unroll
                                 for (int kk = 0; kk < 4; ++kk)   // 4 x k16 per 64-wide slab: +32 bytes each
-                                    mma_ss(d, sw128_desc(xs + kk * 32), sw128_desc(wh + kk * 32), kk != 0);
+                                    mma_ss(d, xd + (uint64_t)((kk * 32) >> 4), wd + (uint64_t)((kk * 32) >> 4), kk != 0);
                             } else {
                                 const uint32_t ac = tmem + acol_of(sl);   // A column 8 j holds K = 16 j .. 16 j + 15
+#pragma unroll
                                 for (int j = 0; j < 16; ++j)
-                                    mma_ts(d, ac + 8 * j, sw128_desc(wh + (j >> 2) * W_SLAB + (j & 3) * 32), j != 0);
+                                    mma_ts(d, ac + 8 * j, wd + (uint64_t)(((j >> 2) * W_SLAB + (j & 3) * 32) >> 4), j != 0);
                             }
                             mma_commit(&bar_mma[sl]);
                             pend_m[sl] = true;
