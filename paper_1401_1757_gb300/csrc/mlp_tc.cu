@@ -13,8 +13,8 @@
 // the even K index in the low half.  Each of the two tiles in flight (slots)
 // owns 128 accumulator columns and 128 activation columns of TMEM, so the
 // tensor cores work on one slot while the epilogue drains the other (see the
-// kernel).  Warp 16 (one thread) issues the TMA copies and the products;
-// warps 0-15 run the epilogue: warp w may only touch TMEM lanes 32 (w % 4) ..
+// kernel).  Warp 16 (one thread) issues the products, warp 17 (one thread)
+// the TMA copies; warps 0-15 run the epilogue: warp w may only touch TMEM lanes 32 (w % 4) ..
 // +31 (the rows of the tile), and takes columns 32 (w / 4) .. +31 of each
 // half.  Every mbarrier wait is bounded; on a timeout the kernel records it in
 // the status word, skips the later waits, lets the copies and products in
@@ -42,7 +42,7 @@ constexpr int W_SLAB = 2 * WH_SLAB;             // 32 KiB: both halves of one K 
 constexpr int W_BYTES = 4 * W_SLAB;             // 128 KiB (K = 256)
 constexpr uint32_t kPoll = 1u << 24;
 constexpr int kEpiWarps = 16;                   // 4 lane quarters x 4 column groups
-constexpr int kThreads = 32 * (kEpiWarps + 1);  // + the issuing warp
+constexpr int kThreads = 32 * (kEpiWarps + 2);  // + the issuing warp and the staging warp
 constexpr uint32_t kTmemCols = 512;
 // TMEM columns of slot s: its accumulator at 256 s, its activation buffer at 256 s + 128
 __device__ __forceinline__ uint32_t dcol_of(int s) { return 256u * (uint32_t)s; }
@@ -190,9 +190,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* Xbuf = base;                  // slot s at s * X_BYTES
     unsigned char* Wbuf = base + 2 * X_BYTES;    // K slab k, half h at k * W_SLAB + h * WH_SLAB
-    // bar_mma[s]: the products of one step of slot s are done; bar_dfree[s]: the
-    // epilogue (s, l, 0) has read D_s; bar_act[s]: the epilogue (s, l, 1) is done
-    __shared__ uint64_t bar_x[2], bar_w[2], bar_mma[2], bar_dfree[2], bar_act[2];
+    // bar_m0: the products of one step of slot 0 are done; bar_m1[h]: those of
+    // slot 1 on weight half h (and every product issued before them); bar_dfree[s]:
+    // the epilogue (s, l, 0) has read D_s; bar_act[s]: the epilogue (s, l, 1) is done
+    __shared__ uint64_t bar_x[2], bar_w[2], bar_m0, bar_m1[2], bar_dfree[2], bar_act[2];
     __shared__ uint32_t tmem_slot;
     __shared__ float head_part[2][4][TM];              // partial head sums per slot and column group
     __shared__ __align__(16) float bias_s[4][TN];      // b_1..b_4
@@ -205,10 +206,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = 0; i < 2; ++i) {
             mbar_init(&bar_x[i], 1);
             mbar_init(&bar_w[i], 1);
-            mbar_init(&bar_mma[i], 1);
+            mbar_init(&bar_m1[i], 1);
             mbar_init(&bar_dfree[i], kEpiWarps);   // one arrival per epilogue warp
             mbar_init(&bar_act[i], kEpiWarps);
         }
+        mbar_init(&bar_m0, 1);
         fence_barrier_init();
     }
     if (warp == 0) {
@@ -228,76 +230,35 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int n_my = (int)blockIdx.x < n_pairs ? (n_pairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     bool failed = false;
 
+    auto wait_on = [&](uint64_t* bar, uint32_t parity) {   // a bounded wait; a timeout is recorded
+        if (failed) return;
+        if (!mbar_wait_bounded(bar, parity, kPoll)) {
+            failed = true;
+            atomicExch(a.status, DEV_TIMEOUT);
+        }
+    };
     if (warp == kEpiWarps) {
+        // ---- the products (one thread).  Step (g, h), g = 4 p + l - 1: slot 0's
+        // products of layer l, half h, then slot 1's.
         if (lane == 0) {
-            const CUtensorMap* maps[4] = {&mapW1, &mapW2, &mapW3, &mapW4};
             // shared-memory descriptors of the operand buffers, built once: the
             // issuing thread runs alone, so every instruction of its address
             // arithmetic would sit on the products' issue path
             const uint64_t wdesc0 = sw128_desc(Wbuf), xdesc0 = sw128_desc(Xbuf);
-            // in flight: copies on bar_x / bar_w, products on bar_mma (with the parity they complete)
-            bool pend_x[2] = {false, false}, pend_w[2] = {false, false}, pend_m[2] = {false, false};
-            uint32_t par_x[2] = {0, 0}, par_w[2] = {0, 0}, par_m[2] = {0, 0};
-            auto wait = [&](uint64_t* bar, uint32_t parity) {
-                if (failed) return;
-                if (!mbar_wait_bounded(bar, parity, kPoll)) {
-                    failed = true;
-                    atomicExch(a.status, DEV_TIMEOUT);
-                }
-            };
-            auto load_w = [&](int h, int layer, uint32_t parity) {   // half h of W_layer
-                const int ns = layer == 1 ? 1 : 4;
-                mbar_arrive_expect_tx(&bar_w[h], ns * WH_SLAB);
-                for (int k = 0; k < ns; ++k)
-                    tma_load_2d(Wbuf + k * W_SLAB + h * WH_SLAB, maps[layer - 1], k * SLAB_K, h * NH, &bar_w[h]);
-                pend_w[h] = true;
-                par_w[h] = parity;
-            };
-            auto load_x = [&](int p, uint32_t parity) {   // both slots' features of this CTA's pair p
-                const int pair = (int)blockIdx.x + p * (int)gridDim.x;
-                for (int sl = 0; sl < 2; ++sl) {
-                    mbar_arrive_expect_tx(&bar_x[sl], X_BYTES);
-                    tma_load_2d(Xbuf + sl * X_BYTES, &mapX, 0, (2 * pair + sl) * TM, &bar_x[sl]);
-                    pend_x[sl] = true;
-                    par_x[sl] = parity;
-                }
-            };
-            // the refill deferred from the previous half step: W half rh for
-            // step rg + 1 (or the next pair's layer 1), once slot 1's products
-            // of (rg, rh) are done (slot 0's were committed before them)
-            int rg = -1, rh = 0;
-            auto refill = [&]() {
-                if (rg < 0 || failed) return;
-                wait(&bar_mma[1], (uint32_t)rh);
-                if (failed) return;
-                const int l = rg % 4 + 1, p = rg / 4;
-                if (l < 4) load_w(rh, l + 1, (uint32_t)((rg + 1) & 1));
-                else if (p + 1 < n_my) load_w(rh, 1, (uint32_t)((rg + 1) & 1));
-                if (l == 1 && rh == 1 && p + 1 < n_my) load_x(p + 1, (uint32_t)((p + 1) & 1));
-                rg = -1;
-            };
-            if (n_my > 0) {
-                load_x(0, 0);
-                load_w(0, 1, 0);
-                load_w(1, 1, 0);
-            }
+            bool pend0 = false, pend1[2] = {false, false};   // commits in flight
+            uint32_t par0 = 0, par1[2] = {0, 0};
             for (int p = 0; p < n_my && !failed; ++p) {
                 for (int l = 1; l <= 4 && !failed; ++l) {
                     const int g = p * 4 + l - 1;
                     for (int h = 0; h < 2 && !failed; ++h) {
-                        wait(&bar_w[h], (uint32_t)(g & 1));
-                        if (failed) break;
-                        pend_w[h] = false;
-                        for (int sl = 0; sl < 2; ++sl) {
+                        wait_on(&bar_w[h], (uint32_t)(g & 1));
+                        for (int sl = 0; sl < 2 && !failed; ++sl) {
                             if (h == 0) {
                                 // A_s(l-1) written and D_s free
-                                if (g > 0) wait(&bar_act[sl], (uint32_t)((g - 1) & 1));
-                                if (l == 1) {
-                                    wait(&bar_x[sl], (uint32_t)(p & 1));
-                                    pend_x[sl] = false;
-                                }
+                                if (g > 0) wait_on(&bar_act[sl], (uint32_t)((g - 1) & 1));
+                                if (l == 1) wait_on(&bar_x[sl], (uint32_t)(p & 1));
                             } else {
-                                wait(&bar_dfree[sl], (uint32_t)(g & 1));   // the epilogue (s, l, 0) has read D_s
+                                wait_on(&bar_dfree[sl], (uint32_t)(g & 1));   // the epilogue (s, l, 0) has read D_s
                             }
                             if (failed) break;
                             fence_after();
@@ -317,24 +278,77 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 for (int j = 0; j < 16; ++j)
                                     mma_ts(d, ac + 8 * j, wd + (uint64_t)(((j >> 2) * W_SLAB + (j & 3) * 32) >> 4), j != 0);
                             }
-                            mma_commit(&bar_mma[sl]);
-                            pend_m[sl] = true;
-                            par_m[sl] = (uint32_t)h;
-                            // with the first product of this half queued, take the
-                            // deferred refill of the previous half
-                            if (sl == 0) refill();
+                            if (sl == 0) {
+                                mma_commit(&bar_m0);
+                                pend0 = true;
+                                par0 = (uint32_t)h;
+                            } else {
+                                mma_commit(&bar_m1[h]);
+                                pend1[h] = true;
+                                par1[h] = (uint32_t)(g & 1);
+                            }
                         }
-                        rg = g;
-                        rh = h;
                     }
                 }
             }
-            refill();
-            if (failed) {   // let the copies and products in flight land before the memory is released
+            if (failed) {   // let the products in flight land before the memory is released
+                if (pend0) mbar_wait_bounded(&bar_m0, par0, kPoll);
+                for (int h = 0; h < 2; ++h)
+                    if (pend1[h]) mbar_wait_bounded(&bar_m1[h], par1[h], kPoll);
+            }
+        }
+        __syncwarp();
+    } else if (warp == kEpiWarps + 1) {
+        // ---- staging (one thread): the features and the weights by TMA.  Weight
+        // half h of the next layer (or of the next pair's layer 1) is copied as
+        // soon as slot 1's products on it are done (bar_m1[h], which also covers
+        // slot 0's, issued before them), and the next pair's features once
+        // layer 1's second half is done, so that no copy waits for the issuing
+        // thread.  bar_w[h] and bar_x[s] complete once per layer and per pair.
+        if (lane == 0) {
+            const CUtensorMap* maps[4] = {&mapW1, &mapW2, &mapW3, &mapW4};
+            bool pend_x = false, pend_w[2] = {false, false};
+            uint32_t par_x = 0, par_w[2] = {0, 0};
+            auto load_w = [&](int h, int layer, uint32_t parity) {   // half h of W_layer
+                const int ns = layer == 1 ? 1 : 4;
+                mbar_arrive_expect_tx(&bar_w[h], ns * WH_SLAB);
+                for (int k = 0; k < ns; ++k)
+                    tma_load_2d(Wbuf + k * W_SLAB + h * WH_SLAB, maps[layer - 1], k * SLAB_K, h * NH, &bar_w[h]);
+                pend_w[h] = true;
+                par_w[h] = parity;
+            };
+            auto load_x = [&](int p) {   // both slots' features of this CTA's pair p
+                const int pair = (int)blockIdx.x + p * (int)gridDim.x;
+                for (int sl = 0; sl < 2; ++sl) {
+                    mbar_arrive_expect_tx(&bar_x[sl], X_BYTES);
+                    tma_load_2d(Xbuf + sl * X_BYTES, &mapX, 0, (2 * pair + sl) * TM, &bar_x[sl]);
+                }
+                pend_x = true;
+                par_x = (uint32_t)(p & 1);
+            };
+            if (n_my > 0) {
+                load_x(0);
+                load_w(0, 1, 0);
+                load_w(1, 1, 0);
+            }
+            for (int p = 0; p < n_my && !failed; ++p) {
+                for (int l = 1; l <= 4 && !failed; ++l) {
+                    const int g = p * 4 + l - 1;
+                    const int next = l < 4 ? l + 1 : (p + 1 < n_my ? 1 : 0);
+                    for (int h = 0; h < 2 && !failed; ++h) {
+                        const bool x_next = l == 1 && h == 1 && p + 1 < n_my;
+                        if (!next && !x_next) continue;
+                        wait_on(&bar_m1[h], (uint32_t)(g & 1));
+                        if (failed) break;
+                        if (next) load_w(h, next, (uint32_t)((g + 1) & 1));
+                        if (x_next) load_x(p + 1);
+                    }
+                }
+            }
+            if (failed) {   // let the copies in flight land before the memory is released
                 for (int i = 0; i < 2; ++i) {
-                    if (pend_x[i]) mbar_wait_bounded(&bar_x[i], par_x[i], kPoll);
+                    if (pend_x) mbar_wait_bounded(&bar_x[i], par_x, kPoll);
                     if (pend_w[i]) mbar_wait_bounded(&bar_w[i], par_w[i], kPoll);
-                    if (pend_m[i]) mbar_wait_bounded(&bar_mma[i], par_m[i], kPoll);
                 }
             }
         }
@@ -359,7 +373,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         // a timeout is recorded and the later waits skipped, so that
                         // every warp still reaches the block-wide barriers below
                         bool ok = true;
-                        if (lane == 0 && !failed) ok = mbar_wait_bounded(&bar_mma[sl], (uint32_t)h, kPoll);
+                        if (lane == 0 && !failed)
+                            ok = sl == 0 ? mbar_wait_bounded(&bar_m0, (uint32_t)h, kPoll)
+                                         : mbar_wait_bounded(&bar_m1[h], (uint32_t)(g & 1), kPoll);
                         ok = __shfl_sync(0xffffffffu, ok, 0);
                         if (!ok && !failed) {
                             failed = true;
