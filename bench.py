@@ -524,6 +524,27 @@ def oracle_runs(pol, tab, v, horizon, runs, warm=1):
     return times, threads
 
 
+def cpu_full_configs(tab, runs, with_c2):
+    """The oracle on whole configurations (the survey's CPU protocol: minimum
+    and median of ``runs`` timed runs after one warm-up, all host cores):
+    configuration 1 always (1,000 annuities, one flat scenario, a few ms),
+    configuration 2 on request (10^5 policies x 1,000 scenarios x 1,200
+    steps, about 80 s a run on 16 cores)."""
+    out = {}
+    cases = [("config1", synth.portfolio_single_life(1000, seed=0), synth.flat_scenarios(n_steps=720),
+              "1,000 single-life annuities x 1 flat 4% scenario x up to 720 steps, in full")]
+    if with_c2:
+        cases.append(("config2", synth.portfolio_mix(C2["n_pol"], seed=C2["seed"]),
+                      synth.vasicek_paths(C2["n_scen"], C2["n_steps"], seed=C2["seed"]), C2_WORKLOAD + ", in full"))
+    for name, pol, v, what in cases:
+        times, threads = oracle_runs(pol, tab, v, 0, runs)
+        vals = len(pol["product"]) * v.shape[0]
+        out[name] = {"value": vals / min(times), "unit": "valuations/s", "median_value": vals / statistics.median(times),
+                     "min_s": min(times), "median_s": statistics.median(times), "runs": runs, "cores": threads,
+                     "cpu_model": cpu_model(), "kind": "oracle", "sample": what}
+    return out
+
+
 def reference_arm(args, rank):
     """The FP64 CPU oracle on the host cores, a bounded sample of the headline
     workload per step (the same policies, all scenarios, the same horizon)."""
@@ -801,6 +822,8 @@ def main():
     ap.add_argument("--cpu-runs", type=int, default=7)
     ap.add_argument("--ref-policies", type=int, default=1000, help="policies per reference-arm step")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="also time the oracle on all of configuration 2 (about 80 s a run on 16 cores)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="only the headline workload")
     ap.add_argument("--no-nested", action="store_true")
@@ -913,6 +936,7 @@ def main():
         cpu = cpu_baseline(pol_all, tab, v, horizon, min(args.cpu_sample, len(pol_all["product"])), args.cpu_runs)
         if "summation_vs_recurrence" in extras:
             extras["summation_vs_recurrence"]["cpu_oracle"] = cpu_figure1(tab)
+        extras["cpu_oracle_full"] = cpu_full_configs(tab, args.cpu_runs, args.cpu_full)
     for f, r in results.items():
         pk = peaks["fp64_fma_tflops"] if f == "f64" else peaks["fp32_fma_tflops"]
         r["algorithmic_frac_of_measured_peak"] = r["algorithmic_tflops"] / pk
