@@ -71,6 +71,7 @@
 namespace rsv {
 
 constexpr int DEFL_KB = 32;        // steps per staged block of the deflator plane
+constexpr uint32_t kDeflTmemCols = 128;   // the TMEM lanes: four warps per lane quarter x 32 columns
 constexpr int DEFL_G = DEFL_KB / 4; // float4 rows (groups of four steps) per block
 
 // One policy slot of a deflated super-tile (64 bytes).  All lanes of a warp
@@ -204,6 +205,69 @@ struct DeflLaneX2 {
         for (int i = 0; i < P; ++i)
 #pragma unroll
             for (int m = 0; m < M; ++m) acc[i][m] = 0ull;
+    }
+};
+
+// Tensor-memory access of one warp: 32 consecutive columns of its 32 lanes
+// (lane quarter warp % 4), one register a column.
+__device__ __forceinline__ void defl_tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+// Store 32 columns and wait for the stores (the next access to them is a
+// span later, so the wait costs nothing and every later load sees them).
+__device__ __forceinline__ void defl_tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]),
+        "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]),
+        "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+// Packed pairs with the double-float sums in tensor memory: (h, l) of a
+// chain are touched once per 16 steps, so the warp keeps them in its 32 TMEM
+// columns (h of chain j = i M + m in column j, l in column 16 + j) and only
+// the accumulators stay in registers.  At 128 registers a thread the CTA
+// holds 16 warps instead of 12.  The arithmetic is DeflLaneX2's: same bits.
+template <int P, int M>
+struct DeflLaneTM {
+    static constexpr bool packed = true;
+    static_assert(M % 2 == 0 && P * M == 16, "h and l of 16 chains in 32 columns");
+    f32x2 acc[P][M];
+    uint32_t taddr = 0;
+    __device__ __forceinline__ void start_all(const float (&h0)[P][M]) const {
+        uint32_t r[32];
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                r[i * M + m] = __float_as_uint(h0[i][m]);
+                r[16 + i * M + m] = 0u;
+            }
+        defl_tmem_st32(taddr, r);
+    }
+    __device__ __forceinline__ void sum_all(float (&H)[P][M], float (&L)[P][M]) const {
+        uint32_t r[32];
+        defl_tmem_ld32(taddr, r);
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                H[i][m] = __uint_as_float(r[i * M + m]);
+                L[i][m] = __uint_as_float(r[16 + i * M + m]);
+            }
     }
 };
 
@@ -369,6 +433,36 @@ __device__ __forceinline__ void defl_fold_all(DeflLaneX2<P, M>& st) {
         }
 }
 
+template <int P, int M>
+__device__ __forceinline__ void defl_fold_all(DeflLaneTM<P, M>& st) {
+    uint32_t r[32];
+    defl_tmem_ld32(st.taddr, r);
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+        for (int k = 0; k < M / 2; ++k) {
+            const int j0 = i * M + 2 * k, j1 = j0 + 1;
+            float x0, y0, x1, y1;
+            x2_unpack(st.acc[i][2 * k], x0, y0);
+            x2_unpack(st.acc[i][2 * k + 1], x1, y1);
+            const float h0 = __uint_as_float(r[j0]), h1 = __uint_as_float(r[j1]);
+            const float b0 = __fadd_rn(x0, y0), b1 = __fadd_rn(x1, y1);
+            const f32x2 hi = x2_pack(fmaxf(h0, b0), fmaxf(h1, b1));
+            const f32x2 lo = x2_pack(fminf(h0, b0), fminf(h1, b1));
+            const f32x2 s = x2_add(hi, lo);
+            const f32x2 l = x2_add(x2_pack(__uint_as_float(r[16 + j0]), __uint_as_float(r[16 + j1])),
+                                   x2_sub(lo, x2_sub(s, hi)));
+            float s0, s1, l0, l1;
+            x2_unpack(s, s0, s1);
+            x2_unpack(l, l0, l1);
+            r[j0] = __float_as_uint(s0);
+            r[j1] = __float_as_uint(s1);
+            r[16 + j0] = __float_as_uint(l0);
+            r[16 + j1] = __float_as_uint(l1);
+        }
+    defl_tmem_st32(st.taddr, r);
+}
+
 // One 16-step span (four groups, descending) from the staged rows r0+3 .. r0.
 template <int KIND, int P, int M, class Lane>
 __device__ __forceinline__ void defl_span(Lane& st, const DeflPol<P>& pp, const float4* __restrict__ tab,
@@ -411,7 +505,7 @@ __device__ __forceinline__ void defl_block(Lane& st, const DeflPol<P>& pp, const
 // mbarrier arrival; the producer refills a buffer once all NW warps have
 // released it.  The per-scenario sums of an item are joined by the warp that
 // finishes the item last (a shared-memory counter), in warp order.
-template <int P, int M, int NW, int NBUF, int MINB, bool X2>
+template <int P, int M, int NW, int NBUF, int MINB, int X2>
 __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArgs a) {
     using SM = DeflSmem<P, M, NW, NBUF>;
     constexpr int CH = SM::CH, W = NW * P;
@@ -420,6 +514,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
     __shared__ uint64_t tbar;
     __shared__ int red_cnt[2];
     __shared__ volatile int done_items, abort_flag;
+    __shared__ uint32_t tmem_slot;
     unsigned char* base = smem_raw + a.tab_bytes;
     float4* ring = reinterpret_cast<float4*>(base);
     float2* red = reinterpret_cast<float2*>(base + SM::ring);
@@ -443,7 +538,18 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
         done_items = 0;
         abort_flag = 0;
     }
+    if constexpr (X2 == 2) {   // 32 TMEM columns for each valuing warp of a lane quarter
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&tmem_slot)),
+                         "r"(kDeflTmemCols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
     __syncthreads();
+    if constexpr (X2 == 2) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     if (warp == NW) {
         // ---------------- producer: lane 0 claims items and stages their blocks
@@ -499,8 +605,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
     }
 
     // -------------------- consumers
-    using Lane = typename std::conditional<X2, DeflLaneX2<P, M>, DeflLane<P, M>>::type;
+    using Lane = typename std::conditional<
+        X2 == 2, DeflLaneTM<P, M>, typename std::conditional<X2 == 1, DeflLaneX2<P, M>, DeflLane<P, M>>::type>::type;
+    constexpr bool kTm = X2 == 2;
     Lane st;
+    if constexpr (kTm) st.taddr = tmem_slot + (((uint32_t)(warp & 3) * 32u) << 16) + (uint32_t)(warp >> 2) * 32u;
     int smin = 0, smax = 0, kind = K_ANN, stt = 0, chunk = 0;
     for (int k = 0;; ++k) {
         const int b = k % NBUF;
@@ -519,6 +628,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
             kind = rec[0].kind;
             smin = 1 << 30;
             smax = 0;
+            float h0all[P][M];
 #pragma unroll
             for (int i = 0; i < P; ++i) {
                 const int4 q4 = *reinterpret_cast<const int4*>(&rec[i].off1);   // off1, off2, S, pol
@@ -539,9 +649,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
                         h0 = __fmul_rn(dS, mat);
                     }
                     h0s[m] = h0;
+                    h0all[i][m] = h0;
                 }
-                st.start(i, h0s);
+                if constexpr (!kTm) st.start(i, h0s);
             }
+            if constexpr (kTm) st.start_all(h0all);
         }
         const float4* ring_b = ring + (size_t)b * DEFL_G * CH;
         if (kind == K_ANN) defl_block<K_ANN, P, M>(st, defl_pol<K_ANN, P>(rec), tab, ring_b, hb.j, lane, smin, smax);
@@ -555,13 +667,23 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
             float ph[M], pl[M];
 #pragma unroll
             for (int m = 0; m < M; ++m) ph[m] = pl[m] = 0.0f;
+            float Hall[P][M], Lall[P][M];
+            if constexpr (kTm) st.sum_all(Hall, Lall);
 #pragma unroll
             for (int i = 0; i < P; ++i) {
                 const int pol = rec[i].pol;
                 if (pol < 0) continue;
                 const float sh = rec[i].sc_h, sl = rec[i].sc_l;
                 float Hs[M], Ls[M];
-                st.sum(i, Hs, Ls);
+                if constexpr (kTm) {
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        Hs[m] = Hall[i][m];
+                        Ls[m] = Lall[i][m];
+                    }
+                } else {
+                    st.sum(i, Hs, Ls);
+                }
 #pragma unroll
                 for (int m = 0; m < M; ++m) {
                     const int s = chunk * CH + m * 32 + lane;
@@ -624,6 +746,14 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
         }
         if (abort_flag) break;
     }
+    if constexpr (kTm) {   // every valuing warp is done with its columns
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("bar.sync 1, %0;" ::"n"(NW * 32) : "memory");
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(kDeflTmemCols)
+                         : "memory");
+    }
 }
 
 // ------------------------------------------------------ variant registry ----
@@ -634,7 +764,7 @@ struct DeflVariant {
     cudaError_t (*occupancy)(int* blocks_per_sm, size_t smem);
 };
 
-template <int P, int M, int NW, int NBUF, int MINB, bool X2>
+template <int P, int M, int NW, int NBUF, int MINB, int X2>
 cudaError_t set_defl_attributes(size_t smem) {
     auto k = defl_kernel<P, M, NW, NBUF, MINB, X2>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -642,7 +772,7 @@ cudaError_t set_defl_attributes(size_t smem) {
     return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
 }
 
-template <int P, int M, int NW, int NBUF, int MINB, bool X2>
+template <int P, int M, int NW, int NBUF, int MINB, int X2>
 cudaError_t launch_defl(const DeflArgs& a, int grid, size_t smem, cudaStream_t st) {
     cudaError_t e = set_defl_attributes<P, M, NW, NBUF, MINB, X2>(smem);
     if (e != cudaSuccess) return e;
@@ -650,7 +780,7 @@ cudaError_t launch_defl(const DeflArgs& a, int grid, size_t smem, cudaStream_t s
     return cudaGetLastError();
 }
 
-template <int P, int M, int NW, int NBUF, int MINB, bool X2>
+template <int P, int M, int NW, int NBUF, int MINB, int X2>
 cudaError_t occupancy_defl(int* blocks, size_t smem) {
     cudaError_t e = set_defl_attributes<P, M, NW, NBUF, MINB, X2>(smem);
     if (e != cudaSuccess) return e;

@@ -129,6 +129,24 @@ def test_packed_variants_give_the_scalar_bits(ctx):
         assert np.array_equal(ta, tb)
 
 
+def test_tmem_variants_give_the_packed_bits(ctx):
+    """The variants that keep each chain's double-float sum in tensor memory
+    (16 warps at 128 registers) run the packed variants' arithmetic: their
+    reserves are bit-identical to the register variant's (the per-scenario
+    totals group the policies by a different super-tile width)."""
+    tab = synth.gm_monthly_survival()
+    pol = with_jl_states(synth.portfolio_mix(300, seed=8))
+    v = synth.vasicek_paths(201, 1200, seed=8)
+    names = {rsv.rsv_variant_name(DEFL, i): i for i in range(rsv.rsv_variant_count(DEFL))}
+    tms = [i for n, i in names.items() if n.endswith(" tm")]
+    assert tms
+    a, ta = run(ctx, pol, [tab], v, variant=names["deflated P4xM4 nw11 buf8 x2"])
+    for t in tms:
+        b, tb = run(ctx, pol, [tab], v, variant=t)
+        assert np.array_equal(a, b), rsv.rsv_variant_name(DEFL, t)
+        assert np.max(np.abs(tb - ta) / np.abs(ta)) <= 1e-14
+
+
 def test_negative_rates_and_steep_weights(ctx):
     """Scenarios with negative rates (discount factors above 1, so the weights
     can grow along the chain) and a steep constant-force table: the ordered
