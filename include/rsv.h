@@ -102,9 +102,10 @@ enum {
  * step, and r_0 = U_0.  The discount products D are FP64 running products, one
  * per scenario, computed on the device in every call; the life tables are
  * built once in FP64 on the host; each chain-step is one FP32 fused
- * multiply-add, summed in FP32 over 8 steps and folded every 16 steps into a
- * double-float.  Every reserve is within about 14 x 2^-24 (8.3e-7) relative
- * of its value on the FP64 inputs, whatever the projection length.  Products
+ * multiply-add, summed in FP32 over 8 steps and folded into a double-float
+ * every 16 steps (or every 32, the two spans' sums first added in FP32).
+ * Every reserve is within about 15 x 2^-24 (8.9e-7) relative of its value on
+ * the FP64 inputs, whatever the projection length.  Products
  * RSV_SL_ANNUITY .. RSV_LAST_SURVIVOR (the reversionary and last-survivor
  * annuities through the reversionary identity of Section 4.2.1, every
  * valuation state); outputs RSV_OUT_V0 and RSV_OUT_SCEN_TOTAL; payment at the

@@ -38,7 +38,9 @@
 // rounded once each (and E of the JL product up to 3 u), so every reserve is
 // within about 14 u = 8.3e-7 of the value the exact arithmetic gives on the
 // FP64 inputs, whatever the projection length; the errors are independent
-// roundings, so typical errors are far smaller.
+// roundings, so typical errors are far smaller.  The two-level variants fold
+// once per 32-step block: the two spans' partial sums are first added in
+// FP32 (one more rounding, about 15 u = 8.9e-7 in all).
 //
 // Mapping.  A work item is a super-tile of NW tiles of P policies (the tiles
 // of one reduced model, consecutive in decreasing-length order) times one
@@ -153,7 +155,7 @@ __device__ __forceinline__ void defl_mbar_arrive(uint64_t* bar) {
 // Per-lane state of one item: P policies x M scenarios.
 template <int P, int M>
 struct DeflLane {
-    static constexpr bool packed = false;
+    static constexpr bool packed = false, two_level = false;
     float a0[P][M], a1[P][M];   // the current 16 steps' two FP32 accumulators
     float h[P][M], l[P][M];     // double-float sums of the folded spans
     __device__ __forceinline__ void start(int i, const float (&h0)[M]) {
@@ -182,7 +184,7 @@ struct DeflLane {
 // (h, l) of scenarios 2k (x) and 2k + 1 (y).
 template <int P, int M>
 struct DeflLaneX2 {
-    static constexpr bool packed = true;
+    static constexpr bool packed = true, two_level = false;
     static_assert(M % 2 == 0, "pairs of scenarios");
     f32x2 acc[P][M];
     f32x2 h[P][M / 2], l[P][M / 2];
@@ -243,7 +245,7 @@ __device__ __forceinline__ void defl_tmem_st32(uint32_t taddr, const uint32_t (&
 // holds 16 warps instead of 12.  The arithmetic is DeflLaneX2's: same bits.
 template <int P, int M>
 struct DeflLaneTM {
-    static constexpr bool packed = true;
+    static constexpr bool packed = true, two_level = false;
     static_assert(M % 2 == 0 && P * M == 16, "h and l of 16 chains in 32 columns");
     f32x2 acc[P][M];
     uint32_t taddr = 0;
@@ -269,6 +271,16 @@ struct DeflLaneTM {
                 L[i][m] = __uint_as_float(r[16 + i * M + m]);
             }
     }
+};
+
+// The sums in tensor memory, folded once per block: the first span of a
+// block parks its accumulators in 32 more columns (mid), and after the
+// second span mid is added to the accumulators (one FP32 rounding) before
+// the one fold of the block.  Each FP32 partial sum then carries 8 terms and
+// one addition (9 u instead of 8 u), for half the folds.
+template <int P, int M>
+struct DeflLaneTM2 : DeflLaneTM<P, M> {
+    static constexpr bool two_level = true;
 };
 
 // What a block needs of a warp's P slots.
@@ -463,8 +475,38 @@ __device__ __forceinline__ void defl_fold_all(DeflLaneTM<P, M>& st) {
     defl_tmem_st32(st.taddr, r);
 }
 
+template <int P, int M>
+__device__ __forceinline__ void defl_stash(DeflLaneTM2<P, M>& st) {   // mid = the accumulators
+    uint32_t r[32];
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            float x, y;
+            x2_unpack(st.acc[i][m], x, y);
+            r[2 * (i * M + m)] = __float_as_uint(x);
+            r[2 * (i * M + m) + 1] = __float_as_uint(y);
+        }
+    defl_tmem_st32(st.taddr + 32u, r);
+}
+template <int P, int M>
+__device__ __forceinline__ void defl_fold_all(DeflLaneTM2<P, M>& st) {
+    {
+        uint32_t r[32];
+        defl_tmem_ld32(st.taddr + 32u, r);
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                st.acc[i][m] = x2_add(x2_pack(__uint_as_float(r[2 * (i * M + m)]), __uint_as_float(r[2 * (i * M + m) + 1])),
+                                      st.acc[i][m]);
+    }
+    defl_fold_all(static_cast<DeflLaneTM<P, M>&>(st));
+}
+
 // One 16-step span (four groups, descending) from the staged rows r0+3 .. r0.
-template <int KIND, int P, int M, class Lane>
+// STAGE (two-level lanes): 1 parks the span's accumulators, 2 folds both spans.
+template <int KIND, int P, int M, int STAGE = 0, class Lane>
 __device__ __forceinline__ void defl_span(Lane& st, const DeflPol<P>& pp, const float4* __restrict__ tab,
                                           const float4* __restrict__ ring_b, int g0, int lane, bool check) {
 #pragma unroll
@@ -475,7 +517,8 @@ __device__ __forceinline__ void defl_span(Lane& st, const DeflPol<P>& pp, const 
         if (u == 3) defl_group<KIND, P, M, true>(st, pp, tab, d, g0 + u, check);
         else defl_group<KIND, P, M, false>(st, pp, tab, d, g0 + u, check);
     }
-    defl_fold_all(st);
+    if constexpr (STAGE == 1) defl_stash(st);
+    else defl_fold_all(st);
 }
 
 // One staged block (two spans, descending) of one item.  The packed lanes
@@ -488,11 +531,17 @@ __device__ __forceinline__ void defl_block(Lane& st, const DeflPol<P>& pp, const
     if (t_lo >= smax) return;                       // every policy of this warp has ended before the block
     const int g_lo = j * DEFL_G;
     if (t_lo + DEFL_KB > smin) {                    // some policy ends within or before the block
+        if constexpr (Lane::two_level) {
+            defl_span<KIND, P, M, 1>(st, pp, tab, ring_b + 4 * (32 * M), g_lo + 4, lane, true);
+            defl_span<KIND, P, M, 2>(st, pp, tab, ring_b, g_lo, lane, true);
+        } else {
 #pragma unroll 1
-        for (int h = 1; h >= 0; --h) defl_span<KIND, P, M>(st, pp, tab, ring_b + h * 4 * (32 * M), g_lo + 4 * h, lane, true);
+            for (int h = 1; h >= 0; --h)
+                defl_span<KIND, P, M>(st, pp, tab, ring_b + h * 4 * (32 * M), g_lo + 4 * h, lane, true);
+        }
     } else if constexpr (Lane::packed) {
-        defl_span<KIND, P, M>(st, pp, tab, ring_b + 4 * (32 * M), g_lo + 4, lane, false);
-        defl_span<KIND, P, M>(st, pp, tab, ring_b, g_lo, lane, false);
+        defl_span<KIND, P, M, Lane::two_level ? 1 : 0>(st, pp, tab, ring_b + 4 * (32 * M), g_lo + 4, lane, false);
+        defl_span<KIND, P, M, Lane::two_level ? 2 : 0>(st, pp, tab, ring_b, g_lo, lane, false);
     } else {
 #pragma unroll 1
         for (int h = 1; h >= 0; --h) defl_span<KIND, P, M>(st, pp, tab, ring_b + h * 4 * (32 * M), g_lo + 4 * h, lane, false);
@@ -538,18 +587,19 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
         done_items = 0;
         abort_flag = 0;
     }
-    if constexpr (X2 == 2) {   // 32 TMEM columns for each valuing warp of a lane quarter
+    constexpr uint32_t kCols = X2 == 3 ? 2 * kDeflTmemCols : kDeflTmemCols;
+    if constexpr (X2 >= 2) {   // 32 (64) TMEM columns for each valuing warp of a lane quarter
         if (warp == 0) {
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                              smem_u32(&tmem_slot)),
-                         "r"(kDeflTmemCols)
+                         "r"(kCols)
                          : "memory");
             asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
     __syncthreads();
-    if constexpr (X2 == 2) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if constexpr (X2 >= 2) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     if (warp == NW) {
         // ---------------- producer: lane 0 claims items and stages their blocks
@@ -606,10 +656,13 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
 
     // -------------------- consumers
     using Lane = typename std::conditional<
-        X2 == 2, DeflLaneTM<P, M>, typename std::conditional<X2 == 1, DeflLaneX2<P, M>, DeflLane<P, M>>::type>::type;
-    constexpr bool kTm = X2 == 2;
+        X2 == 3, DeflLaneTM2<P, M>,
+        typename std::conditional<X2 == 2, DeflLaneTM<P, M>,
+                                  typename std::conditional<X2 == 1, DeflLaneX2<P, M>, DeflLane<P, M>>::type>::type>::type;
+    constexpr bool kTm = X2 >= 2;
     Lane st;
-    if constexpr (kTm) st.taddr = tmem_slot + (((uint32_t)(warp & 3) * 32u) << 16) + (uint32_t)(warp >> 2) * 32u;
+    if constexpr (kTm)
+        st.taddr = tmem_slot + (((uint32_t)(warp & 3) * 32u) << 16) + (uint32_t)(warp >> 2) * (kCols / 4);
     int smin = 0, smax = 0, kind = K_ANN, stt = 0, chunk = 0;
     for (int k = 0;; ++k) {
         const int b = k % NBUF;
@@ -751,7 +804,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB) defl_kernel(const DeflArg
         asm volatile("bar.sync 1, %0;" ::"n"(NW * 32) : "memory");
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (warp == 0)
-            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(kDeflTmemCols)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(kCols)
                          : "memory");
     }
 }

@@ -3,11 +3,12 @@
 The form runs the backward recurrence in deflated units, U_t = U_{t+1} +
 D_{t+1} E_t (one FP32 fused multiply-add per chain-step), with the discount
 products D in FP64 per scenario and the life table in FP64, and compensated
-accumulation.  Its bound: every reserve within about 14 x 2^-24 = 8.3e-7 of
+accumulation.  Its bound: every reserve within about 15 x 2^-24 = 8.9e-7 of
 the value on the FP64 inputs (8 FP32 roundings per 8-term partial sum, one
-for joining the two partial sums, one rounding each of D and of the
-expected cash flow E, up to three for E of the reversionary annuity; the
-double-float fold is exact to 2^-48).  The tests hold it to the 1e-6 target
+for adding two spans' partial sums in the variants that fold once per
+block, one for joining the two partial sums, one rounding each of D and of
+the expected cash flow E, up to three for E of the reversionary annuity;
+the double-float fold is exact to 2^-48).  The tests hold it to the 1e-6 target
 of the compensated forms, and FP32 V0 adds its own rounding (2^-24).
 Error metric: rel = |V_gpu - V_ref| / max(|V_ref|, 1e-9 * amount).
 """
