@@ -105,7 +105,10 @@ def algorithmic_flops(pol, n_scen, horizon=0):
 def issued_flops(pol, form, n_scen, horizon=0, variant_name=""):
     cs = chain_steps_by_product(pol, horizon)
     per = dict(ISSUED_FLOPS[form])
-    if form == "f32defl":   # the JL expected cash flow, amortised over the lane's M scenarios
+    if form == "f32defl":
+        if variant_name.endswith(" tm2"):   # one fold per 32 steps: 2 x 30 + the spans' add (2) + join and fold (7)
+            per = {p: 69.0 / 32 for p in per}
+        # the JL expected cash flow, amortised over the lane's M scenarios
         m = re.search(r"xM(\d+)", variant_name)
         per[1] += 5.0 / (int(m.group(1)) if m else 4)
     return float(sum(per[p] * cs[p] for p in cs) * n_scen)
