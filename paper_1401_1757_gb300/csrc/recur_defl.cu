@@ -13,7 +13,7 @@ namespace rsv {
 // only with the sums in tensor memory).
 static const DeflVariant kDefl[] = {
     // the tuned best on the headline workload first: the default before tuning
-    RSV_DEFL_VARIANT(4, 4, 15, 8, 1, 3, "deflated P4xM4 nw15 buf8 x2 tm2"),
+    RSV_DEFL_VARIANT(4, 4, 15, 6, 1, 3, "deflated P4xM4 nw15 buf6 x2 tm2"),
     RSV_DEFL_VARIANT(4, 4, 15, 8, 1, 2, "deflated P4xM4 nw15 buf8 x2 tm"),
     RSV_DEFL_VARIANT(4, 4, 11, 8, 1, 1, "deflated P4xM4 nw11 buf8 x2"),
     RSV_DEFL_VARIANT(4, 4, 11, 8, 1, false, "deflated P4xM4 nw11 buf8"),
