@@ -7,24 +7,24 @@ namespace rsv {
 // one staging warp), staged blocks in flight NBUF, minimum resident CTAs per
 // SM, arithmetic: 0 scalar, 1 packed pairs, 2 packed pairs with each chain's
 // double-float sum in tensor memory, 3 the same folded once per 32-step
-// block).  One CTA per SM: each of an SM's four
-// schedulers has a quarter of the register file, so NW + 1 = 12 warps leave
-// 168 registers a thread, 16 warps 128 (which the packed accumulators fit
-// only with the sums in tensor memory).
+// block).  One CTA per SM: each of an SM's four schedulers has a quarter of
+// the register file, so NW + 1 = 12 warps leave 168 registers a thread, 16
+// warps 128 (which the packed accumulators fit only with the sums in tensor
+// memory).
 static const DeflVariant kDefl[] = {
     // the tuned best on the headline workload first: the default before tuning
     RSV_DEFL_VARIANT(4, 4, 15, 6, 1, 3, "deflated P4xM4 nw15 buf6 x2 tm2"),
     RSV_DEFL_VARIANT(4, 4, 15, 8, 1, 2, "deflated P4xM4 nw15 buf8 x2 tm"),
     RSV_DEFL_VARIANT(4, 4, 11, 8, 1, 1, "deflated P4xM4 nw11 buf8 x2"),
-    RSV_DEFL_VARIANT(4, 4, 11, 8, 1, false, "deflated P4xM4 nw11 buf8"),
-    RSV_DEFL_VARIANT(4, 4, 11, 4, 1, false, "deflated P4xM4 nw11 buf4"),
-    RSV_DEFL_VARIANT(4, 2, 15, 8, 1, false, "deflated P4xM2 nw15 buf8"),
-    RSV_DEFL_VARIANT(4, 2, 15, 8, 1, true, "deflated P4xM2 nw15 buf8 x2"),
-    RSV_DEFL_VARIANT(4, 4, 10, 8, 1, true, "deflated P4xM4 nw10 buf8 x2"),
-    RSV_DEFL_VARIANT(4, 4, 7, 8, 1, false, "deflated P4xM4 nw7 buf8"),
-    RSV_DEFL_VARIANT(4, 4, 7, 8, 1, true, "deflated P4xM4 nw7 buf8 x2"),
-    RSV_DEFL_VARIANT(2, 4, 15, 6, 1, false, "deflated P2xM4 nw15 buf6"),
-    RSV_DEFL_VARIANT(2, 4, 15, 6, 1, true, "deflated P2xM4 nw15 buf6 x2"),
+    RSV_DEFL_VARIANT(4, 4, 11, 8, 1, 0, "deflated P4xM4 nw11 buf8"),
+    RSV_DEFL_VARIANT(4, 4, 11, 4, 1, 0, "deflated P4xM4 nw11 buf4"),
+    RSV_DEFL_VARIANT(4, 2, 15, 8, 1, 0, "deflated P4xM2 nw15 buf8"),
+    RSV_DEFL_VARIANT(4, 2, 15, 8, 1, 1, "deflated P4xM2 nw15 buf8 x2"),
+    RSV_DEFL_VARIANT(4, 4, 10, 8, 1, 1, "deflated P4xM4 nw10 buf8 x2"),
+    RSV_DEFL_VARIANT(4, 4, 7, 8, 1, 0, "deflated P4xM4 nw7 buf8"),
+    RSV_DEFL_VARIANT(4, 4, 7, 8, 1, 1, "deflated P4xM4 nw7 buf8 x2"),
+    RSV_DEFL_VARIANT(2, 4, 15, 6, 1, 0, "deflated P2xM4 nw15 buf6"),
+    RSV_DEFL_VARIANT(2, 4, 15, 6, 1, 1, "deflated P2xM4 nw15 buf6 x2"),
 };
 
 const DeflVariant* variants_defl(int* n) {
