@@ -652,8 +652,12 @@ rsv_status rsv_selftest_generator_math(int32_t device, void *cuda_stream, const 
  * counterpart.  Blocks until done.  Errors: RSV_E_ARG, RSV_E_CUDA, RSV_E_NOMEM. */
 rsv_status rsv_probe_fma_peak(int32_t device, void *cuda_stream, int32_t fp64, double *tflops);
 
-/* Kernel variants of a form (policies x scenarios per thread, CTA size):
- * how many there are, and a printable description of one. */
+/* Kernel variants of a form (policies x scenarios per thread, CTA size; for
+ * the deflated form also the arithmetic: scalar, packed FP32 pairs "x2", the
+ * double-float sums in tensor memory "tm", and one fold per 32-step block
+ * "tm2"): how many there are, and a printable description of one.  Variants
+ * of one form give the same reserves within the form's bound; those that
+ * differ only in shape (not in the summation order) give the same bits. */
 int32_t rsv_variant_count(int32_t form);
 const char *rsv_variant_name(int32_t form, int32_t variant);
 
