@@ -528,8 +528,9 @@ def oracle_runs(pol, tab, v, horizon, runs, warm=1):
 
 
 def cpu_full_configs(tab, runs, with_c2):
-    """The oracle on whole configurations (the survey's CPU protocol: minimum
-    and median of ``runs`` timed runs after one warm-up, all host cores):
+    """The oracle on whole configurations (the paper's timing method, Section
+    5.2.1: minimum and median of ``runs`` timed runs after one warm-up, all
+    host cores):
     configuration 1 always (1,000 annuities, one flat scenario, a few ms),
     configuration 2 on request (10^5 policies x 1,000 scenarios x 1,200
     steps, about 80 s a run on 16 cores)."""
