@@ -333,8 +333,14 @@ struct Tile {
     __device__ __forceinline__ void step(int t, const VP& vv) {
         if constexpr (PAYF) {
             step_pay<CHECK>(t, vv);
-            return;
+        } else {
+            step_end<CHECK>(t, vv);
         }
+    }
+
+    // payment at the end of the step
+    template <bool CHECK>
+    __device__ __forceinline__ void step_end(int t, const VP& vv) {
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             if (CHECK && t >= Sp[i]) continue;
