@@ -227,7 +227,7 @@ rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
         };
         {
             const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-            const int T = std::max(1, std::min(std::min(hw, 16), L.n_tiles / 512));
+            const int T = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::min(hw, 16), n_slots / 16384));
             run_parts(T, [&](int k) {
                 fill((int)((long long)L.n_tiles * k / T), (int)((long long)L.n_tiles * (k + 1) / T));
             });

@@ -439,7 +439,8 @@ rsv_status rsv::build_layout(rsv_ctx* c, int P, int horizon, int max_steps, int 
     };
     {
         const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-        const int T = std::max(1, std::min(std::min(hw, 16), n_tiles / 4096));
+        // by slots, not tiles: wide tiles (the deflated form's 60 policies) are few
+        const int T = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::min(hw, 16), n_slots / 16384));
         run_parts(T, [&](int k) {
             fill((int)((long long)n_tiles * k / T), (int)((long long)n_tiles * (k + 1) / T));
         });
