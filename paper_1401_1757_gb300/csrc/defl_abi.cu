@@ -176,8 +176,10 @@ rsv_status compute_deflated(rsv_ctx* c, const rsv_opts* o, rsv_out* out) {
             for (int k = 0; k < W; ++k) {
                 const SlotRec& r = L.h_s2[(size_t)f * W + k];
                 DeflSlot d{};
-                const int tb1 = r.idx1 / L.tab_pad, a1 = r.idx1 % L.tab_pad;
-                const int tb2 = r.idx2 / L.tab_pad, a2 = r.idx2 % L.tab_pad;
+                // (table, age) of each life; no division for the first table
+                const int tp = L.tab_pad;
+                const int tb1 = r.idx1 < tp ? 0 : r.idx1 / tp, a1 = r.idx1 - tb1 * tp;
+                const int tb2 = r.idx2 < tp ? 0 : r.idx2 / tp, a2 = r.idx2 - tb2 * tp;
                 // survivors are zero from the table's length on, deaths one step
                 // later (everyone left dies in the month at the limiting age)
                 const int z1 = (int)c->tab[tb1].size() + (kind == K_ASS ? 1 : 0), z2 = (int)c->tab[tb2].size();
