@@ -64,6 +64,13 @@
 // of chains (scenarios m and m + 1): the ordering by max and min per chain (the
 // terms are non-negative), then the ordered Fast2Sum on the pair, so the X2
 // variants give the same bits as the scalar ones.
+//
+// Sums in tensor memory (TM variants).  A chain's double-float sum is touched
+// once per fold, so the packed variants can keep it in the warp's columns of
+// tensor memory (tcgen05.ld/st) instead of registers: 128 registers a thread,
+// 16 warps a CTA instead of 12, the same bits.  The two-level variant (TM2)
+// also parks the first span's accumulators of each 32-step block there and
+// folds once per block.
 #pragma once
 
 #include <type_traits>
